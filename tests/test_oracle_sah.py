@@ -1,0 +1,216 @@
+"""Pins of the step-by-step oracle (oracle/sah.py) against the paper's identities,
+lemmas and hand-worked examples, and against the plain-definition oracle."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import sah
+import workload
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden():
+    with open(os.path.join(GOLDEN, "sah_steps_2d.json")) as f:
+        return json.load(f)
+
+
+def test_golden_sat_eq6_to_eq8():
+    g = _golden()["sat"]
+    P = np.array(g["P"], float)
+    c = P.mean(axis=0)
+    R = max(np.linalg.norm(p - c) for p in P)
+    assert np.allclose(c, g["c"]) and np.isclose(R, g["R"])
+    I0 = sah.sat_item(P[0], c, R)
+    Uu = sah.sat_user(np.array(g["u"], float), R)
+    # sqrt of a rounding residue of R^2 - ||p - c||^2 is ~1e-8, hence atol
+    assert np.allclose(I0, g["I0"], atol=1e-7) and np.allclose(Uu, g["Uu"])
+    assert np.isclose(I0 @ Uu / (R * R), g["cos"])
+
+
+def test_golden_lemma2_lemma3_tight():
+    g = _golden()
+    l2, l3 = g["lemma2"], g["lemma3"]
+    b2 = sah.node_upper_bound(np.array(l2["q"], float), np.array(l2["c"], float), l2["omega"])
+    assert np.isclose(b2, l2["bound"])
+    assert np.isclose(np.dot(l2["tight_user"], l2["q"]), b2)
+    b3 = sah.vector_upper_bound(np.array(l3["q"], float), np.array(l3["c"], float), l3["theta"])
+    assert np.isclose(b3, l3["bound"])
+    assert np.isclose(np.dot(l3["tight_user"], l3["q"]), b3)
+
+
+def test_golden_partitions_alg1():
+    g = _golden()["partitions"]
+    norms = np.array(g["norms"], float)
+    P = norms[:, None] * np.eye(1, 3, 0)          # vectors with the given norms
+    A = workload.srp_matrix(4, 4).astype(np.float64)
+    ix = sah.sa_alsh_index(P, norms, 0, g["b"], A, 1, 4)
+    assert [len(s) for s in ix.items] == g["sizes"]
+    assert np.allclose(ix.M, g["M"])
+
+
+def test_golden_cone_tree_alg3():
+    g = _golden()["cone_tree"]
+    ang = np.deg2rad(g["angles_deg"])
+    Uhat = np.stack([np.cos(ang), np.sin(ang)], axis=1)
+    for seed in range(8):
+        leaves = sah.cone_tree(Uhat, np.arange(len(ang)), g["N0"], seed)
+        assert sorted(sorted(l.members.tolist()) for l in leaves) == g["leaves"]
+
+
+def test_sat_norms_and_eq8_identity_random():
+    rng = np.random.default_rng(0)
+    P = rng.standard_normal((50, 7)) * rng.lognormal(0, 0.5, (50, 1))
+    c = P.mean(axis=0)
+    R = max(np.linalg.norm(p - c) for p in P)
+    for _ in range(20):
+        u = rng.standard_normal(7)
+        Uu = sah.sat_user(u, R)
+        assert np.isclose(np.linalg.norm(Uu), R)
+        for p in P[:10]:
+            I = sah.sat_item(p, c, R)
+            assert np.isclose(np.linalg.norm(I), R)
+            assert np.isclose(I @ Uu / (R * R), (p - c) @ u / (R * np.linalg.norm(u)))
+        # Fact 1: the shift does not move the argmax over items
+        scores_sat = [sah.sat_item(p, c, R) @ Uu for p in P]
+        assert int(np.argmax(scores_sat)) == int(np.argmax(P @ u))
+
+
+def test_srp_collision_probability_eq2():
+    rng = np.random.default_rng(1)
+    d, N = 16, 10000
+    A = rng.standard_normal((N, d))
+    for target in (0.3, 1.0, 2.0, 2.8):
+        x = rng.standard_normal(d)
+        x /= np.linalg.norm(x)
+        y0 = rng.standard_normal(d)
+        y0 -= (y0 @ x) * x
+        y0 /= np.linalg.norm(y0)
+        y = np.cos(target) * x + np.sin(target) * y0
+        delta = sah.angle(x, y)
+        hit = np.mean(sah.srp_bits(A, x) == sah.srp_bits(A, y))
+        p = 1 - delta / np.pi
+        assert abs(hit - p) < 4 * np.sqrt(p * (1 - p) / N) + 1e-9
+
+
+def _random_cone(rng, d, m, omega):
+    c = rng.standard_normal(d)
+    c /= np.linalg.norm(c)
+    out = []
+    while len(out) < m:
+        v = rng.standard_normal(d)
+        v /= np.linalg.norm(v)
+        if sah.angle(v, c) <= omega:
+            out.append(v)
+        else:  # pull towards the centre until inside
+            t = rng.uniform(0, 1)
+            w = t * c + (1 - t) * v
+            w /= np.linalg.norm(w)
+            if sah.angle(w, c) <= omega:
+                out.append(w)
+    return c, np.array(out)
+
+
+def test_lemma2_lemma3_hold_on_random_cones():
+    rng = np.random.default_rng(2)
+    for trial in range(40):
+        d = 3 + trial % 6
+        omega = rng.uniform(0.1, 2.5)
+        c, X = _random_cone(rng, d, 30, omega)
+        mean = X.mean(axis=0)
+        om = max(sah.angle(x, mean) for x in X)
+        for _ in range(5):
+            q = rng.standard_normal(d) * rng.lognormal()
+            nb = sah.node_upper_bound(q, mean, om)
+            assert (X @ q).max() <= nb + 1e-12
+            for x in X[:8]:
+                vb = sah.vector_upper_bound(q, mean, sah.angle(x, mean))
+                assert x @ q <= vb + 1e-12
+                assert vb <= np.linalg.norm(q) + 1e-12       # never looser than Cauchy-Schwarz
+
+
+def test_cone_tree_invariants_alg3():
+    W = workload.make("c2", m=3000, n=10)
+    U = W.U.astype(np.float64)
+    Uhat = U / np.linalg.norm(U, axis=1, keepdims=True)
+    leaves = sah.cone_tree(Uhat, np.arange(W.m), 20, seed=5)
+    allm = np.concatenate([l.members for l in leaves])
+    assert np.array_equal(np.sort(allm), np.arange(W.m))          # disjoint cover
+    for l in leaves:
+        assert 1 <= len(l.members) <= 20
+        assert np.allclose(l.center, Uhat[l.members].mean(axis=0))
+        assert np.all(l.theta <= l.omega + 1e-12)
+
+
+def test_alg1_partition_invariants():
+    W = workload.make("c2", m=10, n=2000)
+    P = W.P.astype(np.float64)
+    nrm = np.linalg.norm(P, axis=1)
+    order = np.argsort(-nrm, kind="stable")
+    A = workload.srp_matrix(16, W.d + 1).astype(np.float64)
+    ix = sah.sa_alsh_index(P[order], nrm[order], 200, 0.5, A, 4, 4)
+    cover = np.concatenate(ix.items)
+    assert np.array_equal(cover, np.arange(200, 2000))
+    assert np.all(np.diff(ix.M) < 0)
+    for S, M in zip(ix.items, ix.M):
+        assert np.all(nrm[order][S] <= M) and np.all(nrm[order][S] > 0.5 * M)
+
+
+def test_alg4_bound_chain():
+    W = workload.make("c2", m=600, n=800)
+    ix = sah.sah_index(W.P, W.U, kmax=20, N0=20, p_prime=60)
+    Uhat = ix.Uhat
+    T = oracle.tau(Uhat.astype(np.float32), W.P, 20)     # tau of the unit users (fp32 inputs)
+    for bi, blk in enumerate(ix.blocks):
+        assert np.all(ix.LB[bi] <= ix.L[blk.members] + 1e-12)
+    assert np.all(ix.L <= T + 1e-6)                               # P' scores <= tau over P
+    assert np.all(ix.norms[:20][None, :] >= T - 1e-6)             # ||p_k|| >= tau(k), unit u
+
+
+def test_alg5_exact_mode_equals_definition():
+    W = workload.make("c2", m=700, n=900)
+    for p_prime in (20, 80, 900):
+        ix = sah.sah_index(W.P, W.U, kmax=20, N0=20, p_prime=p_prime, seed=3)
+        for qi in W.query_idx[:3]:
+            q = W.P[qi]
+            for k in (1, 5, 20, 25):
+                got = sah.sah_query(ix, q, k, "exact")
+                ref = oracle.rkmips(W.U, W.P, q, k)
+                assert np.array_equal(got, ref), (p_prime, k)
+
+
+def test_alg5_saalsh_mode_superset_and_full_probe_is_exact():
+    W = workload.make("c2", m=300, n=600)
+    code_bits, n_tables = 4, 3
+    A = workload.srp_matrix(n_tables * code_bits, W.d + 1, seed=4).astype(np.float64)
+    ix = sah.sah_index(W.P, W.U, kmax=10, N0=20, p_prime=40, A=A, n_tables=n_tables,
+                       code_bits=code_bits, seed=1)
+    for qi in W.query_idx[:3]:
+        q = W.P[qi]
+        for k in (1, 10):
+            exact = set(oracle.rkmips(W.U, W.P, q, k).tolist())
+            approx = set(sah.sah_query(ix, q, k, "saalsh", probe_radius=0).tolist())
+            assert exact <= approx                                   # every "no" is sound
+            full = set(sah.sah_query(ix, q, k, "saalsh", probe_radius=code_bits).tolist())
+            assert full == exact
+
+
+def test_zero_norm_users_always_answer_yes():
+    W = workload.make("c1", m=50, n=60)
+    U = W.U.copy()
+    U[[3, 17]] = 0.0
+    ix = sah.sah_index(W.P, U, kmax=10, N0=8, p_prime=20)
+    got = sah.sah_query(ix, W.P[W.query_idx[0]], 1)
+    assert {3, 17} <= set(got.tolist())
+    assert {3, 17} <= set(oracle.rkmips(U, W.P, W.P[W.query_idx[0]], 1).tolist())
+
+
+def test_splitmix64_reference_values():
+    # SplitMix64 (Steele, Lea, Flood 2014) from state 0: the first output of the
+    # generator whose state starts at 0 is 0xE220A8397B1DCDAF.
+    assert sah.splitmix64(0) == 0xE220A8397B1DCDAF
+    # second output: state advanced by the golden gamma once more
+    assert sah.splitmix64(0x9E3779B97F4A7C15) == 0x6E789E6AA1B965F4
