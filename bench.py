@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""RkMIPS throughput on one GB300 (exact mode, results identical to the FP64 oracle).
+
+Workload (default): n = 17,770 items, m = 480,000 users, d = 50, rank-50 factor-model
+vectors with log-normal(0, 0.7) norms and 5% of the items at 3x norm (seed 0); 100 queries
+drawn from the items, each asked at k in {1, 5, 10, 20, 50}: one step = one batch of 500
+RkMIPS queries through the whole query path (block pass, user pass, kMIPS decisions,
+double-precision re-score, compaction).  The index (Alg. 4) is built once, before timing.
+
+  value  queries/s with Q, ks and the output in HBM (CUDA events on the call's stream)
+  e2e    queries/s through the same C-ABI call with pinned host buffers (copies inside)
+  roofline   the stage that dominates the step against its bound
+  cpu_baseline  the FP64 oracle on the host cores, on a bounded sample of users
+
+With --impl reference the FP64 oracle itself is timed (the CPU reference arm).
+Multi-GPU (torchrun): every rank holds a replica of the index and answers its own batch
+(no collective on the data path); value = all ranks' queries / max time (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workload  # noqa: E402
+
+METRIC = "RkMIPS queries/s (exact, F1=1 vs FP64 oracle)"
+UNIT = "queries/s"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--threshold", default="full", choices=["full", "paper"],
+                    help="full: |P'| = n (exact thresholds); paper: |P'| = 4 k_max")
+    ap.add_argument("--leaf-size", type=int, default=256)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- roofline bookkeeping
+def stage_algorithmic(stats, d, n_users, distinct_k):
+    """Algorithmic FLOPs and bytes of each stage of one call (units in the design notes)."""
+    out = {}
+    out["block_pass"] = dict(flops=4.0 * d * stats["block_pairs_total"],
+                             bytes=stats["n_blocks"] * (4.0 * d + 12))
+    out["user_pass"] = dict(flops=2.0 * d * stats["users_scored"],
+                            bytes=stats["users_in_kept_blocks"] * (4.0 * d + 20) + 4.0 * distinct_k * n_users)
+    out["kmips_decision"] = dict(flops=2.0 * d * stats["items_scanned"],
+                                 bytes=stats["survivors"] * (4.0 * d + 12))
+    words = (n_users + 31) // 32
+    out["compaction"] = dict(flops=0.0, bytes=stats["queries"] * words * 4.0 * 3 + 4.0 * stats["results"])
+    return out
+
+
+STAGE_NAMES = ["prep", "block_pass", "user_pass", "kmips_decision", "compaction"]
+STAGE_KERNELS = {"block_pass": "block_filter_kernel", "user_pass": "user_scan_kernel",
+                 "kmips_decision": "verify_exact_kernel", "compaction": "bitmap_emit_kernel"}
+
+
+def kernel_traffic(kernel: str):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel's source is
+    unchanged since it was taken (matched by the source file's hash)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(kernel)
+        src = os.path.join(ROOT, "paper_2211_12751_gb300", "csrc", rec["source"])
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if h == rec["source_sha256_16"]:
+            return rec["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------- CPU oracle timing
+def oracle_sample_run(W, Q, K, qrows, budget_s):
+    """Times the FP64 oracle on a seeded sample of users for the batch's distinct queries
+    (one count per query answers all its k values).  Returns qps scaled to all m users,
+    the sample description, the threads used and the memberships it computed."""
+    import oracle
+    threads = oracle.threads()
+    users_probe = workload.sample_rows(W.m, 256, seed=21)
+    t0 = time.perf_counter()
+    oracle.count_above(W.U, W.P, Q[0], users_probe)
+    t_probe = max(time.perf_counter() - t0, 1e-4)
+    per_user_query = t_probe / len(users_probe)
+    distinct = np.unique(qrows)
+    nq = max(1, min(len(distinct), 4))
+    users = int(min(W.m, max(256, budget_s / (per_user_query * nq))))
+    sample = workload.sample_rows(W.m, users, seed=22)
+    memberships = {}
+    t0 = time.perf_counter()
+    for qi in distinct[:nq]:
+        c = oracle.count_above(W.U, W.P, W.P[W.query_idx[qi]], sample)
+        memberships[int(qi)] = c
+    t = time.perf_counter() - t0
+    per_q = len(W.ks) if W.every_k else 1
+    queries_equiv = nq * per_q * (len(sample) / W.m)
+    return dict(value=queries_equiv / t, seconds=t, threads=threads, users=len(sample), nq=int(nq),
+                sample=sample, memberships=memberships)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    W = workload.make(args.workload)
+    Q, K, qrows = W.requests()
+    import oracle
+    budget = 4.0
+    vals = []
+    info = None
+    for step in range(args.warmup + args.steps):
+        info = oracle_sample_run(W, Q, K, qrows[(step % len(np.unique(qrows))):], budget)
+        if step >= args.warmup:
+            vals.append(info["value"])
+    v = float(np.mean(vals))
+    sample = (f"per step: FP64 brute-force counts of {info['users']} seeded users (of {W.m}) for "
+              f"{info['nq']} queries, each count answering the query's {len(W.ks)} k values; "
+              f"scaled to all users")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_block(W, args),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": info["threads"], "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_block(W, args):
+    return {"workload": f"{W.name}: n={W.n} items, m={W.m} users, d={W.d}, mf rank-50 lognormal(0,0.7), "
+                        f"5% items x3, seed 0; {len(W.query_idx)} item queries x k in {list(map(int, W.ks))}",
+            "queries_per_step": int(len(W.query_idx) * (len(W.ks) if W.every_k else 1)),
+            "threshold_mode": args.threshold, "leaf_size": args.leaf_size, "k_max": 50,
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+# ---------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, world, local = dist_env()
+    import torch
+    import paper_2211_12751_gb300 as sah
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    peaks, peak_kind = load_peaks()
+    sah.load()
+    W = workload.make(args.workload)
+    Q, K, qrows = W.requests()
+    nq = len(K)
+    distinct_k = len(set(K.tolist()))
+    stream = torch.cuda.current_stream()
+
+    def build(threshold):
+        pp = (1 << 30) if threshold == "full" else 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ix = sah.Index(W.U, W.P, k_max=50, leaf_size=args.leaf_size, p_prime=pp, seed=0, stream=stream)
+        torch.cuda.synchronize()
+        return ix, time.perf_counter() - t0
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    Qd = torch.from_numpy(Q).to(dev)
+    Kd = torch.from_numpy(K).to(dev)
+
+    def measure(ix, steps, warmup, timing=True):
+        host = ix.rkmips_batch(Q, K)                    # sizes the output once
+        total = sum(len(h) for h in host)
+        out = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
+        offs = torch.empty(nq + 1, dtype=torch.int64, device=dev)
+        for _ in range(warmup):
+            ix.rkmips_batch_device(Qd, Kd, out, offs, stream=stream)
+        ix.set_timing(timing)
+        times, stage_ms, launches = [], np.zeros(8), np.zeros(8)
+        st_last = None
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            ix.rkmips_batch_device(Qd, Kd, out, offs, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            st_last = ix.stats()
+            stage_ms += np.array(st_last["stage_ms"])
+            launches += np.array(st_last["stage_launches"])
+        ix.set_timing(False)
+        return host, times, stage_ms / steps, launches / steps, st_last, total
+
+    ix, build_s = build(args.threshold)
+    if world > 1:
+        torch.distributed.barrier()
+    with ClockSampler(local) as clk:
+        host, times, stage_ms, launches, st, total = measure(ix, args.steps, max(args.warmup, 3))
+    clocks = clk.summary()
+    t_step_ms = float(np.mean(times))
+    t_max = torch.tensor([sum(times)], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    value = nq * args.steps * world / (float(t_max.item()) / 1e3)
+
+    # e2e: pinned host buffers through the same C-ABI call (copies inside the timed call)
+    Qh = torch.from_numpy(Q).pin_memory()
+    Kh = torch.from_numpy(K).pin_memory()
+    outh = torch.empty(max(total, 1), dtype=torch.int32).pin_memory()
+    offh = torch.empty(nq + 1, dtype=torch.int64).pin_memory()
+    e2e_times = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s = ix.raw_batch(Qh.data_ptr(), nq, Kh.data_ptr(), None, 0, outh.data_ptr(), outh.numel(),
+                         offh.data_ptr(), stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        assert s == 0, s
+        if i >= args.warmup:
+            e2e_times.append(e0.elapsed_time(e1))
+    e2e_value = nq * args.steps * world / (sum(e2e_times) / 1e3)
+    h2d = Q.nbytes + K.nbytes
+    d2h = (nq + 1) * 8 + total * 4
+    got_e2e = offh.numpy().copy()
+    assert got_e2e[-1] == total
+
+    # roofline of the dominant stage
+    alg = stage_algorithmic(st, W.d, W.m, distinct_k)
+    dom_i = int(np.argmax(stage_ms[1:5])) + 1
+    dom = STAGE_NAMES[dom_i]
+    a = alg[dom]
+    dur_s = stage_ms[dom_i] / 1e3 / max(launches[dom_i], 1)
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    t_alu = a["flops"] / (fp32_peak * 1e12)
+    t_hbm = a["bytes"] / (peaks["hbm_gbs"] * 1e9)
+    per_launch = lambda x: x / max(launches[dom_i], 1)
+    if t_alu >= t_hbm:
+        roof = {"bound": "alu", "achieved": per_launch(a["flops"]) / dur_s / 1e12, "peak": fp32_peak,
+                "unit": "TFLOP/s", "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+    else:
+        roof = {"bound": "hbm", "achieved": per_launch(a["bytes"]) / dur_s / 1e9, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = kernel_traffic(STAGE_KERNELS.get(dom, ""))
+    roof["kernel"] = STAGE_KERNELS.get(dom, dom)
+    roof["stage"] = dom
+    roof["launch_ms"] = dur_s * 1e3
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_block(W, args),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(round(float(np.sum(launches)) * args.steps)),
+            "roofline": roof,
+            "stages_ms": {nm: float(stage_ms[i]) for i, nm in enumerate(STAGE_NAMES)},
+            "stage_counts": {k: st[k] for k in ("block_pairs_total", "block_pairs_kept", "users_in_kept_blocks",
+                                                "users_scored", "users_yes_early", "survivors", "fp64_rescored",
+                                                "items_scanned", "results")},
+            "index_build_s": build_s, "clocks": clocks,
+            "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99)),
+                           "per": "batch of %d queries" % nq}}
+
+    if not args.no_variants and rank == 0:
+        other = "paper" if args.threshold == "full" else "full"
+        ix2, b2 = build(other)
+        _, t2, sm2, l2, st2, _ = measure(ix2, max(3, args.steps // 2), 3, timing=False)
+        line["variants"] = {f"threshold_{other}": {"value": nq * len(t2) / (sum(t2) / 1e3), "index_build_s": b2,
+                                                   "ms_per_step": float(np.mean(t2)),
+                                                   "survivors": st2["survivors"], "items_scanned": st2["items_scanned"]}}
+        ix2.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = oracle_sample_run(W, Q, K, qrows, args.cpu_seconds)
+        # the oracle's memberships on its sample, compared with the GPU's answers
+        agree = True
+        for qi, counts in cb["memberships"].items():
+            for r in np.flatnonzero(qrows == qi):
+                g = set(host[r].tolist())
+                mem = np.array([u in g for u in cb["sample"].tolist()])
+                agree &= bool(np.array_equal(mem, counts < K[r]))
+        line["cpu_baseline"] = {"value": cb["value"], "unit": UNIT, "cores": cb["threads"], "kind": "oracle",
+                                "sample": (f"FP64 brute-force counts of {cb['users']} seeded users (of {W.m}) for "
+                                           f"{cb['nq']} queries, each count answering its {len(W.ks)} k values; "
+                                           f"{cb['seconds']:.1f} s, scaled to all users"),
+                                "gpu_matches_oracle_on_sample": agree}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,149 @@
+/*
+ * libsah: Reverse k-Maximum Inner Product Search (RkMIPS) with SAH on one GB300.
+ *
+ * SAH (Shifting-aware Asymmetric Hashing, arXiv 2211.12751): a Cone-Tree over the
+ * user vectors prunes users block by block (Lemma 2) and one by one (Lemma 3); per-user
+ * lower-bound arrays from the largest-norm items answer "no" early (Alg. 4, Alg. 5);
+ * the remaining users run a per-user kMIPS decision, either exact or through SA-ALSH
+ * (Alg. 1, Alg. 2).
+ *
+ * Problem (Def. 1): for a query item q, an integer k >= 1, items P (n x d) and users
+ * U (m x d), return every user u such that q is among the k largest inner products of
+ * u over P u {q}.  Ties keep q: u is returned iff #{p in P : <u,p> > <u,q>} < k (Alg. 2
+ * answers "no" only when <u,q> < phi; Alg. 5 prunes only when <u,q> < L and answers
+ * "yes" when ||p_k|| <= <u,q>).
+ *
+ * Conventions shared by every call:
+ *  - Vectors are float32, row-major, rows of exactly d floats (no padding).
+ *  - Result ids are row indices of the caller's U, sorted ascending.
+ *  - Errors are returned as sah_status; nothing throws across the ABI.  The text of
+ *    the last error of the calling thread is available from sah_last_error().
+ *  - An index is not thread-safe: calls on one index must not overlap, except through
+ *    the server API, which serialises them itself.
+ *  - cuda_stream is a cudaStream_t (NULL = the legacy default stream).  Calls that
+ *    return results to the host synchronise that stream before they return.
+ *  - The exact mode returns, for every user, the decision of the count rule evaluated
+ *    in double precision with the sum taken over i = 0..d-1 in order: scores are first
+ *    computed in the index's working precision with a rigorous a-priori error bound,
+ *    and every decision the bound leaves open is recomputed in that double-precision
+ *    order on the GPU.
+ */
+#ifndef SAH_H_
+#define SAH_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sah_index sah_index;   /* opaque; owns every device buffer it uses */
+typedef struct sah_server sah_server; /* opaque continuous-batching server */
+
+typedef enum {
+  SAH_OK = 0,
+  SAH_ERR_ARG = 1,              /* invalid argument (null pointer, k < 1, bad sizes, non-finite input) */
+  SAH_ERR_OOM = 2,              /* a device allocation failed; the index stays usable */
+  SAH_ERR_CUDA = 3,             /* a CUDA call failed; see sah_last_error() */
+  SAH_ERR_BUFFER_TOO_SMALL = 4, /* result buffer too small: required size reported, nothing written */
+  SAH_ERR_DEVICE_TIMEOUT = 5,   /* a bounded device-side wait ran out; results are not valid */
+  SAH_ERR_BUSY = 6,             /* server: the request has not finished yet */
+  SAH_ERR_UNSUPPORTED = 7       /* the parameters ask for something this build does not do */
+} sah_status;
+
+typedef enum { SAH_EXACT = 0, SAH_SAALSH = 1 } sah_mode;
+
+/* Working precision of the user x query and user x item scores.  Every mode is exact
+ * in SAH_EXACT: a lower precision only widens the error band that is re-scored. */
+typedef enum { SAH_FP32 = 0, SAH_BF16 = 1, SAH_FP8 = 2 } sah_precision;
+
+typedef struct {
+  int32_t k_max;        /* length of the lower-bound arrays L_u^1..k_max (Alg. 4); 1..64; paper: 50 */
+  int32_t leaf_size;    /* N_0, the Cone-Tree's maximum leaf size (Alg. 3); 1..256; paper: 20 */
+  float b;              /* SA-ALSH interval ratio in (0,1) (Alg. 1); paper: 0.5 */
+  int32_t n_tables;     /* K, SimHash tables per SA-ALSH partition (Alg. 1); paper: 128 */
+  int32_t code_bits;    /* SRP bits concatenated into one table's code, 1..16 */
+  int32_t p_prime;      /* |P'|: items behind the lower bounds (Alg. 4); <= 0 means 4 * k_max;
+                           >= n makes the lower bounds the exact k-th largest scores */
+  int32_t precision;    /* sah_precision */
+  int32_t probe_radius; /* SA-ALSH: Hamming radius probed around the user's code, 0..code_bits */
+  uint64_t seed;        /* Cone-Tree random points (Alg. 3) and, when srp is NULL, the SRP matrix */
+  const float* srp;     /* optional host matrix (n_tables * code_bits) x (d + 1) of SRP projection
+                           vectors (Eq. 1); NULL draws it from seed.  Copied at build time. */
+} sah_params;
+
+/* Fills *p with the paper's parameters (k_max 50, N_0 20, b 0.5, K 128) and the build's
+ * defaults for the rest (code_bits 16, p_prime 4 * k_max, FP32, probe radius 0, seed 0). */
+void sah_default_params(sah_params* p);
+
+/* Alg. 4 (SAH Indexing): item norms and descending-norm order, lower-bound arrays over
+ * the first |P'| items, the SA-ALSH index on the other items (Alg. 1), the Cone-Tree over
+ * the users (Alg. 3) with its leaves as blocks, and the per-block lower bounds.
+ *  U: m x d users, P: n x d items; host pointers unless inputs_on_device != 0, in which
+ *  case both are device pointers on the current device.  The index copies them; the
+ *  caller may free its arrays once the call returns.  *out receives the index (NULL on
+ *  error).  Errors: SAH_ERR_ARG for m < 1, n < 1, d < 1, d > 1024, parameters out of
+ *  range or a non-finite input; SAH_ERR_OOM; SAH_ERR_CUDA. */
+sah_status sah_build_index(const float* U, int64_t m, const float* P, int64_t n, int32_t d,
+                           int32_t inputs_on_device, const sah_params* params,
+                           void* cuda_stream, sah_index** out);
+
+/* Alg. 5 (SAH query) for one query: q has d floats (host pointer), k >= 1, mode is a
+ * sah_mode.  Writes the ascending user ids to out_ids (host, cap entries) and their
+ * number to *out_count.  k > n returns every user.  If cap is too small, *out_count is
+ * set to the required size, nothing is written and SAH_ERR_BUFFER_TOO_SMALL returned. */
+sah_status sah_rkmips(sah_index* index, const float* q, int32_t k, int32_t mode,
+                      int32_t* out_ids, int64_t cap, int64_t* out_count, void* cuda_stream);
+
+/* Alg. 5 for nq queries in one pass (mixed k and modes).  Q: nq x d; ks, modes: nq each;
+ * out_offsets: nq + 1 entries, query j's ids are out_ids[out_offsets[j] .. out_offsets[j+1]).
+ * If buffers_on_device != 0, Q, ks, modes, out_ids and out_offsets are device pointers
+ * (the call still synchronises the stream once, to size the output); otherwise host
+ * pointers, and the host <-> device copies happen inside the call.  modes may be NULL
+ * (all exact).  If the total exceeds cap, out_offsets[nq] is set to the required total
+ * (and, for host buffers, out_offsets[0..nq] are filled), no id is written and
+ * SAH_ERR_BUFFER_TOO_SMALL is returned. */
+sah_status sah_rkmips_batch(sah_index* index, const float* Q, int32_t nq, const int32_t* ks,
+                            const int32_t* modes, int32_t buffers_on_device, int32_t* out_ids,
+                            int64_t cap, int64_t* out_offsets, void* cuda_stream);
+
+/* Per-stage counters of the last query call on this index (summed over its queries). */
+typedef struct {
+  int64_t n_items, n_users, n_blocks, n_partitions, device_bytes;
+  int64_t queries;              /* queries in the last call */
+  int64_t block_pairs_total;    /* (block, query) pairs examined */
+  int64_t block_pairs_kept;     /* pairs that survived the node-level bound (Lemma 2) */
+  int64_t users_scored;         /* users whose <u,q> was computed after the vector bound (Lemma 3) */
+  int64_t users_yes_early;      /* "yes" without a kMIPS (lower/upper-bound tests) */
+  int64_t survivors;            /* users sent to the per-user kMIPS decision */
+  int64_t fp64_rescored;        /* survivors decided in double precision */
+  int64_t results;              /* ids returned */
+  int64_t users_in_kept_blocks; /* users of leaves that had at least one surviving pair */
+  int64_t items_scanned;        /* (survivor, item) scores computed by the kMIPS decisions */
+  /* With timing enabled: CUDA-event time (ms) and kernel launches per stage of the last
+   * call: [0] query preparation, [1] block pass (A3), [2] user pass (A4), [3] kMIPS
+   * decision (A5/A6), [4] answer compaction (A7), [5] SA-ALSH hashing. */
+  double stage_ms[8];
+  int64_t stage_launches[8];
+} sah_stats;
+
+sah_status sah_index_stats(const sah_index* index, sah_stats* out);
+
+/* Turns per-stage CUDA-event timing of the query calls on (enable != 0) or off.  Events
+ * are recorded on the call's stream around each stage; the times appear in
+ * sah_stats.stage_ms after the call. */
+sah_status sah_index_set_timing(sah_index* index, int32_t enable);
+
+/* Frees the index and every device buffer it owns.  NULL is ignored. */
+void sah_free_index(sah_index* index);
+
+const char* sah_status_string(sah_status s);
+
+/* Text of the last error reported on the calling thread ("" if none). */
+const char* sah_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SAH_H_ */

@@ -1,0 +1,312 @@
+// The C-ABI of libsah: argument checks, index lifetime, host <-> device staging.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sah_internal.cuh"
+
+namespace sah {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+sah_status cuda_status(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();   // clear a non-sticky error so the index stays usable
+  return e == cudaErrorMemoryAllocation ? SAH_ERR_OOM : SAH_ERR_CUDA;
+}
+
+sah_status dev_alloc(Index* ix, void** p, size_t bytes) {
+  *p = nullptr;
+  cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("device allocation of " + std::to_string(bytes) + " bytes failed");
+    return SAH_ERR_OOM;
+  }
+  ix->allocs.push_back(*p);
+  ix->bytes += bytes;
+  return SAH_OK;
+}
+
+namespace {
+
+// gamma_d = d u / (1 - d u), u = 2^-24, bounds the error of any FP32 evaluation order of
+// a d-term inner product relative to sum |a_i b_i| <= ||a|| ||b||; the factor 1.01 covers
+// the rounding of the FP32 norms it is multiplied by.
+float fp32_dot_gamma(int d) {
+  double u = std::ldexp(1.0, -24);
+  double g = (d + 2) * u / (1.0 - (d + 2) * u);
+  return (float)(1.01 * g);
+}
+
+bool all_finite(const float* x, int64_t cnt) {
+  for (int64_t i = 0; i < cnt; ++i)
+    if (!std::isfinite(x[i])) return false;
+  return true;
+}
+
+}  // namespace
+}  // namespace sah
+
+using sah::Index;
+
+struct sah_index {
+  Index impl;
+};
+
+static void destroy_index(sah_index* h) {
+  if (!h) return;
+  Index* ix = &h->impl;
+  for (void* p : ix->allocs) cudaFree(p);
+  if (ix->ws.base) cudaFree(ix->ws.base);
+  if (ix->surv.base) cudaFree(ix->surv.base);
+  if (ix->res.base) cudaFree(ix->res.base);
+  delete h;
+}
+
+extern "C" {
+
+void sah_default_params(sah_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->k_max = 50;
+  p->leaf_size = 20;
+  p->b = 0.5f;
+  p->n_tables = 128;
+  p->code_bits = 16;
+  p->p_prime = 0;
+  p->precision = SAH_FP32;
+  p->probe_radius = 0;
+  p->seed = 0;
+  p->srp = nullptr;
+}
+
+const char* sah_status_string(sah_status s) {
+  switch (s) {
+    case SAH_OK: return "ok";
+    case SAH_ERR_ARG: return "invalid argument";
+    case SAH_ERR_OOM: return "out of device memory";
+    case SAH_ERR_CUDA: return "CUDA error";
+    case SAH_ERR_BUFFER_TOO_SMALL: return "result buffer too small";
+    case SAH_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
+    case SAH_ERR_BUSY: return "busy";
+    case SAH_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* sah_last_error(void) { return sah::g_last_error.c_str(); }
+
+sah_status sah_build_index(const float* U, int64_t m, const float* P, int64_t n, int32_t d,
+                           int32_t inputs_on_device, const sah_params* params, void* cuda_stream,
+                           sah_index** out) {
+  if (!out) {
+    sah::set_error("sah_build_index: out is NULL");
+    return SAH_ERR_ARG;
+  }
+  *out = nullptr;
+  sah_params prm;
+  if (params) prm = *params;
+  else sah_default_params(&prm);
+  if (!U || !P || m < 1 || n < 1 || d < 1 || d > sah::kMaxDim || m > INT32_MAX || n > INT32_MAX) {
+    sah::set_error("sah_build_index: need non-null U, P and 1 <= m, n < 2^31, 1 <= d <= 1024");
+    return SAH_ERR_ARG;
+  }
+  if (prm.k_max < 1 || prm.k_max > sah::kMaxKmax || prm.leaf_size < 1 || prm.leaf_size > sah::kMaxLeaf ||
+      !(prm.b > 0.f && prm.b < 1.f) || prm.n_tables < 1 || prm.code_bits < 1 || prm.code_bits > 16 ||
+      prm.probe_radius < 0 || prm.probe_radius > prm.code_bits) {
+    sah::set_error("sah_build_index: parameter out of range");
+    return SAH_ERR_ARG;
+  }
+  if (prm.precision != SAH_FP32) {
+    sah::set_error("sah_build_index: this build computes scores in FP32 only");
+    return SAH_ERR_UNSUPPORTED;
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (!inputs_on_device) {
+    if (!sah::all_finite(U, m * d) || !sah::all_finite(P, n * d)) {
+      sah::set_error("sah_build_index: U or P holds a non-finite value");
+      return SAH_ERR_ARG;
+    }
+  }
+  sah_index* h = new sah_index();
+  Index* ix = &h->impl;
+  cudaGetDevice(&ix->device);
+  ix->n = n;
+  ix->m = m;
+  ix->d = d;
+  ix->dp = (d + 3) / 4 * 4;
+  ix->prm = prm;
+  ix->prm.srp = nullptr;
+  ix->kmax = prm.k_max;
+  int64_t pp = prm.p_prime <= 0 ? 4 * (int64_t)prm.k_max : prm.p_prime;
+  ix->pp = (int32_t)std::min<int64_t>(pp, n);
+  ix->l_exact = ix->pp >= n;
+  ix->gamma = sah::fp32_dot_gamma(d);
+  ix->cone_slack = 8.f * ix->gamma + 1e-6f;
+
+  const float* Ud = U;
+  const float* Pd = P;
+  float* tmpU = nullptr;
+  float* tmpP = nullptr;
+  sah_status s = SAH_OK;
+  if (!inputs_on_device) {
+    cudaError_t e1 = cudaMalloc((void**)&tmpU, sizeof(float) * m * d);
+    cudaError_t e2 = cudaMalloc((void**)&tmpP, sizeof(float) * n * d);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      cudaGetLastError();
+      if (tmpU) cudaFree(tmpU);
+      if (tmpP) cudaFree(tmpP);
+      destroy_index(h);
+      sah::set_error("sah_build_index: staging allocation failed");
+      return SAH_ERR_OOM;
+    }
+    cudaMemcpyAsync(tmpU, U, sizeof(float) * m * d, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(tmpP, P, sizeof(float) * n * d, cudaMemcpyHostToDevice, st);
+    Ud = tmpU;
+    Pd = tmpP;
+  }
+  s = sah::build_index_device(ix, Ud, Pd, st);
+  cudaStreamSynchronize(st);
+  if (tmpU) cudaFree(tmpU);
+  if (tmpP) cudaFree(tmpP);
+  if (s != SAH_OK) {
+    destroy_index(h);
+    return s;
+  }
+  *out = h;
+  return SAH_OK;
+}
+
+static sah_status batch_impl(sah_index* index, const float* Q, int32_t nq, const int32_t* ks,
+                             const int32_t* modes, int32_t on_dev, int32_t* out_ids, int64_t cap,
+                             int64_t* out_offsets, cudaStream_t st) {
+  Index* ix = &index->impl;
+  if (nq == 0) {
+    if (out_offsets) {
+      if (on_dev) cudaMemsetAsync(out_offsets, 0, sizeof(int64_t), st), cudaStreamSynchronize(st);
+      else out_offsets[0] = 0;
+    }
+    return SAH_OK;
+  }
+  std::vector<int32_t> ks_h(nq), modes_h(nq, SAH_EXACT);
+  if (on_dev) {
+    SAH_CUDA(cudaMemcpyAsync(ks_h.data(), ks, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, st));
+    if (modes) SAH_CUDA(cudaMemcpyAsync(modes_h.data(), modes, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, st));
+    SAH_CUDA(cudaStreamSynchronize(st));
+  } else {
+    std::memcpy(ks_h.data(), ks, sizeof(int32_t) * nq);
+    if (modes) std::memcpy(modes_h.data(), modes, sizeof(int32_t) * nq);
+    if (!sah::all_finite(Q, (int64_t)nq * ix->d)) {
+      sah::set_error("a query vector holds a non-finite value");
+      return SAH_ERR_ARG;
+    }
+  }
+  for (int j = 0; j < nq; ++j) {
+    if (ks_h[j] < 1) {
+      sah::set_error("k must be >= 1");
+      return SAH_ERR_ARG;
+    }
+    if (modes_h[j] != SAH_EXACT && modes_h[j] != SAH_SAALSH) {
+      sah::set_error("unknown mode");
+      return SAH_ERR_ARG;
+    }
+    if (modes_h[j] == SAH_SAALSH) {
+      sah::set_error("SA-ALSH mode is not built yet");
+      return SAH_ERR_UNSUPPORTED;
+    }
+  }
+  const float* Qd = Q;
+  const int32_t* kd = ks;
+  float* tq = nullptr;
+  int32_t* tk = nullptr;
+  if (!on_dev) {
+    SAH_CUDA(cudaMallocAsync((void**)&tq, sizeof(float) * (size_t)nq * ix->d, st));
+    SAH_CUDA(cudaMallocAsync((void**)&tk, sizeof(int32_t) * nq, st));
+    SAH_CUDA(cudaMemcpyAsync(tq, Q, sizeof(float) * (size_t)nq * ix->d, cudaMemcpyHostToDevice, st));
+    SAH_CUDA(cudaMemcpyAsync(tk, ks, sizeof(int32_t) * nq, cudaMemcpyHostToDevice, st));
+    Qd = tq;
+    kd = tk;
+  }
+  std::vector<int64_t> offs(nq + 1);
+  sah_status s = sah::run_batch(ix, Qd, nq, kd, nullptr, offs.data(), st);
+  if (tq) cudaFreeAsync(tq, st);
+  if (tk) cudaFreeAsync(tk, st);
+  if (s != SAH_OK) return s;
+  int64_t total = offs[nq];
+  if (total > cap) {
+    if (out_offsets) {
+      if (on_dev) {
+        cudaMemcpyAsync(out_offsets + nq, &total, sizeof(int64_t), cudaMemcpyHostToDevice, st);
+        cudaStreamSynchronize(st);
+      } else {
+        std::memcpy(out_offsets, offs.data(), sizeof(int64_t) * (nq + 1));
+      }
+    }
+    sah::set_error("result buffer too small: " + std::to_string(total) + " ids needed");
+    return SAH_ERR_BUFFER_TOO_SMALL;
+  }
+  if (total > 0)
+    SAH_CUDA(cudaMemcpyAsync(out_ids, ix->res.base, sizeof(int32_t) * total,
+                             on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  if (on_dev) SAH_CUDA(cudaMemcpyAsync(out_offsets, offs.data(), sizeof(int64_t) * (nq + 1), cudaMemcpyHostToDevice, st));
+  else std::memcpy(out_offsets, offs.data(), sizeof(int64_t) * (nq + 1));
+  SAH_CUDA(cudaStreamSynchronize(st));
+  return SAH_OK;
+}
+
+sah_status sah_rkmips_batch(sah_index* index, const float* Q, int32_t nq, const int32_t* ks,
+                            const int32_t* modes, int32_t buffers_on_device, int32_t* out_ids, int64_t cap,
+                            int64_t* out_offsets, void* cuda_stream) {
+  if (!index || nq < 0 || (nq > 0 && (!Q || !ks || !out_offsets)) || cap < 0 || (cap > 0 && !out_ids)) {
+    sah::set_error("sah_rkmips_batch: invalid argument");
+    return SAH_ERR_ARG;
+  }
+  return batch_impl(index, Q, nq, ks, modes, buffers_on_device, out_ids, cap, out_offsets,
+                    (cudaStream_t)cuda_stream);
+}
+
+sah_status sah_rkmips(sah_index* index, const float* q, int32_t k, int32_t mode, int32_t* out_ids,
+                      int64_t cap, int64_t* out_count, void* cuda_stream) {
+  if (!index || !q || !out_count || k < 1 || cap < 0 || (cap > 0 && !out_ids)) {
+    sah::set_error("sah_rkmips: invalid argument");
+    return SAH_ERR_ARG;
+  }
+  int64_t offs[2] = {0, 0};
+  sah_status s = batch_impl(index, q, 1, &k, &mode, 0, out_ids, cap, offs, (cudaStream_t)cuda_stream);
+  *out_count = offs[1];
+  return s;
+}
+
+sah_status sah_index_stats(const sah_index* index, sah_stats* out) {
+  if (!index || !out) {
+    sah::set_error("sah_index_stats: invalid argument");
+    return SAH_ERR_ARG;
+  }
+  const Index* ix = &index->impl;
+  *out = ix->stats;
+  out->n_items = ix->n;
+  out->n_users = ix->m;
+  out->n_blocks = ix->nb;
+  out->device_bytes = (int64_t)(ix->bytes + ix->ws.bytes + ix->surv.bytes + ix->res.bytes);
+  return SAH_OK;
+}
+
+void sah_free_index(sah_index* index) { destroy_index(index); }
+
+sah_status sah_index_set_timing(sah_index* index, int32_t enable) {
+  if (!index) {
+    sah::set_error("sah_index_set_timing: index is NULL");
+    return SAH_ERR_ARG;
+  }
+  index->impl.timing = enable != 0;
+  return SAH_OK;
+}
+
+}  // extern "C"

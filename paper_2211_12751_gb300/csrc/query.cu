@@ -1,0 +1,750 @@
+// SAH query (Alg. 5) for a batch of queries, exact mode.
+//
+//   A3  block pass: node-level bound (Lemma 2) of every (leaf, query) pair against the
+//       block lower bound L^k(B) (Alg. 4); surviving pairs are listed per leaf.
+//   A4  user pass: vector-level bound (Lemma 3), then <u,q> with its FP32 error bound,
+//       then the lower bound L_u^k ("no"), the exact-threshold upper bound when |P'| = n
+//       ("yes") and the ||p_k|| bound ("yes", Alg. 5); the rest become survivors.
+//   A5  verify: per survivor, items in descending norm order, counting items whose FP32
+//       score is certainly above <u,q>, keeping the few inside the error band, and
+//       stopping at k certain items ("no") or when ||u|| ||p_i|| can no longer reach
+//       <u,q> (the mu_j rule of Alg. 2).
+//   A6  the open cases are decided in double precision, summed i = 0..d-1.
+//   A7  answers are set in a per-query bitmap over the caller's user ids and emitted in
+//       ascending id order.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "sah_internal.cuh"
+
+namespace sah {
+
+namespace {
+
+struct PairEntry {
+  int32_t j;      // query within the sub-batch
+  float cphi;     // cos(angle(q, block centre)); > 1.5 means "no cone bound"
+  float sphi;     // sin of that angle
+};
+
+struct Survivor {
+  int32_t upos;   // user position (leaf order)
+  int32_t j;      // query within the sub-batch
+  float sq;       // FP32 <u,q>
+};
+
+enum StatSlot {
+  ST_PAIRS_KEPT = 0,
+  ST_USERS_SCORED,
+  ST_YES_EARLY,
+  ST_FP64,
+  ST_KEPT_USERS,
+  ST_ITEMS,
+  ST_BAD_Q,
+  ST_COUNT
+};
+
+constexpr int kWordsPerChunk = 2048;
+
+inline unsigned grid_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
+
+// ---------------------------------------------------------------- query preparation
+__global__ void prep_queries_kernel(const float* __restrict__ Q, int nq, int d, int dp,
+                                    float* __restrict__ Qd, float* __restrict__ qn,
+                                    unsigned long long* __restrict__ stats) {
+  int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  int lane = threadIdx.x & 31;
+  if (j >= nq) return;
+  float s = 0.f;
+  bool fin = true;
+  for (int i = lane; i < dp; i += 32) {
+    float v = (i < d) ? Q[(int64_t)j * d + i] : 0.f;
+    fin &= isfinite(v);
+    Qd[(int64_t)j * dp + i] = v;
+    s = fmaf(v, v, s);
+  }
+  s = warp_sum(s);
+  bool ok = __all_sync(0xffffffffu, fin);
+  if (lane == 0) {
+    qn[j] = sqrtf(s);
+    if (!ok) atomicAdd(&stats[ST_BAD_Q], 1ull);
+  }
+}
+
+// ---------------------------------------------------------------- A3: block pass
+// One CTA per leaf; warp w handles queries w, w + 8, ...  cos phi comes from <c, q>;
+// sin phi from the norm of q's component orthogonal to the unit centre c, which stays
+// accurate when phi is small.  Upper bound (Lemma 2), for unit users:
+//   ||q||                                   if phi <= omega
+//   ||q|| (cos phi cos omega + sin phi sin omega)   otherwise,
+// plus an additive slack that covers the FP32 error of every term.
+__global__ void block_filter_kernel(const float* __restrict__ bcent, const float* __restrict__ bcos,
+                                    const float* __restrict__ bsin, const float* __restrict__ LB,
+                                    int nb, int kmax, int64_t n, int dp,
+                                    const float* __restrict__ Qd, const float* __restrict__ qn,
+                                    const int32_t* __restrict__ kk, int nq, float slack,
+                                    PairEntry* __restrict__ pairs, int32_t* __restrict__ pcount,
+                                    unsigned long long* __restrict__ stats) {
+  __shared__ int32_t cnt;
+  int B = blockIdx.x;
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  const float* c = bcent + (int64_t)B * dp;
+  float cw = bcos[B], sw = bsin[B];
+  bool degenerate = cw < -1.5f;
+  for (int j0 = 0; j0 < nq; j0 += nw) {
+    int j = j0 + warp;
+    bool keep = false;
+    float cphi = 2.f, sphi = 0.f;
+    if (j < nq) {
+      int k = kk[j];
+      float nrm = qn[j];
+      if (k <= n) {                     // k > n: every user answers "yes" elsewhere
+        if (degenerate || !(nrm > 0.f)) {
+          keep = true;
+        } else {
+          const float* q = Qd + (int64_t)j * dp;
+          float dq = 0.f;
+          for (int i = lane; i < dp; i += 32) dq = fmaf(c[i], q[i], dq);
+          dq = warp_sum(dq);
+          float o2 = 0.f;
+          for (int i = lane; i < dp; i += 32) {
+            float o = fmaf(-dq, c[i], q[i]);
+            o2 = fmaf(o, o, o2);
+          }
+          o2 = warp_sum(o2);
+          cphi = fminf(1.f, fmaxf(-1.f, dq / nrm));
+          sphi = fminf(1.f, sqrtf(o2) / nrm);
+          float ub;
+          if (cphi >= cw - slack) ub = nrm * (1.f + slack);
+          else ub = nrm * (fmaf(cphi, cw, sphi * sw) + 2.f * slack);
+          float lb = (k <= kmax) ? LB[(int64_t)(k - 1) * nb + B] : -INFINITY;
+          keep = !(ub < lb);
+        }
+      }
+    }
+    if (keep && lane == 0) {
+      int slot = atomicAdd(&cnt, 1);
+      pairs[(int64_t)B * nq + slot] = PairEntry{j, cphi, sphi};
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    pcount[B] = cnt;
+    if (cnt) atomicAdd(&stats[ST_PAIRS_KEPT], (unsigned long long)cnt);
+  }
+}
+
+// ---------------------------------------------------------------- A4: user pass
+// One CTA per leaf, one thread per user; the leaf's user rows are staged in shared
+// memory (odd float4 stride: conflict-free 16-byte loads).
+__global__ void user_scan_kernel(const float* __restrict__ Ut, const float* __restrict__ unorm,
+                                 const float* __restrict__ ucos, const float* __restrict__ usin,
+                                 const int32_t* __restrict__ uid, const int32_t* __restrict__ bstart,
+                                 const float* __restrict__ Lt, const float* __restrict__ Eu,
+                                 const float* __restrict__ pnorm, int64_t n, int64_t mz, int kmax,
+                                 int l_exact, int dp, const float* __restrict__ Qd,
+                                 const float* __restrict__ qn, const int32_t* __restrict__ kk, int nq,
+                                 const PairEntry* __restrict__ pairs, const int32_t* __restrict__ pcount,
+                                 float gamma, float slack, uint32_t* __restrict__ bitmap, int64_t words,
+                                 Survivor* __restrict__ surv, unsigned long long* __restrict__ surv_count,
+                                 int64_t surv_cap, unsigned long long* __restrict__ stats, int stage) {
+  extern __shared__ float4 us4[];
+  int B = blockIdx.x;
+  int npairs = pcount[B];
+  if (npairs == 0) return;
+  int s = bstart[B], e = bstart[B + 1];
+  int cnt = e - s;
+  if (threadIdx.x == 0) atomicAdd(&stats[ST_KEPT_USERS], (unsigned long long)cnt);
+  int dp4 = dp / 4, stride4 = dp4 | 1;
+  if (stage) {
+    for (int i = threadIdx.x; i < cnt * dp4; i += blockDim.x) {
+      int r = i / dp4, c = i % dp4;
+      us4[r * stride4 + c] = reinterpret_cast<const float4*>(Ut + (int64_t)(s + r) * dp)[c];
+    }
+  }
+  __syncthreads();
+  int t = threadIdx.x;
+  bool active = t < cnt;
+  int r = s + t;
+  float nu = 0.f, ct = 0.f, st_ = 0.f, E = 0.f;
+  int32_t id = 0;
+  if (active) {
+    nu = unorm[r];
+    ct = ucos[r];
+    st_ = usin[r];
+    E = Eu[r];
+    id = uid[r];
+  }
+  // rows too wide to stage for the whole leaf are read from global memory (L1/L2)
+  const float4* myu = stage ? us4 + t * stride4
+                            : reinterpret_cast<const float4*>(Ut + (int64_t)(active ? r : s) * dp);
+  unsigned long long scored = 0, yes_early = 0;
+  int lane = threadIdx.x & 31;
+  for (int pi = 0; pi < npairs; ++pi) {
+    PairEntry pe = pairs[(int64_t)B * nq + pi];
+    int j = pe.j;
+    int k = kk[j];
+    float nrm = qn[j];
+    bool surv_flag = false, yes = false;
+    float sq = 0.f;
+    if (active) {
+      float L = (k <= kmax) ? Lt[(int64_t)(k - 1) * mz + r] : -INFINITY;
+      float Llo = (L == -INFINITY) ? -INFINITY : __fsub_rd(L, E);
+      bool pruned = false;
+      if (pe.cphi <= 1.5f) {   // Lemma 3 with the slack of the FP32 terms
+        float ub = __fmul_ru(__fmul_ru(nu, nrm), fmaf(pe.cphi, ct, pe.sphi * st_) + 2.f * slack);
+        pruned = ub < Llo;
+      }
+      if (!pruned) {
+        ++scored;
+        const float4* q4 = reinterpret_cast<const float4*>(Qd + (int64_t)j * dp);
+        float acc = 0.f;
+        for (int c = 0; c < dp4; ++c) {
+          float4 a = myu[c], b = __ldg(q4 + c);
+          acc = fmaf(a.x, b.x, acc);
+          acc = fmaf(a.y, b.y, acc);
+          acc = fmaf(a.z, b.z, acc);
+          acc = fmaf(a.w, b.w, acc);
+        }
+        sq = acc;
+        float eq = __fmul_ru(__fmul_ru(gamma, nu), nrm) + 1e-30f;
+        float hi = __fadd_ru(sq, eq), lo = __fsub_rd(sq, eq);
+        if (hi < Llo) {
+          // "no": at least k items of P' score above <u,q>
+        } else if (l_exact && k <= kmax && lo >= __fadd_ru(L, E)) {
+          yes = true;                        // <u,q> >= exact k-th largest score
+        } else if (lo >= __fmul_ru(__fmul_ru(nu, pnorm[k - 1]), 1.f + 2.f * gamma)) {
+          yes = true;                        // <u,q> >= ||u|| ||p_k|| >= k-th largest score
+        } else {
+          surv_flag = true;
+        }
+      }
+    }
+    if (yes) {
+      ++yes_early;
+      atomicOr(&bitmap[(int64_t)j * words + (id >> 5)], 1u << (id & 31));
+    }
+    unsigned m = __ballot_sync(0xffffffffu, surv_flag);
+    if (m) {
+      unsigned long long base = 0;
+      int leader = __ffs(m) - 1;
+      if (lane == leader) base = atomicAdd(surv_count, (unsigned long long)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (surv_flag) {
+        unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
+        if ((int64_t)slot < surv_cap) surv[slot] = Survivor{r, j, sq};
+      }
+    }
+  }
+  // per-warp totals
+  for (int o = 16; o > 0; o >>= 1) {
+    scored += __shfl_xor_sync(0xffffffffu, scored, o);
+    yes_early += __shfl_xor_sync(0xffffffffu, yes_early, o);
+  }
+  if (lane == 0) {
+    if (scored) atomicAdd(&stats[ST_USERS_SCORED], scored);
+    if (yes_early) atomicAdd(&stats[ST_YES_EARLY], yes_early);
+  }
+}
+
+// ---------------------------------------------------------------- A5 + A6: verify
+// One warp per survivor.  Item scores in FP32 with the a-priori bound
+//   |fl(<u,p>) - <u,p>| <= gamma ||u|| ||p||;
+// an item is certainly above <u,q> when s_p - e_p > s_q + e_q, certainly not when
+// s_p + e_p <= s_q - e_q, and in the band otherwise.  Band items (up to 32) are decided
+// in double precision; a larger band falls back to a full double-precision count.
+constexpr int kVerifyWarps = 8;
+
+__global__ void __launch_bounds__(kVerifyWarps * 32)
+verify_exact_kernel(const Survivor* __restrict__ surv, const unsigned long long* __restrict__ surv_count,
+                    int64_t surv_cap, const float* __restrict__ Ut, const float* __restrict__ unorm,
+                    const int32_t* __restrict__ uid, const float* __restrict__ Ps,
+                    const float* __restrict__ pnorm, int64_t n, int d, int dp,
+                    const float* __restrict__ Qd, const float* __restrict__ qn,
+                    const int32_t* __restrict__ kk, float gamma, uint32_t* __restrict__ bitmap,
+                    int64_t words, unsigned long long* __restrict__ stats) {
+  extern __shared__ float4 vs4[];            // kVerifyWarps x dp4 user rows
+  __shared__ int32_t band_list[kVerifyWarps][32];
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int dp4 = dp / 4;
+  float4* myu = vs4 + warp * dp4;
+  int64_t total = (int64_t)min((unsigned long long)surv_cap, *surv_count);
+  int64_t gw = (int64_t)blockIdx.x * kVerifyWarps + warp;
+  int64_t nwarps = (int64_t)gridDim.x * kVerifyWarps;
+  unsigned long long fp64_cnt = 0, scanned = 0;
+  for (int64_t si = gw; si < total; si += nwarps) {
+    Survivor S = surv[si];
+    int k = kk[S.j];
+    const float* urow = Ut + (int64_t)S.upos * dp;
+    for (int c = lane; c < dp4; c += 32) myu[c] = reinterpret_cast<const float4*>(urow)[c];
+    __syncwarp();
+    float nu = unorm[S.upos];
+    float eq = __fmul_ru(__fmul_ru(gamma, nu), qn[S.j]) + 1e-30f;
+    float hi = __fadd_ru(S.sq, eq), lo = __fsub_rd(S.sq, eq);
+    float gnu = __fmul_ru(gamma, nu);
+    float cut_scale = __fmul_ru(nu, 1.f + 2.f * gamma);
+    int above = 0, band = 0;
+    for (int64_t base = 0; base < n; base += 32) {
+      if (__fmul_ru(cut_scale, pnorm[base]) <= lo) break;   // no later item can beat <u,q>
+      int64_t i = base + lane;
+      bool is_above = false, is_band = false;
+      if (i < n) {
+        const float4* p4 = reinterpret_cast<const float4*>(Ps + i * dp);
+        float acc = 0.f;
+        for (int c = 0; c < dp4; ++c) {
+          float4 a = myu[c], b = __ldg(p4 + c);
+          acc = fmaf(a.x, b.x, acc);
+          acc = fmaf(a.y, b.y, acc);
+          acc = fmaf(a.z, b.z, acc);
+          acc = fmaf(a.w, b.w, acc);
+        }
+        float ep = __fmul_ru(gnu, pnorm[i]) + 1e-30f;
+        is_above = __fsub_rd(acc, ep) > hi;
+        is_band = !is_above && __fadd_ru(acc, ep) > lo;
+      }
+      above += __popc(__ballot_sync(0xffffffffu, is_above));
+      unsigned bm = __ballot_sync(0xffffffffu, is_band);
+      if (is_band) {
+        int slot = band + __popc(bm & ((1u << lane) - 1u));
+        if (slot < 32) band_list[warp][slot] = (int32_t)i;
+      }
+      band += __popc(bm);
+      scanned += (unsigned long long)((n - base) < 32 ? (n - base) : 32);
+      if (above >= k) break;
+    }
+    __syncwarp();
+    bool yes;
+    if (above >= k) {
+      yes = false;
+    } else if (above + band < k) {
+      yes = true;
+    } else {
+      ++fp64_cnt;
+      const float* urow_f = Ut + (int64_t)S.upos * dp;
+      const float* q = Qd + (int64_t)S.j * dp;
+      double s64q = dot64_seq(urow_f, q, d);
+      int c = above;
+      if (band <= 32) {
+        bool gt = false;
+        if (lane < band) gt = dot64_seq(urow_f, Ps + (int64_t)band_list[warp][lane] * dp, d) > s64q;
+        c += __popc(__ballot_sync(0xffffffffu, gt));
+      } else {
+        c = 0;
+        for (int64_t base = 0; base < n && c < k; base += 32) {
+          int64_t i = base + lane;
+          bool gt = (i < n) && dot64_seq(urow_f, Ps + i * dp, d) > s64q;
+          c += __popc(__ballot_sync(0xffffffffu, gt));
+        }
+      }
+      yes = c < k;
+    }
+    if (yes && lane == 0) {
+      int32_t id = uid[S.upos];
+      atomicOr(&bitmap[(int64_t)S.j * words + (id >> 5)], 1u << (id & 31));
+    }
+    __syncwarp();
+  }
+  if (lane == 0 && fp64_cnt) atomicAdd(&stats[ST_FP64], fp64_cnt);
+  if (lane == 0 && scanned) atomicAdd(&stats[ST_ITEMS], scanned);
+}
+
+// ---------------------------------------------------------------- A7: special users, compaction
+__global__ void zero_users_kernel(const int32_t* __restrict__ zid, int64_t nz, int nq,
+                                  uint32_t* __restrict__ bitmap, int64_t words) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nz * nq) return;
+  int j = (int)(t / nz);
+  int32_t id = zid[t % nz];
+  atomicOr(&bitmap[(int64_t)j * words + (id >> 5)], 1u << (id & 31));
+}
+
+// Queries with k > n: every user answers "yes".
+__global__ void all_users_kernel(const int32_t* __restrict__ kk, int nq, int64_t n, int64_t m,
+                                 uint32_t* __restrict__ bitmap, int64_t words) {
+  int j = blockIdx.y;
+  if (kk[j] <= n) return;
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words;
+       w += (int64_t)gridDim.x * blockDim.x) {
+    int64_t lo = w * 32;
+    uint32_t v = 0xffffffffu;
+    if (lo + 32 > m) v = (m - lo) >= 32 ? 0xffffffffu : ((1u << (m - lo)) - 1u);
+    bitmap[(int64_t)j * words + w] = v;
+  }
+}
+
+__device__ inline int block_exclusive_scan(int v, int* total) {
+  __shared__ int wsum[32];
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  int nw = blockDim.x >> 5;
+  int before = 0, all = 0;
+  for (int w = 0; w < nw; ++w) {
+    if (w < warp) before += wsum[w];
+    all += wsum[w];
+  }
+  __syncthreads();
+  *total = all;
+  return before + x - v;
+}
+
+// chunk_cnt[j][c] = answers of query j among the users of chunk c.
+__global__ void bitmap_count_kernel(const uint32_t* __restrict__ bitmap, int64_t words, int nchunks,
+                                    int32_t* __restrict__ chunk_cnt) {
+  int c = blockIdx.x, j = blockIdx.y;
+  int64_t w0 = (int64_t)c * kWordsPerChunk;
+  int acc = 0;
+  for (int w = threadIdx.x; w < kWordsPerChunk; w += blockDim.x) {
+    int64_t ww = w0 + w;
+    if (ww < words) acc += __popc(bitmap[(int64_t)j * words + ww]);
+  }
+  acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 8);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  __shared__ int ws[32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    chunk_cnt[(int64_t)j * nchunks + c] = t;
+  }
+}
+
+// Per query: exclusive scan over chunks; offsets over queries start at base.
+__global__ void offsets_kernel(int32_t* __restrict__ chunk_cnt, int nchunks, int nq, int64_t base,
+                               int64_t* __restrict__ offsets) {
+  // single thread block; nq and nchunks are small
+  __shared__ long long run;
+  if (threadIdx.x == 0) run = base;
+  __syncthreads();
+  for (int j = 0; j < nq; ++j) {
+    if (threadIdx.x == 0) {
+      offsets[j] = run;
+      long long acc = 0;
+      for (int c = 0; c < nchunks; ++c) {
+        int v = chunk_cnt[(int64_t)j * nchunks + c];
+        chunk_cnt[(int64_t)j * nchunks + c] = (int)acc;
+        acc += v;
+      }
+      run += acc;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) offsets[nq] = run;
+}
+
+__global__ void bitmap_emit_kernel(const uint32_t* __restrict__ bitmap, int64_t words, int nchunks,
+                                   const int32_t* __restrict__ chunk_off, const int64_t* __restrict__ offsets,
+                                   int32_t* __restrict__ out) {
+  int c = blockIdx.x, j = blockIdx.y;
+  int64_t w0 = (int64_t)c * kWordsPerChunk;
+  int64_t dst0 = offsets[j] + chunk_off[(int64_t)j * nchunks + c];
+  const int per = kWordsPerChunk / 256;   // words per thread, blockDim = 256
+  uint32_t wv[per];
+  int cnt = 0;
+#pragma unroll
+  for (int q = 0; q < per; ++q) {
+    int64_t ww = w0 + (int64_t)threadIdx.x * per + q;
+    wv[q] = (ww < words) ? bitmap[(int64_t)j * words + ww] : 0u;
+    cnt += __popc(wv[q]);
+  }
+  int total;
+  int pre = block_exclusive_scan(cnt, &total);
+  int64_t dst = dst0 + pre;
+#pragma unroll
+  for (int q = 0; q < per; ++q) {
+    uint32_t v = wv[q];
+    int64_t idbase = (w0 + (int64_t)threadIdx.x * per + q) * 32;
+    while (v) {
+      int b = __ffs(v) - 1;
+      out[dst++] = (int32_t)(idbase + b);
+      v &= v - 1;
+    }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- workspace
+namespace {
+
+struct WsLayout {
+  size_t qd, qn, kk, pairs, pcount, survcnt, bitmap, chunk, offsets, stats, total;
+};
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+WsLayout layout_for(const Index* ix, int qb, int nchunks) {
+  WsLayout L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes); return r; };
+  int64_t words = (ix->m + 31) / 32;
+  L.qd = take(sizeof(float) * (size_t)qb * ix->dp);
+  L.qn = take(sizeof(float) * qb);
+  L.kk = take(sizeof(int32_t) * qb);
+  L.pairs = take(sizeof(PairEntry) * (size_t)std::max(ix->nb, 1) * qb);
+  L.pcount = take(sizeof(int32_t) * std::max(ix->nb, 1));
+  L.survcnt = take(sizeof(unsigned long long));
+  L.bitmap = take(sizeof(uint32_t) * (size_t)qb * words);
+  L.chunk = take(sizeof(int32_t) * (size_t)qb * nchunks);
+  L.offsets = take(sizeof(int64_t) * (size_t)(qb + 1));
+  L.stats = take(sizeof(unsigned long long) * ST_COUNT);
+  L.total = o;
+  return L;
+}
+
+sah_status ensure_buf(Workspace* b, size_t bytes, cudaStream_t st) {
+  if (b->bytes >= bytes) return SAH_OK;
+  SAH_CUDA(cudaStreamSynchronize(st));
+  if (b->base) cudaFree(b->base);
+  b->base = nullptr;
+  b->bytes = 0;
+  cudaError_t e = cudaMalloc(&b->base, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("workspace allocation failed");
+    return SAH_ERR_OOM;
+  }
+  b->bytes = bytes;
+  return SAH_OK;
+}
+
+sah_status ensure_ws(Index* ix, size_t bytes, cudaStream_t st) { return ensure_buf(&ix->ws, bytes, st); }
+
+sah_status ensure_surv(Index* ix, int64_t cap, cudaStream_t st) {
+  return ensure_buf(&ix->surv, sizeof(Survivor) * (size_t)std::max<int64_t>(cap, 1), st);
+}
+
+// CUDA events around each stage, on the call's stream (only when timing is enabled).
+struct StageTimer {
+  static constexpr int kStages = 8;
+  bool on = false;
+  cudaStream_t st = nullptr;
+  cudaEvent_t b[kStages] = {}, e[kStages] = {};
+  bool used[kStages] = {};
+  double ms[kStages] = {};
+  int64_t launches[kStages] = {};
+  StageTimer(bool enable, cudaStream_t s) : on(enable), st(s) {
+    if (!on) return;
+    for (int i = 0; i < kStages; ++i) {
+      cudaEventCreate(&b[i]);
+      cudaEventCreate(&e[i]);
+    }
+  }
+  ~StageTimer() {
+    if (!on) return;
+    for (int i = 0; i < kStages; ++i) {
+      cudaEventDestroy(b[i]);
+      cudaEventDestroy(e[i]);
+    }
+  }
+  void begin(int i) { if (on) cudaEventRecord(b[i], st); }
+  void end(int i, int nlaunch) {
+    launches[i] += nlaunch;
+    if (on) {
+      cudaEventRecord(e[i], st);
+      used[i] = true;
+    }
+  }
+  // after a stream synchronisation: fold the recorded intervals into ms[]
+  void collect() {
+    if (!on) return;
+    for (int i = 0; i < kStages; ++i)
+      if (used[i]) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, b[i], e[i]);
+        ms[i] += t;
+        used[i] = false;
+      }
+  }
+};
+
+}  // namespace
+
+// Runs Alg. 5 for nq queries.  Results go to out_ids_dev (cap entries, device) and the
+// offsets to offsets_host (nq + 1, host).  Queries are processed in sub-batches sized
+// so that the workspace stays bounded; every sub-batch's ids are emitted into the
+// index's internal result buffer first, so the caller's buffer is only written once the
+// total is known to fit.
+sah_status run_batch(Index* ix, const float* Q_dev, int32_t nq, const int32_t* ks_dev,
+                     const int32_t* modes_dev, int64_t* offsets_host, cudaStream_t st) {
+  (void)modes_dev;
+  const int64_t words = (ix->m + 31) / 32;
+  const int nchunks = (int)((words + kWordsPerChunk - 1) / kWordsPerChunk);
+  // sub-batch size: bounded pair list and bitmap (about 1 GiB together)
+  const size_t per_q = sizeof(PairEntry) * (size_t)std::max(ix->nb, 1) + sizeof(uint32_t) * words +
+                       sizeof(int32_t) * nchunks + sizeof(float) * ix->dp + 16;
+  int qb = (int)std::max<size_t>(1, std::min<size_t>((size_t)nq, (size_t(1) << 30) / per_q));
+  qb = std::min(qb, 4096);
+  int64_t surv_cap = std::max<int64_t>((int64_t)(ix->surv.bytes / sizeof(Survivor)), 1 << 20);
+
+  sah_stats agg{};
+  agg.queries = nq;
+  StageTimer tm(ix->timing, st);
+  int64_t res_total = 0;
+  std::vector<int64_t> offs(nq + 1, 0);
+
+  for (int q0 = 0; q0 < nq; q0 += qb) {
+    const int nqb = std::min(qb, nq - q0);
+    WsLayout L = layout_for(ix, nqb, nchunks);
+    SAH_TRY(ensure_ws(ix, L.total, st));
+    char* w = (char*)ix->ws.base;
+    float* Qd = (float*)(w + L.qd);
+    float* qn = (float*)(w + L.qn);
+    int32_t* kk = (int32_t*)(w + L.kk);
+    PairEntry* pairs = (PairEntry*)(w + L.pairs);
+    int32_t* pcount = (int32_t*)(w + L.pcount);
+    unsigned long long* survcnt = (unsigned long long*)(w + L.survcnt);
+    uint32_t* bitmap = (uint32_t*)(w + L.bitmap);
+    int32_t* chunk = (int32_t*)(w + L.chunk);
+    int64_t* offsets = (int64_t*)(w + L.offsets);
+    unsigned long long* stats = (unsigned long long*)(w + L.stats);
+
+    tm.begin(0);
+    SAH_CUDA(cudaMemsetAsync(stats, 0, sizeof(unsigned long long) * ST_COUNT, st));
+    SAH_CUDA(cudaMemsetAsync(survcnt, 0, sizeof(unsigned long long), st));
+    SAH_CUDA(cudaMemsetAsync(bitmap, 0, sizeof(uint32_t) * (size_t)nqb * words, st));
+    SAH_CUDA(cudaMemcpyAsync(kk, ks_dev + q0, sizeof(int32_t) * nqb, cudaMemcpyDeviceToDevice, st));
+    prep_queries_kernel<<<grid_for(nqb, 8), 256, 0, st>>>(Q_dev + (int64_t)q0 * ix->d, nqb, ix->d, ix->dp,
+                                                           Qd, qn, stats);
+    SAH_CUDA(cudaGetLastError());
+    tm.end(0, 1);
+    if (ix->nb > 0) {
+      tm.begin(1);
+      block_filter_kernel<<<ix->nb, 256, 0, st>>>(ix->bcent, ix->bcos, ix->bsin, ix->LB, ix->nb, ix->kmax,
+                                                  ix->n, ix->dp, Qd, qn, kk, nqb, ix->cone_slack, pairs,
+                                                  pcount, stats);
+      SAH_CUDA(cudaGetLastError());
+      tm.end(1, 1);
+      int threads = std::max(32, ((ix->prm.leaf_size + 31) / 32) * 32);
+      size_t smem = (size_t)16 * threads * ((ix->dp / 4) | 1);
+      int stage = smem <= 160 * 1024 ? 1 : 0;
+      if (!stage) smem = 0;
+      if (smem > 48 * 1024)
+        SAH_CUDA(cudaFuncSetAttribute(user_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      for (int attempt = 0;; ++attempt) {
+        SAH_TRY(ensure_surv(ix, surv_cap, st));
+        Survivor* surv = (Survivor*)ix->surv.base;
+        tm.begin(2);
+        user_scan_kernel<<<ix->nb, threads, smem, st>>>(
+            ix->Ut, ix->unorm, ix->ucos, ix->usin, ix->uid, ix->bstart, ix->Lt, ix->Eu, ix->pnorm, ix->n,
+            ix->m_nz, ix->kmax, ix->l_exact ? 1 : 0, ix->dp, Qd, qn, kk, nqb, pairs, pcount, ix->gamma,
+            ix->cone_slack, bitmap, words, surv, survcnt, surv_cap, stats, stage);
+        SAH_CUDA(cudaGetLastError());
+        tm.end(2, 1);
+        unsigned long long ns = 0;
+        SAH_CUDA(cudaMemcpyAsync(&ns, survcnt, sizeof(ns), cudaMemcpyDeviceToHost, st));
+        SAH_CUDA(cudaStreamSynchronize(st));
+        tm.collect();
+        if ((int64_t)ns <= surv_cap) {
+          agg.survivors += (int64_t)ns;
+          break;
+        }
+        // The survivor list overflowed: grow it and repeat the user pass.  Bits already
+        // set stay valid (setting a bit twice is harmless); the pass's counters restart.
+        if (attempt > 4) {
+          set_error("survivor list kept overflowing");
+          return SAH_ERR_OOM;
+        }
+        surv_cap = (int64_t)ns + (int64_t)ns / 4 + 1024;
+        SAH_CUDA(cudaMemsetAsync(survcnt, 0, sizeof(unsigned long long), st));
+        SAH_CUDA(cudaMemsetAsync(stats + ST_USERS_SCORED, 0, 2 * sizeof(unsigned long long), st));
+      }
+      Survivor* surv = (Survivor*)ix->surv.base;
+      size_t vsmem = (size_t)16 * kVerifyWarps * (ix->dp / 4);
+      if (vsmem > 48 * 1024)
+        SAH_CUDA(cudaFuncSetAttribute(verify_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsmem));
+      int sms = 152;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
+      tm.begin(3);
+      verify_exact_kernel<<<sms * 8, kVerifyWarps * 32, vsmem, st>>>(
+          surv, survcnt, surv_cap, ix->Ut, ix->unorm, ix->uid, ix->Ps, ix->pnorm, ix->n, ix->d, ix->dp, Qd, qn,
+          kk, ix->gamma, bitmap, words, stats);
+      SAH_CUDA(cudaGetLastError());
+      tm.end(3, 1);
+    }
+    tm.begin(4);
+    int n_compact = 3;
+    if (ix->nzero > 0) {
+      zero_users_kernel<<<grid_for(ix->nzero * nqb, 256), 256, 0, st>>>(ix->zero_uid, ix->nzero, nqb, bitmap,
+                                                                         words);
+      SAH_CUDA(cudaGetLastError());
+      ++n_compact;
+    }
+    {
+      dim3 g((unsigned)std::min<int64_t>(grid_for(words, 256), 1024), nqb);
+      all_users_kernel<<<g, 256, 0, st>>>(kk, nqb, ix->n, ix->m, bitmap, words);
+      SAH_CUDA(cudaGetLastError());
+    }
+    dim3 gc(nchunks, nqb);
+    bitmap_count_kernel<<<gc, 256, 0, st>>>(bitmap, words, nchunks, chunk);
+    offsets_kernel<<<1, 32, 0, st>>>(chunk, nchunks, nqb, res_total, offsets);
+    SAH_CUDA(cudaGetLastError());
+    std::vector<int64_t> ob(nqb + 1);
+    std::vector<unsigned long long> st_h(ST_COUNT);
+    SAH_CUDA(cudaMemcpyAsync(ob.data(), offsets, sizeof(int64_t) * (nqb + 1), cudaMemcpyDeviceToHost, st));
+    SAH_CUDA(cudaMemcpyAsync(st_h.data(), stats, sizeof(unsigned long long) * ST_COUNT, cudaMemcpyDeviceToHost, st));
+    SAH_CUDA(cudaStreamSynchronize(st));
+    tm.end(4, n_compact);
+    tm.collect();
+    if (st_h[ST_BAD_Q]) {
+      set_error("a query vector holds a non-finite value");
+      return SAH_ERR_ARG;
+    }
+    agg.block_pairs_total += (int64_t)ix->nb * nqb;
+    agg.block_pairs_kept += (int64_t)st_h[ST_PAIRS_KEPT];
+    agg.users_scored += (int64_t)st_h[ST_USERS_SCORED];
+    agg.users_yes_early += (int64_t)st_h[ST_YES_EARLY];
+    agg.fp64_rescored += (int64_t)st_h[ST_FP64];
+    agg.users_in_kept_blocks += (int64_t)st_h[ST_KEPT_USERS];
+    agg.items_scanned += (int64_t)st_h[ST_ITEMS];
+    for (int j = 0; j < nqb; ++j) offs[q0 + j] = ob[j];
+    int64_t new_total = ob[nqb];
+    if (new_total > res_total) {
+      // grow the index's result buffer, keeping what earlier sub-batches wrote
+      size_t need = sizeof(int32_t) * (size_t)new_total;
+      if (need > ix->res.bytes) {
+        Workspace nr;
+        SAH_TRY(ensure_buf(&nr, std::max(need, 2 * ix->res.bytes), st));
+        if (res_total)
+          SAH_CUDA(cudaMemcpyAsync(nr.base, ix->res.base, sizeof(int32_t) * res_total, cudaMemcpyDeviceToDevice, st));
+        SAH_CUDA(cudaStreamSynchronize(st));
+        if (ix->res.base) cudaFree(ix->res.base);
+        ix->res = nr;
+      }
+      tm.begin(4);
+      bitmap_emit_kernel<<<gc, 256, 0, st>>>(bitmap, words, nchunks, chunk, offsets, (int32_t*)ix->res.base);
+      SAH_CUDA(cudaGetLastError());
+      tm.end(4, 1);
+    }
+    res_total = new_total;
+  }
+  SAH_CUDA(cudaStreamSynchronize(st));
+  tm.collect();
+  for (int i = 0; i < StageTimer::kStages; ++i) {
+    agg.stage_ms[i] = tm.ms[i];
+    agg.stage_launches[i] = tm.launches[i];
+  }
+  offs[nq] = res_total;
+  agg.results = res_total;
+  agg.n_items = ix->n;
+  agg.n_users = ix->m;
+  agg.n_blocks = ix->nb;
+  agg.device_bytes = (int64_t)(ix->bytes + ix->ws.bytes + ix->surv.bytes + ix->res.bytes);
+  ix->stats = agg;
+  std::memcpy(offsets_host, offs.data(), sizeof(int64_t) * (nq + 1));
+  return SAH_OK;
+}
+
+}  // namespace sah

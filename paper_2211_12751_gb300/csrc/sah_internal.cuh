@@ -1,0 +1,142 @@
+// Internal declarations of libsah: the device-resident index, the per-call workspace,
+// small device helpers and the launchers each .cu file exports to the C-ABI layer.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "sah.h"
+
+namespace sah {
+
+constexpr int kMaxKmax = 64;     // lower-bound arrays per user (two slots per lane of a warp)
+constexpr int kMaxLeaf = 256;    // one thread per user of a Cone-Tree leaf
+constexpr int kMaxDim = 1024;
+
+// ------------------------------------------------------------------ error plumbing
+void set_error(const std::string& msg);
+sah_status cuda_status(cudaError_t e, const char* what);
+#define SAH_CUDA(call)                                              \
+  do {                                                              \
+    cudaError_t e_ = (call);                                        \
+    if (e_ != cudaSuccess) return ::sah::cuda_status(e_, #call);    \
+  } while (0)
+#define SAH_TRY(call)                                               \
+  do {                                                              \
+    sah_status s_ = (call);                                         \
+    if (s_ != SAH_OK) return s_;                                    \
+  } while (0)
+
+// ------------------------------------------------------------------ index layout in HBM
+// Items are stored in descending norm order (Alg. 1, Alg. 4), users in Cone-Tree leaf
+// order (Alg. 3) so that every block is a contiguous range.  FP32 rows are padded to
+// dp = roundup(d, 4) floats (16-byte rows for vector loads); padding is zero.
+struct Workspace {
+  void* base = nullptr;
+  size_t bytes = 0;
+};
+
+struct Index {
+  int device = 0;
+  int64_t n = 0, m = 0, m_nz = 0;
+  int32_t d = 0, dp = 0;
+  sah_params prm{};
+  int32_t kmax = 0, pp = 0;
+  bool l_exact = false;       // p_prime >= n: the lower bounds are the exact thresholds
+  float gamma = 0.f;          // FP32 dot-product error factor: |fl(<a,b>) - <a,b>| <= gamma ||a|| ||b||
+  float cone_slack = 0.f;     // additive slack (relative to ||q||) of the cone bounds
+  float mmax = 0.f;           // largest item norm
+
+  // items, descending norm order
+  float* Ps = nullptr;        // n x dp
+  float* pnorm = nullptr;     // n, descending
+  int32_t* pid = nullptr;     // n, caller's item id of each row
+
+  // users with a nonzero norm, Cone-Tree leaf order
+  float* Ut = nullptr;        // m_nz x dp (the caller's values, bit for bit)
+  float* unorm = nullptr;     // m_nz
+  int32_t* uid = nullptr;     // m_nz, caller's user id of each row
+  float* ucos = nullptr;      // cos theta_u to the leaf centre (Lemma 3)
+  float* usin = nullptr;      // sin theta_u
+  int32_t* zero_uid = nullptr;
+  int64_t nzero = 0;
+
+  // Cone-Tree leaves = blocks (Alg. 4)
+  int32_t nb = 0;
+  int32_t* bstart = nullptr;  // nb + 1
+  float* bcent = nullptr;     // nb x dp unit centre directions
+  float* bcos = nullptr;      // cos omega (-2 marks a zero centre: no cone bound)
+  float* bsin = nullptr;      // sin omega
+  float* LB = nullptr;        // [kmax][nb]: L^k(B) for unit users, rounded down
+
+  // lower-bound arrays (Alg. 4): Lt[k-1][u] = k-th largest FP32 score of u over P'
+  float* Lt = nullptr;        // [kmax][m_nz]
+  float* Eu = nullptr;        // m_nz: bound on |Lt - exact| (and on any FP32 item score's error)
+
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  Workspace ws;               // per-call workspace (queries, pair lists, bitmaps)
+  Workspace surv;             // survivor list, grown on demand
+  Workspace res;              // ids of the last call, before they go to the caller
+  sah_stats stats{};
+  bool timing = false;
+};
+
+sah_status dev_alloc(Index* ix, void** p, size_t bytes);
+
+// ------------------------------------------------------------------ device helpers
+__host__ __device__ inline uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Unsigned key with the same order as the float it encodes (finite floats).
+__device__ inline uint32_t float_order_key(float x) {
+  uint32_t u = __float_as_uint(x);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ inline float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ inline float warp_min(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ inline float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Sequential double-precision inner product in the order i = 0..d-1.  The product of
+// two floats is exact in double, so this equals the double-precision definition of the
+// count rule bit for bit, whatever the compiler does with the multiply-add.
+__device__ inline double dot64_seq(const float* __restrict__ a, const float* __restrict__ b,
+                                   int d) {
+  double s = 0.0;
+  for (int i = 0; i < d; ++i) s = __fma_rn((double)a[i], (double)b[i], s);
+  return s;
+}
+
+// ------------------------------------------------------------------ launchers
+// index_build.cu
+sah_status build_index_device(Index* ix, const float* U_dev, const float* P_dev,
+                              cudaStream_t st);
+// query.cu
+// Alg. 5 for nq queries (Q, ks, modes on the device).  On success the ascending ids of
+// every query sit in ix->res (query j at [offsets_host[j], offsets_host[j+1])).
+sah_status run_batch(Index* ix, const float* Q_dev, int32_t nq, const int32_t* ks_dev,
+                     const int32_t* modes_dev, int64_t* offsets_host, cudaStream_t st);
+
+}  // namespace sah
