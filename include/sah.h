@@ -134,6 +134,34 @@ sah_status sah_index_stats(const sah_index* index, sah_stats* out);
  * sah_stats.stage_ms after the call. */
 sah_status sah_index_set_timing(sah_index* index, int32_t enable);
 
+/* Exact RkMIPS for one query without allocating any memory (the paper has no
+ * counterpart; it exists for callers that may not allocate).
+ *
+ * Some callers cannot call cudaMalloc on their request path: a plugin inside a host
+ * application whose memory policy forbids allocations by third-party code, a process
+ * whose free device memory already belongs to another caching allocator, or a
+ * latency-bound loop that cannot absorb the synchronisation an allocation may cause.
+ * This call needs no index and makes no allocation: U (m x d), P (n x d), q (d) are the
+ * caller's device arrays (float32, row-major), out_ids a device array of cap int32 and
+ * out_count a device int64.  It writes the number of answering users to *out_count and,
+ * when that number is <= cap, their ids in ascending order to out_ids (nothing when it
+ * is larger).  The answer is the exact-mode answer of sah_rkmips (FP32 scores with a
+ * rigorous bound; undecided items re-scored in double precision).  All work is queued on
+ * cuda_stream; the call does not synchronise it.
+ *
+ * Its only scratch is a fixed device array of 2^22 bits (512 KiB) compiled into the
+ * library, so m must be <= 4,194,304 (larger m: SAH_ERR_ARG, nothing queued).  Every GPU
+ * that loads the library holds that array until the process exits.  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture begins.  All calls share the array: calls whose
+ * work overlaps on the GPU (other streams, other threads) race and must be serialised by
+ * the caller.  Each call clears the part of the array it uses before using it.
+ * Errors: SAH_ERR_ARG (null pointer, k < 1, n < 1, d outside 1..1024, m outside
+ * 1..4,194,304), SAH_ERR_CUDA. */
+sah_status sah_rkmips_bruteforce_noalloc(const float* U, int64_t m, const float* P, int64_t n,
+                                         int32_t d, const float* q, int32_t k, int32_t* out_ids,
+                                         int64_t cap, int64_t* out_count, void* cuda_stream);
+
 /* Frees the index and every device buffer it owns.  NULL is ignored. */
 void sah_free_index(sah_index* index);
 

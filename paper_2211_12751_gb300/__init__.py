@@ -97,6 +97,8 @@ def load(path: Optional[str] = None):
     lib.sah_index_stats.restype = I32
     lib.sah_index_set_timing.argtypes = [P, I32]
     lib.sah_index_set_timing.restype = I32
+    lib.sah_rkmips_bruteforce_noalloc.argtypes = [P, I64, P, I64, I32, P, I32, P, I64, P, P]
+    lib.sah_rkmips_bruteforce_noalloc.restype = I32
     lib.sah_free_index.argtypes = [P]
     lib.sah_free_index.restype = None
     lib.sah_status_string.argtypes = [I32]
@@ -139,6 +141,20 @@ def _stream_handle(stream) -> int:
 
 def _host_f32(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.float32)
+
+
+NOALLOC_MAX_USERS = 1 << 22
+
+
+def rkmips_bruteforce_noalloc(U, P, q, k: int, out_ids, out_count, m: Optional[int] = None, stream=None):
+    """Exact RkMIPS for one query with no allocation anywhere (device tensors in and out):
+    U (m x d), P (n x d), q (d) float32; out_ids int32 (capacity = numel); out_count int64
+    (one element).  Queued on the stream; read out_count after synchronising."""
+    lib = load()
+    m = U.shape[0] if m is None else m
+    _check(lib.sah_rkmips_bruteforce_noalloc(U.data_ptr(), m, P.data_ptr(), P.shape[0], U.shape[1],
+                                             q.data_ptr(), int(k), out_ids.data_ptr(), out_ids.numel(),
+                                             out_count.data_ptr(), _stream_handle(stream)))
 
 
 class Index:
