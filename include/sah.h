@@ -129,6 +129,14 @@ typedef struct {
 
 sah_status sah_index_stats(const sah_index* index, sah_stats* out);
 
+/* Copies the index's Cone-Tree blocks (the leaves of Alg. 3, Alg. 4) to host arrays:
+ * ids[m_nz] the caller ids of the users with a nonzero norm in leaf order, starts[nb + 1]
+ * the first position of every leaf, cos_theta[m_nz] each user's cos(theta_u) to its
+ * leaf centre, cos_omega[nb] each leaf's cos(omega) (-2 for a zero centre).  *m_nz and
+ * *nb receive the sizes; any array pointer may be NULL (to query the sizes first). */
+sah_status sah_index_blocks(const sah_index* index, int64_t* m_nz, int32_t* nb, int32_t* ids,
+                            int32_t* starts, float* cos_theta, float* cos_omega);
+
 /* Turns per-stage CUDA-event timing of the query calls on (enable != 0) or off.  Events
  * are recorded on the call's stream around each stage; the times appear in
  * sah_stats.stage_ms after the call. */

@@ -95,6 +95,8 @@ def load(path: Optional[str] = None):
     lib.sah_rkmips_batch.restype = I32
     lib.sah_index_stats.argtypes = [P, ctypes.POINTER(Stats)]
     lib.sah_index_stats.restype = I32
+    lib.sah_index_blocks.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I32), P, P, P, P]
+    lib.sah_index_blocks.restype = I32
     lib.sah_index_set_timing.argtypes = [P, I32]
     lib.sah_index_set_timing.restype = I32
     lib.sah_rkmips_bruteforce_noalloc.argtypes = [P, I64, P, I64, I32, P, I32, P, I64, P, P]
@@ -243,6 +245,19 @@ class Index:
         """Direct call of sah_rkmips_batch with raw pointers; returns the status."""
         return load().sah_rkmips_batch(self._h, Q, nq, ks, modes, on_device, out_ids, cap, offsets,
                                        _stream_handle(stream))
+
+    def blocks(self):
+        """Cone-Tree leaves: (ids in leaf order, leaf starts, cos theta_u, cos omega)."""
+        lib = load()
+        mnz, nb = ctypes.c_int64(), ctypes.c_int32()
+        _check(lib.sah_index_blocks(self._h, ctypes.byref(mnz), ctypes.byref(nb), None, None, None, None))
+        ids = np.empty(mnz.value, np.int32)
+        starts = np.empty(nb.value + 1, np.int32)
+        ct = np.empty(mnz.value, np.float32)
+        cw = np.empty(nb.value, np.float32)
+        _check(lib.sah_index_blocks(self._h, ctypes.byref(mnz), ctypes.byref(nb), ids.ctypes.data,
+                                    starts.ctypes.data, ct.ctypes.data, cw.ctypes.data))
+        return ids, starts, ct, cw
 
     def set_timing(self, enable: bool = True):
         _check(load().sah_index_set_timing(self._h, 1 if enable else 0))

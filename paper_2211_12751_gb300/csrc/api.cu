@@ -67,6 +67,7 @@ static void destroy_index(sah_index* h) {
   if (ix->ws.base) cudaFree(ix->ws.base);
   if (ix->surv.base) cudaFree(ix->surv.base);
   if (ix->res.base) cudaFree(ix->res.base);
+  if (ix->tcws.base) cudaFree(ix->tcws.base);
   delete h;
 }
 
@@ -124,8 +125,12 @@ sah_status sah_build_index(const float* U, int64_t m, const float* P, int64_t n,
     sah::set_error("sah_build_index: parameter out of range");
     return SAH_ERR_ARG;
   }
-  if (prm.precision != SAH_FP32) {
-    sah::set_error("sah_build_index: this build computes scores in FP32 only");
+  if (prm.precision != SAH_FP32 && prm.precision != SAH_BF16) {
+    sah::set_error("sah_build_index: precision must be SAH_FP32 or SAH_BF16 in this build");
+    return SAH_ERR_UNSUPPORTED;
+  }
+  if (prm.precision == SAH_BF16 && d > 128) {
+    sah::set_error("sah_build_index: the BF16 tensor-core path supports d <= 128");
     return SAH_ERR_UNSUPPORTED;
   }
   cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -294,11 +299,28 @@ sah_status sah_index_stats(const sah_index* index, sah_stats* out) {
   out->n_items = ix->n;
   out->n_users = ix->m;
   out->n_blocks = ix->nb;
-  out->device_bytes = (int64_t)(ix->bytes + ix->ws.bytes + ix->surv.bytes + ix->res.bytes);
+  out->device_bytes = (int64_t)(ix->bytes + ix->ws.bytes + ix->surv.bytes + ix->res.bytes + ix->tcws.bytes);
   return SAH_OK;
 }
 
 void sah_free_index(sah_index* index) { destroy_index(index); }
+
+sah_status sah_index_blocks(const sah_index* index, int64_t* m_nz, int32_t* nb, int32_t* ids, int32_t* starts,
+                            float* cos_theta, float* cos_omega) {
+  if (!index || !m_nz || !nb) {
+    sah::set_error("sah_index_blocks: invalid argument");
+    return SAH_ERR_ARG;
+  }
+  const Index* ix = &index->impl;
+  *m_nz = ix->m_nz;
+  *nb = ix->nb;
+  if (ids && ix->m_nz) SAH_CUDA(cudaMemcpy(ids, ix->uid, sizeof(int32_t) * ix->m_nz, cudaMemcpyDeviceToHost));
+  if (starts) SAH_CUDA(cudaMemcpy(starts, ix->bstart, sizeof(int32_t) * (ix->nb + 1), cudaMemcpyDeviceToHost));
+  if (cos_theta && ix->m_nz)
+    SAH_CUDA(cudaMemcpy(cos_theta, ix->ucos, sizeof(float) * ix->m_nz, cudaMemcpyDeviceToHost));
+  if (cos_omega && ix->nb) SAH_CUDA(cudaMemcpy(cos_omega, ix->bcos, sizeof(float) * ix->nb, cudaMemcpyDeviceToHost));
+  return SAH_OK;
+}
 
 sah_status sah_index_set_timing(sah_index* index, int32_t enable) {
   if (!index) {

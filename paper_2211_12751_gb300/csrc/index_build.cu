@@ -398,6 +398,8 @@ sah_status build_index_device(Index* ix, const float* U_dev, const float* P_dev,
   int* bad = nullptr;
   SAH_TRY(dev_alloc(ix, (void**)&bad, sizeof(int)));
   SAH_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
+  SAH_TRY(dev_alloc(ix, (void**)&ix->dev_timeout, sizeof(int)));
+  SAH_CUDA(cudaMemsetAsync(ix->dev_timeout, 0, sizeof(int), st));
 
   // ---- A0: item norms, descending order (ties: lower id first), padded rows
   float* pn_raw = nullptr;
@@ -636,6 +638,7 @@ sah_status build_index_device(Index* ix, const float* U_dev, const float* P_dev,
   block_lower_bounds_kernel<<<grid_for((int64_t)kmax * ix->nb, 256), 256, 0, st>>>(
       ix->Lt, ix->Eu, ix->unorm, ix->bstart, ix->nb, mz, kmax, ix->LB);
   SAH_CUDA(cudaGetLastError());
+  if (ix->prm.precision == SAH_BF16) SAH_TRY(build_bf16_copies(ix, st));
   SAH_CUDA(cudaStreamSynchronize(st));
 
   cudaFreeAsync(pn_raw, st);

@@ -28,12 +28,6 @@ struct PairEntry {
   float sphi;     // sin of that angle
 };
 
-struct Survivor {
-  int32_t upos;   // user position (leaf order)
-  int32_t j;      // query within the sub-batch
-  float sq;       // FP32 <u,q>
-};
-
 enum StatSlot {
   ST_PAIRS_KEPT = 0,
   ST_USERS_SCORED,
@@ -73,10 +67,11 @@ __global__ void prep_queries_kernel(const float* __restrict__ Q, int nq, int d, 
 }
 
 // ---------------------------------------------------------------- A3: block pass
-// One CTA per leaf; warp w handles queries w, w + 8, ...  cos phi comes from <c, q>;
-// sin phi from the norm of q's component orthogonal to the unit centre c, which stays
-// accurate when phi is small.  Upper bound (Lemma 2), for unit users:
-//   ||q||                                   if phi <= omega
+// One CTA per leaf, one thread per (leaf, query) pair.  cos phi = <c, q> / ||q|| with
+// the unit centre c.  sin phi = sqrt(1 - cos^2 phi) while cos^2 phi <= 1/2, where that
+// formula is well conditioned (|d sin / d cos| <= 1); closer to the centre it comes
+// from the norm of q's component orthogonal to c.  Upper bound (Lemma 2), unit users:
+//   ||q||                                           if phi <= omega
 //   ||q|| (cos phi cos omega + sin phi sin omega)   otherwise,
 // plus an additive slack that covers the FP32 error of every term.
 __global__ void block_filter_kernel(const float* __restrict__ bcent, const float* __restrict__ bcos,
@@ -86,48 +81,67 @@ __global__ void block_filter_kernel(const float* __restrict__ bcent, const float
                                     const int32_t* __restrict__ kk, int nq, float slack,
                                     PairEntry* __restrict__ pairs, int32_t* __restrict__ pcount,
                                     unsigned long long* __restrict__ stats) {
+  extern __shared__ float4 c4s[];   // the leaf's unit centre
   __shared__ int32_t cnt;
-  int B = blockIdx.x;
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int B = blockIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int dp4 = dp / 4;
   if (threadIdx.x == 0) cnt = 0;
+  for (int i = threadIdx.x; i < dp4; i += blockDim.x)
+    c4s[i] = reinterpret_cast<const float4*>(bcent + (int64_t)B * dp)[i];
   __syncthreads();
-  const float* c = bcent + (int64_t)B * dp;
-  float cw = bcos[B], sw = bsin[B];
-  bool degenerate = cw < -1.5f;
-  for (int j0 = 0; j0 < nq; j0 += nw) {
-    int j = j0 + warp;
+  const float cw = bcos[B], sw = bsin[B];
+  const bool degenerate = cw < -1.5f;
+  for (int j0 = 0; j0 < nq; j0 += blockDim.x) {
+    const int j = j0 + threadIdx.x;
     bool keep = false;
     float cphi = 2.f, sphi = 0.f;
     if (j < nq) {
-      int k = kk[j];
-      float nrm = qn[j];
+      const int k = kk[j];
+      const float nrm = qn[j];
       if (k <= n) {                     // k > n: every user answers "yes" elsewhere
         if (degenerate || !(nrm > 0.f)) {
           keep = true;
         } else {
-          const float* q = Qd + (int64_t)j * dp;
+          const float4* q4 = reinterpret_cast<const float4*>(Qd + (int64_t)j * dp);
           float dq = 0.f;
-          for (int i = lane; i < dp; i += 32) dq = fmaf(c[i], q[i], dq);
-          dq = warp_sum(dq);
-          float o2 = 0.f;
-          for (int i = lane; i < dp; i += 32) {
-            float o = fmaf(-dq, c[i], q[i]);
-            o2 = fmaf(o, o, o2);
+          for (int i = 0; i < dp4; ++i) {
+            const float4 a = c4s[i], b = __ldg(q4 + i);
+            dq = fmaf(a.x, b.x, dq);
+            dq = fmaf(a.y, b.y, dq);
+            dq = fmaf(a.z, b.z, dq);
+            dq = fmaf(a.w, b.w, dq);
           }
-          o2 = warp_sum(o2);
           cphi = fminf(1.f, fmaxf(-1.f, dq / nrm));
-          sphi = fminf(1.f, sqrtf(o2) / nrm);
+          if (cphi * cphi <= 0.5f) {
+            sphi = sqrtf(fmaxf(0.f, fmaf(-cphi, cphi, 1.f)));
+          } else {
+            float o2 = 0.f;
+            for (int i = 0; i < dp4; ++i) {
+              const float4 a = c4s[i], b = __ldg(q4 + i);
+              float o;
+              o = fmaf(-dq, a.x, b.x); o2 = fmaf(o, o, o2);
+              o = fmaf(-dq, a.y, b.y); o2 = fmaf(o, o, o2);
+              o = fmaf(-dq, a.z, b.z); o2 = fmaf(o, o, o2);
+              o = fmaf(-dq, a.w, b.w); o2 = fmaf(o, o, o2);
+            }
+            sphi = fminf(1.f, sqrtf(o2) / nrm);
+          }
           float ub;
           if (cphi >= cw - slack) ub = nrm * (1.f + slack);
           else ub = nrm * (fmaf(cphi, cw, sphi * sw) + 2.f * slack);
-          float lb = (k <= kmax) ? LB[(int64_t)(k - 1) * nb + B] : -INFINITY;
+          const float lb = (k <= kmax) ? LB[(int64_t)(k - 1) * nb + B] : -INFINITY;
           keep = !(ub < lb);
         }
       }
     }
-    if (keep && lane == 0) {
-      int slot = atomicAdd(&cnt, 1);
-      pairs[(int64_t)B * nq + slot] = PairEntry{j, cphi, sphi};
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (m) {
+      int base = 0;
+      const int leader = __ffs(m) - 1;
+      if (lane == leader) base = atomicAdd(&cnt, __popc(m));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (keep) pairs[(int64_t)B * nq + base + __popc(m & ((1u << lane) - 1u))] = PairEntry{j, cphi, sphi};
     }
   }
   __syncthreads();
@@ -139,7 +153,15 @@ __global__ void block_filter_kernel(const float* __restrict__ bcent, const float
 
 // ---------------------------------------------------------------- A4: user pass
 // One CTA per leaf, one thread per user; the leaf's user rows are staged in shared
-// memory (odd float4 stride: conflict-free 16-byte loads).
+// memory (odd float4 stride: conflict-free 16-byte loads), and so are the leaf's
+// surviving (query, k, ||q||, cos phi, sin phi) records, 512 at a time.  The lower bound
+// of the next record is loaded one iteration ahead.
+struct PairInfo {
+  int32_t j, k;
+  float cphi, sphi, nrm;
+};
+constexpr int kPairChunk = 512;
+
 __global__ void user_scan_kernel(const float* __restrict__ Ut, const float* __restrict__ unorm,
                                  const float* __restrict__ ucos, const float* __restrict__ usin,
                                  const int32_t* __restrict__ uid, const int32_t* __restrict__ bstart,
@@ -152,23 +174,23 @@ __global__ void user_scan_kernel(const float* __restrict__ Ut, const float* __re
                                  Survivor* __restrict__ surv, unsigned long long* __restrict__ surv_count,
                                  int64_t surv_cap, unsigned long long* __restrict__ stats, int stage) {
   extern __shared__ float4 us4[];
-  int B = blockIdx.x;
-  int npairs = pcount[B];
+  const int B = blockIdx.x;
+  const int npairs = pcount[B];
   if (npairs == 0) return;
-  int s = bstart[B], e = bstart[B + 1];
-  int cnt = e - s;
+  const int s = bstart[B], e = bstart[B + 1];
+  const int cnt = e - s;
   if (threadIdx.x == 0) atomicAdd(&stats[ST_KEPT_USERS], (unsigned long long)cnt);
-  int dp4 = dp / 4, stride4 = dp4 | 1;
+  const int dp4 = dp / 4, stride4 = dp4 | 1;
+  PairInfo* pinfo = reinterpret_cast<PairInfo*>(us4 + (stage ? (size_t)blockDim.x * stride4 : 0));
   if (stage) {
     for (int i = threadIdx.x; i < cnt * dp4; i += blockDim.x) {
-      int r = i / dp4, c = i % dp4;
+      const int r = i / dp4, c = i % dp4;
       us4[r * stride4 + c] = reinterpret_cast<const float4*>(Ut + (int64_t)(s + r) * dp)[c];
     }
   }
-  __syncthreads();
-  int t = threadIdx.x;
-  bool active = t < cnt;
-  int r = s + t;
+  const int t = threadIdx.x;
+  const bool active = t < cnt;
+  const int r = s + t;
   float nu = 0.f, ct = 0.f, st_ = 0.f, E = 0.f;
   int32_t id = 0;
   if (active) {
@@ -182,64 +204,80 @@ __global__ void user_scan_kernel(const float* __restrict__ Ut, const float* __re
   const float4* myu = stage ? us4 + t * stride4
                             : reinterpret_cast<const float4*>(Ut + (int64_t)(active ? r : s) * dp);
   unsigned long long scored = 0, yes_early = 0;
-  int lane = threadIdx.x & 31;
-  for (int pi = 0; pi < npairs; ++pi) {
-    PairEntry pe = pairs[(int64_t)B * nq + pi];
-    int j = pe.j;
-    int k = kk[j];
-    float nrm = qn[j];
-    bool surv_flag = false, yes = false;
-    float sq = 0.f;
+  const int lane = threadIdx.x & 31;
+  for (int p0 = 0; p0 < npairs; p0 += kPairChunk) {
+    const int pn = min(kPairChunk, npairs - p0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < pn; i += blockDim.x) {
+      const PairEntry pe = pairs[(int64_t)B * nq + p0 + i];
+      pinfo[i] = PairInfo{pe.j, kk[pe.j], pe.cphi, pe.sphi, qn[pe.j]};
+    }
+    __syncthreads();
+    float Lnext = 0.f;
     if (active) {
-      float L = (k <= kmax) ? Lt[(int64_t)(k - 1) * mz + r] : -INFINITY;
-      float Llo = (L == -INFINITY) ? -INFINITY : __fsub_rd(L, E);
-      bool pruned = false;
-      if (pe.cphi <= 1.5f) {   // Lemma 3 with the slack of the FP32 terms
-        float ub = __fmul_ru(__fmul_ru(nu, nrm), fmaf(pe.cphi, ct, pe.sphi * st_) + 2.f * slack);
-        pruned = ub < Llo;
-      }
-      if (!pruned) {
-        ++scored;
-        const float4* q4 = reinterpret_cast<const float4*>(Qd + (int64_t)j * dp);
-        float acc = 0.f;
-        for (int c = 0; c < dp4; ++c) {
-          float4 a = myu[c], b = __ldg(q4 + c);
-          acc = fmaf(a.x, b.x, acc);
-          acc = fmaf(a.y, b.y, acc);
-          acc = fmaf(a.z, b.z, acc);
-          acc = fmaf(a.w, b.w, acc);
-        }
-        sq = acc;
-        float eq = __fmul_ru(__fmul_ru(gamma, nu), nrm) + 1e-30f;
-        float hi = __fadd_ru(sq, eq), lo = __fsub_rd(sq, eq);
-        if (hi < Llo) {
-          // "no": at least k items of P' score above <u,q>
-        } else if (l_exact && k <= kmax && lo >= __fadd_ru(L, E)) {
-          yes = true;                        // <u,q> >= exact k-th largest score
-        } else if (lo >= __fmul_ru(__fmul_ru(nu, pnorm[k - 1]), 1.f + 2.f * gamma)) {
-          yes = true;                        // <u,q> >= ||u|| ||p_k|| >= k-th largest score
-        } else {
-          surv_flag = true;
-        }
-      }
+      const int k0 = pinfo[0].k;
+      Lnext = (k0 <= kmax) ? Lt[(int64_t)(k0 - 1) * mz + r] : -INFINITY;
     }
-    if (yes) {
-      ++yes_early;
-      atomicOr(&bitmap[(int64_t)j * words + (id >> 5)], 1u << (id & 31));
-    }
-    unsigned m = __ballot_sync(0xffffffffu, surv_flag);
-    if (m) {
-      unsigned long long base = 0;
-      int leader = __ffs(m) - 1;
-      if (lane == leader) base = atomicAdd(surv_count, (unsigned long long)__popc(m));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if (surv_flag) {
-        unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
-        if ((int64_t)slot < surv_cap) surv[slot] = Survivor{r, j, sq};
+    for (int pi = 0; pi < pn; ++pi) {
+      const PairInfo pe = pinfo[pi];
+      const float L = Lnext;
+      if (active && pi + 1 < pn) {
+        const int k1 = pinfo[pi + 1].k;
+        Lnext = (k1 <= kmax) ? Lt[(int64_t)(k1 - 1) * mz + r] : -INFINITY;
+      }
+      const int j = pe.j, k = pe.k;
+      const float nrm = pe.nrm;
+      bool surv_flag = false, yes = false;
+      float sq = 0.f;
+      if (active) {
+        const float Llo = (L == -INFINITY) ? -INFINITY : __fsub_rd(L, E);
+        bool pruned = false;
+        if (pe.cphi <= 1.5f) {   // Lemma 3 with the slack of the FP32 terms
+          const float ub = __fmul_ru(__fmul_ru(nu, nrm), fmaf(pe.cphi, ct, pe.sphi * st_) + 2.f * slack);
+          pruned = ub < Llo;
+        }
+        if (!pruned) {
+          ++scored;
+          const float4* q4 = reinterpret_cast<const float4*>(Qd + (int64_t)j * dp);
+          float acc = 0.f;
+          for (int c = 0; c < dp4; ++c) {
+            const float4 a = myu[c], b = __ldg(q4 + c);
+            acc = fmaf(a.x, b.x, acc);
+            acc = fmaf(a.y, b.y, acc);
+            acc = fmaf(a.z, b.z, acc);
+            acc = fmaf(a.w, b.w, acc);
+          }
+          sq = acc;
+          const float eq = __fmul_ru(__fmul_ru(gamma, nu), nrm) + 1e-30f;
+          const float hi = __fadd_ru(sq, eq), lo = __fsub_rd(sq, eq);
+          if (hi < Llo) {
+            // "no": at least k items of P' score above <u,q>
+          } else if (l_exact && k <= kmax && lo >= __fadd_ru(L, E)) {
+            yes = true;                        // <u,q> >= exact k-th largest score
+          } else if (lo >= __fmul_ru(__fmul_ru(nu, pnorm[k - 1]), 1.f + 2.f * gamma)) {
+            yes = true;                        // <u,q> >= ||u|| ||p_k|| >= k-th largest score
+          } else {
+            surv_flag = true;
+          }
+        }
+      }
+      if (yes) {
+        ++yes_early;
+        atomicOr(&bitmap[(int64_t)j * words + (id >> 5)], 1u << (id & 31));
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, surv_flag);
+      if (m) {
+        unsigned long long base = 0;
+        const int leader = __ffs(m) - 1;
+        if (lane == leader) base = atomicAdd(surv_count, (unsigned long long)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (surv_flag) {
+          const unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
+          if ((int64_t)slot < surv_cap) surv[slot] = Survivor{r, j, sq};
+        }
       }
     }
   }
-  // per-warp totals
   for (int o = 16; o > 0; o >>= 1) {
     scored += __shfl_xor_sync(0xffffffffu, scored, o);
     yes_early += __shfl_xor_sync(0xffffffffu, yes_early, o);
@@ -597,6 +635,7 @@ sah_status run_batch(Index* ix, const float* Q_dev, int32_t nq, const int32_t* k
 
   for (int q0 = 0; q0 < nq; q0 += qb) {
     const int nqb = std::min(qb, nq - q0);
+    int64_t agg_last_ns = 0;
     WsLayout L = layout_for(ix, nqb, nchunks);
     SAH_TRY(ensure_ws(ix, L.total, st));
     char* w = (char*)ix->ws.base;
@@ -622,7 +661,7 @@ sah_status run_batch(Index* ix, const float* Q_dev, int32_t nq, const int32_t* k
     tm.end(0, 1);
     if (ix->nb > 0) {
       tm.begin(1);
-      block_filter_kernel<<<ix->nb, 256, 0, st>>>(ix->bcent, ix->bcos, ix->bsin, ix->LB, ix->nb, ix->kmax,
+      block_filter_kernel<<<ix->nb, 128, sizeof(float) * ix->dp, st>>>(ix->bcent, ix->bcos, ix->bsin, ix->LB, ix->nb, ix->kmax,
                                                   ix->n, ix->dp, Qd, qn, kk, nqb, ix->cone_slack, pairs,
                                                   pcount, stats);
       SAH_CUDA(cudaGetLastError());
@@ -631,6 +670,7 @@ sah_status run_batch(Index* ix, const float* Q_dev, int32_t nq, const int32_t* k
       size_t smem = (size_t)16 * threads * ((ix->dp / 4) | 1);
       int stage = smem <= 160 * 1024 ? 1 : 0;
       if (!stage) smem = 0;
+      smem += sizeof(PairInfo) * kPairChunk;
       if (smem > 48 * 1024)
         SAH_CUDA(cudaFuncSetAttribute(user_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       for (int attempt = 0;; ++attempt) {
@@ -649,6 +689,7 @@ sah_status run_batch(Index* ix, const float* Q_dev, int32_t nq, const int32_t* k
         tm.collect();
         if ((int64_t)ns <= surv_cap) {
           agg.survivors += (int64_t)ns;
+          agg_last_ns = (int64_t)ns;
           break;
         }
         // The survivor list overflowed: grow it and repeat the user pass.  Bits already
@@ -662,17 +703,24 @@ sah_status run_batch(Index* ix, const float* Q_dev, int32_t nq, const int32_t* k
         SAH_CUDA(cudaMemsetAsync(stats + ST_USERS_SCORED, 0, 2 * sizeof(unsigned long long), st));
       }
       Survivor* surv = (Survivor*)ix->surv.base;
-      size_t vsmem = (size_t)16 * kVerifyWarps * (ix->dp / 4);
-      if (vsmem > 48 * 1024)
-        SAH_CUDA(cudaFuncSetAttribute(verify_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsmem));
-      int sms = 152;
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
       tm.begin(3);
-      verify_exact_kernel<<<sms * 8, kVerifyWarps * 32, vsmem, st>>>(
-          surv, survcnt, surv_cap, ix->Ut, ix->unorm, ix->uid, ix->Ps, ix->pnorm, ix->n, ix->d, ix->dp, Qd, qn,
-          kk, ix->gamma, bitmap, words, stats);
-      SAH_CUDA(cudaGetLastError());
-      tm.end(3, 1);
+      int nl = 0;
+      if (ix->dk > 0) {
+        SAH_TRY(run_verify_tc(ix, surv, survcnt, std::min<int64_t>(agg_last_ns, surv_cap), Qd, qn, kk, bitmap,
+                              words, stats, ST_FP64, ST_ITEMS, st, &nl));
+      } else {
+        size_t vsmem = (size_t)16 * kVerifyWarps * (ix->dp / 4);
+        if (vsmem > 48 * 1024)
+          SAH_CUDA(cudaFuncSetAttribute(verify_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsmem));
+        int sms = 152;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
+        verify_exact_kernel<<<sms * 8, kVerifyWarps * 32, vsmem, st>>>(
+            surv, survcnt, surv_cap, ix->Ut, ix->unorm, ix->uid, ix->Ps, ix->pnorm, ix->n, ix->d, ix->dp, Qd, qn,
+            kk, ix->gamma, bitmap, words, stats);
+        SAH_CUDA(cudaGetLastError());
+        nl = 1;
+      }
+      tm.end(3, nl);
     }
     tm.begin(4);
     int n_compact = 3;
@@ -732,6 +780,15 @@ sah_status run_batch(Index* ix, const float* Q_dev, int32_t nq, const int32_t* k
   }
   SAH_CUDA(cudaStreamSynchronize(st));
   tm.collect();
+  if (ix->dev_timeout) {
+    int to = 0;
+    SAH_CUDA(cudaMemcpy(&to, ix->dev_timeout, sizeof(int), cudaMemcpyDeviceToHost));
+    if (to) {
+      SAH_CUDA(cudaMemset(ix->dev_timeout, 0, sizeof(int)));
+      set_error("a bounded device-side wait of the tensor-core kMIPS decision ran out");
+      return SAH_ERR_DEVICE_TIMEOUT;
+    }
+  }
   for (int i = 0; i < StageTimer::kStages; ++i) {
     agg.stage_ms[i] = tm.ms[i];
     agg.stage_launches[i] = tm.launches[i];
@@ -741,7 +798,7 @@ sah_status run_batch(Index* ix, const float* Q_dev, int32_t nq, const int32_t* k
   agg.n_items = ix->n;
   agg.n_users = ix->m;
   agg.n_blocks = ix->nb;
-  agg.device_bytes = (int64_t)(ix->bytes + ix->ws.bytes + ix->surv.bytes + ix->res.bytes);
+  agg.device_bytes = (int64_t)(ix->bytes + ix->ws.bytes + ix->surv.bytes + ix->res.bytes + ix->tcws.bytes);
   ix->stats = agg;
   std::memcpy(offsets_host, offs.data(), sizeof(int64_t) * (nq + 1));
   return SAH_OK;

@@ -2,6 +2,7 @@
 // small device helpers and the launchers each .cu file exports to the C-ABI layer.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -29,6 +30,13 @@ sah_status cuda_status(cudaError_t e, const char* what);
     sah_status s_ = (call);                                         \
     if (s_ != SAH_OK) return s_;                                    \
   } while (0)
+
+// A user sent to the per-user kMIPS decision (Alg. 2 / exact count) for one query.
+struct Survivor {
+  int32_t upos;   // user position (leaf order)
+  int32_t j;      // query within the sub-batch
+  float sq;       // FP32 <u,q>
+};
 
 // ------------------------------------------------------------------ index layout in HBM
 // Items are stored in descending norm order (Alg. 1, Alg. 4), users in Cone-Tree leaf
@@ -76,11 +84,36 @@ struct Index {
   float* Lt = nullptr;        // [kmax][m_nz]
   float* Eu = nullptr;        // m_nz: bound on |Lt - exact| (and on any FP32 item score's error)
 
+  // BF16 copies for the tensor-core kMIPS decision (precision SAH_BF16), K padded to dk
+  int32_t dk = 0;             // roundup(d, 64); 0 when the tensor-core path is off
+  uint16_t* Ub = nullptr;     // m_nz x dk, leaf order
+  uint16_t* Pb = nullptr;     // n x dk, descending norm order
+  CUtensorMap tmap_P{};       // TMA map of Pb: box 64 x 256, 128-byte swizzle
+  int* dev_timeout = nullptr; // set by a kernel whose bounded wait ran out
+
+  // SA-ALSH over the items behind P' (Alg. 1): norm partitions S_j (descending M_j), their
+  // centroids and radii, SRP codes of the SAT-transformed items (Eq. 6, Eq. 9) sorted
+  // into buckets per (partition, table), and the users' codes (Eq. 7, Eq. 9).
+  int32_t sa_parts = 0;
+  int32_t sa_K = 0, sa_bits = 0, sa_d1p = 0, sa_nprobes = 0;
+  std::vector<int32_t> sa_start_h;   // t + 1 item positions
+  int32_t* sa_start = nullptr;
+  float* sa_M = nullptr;             // t: M_j
+  float* sa_R = nullptr;             // t: R_j
+  float* sa_cent = nullptr;          // t x dp: c_j
+  float* sa_A = nullptr;             // (K * bits) x d1p SRP projection vectors
+  uint16_t* sa_ucode = nullptr;      // m_nz x K user codes (leaf order)
+  int32_t* sa_boff = nullptr;        // t * K + 1 bucket-array offsets
+  uint16_t* sa_bcode = nullptr;      // codes, sorted within each (partition, table)
+  int32_t* sa_bitem = nullptr;       // matching item positions
+  uint32_t* sa_probes = nullptr;     // XOR masks with popcount <= probe_radius
+
   std::vector<void*> allocs;
   size_t bytes = 0;
   Workspace ws;               // per-call workspace (queries, pair lists, bitmaps)
   Workspace surv;             // survivor list, grown on demand
   Workspace res;              // ids of the last call, before they go to the caller
+  Workspace tcws;             // tensor-core kMIPS decision: sorted rows, statuses, band lists
   sah_stats stats{};
   bool timing = false;
 };
@@ -133,6 +166,20 @@ __device__ inline double dot64_seq(const float* __restrict__ a, const float* __r
 // index_build.cu
 sah_status build_index_device(Index* ix, const float* U_dev, const float* P_dev,
                               cudaStream_t st);
+// saalsh.cu
+sah_status build_saalsh(Index* ix, const float* srp_host, cudaStream_t st);
+// Alg. 2 for every SA-ALSH survivor; sets the answer bits of the "yes" ones.
+sah_status run_saalsh(Index* ix, const Survivor* surv, int64_t nsurv, const float* Qd, const float* qn,
+                      const int32_t* kk, uint32_t* bitmap, int64_t words, unsigned long long* stats,
+                      int stat_items, cudaStream_t st, int* launches);
+// verify_tc.cu
+sah_status build_bf16_copies(Index* ix, cudaStream_t st);
+// Decides every survivor with the tcgen05 kernel and sets the answer bits; the counters
+// of double-precision decisions and scanned items go to stats[stat_fp64], stats[stat_items].
+sah_status run_verify_tc(Index* ix, const Survivor* surv, const unsigned long long* surv_count_dev,
+                         int64_t nsurv, const float* Qd, const float* qn, const int32_t* kk, uint32_t* bitmap,
+                         int64_t words, unsigned long long* stats, int stat_fp64, int stat_items,
+                         cudaStream_t st, int* launches);
 // query.cu
 // Alg. 5 for nq queries (Q, ks, modes on the device).  On success the ascending ids of
 // every query sit in ix->res (query j at [offsets_host[j], offsets_host[j+1])).

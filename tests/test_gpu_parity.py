@@ -29,11 +29,12 @@ def test_c1_every_query_and_k(sah):
             assert np.array_equal(ix.rkmips(q, k), want[k]), (qi, k)
 
 
+@pytest.mark.parametrize("precision", [0, 1])               # FP32 SIMT, BF16 tensor cores
 @pytest.mark.parametrize("leaf", [1, 20, 256])
 @pytest.mark.parametrize("p_prime", [10, 0, 1 << 30])      # small P', 4 k_max, all items
-def test_mf_batch_mixed_k(sah, leaf, p_prime):
+def test_mf_batch_mixed_k(sah, leaf, p_prime, precision):
     W = workload.make("c2", m=6000, n=2500)
-    ix = sah.Index(W.U, W.P, k_max=50, leaf_size=leaf, p_prime=p_prime, seed=7)
+    ix = sah.Index(W.U, W.P, k_max=50, leaf_size=leaf, p_prime=p_prime, seed=7, precision=precision)
     ks = [1, 5, 10, 20, 50, 64]
     qidx = W.query_idx[:8]
     Q = np.repeat(W.P[qidx], len(ks), axis=0)
@@ -47,10 +48,11 @@ def test_mf_batch_mixed_k(sah, leaf, p_prime):
     assert st["queries"] == len(Q) and st["results"] == sum(len(g) for g in got)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("seed", range(4))
-def test_integer_ties(sah, seed):
+def test_integer_ties(sah, seed, precision):
     P, U, q = workload.tie_case(40, 300, 3, lo=-2, hi=2, seed=seed)
-    ix = sah.Index(U, P, k_max=8, leaf_size=4, p_prime=6, seed=seed)
+    ix = sah.Index(U, P, k_max=8, leaf_size=4, p_prime=6, seed=seed, precision=precision)
     for qq in (q, P[seed]):                                         # q outside and inside P
         want = _truth(U, P, qq, range(1, 42))
         for k in range(1, 42):
@@ -81,10 +83,16 @@ def test_zero_query_and_foreign_query(sah):
             assert np.array_equal(ix.rkmips(q, k), want[k])
 
 
-@pytest.mark.parametrize("d", [1, 3, 50, 300])
-def test_dimensions(sah, d):
-    W = workload.make("c1", m=700, n=400, d=d)
-    ix = sah.Index(W.U, W.P, k_max=10, leaf_size=32)
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("d", [1, 3, 50, 100, 128, 300])
+def test_dimensions(sah, d, precision):
+    W = workload.make("c1", m=700, n=600, d=d)
+    if precision == 1 and d > 128:
+        with pytest.raises(sah.SahError) as e:
+            sah.Index(W.U, W.P, k_max=10, leaf_size=32, precision=precision)
+        assert e.value.status == sah.SAH_ERR_UNSUPPORTED
+        return
+    ix = sah.Index(W.U, W.P, k_max=10, leaf_size=32, p_prime=12, precision=precision)
     for qi in W.query_idx[:3]:
         q = W.P[qi]
         want = _truth(W.U, W.P, q, (1, 10, 11))
@@ -164,12 +172,13 @@ def test_empty_batch(sah):
 
 
 @pytest.mark.slow
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("p_prime", [0, 1 << 30])
-def test_c2_full_size_sampled(sah, p_prime):
+def test_c2_full_size_sampled(sah, p_prime, precision):
     """n = 17,770, m = 480,000, d = 50 (the benchmark's workload): the answers of a fixed
     sample of users, plus every user the GPU returned, agree with the oracle."""
     W = workload.make("c2")
-    ix = sah.Index(W.U, W.P, k_max=50, leaf_size=256, p_prime=p_prime)
+    ix = sah.Index(W.U, W.P, k_max=50, leaf_size=256, p_prime=p_prime, precision=precision)
     ks = [int(k) for k in W.ks]
     qidx = W.query_idx[:6]
     Q = np.repeat(W.P[qidx], len(ks), axis=0)
@@ -184,3 +193,20 @@ def test_c2_full_size_sampled(sah, p_prime):
             g = set(got[a * len(ks) + b].tolist())
             member = np.array([u in g for u in users.tolist()])
             assert np.array_equal(member, c < k), (qi, k)
+
+
+def test_tensor_core_path_runs_and_counts(sah):
+    """With BF16 the kMIPS decisions go through the tcgen05 kernel (several launches per
+    call in the decision stage) and give the oracle's answers."""
+    W = workload.make("c2", m=8000, n=3000)
+    ix = sah.Index(W.U, W.P, k_max=50, leaf_size=128, p_prime=60, precision=sah.BF16)
+    ix.set_timing(True)
+    Q, K, _ = W.requests()
+    Q, K = Q[:50], K[:50]
+    got = ix.rkmips_batch(Q, K)
+    st = ix.stats()
+    assert st["survivors"] > 1000 and st["items_scanned"] > 0
+    assert st["stage_launches"][3] >= 6
+    for j in range(0, 50, 7):
+        c = oracle.count_above(W.U, W.P, Q[j])
+        assert np.array_equal(got[j], np.flatnonzero(c < K[j]))
