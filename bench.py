@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--threshold", default="full", choices=["full", "paper"],
                     help="full: |P'| = n (exact thresholds); paper: |P'| = 4 k_max")
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"],
+                    help="working precision of the kMIPS decision (bf16: tcgen05 tensor cores)")
     ap.add_argument("--leaf-size", type=int, default=256)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -139,12 +141,14 @@ def stage_algorithmic(stats, d, n_users, distinct_k):
                                  bytes=stats["survivors"] * (4.0 * d + 12))
     words = (n_users + 31) // 32
     out["compaction"] = dict(flops=0.0, bytes=stats["queries"] * words * 4.0 * 3 + 4.0 * stats["results"])
+    out["saalsh"] = dict(flops=2.0 * d * stats["items_scanned"], bytes=stats["items_scanned"] * 4.0 * d)
     return out
 
 
-STAGE_NAMES = ["prep", "block_pass", "user_pass", "kmips_decision", "compaction"]
+STAGE_NAMES = ["prep", "block_pass", "user_pass", "kmips_decision", "compaction", "saalsh"]
 STAGE_KERNELS = {"block_pass": "block_filter_kernel", "user_pass": "user_scan_kernel",
-                 "kmips_decision": "verify_exact_kernel", "compaction": "bitmap_emit_kernel"}
+                 "kmips_decision": "verify_exact_kernel", "compaction": "bitmap_emit_kernel",
+                 "saalsh": "saalsh_decide_kernel"}
 
 
 def kernel_traffic(kernel: str):
@@ -223,7 +227,8 @@ def config_block(W, args):
     return {"workload": f"{W.name}: n={W.n} items, m={W.m} users, d={W.d}, mf rank-50 lognormal(0,0.7), "
                         f"5% items x3, seed 0; {len(W.query_idx)} item queries x k in {list(map(int, W.ks))}",
             "queries_per_step": int(len(W.query_idx) * (len(W.ks) if W.every_k else 1)),
-            "threshold_mode": args.threshold, "leaf_size": args.leaf_size, "k_max": 50,
+            "threshold_mode": args.threshold, "precision": args.precision, "leaf_size": args.leaf_size,
+            "k_max": 50,
             "l2": "flushed between timed steps (256 MiB write)"}
 
 
@@ -249,11 +254,13 @@ def main():
     distinct_k = len(set(K.tolist()))
     stream = torch.cuda.current_stream()
 
-    def build(threshold):
+    def build(threshold, precision):
         pp = (1 << 30) if threshold == "full" else 0
+        prec = sah.BF16 if precision == "bf16" else sah.FP32
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ix = sah.Index(W.U, W.P, k_max=50, leaf_size=args.leaf_size, p_prime=pp, seed=0, stream=stream)
+        ix = sah.Index(W.U, W.P, k_max=50, leaf_size=args.leaf_size, p_prime=pp, seed=0, precision=prec,
+                       n_tables=128, code_bits=16, stream=stream)
         torch.cuda.synchronize()
         return ix, time.perf_counter() - t0
 
@@ -261,13 +268,14 @@ def main():
     Qd = torch.from_numpy(Q).to(dev)
     Kd = torch.from_numpy(K).to(dev)
 
-    def measure(ix, steps, warmup, timing=True):
-        host = ix.rkmips_batch(Q, K)                    # sizes the output once
+    def measure(ix, steps, warmup, timing=True, modes=None):
+        host = ix.rkmips_batch(Q, K, modes=modes)       # sizes the output once
         total = sum(len(h) for h in host)
         out = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
         offs = torch.empty(nq + 1, dtype=torch.int64, device=dev)
+        Md = None if modes is None else torch.from_numpy(np.ascontiguousarray(modes, dtype=np.int32)).to(dev)
         for _ in range(warmup):
-            ix.rkmips_batch_device(Qd, Kd, out, offs, stream=stream)
+            ix.rkmips_batch_device(Qd, Kd, out, offs, modes=Md, stream=stream)
         ix.set_timing(timing)
         times, stage_ms, launches = [], np.zeros(8), np.zeros(8)
         st_last = None
@@ -277,7 +285,7 @@ def main():
             e1 = torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record(stream)
-            ix.rkmips_batch_device(Qd, Kd, out, offs, stream=stream)
+            ix.rkmips_batch_device(Qd, Kd, out, offs, modes=Md, stream=stream)
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -287,7 +295,7 @@ def main():
         ix.set_timing(False)
         return host, times, stage_ms / steps, launches / steps, st_last, total
 
-    ix, build_s = build(args.threshold)
+    ix, build_s = build(args.threshold, args.precision)
     if world > 1:
         torch.distributed.barrier()
     with ClockSampler(local) as clk:
@@ -327,23 +335,32 @@ def main():
 
     # roofline of the dominant stage
     alg = stage_algorithmic(st, W.d, W.m, distinct_k)
-    dom_i = int(np.argmax(stage_ms[1:5])) + 1
+    dom_i = int(np.argmax(stage_ms[1:6])) + 1
     dom = STAGE_NAMES[dom_i]
     a = alg[dom]
     dur_s = stage_ms[dom_i] / 1e3 / max(launches[dom_i], 1)
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    t_alu = a["flops"] / (fp32_peak * 1e12)
-    t_hbm = a["bytes"] / (peaks["hbm_gbs"] * 1e9)
     per_launch = lambda x: x / max(launches[dom_i], 1)
-    if t_alu >= t_hbm:
-        roof = {"bound": "alu", "achieved": per_launch(a["flops"]) / dur_s / 1e12, "peak": fp32_peak,
-                "unit": "TFLOP/s", "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    kernel = STAGE_KERNELS.get(dom, dom)
+    if dom == "kmips_decision" and args.precision == "bf16":
+        # the tcgen05 GEMM: useful BF16 MACs of the rows still open, per launch of the
+        # stage's kernels (the GEMM itself is one of them)
+        kernel = "verify_tc_kernel"
+        roof = {"bound": "tensor", "achieved": per_launch(a["flops"]) / dur_s / 1e12,
+                "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json bf16_tflops, burst)"}
     else:
-        roof = {"bound": "hbm", "achieved": per_launch(a["bytes"]) / dur_s / 1e9, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+        t_alu = a["flops"] / (fp32_peak * 1e12)
+        t_hbm = a["bytes"] / (peaks["hbm_gbs"] * 1e9)
+        if t_alu >= t_hbm:
+            roof = {"bound": "alu", "achieved": per_launch(a["flops"]) / dur_s / 1e12, "peak": fp32_peak,
+                    "unit": "TFLOP/s", "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+        else:
+            roof = {"bound": "hbm", "achieved": per_launch(a["bytes"]) / dur_s / 1e9, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = kernel_traffic(STAGE_KERNELS.get(dom, ""))
-    roof["kernel"] = STAGE_KERNELS.get(dom, dom)
+    roof["traffic"] = kernel_traffic(kernel)
+    roof["kernel"] = kernel
     roof["stage"] = dom
     roof["launch_ms"] = dur_s * 1e3
 
@@ -363,13 +380,33 @@ def main():
                            "per": "batch of %d queries" % nq}}
 
     if not args.no_variants and rank == 0:
-        other = "paper" if args.threshold == "full" else "full"
-        ix2, b2 = build(other)
-        _, t2, sm2, l2, st2, _ = measure(ix2, max(3, args.steps // 2), 3, timing=False)
-        line["variants"] = {f"threshold_{other}": {"value": nq * len(t2) / (sum(t2) / 1e3), "index_build_s": b2,
-                                                   "ms_per_step": float(np.mean(t2)),
-                                                   "survivors": st2["survivors"], "items_scanned": st2["items_scanned"]}}
-        ix2.close()
+        # the other threshold modes and precisions, and SA-ALSH mode with its F1 against
+        # the exact answers (which equal the FP64 oracle's, as the GPU tests check)
+        line["variants"] = {}
+        vsteps = max(3, args.steps // 2)
+        for thr in ("full", "paper"):
+            for prec in ("fp32", "bf16"):
+                same = thr == args.threshold and prec == args.precision
+                ixv, bv = (ix, build_s) if same else build(thr, prec)
+                rec = {"index_build_s": bv}
+                if not same:
+                    _, tv, _, _, stv, _ = measure(ixv, vsteps, 3, timing=False)
+                    rec.update(value=nq * len(tv) / (sum(tv) / 1e3), ms_per_step=float(np.mean(tv)),
+                               survivors=stv["survivors"], items_scanned=stv["items_scanned"])
+                else:
+                    rec.update(value=value, ms_per_step=t_step_ms, survivors=st["survivors"],
+                               items_scanned=st["items_scanned"])
+                if thr == "paper":
+                    sa_modes = np.full(nq, sah.SAALSH, np.int32)
+                    hsa, tsa, _, _, stsa, _ = measure(ixv, vsteps, 3, timing=False, modes=sa_modes)
+                    exact_sets = host if same else ixv.rkmips_batch(Q, K)
+                    f1 = [2 * len(set(a.tolist()) & set(b.tolist())) / max(1, len(a) + len(b)) if (len(a) + len(b))
+                          else 1.0 for a, b in zip(hsa, exact_sets)]
+                    rec["saalsh"] = {"value": nq * len(tsa) / (sum(tsa) / 1e3), "ms_per_step": float(np.mean(tsa)),
+                                     "f1_vs_exact": float(np.mean(f1)), "min_f1": float(np.min(f1))}
+                line["variants"][f"{thr}_{prec}"] = rec
+                if not same:
+                    ixv.close()
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_sample_run(W, Q, K, qrows, args.cpu_seconds)

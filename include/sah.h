@@ -107,6 +107,44 @@ sah_status sah_rkmips_batch(sah_index* index, const float* Q, int32_t nq, const 
                             const int32_t* modes, int32_t buffers_on_device, int32_t* out_ids,
                             int64_t cap, int64_t* out_offsets, void* cuda_stream);
 
+/* ---- Serving: continuous batching over one index -------------------------------------
+ * A server owns `workers` host threads, each with its own CUDA stream, workspace and
+ * pinned staging buffers.  Requests are queued by sah_server_submit (any thread); every
+ * free worker takes all queued requests up to max_batch as one batch, answers them with
+ * one pass of the query path and publishes each request's ids and latency (submit to
+ * completion).  Requests arriving while batches run are taken by the next free worker,
+ * so batches overlap on the device.  A batch is admitted only if its workspace fits the
+ * worker's share of hbm_budget_bytes (0: 8 GiB) and the device's free memory; otherwise it
+ * is halved until it fits.  Results are identical to sah_rkmips for the same request.
+ * The index must outlive the server and must not be used through the blocking calls
+ * while the server runs. */
+
+/* Starts a server.  max_slots bounds requests held at once (queued, running or finished
+ * but not yet polled); 1 <= workers <= 8.  Errors: SAH_ERR_ARG, SAH_ERR_OOM. */
+sah_status sah_server_start(sah_index* index, int32_t max_slots, int32_t max_batch, int32_t workers,
+                            int64_t hbm_budget_bytes, sah_server** out);
+
+/* Queues one request (q: d floats, host; copied).  *ticket identifies it.  Returns
+ * SAH_ERR_BUSY when max_slots requests are held (poll finished ones first), SAH_ERR_ARG
+ * for k < 1, an unknown mode or a non-finite q. */
+sah_status sah_server_submit(sah_server* server, const float* q, int32_t k, int32_t mode, uint64_t* ticket);
+
+/* Collects a finished request: ids (ascending) to out_ids (host, cap entries), their
+ * number to *out_count, its latency in seconds to *latency_s (may be NULL).  Returns
+ * SAH_ERR_BUSY while it is queued or running, SAH_ERR_BUFFER_TOO_SMALL (with *out_count
+ * set; the result is kept) when cap is too small, SAH_ERR_ARG for an unknown ticket, or
+ * the error of its batch.  A collected ticket is forgotten. */
+sah_status sah_server_poll(sah_server* server, uint64_t ticket, int32_t* out_ids, int64_t cap,
+                           int64_t* out_count, double* latency_s);
+
+/* Batches run so far, requests they held, the largest batch, and admissions that had to
+ * halve a batch to fit the memory budget.  Any pointer may be NULL. */
+sah_status sah_server_info(sah_server* server, int64_t* batches, int64_t* batched_requests,
+                           int64_t* max_batch_seen, int64_t* split_ticks);
+
+/* Finishes every queued request, stops the workers and frees the server.  NULL is ignored. */
+sah_status sah_server_stop(sah_server* server);
+
 /* Per-stage counters of the last query call on this index (summed over its queries). */
 typedef struct {
   int64_t n_items, n_users, n_blocks, n_partitions, device_bytes;

@@ -101,6 +101,17 @@ def load(path: Optional[str] = None):
     lib.sah_index_set_timing.restype = I32
     lib.sah_rkmips_bruteforce_noalloc.argtypes = [P, I64, P, I64, I32, P, I32, P, I64, P, P]
     lib.sah_rkmips_bruteforce_noalloc.restype = I32
+    lib.sah_server_start.argtypes = [P, I32, I32, I32, I64, ctypes.POINTER(P)]
+    lib.sah_server_start.restype = I32
+    lib.sah_server_submit.argtypes = [P, P, I32, I32, ctypes.POINTER(ctypes.c_uint64)]
+    lib.sah_server_submit.restype = I32
+    lib.sah_server_poll.argtypes = [P, ctypes.c_uint64, P, I64, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_double)]
+    lib.sah_server_poll.restype = I32
+    lib.sah_server_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64),
+                                    ctypes.POINTER(I64)]
+    lib.sah_server_info.restype = I32
+    lib.sah_server_stop.argtypes = [P]
+    lib.sah_server_stop.restype = I32
     lib.sah_free_index.argtypes = [P]
     lib.sah_free_index.restype = None
     lib.sah_status_string.argtypes = [I32]
@@ -164,10 +175,10 @@ class Index:
 
     def __init__(self, U, P, params: Optional[Params] = None, stream=None, **kw):
         lib = load()
+        srp = kw.pop("srp_matrix", None)
         if params is None:
             params = default_params(**kw)
         self._keep = []
-        srp = kw.get("srp_matrix")
         if srp is not None:
             srp = _host_f32(srp)
             self._keep.append(srp)
@@ -266,3 +277,60 @@ class Index:
         s = Stats()
         _check(load().sah_index_stats(self._h, ctypes.byref(s)))
         return s.as_dict()
+
+
+class Server:
+    """Continuous-batching server over an Index (see sah_server_* in include/sah.h)."""
+
+    def __init__(self, index: "Index", max_slots: int = 4096, max_batch: int = 512, workers: int = 2,
+                 hbm_budget_bytes: int = 0):
+        self._lib = load()
+        self.index = index
+        h = ctypes.c_void_p()
+        _check(self._lib.sah_server_start(index._h, max_slots, max_batch, workers, hbm_budget_bytes,
+                                          ctypes.byref(h)))
+        self._h = h
+        self._buf = np.empty(index.m, dtype=np.int32)
+
+    def submit(self, q, k: int, mode: int = EXACT) -> int:
+        q = _host_f32(q).ravel()
+        t = ctypes.c_uint64()
+        _check(self._lib.sah_server_submit(self._h, q.ctypes.data, int(k), int(mode), ctypes.byref(t)))
+        return int(t.value)
+
+    def try_submit(self, q, k: int, mode: int = EXACT):
+        """Like submit, but returns None instead of raising when every slot is taken."""
+        q = _host_f32(q).ravel()
+        t = ctypes.c_uint64()
+        st = self._lib.sah_server_submit(self._h, q.ctypes.data, int(k), int(mode), ctypes.byref(t))
+        if st == SAH_ERR_BUSY:
+            return None
+        _check(st)
+        return int(t.value)
+
+    def poll(self, ticket: int):
+        """(ids, latency_s) once finished, None while queued or running."""
+        cnt = ctypes.c_int64()
+        lat = ctypes.c_double()
+        st = self._lib.sah_server_poll(self._h, ticket, self._buf.ctypes.data, self._buf.shape[0],
+                                       ctypes.byref(cnt), ctypes.byref(lat))
+        if st == SAH_ERR_BUSY:
+            return None
+        _check(st)
+        return self._buf[:cnt.value].copy(), lat.value
+
+    def info(self) -> dict:
+        v = [ctypes.c_int64() for _ in range(4)]
+        _check(self._lib.sah_server_info(self._h, *[ctypes.byref(x) for x in v]))
+        return dict(zip(("batches", "batched_requests", "max_batch_seen", "split_ticks"), [x.value for x in v]))
+
+    def stop(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.sah_server_stop(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass

@@ -60,14 +60,15 @@ struct sah_index {
   Index impl;
 };
 
+namespace sah {
+Index* index_impl(sah_index* h) { return &h->impl; }
+}  // namespace sah
+
 static void destroy_index(sah_index* h) {
   if (!h) return;
   Index* ix = &h->impl;
   for (void* p : ix->allocs) cudaFree(p);
-  if (ix->ws.base) cudaFree(ix->ws.base);
-  if (ix->surv.base) cudaFree(ix->surv.base);
-  if (ix->res.base) cudaFree(ix->res.base);
-  if (ix->tcws.base) cudaFree(ix->tcws.base);
+  sah::free_ctx(&ix->main_ctx);
   delete h;
 }
 
@@ -178,6 +179,7 @@ sah_status sah_build_index(const float* U, int64_t m, const float* P, int64_t n,
     Pd = tmpP;
   }
   s = sah::build_index_device(ix, Ud, Pd, st);
+  if (s == SAH_OK) s = sah::build_saalsh(ix, params ? params->srp : nullptr, st);
   cudaStreamSynchronize(st);
   if (tmpU) cudaFree(tmpU);
   if (tmpP) cudaFree(tmpP);
@@ -222,25 +224,31 @@ static sah_status batch_impl(sah_index* index, const float* Q, int32_t nq, const
       sah::set_error("unknown mode");
       return SAH_ERR_ARG;
     }
-    if (modes_h[j] == SAH_SAALSH) {
-      sah::set_error("SA-ALSH mode is not built yet");
+    if (modes_h[j] == SAH_SAALSH && ix->sa_parts == 0 && ix->pp < ix->n) {
+      sah::set_error("this index has no SA-ALSH tables (n_tables < 1)");
       return SAH_ERR_UNSUPPORTED;
     }
   }
+  bool any_sa = false;
+  for (int j = 0; j < nq; ++j) any_sa |= modes_h[j] == SAH_SAALSH;
   const float* Qd = Q;
   const int32_t* kd = ks;
+  const int32_t* md = any_sa ? modes : nullptr;
   float* tq = nullptr;
   int32_t* tk = nullptr;
   if (!on_dev) {
     SAH_CUDA(cudaMallocAsync((void**)&tq, sizeof(float) * (size_t)nq * ix->d, st));
-    SAH_CUDA(cudaMallocAsync((void**)&tk, sizeof(int32_t) * nq, st));
+    SAH_CUDA(cudaMallocAsync((void**)&tk, sizeof(int32_t) * nq * 2, st));
     SAH_CUDA(cudaMemcpyAsync(tq, Q, sizeof(float) * (size_t)nq * ix->d, cudaMemcpyHostToDevice, st));
     SAH_CUDA(cudaMemcpyAsync(tk, ks, sizeof(int32_t) * nq, cudaMemcpyHostToDevice, st));
+    if (any_sa) SAH_CUDA(cudaMemcpyAsync(tk + nq, modes_h.data(), sizeof(int32_t) * nq, cudaMemcpyHostToDevice, st));
     Qd = tq;
     kd = tk;
+    md = any_sa ? tk + nq : nullptr;
   }
   std::vector<int64_t> offs(nq + 1);
-  sah_status s = sah::run_batch(ix, Qd, nq, kd, nullptr, offs.data(), st);
+  sah::CallCtx* cx = &ix->main_ctx;
+  sah_status s = sah::run_batch(ix, cx, Qd, nq, kd, md, offs.data(), st);
   if (tq) cudaFreeAsync(tq, st);
   if (tk) cudaFreeAsync(tk, st);
   if (s != SAH_OK) return s;
@@ -258,7 +266,7 @@ static sah_status batch_impl(sah_index* index, const float* Q, int32_t nq, const
     return SAH_ERR_BUFFER_TOO_SMALL;
   }
   if (total > 0)
-    SAH_CUDA(cudaMemcpyAsync(out_ids, ix->res.base, sizeof(int32_t) * total,
+    SAH_CUDA(cudaMemcpyAsync(out_ids, cx->res.base, sizeof(int32_t) * total,
                              on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   if (on_dev) SAH_CUDA(cudaMemcpyAsync(out_offsets, offs.data(), sizeof(int64_t) * (nq + 1), cudaMemcpyHostToDevice, st));
   else std::memcpy(out_offsets, offs.data(), sizeof(int64_t) * (nq + 1));
@@ -295,11 +303,12 @@ sah_status sah_index_stats(const sah_index* index, sah_stats* out) {
     return SAH_ERR_ARG;
   }
   const Index* ix = &index->impl;
-  *out = ix->stats;
+  *out = ix->main_ctx.stats;
   out->n_items = ix->n;
   out->n_users = ix->m;
   out->n_blocks = ix->nb;
-  out->device_bytes = (int64_t)(ix->bytes + ix->ws.bytes + ix->surv.bytes + ix->res.bytes + ix->tcws.bytes);
+  out->n_partitions = ix->sa_parts;
+  out->device_bytes = (int64_t)(ix->bytes + sah::ctx_bytes(&ix->main_ctx));
   return SAH_OK;
 }
 

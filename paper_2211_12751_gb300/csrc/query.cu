@@ -172,7 +172,10 @@ __global__ void user_scan_kernel(const float* __restrict__ Ut, const float* __re
                                  const PairEntry* __restrict__ pairs, const int32_t* __restrict__ pcount,
                                  float gamma, float slack, uint32_t* __restrict__ bitmap, int64_t words,
                                  Survivor* __restrict__ surv, unsigned long long* __restrict__ surv_count,
-                                 int64_t surv_cap, unsigned long long* __restrict__ stats, int stage) {
+                                 int64_t surv_cap, unsigned long long* __restrict__ stats, int stage,
+                                 const int32_t* __restrict__ modes) {
+  // survivors of exact-mode queries go to surv[0, surv_cap) (counter surv_count[0]),
+  // those of SA-ALSH-mode queries with k <= k_max to surv[surv_cap, 2 surv_cap)
   extern __shared__ float4 us4[];
   const int B = blockIdx.x;
   const int npairs = pcount[B];
@@ -210,7 +213,9 @@ __global__ void user_scan_kernel(const float* __restrict__ Ut, const float* __re
     __syncthreads();
     for (int i = threadIdx.x; i < pn; i += blockDim.x) {
       const PairEntry pe = pairs[(int64_t)B * nq + p0 + i];
-      pinfo[i] = PairInfo{pe.j, kk[pe.j], pe.cphi, pe.sphi, qn[pe.j]};
+      const int kj = kk[pe.j];
+      const int sa = (modes != nullptr && modes[pe.j] == SAH_SAALSH && kj <= kmax) ? 1 : 0;
+      pinfo[i] = PairInfo{pe.j | (sa << 30), kj, pe.cphi, pe.sphi, qn[pe.j]};
     }
     __syncthreads();
     float Lnext = 0.f;
@@ -225,7 +230,8 @@ __global__ void user_scan_kernel(const float* __restrict__ Ut, const float* __re
         const int k1 = pinfo[pi + 1].k;
         Lnext = (k1 <= kmax) ? Lt[(int64_t)(k1 - 1) * mz + r] : -INFINITY;
       }
-      const int j = pe.j, k = pe.k;
+      const int j = pe.j & 0x3fffffff, k = pe.k;
+      const bool sa_row = (pe.j >> 30) & 1;
       const float nrm = pe.nrm;
       bool surv_flag = false, yes = false;
       float sq = 0.f;
@@ -265,15 +271,16 @@ __global__ void user_scan_kernel(const float* __restrict__ Ut, const float* __re
         ++yes_early;
         atomicOr(&bitmap[(int64_t)j * words + (id >> 5)], 1u << (id & 31));
       }
+      // every record in this loop iteration belongs to one query, so one list per warp step
       const unsigned m = __ballot_sync(0xffffffffu, surv_flag);
       if (m) {
         unsigned long long base = 0;
         const int leader = __ffs(m) - 1;
-        if (lane == leader) base = atomicAdd(surv_count, (unsigned long long)__popc(m));
+        if (lane == leader) base = atomicAdd(surv_count + (sa_row ? 1 : 0), (unsigned long long)__popc(m));
         base = __shfl_sync(0xffffffffu, base, leader);
         if (surv_flag) {
           const unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
-          if ((int64_t)slot < surv_cap) surv[slot] = Survivor{r, j, sq};
+          if ((int64_t)slot < surv_cap) surv[(sa_row ? surv_cap : 0) + slot] = Survivor{r, j, sq};
         }
       }
     }
@@ -533,7 +540,7 @@ WsLayout layout_for(const Index* ix, int qb, int nchunks) {
   L.kk = take(sizeof(int32_t) * qb);
   L.pairs = take(sizeof(PairEntry) * (size_t)std::max(ix->nb, 1) * qb);
   L.pcount = take(sizeof(int32_t) * std::max(ix->nb, 1));
-  L.survcnt = take(sizeof(unsigned long long));
+  L.survcnt = take(2 * sizeof(unsigned long long));
   L.bitmap = take(sizeof(uint32_t) * (size_t)qb * words);
   L.chunk = take(sizeof(int32_t) * (size_t)qb * nchunks);
   L.offsets = take(sizeof(int64_t) * (size_t)(qb + 1));
@@ -558,10 +565,10 @@ sah_status ensure_buf(Workspace* b, size_t bytes, cudaStream_t st) {
   return SAH_OK;
 }
 
-sah_status ensure_ws(Index* ix, size_t bytes, cudaStream_t st) { return ensure_buf(&ix->ws, bytes, st); }
+sah_status ensure_ws(CallCtx* cx, size_t bytes, cudaStream_t st) { return ensure_buf(&cx->ws, bytes, st); }
 
-sah_status ensure_surv(Index* ix, int64_t cap, cudaStream_t st) {
-  return ensure_buf(&ix->surv, sizeof(Survivor) * (size_t)std::max<int64_t>(cap, 1), st);
+sah_status ensure_surv(CallCtx* cx, int64_t cap, cudaStream_t st) {
+  return ensure_buf(&cx->surv, 2 * sizeof(Survivor) * (size_t)std::max<int64_t>(cap, 1), st);
 }
 
 // CUDA events around each stage, on the call's stream (only when timing is enabled).
@@ -615,7 +622,23 @@ struct StageTimer {
 // so that the workspace stays bounded; every sub-batch's ids are emitted into the
 // index's internal result buffer first, so the caller's buffer is only written once the
 // total is known to fit.
-sah_status run_batch(Index* ix, const float* Q_dev, int32_t nq, const int32_t* ks_dev,
+void free_ctx(CallCtx* cx) {
+  for (Workspace* w : {&cx->ws, &cx->surv, &cx->res, &cx->tcws}) {
+    if (w->base) cudaFree(w->base);
+    w->base = nullptr;
+    w->bytes = 0;
+  }
+}
+
+size_t ctx_bytes(const CallCtx* cx) { return cx->ws.bytes + cx->surv.bytes + cx->res.bytes + cx->tcws.bytes; }
+
+size_t batch_workspace_bytes(const Index* ix, int32_t nq) {
+  const int64_t words = (ix->m + 31) / 32;
+  const int nchunks = (int)((words + kWordsPerChunk - 1) / kWordsPerChunk);
+  return layout_for(ix, std::max(nq, 1), nchunks).total;
+}
+
+sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, const int32_t* ks_dev,
                      const int32_t* modes_dev, int64_t* offsets_host, cudaStream_t st) {
   (void)modes_dev;
   const int64_t words = (ix->m + 31) / 32;
@@ -625,7 +648,7 @@ sah_status run_batch(Index* ix, const float* Q_dev, int32_t nq, const int32_t* k
                        sizeof(int32_t) * nchunks + sizeof(float) * ix->dp + 16;
   int qb = (int)std::max<size_t>(1, std::min<size_t>((size_t)nq, (size_t(1) << 30) / per_q));
   qb = std::min(qb, 4096);
-  int64_t surv_cap = std::max<int64_t>((int64_t)(ix->surv.bytes / sizeof(Survivor)), 1 << 20);
+  int64_t surv_cap = std::max<int64_t>((int64_t)(cx->surv.bytes / (2 * sizeof(Survivor))), 1 << 20);
 
   sah_stats agg{};
   agg.queries = nq;
@@ -635,10 +658,10 @@ sah_status run_batch(Index* ix, const float* Q_dev, int32_t nq, const int32_t* k
 
   for (int q0 = 0; q0 < nq; q0 += qb) {
     const int nqb = std::min(qb, nq - q0);
-    int64_t agg_last_ns = 0;
+    int64_t agg_last_ns = 0, agg_last_sa = 0;
     WsLayout L = layout_for(ix, nqb, nchunks);
-    SAH_TRY(ensure_ws(ix, L.total, st));
-    char* w = (char*)ix->ws.base;
+    SAH_TRY(ensure_ws(cx, L.total, st));
+    char* w = (char*)cx->ws.base;
     float* Qd = (float*)(w + L.qd);
     float* qn = (float*)(w + L.qn);
     int32_t* kk = (int32_t*)(w + L.kk);
@@ -652,7 +675,7 @@ sah_status run_batch(Index* ix, const float* Q_dev, int32_t nq, const int32_t* k
 
     tm.begin(0);
     SAH_CUDA(cudaMemsetAsync(stats, 0, sizeof(unsigned long long) * ST_COUNT, st));
-    SAH_CUDA(cudaMemsetAsync(survcnt, 0, sizeof(unsigned long long), st));
+    SAH_CUDA(cudaMemsetAsync(survcnt, 0, 2 * sizeof(unsigned long long), st));
     SAH_CUDA(cudaMemsetAsync(bitmap, 0, sizeof(uint32_t) * (size_t)nqb * words, st));
     SAH_CUDA(cudaMemcpyAsync(kk, ks_dev + q0, sizeof(int32_t) * nqb, cudaMemcpyDeviceToDevice, st));
     prep_queries_kernel<<<grid_for(nqb, 8), 256, 0, st>>>(Q_dev + (int64_t)q0 * ix->d, nqb, ix->d, ix->dp,
@@ -674,22 +697,25 @@ sah_status run_batch(Index* ix, const float* Q_dev, int32_t nq, const int32_t* k
       if (smem > 48 * 1024)
         SAH_CUDA(cudaFuncSetAttribute(user_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       for (int attempt = 0;; ++attempt) {
-        SAH_TRY(ensure_surv(ix, surv_cap, st));
-        Survivor* surv = (Survivor*)ix->surv.base;
+        SAH_TRY(ensure_surv(cx, surv_cap, st));
+        Survivor* surv = (Survivor*)cx->surv.base;
         tm.begin(2);
         user_scan_kernel<<<ix->nb, threads, smem, st>>>(
             ix->Ut, ix->unorm, ix->ucos, ix->usin, ix->uid, ix->bstart, ix->Lt, ix->Eu, ix->pnorm, ix->n,
             ix->m_nz, ix->kmax, ix->l_exact ? 1 : 0, ix->dp, Qd, qn, kk, nqb, pairs, pcount, ix->gamma,
-            ix->cone_slack, bitmap, words, surv, survcnt, surv_cap, stats, stage);
+            ix->cone_slack, bitmap, words, surv, survcnt, surv_cap, stats, stage,
+            modes_dev ? modes_dev + q0 : nullptr);
         SAH_CUDA(cudaGetLastError());
         tm.end(2, 1);
-        unsigned long long ns = 0;
-        SAH_CUDA(cudaMemcpyAsync(&ns, survcnt, sizeof(ns), cudaMemcpyDeviceToHost, st));
+        unsigned long long ns2[2] = {0, 0};
+        SAH_CUDA(cudaMemcpyAsync(ns2, survcnt, sizeof(ns2), cudaMemcpyDeviceToHost, st));
         SAH_CUDA(cudaStreamSynchronize(st));
         tm.collect();
+        const unsigned long long ns = std::max(ns2[0], ns2[1]);
         if ((int64_t)ns <= surv_cap) {
-          agg.survivors += (int64_t)ns;
-          agg_last_ns = (int64_t)ns;
+          agg.survivors += (int64_t)(ns2[0] + ns2[1]);
+          agg_last_ns = (int64_t)ns2[0];
+          agg_last_sa = (int64_t)ns2[1];
           break;
         }
         // The survivor list overflowed: grow it and repeat the user pass.  Bits already
@@ -699,15 +725,15 @@ sah_status run_batch(Index* ix, const float* Q_dev, int32_t nq, const int32_t* k
           return SAH_ERR_OOM;
         }
         surv_cap = (int64_t)ns + (int64_t)ns / 4 + 1024;
-        SAH_CUDA(cudaMemsetAsync(survcnt, 0, sizeof(unsigned long long), st));
+        SAH_CUDA(cudaMemsetAsync(survcnt, 0, 2 * sizeof(unsigned long long), st));
         SAH_CUDA(cudaMemsetAsync(stats + ST_USERS_SCORED, 0, 2 * sizeof(unsigned long long), st));
       }
-      Survivor* surv = (Survivor*)ix->surv.base;
+      Survivor* surv = (Survivor*)cx->surv.base;
       tm.begin(3);
       int nl = 0;
       if (ix->dk > 0) {
-        SAH_TRY(run_verify_tc(ix, surv, survcnt, std::min<int64_t>(agg_last_ns, surv_cap), Qd, qn, kk, bitmap,
-                              words, stats, ST_FP64, ST_ITEMS, st, &nl));
+        SAH_TRY(run_verify_tc(ix, cx, surv, survcnt, agg_last_ns, Qd, qn, kk, bitmap, words, stats, ST_FP64,
+                              ST_ITEMS, st, &nl));
       } else {
         size_t vsmem = (size_t)16 * kVerifyWarps * (ix->dp / 4);
         if (vsmem > 48 * 1024)
@@ -721,6 +747,12 @@ sah_status run_batch(Index* ix, const float* Q_dev, int32_t nq, const int32_t* k
         nl = 1;
       }
       tm.end(3, nl);
+      if (agg_last_sa > 0) {
+        int nsa = 0;
+        tm.begin(5);
+        SAH_TRY(run_saalsh(ix, surv + surv_cap, agg_last_sa, Qd, qn, kk, bitmap, words, stats, ST_ITEMS, st, &nsa));
+        tm.end(5, nsa);
+      }
     }
     tm.begin(4);
     int n_compact = 3;
@@ -762,17 +794,17 @@ sah_status run_batch(Index* ix, const float* Q_dev, int32_t nq, const int32_t* k
     if (new_total > res_total) {
       // grow the index's result buffer, keeping what earlier sub-batches wrote
       size_t need = sizeof(int32_t) * (size_t)new_total;
-      if (need > ix->res.bytes) {
+      if (need > cx->res.bytes) {
         Workspace nr;
-        SAH_TRY(ensure_buf(&nr, std::max(need, 2 * ix->res.bytes), st));
+        SAH_TRY(ensure_buf(&nr, std::max(need, 2 * cx->res.bytes), st));
         if (res_total)
-          SAH_CUDA(cudaMemcpyAsync(nr.base, ix->res.base, sizeof(int32_t) * res_total, cudaMemcpyDeviceToDevice, st));
+          SAH_CUDA(cudaMemcpyAsync(nr.base, cx->res.base, sizeof(int32_t) * res_total, cudaMemcpyDeviceToDevice, st));
         SAH_CUDA(cudaStreamSynchronize(st));
-        if (ix->res.base) cudaFree(ix->res.base);
-        ix->res = nr;
+        if (cx->res.base) cudaFree(cx->res.base);
+        cx->res = nr;
       }
       tm.begin(4);
-      bitmap_emit_kernel<<<gc, 256, 0, st>>>(bitmap, words, nchunks, chunk, offsets, (int32_t*)ix->res.base);
+      bitmap_emit_kernel<<<gc, 256, 0, st>>>(bitmap, words, nchunks, chunk, offsets, (int32_t*)cx->res.base);
       SAH_CUDA(cudaGetLastError());
       tm.end(4, 1);
     }
@@ -798,8 +830,9 @@ sah_status run_batch(Index* ix, const float* Q_dev, int32_t nq, const int32_t* k
   agg.n_items = ix->n;
   agg.n_users = ix->m;
   agg.n_blocks = ix->nb;
-  agg.device_bytes = (int64_t)(ix->bytes + ix->ws.bytes + ix->surv.bytes + ix->res.bytes + ix->tcws.bytes);
-  ix->stats = agg;
+  agg.n_partitions = ix->sa_parts;
+  agg.device_bytes = (int64_t)(ix->bytes + ctx_bytes(cx));
+  cx->stats = agg;
   std::memcpy(offsets_host, offs.data(), sizeof(int64_t) * (nq + 1));
   return SAH_OK;
 }

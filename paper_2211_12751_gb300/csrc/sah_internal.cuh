@@ -47,6 +47,20 @@ struct Workspace {
   size_t bytes = 0;
 };
 
+// Everything one query call needs besides the index: a caller (the C-ABI's blocking
+// calls, or one worker of the serving loop) owns one of these, so calls with different
+// contexts can run concurrently on different streams.
+struct CallCtx {
+  Workspace ws;      // queries, pair lists, bitmaps, counters
+  Workspace surv;    // survivor lists, grown on demand
+  Workspace res;     // ids of the last call, before they go to the caller
+  Workspace tcws;    // tensor-core kMIPS decision: sorted rows, statuses, band lists
+  sah_stats stats{};
+};
+
+void free_ctx(CallCtx* cx);
+size_t ctx_bytes(const CallCtx* cx);
+
 struct Index {
   int device = 0;
   int64_t n = 0, m = 0, m_nz = 0;
@@ -110,11 +124,7 @@ struct Index {
 
   std::vector<void*> allocs;
   size_t bytes = 0;
-  Workspace ws;               // per-call workspace (queries, pair lists, bitmaps)
-  Workspace surv;             // survivor list, grown on demand
-  Workspace res;              // ids of the last call, before they go to the caller
-  Workspace tcws;             // tensor-core kMIPS decision: sorted rows, statuses, band lists
-  sah_stats stats{};
+  CallCtx main_ctx;           // context of the blocking C-ABI calls
   bool timing = false;
 };
 
@@ -176,14 +186,16 @@ sah_status run_saalsh(Index* ix, const Survivor* surv, int64_t nsurv, const floa
 sah_status build_bf16_copies(Index* ix, cudaStream_t st);
 // Decides every survivor with the tcgen05 kernel and sets the answer bits; the counters
 // of double-precision decisions and scanned items go to stats[stat_fp64], stats[stat_items].
-sah_status run_verify_tc(Index* ix, const Survivor* surv, const unsigned long long* surv_count_dev,
+sah_status run_verify_tc(Index* ix, CallCtx* cx, const Survivor* surv, const unsigned long long* surv_count_dev,
                          int64_t nsurv, const float* Qd, const float* qn, const int32_t* kk, uint32_t* bitmap,
                          int64_t words, unsigned long long* stats, int stat_fp64, int stat_items,
                          cudaStream_t st, int* launches);
 // query.cu
 // Alg. 5 for nq queries (Q, ks, modes on the device).  On success the ascending ids of
-// every query sit in ix->res (query j at [offsets_host[j], offsets_host[j+1])).
-sah_status run_batch(Index* ix, const float* Q_dev, int32_t nq, const int32_t* ks_dev,
+// every query sit in cx->res (query j at [offsets_host[j], offsets_host[j+1])).
+sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, const int32_t* ks_dev,
                      const int32_t* modes_dev, int64_t* offsets_host, cudaStream_t st);
+// Device bytes a call with nq queries needs in its workspace (pair lists, bitmaps).
+size_t batch_workspace_bytes(const Index* ix, int32_t nq);
 
 }  // namespace sah

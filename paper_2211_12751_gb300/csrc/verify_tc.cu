@@ -482,7 +482,7 @@ sah_status build_bf16_copies(Index* ix, cudaStream_t st) {
   return SAH_OK;
 }
 
-sah_status run_verify_tc(Index* ix, const Survivor* surv, const unsigned long long* surv_count_dev,
+sah_status run_verify_tc(Index* ix, CallCtx* cx, const Survivor* surv, const unsigned long long* surv_count_dev,
                          int64_t ns, const float* Qd, const float* qn, const int32_t* kk, uint32_t* bitmap,
                          int64_t words, unsigned long long* stats, int stat_fp64, int stat_items,
                          cudaStream_t st, int* launches) {
@@ -496,20 +496,20 @@ sah_status run_verify_tc(Index* ix, const Survivor* surv, const unsigned long lo
                o_rows = take(sizeof(Survivor) * ns), o_scut = take(sizeof(int32_t) * ns),
                o_stat = take(sizeof(int32_t) * ns), o_cert = take(sizeof(int32_t) * ns),
                o_band = take(sizeof(int32_t) * ns), o_items = take(sizeof(int32_t) * ns * kBandCap);
-  if (ix->tcws.bytes < need) {
+  if (cx->tcws.bytes < need) {
     SAH_CUDA(cudaStreamSynchronize(st));
-    if (ix->tcws.base) cudaFree(ix->tcws.base);
-    ix->tcws.base = nullptr;
-    ix->tcws.bytes = 0;
-    cudaError_t e = cudaMalloc(&ix->tcws.base, need + need / 4);
+    if (cx->tcws.base) cudaFree(cx->tcws.base);
+    cx->tcws.base = nullptr;
+    cx->tcws.bytes = 0;
+    cudaError_t e = cudaMalloc(&cx->tcws.base, need + need / 4);
     if (e != cudaSuccess) {
       cudaGetLastError();
       set_error("tensor-core verify workspace allocation failed");
       return SAH_ERR_OOM;
     }
-    ix->tcws.bytes = need + need / 4;
+    cx->tcws.bytes = need + need / 4;
   }
-  char* w = (char*)ix->tcws.base;
+  char* w = (char*)cx->tcws.base;
   int32_t* cut = (int32_t*)(w + o_cut);
   int32_t* hist = (int32_t*)(w + o_hist);
   Survivor* rows = (Survivor*)(w + o_rows);
