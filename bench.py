@@ -57,7 +57,29 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-rate", type=float, default=20000.0, help="Poisson arrival rate (requests/s)")
+    ap.add_argument("--serve-requests", type=int, default=6000)
     return ap.parse_args()
+
+
+def whole_job_value(local_ms_total, queries_per_rank_step, steps, world, all_reduce_max):
+    """Weak scaling: every rank answers its own batch of the same size each step; the job's
+    time is the slowest rank's, and the value counts every rank's queries."""
+    t_ms = float(all_reduce_max(float(local_ms_total)))
+    return queries_per_rank_step * steps * world / (t_ms / 1e3), t_ms
+
+
+def torch_max_reducer(device):
+    import torch
+    import torch.distributed as dist
+
+    def red(x):
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return t.item()
+    return red
 
 
 def dist_env():
@@ -146,7 +168,7 @@ def stage_algorithmic(stats, d, n_users, distinct_k):
 
 
 STAGE_NAMES = ["prep", "block_pass", "user_pass", "kmips_decision", "compaction", "saalsh"]
-STAGE_KERNELS = {"block_pass": "block_filter_kernel", "user_pass": "user_scan_kernel",
+STAGE_KERNELS = {"block_pass": "block_filter_kernel", "user_pass": "user_scan_reg_kernel",
                  "kmips_decision": "verify_exact_kernel", "compaction": "bitmap_emit_kernel",
                  "saalsh": "saalsh_decide_kernel"}
 
@@ -193,6 +215,41 @@ def oracle_sample_run(W, Q, K, qrows, budget_s):
     queries_equiv = nq * per_q * (len(sample) / W.m)
     return dict(value=queries_equiv / t, seconds=t, threads=threads, users=len(sample), nq=int(nq),
                 sample=sample, memberships=memberships)
+
+
+def serve_stream(sah, ix, W, rate, count, seed=1):
+    """Poisson arrivals (k uniform in 1..50, modes half exact, half SA-ALSH) through the
+    continuous-batching server; latencies are the library's submit-to-completion times."""
+    arrivals = workload.poisson_arrivals(count, rate, seed=seed)
+    rng = np.random.default_rng(seed + 1)
+    qrows = rng.integers(0, W.n, count)
+    ks = rng.integers(1, 51, count)
+    modes = rng.integers(0, 2, count)
+    srv = sah.Server(ix, max_slots=max(4096, count), max_batch=512, workers=2)
+    lat, pending = [], []
+    t_start = time.perf_counter()
+    i = 0
+    while i < count or pending:
+        now = time.perf_counter() - t_start
+        while i < count and arrivals[i] <= now:
+            pending.append(srv.submit(W.P[qrows[i]], int(ks[i]), int(modes[i])))
+            i += 1
+        still = []
+        for t in pending:
+            r = srv.poll(t)
+            if r is None:
+                still.append(t)
+            else:
+                lat.append(r[1])
+        pending = still
+    wall = time.perf_counter() - t_start
+    info = srv.info()
+    srv.stop()
+    lat = np.array(lat) * 1e3
+    return {"offered_rate": rate, "requests": count, "throughput_qps": count / wall,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_batch": info["batched_requests"] / max(1, info["batches"]), "max_batch": info["max_batch_seen"],
+            "mix": "k uniform 1..50, modes 50/50 exact / SA-ALSH, item queries"}
 
 
 def run_reference(args):
@@ -302,11 +359,9 @@ def main():
         host, times, stage_ms, launches, st, total = measure(ix, args.steps, max(args.warmup, 3))
     clocks = clk.summary()
     t_step_ms = float(np.mean(times))
-    t_max = torch.tensor([sum(times)], dtype=torch.float64, device=dev)
     if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    value = nq * args.steps * world / (float(t_max.item()) / 1e3)
+        torch.distributed.barrier()
+    value, _ = whole_job_value(sum(times), nq, args.steps, world, torch_max_reducer(dev))
 
     # e2e: pinned host buffers through the same C-ABI call (copies inside the timed call)
     Qh = torch.from_numpy(Q).pin_memory()
@@ -327,7 +382,7 @@ def main():
         assert s == 0, s
         if i >= args.warmup:
             e2e_times.append(e0.elapsed_time(e1))
-    e2e_value = nq * args.steps * world / (sum(e2e_times) / 1e3)
+    e2e_value, _ = whole_job_value(sum(e2e_times), nq, args.steps, world, torch_max_reducer(dev))
     h2d = Q.nbytes + K.nbytes
     d2h = (nq + 1) * 8 + total * 4
     got_e2e = offh.numpy().copy()
@@ -407,6 +462,9 @@ def main():
                 line["variants"][f"{thr}_{prec}"] = rec
                 if not same:
                     ixv.close()
+
+    if rank == 0 and not args.no_serving:
+        line["serving"] = serve_stream(sah, ix, W, args.serve_rate, args.serve_requests)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_sample_run(W, Q, K, qrows, args.cpu_seconds)

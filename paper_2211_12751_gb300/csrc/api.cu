@@ -197,43 +197,36 @@ static sah_status batch_impl(sah_index* index, const float* Q, int32_t nq, const
   Index* ix = &index->impl;
   if (nq == 0) {
     if (out_offsets) {
-      if (on_dev) cudaMemsetAsync(out_offsets, 0, sizeof(int64_t), st), cudaStreamSynchronize(st);
-      else out_offsets[0] = 0;
+      if (on_dev) {
+        SAH_CUDA(cudaMemsetAsync(out_offsets, 0, sizeof(int64_t), st));
+        SAH_CUDA(cudaStreamSynchronize(st));
+      } else {
+        out_offsets[0] = 0;
+      }
     }
     return SAH_OK;
   }
-  std::vector<int32_t> ks_h(nq), modes_h(nq, SAH_EXACT);
-  if (on_dev) {
-    SAH_CUDA(cudaMemcpyAsync(ks_h.data(), ks, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, st));
-    if (modes) SAH_CUDA(cudaMemcpyAsync(modes_h.data(), modes, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, st));
-    SAH_CUDA(cudaStreamSynchronize(st));
-  } else {
-    std::memcpy(ks_h.data(), ks, sizeof(int32_t) * nq);
-    if (modes) std::memcpy(modes_h.data(), modes, sizeof(int32_t) * nq);
+  // host buffers are checked here; device buffers (k, mode, finiteness) on the device
+  if (!on_dev) {
+    for (int j = 0; j < nq; ++j) {
+      if (ks[j] < 1) {
+        sah::set_error("k must be >= 1");
+        return SAH_ERR_ARG;
+      }
+      if (modes && modes[j] != SAH_EXACT && modes[j] != SAH_SAALSH) {
+        sah::set_error("unknown mode");
+        return SAH_ERR_ARG;
+      }
+    }
     if (!sah::all_finite(Q, (int64_t)nq * ix->d)) {
       sah::set_error("a query vector holds a non-finite value");
       return SAH_ERR_ARG;
     }
   }
-  for (int j = 0; j < nq; ++j) {
-    if (ks_h[j] < 1) {
-      sah::set_error("k must be >= 1");
-      return SAH_ERR_ARG;
-    }
-    if (modes_h[j] != SAH_EXACT && modes_h[j] != SAH_SAALSH) {
-      sah::set_error("unknown mode");
-      return SAH_ERR_ARG;
-    }
-    if (modes_h[j] == SAH_SAALSH && ix->sa_parts == 0 && ix->pp < ix->n) {
-      sah::set_error("this index has no SA-ALSH tables (n_tables < 1)");
-      return SAH_ERR_UNSUPPORTED;
-    }
-  }
-  bool any_sa = false;
-  for (int j = 0; j < nq; ++j) any_sa |= modes_h[j] == SAH_SAALSH;
+  sah::CallCtx* cx = &ix->main_ctx;
   const float* Qd = Q;
   const int32_t* kd = ks;
-  const int32_t* md = any_sa ? modes : nullptr;
+  const int32_t* md = modes;
   float* tq = nullptr;
   int32_t* tk = nullptr;
   if (!on_dev) {
@@ -241,19 +234,19 @@ static sah_status batch_impl(sah_index* index, const float* Q, int32_t nq, const
     SAH_CUDA(cudaMallocAsync((void**)&tk, sizeof(int32_t) * nq * 2, st));
     SAH_CUDA(cudaMemcpyAsync(tq, Q, sizeof(float) * (size_t)nq * ix->d, cudaMemcpyHostToDevice, st));
     SAH_CUDA(cudaMemcpyAsync(tk, ks, sizeof(int32_t) * nq, cudaMemcpyHostToDevice, st));
-    if (any_sa) SAH_CUDA(cudaMemcpyAsync(tk + nq, modes_h.data(), sizeof(int32_t) * nq, cudaMemcpyHostToDevice, st));
+    if (modes) SAH_CUDA(cudaMemcpyAsync(tk + nq, modes, sizeof(int32_t) * nq, cudaMemcpyHostToDevice, st));
     Qd = tq;
     kd = tk;
-    md = any_sa ? tk + nq : nullptr;
+    md = modes ? tk + nq : nullptr;
   }
   std::vector<int64_t> offs(nq + 1);
-  sah::CallCtx* cx = &ix->main_ctx;
-  sah_status s = sah::run_batch(ix, cx, Qd, nq, kd, md, offs.data(), st);
+  bool wrote = false;
+  sah_status s = sah::run_batch(ix, cx, Qd, nq, kd, md, on_dev ? out_ids : nullptr, cap,
+                                on_dev ? out_offsets : nullptr, offs.data(), &wrote, st);
   if (tq) cudaFreeAsync(tq, st);
   if (tk) cudaFreeAsync(tk, st);
-  if (s != SAH_OK) return s;
-  int64_t total = offs[nq];
-  if (total > cap) {
+  const int64_t total = offs[nq];
+  if (s == SAH_ERR_BUFFER_TOO_SMALL || (s == SAH_OK && total > cap)) {
     if (out_offsets) {
       if (on_dev) {
         cudaMemcpyAsync(out_offsets + nq, &total, sizeof(int64_t), cudaMemcpyHostToDevice, st);
@@ -265,12 +258,16 @@ static sah_status batch_impl(sah_index* index, const float* Q, int32_t nq, const
     sah::set_error("result buffer too small: " + std::to_string(total) + " ids needed");
     return SAH_ERR_BUFFER_TOO_SMALL;
   }
-  if (total > 0)
-    SAH_CUDA(cudaMemcpyAsync(out_ids, cx->res.base, sizeof(int32_t) * total,
-                             on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-  if (on_dev) SAH_CUDA(cudaMemcpyAsync(out_offsets, offs.data(), sizeof(int64_t) * (nq + 1), cudaMemcpyHostToDevice, st));
-  else std::memcpy(out_offsets, offs.data(), sizeof(int64_t) * (nq + 1));
-  SAH_CUDA(cudaStreamSynchronize(st));
+  if (s != SAH_OK) return s;
+  if (!wrote) {
+    if (total > 0)
+      SAH_CUDA(cudaMemcpyAsync(out_ids, cx->res.base, sizeof(int32_t) * total,
+                               on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    if (on_dev)
+      SAH_CUDA(cudaMemcpyAsync(out_offsets, offs.data(), sizeof(int64_t) * (nq + 1), cudaMemcpyHostToDevice, st));
+    SAH_CUDA(cudaStreamSynchronize(st));
+  }
+  if (!on_dev) std::memcpy(out_offsets, offs.data(), sizeof(int64_t) * (nq + 1));
   return SAH_OK;
 }
 

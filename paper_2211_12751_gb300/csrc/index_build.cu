@@ -260,14 +260,19 @@ __global__ void leaf_stats_kernel(const float* __restrict__ Uh, int dp, const in
 constexpr int kUsersPerWarp = 4;
 constexpr int kTopkWarps = 8;
 
-__device__ inline void list_insert(float& a, float& b, float v, int lane) {
+__device__ inline void list_insert(float& a, float& b, int& ia, int& ib, float v, int id, int lane) {
   int pos = __popc(__ballot_sync(0xffffffffu, a > v)) + __popc(__ballot_sync(0xffffffffu, b > v));
   float prev_b = __shfl_up_sync(0xffffffffu, b, 1);
+  int prev_ib = __shfl_up_sync(0xffffffffu, ib, 1);
   int s0 = 2 * lane, s1 = 2 * lane + 1;
   float na = (s0 < pos) ? a : (s0 == pos ? v : prev_b);
+  int nia = (s0 < pos) ? ia : (s0 == pos ? id : prev_ib);
   float nb = (s1 < pos) ? b : (s1 == pos ? v : a);
+  int nib = (s1 < pos) ? ib : (s1 == pos ? id : ia);
   a = na;
   b = nb;
+  ia = nia;
+  ib = nib;
 }
 
 __device__ inline float list_get(float a, float b, int slot) {
@@ -279,7 +284,7 @@ __device__ inline float list_get(float a, float b, int slot) {
 __global__ void __launch_bounds__(kTopkWarps * 32)
 topk_lower_bounds_kernel(const float* __restrict__ Ut, const float* __restrict__ Ps, int dp,
                          int64_t m, int pp, int kmax, int tile_items, int stride4,
-                         float* __restrict__ Lt) {
+                         float* __restrict__ Lt, int32_t* __restrict__ ids_out, float* __restrict__ vlast_out) {
   extern __shared__ float4 sm4[];
   float4* tileP = sm4;                                        // tile_items x stride4
   float4* us = sm4 + (size_t)tile_items * stride4;            // 32 users x (dp/4)
@@ -292,11 +297,16 @@ topk_lower_bounds_kernel(const float* __restrict__ Ut, const float* __restrict__
     us[i] = (u < m) ? reinterpret_cast<const float4*>(Ut + u * dp)[c] : make_float4(0.f, 0.f, 0.f, 0.f);
   }
   float la[kUsersPerWarp], lb[kUsersPerWarp], thr[kUsersPerWarp];
+  int ia[kUsersPerWarp], ib[kUsersPerWarp];
+  // with ids requested, all 64 slots are kept and the threshold is the 64th value
+  const int keep = ids_out ? 64 : kmax;
 #pragma unroll
   for (int w = 0; w < kUsersPerWarp; ++w) {
     la[w] = -INFINITY;
     lb[w] = -INFINITY;
     thr[w] = -INFINITY;
+    ia[w] = -1;
+    ib[w] = -1;
   }
   const float4* myu = us + (size_t)(warp * kUsersPerWarp) * dp4;
   for (int t0 = 0; t0 < pp; t0 += tile_items) {
@@ -333,8 +343,8 @@ topk_lower_bounds_kernel(const float* __restrict__ Ut, const float* __restrict__
         while (mask) {
           int src = __ffs(mask) - 1;
           float v = __shfl_sync(0xffffffffu, s[w], src);
-          list_insert(la[w], lb[w], v, lane);
-          thr[w] = list_get(la[w], lb[w], kmax - 1);
+          list_insert(la[w], lb[w], ia[w], ib[w], v, t0 + base + src, lane);
+          thr[w] = list_get(la[w], lb[w], keep - 1);
           mask &= ~(1u << src);
           // drop candidates the new threshold already excludes
           mask &= __ballot_sync(0xffffffffu, cand && s[w] > thr[w]);
@@ -345,11 +355,64 @@ topk_lower_bounds_kernel(const float* __restrict__ Ut, const float* __restrict__
 #pragma unroll
   for (int w = 0; w < kUsersPerWarp; ++w) {
     int64_t u = u0 + warp * kUsersPerWarp + w;
+    const float last = list_get(la[w], lb[w], 63);
     if (u < m) {
       int s0 = 2 * lane, s1 = 2 * lane + 1;
       if (s0 < kmax) Lt[(int64_t)s0 * m + u] = la[w];
       if (s1 < kmax) Lt[(int64_t)s1 * m + u] = lb[w];
+      if (ids_out) {
+        ids_out[(int64_t)s0 * m + u] = ia[w];
+        ids_out[(int64_t)s1 * m + u] = ib[w];
+        if (lane == 0) vlast_out[u] = last;
+      }
     }
+  }
+}
+
+// Exact thresholds (all items in P'): the 64 listed items of every user re-scored in
+// double precision in the order i = 0..d-1 and ranked; T64[k-1][u] is the k-th largest
+// double-precision score whenever the list provably holds every item that can rank k or
+// better: the 64th FP32 score plus twice the FP32 bound (and a margin for the double
+// rounding) stays below the k-th FP32 score.  Otherwise T64 is NaN for that k.
+__global__ void tau64_kernel(const float* __restrict__ Ut, const float* __restrict__ Ps, int d, int dp, int64_t m,
+                             int kmax, const int32_t* __restrict__ ids, const float* __restrict__ vlast,
+                             const float* __restrict__ Lt, const float* __restrict__ Eu,
+                             const float* __restrict__ unorm, float mmax, double* __restrict__ T64) {
+  __shared__ double sv[8][64];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t u = (int64_t)blockIdx.x * 8 + warp;
+  if (u >= m) return;
+  const float* ur = Ut + u * dp;
+  double x[2];
+  for (int h = 0; h < 2; ++h) {
+    const int id = ids[(int64_t)(2 * lane + h) * m + u];
+    x[h] = id >= 0 ? dot64_seq(ur, Ps + (int64_t)id * dp, d) : -INFINITY;
+    sv[warp][2 * lane + h] = x[h];
+  }
+  __syncwarp();
+  // rank of each value (ties broken by slot), then the sorted order
+  double sorted_me[2];
+  int rank[2];
+  for (int h = 0; h < 2; ++h) {
+    const int me = 2 * lane + h;
+    int r = 0;
+    for (int o = 0; o < 64; ++o) {
+      const double y = sv[warp][o];
+      r += (y > x[h]) || (y == x[h] && o < me);
+    }
+    rank[h] = r;
+    sorted_me[h] = x[h];
+  }
+  __syncwarp();
+  for (int h = 0; h < 2; ++h) sv[warp][rank[h]] = sorted_me[h];
+  __syncwarp();
+  const float E = Eu[u];
+  const float last = vlast[u];
+  const double margin = 1e-9 * (double)unorm[u] * (double)mmax;
+  for (int k0 = lane; k0 < kmax; k0 += 32) {
+    const float tk = Lt[(int64_t)k0 * m + u];
+    const bool covered = (last == -INFINITY) || ((double)last + 2.0 * (double)E + margin < (double)tk);
+    T64[(int64_t)k0 * m + u] = covered ? sv[warp][k0] : (double)NAN;
   }
 }
 
@@ -613,6 +676,8 @@ sah_status build_index_device(Index* ix, const float* U_dev, const float* P_dev,
 
   // ---- A1: lower-bound arrays over P' and the per-block bounds
   const int kmax = ix->kmax;
+  int32_t* ids64 = nullptr;
+  float* vlast = nullptr;
   SAH_TRY(dev_alloc(ix, (void**)&ix->Lt, sizeof(float) * (size_t)kmax * mz));
   SAH_TRY(dev_alloc(ix, (void**)&ix->Eu, sizeof(float) * mz));
   {
@@ -624,8 +689,12 @@ sah_status build_index_device(Index* ix, const float* U_dev, const float* P_dev,
                                   (int)smem));
     unsigned grid = grid_for(mz, kTopkWarps * kUsersPerWarp);
     if (ix->pp > 0) {
+      if (ix->l_exact) {
+        SAH_CUDA(cudaMallocAsync((void**)&ids64, sizeof(int32_t) * 64 * (size_t)mz, st));
+        SAH_CUDA(cudaMallocAsync((void**)&vlast, sizeof(float) * (size_t)mz, st));
+      }
       topk_lower_bounds_kernel<<<grid, kTopkWarps * 32, smem, st>>>(ix->Ut, ix->Ps, dp, mz, ix->pp, kmax,
-                                                                    tile_items, stride4, ix->Lt);
+                                                                    tile_items, stride4, ix->Lt, ids64, vlast);
     } else {
       // no P': every lower bound is -inf
       fill_i32_kernel<<<grid_for((int64_t)kmax * mz, 256), 256, 0, st>>>(
@@ -634,6 +703,12 @@ sah_status build_index_device(Index* ix, const float* U_dev, const float* P_dev,
     SAH_CUDA(cudaGetLastError());
   }
   user_error_kernel<<<grid_for(mz, 256), 256, 0, st>>>(ix->unorm, mz, ix->gamma, ix->mmax, ix->Eu);
+  if (ids64) {
+    SAH_TRY(dev_alloc(ix, (void**)&ix->T64, sizeof(double) * (size_t)kmax * mz));
+    tau64_kernel<<<grid_for(mz, 8), 256, 0, st>>>(ix->Ut, ix->Ps, ix->d, dp, mz, kmax, ids64, vlast, ix->Lt, ix->Eu,
+                                                  ix->unorm, ix->mmax, ix->T64);
+    SAH_CUDA(cudaGetLastError());
+  }
   SAH_TRY(dev_alloc(ix, (void**)&ix->LB, sizeof(float) * (size_t)kmax * ix->nb));
   block_lower_bounds_kernel<<<grid_for((int64_t)kmax * ix->nb, 256), 256, 0, st>>>(
       ix->Lt, ix->Eu, ix->unorm, ix->bstart, ix->nb, mz, kmax, ix->LB);
@@ -654,6 +729,8 @@ sah_status build_index_device(Index* ix, const float* U_dev, const float* P_dev,
   cudaFreeAsync(tile_i32, st);
   cudaFreeAsync(best_d, st);
   cudaFreeAsync(orig_of_pos, st);
+  if (ids64) cudaFreeAsync(ids64, st);
+  if (vlast) cudaFreeAsync(vlast, st);
   SAH_CUDA(cudaStreamSynchronize(st));
   return SAH_OK;
 }

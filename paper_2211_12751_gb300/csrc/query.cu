@@ -36,6 +36,8 @@ enum StatSlot {
   ST_KEPT_USERS,
   ST_ITEMS,
   ST_BAD_Q,
+  ST_BAD_K,
+  ST_EMIT_OVERFLOW,
   ST_COUNT
 };
 
@@ -46,10 +48,13 @@ inline unsigned grid_for(int64_t n, int per) { return (unsigned)((n + per - 1) /
 // ---------------------------------------------------------------- query preparation
 __global__ void prep_queries_kernel(const float* __restrict__ Q, int nq, int d, int dp,
                                     float* __restrict__ Qd, float* __restrict__ qn,
+                                    const int32_t* __restrict__ kk, const int32_t* __restrict__ modes,
                                     unsigned long long* __restrict__ stats) {
   int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   int lane = threadIdx.x & 31;
   if (j >= nq) return;
+  if (lane == 0 && (kk[j] < 1 || (modes && modes[j] != SAH_EXACT && modes[j] != SAH_SAALSH)))
+    atomicAdd(&stats[ST_BAD_K], 1ull);
   float s = 0.f;
   bool fin = true;
   for (int i = lane; i < dp; i += 32) {
@@ -173,7 +178,7 @@ __global__ void user_scan_kernel(const float* __restrict__ Ut, const float* __re
                                  float gamma, float slack, uint32_t* __restrict__ bitmap, int64_t words,
                                  Survivor* __restrict__ surv, unsigned long long* __restrict__ surv_count,
                                  int64_t surv_cap, unsigned long long* __restrict__ stats, int stage,
-                                 const int32_t* __restrict__ modes) {
+                                 const int32_t* __restrict__ modes, const double* __restrict__ T64, int d) {
   // survivors of exact-mode queries go to surv[0, surv_cap) (counter surv_count[0]),
   // those of SA-ALSH-mode queries with k <= k_max to surv[surv_cap, 2 surv_cap)
   extern __shared__ float4 us4[];
@@ -206,7 +211,7 @@ __global__ void user_scan_kernel(const float* __restrict__ Ut, const float* __re
   // rows too wide to stage for the whole leaf are read from global memory (L1/L2)
   const float4* myu = stage ? us4 + t * stride4
                             : reinterpret_cast<const float4*>(Ut + (int64_t)(active ? r : s) * dp);
-  unsigned long long scored = 0, yes_early = 0;
+  unsigned long long scored = 0, yes_early = 0, fp64_here = 0;
   const int lane = threadIdx.x & 31;
   for (int p0 = 0; p0 < npairs; p0 += kPairChunk) {
     const int pn = min(kPairChunk, npairs - p0);
@@ -262,6 +267,15 @@ __global__ void user_scan_kernel(const float* __restrict__ Ut, const float* __re
             yes = true;                        // <u,q> >= exact k-th largest score
           } else if (lo >= __fmul_ru(__fmul_ru(nu, pnorm[k - 1]), 1.f + 2.f * gamma)) {
             yes = true;                        // <u,q> >= ||u|| ||p_k|| >= k-th largest score
+          } else if (T64 != nullptr && k <= kmax && !sa_row) {
+            // exact thresholds: the count rule in double precision is <u,q> >= tau_u(k)
+            const double t64 = T64[(int64_t)(k - 1) * mz + r];
+            if (t64 == t64) {
+              ++fp64_here;
+              yes = dot64_seq(reinterpret_cast<const float*>(Ut + (int64_t)r * dp), Qd + (int64_t)j * dp, d) >= t64;
+            } else {
+              surv_flag = true;
+            }
           } else {
             surv_flag = true;
           }
@@ -288,10 +302,171 @@ __global__ void user_scan_kernel(const float* __restrict__ Ut, const float* __re
   for (int o = 16; o > 0; o >>= 1) {
     scored += __shfl_xor_sync(0xffffffffu, scored, o);
     yes_early += __shfl_xor_sync(0xffffffffu, yes_early, o);
+    fp64_here += __shfl_xor_sync(0xffffffffu, fp64_here, o);
   }
   if (lane == 0) {
     if (scored) atomicAdd(&stats[ST_USERS_SCORED], scored);
     if (yes_early) atomicAdd(&stats[ST_YES_EARLY], yes_early);
+    if (fp64_here) atomicAdd(&stats[ST_FP64], fp64_here);
+  }
+}
+
+// Register-tiled form of the user pass for d <= 128: each thread keeps its user's row in
+// registers; the leaf's surviving queries are staged in shared memory kQChunk at a time
+// and scored kQG at a time (kQG FMAs per broadcast shared-memory load).  Every (user,
+// query) decision is the same as in user_scan_kernel: Lemma 3 first, then the FP32
+// score against the lower bound, the exact threshold and the ||p_k|| bound.
+constexpr int kQG = 4;
+constexpr int kQChunk = 128;
+
+template <int DP4MAX>
+__global__ void __launch_bounds__(256)
+user_scan_reg_kernel(const float* __restrict__ Ut, const float* __restrict__ unorm,
+                     const float* __restrict__ ucos, const float* __restrict__ usin,
+                     const int32_t* __restrict__ uid, const int32_t* __restrict__ bstart,
+                     const float* __restrict__ Lt, const float* __restrict__ Eu,
+                     const float* __restrict__ pnorm, int64_t n, int64_t mz, int kmax,
+                     int l_exact, int dp, const float* __restrict__ Qd,
+                     const float* __restrict__ qn, const int32_t* __restrict__ kk, int nq,
+                     const PairEntry* __restrict__ pairs, const int32_t* __restrict__ pcount,
+                     float gamma, float slack, uint32_t* __restrict__ bitmap, int64_t words,
+                     Survivor* __restrict__ surv, unsigned long long* __restrict__ surv_count,
+                     int64_t surv_cap, unsigned long long* __restrict__ stats,
+                     const int32_t* __restrict__ modes, const double* __restrict__ T64, int d) {
+  extern __shared__ float4 sq4[];
+  const int B = blockIdx.x;
+  const int npairs = pcount[B];
+  if (npairs == 0) return;
+  const int s = bstart[B], e = bstart[B + 1];
+  const int cnt = e - s;
+  if (threadIdx.x == 0) atomicAdd(&stats[ST_KEPT_USERS], (unsigned long long)cnt);
+  const int dp4 = dp / 4;
+  float4* qs = sq4;                                              // kQChunk x dp4
+  PairInfo* pinfo = reinterpret_cast<PairInfo*>(qs + (size_t)kQChunk * dp4);
+  const int t = threadIdx.x;
+  const bool active = t < cnt;
+  const int r = s + (active ? t : 0);
+  float4 ur[DP4MAX];
+#pragma unroll
+  for (int c = 0; c < DP4MAX; ++c)
+    ur[c] = (c < dp4 && active) ? reinterpret_cast<const float4*>(Ut + (int64_t)r * dp)[c]
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+  float nu = 0.f, ct = 0.f, st_ = 0.f, E = 0.f;
+  int32_t id = 0;
+  if (active) {
+    nu = unorm[r];
+    ct = ucos[r];
+    st_ = usin[r];
+    E = Eu[r];
+    id = uid[r];
+  }
+  unsigned long long scored = 0, yes_early = 0, fp64_here = 0;
+  const int lane = threadIdx.x & 31;
+  for (int p0 = 0; p0 < npairs; p0 += kQChunk) {
+    const int pn = min(kQChunk, npairs - p0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < pn; i += blockDim.x) {
+      const PairEntry pe = pairs[(int64_t)B * nq + p0 + i];
+      const int kj = kk[pe.j];
+      const int sa = (modes != nullptr && modes[pe.j] == SAH_SAALSH && kj <= kmax) ? 1 : 0;
+      pinfo[i] = PairInfo{pe.j | (sa << 30), kj, pe.cphi, pe.sphi, qn[pe.j]};
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < pn * dp4; i += blockDim.x) {
+      const int row = i / dp4, c = i % dp4;
+      qs[i] = reinterpret_cast<const float4*>(Qd + (int64_t)(pinfo[row].j & 0x3fffffff) * dp)[c];
+    }
+    __syncthreads();
+    for (int pi = 0; pi < pn; pi += kQG) {
+      float Lg[kQG];
+#pragma unroll
+      for (int g = 0; g < kQG; ++g) {
+        const int kg = pinfo[min(pi + g, pn - 1)].k;
+        Lg[g] = (active && kg <= kmax) ? Lt[(int64_t)(kg - 1) * mz + r] : -INFINITY;
+      }
+      float acc[kQG];
+#pragma unroll
+      for (int g = 0; g < kQG; ++g) acc[g] = 0.f;
+#pragma unroll
+      for (int c = 0; c < DP4MAX; ++c) {
+        if (c < dp4) {
+          const float4 a = ur[c];
+#pragma unroll
+          for (int g = 0; g < kQG; ++g) {
+            const float4 b = qs[(pi + g) * dp4 + c];
+            acc[g] = fmaf(a.x, b.x, acc[g]);
+            acc[g] = fmaf(a.y, b.y, acc[g]);
+            acc[g] = fmaf(a.z, b.z, acc[g]);
+            acc[g] = fmaf(a.w, b.w, acc[g]);
+          }
+        }
+      }
+#pragma unroll
+      for (int g = 0; g < kQG; ++g) {
+        if (pi + g >= pn) break;
+        const PairInfo pe = pinfo[pi + g];
+        const int j = pe.j & 0x3fffffff, k = pe.k;
+        const bool sa_row = (pe.j >> 30) & 1;
+        const float nrm = pe.nrm, L = Lg[g];
+        bool surv_flag = false, yes = false;
+        const float sq = acc[g];
+        if (active) {
+          const float Llo = (L == -INFINITY) ? -INFINITY : __fsub_rd(L, E);
+          bool pruned = false;
+          if (pe.cphi <= 1.5f) {   // Lemma 3 with the slack of the FP32 terms
+            const float ub = __fmul_ru(__fmul_ru(nu, nrm), fmaf(pe.cphi, ct, pe.sphi * st_) + 2.f * slack);
+            pruned = ub < Llo;
+          }
+          if (!pruned) {
+            ++scored;
+            const float eq = __fmul_ru(__fmul_ru(gamma, nu), nrm) + 1e-30f;
+            const float hi = __fadd_ru(sq, eq), lo = __fsub_rd(sq, eq);
+            if (hi < Llo) {
+              // "no": at least k items of P' score above <u,q>
+            } else if (l_exact && k <= kmax && lo >= __fadd_ru(L, E)) {
+              yes = true;
+            } else if (lo >= __fmul_ru(__fmul_ru(nu, pnorm[k - 1]), 1.f + 2.f * gamma)) {
+              yes = true;
+            } else if (T64 != nullptr && k <= kmax && !sa_row) {
+              const double t64 = T64[(int64_t)(k - 1) * mz + r];
+              if (t64 == t64) {
+                ++fp64_here;
+                yes = dot64_seq(Ut + (int64_t)r * dp, Qd + (int64_t)j * dp, d) >= t64;
+              } else {
+                surv_flag = true;
+              }
+            } else {
+              surv_flag = true;
+            }
+          }
+        }
+        if (yes) {
+          ++yes_early;
+          atomicOr(&bitmap[(int64_t)j * words + (id >> 5)], 1u << (id & 31));
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, surv_flag);
+        if (m) {
+          unsigned long long base = 0;
+          const int leader = __ffs(m) - 1;
+          if (lane == leader) base = atomicAdd(surv_count + (sa_row ? 1 : 0), (unsigned long long)__popc(m));
+          base = __shfl_sync(0xffffffffu, base, leader);
+          if (surv_flag) {
+            const unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
+            if ((int64_t)slot < surv_cap) surv[(sa_row ? surv_cap : 0) + slot] = Survivor{r, j, sq};
+          }
+        }
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    scored += __shfl_xor_sync(0xffffffffu, scored, o);
+    yes_early += __shfl_xor_sync(0xffffffffu, yes_early, o);
+    fp64_here += __shfl_xor_sync(0xffffffffu, fp64_here, o);
+  }
+  if (lane == 0) {
+    if (scored) atomicAdd(&stats[ST_USERS_SCORED], scored);
+    if (yes_early) atomicAdd(&stats[ST_YES_EARLY], yes_early);
+    if (fp64_here) atomicAdd(&stats[ST_FP64], fp64_here);
   }
 }
 
@@ -466,33 +641,56 @@ __global__ void bitmap_count_kernel(const uint32_t* __restrict__ bitmap, int64_t
   }
 }
 
-// Per query: exclusive scan over chunks; offsets over queries start at base.
+// Per query: exclusive scan over its chunks (one thread per query), then an exclusive
+// scan of the query totals across the CTA; offsets over queries start at base.  One CTA
+// of 1024 threads.
 __global__ void offsets_kernel(int32_t* __restrict__ chunk_cnt, int nchunks, int nq, int64_t base,
                                int64_t* __restrict__ offsets) {
-  // single thread block; nq and nchunks are small
-  __shared__ long long run;
-  if (threadIdx.x == 0) run = base;
+  __shared__ long long warp_tot[32];
+  __shared__ long long carry;
+  if (threadIdx.x == 0) carry = base;
   __syncthreads();
-  for (int j = 0; j < nq; ++j) {
-    if (threadIdx.x == 0) {
-      offsets[j] = run;
-      long long acc = 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int j0 = 0; j0 < nq; j0 += blockDim.x) {
+    const int j = j0 + threadIdx.x;
+    long long tot = 0;
+    if (j < nq) {
       for (int c = 0; c < nchunks; ++c) {
-        int v = chunk_cnt[(int64_t)j * nchunks + c];
-        chunk_cnt[(int64_t)j * nchunks + c] = (int)acc;
-        acc += v;
+        const int v = chunk_cnt[(int64_t)j * nchunks + c];
+        chunk_cnt[(int64_t)j * nchunks + c] = (int)tot;
+        tot += v;
       }
-      run += acc;
     }
+    long long x = tot;
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    long long before = carry, all = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      if (w < warp) before += warp_tot[w];
+      all += warp_tot[w];
+    }
+    if (j < nq) offsets[j] = before + x - tot;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += all;
     __syncthreads();
   }
-  if (threadIdx.x == 0) offsets[nq] = run;
+  if (threadIdx.x == 0) offsets[nq] = carry;
 }
 
+// Writes the ids only if the call's total fits in out_cap; otherwise raises *overflow.
 __global__ void bitmap_emit_kernel(const uint32_t* __restrict__ bitmap, int64_t words, int nchunks,
                                    const int32_t* __restrict__ chunk_off, const int64_t* __restrict__ offsets,
-                                   int32_t* __restrict__ out) {
+                                   int nq, int32_t* __restrict__ out, int64_t out_cap,
+                                   unsigned long long* __restrict__ overflow) {
   int c = blockIdx.x, j = blockIdx.y;
+  if (offsets[nq] > out_cap) {
+    if (c == 0 && j == 0 && threadIdx.x == 0) atomicExch(overflow, 1ull);
+    return;
+  }
   int64_t w0 = (int64_t)c * kWordsPerChunk;
   int64_t dst0 = offsets[j] + chunk_off[(int64_t)j * nchunks + c];
   const int per = kWordsPerChunk / 256;   // words per thread, blockDim = 256
@@ -639,8 +837,8 @@ size_t batch_workspace_bytes(const Index* ix, int32_t nq) {
 }
 
 sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, const int32_t* ks_dev,
-                     const int32_t* modes_dev, int64_t* offsets_host, cudaStream_t st) {
-  (void)modes_dev;
+                     const int32_t* modes_dev, int32_t* out_dev, int64_t out_cap, int64_t* offsets_dev,
+                     int64_t* offsets_host, bool* wrote_out, cudaStream_t st) {
   const int64_t words = (ix->m + 31) / 32;
   const int nchunks = (int)((words + kWordsPerChunk - 1) / kWordsPerChunk);
   // sub-batch size: bounded pair list and bitmap (about 1 GiB together)
@@ -648,7 +846,13 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
                        sizeof(int32_t) * nchunks + sizeof(float) * ix->dp + 16;
   int qb = (int)std::max<size_t>(1, std::min<size_t>((size_t)nq, (size_t(1) << 30) / per_q));
   qb = std::min(qb, 4096);
-  int64_t surv_cap = std::max<int64_t>((int64_t)(cx->surv.bytes / (2 * sizeof(Survivor))), 1 << 20);
+  const bool direct = out_dev != nullptr && qb >= nq;   // one sub-batch: emit into the caller's buffer
+  *wrote_out = false;
+  // survivor-list capacity used by this call: twice the last call's count (at least 64k),
+  // grown and re-run if a sub-batch exceeds it
+  int64_t surv_cap = std::max<int64_t>(cx->surv_hint, 1 << 16);
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
 
   sah_stats agg{};
   agg.queries = nq;
@@ -658,180 +862,213 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
 
   for (int q0 = 0; q0 < nq; q0 += qb) {
     const int nqb = std::min(qb, nq - q0);
-    int64_t agg_last_ns = 0, agg_last_sa = 0;
-    WsLayout L = layout_for(ix, nqb, nchunks);
-    SAH_TRY(ensure_ws(cx, L.total, st));
-    char* w = (char*)cx->ws.base;
-    float* Qd = (float*)(w + L.qd);
-    float* qn = (float*)(w + L.qn);
-    int32_t* kk = (int32_t*)(w + L.kk);
-    PairEntry* pairs = (PairEntry*)(w + L.pairs);
-    int32_t* pcount = (int32_t*)(w + L.pcount);
-    unsigned long long* survcnt = (unsigned long long*)(w + L.survcnt);
-    uint32_t* bitmap = (uint32_t*)(w + L.bitmap);
-    int32_t* chunk = (int32_t*)(w + L.chunk);
-    int64_t* offsets = (int64_t*)(w + L.offsets);
-    unsigned long long* stats = (unsigned long long*)(w + L.stats);
+    const int32_t* modes_q = modes_dev ? modes_dev + q0 : nullptr;
+    for (int attempt = 0;; ++attempt) {
+      WsLayout L = layout_for(ix, nqb, nchunks);
+      SAH_TRY(ensure_ws(cx, L.total, st));
+      SAH_TRY(ensure_surv(cx, surv_cap, st));
+      char* w = (char*)cx->ws.base;
+      float* Qd = (float*)(w + L.qd);
+      float* qn = (float*)(w + L.qn);
+      int32_t* kk = (int32_t*)(w + L.kk);
+      PairEntry* pairs = (PairEntry*)(w + L.pairs);
+      int32_t* pcount = (int32_t*)(w + L.pcount);
+      unsigned long long* survcnt = (unsigned long long*)(w + L.survcnt);
+      uint32_t* bitmap = (uint32_t*)(w + L.bitmap);
+      int32_t* chunk = (int32_t*)(w + L.chunk);
+      int64_t* offsets = (int64_t*)(w + L.offsets);
+      unsigned long long* stats = (unsigned long long*)(w + L.stats);
+      Survivor* surv = (Survivor*)cx->surv.base;
 
-    tm.begin(0);
-    SAH_CUDA(cudaMemsetAsync(stats, 0, sizeof(unsigned long long) * ST_COUNT, st));
-    SAH_CUDA(cudaMemsetAsync(survcnt, 0, 2 * sizeof(unsigned long long), st));
-    SAH_CUDA(cudaMemsetAsync(bitmap, 0, sizeof(uint32_t) * (size_t)nqb * words, st));
-    SAH_CUDA(cudaMemcpyAsync(kk, ks_dev + q0, sizeof(int32_t) * nqb, cudaMemcpyDeviceToDevice, st));
-    prep_queries_kernel<<<grid_for(nqb, 8), 256, 0, st>>>(Q_dev + (int64_t)q0 * ix->d, nqb, ix->d, ix->dp,
-                                                           Qd, qn, stats);
-    SAH_CUDA(cudaGetLastError());
-    tm.end(0, 1);
-    if (ix->nb > 0) {
-      tm.begin(1);
-      block_filter_kernel<<<ix->nb, 128, sizeof(float) * ix->dp, st>>>(ix->bcent, ix->bcos, ix->bsin, ix->LB, ix->nb, ix->kmax,
-                                                  ix->n, ix->dp, Qd, qn, kk, nqb, ix->cone_slack, pairs,
-                                                  pcount, stats);
+      tm.begin(0);
+      SAH_CUDA(cudaMemsetAsync(stats, 0, sizeof(unsigned long long) * ST_COUNT, st));
+      SAH_CUDA(cudaMemsetAsync(survcnt, 0, 2 * sizeof(unsigned long long), st));
+      SAH_CUDA(cudaMemsetAsync(bitmap, 0, sizeof(uint32_t) * (size_t)nqb * words, st));
+      SAH_CUDA(cudaMemcpyAsync(kk, ks_dev + q0, sizeof(int32_t) * nqb, cudaMemcpyDeviceToDevice, st));
+      prep_queries_kernel<<<grid_for(nqb, 8), 256, 0, st>>>(Q_dev + (int64_t)q0 * ix->d, nqb, ix->d, ix->dp, Qd, qn,
+                                                             kk, modes_q, stats);
       SAH_CUDA(cudaGetLastError());
-      tm.end(1, 1);
-      int threads = std::max(32, ((ix->prm.leaf_size + 31) / 32) * 32);
-      size_t smem = (size_t)16 * threads * ((ix->dp / 4) | 1);
-      int stage = smem <= 160 * 1024 ? 1 : 0;
-      if (!stage) smem = 0;
-      smem += sizeof(PairInfo) * kPairChunk;
-      if (smem > 48 * 1024)
-        SAH_CUDA(cudaFuncSetAttribute(user_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      for (int attempt = 0;; ++attempt) {
-        SAH_TRY(ensure_surv(cx, surv_cap, st));
-        Survivor* surv = (Survivor*)cx->surv.base;
+      tm.end(0, 1);
+      if (ix->nb > 0) {
+        tm.begin(1);
+        block_filter_kernel<<<ix->nb, 128, sizeof(float) * ix->dp, st>>>(ix->bcent, ix->bcos, ix->bsin, ix->LB,
+                                                                          ix->nb, ix->kmax, ix->n, ix->dp, Qd, qn,
+                                                                          kk, nqb, ix->cone_slack, pairs, pcount,
+                                                                          stats);
+        SAH_CUDA(cudaGetLastError());
+        tm.end(1, 1);
+        // ---- A4: register-tiled kernel for d <= 128, the shared-memory one otherwise
+        const int threads = std::max(32, ((ix->prm.leaf_size + 31) / 32) * 32);
+        const int dp4 = ix->dp / 4;
+        const int reg_variant = dp4 <= 16 ? 16 : (dp4 <= 32 ? 32 : 0);
         tm.begin(2);
-        user_scan_kernel<<<ix->nb, threads, smem, st>>>(
-            ix->Ut, ix->unorm, ix->ucos, ix->usin, ix->uid, ix->bstart, ix->Lt, ix->Eu, ix->pnorm, ix->n,
-            ix->m_nz, ix->kmax, ix->l_exact ? 1 : 0, ix->dp, Qd, qn, kk, nqb, pairs, pcount, ix->gamma,
-            ix->cone_slack, bitmap, words, surv, survcnt, surv_cap, stats, stage,
-            modes_dev ? modes_dev + q0 : nullptr);
+        if (reg_variant) {
+          const size_t smem = (size_t)16 * kQChunk * dp4 + sizeof(PairInfo) * kQChunk;
+          auto fn = reg_variant == 16 ? user_scan_reg_kernel<16> : user_scan_reg_kernel<32>;
+          if (smem > 48 * 1024)
+            SAH_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+          fn<<<ix->nb, threads, smem, st>>>(
+              ix->Ut, ix->unorm, ix->ucos, ix->usin, ix->uid, ix->bstart, ix->Lt, ix->Eu, ix->pnorm, ix->n,
+              ix->m_nz, ix->kmax, ix->l_exact ? 1 : 0, ix->dp, Qd, qn, kk, nqb, pairs, pcount, ix->gamma,
+              ix->cone_slack, bitmap, words, surv, survcnt, surv_cap, stats, modes_q, ix->T64, ix->d);
+        } else {
+          size_t smem = (size_t)16 * threads * ((ix->dp / 4) | 1);
+          const int stage = smem <= 160 * 1024 ? 1 : 0;
+          if (!stage) smem = 0;
+          smem += sizeof(PairInfo) * kPairChunk;
+          if (smem > 48 * 1024)
+            SAH_CUDA(cudaFuncSetAttribute(user_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+          user_scan_kernel<<<ix->nb, threads, smem, st>>>(
+              ix->Ut, ix->unorm, ix->ucos, ix->usin, ix->uid, ix->bstart, ix->Lt, ix->Eu, ix->pnorm, ix->n,
+              ix->m_nz, ix->kmax, ix->l_exact ? 1 : 0, ix->dp, Qd, qn, kk, nqb, pairs, pcount, ix->gamma,
+              ix->cone_slack, bitmap, words, surv, survcnt, surv_cap, stats, stage, modes_q, ix->T64, ix->d);
+        }
         SAH_CUDA(cudaGetLastError());
         tm.end(2, 1);
-        unsigned long long ns2[2] = {0, 0};
-        SAH_CUDA(cudaMemcpyAsync(ns2, survcnt, sizeof(ns2), cudaMemcpyDeviceToHost, st));
-        SAH_CUDA(cudaStreamSynchronize(st));
-        tm.collect();
-        const unsigned long long ns = std::max(ns2[0], ns2[1]);
-        if ((int64_t)ns <= surv_cap) {
-          agg.survivors += (int64_t)(ns2[0] + ns2[1]);
-          agg_last_ns = (int64_t)ns2[0];
-          agg_last_sa = (int64_t)ns2[1];
-          break;
+        // ---- A5/A6 on the survivors (their number stays on the device)
+        tm.begin(3);
+        int nl = 0;
+        if (ix->dk > 0) {
+          SAH_TRY(run_verify_tc(ix, cx, surv, survcnt, surv_cap, Qd, qn, kk, bitmap, words, stats, ST_FP64, ST_ITEMS,
+                                st, &nl));
+        } else {
+          const size_t vsmem = (size_t)16 * kVerifyWarps * (ix->dp / 4);
+          if (vsmem > 48 * 1024)
+            SAH_CUDA(cudaFuncSetAttribute(verify_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)vsmem));
+          verify_exact_kernel<<<sms * 8, kVerifyWarps * 32, vsmem, st>>>(
+              surv, survcnt, surv_cap, ix->Ut, ix->unorm, ix->uid, ix->Ps, ix->pnorm, ix->n, ix->d, ix->dp, Qd, qn,
+              kk, ix->gamma, bitmap, words, stats);
+          SAH_CUDA(cudaGetLastError());
+          nl = 1;
         }
-        // The survivor list overflowed: grow it and repeat the user pass.  Bits already
-        // set stay valid (setting a bit twice is harmless); the pass's counters restart.
+        tm.end(3, nl);
+        if (modes_q) {
+          int nsa = 0;
+          tm.begin(5);
+          SAH_TRY(run_saalsh(ix, surv + surv_cap, survcnt + 1, surv_cap, Qd, qn, kk, bitmap, words, stats, ST_ITEMS,
+                             st, &nsa));
+          tm.end(5, nsa);
+        }
+      }
+      tm.begin(4);
+      int n_compact = 4;
+      if (ix->nzero > 0) {
+        zero_users_kernel<<<grid_for(ix->nzero * nqb, 256), 256, 0, st>>>(ix->zero_uid, ix->nzero, nqb, bitmap,
+                                                                           words);
+        ++n_compact;
+      }
+      {
+        dim3 g((unsigned)std::min<int64_t>(grid_for(words, 256), 1024), nqb);
+        all_users_kernel<<<g, 256, 0, st>>>(kk, nqb, ix->n, ix->m, bitmap, words);
+      }
+      const dim3 gc(nchunks, nqb);
+      bitmap_count_kernel<<<gc, 256, 0, st>>>(bitmap, words, nchunks, chunk);
+      offsets_kernel<<<1, 1024, 0, st>>>(chunk, nchunks, nqb, direct ? 0 : res_total, offsets);
+      int32_t* dst;
+      int64_t dst_cap;
+      if (direct) {
+        dst = out_dev;
+        dst_cap = out_cap;
+      } else {
+        dst = (int32_t*)cx->res.base;
+        dst_cap = (int64_t)(cx->res.bytes / sizeof(int32_t));
+      }
+      if (dst) {
+        bitmap_emit_kernel<<<gc, 256, 0, st>>>(bitmap, words, nchunks, chunk, offsets, nqb, dst, dst_cap,
+                                               &stats[ST_EMIT_OVERFLOW]);
+      } else {
+        SAH_CUDA(cudaMemsetAsync(&stats[ST_EMIT_OVERFLOW], 0xff, sizeof(unsigned long long), st));
+      }
+      if (direct && offsets_dev)
+        SAH_CUDA(cudaMemcpyAsync(offsets_dev, offsets, sizeof(int64_t) * (nqb + 1), cudaMemcpyDeviceToDevice, st));
+      SAH_CUDA(cudaGetLastError());
+      tm.end(4, n_compact);
+      // ---- the one synchronisation of the sub-batch: offsets, counters, survivor counts
+      std::vector<int64_t> ob(nqb + 1);
+      std::vector<unsigned long long> st_h(ST_COUNT);
+      unsigned long long ns2[2] = {0, 0};
+      int timeout = 0;
+      SAH_CUDA(cudaMemcpyAsync(ob.data(), offsets, sizeof(int64_t) * (nqb + 1), cudaMemcpyDeviceToHost, st));
+      SAH_CUDA(cudaMemcpyAsync(st_h.data(), stats, sizeof(unsigned long long) * ST_COUNT, cudaMemcpyDeviceToHost, st));
+      SAH_CUDA(cudaMemcpyAsync(ns2, survcnt, sizeof(ns2), cudaMemcpyDeviceToHost, st));
+      if (ix->dev_timeout) SAH_CUDA(cudaMemcpyAsync(&timeout, ix->dev_timeout, sizeof(int), cudaMemcpyDeviceToHost, st));
+      SAH_CUDA(cudaStreamSynchronize(st));
+      tm.collect();
+      if (timeout) {
+        SAH_CUDA(cudaMemsetAsync(ix->dev_timeout, 0, sizeof(int), st));
+        SAH_CUDA(cudaStreamSynchronize(st));
+        set_error("a bounded device-side wait of the tensor-core kMIPS decision ran out");
+        return SAH_ERR_DEVICE_TIMEOUT;
+      }
+      if (st_h[ST_BAD_Q]) {
+        set_error("a query vector holds a non-finite value");
+        return SAH_ERR_ARG;
+      }
+      if (st_h[ST_BAD_K]) {
+        set_error("k must be >= 1 and the mode SAH_EXACT or SAH_SAALSH");
+        return SAH_ERR_ARG;
+      }
+      if ((int64_t)std::max(ns2[0], ns2[1]) > surv_cap) {
+        // a survivor list overflowed: grow it and run this sub-batch again
         if (attempt > 4) {
           set_error("survivor list kept overflowing");
           return SAH_ERR_OOM;
         }
-        surv_cap = (int64_t)ns + (int64_t)ns / 4 + 1024;
-        SAH_CUDA(cudaMemsetAsync(survcnt, 0, 2 * sizeof(unsigned long long), st));
-        SAH_CUDA(cudaMemsetAsync(stats + ST_USERS_SCORED, 0, 2 * sizeof(unsigned long long), st));
+        surv_cap = (int64_t)std::max(ns2[0], ns2[1]) * 5 / 4 + 1024;
+        continue;
       }
-      Survivor* surv = (Survivor*)cx->surv.base;
-      tm.begin(3);
-      int nl = 0;
-      if (ix->dk > 0) {
-        SAH_TRY(run_verify_tc(ix, cx, surv, survcnt, agg_last_ns, Qd, qn, kk, bitmap, words, stats, ST_FP64,
-                              ST_ITEMS, st, &nl));
-      } else {
-        size_t vsmem = (size_t)16 * kVerifyWarps * (ix->dp / 4);
-        if (vsmem > 48 * 1024)
-          SAH_CUDA(cudaFuncSetAttribute(verify_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsmem));
-        int sms = 152;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
-        verify_exact_kernel<<<sms * 8, kVerifyWarps * 32, vsmem, st>>>(
-            surv, survcnt, surv_cap, ix->Ut, ix->unorm, ix->uid, ix->Ps, ix->pnorm, ix->n, ix->d, ix->dp, Qd, qn,
-            kk, ix->gamma, bitmap, words, stats);
-        SAH_CUDA(cudaGetLastError());
-        nl = 1;
-      }
-      tm.end(3, nl);
-      if (agg_last_sa > 0) {
-        int nsa = 0;
-        tm.begin(5);
-        SAH_TRY(run_saalsh(ix, surv + surv_cap, agg_last_sa, Qd, qn, kk, bitmap, words, stats, ST_ITEMS, st, &nsa));
-        tm.end(5, nsa);
-      }
-    }
-    tm.begin(4);
-    int n_compact = 3;
-    if (ix->nzero > 0) {
-      zero_users_kernel<<<grid_for(ix->nzero * nqb, 256), 256, 0, st>>>(ix->zero_uid, ix->nzero, nqb, bitmap,
-                                                                         words);
-      SAH_CUDA(cudaGetLastError());
-      ++n_compact;
-    }
-    {
-      dim3 g((unsigned)std::min<int64_t>(grid_for(words, 256), 1024), nqb);
-      all_users_kernel<<<g, 256, 0, st>>>(kk, nqb, ix->n, ix->m, bitmap, words);
-      SAH_CUDA(cudaGetLastError());
-    }
-    dim3 gc(nchunks, nqb);
-    bitmap_count_kernel<<<gc, 256, 0, st>>>(bitmap, words, nchunks, chunk);
-    offsets_kernel<<<1, 32, 0, st>>>(chunk, nchunks, nqb, res_total, offsets);
-    SAH_CUDA(cudaGetLastError());
-    std::vector<int64_t> ob(nqb + 1);
-    std::vector<unsigned long long> st_h(ST_COUNT);
-    SAH_CUDA(cudaMemcpyAsync(ob.data(), offsets, sizeof(int64_t) * (nqb + 1), cudaMemcpyDeviceToHost, st));
-    SAH_CUDA(cudaMemcpyAsync(st_h.data(), stats, sizeof(unsigned long long) * ST_COUNT, cudaMemcpyDeviceToHost, st));
-    SAH_CUDA(cudaStreamSynchronize(st));
-    tm.end(4, n_compact);
-    tm.collect();
-    if (st_h[ST_BAD_Q]) {
-      set_error("a query vector holds a non-finite value");
-      return SAH_ERR_ARG;
-    }
-    agg.block_pairs_total += (int64_t)ix->nb * nqb;
-    agg.block_pairs_kept += (int64_t)st_h[ST_PAIRS_KEPT];
-    agg.users_scored += (int64_t)st_h[ST_USERS_SCORED];
-    agg.users_yes_early += (int64_t)st_h[ST_YES_EARLY];
-    agg.fp64_rescored += (int64_t)st_h[ST_FP64];
-    agg.users_in_kept_blocks += (int64_t)st_h[ST_KEPT_USERS];
-    agg.items_scanned += (int64_t)st_h[ST_ITEMS];
-    for (int j = 0; j < nqb; ++j) offs[q0 + j] = ob[j];
-    int64_t new_total = ob[nqb];
-    if (new_total > res_total) {
-      // grow the index's result buffer, keeping what earlier sub-batches wrote
-      size_t need = sizeof(int32_t) * (size_t)new_total;
-      if (need > cx->res.bytes) {
+      const int64_t new_total = ob[nqb];
+      if (st_h[ST_EMIT_OVERFLOW]) {
+        if (direct) {
+          // the caller's buffer is too small: report the sizes, nothing was written
+          for (int j = 0; j <= nqb; ++j) offs[q0 + j] = ob[j];
+          agg.results = new_total;
+          cx->stats = agg;
+          std::memcpy(offsets_host, offs.data(), sizeof(int64_t) * (nq + 1));
+          set_error("result buffer too small: " + std::to_string(new_total) + " ids needed");
+          return SAH_ERR_BUFFER_TOO_SMALL;
+        }
+        // internal buffer too small: grow it (keeping earlier sub-batches) and emit again
         Workspace nr;
-        SAH_TRY(ensure_buf(&nr, std::max(need, 2 * cx->res.bytes), st));
+        SAH_TRY(ensure_buf(&nr, std::max(sizeof(int32_t) * (size_t)new_total, 2 * cx->res.bytes), st));
         if (res_total)
           SAH_CUDA(cudaMemcpyAsync(nr.base, cx->res.base, sizeof(int32_t) * res_total, cudaMemcpyDeviceToDevice, st));
         SAH_CUDA(cudaStreamSynchronize(st));
         if (cx->res.base) cudaFree(cx->res.base);
         cx->res = nr;
+        SAH_CUDA(cudaMemsetAsync(&stats[ST_EMIT_OVERFLOW], 0, sizeof(unsigned long long), st));
+        bitmap_emit_kernel<<<gc, 256, 0, st>>>(bitmap, words, nchunks, chunk, offsets, nqb, (int32_t*)cx->res.base,
+                                               (int64_t)(cx->res.bytes / sizeof(int32_t)), &stats[ST_EMIT_OVERFLOW]);
+        SAH_CUDA(cudaGetLastError());
+        SAH_CUDA(cudaStreamSynchronize(st));
       }
-      tm.begin(4);
-      bitmap_emit_kernel<<<gc, 256, 0, st>>>(bitmap, words, nchunks, chunk, offsets, (int32_t*)cx->res.base);
-      SAH_CUDA(cudaGetLastError());
-      tm.end(4, 1);
+      agg.survivors += (int64_t)(ns2[0] + ns2[1]);
+      cx->surv_hint = std::max<int64_t>(1 << 16, 2 * (int64_t)std::max(ns2[0], ns2[1]));
+      agg.block_pairs_total += (int64_t)ix->nb * nqb;
+      agg.block_pairs_kept += (int64_t)st_h[ST_PAIRS_KEPT];
+      agg.users_scored += (int64_t)st_h[ST_USERS_SCORED];
+      agg.users_yes_early += (int64_t)st_h[ST_YES_EARLY];
+      agg.fp64_rescored += (int64_t)st_h[ST_FP64];
+      agg.users_in_kept_blocks += (int64_t)st_h[ST_KEPT_USERS];
+      agg.items_scanned += (int64_t)st_h[ST_ITEMS];
+      for (int j = 0; j < nqb; ++j) offs[q0 + j] = ob[j];
+      res_total = new_total;
+      break;
     }
-    res_total = new_total;
-  }
-  SAH_CUDA(cudaStreamSynchronize(st));
-  tm.collect();
-  if (ix->dev_timeout) {
-    int to = 0;
-    SAH_CUDA(cudaMemcpy(&to, ix->dev_timeout, sizeof(int), cudaMemcpyDeviceToHost));
-    if (to) {
-      SAH_CUDA(cudaMemset(ix->dev_timeout, 0, sizeof(int)));
-      set_error("a bounded device-side wait of the tensor-core kMIPS decision ran out");
-      return SAH_ERR_DEVICE_TIMEOUT;
-    }
-  }
-  for (int i = 0; i < StageTimer::kStages; ++i) {
-    agg.stage_ms[i] = tm.ms[i];
-    agg.stage_launches[i] = tm.launches[i];
   }
   offs[nq] = res_total;
+  *wrote_out = direct;
   agg.results = res_total;
   agg.n_items = ix->n;
   agg.n_users = ix->m;
   agg.n_blocks = ix->nb;
   agg.n_partitions = ix->sa_parts;
   agg.device_bytes = (int64_t)(ix->bytes + ctx_bytes(cx));
+  for (int i = 0; i < StageTimer::kStages; ++i) {
+    agg.stage_ms[i] = tm.ms[i];
+    agg.stage_launches[i] = tm.launches[i];
+  }
   cx->stats = agg;
   std::memcpy(offsets_host, offs.data(), sizeof(int64_t) * (nq + 1));
   return SAH_OK;

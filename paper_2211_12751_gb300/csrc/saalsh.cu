@@ -153,7 +153,8 @@ __device__ __forceinline__ float slot_value(float a, float b, int slot) {
 
 struct SaParams {
   const Survivor* rows;
-  int64_t nrows;
+  const unsigned long long* nrows_dev;
+  int64_t cap;
   const float* Ut;
   const float* unorm;
   const int32_t* uid;
@@ -199,7 +200,8 @@ __global__ void __launch_bounds__(kSaWarps * 32) saalsh_decide_kernel(SaParams p
   const int64_t nw = (int64_t)gridDim.x * kSaWarps;
   int32_t* q = queue[warp];
   unsigned long long scored = 0;
-  for (int64_t r = gw; r < prm.nrows; r += nw) {
+  const int64_t nrows = min((int64_t)*prm.nrows_dev, prm.cap);
+  for (int64_t r = gw; r < nrows; r += nw) {
     const Survivor S = prm.rows[r];
     const int k = prm.kk[S.j];
     const float* u = prm.Ut + (int64_t)S.upos * prm.dp;
@@ -465,14 +467,16 @@ sah_status build_saalsh(Index* ix, const float* srp_host, cudaStream_t st) {
   return SAH_OK;
 }
 
-sah_status run_saalsh(Index* ix, const Survivor* surv, int64_t ns, const float* Qd, const float* qn,
-                      const int32_t* kk, uint32_t* bitmap, int64_t words, unsigned long long* stats, int stat_items,
-                      cudaStream_t st, int* launches) {
+sah_status run_saalsh(Index* ix, const Survivor* surv, const unsigned long long* count_dev, int64_t cap,
+                      const float* Qd, const float* qn, const int32_t* kk, uint32_t* bitmap, int64_t words,
+                      unsigned long long* stats, int stat_items, cudaStream_t st, int* launches) {
   (void)Qd;
-  if (ns <= 0) return SAH_OK;
+  if (cap <= 0) return SAH_OK;
+  const int64_t ns = cap;
   SaParams p;
   p.rows = surv;
-  p.nrows = ns;
+  p.nrows_dev = count_dev;
+  p.cap = cap;
   p.Ut = ix->Ut;
   p.unorm = ix->unorm;
   p.uid = ix->uid;

@@ -55,6 +55,7 @@ struct CallCtx {
   Workspace surv;    // survivor lists, grown on demand
   Workspace res;     // ids of the last call, before they go to the caller
   Workspace tcws;    // tensor-core kMIPS decision: sorted rows, statuses, band lists
+  int64_t surv_hint = 1 << 16;   // survivor-list capacity for the next call
   sah_stats stats{};
 };
 
@@ -97,6 +98,8 @@ struct Index {
   // lower-bound arrays (Alg. 4): Lt[k-1][u] = k-th largest FP32 score of u over P'
   float* Lt = nullptr;        // [kmax][m_nz]
   float* Eu = nullptr;        // m_nz: bound on |Lt - exact| (and on any FP32 item score's error)
+  double* T64 = nullptr;      // [kmax][m_nz] when |P'| = n: the exact double-precision k-th largest
+                              // score (NaN where it could not be certified)
 
   // BF16 copies for the tensor-core kMIPS decision (precision SAH_BF16), K padded to dk
   int32_t dk = 0;             // roundup(d, 64); 0 when the tensor-core path is off
@@ -179,22 +182,27 @@ sah_status build_index_device(Index* ix, const float* U_dev, const float* P_dev,
 // saalsh.cu
 sah_status build_saalsh(Index* ix, const float* srp_host, cudaStream_t st);
 // Alg. 2 for every SA-ALSH survivor; sets the answer bits of the "yes" ones.
-sah_status run_saalsh(Index* ix, const Survivor* surv, int64_t nsurv, const float* Qd, const float* qn,
-                      const int32_t* kk, uint32_t* bitmap, int64_t words, unsigned long long* stats,
-                      int stat_items, cudaStream_t st, int* launches);
+// (the number of survivors is read on the device from *count_dev, at most cap)
+sah_status run_saalsh(Index* ix, const Survivor* surv, const unsigned long long* count_dev, int64_t cap,
+                      const float* Qd, const float* qn, const int32_t* kk, uint32_t* bitmap, int64_t words,
+                      unsigned long long* stats, int stat_items, cudaStream_t st, int* launches);
 // verify_tc.cu
 sah_status build_bf16_copies(Index* ix, cudaStream_t st);
 // Decides every survivor with the tcgen05 kernel and sets the answer bits; the counters
 // of double-precision decisions and scanned items go to stats[stat_fp64], stats[stat_items].
 sah_status run_verify_tc(Index* ix, CallCtx* cx, const Survivor* surv, const unsigned long long* surv_count_dev,
-                         int64_t nsurv, const float* Qd, const float* qn, const int32_t* kk, uint32_t* bitmap,
+                         int64_t surv_cap, const float* Qd, const float* qn, const int32_t* kk, uint32_t* bitmap,
                          int64_t words, unsigned long long* stats, int stat_fp64, int stat_items,
                          cudaStream_t st, int* launches);
 // query.cu
-// Alg. 5 for nq queries (Q, ks, modes on the device).  On success the ascending ids of
-// every query sit in cx->res (query j at [offsets_host[j], offsets_host[j+1])).
+// Alg. 5 for nq queries (Q, ks, modes on the device), with one stream synchronisation
+// per sub-batch.  When out_dev is given and the call fits one sub-batch, the ascending
+// ids go straight to out_dev (only if they fit in out_cap; SAH_ERR_BUFFER_TOO_SMALL with
+// the offsets filled otherwise) and the offsets also to offsets_dev; *wrote_out tells.
+// Otherwise the ids sit in cx->res (query j at [offsets_host[j], offsets_host[j+1])).
 sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, const int32_t* ks_dev,
-                     const int32_t* modes_dev, int64_t* offsets_host, cudaStream_t st);
+                     const int32_t* modes_dev, int32_t* out_dev, int64_t out_cap, int64_t* offsets_dev,
+                     int64_t* offsets_host, bool* wrote_out, cudaStream_t st);
 // Device bytes a call with nq queries needs in its workspace (pair lists, bitmaps).
 size_t batch_workspace_bytes(const Index* ix, int32_t nq);
 

@@ -124,9 +124,10 @@ void worker_loop(sah_server* s, Worker* w) {
             cudaSuccess) {
       st = SAH_ERR_CUDA;
     }
+    bool wrote = false;
     if (st == SAH_OK)
-      st = sah::run_batch(ix, &w->ctx, w->q_d, B, w->km_d, any_sa ? w->km_d + s->max_batch : nullptr, offs.data(),
-                          w->stream);
+      st = sah::run_batch(ix, &w->ctx, w->q_d, B, w->km_d, any_sa ? w->km_d + s->max_batch : nullptr, nullptr, 0,
+                          nullptr, offs.data(), &wrote, w->stream);
     const int64_t total = st == SAH_OK ? offs[B] : 0;
     if (st == SAH_OK && total > 0) {
       if ((size_t)total > w->ids_cap) {

@@ -47,9 +47,11 @@ __global__ void f32_to_bf16_rows_kernel(const float* __restrict__ src, int64_t r
 
 // Tile (of kTileN items) at which a row's norm cut falls: the first t with
 // ||u|| ||p_{t kTileN}|| (1 + 2 gamma) <= <u,q> - e_q; ntiles when it never falls.
-__global__ void cut_kernel(const Survivor* __restrict__ surv, int64_t ns, const float* __restrict__ unorm,
-                           const float* __restrict__ pnorm, int64_t n, const float* __restrict__ qn, float gamma,
-                           int ntiles, int32_t* __restrict__ cut, int32_t* __restrict__ hist) {
+__global__ void cut_kernel(const Survivor* __restrict__ surv, const unsigned long long* __restrict__ count,
+                           int64_t cap, const float* __restrict__ unorm, const float* __restrict__ pnorm, int64_t n,
+                           const float* __restrict__ qn, float gamma, int ntiles, int32_t* __restrict__ cut,
+                           int32_t* __restrict__ hist) {
+  const int64_t ns = min((int64_t)*count, cap);
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ns) return;
   Survivor S = surv[i];
@@ -78,9 +80,11 @@ __global__ void exclusive_scan_small_kernel(int32_t* __restrict__ v, int count) 
   }
 }
 
-__global__ void sort_by_cut_kernel(const Survivor* __restrict__ surv, const int32_t* __restrict__ cut, int64_t ns,
+__global__ void sort_by_cut_kernel(const Survivor* __restrict__ surv, const int32_t* __restrict__ cut,
+                                   const unsigned long long* __restrict__ count, int64_t cap,
                                    int32_t* __restrict__ off, Survivor* __restrict__ out_rows,
                                    int32_t* __restrict__ out_cut) {
+  const int64_t ns = min((int64_t)*count, cap);
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ns) return;
   int32_t c = cut[i];
@@ -109,7 +113,8 @@ __device__ __forceinline__ float max3(float a, float b, float c) {
 struct TcParams {
   const Survivor* rows;
   const int32_t* cut;
-  int64_t nrows;
+  const unsigned long long* nrows_dev;   // survivors, read on the device
+  int64_t cap;
   const uint16_t* Ub;
   int dk;
   const float* unorm;
@@ -143,7 +148,9 @@ verify_tc_kernel(const __grid_constant__ CUtensorMap tmapP, TcParams prm) {
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t r0 = (int64_t)blockIdx.x * kRows;
-  const int64_t nrows_cta = std::min<int64_t>(kRows, prm.nrows - r0);
+  const int64_t nrows_all = std::min<int64_t>((int64_t)*prm.nrows_dev, prm.cap);
+  if (r0 >= nrows_all) return;                          // the grid is sized for the list's capacity
+  const int64_t nrows_cta = std::min<int64_t>(kRows, nrows_all - r0);
   const int T = prm.cut[r0 + nrows_cta - 1];          // rows are sorted by cut: the last needs most
 
   if (threadIdx.x == 0) {
@@ -263,6 +270,7 @@ verify_tc_kernel(const __grid_constant__ CUtensorMap tmapP, TcParams prm) {
       lo = __fsub_rd(S.sq, eq);
     }
     const float cbu = __fmul_ru(prm.cbf, nu);
+    float pn_next = T > 0 ? prm.pnorm[0] : 0.f;
     int certain = 0, band = 0;
     bool decided = !valid, failed = false;
     unsigned long long scanned = 0;
@@ -274,33 +282,38 @@ verify_tc_kernel(const __grid_constant__ CUtensorMap tmapP, TcParams prm) {
       }
       tc::tc_fence_after();
       const bool need = !failed && !decided && t < cut_r;
+      const float pn_tile = pn_next;                       // ||p|| of the tile's first item
+      if (t + 1 < T) pn_next = prm.pnorm[(int64_t)(t + 1) * kTileN];
       if (__any_sync(0xffffffffu, need)) {
-        const float E = __fmul_ru(cbu, prm.pnorm[(int64_t)t * kTileN]) + 1e-30f;
+        const float E = __fmul_ru(cbu, pn_tile) + 1e-30f;
         const float thb = __fsub_rd(lo, E), tha = __fadd_ru(hi, E);
         const int ncols = (int)std::min<int64_t>(kTileN, prm.n - (int64_t)t * kTileN);
         if (need) scanned += ncols;
 #pragma unroll 1
-        for (int c0 = 0; c0 < kTileN; c0 += 32) {
-          float v[32];
-          tc::tmem_ld32(tbase + ((uint32_t)(quad * 32) << 16) + a * kTileN + c0, v);
+        for (int h = 0; h < kTileN; h += 128) {
+          float v[128];
+          tc::tmem_ld128(tbase + ((uint32_t)(quad * 32) << 16) + a * kTileN + h, v);
           tc::tmem_ld_wait();
           if (need) {
-            float g0 = max3(v[0], v[1], v[2]), g1 = max3(v[3], v[4], v[5]), g2 = max3(v[6], v[7], v[8]);
-            float g3 = max3(v[9], v[10], v[11]), g4 = max3(v[12], v[13], v[14]), g5 = max3(v[15], v[16], v[17]);
-            float g6 = max3(v[18], v[19], v[20]), g7 = max3(v[21], v[22], v[23]), g8 = max3(v[24], v[25], v[26]);
-            float g9 = max3(v[27], v[28], v[29]), g10 = fmaxf(v[30], v[31]);
-            float h0 = max3(g0, g1, g2), h1 = max3(g3, g4, g5), h2 = max3(g6, g7, g8), h3 = max3(g9, g10, h0);
-            float gm = max3(h1, h2, h3);
-            if (gm > thb) {
 #pragma unroll
-              for (int i = 0; i < 32; ++i) {
-                const int col = c0 + i;
-                if (col < ncols && v[i] > thb) {
-                  if (v[i] > tha) {
-                    ++certain;
-                  } else {
-                    if (band < kBandCap) prm.band_items[gi * kBandCap + band] = t * kTileN + col;
-                    ++band;
+            for (int c0 = 0; c0 < 128; c0 += 32) {
+              float g[11];
+#pragma unroll
+              for (int i = 0; i < 10; ++i) g[i] = max3(v[c0 + 3 * i], v[c0 + 3 * i + 1], v[c0 + 3 * i + 2]);
+              g[10] = fmaxf(v[c0 + 30], v[c0 + 31]);
+              const float gm = max3(max3(g[0], g[1], g[2]), max3(g[3], g[4], g[5]),
+                                    max3(max3(g[6], g[7], g[8]), g[9], g[10]));
+              if (gm > thb) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                  const int col = h + c0 + i;
+                  if (col < ncols && v[c0 + i] > thb) {
+                    if (v[c0 + i] > tha) {
+                      ++certain;
+                    } else {
+                      if (band < kBandCap) prm.band_items[gi * kBandCap + band] = t * kTileN + col;
+                      ++band;
+                    }
                   }
                 }
               }
@@ -345,7 +358,8 @@ verify_tc_kernel(const __grid_constant__ CUtensorMap tmapP, TcParams prm) {
 // Decides every row of the tensor-core pass: "yes"/"no" as found, band items (or, when
 // the band overflowed, the whole row) in FP32 with the bound and in double precision
 // where the bound cannot separate.  One warp per row.
-__global__ void resolve_kernel(const Survivor* __restrict__ rows, int64_t nrows, const int32_t* __restrict__ status,
+__global__ void resolve_kernel(const Survivor* __restrict__ rows, const unsigned long long* __restrict__ count,
+                               int64_t cap, const int32_t* __restrict__ status,
                                const int32_t* __restrict__ certain_in, const int32_t* __restrict__ band_in,
                                const int32_t* __restrict__ band_items, const float* __restrict__ Ut,
                                const float* __restrict__ unorm, const int32_t* __restrict__ uid,
@@ -355,6 +369,7 @@ __global__ void resolve_kernel(const Survivor* __restrict__ rows, int64_t nrows,
                                int64_t words, unsigned long long* __restrict__ fp64_stat,
                                unsigned long long* __restrict__ items_stat) {
   const int lane = threadIdx.x & 31;
+  const int64_t nrows = min((int64_t)*count, cap);
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long fp64 = 0, scanned = 0;
@@ -370,23 +385,36 @@ __global__ void resolve_kernel(const Survivor* __restrict__ rows, int64_t nrows,
       const float eq = __fmul_ru(__fmul_ru(gamma, nu), qn[S.j]) + 1e-30f;
       const float hi = __fadd_ru(S.sq, eq), lo = __fsub_rd(S.sq, eq);
       const float gnu = __fmul_ru(gamma, nu);
-      const double s64q = dot64_seq(u, Qd + (int64_t)S.j * dp, d);
+      // <u,q> in double precision, computed once per row and only if some item needs it
+      bool have64 = false;
+      double s64q = 0.0;
+      auto need64 = [&](bool any) {
+        if (any && !have64) {
+          double v64 = 0.0;
+          if (lane == 0) v64 = dot64_seq(u, Qd + (int64_t)S.j * dp, d);
+          s64q = __shfl_sync(0xffffffffu, v64, 0);
+          have64 = true;
+        }
+      };
       int c;
       if (st == ROW_BAND) {
         c = certain_in[r];
         const int nb = band_in[r];
-        bool gt = false;
+        bool gt = false, amb = false;
+        const float* p = nullptr;
         if (lane < nb) {
           const int64_t it = band_items[r * kBandCap + lane];
-          const float* p = Ps + it * dp;
+          p = Ps + it * dp;
           float s = 0.f;
           for (int i = 0; i < dp; ++i) s = fmaf(u[i], p[i], s);
           const float ep = __fmul_ru(gnu, pnorm[it]) + 1e-30f;
           if (__fsub_rd(s, ep) > hi) gt = true;
-          else if (__fadd_ru(s, ep) > lo) gt = dot64_seq(u, p, d) > s64q;
+          else amb = __fadd_ru(s, ep) > lo;
         }
+        need64(__any_sync(0xffffffffu, amb));
+        if (amb) gt = dot64_seq(u, p, d) > s64q;
         c += __popc(__ballot_sync(0xffffffffu, gt));
-        ++fp64;
+        if (have64) ++fp64;
       } else {
         // whole row: certain counts in FP32, everything undecided in double precision
         const float scale = __fmul_ru(nu, 1.f + 2.f * gamma);
@@ -394,15 +422,17 @@ __global__ void resolve_kernel(const Survivor* __restrict__ rows, int64_t nrows,
         for (int64_t b0 = 0; b0 < n && c < k; b0 += 32) {
           if (__fmul_ru(scale, pnorm[b0]) <= lo) break;
           const int64_t i = b0 + lane;
-          bool gt = false;
+          bool gt = false, amb = false;
+          const float* p = Ps + i * dp;
           if (i < n) {
-            const float* p = Ps + i * dp;
             float s = 0.f;
             for (int e = 0; e < dp; ++e) s = fmaf(u[e], p[e], s);
             const float ep = __fmul_ru(gnu, pnorm[i]) + 1e-30f;
             if (__fsub_rd(s, ep) > hi) gt = true;
-            else if (__fadd_ru(s, ep) > lo) gt = dot64_seq(u, p, d) > s64q;
+            else amb = __fadd_ru(s, ep) > lo;
           }
+          need64(__any_sync(0xffffffffu, amb));
+          if (amb) gt = dot64_seq(u, p, d) > s64q;
           c += __popc(__ballot_sync(0xffffffffu, gt));
           scanned += 32;
         }
@@ -482,11 +512,11 @@ sah_status build_bf16_copies(Index* ix, cudaStream_t st) {
   return SAH_OK;
 }
 
-sah_status run_verify_tc(Index* ix, CallCtx* cx, const Survivor* surv, const unsigned long long* surv_count_dev,
+sah_status run_verify_tc(Index* ix, CallCtx* cx, const Survivor* surv, const unsigned long long* count_dev,
                          int64_t ns, const float* Qd, const float* qn, const int32_t* kk, uint32_t* bitmap,
                          int64_t words, unsigned long long* stats, int stat_fp64, int stat_items,
                          cudaStream_t st, int* launches) {
-  (void)surv_count_dev;
+  // ns is the capacity of the survivor list; the number of survivors stays on the device
   if (ns <= 0) return SAH_OK;
   const int ntiles = (int)((ix->n + kTileN - 1) / kTileN);
   // scratch: cut, hist, sorted rows, sorted cut, status, certain, band, band items
@@ -520,16 +550,17 @@ sah_status run_verify_tc(Index* ix, CallCtx* cx, const Survivor* surv, const uns
   int32_t* items = (int32_t*)(w + o_items);
 
   SAH_CUDA(cudaMemsetAsync(hist, 0, sizeof(int32_t) * (ntiles + 2), st));
-  cut_kernel<<<grid_for(ns, 256), 256, 0, st>>>(surv, ns, ix->unorm, ix->pnorm, ix->n, qn, ix->gamma, ntiles, cut,
-                                                hist);
+  cut_kernel<<<grid_for(ns, 256), 256, 0, st>>>(surv, count_dev, ns, ix->unorm, ix->pnorm, ix->n, qn, ix->gamma,
+                                                ntiles, cut, hist);
   exclusive_scan_small_kernel<<<1, 32, 0, st>>>(hist, ntiles + 1);
-  sort_by_cut_kernel<<<grid_for(ns, 256), 256, 0, st>>>(surv, cut, ns, hist, rows, scut);
+  sort_by_cut_kernel<<<grid_for(ns, 256), 256, 0, st>>>(surv, cut, count_dev, ns, hist, rows, scut);
   SAH_CUDA(cudaGetLastError());
 
   TcParams prm;
   prm.rows = rows;
   prm.cut = scut;
-  prm.nrows = ns;
+  prm.nrows_dev = count_dev;
+  prm.cap = ns;
   prm.Ub = ix->Ub;
   prm.dk = ix->dk;
   prm.unorm = ix->unorm;
@@ -558,7 +589,7 @@ sah_status run_verify_tc(Index* ix, CallCtx* cx, const Survivor* surv, const uns
   SAH_CUDA(cudaGetLastError());
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
-  resolve_kernel<<<sms * 8, 256, 0, st>>>(rows, ns, status, cert, band, items, ix->Ut, ix->unorm, ix->uid, ix->Ps,
+  resolve_kernel<<<sms * 8, 256, 0, st>>>(rows, count_dev, ns, status, cert, band, items, ix->Ut, ix->unorm, ix->uid, ix->Ps,
                                           ix->pnorm, ix->n, ix->d, ix->dp, Qd, qn, kk, ix->gamma, bitmap, words,
                                           stats + stat_fp64, stats + stat_items);
   SAH_CUDA(cudaGetLastError());

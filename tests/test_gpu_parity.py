@@ -210,3 +210,19 @@ def test_tensor_core_path_runs_and_counts(sah):
     for j in range(0, 50, 7):
         c = oracle.count_above(W.U, W.P, Q[j])
         assert np.array_equal(got[j], np.flatnonzero(c < K[j]))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_survivor_list_overflow_reruns(sah, precision):
+    """More survivors than the list's first capacity (64k): the call grows the list, runs
+    the sub-batch again and still returns the oracle's answers."""
+    W = workload.make("c2", m=20000, n=800)
+    ix = sah.Index(W.U, W.P, k_max=50, leaf_size=128, p_prime=5, precision=precision)
+    rng = np.random.default_rng(3)
+    rows = rng.integers(0, W.n, 200)
+    Q = W.P[rows]
+    K = np.full(200, 30, np.int32)
+    got = ix.rkmips_batch(Q, K)
+    assert ix.stats()["survivors"] > (1 << 16)
+    for r in (0, 57, 123, 199):
+        assert np.array_equal(got[r], _truth(W.U, W.P, Q[r], (30,))[30]), r
