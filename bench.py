@@ -311,13 +311,13 @@ def main():
     distinct_k = len(set(K.tolist()))
     stream = torch.cuda.current_stream()
 
-    def build(threshold, precision):
+    def build(threshold, precision, tc_user_pass=0):
         pp = (1 << 30) if threshold == "full" else 0
         prec = sah.BF16 if precision == "bf16" else sah.FP32
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ix = sah.Index(W.U, W.P, k_max=50, leaf_size=args.leaf_size, p_prime=pp, seed=0, precision=prec,
-                       n_tables=128, code_bits=16, stream=stream)
+                       n_tables=128, code_bits=16, tc_user_pass=tc_user_pass, stream=stream)
         torch.cuda.synchronize()
         return ix, time.perf_counter() - t0
 
@@ -462,6 +462,14 @@ def main():
                 line["variants"][f"{thr}_{prec}"] = rec
                 if not same:
                     ixv.close()
+        # the user pass as per-leaf tcgen05 GEMMs (BF16 bound, FP32 re-score of what it leaves open)
+        for thr in ("full", "paper"):
+            ixv, bv = build(thr, "bf16", tc_user_pass=1)
+            _, tv, smv, lv, stv, _ = measure(ixv, vsteps, 3, timing=True)
+            line["variants"][f"{thr}_bf16_tc_user_pass"] = {
+                "value": nq * len(tv) / (sum(tv) / 1e3), "ms_per_step": float(np.mean(tv)),
+                "user_pass_ms": float(smv[2]), "index_build_s": bv}
+            ixv.close()
 
     if rank == 0 and not args.no_serving:
         line["serving"] = serve_stream(sah, ix, W, args.serve_rate, args.serve_requests)

@@ -70,6 +70,8 @@ typedef struct {
   uint64_t seed;        /* Cone-Tree random points (Alg. 3) and, when srp is NULL, the SRP matrix */
   const float* srp;     /* optional host matrix (n_tables * code_bits) x (d + 1) of SRP projection
                            vectors (Eq. 1); NULL draws it from seed.  Copied at build time. */
+  int32_t tc_user_pass; /* with SAH_BF16: 1 runs the user pass (Lemma 3 and the bound tests of
+                           Alg. 5) as per-leaf tcgen05 GEMMs; 0 (default) as register-tiled FP32 */
 } sah_params;
 
 /* Fills *p with the paper's parameters (k_max 50, N_0 20, b 0.5, K 128) and the build's

@@ -45,6 +45,7 @@ class Params(ctypes.Structure):
         ("probe_radius", ctypes.c_int32),
         ("seed", ctypes.c_uint64),
         ("srp", ctypes.c_void_p),
+        ("tc_user_pass", ctypes.c_int32),
     ]
 
 

@@ -334,6 +334,8 @@ user_scan_reg_kernel(const float* __restrict__ Ut, const float* __restrict__ uno
                      int64_t surv_cap, unsigned long long* __restrict__ stats,
                      const int32_t* __restrict__ modes, const double* __restrict__ T64, int d) {
   extern __shared__ float4 sq4[];
+  __shared__ int32_t kslot[65], klist[64];
+  __shared__ int32_t nslots;
   const int B = blockIdx.x;
   const int npairs = pcount[B];
   if (npairs == 0) return;
@@ -343,9 +345,30 @@ user_scan_reg_kernel(const float* __restrict__ Ut, const float* __restrict__ uno
   const int dp4 = dp / 4;
   float4* qs = sq4;                                              // kQChunk x dp4
   PairInfo* pinfo = reinterpret_cast<PairInfo*>(qs + (size_t)kQChunk * dp4);
+  float* Ls = reinterpret_cast<float*>(pinfo + kQChunk);         // [nslots][blockDim]
   const int t = threadIdx.x;
   const bool active = t < cnt;
   const int r = s + (active ? t : 0);
+  // lower bounds of the k values this leaf's queries ask for, one row per distinct k
+  for (int k = t; k <= 64; k += blockDim.x) kslot[k] = -1;
+  __syncthreads();
+  for (int i = t; i < npairs; i += blockDim.x) {
+    const int k = kk[pairs[(int64_t)B * nq + i].j];
+    if (k <= kmax) kslot[k] = 0;
+  }
+  __syncthreads();
+  if (t == 0) {
+    int ns = 0;
+    for (int k = 1; k <= kmax; ++k)
+      if (kslot[k] == 0) {
+        kslot[k] = ns;
+        klist[ns++] = k;
+      }
+    nslots = ns;
+  }
+  __syncthreads();
+  for (int sl = 0; sl < nslots; ++sl)
+    Ls[sl * blockDim.x + t] = active ? Lt[(int64_t)(klist[sl] - 1) * mz + r] : -INFINITY;
   float4 ur[DP4MAX];
 #pragma unroll
   for (int c = 0; c < DP4MAX; ++c)
@@ -360,6 +383,7 @@ user_scan_reg_kernel(const float* __restrict__ Ut, const float* __restrict__ uno
     E = Eu[r];
     id = uid[r];
   }
+  const float nun = __fmul_ru(nu, 1.f + 2.f * gamma);
   unsigned long long scored = 0, yes_early = 0, fp64_here = 0;
   const int lane = threadIdx.x & 31;
   for (int p0 = 0; p0 < npairs; p0 += kQChunk) {
@@ -369,7 +393,9 @@ user_scan_reg_kernel(const float* __restrict__ Ut, const float* __restrict__ uno
       const PairEntry pe = pairs[(int64_t)B * nq + p0 + i];
       const int kj = kk[pe.j];
       const int sa = (modes != nullptr && modes[pe.j] == SAH_SAALSH && kj <= kmax) ? 1 : 0;
-      pinfo[i] = PairInfo{pe.j | (sa << 30), kj, pe.cphi, pe.sphi, qn[pe.j]};
+      // k is stored with its lower-bound slot in the high bits
+      const int slot = kj <= kmax ? kslot[kj] : 63;
+      pinfo[i] = PairInfo{pe.j | (sa << 30), kj | (slot << 24), pe.cphi, pe.sphi, qn[pe.j]};
     }
     __syncthreads();
     for (int i = threadIdx.x; i < pn * dp4; i += blockDim.x) {
@@ -378,15 +404,29 @@ user_scan_reg_kernel(const float* __restrict__ Ut, const float* __restrict__ uno
     }
     __syncthreads();
     for (int pi = 0; pi < pn; pi += kQG) {
-      float Lg[kQG];
+      // Lemma 3 first: groups no lane of the warp needs are not scored at all
+      float Lg[kQG], Llo[kQG];
+      bool need[kQG];
 #pragma unroll
       for (int g = 0; g < kQG; ++g) {
-        const int kg = pinfo[min(pi + g, pn - 1)].k;
-        Lg[g] = (active && kg <= kmax) ? Lt[(int64_t)(kg - 1) * mz + r] : -INFINITY;
+        const int col = min(pi + g, pn - 1);
+        const PairInfo pe = pinfo[col];
+        const int k = pe.k & 0xffffff, slot = pe.k >> 24;
+        Lg[g] = (k <= kmax) ? Ls[slot * blockDim.x + t] : -INFINITY;
+        Llo[g] = (Lg[g] == -INFINITY) ? -INFINITY : __fsub_rd(Lg[g], E);
+        bool pruned = false;
+        if (pe.cphi <= 1.5f) {
+          const float ub = __fmul_ru(__fmul_ru(nu, pe.nrm), fmaf(pe.cphi, ct, pe.sphi * st_) + 2.f * slack);
+          pruned = ub < Llo[g];
+        }
+        need[g] = active && (pi + g < pn) && !pruned;
       }
-      float acc[kQG];
+      const bool any = __any_sync(0xffffffffu, need[0] || need[1] || need[2] || need[3]);
+      if (!any) continue;
+      // four partial sums per query (one per float4 lane): 16 independent FMA chains
+      float ax[kQG], ay[kQG], az[kQG], aw[kQG];
 #pragma unroll
-      for (int g = 0; g < kQG; ++g) acc[g] = 0.f;
+      for (int g = 0; g < kQG; ++g) ax[g] = ay[g] = az[g] = aw[g] = 0.f;
 #pragma unroll
       for (int c = 0; c < DP4MAX; ++c) {
         if (c < dp4) {
@@ -394,10 +434,10 @@ user_scan_reg_kernel(const float* __restrict__ Ut, const float* __restrict__ uno
 #pragma unroll
           for (int g = 0; g < kQG; ++g) {
             const float4 b = qs[(pi + g) * dp4 + c];
-            acc[g] = fmaf(a.x, b.x, acc[g]);
-            acc[g] = fmaf(a.y, b.y, acc[g]);
-            acc[g] = fmaf(a.z, b.z, acc[g]);
-            acc[g] = fmaf(a.w, b.w, acc[g]);
+            ax[g] = fmaf(a.x, b.x, ax[g]);
+            ay[g] = fmaf(a.y, b.y, ay[g]);
+            az[g] = fmaf(a.z, b.z, az[g]);
+            aw[g] = fmaf(a.w, b.w, aw[g]);
           }
         }
       }
@@ -405,39 +445,31 @@ user_scan_reg_kernel(const float* __restrict__ Ut, const float* __restrict__ uno
       for (int g = 0; g < kQG; ++g) {
         if (pi + g >= pn) break;
         const PairInfo pe = pinfo[pi + g];
-        const int j = pe.j & 0x3fffffff, k = pe.k;
+        const int j = pe.j & 0x3fffffff, k = pe.k & 0xffffff;
         const bool sa_row = (pe.j >> 30) & 1;
-        const float nrm = pe.nrm, L = Lg[g];
         bool surv_flag = false, yes = false;
-        const float sq = acc[g];
-        if (active) {
-          const float Llo = (L == -INFINITY) ? -INFINITY : __fsub_rd(L, E);
-          bool pruned = false;
-          if (pe.cphi <= 1.5f) {   // Lemma 3 with the slack of the FP32 terms
-            const float ub = __fmul_ru(__fmul_ru(nu, nrm), fmaf(pe.cphi, ct, pe.sphi * st_) + 2.f * slack);
-            pruned = ub < Llo;
-          }
-          if (!pruned) {
-            ++scored;
-            const float eq = __fmul_ru(__fmul_ru(gamma, nu), nrm) + 1e-30f;
-            const float hi = __fadd_ru(sq, eq), lo = __fsub_rd(sq, eq);
-            if (hi < Llo) {
-              // "no": at least k items of P' score above <u,q>
-            } else if (l_exact && k <= kmax && lo >= __fadd_ru(L, E)) {
-              yes = true;
-            } else if (lo >= __fmul_ru(__fmul_ru(nu, pnorm[k - 1]), 1.f + 2.f * gamma)) {
-              yes = true;
-            } else if (T64 != nullptr && k <= kmax && !sa_row) {
-              const double t64 = T64[(int64_t)(k - 1) * mz + r];
-              if (t64 == t64) {
-                ++fp64_here;
-                yes = dot64_seq(Ut + (int64_t)r * dp, Qd + (int64_t)j * dp, d) >= t64;
-              } else {
-                surv_flag = true;
-              }
+        const float sq = (ax[g] + ay[g]) + (az[g] + aw[g]);
+        if (need[g]) {
+          ++scored;
+          const float L = Lg[g];
+          const float eq = __fmul_ru(__fmul_ru(gamma, nu), pe.nrm) + 1e-30f;
+          const float hi = __fadd_ru(sq, eq), lo = __fsub_rd(sq, eq);
+          if (hi < Llo[g]) {
+            // "no": at least k items of P' score above <u,q>
+          } else if (l_exact && k <= kmax && lo >= __fadd_ru(L, E)) {
+            yes = true;
+          } else if (lo >= __fmul_ru(nun, pnorm[k - 1])) {
+            yes = true;
+          } else if (T64 != nullptr && k <= kmax && !sa_row) {
+            const double t64 = T64[(int64_t)(k - 1) * mz + r];
+            if (t64 == t64) {
+              ++fp64_here;
+              yes = dot64_seq(Ut + (int64_t)r * dp, Qd + (int64_t)j * dp, d) >= t64;
             } else {
               surv_flag = true;
             }
+          } else {
+            surv_flag = true;
           }
         }
         if (yes) {
@@ -723,7 +755,7 @@ __global__ void bitmap_emit_kernel(const uint32_t* __restrict__ bitmap, int64_t 
 namespace {
 
 struct WsLayout {
-  size_t qd, qn, kk, pairs, pcount, survcnt, bitmap, chunk, offsets, stats, total;
+  size_t qd, qb, qn, kk, pairs, pcount, survcnt, bitmap, chunk, offsets, stats, total;
 };
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -734,11 +766,12 @@ WsLayout layout_for(const Index* ix, int qb, int nchunks) {
   auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes); return r; };
   int64_t words = (ix->m + 31) / 32;
   L.qd = take(sizeof(float) * (size_t)qb * ix->dp);
+  L.qb = take(sizeof(uint16_t) * (size_t)qb * std::max(ix->dk, 1));
   L.qn = take(sizeof(float) * qb);
   L.kk = take(sizeof(int32_t) * qb);
   L.pairs = take(sizeof(PairEntry) * (size_t)std::max(ix->nb, 1) * qb);
   L.pcount = take(sizeof(int32_t) * std::max(ix->nb, 1));
-  L.survcnt = take(2 * sizeof(unsigned long long));
+  L.survcnt = take(3 * sizeof(unsigned long long));
   L.bitmap = take(sizeof(uint32_t) * (size_t)qb * words);
   L.chunk = take(sizeof(int32_t) * (size_t)qb * nchunks);
   L.offsets = take(sizeof(int64_t) * (size_t)(qb + 1));
@@ -765,8 +798,10 @@ sah_status ensure_buf(Workspace* b, size_t bytes, cudaStream_t st) {
 
 sah_status ensure_ws(CallCtx* cx, size_t bytes, cudaStream_t st) { return ensure_buf(&cx->ws, bytes, st); }
 
+// three lists of cap entries: exact-mode survivors, SA-ALSH survivors, and the pairs the
+// tensor-core user pass leaves to the FP32 re-score
 sah_status ensure_surv(CallCtx* cx, int64_t cap, cudaStream_t st) {
-  return ensure_buf(&cx->surv, 2 * sizeof(Survivor) * (size_t)std::max<int64_t>(cap, 1), st);
+  return ensure_buf(&cx->surv, 3 * sizeof(Survivor) * (size_t)std::max<int64_t>(cap, 1), st);
 }
 
 // CUDA events around each stage, on the call's stream (only when timing is enabled).
@@ -882,7 +917,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
 
       tm.begin(0);
       SAH_CUDA(cudaMemsetAsync(stats, 0, sizeof(unsigned long long) * ST_COUNT, st));
-      SAH_CUDA(cudaMemsetAsync(survcnt, 0, 2 * sizeof(unsigned long long), st));
+      SAH_CUDA(cudaMemsetAsync(survcnt, 0, 3 * sizeof(unsigned long long), st));
       SAH_CUDA(cudaMemsetAsync(bitmap, 0, sizeof(uint32_t) * (size_t)nqb * words, st));
       SAH_CUDA(cudaMemcpyAsync(kk, ks_dev + q0, sizeof(int32_t) * nqb, cudaMemcpyDeviceToDevice, st));
       prep_queries_kernel<<<grid_for(nqb, 8), 256, 0, st>>>(Q_dev + (int64_t)q0 * ix->d, nqb, ix->d, ix->dp, Qd, qn,
@@ -902,8 +937,13 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
         const int dp4 = ix->dp / 4;
         const int reg_variant = dp4 <= 16 ? 16 : (dp4 <= 32 ? 32 : 0);
         tm.begin(2);
-        if (reg_variant) {
-          const size_t smem = (size_t)16 * kQChunk * dp4 + sizeof(PairInfo) * kQChunk;
+        int up_launches = 1;
+        if (ix->dk > 0 && ix->prm.tc_user_pass) {
+          SAH_TRY(run_user_pass_tc(ix, Qd, (uint16_t*)(w + L.qb), qn, kk, modes_q, nqb, pairs, pcount, bitmap, words,
+                                   surv + 2 * surv_cap, survcnt + 2, surv, survcnt, surv_cap, stats, ST_USERS_SCORED,
+                                   ST_YES_EARLY, ST_KEPT_USERS, ST_FP64, st, &up_launches));
+        } else if (reg_variant) {
+          const size_t smem = (size_t)16 * kQChunk * dp4 + sizeof(PairInfo) * kQChunk + sizeof(float) * 64 * threads;
           auto fn = reg_variant == 16 ? user_scan_reg_kernel<16> : user_scan_reg_kernel<32>;
           if (smem > 48 * 1024)
             SAH_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -924,7 +964,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
               ix->cone_slack, bitmap, words, surv, survcnt, surv_cap, stats, stage, modes_q, ix->T64, ix->d);
         }
         SAH_CUDA(cudaGetLastError());
-        tm.end(2, 1);
+        tm.end(2, up_launches);
         // ---- A5/A6 on the survivors (their number stays on the device)
         tm.begin(3);
         int nl = 0;
@@ -987,7 +1027,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
       // ---- the one synchronisation of the sub-batch: offsets, counters, survivor counts
       std::vector<int64_t> ob(nqb + 1);
       std::vector<unsigned long long> st_h(ST_COUNT);
-      unsigned long long ns2[2] = {0, 0};
+      unsigned long long ns2[3] = {0, 0, 0};
       int timeout = 0;
       SAH_CUDA(cudaMemcpyAsync(ob.data(), offsets, sizeof(int64_t) * (nqb + 1), cudaMemcpyDeviceToHost, st));
       SAH_CUDA(cudaMemcpyAsync(st_h.data(), stats, sizeof(unsigned long long) * ST_COUNT, cudaMemcpyDeviceToHost, st));
@@ -1009,13 +1049,14 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
         set_error("k must be >= 1 and the mode SAH_EXACT or SAH_SAALSH");
         return SAH_ERR_ARG;
       }
-      if ((int64_t)std::max(ns2[0], ns2[1]) > surv_cap) {
+      const int64_t nsmax = (int64_t)std::max(ns2[0], std::max(ns2[1], ns2[2]));
+      if (nsmax > surv_cap) {
         // a survivor list overflowed: grow it and run this sub-batch again
         if (attempt > 4) {
           set_error("survivor list kept overflowing");
           return SAH_ERR_OOM;
         }
-        surv_cap = (int64_t)std::max(ns2[0], ns2[1]) * 5 / 4 + 1024;
+        surv_cap = nsmax * 5 / 4 + 1024;
         continue;
       }
       const int64_t new_total = ob[nqb];
@@ -1044,7 +1085,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
         SAH_CUDA(cudaStreamSynchronize(st));
       }
       agg.survivors += (int64_t)(ns2[0] + ns2[1]);
-      cx->surv_hint = std::max<int64_t>(1 << 16, 2 * (int64_t)std::max(ns2[0], ns2[1]));
+      cx->surv_hint = std::max<int64_t>(1 << 16, 2 * nsmax);
       agg.block_pairs_total += (int64_t)ix->nb * nqb;
       agg.block_pairs_kept += (int64_t)st_h[ST_PAIRS_KEPT];
       agg.users_scored += (int64_t)st_h[ST_USERS_SCORED];

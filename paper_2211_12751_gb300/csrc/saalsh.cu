@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <thread>
 #include <vector>
 
 #include "sah_internal.cuh"
@@ -108,9 +109,53 @@ __global__ void item_codes_kernel(const float* __restrict__ Ps, int d, int dp, i
   codes[it * K + t] = (uint16_t)code;
 }
 
-// User codes: signs of <a, u> (Eq. 7 up to a positive factor), one thread per (user, table).
+// User codes: signs of <a, u> (Eq. 7 up to a positive factor).  A CTA takes 128 users and
+// kCodeTables tables: their projection rows and the users' rows are staged in shared
+// memory (odd row stride: conflict-free), one thread per (user, table).
+constexpr int kCodeUsers = 128;
+constexpr int kCodeTables = 2;
+
 __global__ void user_codes_kernel(const float* __restrict__ Ut, int d, int dp, int64_t m, const float* __restrict__ A,
                                   int d1p, int K, int bits, uint16_t* __restrict__ codes) {
+  extern __shared__ float sh[];
+  const int ds = d | 1;                                   // odd stride
+  float* us = sh;                                         // kCodeUsers x ds
+  float* as = sh + kCodeUsers * ds;                       // kCodeTables * bits x ds
+  const int64_t u0 = (int64_t)blockIdx.x * kCodeUsers;
+  const int t0 = blockIdx.y * kCodeTables;
+  const int nt = min(kCodeTables, K - t0);
+  for (int i = threadIdx.x; i < kCodeUsers * d; i += blockDim.x) {
+    const int r = i / d, e = i % d;
+    us[r * ds + e] = (u0 + r < m) ? Ut[(u0 + r) * dp + e] : 0.f;
+  }
+  for (int i = threadIdx.x; i < nt * bits * d; i += blockDim.x) {
+    const int r = i / d, e = i % d;
+    as[r * ds + e] = A[(int64_t)(t0 * bits + r) * d1p + e];
+  }
+  __syncthreads();
+  const int r = threadIdx.x % kCodeUsers, tl = threadIdx.x / kCodeUsers;
+  if (tl >= nt || u0 + r >= m) return;
+  const float* x = us + r * ds;
+  uint32_t code = 0;
+  for (int b = 0; b < bits; ++b) {
+    const float* a = as + (tl * bits + b) * ds;
+    float s0 = 0.f, s1 = 0.f;
+    int e = 0;
+    for (; e + 1 < d; e += 2) {
+      s0 = fmaf(a[e], x[e], s0);
+      s1 = fmaf(a[e + 1], x[e + 1], s1);
+    }
+    if (e < d) s0 = fmaf(a[e], x[e], s0);
+    code |= ((s0 + s1) >= 0.f ? 1u : 0u) << b;
+  }
+  codes[(u0 + r) * K + t0 + tl] = (uint16_t)code;
+}
+
+// The same codes without staging, for dimensions too large for the tile: one thread per
+// (user, table).
+__global__ void user_codes_simple_kernel(const float* __restrict__ Ut, int d, int dp, int64_t m,
+                                         const float* __restrict__ A, int d1p, int K, int bits,
+                                         uint16_t* __restrict__ codes) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= m * K) return;
   const int64_t u = g / K;
@@ -415,24 +460,34 @@ sah_status build_saalsh(Index* ix, const float* srp_host, cudaStream_t st) {
   std::vector<uint16_t> bcode((size_t)ni * K);
   std::vector<int32_t> bitem((size_t)ni * K);
   {
-    size_t o = 0;
-    std::vector<int32_t> idx;
-    for (int j = 0; j < t; ++j) {
-      for (int tb = 0; tb < K; ++tb) {
-        boff[(size_t)j * K + tb] = (int32_t)o;
-        idx.resize(start[j + 1] - start[j]);
-        std::iota(idx.begin(), idx.end(), start[j]);
-        std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) {
-          return ic[(size_t)(x - first) * K + tb] < ic[(size_t)(y - first) * K + tb];
-        });
-        for (int32_t x : idx) {
-          bcode[o] = ic[(size_t)(x - first) * K + tb];
-          bitem[o] = x;
-          ++o;
+    // segment (partition j, table tb) starts at start[j] - first times K plus tb times |S_j|
+    for (int j = 0; j < t; ++j)
+      for (int tb = 0; tb < K; ++tb)
+        boff[(size_t)j * K + tb] = (int32_t)((size_t)(start[j] - first) * K + (size_t)tb * (start[j + 1] - start[j]));
+    boff[(size_t)t * K] = (int32_t)((size_t)ni * K);
+    // every (partition, table) segment is sorted by code independently: spread them over threads
+    const int nthreads = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> pool;
+    for (int w = 0; w < nthreads; ++w) {
+      pool.emplace_back([&, w]() {
+        std::vector<int32_t> idx;
+        for (int seg = w; seg < t * K; seg += nthreads) {
+          const int j = seg / K, tb = seg % K;
+          idx.resize(start[j + 1] - start[j]);
+          std::iota(idx.begin(), idx.end(), start[j]);
+          std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) {
+            return ic[(size_t)(x - first) * K + tb] < ic[(size_t)(y - first) * K + tb];
+          });
+          size_t o = (size_t)boff[seg];
+          for (int32_t x : idx) {
+            bcode[o] = ic[(size_t)(x - first) * K + tb];
+            bitem[o] = x;
+            ++o;
+          }
         }
-      }
+      });
     }
-    boff[(size_t)t * K] = (int32_t)o;
+    for (auto& th : pool) th.join();
   }
   SAH_TRY(dev_alloc(ix, (void**)&ix->sa_boff, sizeof(int32_t) * boff.size()));
   SAH_TRY(dev_alloc(ix, (void**)&ix->sa_bcode, sizeof(uint16_t) * bcode.size()));
@@ -444,8 +499,17 @@ sah_status build_saalsh(Index* ix, const float* srp_host, cudaStream_t st) {
   // user codes (leaf order)
   if (ix->m_nz > 0) {
     SAH_TRY(dev_alloc(ix, (void**)&ix->sa_ucode, sizeof(uint16_t) * (size_t)ix->m_nz * K));
-    user_codes_kernel<<<grid_for(ix->m_nz * K, 256), 256, 0, st>>>(ix->Ut, d, dp, ix->m_nz, ix->sa_A, ix->sa_d1p,
-                                                                   K, bits, ix->sa_ucode);
+    const size_t smem = sizeof(float) * (size_t)(kCodeUsers + kCodeTables * bits) * (d | 1);
+    if (smem <= 160 * 1024) {
+      if (smem > 48 * 1024)
+        SAH_CUDA(cudaFuncSetAttribute(user_codes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      dim3 g(grid_for(ix->m_nz, kCodeUsers), (K + kCodeTables - 1) / kCodeTables);
+      user_codes_kernel<<<g, kCodeUsers * kCodeTables, smem, st>>>(ix->Ut, d, dp, ix->m_nz, ix->sa_A, ix->sa_d1p, K,
+                                                                  bits, ix->sa_ucode);
+    } else {
+      user_codes_simple_kernel<<<grid_for(ix->m_nz * K, 256), 256, 0, st>>>(ix->Ut, d, dp, ix->m_nz, ix->sa_A,
+                                                                            ix->sa_d1p, K, bits, ix->sa_ucode);
+    }
     SAH_CUDA(cudaGetLastError());
   }
   // Hamming probes: every mask over code_bits bits with popcount <= probe_radius

@@ -106,6 +106,7 @@ struct Index {
   uint16_t* Ub = nullptr;     // m_nz x dk, leaf order
   uint16_t* Pb = nullptr;     // n x dk, descending norm order
   CUtensorMap tmap_P{};       // TMA map of Pb: box 64 x 256, 128-byte swizzle
+  CUtensorMap tmap_U{};       // TMA map of Ub: box 64 x 128, 128-byte swizzle
   int* dev_timeout = nullptr; // set by a kernel whose bounded wait ran out
 
   // SA-ALSH over the items behind P' (Alg. 1): norm partitions S_j (descending M_j), their
@@ -186,6 +187,13 @@ sah_status build_saalsh(Index* ix, const float* srp_host, cudaStream_t st);
 sah_status run_saalsh(Index* ix, const Survivor* surv, const unsigned long long* count_dev, int64_t cap,
                       const float* Qd, const float* qn, const int32_t* kk, uint32_t* bitmap, int64_t words,
                       unsigned long long* stats, int stat_items, cudaStream_t st, int* launches);
+// user_pass_tc.cu: the user pass on tcgen05 (BF16 copies present); the pairs its bound
+// leaves open go to resc and are re-scored in FP32 by a second kernel.
+sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qb, const float* qn, const int32_t* kk,
+                            const int32_t* modes, int nq, const void* pairs, const int32_t* pcount, uint32_t* bitmap,
+                            int64_t words, Survivor* resc, unsigned long long* resc_count, Survivor* surv,
+                            unsigned long long* surv_count, int64_t surv_cap, unsigned long long* stats,
+                            int st_scored, int st_yes, int st_kept, int st_fp64, cudaStream_t st, int* launches);
 // verify_tc.cu
 sah_status build_bf16_copies(Index* ix, cudaStream_t st);
 // Decides every survivor with the tcgen05 kernel and sets the answer bits; the counters

@@ -509,6 +509,17 @@ sah_status build_bf16_copies(Index* ix, cudaStream_t st) {
     set_error("cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
     return SAH_ERR_CUDA;
   }
+  if (ix->m_nz > 0) {
+    cuuint64_t udims[2] = {(cuuint64_t)dk, (cuuint64_t)ix->m_nz};
+    cuuint32_t ubox[2] = {64, 128};
+    r = encode(&ix->tmap_U, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ix->Ub, udims, strides, ubox, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      set_error("cuTensorMapEncodeTiled (users) failed with code " + std::to_string((int)r));
+      return SAH_ERR_CUDA;
+    }
+  }
   return SAH_OK;
 }
 

@@ -226,3 +226,17 @@ def test_survivor_list_overflow_reruns(sah, precision):
     assert ix.stats()["survivors"] > (1 << 16)
     for r in (0, 57, 123, 199):
         assert np.array_equal(got[r], _truth(W.U, W.P, Q[r], (30,))[30]), r
+
+
+@pytest.mark.parametrize("p_prime", [10, 1 << 30])
+@pytest.mark.parametrize("d", [50, 100])
+def test_tensor_core_user_pass(sah, p_prime, d):
+    """The opt-in tcgen05 user pass (per-leaf GEMMs with the BF16 bound, FP32 re-score of
+    what it leaves open) gives the oracle's answers."""
+    W = workload.make("c2", m=6000, n=2000, d=d)
+    ix = sah.Index(W.U, W.P, k_max=50, leaf_size=256, p_prime=p_prime, precision=sah.BF16, tc_user_pass=1)
+    Q, K, _ = W.requests()
+    Q, K = Q[:40], K[:40]
+    got = ix.rkmips_batch(Q, K)
+    for j in range(len(K)):
+        assert np.array_equal(got[j], _truth(W.U, W.P, Q[j], (int(K[j]),))[int(K[j])]), j
