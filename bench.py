@@ -353,6 +353,16 @@ def main():
         return host, times, stage_ms / steps, launches / steps, st_last, total
 
     ix, build_s = build(args.threshold, args.precision)
+    ist = ix.stats()
+    index_gemm = None
+    if ist.get("build_gemm_ms", 0.0) > 0:
+        # index-time exact thresholds on tcgen05: S = U P^T over all users and items
+        fl = 2.0 * W.m * W.n * W.d
+        index_gemm = {"ms": ist["build_gemm_ms"], "tflops_algorithmic": fl / (ist["build_gemm_ms"] / 1e3) / 1e12,
+                      "peak_tflops": peaks["bf16_tflops"],
+                      "frac": fl / (ist["build_gemm_ms"] / 1e3) / 1e12 / peaks["bf16_tflops"],
+                      "k_padded": 64 if W.d <= 64 else 128, "overflow_rows": ist["build_overflow_rows"],
+                      "kernel": "topk_tc_kernel"}
     if world > 1:
         torch.distributed.barrier()
     with ClockSampler(local) as clk:
@@ -430,7 +440,7 @@ def main():
             "stage_counts": {k: st[k] for k in ("block_pairs_total", "block_pairs_kept", "users_in_kept_blocks",
                                                 "users_scored", "users_yes_early", "survivors", "fp64_rescored",
                                                 "items_scanned", "results")},
-            "index_build_s": build_s, "clocks": clocks,
+            "index_build_s": build_s, "index_gemm": index_gemm, "clocks": clocks,
             "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99)),
                            "per": "batch of %d queries" % nq}}
 

@@ -165,6 +165,8 @@ typedef struct {
    * decision (A5/A6), [4] answer compaction (A7), [5] SA-ALSH hashing. */
   double stage_ms[8];
   int64_t stage_launches[8];
+  double build_gemm_ms;         /* index build, |P'| = n with SAH_BF16: the tcgen05 GEMM's time */
+  int64_t build_overflow_rows;  /* users of that GEMM whose candidate list overflowed */
 } sah_stats;
 
 sah_status sah_index_stats(const sah_index* index, sah_stats* out);

@@ -54,13 +54,14 @@ class Stats(ctypes.Structure):
         "n_items", "n_users", "n_blocks", "n_partitions", "device_bytes", "queries",
         "block_pairs_total", "block_pairs_kept", "users_scored", "users_yes_early",
         "survivors", "fp64_rescored", "results", "users_in_kept_blocks", "items_scanned")] + [
-        ("stage_ms", ctypes.c_double * 8), ("stage_launches", ctypes.c_int64 * 8)]
+        ("stage_ms", ctypes.c_double * 8), ("stage_launches", ctypes.c_int64 * 8),
+        ("build_gemm_ms", ctypes.c_double), ("build_overflow_rows", ctypes.c_int64)]
 
     def as_dict(self):
         out = {}
         for name, _ in self._fields_:
             v = getattr(self, name)
-            out[name] = list(v) if name.startswith("stage_") else int(v)
+            out[name] = list(v) if name.startswith("stage_") else (float(v) if name.endswith("_ms") else int(v))
         return out
 
 

@@ -307,6 +307,8 @@ sah_status sah_index_stats(const sah_index* index, sah_stats* out) {
   out->n_blocks = ix->nb;
   out->n_partitions = ix->sa_parts;
   out->device_bytes = (int64_t)(ix->bytes + sah::ctx_bytes(&ix->main_ctx));
+  out->build_gemm_ms = ix->build_gemm_ms;
+  out->build_overflow_rows = ix->build_overflow_rows;
   return SAH_OK;
 }
 

@@ -440,6 +440,13 @@ __global__ void block_lower_bounds_kernel(const float* __restrict__ Lt, const fl
   LB[(int64_t)k * nb + B] = mn;
 }
 
+// leaf (block) of every user position
+__global__ void user_block_kernel(const int32_t* __restrict__ bstart, int nb, int32_t* __restrict__ ublock) {
+  const int B = blockIdx.x;
+  if (B >= nb) return;
+  for (int r = bstart[B] + threadIdx.x; r < bstart[B + 1]; r += blockDim.x) ublock[r] = B;
+}
+
 __global__ void fill_i32_kernel(int32_t* p, int64_t n, int32_t v) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) p[i] = v;
@@ -673,6 +680,9 @@ sah_status build_index_device(Index* ix, const float* U_dev, const float* P_dev,
   leaf_stats_kernel<<<ix->nb, 256, sizeof(float) * dp, st>>>(Uh_t, dp, ix->bstart, ix->bcent, ix->bcos,
                                                              ix->bsin, ix->ucos, ix->usin);
   SAH_CUDA(cudaGetLastError());
+  SAH_TRY(dev_alloc(ix, (void**)&ix->ublock, sizeof(int32_t) * mz));
+  user_block_kernel<<<ix->nb, 256, 0, st>>>(ix->bstart, ix->nb, ix->ublock);
+  SAH_CUDA(cudaGetLastError());
 
   // ---- A1: lower-bound arrays over P' and the per-block bounds
   const int kmax = ix->kmax;
@@ -688,13 +698,22 @@ sah_status build_index_device(Index* ix, const float* U_dev, const float* P_dev,
     SAH_CUDA(cudaFuncSetAttribute(topk_lower_bounds_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
     unsigned grid = grid_for(mz, kTopkWarps * kUsersPerWarp);
+    if (ix->prm.precision == SAH_BF16) SAH_TRY(build_bf16_copies(ix, st));
     if (ix->pp > 0) {
       if (ix->l_exact) {
         SAH_CUDA(cudaMallocAsync((void**)&ids64, sizeof(int32_t) * 64 * (size_t)mz, st));
         SAH_CUDA(cudaMallocAsync((void**)&vlast, sizeof(float) * (size_t)mz, st));
       }
-      topk_lower_bounds_kernel<<<grid, kTopkWarps * 32, smem, st>>>(ix->Ut, ix->Ps, dp, mz, ix->pp, kmax,
-                                                                    tile_items, stride4, ix->Lt, ids64, vlast);
+      if (ix->l_exact && ix->dk > 0 && ix->n > 256) {
+        // tensor cores: a floor from the first 256 items, then every item through tcgen05
+        topk_lower_bounds_kernel<<<grid, kTopkWarps * 32, smem, st>>>(ix->Ut, ix->Ps, dp, mz, 256, kmax, tile_items,
+                                                                      stride4, ix->Lt, ids64, vlast);
+        SAH_CUDA(cudaGetLastError());
+        SAH_TRY(topk_full_tc(ix, vlast, ids64, st, nullptr));
+      } else {
+        topk_lower_bounds_kernel<<<grid, kTopkWarps * 32, smem, st>>>(ix->Ut, ix->Ps, dp, mz, ix->pp, kmax,
+                                                                      tile_items, stride4, ix->Lt, ids64, vlast);
+      }
     } else {
       // no P': every lower bound is -inf
       fill_i32_kernel<<<grid_for((int64_t)kmax * mz, 256), 256, 0, st>>>(
@@ -713,7 +732,6 @@ sah_status build_index_device(Index* ix, const float* U_dev, const float* P_dev,
   block_lower_bounds_kernel<<<grid_for((int64_t)kmax * ix->nb, 256), 256, 0, st>>>(
       ix->Lt, ix->Eu, ix->unorm, ix->bstart, ix->nb, mz, kmax, ix->LB);
   SAH_CUDA(cudaGetLastError());
-  if (ix->prm.precision == SAH_BF16) SAH_TRY(build_bf16_copies(ix, st));
   SAH_CUDA(cudaStreamSynchronize(st));
 
   cudaFreeAsync(pn_raw, st);

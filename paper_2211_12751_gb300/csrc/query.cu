@@ -85,7 +85,8 @@ __global__ void block_filter_kernel(const float* __restrict__ bcent, const float
                                     const float* __restrict__ Qd, const float* __restrict__ qn,
                                     const int32_t* __restrict__ kk, int nq, float slack,
                                     PairEntry* __restrict__ pairs, int32_t* __restrict__ pcount,
-                                    unsigned long long* __restrict__ stats) {
+                                    unsigned long long* __restrict__ stats, uint32_t* __restrict__ kept_mask,
+                                    int mask_words) {
   extern __shared__ float4 c4s[];   // the leaf's unit centre
   __shared__ int32_t cnt;
   const int B = blockIdx.x;
@@ -141,6 +142,9 @@ __global__ void block_filter_kernel(const float* __restrict__ bcent, const float
       }
     }
     const unsigned m = __ballot_sync(0xffffffffu, keep);
+    // the same decisions as a dense bitmask per leaf: bit j of word j / 32
+    if (kept_mask && lane == 0 && (j0 + threadIdx.x) / 32 < mask_words)
+      kept_mask[(int64_t)B * mask_words + (j0 + threadIdx.x) / 32] = m;
     if (m) {
       int base = 0;
       const int leader = __ffs(m) - 1;
@@ -929,7 +933,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
         block_filter_kernel<<<ix->nb, 128, sizeof(float) * ix->dp, st>>>(ix->bcent, ix->bcos, ix->bsin, ix->LB,
                                                                           ix->nb, ix->kmax, ix->n, ix->dp, Qd, qn,
                                                                           kk, nqb, ix->cone_slack, pairs, pcount,
-                                                                          stats);
+                                                                          stats, nullptr, 0);
         SAH_CUDA(cudaGetLastError());
         tm.end(1, 1);
         // ---- A4: register-tiled kernel for d <= 128, the shared-memory one otherwise

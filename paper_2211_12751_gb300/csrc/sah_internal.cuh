@@ -84,6 +84,7 @@ struct Index {
   int32_t* uid = nullptr;     // m_nz, caller's user id of each row
   float* ucos = nullptr;      // cos theta_u to the leaf centre (Lemma 3)
   float* usin = nullptr;      // sin theta_u
+  int32_t* ublock = nullptr;  // m_nz: leaf of each user position
   int32_t* zero_uid = nullptr;
   int64_t nzero = 0;
 
@@ -125,6 +126,9 @@ struct Index {
   uint16_t* sa_bcode = nullptr;      // codes, sorted within each (partition, table)
   int32_t* sa_bitem = nullptr;       // matching item positions
   uint32_t* sa_probes = nullptr;     // XOR masks with popcount <= probe_radius
+
+  double build_gemm_ms = 0.0;         // index-time tensor-core GEMM (|P'| = n, BF16)
+  int64_t build_overflow_rows = 0;    // users whose candidate list overflowed (scanned in full)
 
   std::vector<void*> allocs;
   size_t bytes = 0;
@@ -194,6 +198,8 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qb, const floa
                             int64_t words, Survivor* resc, unsigned long long* resc_count, Survivor* surv,
                             unsigned long long* surv_count, int64_t surv_cap, unsigned long long* stats,
                             int st_scored, int st_yes, int st_kept, int st_fp64, cudaStream_t st, int* launches);
+// topk_tc.cu: the 64 largest FP32 scores of every user over all items, through tcgen05
+sah_status topk_full_tc(Index* ix, float* vlast, int32_t* ids64, cudaStream_t st, double* gemm_ms);
 // verify_tc.cu
 sah_status build_bf16_copies(Index* ix, cudaStream_t st);
 // Decides every survivor with the tcgen05 kernel and sets the answer bits; the counters

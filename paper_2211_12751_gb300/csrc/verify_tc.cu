@@ -286,7 +286,7 @@ verify_tc_kernel(const __grid_constant__ CUtensorMap tmapP, TcParams prm) {
       if (t + 1 < T) pn_next = prm.pnorm[(int64_t)(t + 1) * kTileN];
       if (__any_sync(0xffffffffu, need)) {
         const float E = __fmul_ru(cbu, pn_tile) + 1e-30f;
-        const float thb = __fsub_rd(lo, E), tha = __fadd_ru(hi, E);
+        const float thb = __fsub_rd(lo, E);
         const int ncols = (int)std::min<int64_t>(kTileN, prm.n - (int64_t)t * kTileN);
         if (need) scanned += ncols;
 #pragma unroll 1
@@ -304,13 +304,15 @@ verify_tc_kernel(const __grid_constant__ CUtensorMap tmapP, TcParams prm) {
               const float gm = max3(max3(g[0], g[1], g[2]), max3(g[3], g[4], g[5]),
                                     max3(max3(g[6], g[7], g[8]), g[9], g[10]));
               if (gm > thb) {
+                // per item: the bound of its own norm (items fall in norm within a tile)
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
                   const int col = h + c0 + i;
                   if (col < ncols && v[c0 + i] > thb) {
-                    if (v[c0 + i] > tha) {
+                    const float Ei = __fmul_ru(cbu, prm.pnorm[(int64_t)t * kTileN + col]) + 1e-30f;
+                    if (__fsub_rd(v[c0 + i], Ei) > hi) {
                       ++certain;
-                    } else {
+                    } else if (__fadd_ru(v[c0 + i], Ei) > lo) {
                       if (band < kBandCap) prm.band_items[gi * kBandCap + band] = t * kTileN + col;
                       ++band;
                     }
