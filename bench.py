@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"],
                     help="working precision of the kMIPS decision (bf16: tcgen05 tensor cores)")
     ap.add_argument("--leaf-size", type=int, default=256)
+    ap.add_argument("--tc-user-pass", type=int, default=1, choices=[0, 1],
+                    help="with bf16: 1 runs the user pass as one tcgen05 GEMM per 256 queries "
+                         "(split BF16 operands), 0 on the CUDA cores in FP32")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -285,6 +288,7 @@ def config_block(W, args):
                         f"5% items x3, seed 0; {len(W.query_idx)} item queries x k in {list(map(int, W.ks))}",
             "queries_per_step": int(len(W.query_idx) * (len(W.ks) if W.every_k else 1)),
             "threshold_mode": args.threshold, "precision": args.precision, "leaf_size": args.leaf_size,
+            "tc_user_pass": int(args.tc_user_pass and args.precision == "bf16"),
             "k_max": 50,
             "l2": "flushed between timed steps (256 MiB write)"}
 
@@ -352,7 +356,8 @@ def main():
         ix.set_timing(False)
         return host, times, stage_ms / steps, launches / steps, st_last, total
 
-    ix, build_s = build(args.threshold, args.precision)
+    tc_main = int(args.tc_user_pass and args.precision == "bf16")
+    ix, build_s = build(args.threshold, args.precision, tc_user_pass=tc_main)
     ist = ix.stats()
     index_gemm = None
     if ist.get("build_gemm_ms", 0.0) > 0:
@@ -407,7 +412,15 @@ def main():
     per_launch = lambda x: x / max(launches[dom_i], 1)
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     kernel = STAGE_KERNELS.get(dom, dom)
-    if dom == "kmips_decision" and args.precision == "bf16":
+    if dom == "user_pass" and tc_main:
+        # one dense GEMM U Q^T over the users of the kept leaves (A8), useful FLOPs only
+        # (the three split-BF16 products count once)
+        kernel = "user_pass_tc_kernel"
+        fl = 2.0 * W.d * st["users_in_kept_blocks"] * nq
+        roof = {"bound": "tensor", "achieved": fl / (stage_ms[dom_i] / 1e3) / 1e12,
+                "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json bf16_tflops, burst)"}
+    elif dom == "kmips_decision" and args.precision == "bf16":
         # the tcgen05 GEMM: useful BF16 MACs of the rows still open, per launch of the
         # stage's kernels (the GEMM itself is one of them)
         kernel = "verify_tc_kernel"
@@ -450,18 +463,21 @@ def main():
         line["variants"] = {}
         vsteps = max(3, args.steps // 2)
         for thr in ("full", "paper"):
-            for prec in ("fp32", "bf16"):
-                same = thr == args.threshold and prec == args.precision
-                ixv, bv = (ix, build_s) if same else build(thr, prec)
+            for prec, tc in (("fp32", 0), ("bf16", 0), ("bf16", 1)):
+                name = f"{thr}_{prec}" + ("_tc_user_pass" if tc else "")
+                same = thr == args.threshold and prec == args.precision and tc == tc_main
+                ixv, bv = (ix, build_s) if same else build(thr, prec, tc_user_pass=tc)
                 rec = {"index_build_s": bv}
                 if not same:
-                    _, tv, _, _, stv, _ = measure(ixv, vsteps, 3, timing=False)
+                    _, tv, smv, _, stv, _ = measure(ixv, vsteps, 3, timing=True)
                     rec.update(value=nq * len(tv) / (sum(tv) / 1e3), ms_per_step=float(np.mean(tv)),
+                               user_pass_ms=float(smv[2]), kmips_decision_ms=float(smv[3]),
                                survivors=stv["survivors"], items_scanned=stv["items_scanned"])
                 else:
-                    rec.update(value=value, ms_per_step=t_step_ms, survivors=st["survivors"],
+                    rec.update(value=value, ms_per_step=t_step_ms, user_pass_ms=float(stage_ms[2]),
+                               kmips_decision_ms=float(stage_ms[3]), survivors=st["survivors"],
                                items_scanned=st["items_scanned"])
-                if thr == "paper":
+                if thr == "paper" and not tc:
                     sa_modes = np.full(nq, sah.SAALSH, np.int32)
                     hsa, tsa, _, _, stsa, _ = measure(ixv, vsteps, 3, timing=False, modes=sa_modes)
                     exact_sets = host if same else ixv.rkmips_batch(Q, K)
@@ -469,17 +485,9 @@ def main():
                           else 1.0 for a, b in zip(hsa, exact_sets)]
                     rec["saalsh"] = {"value": nq * len(tsa) / (sum(tsa) / 1e3), "ms_per_step": float(np.mean(tsa)),
                                      "f1_vs_exact": float(np.mean(f1)), "min_f1": float(np.min(f1))}
-                line["variants"][f"{thr}_{prec}"] = rec
+                line["variants"][name] = rec
                 if not same:
                     ixv.close()
-        # the user pass as per-leaf tcgen05 GEMMs (BF16 bound, FP32 re-score of what it leaves open)
-        for thr in ("full", "paper"):
-            ixv, bv = build(thr, "bf16", tc_user_pass=1)
-            _, tv, smv, lv, stv, _ = measure(ixv, vsteps, 3, timing=True)
-            line["variants"][f"{thr}_bf16_tc_user_pass"] = {
-                "value": nq * len(tv) / (sum(tv) / 1e3), "ms_per_step": float(np.mean(tv)),
-                "user_pass_ms": float(smv[2]), "index_build_s": bv}
-            ixv.close()
 
     if rank == 0 and not args.no_serving:
         line["serving"] = serve_stream(sah, ix, W, args.serve_rate, args.serve_requests)

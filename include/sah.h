@@ -70,12 +70,16 @@ typedef struct {
   uint64_t seed;        /* Cone-Tree random points (Alg. 3) and, when srp is NULL, the SRP matrix */
   const float* srp;     /* optional host matrix (n_tables * code_bits) x (d + 1) of SRP projection
                            vectors (Eq. 1); NULL draws it from seed.  Copied at build time. */
-  int32_t tc_user_pass; /* with SAH_BF16: 1 runs the user pass (Lemma 3 and the bound tests of
-                           Alg. 5) as per-leaf tcgen05 GEMMs; 0 (default) as register-tiled FP32 */
+  int32_t tc_user_pass; /* with SAH_BF16: 1 (default) runs the user pass as one tcgen05 GEMM
+                           U Q^T per 256 queries (split BF16 operands, FP32 accumulation) whose
+                           epilogue applies the bound tests of Alg. 5 to the pairs of the leaves
+                           Lemma 2 kept; 0 runs Lemma 3 and FP32 dot products on the CUDA cores.
+                           Results are identical; only the speed differs. */
 } sah_params;
 
 /* Fills *p with the paper's parameters (k_max 50, N_0 20, b 0.5, K 128) and the build's
- * defaults for the rest (code_bits 16, p_prime 4 * k_max, FP32, probe radius 0, seed 0). */
+ * defaults for the rest (code_bits 16, p_prime 4 * k_max, FP32, probe radius 0, seed 0,
+ * tensor-core user pass on when the precision is SAH_BF16). */
 void sah_default_params(sah_params* p);
 
 /* Alg. 4 (SAH Indexing): item norms and descending-norm order, lower-bound arrays over
@@ -153,7 +157,9 @@ typedef struct {
   int64_t queries;              /* queries in the last call */
   int64_t block_pairs_total;    /* (block, query) pairs examined */
   int64_t block_pairs_kept;     /* pairs that survived the node-level bound (Lemma 2) */
-  int64_t users_scored;         /* users whose <u,q> was computed after the vector bound (Lemma 3) */
+  int64_t users_scored;         /* (user, query) pairs whose <u,q> the user pass used: after the
+                                   vector bound (Lemma 3) on the CUDA cores, every pair of a
+                                   kept leaf on the tensor cores */
   int64_t users_yes_early;      /* "yes" without a kMIPS (lower/upper-bound tests) */
   int64_t survivors;            /* users sent to the per-user kMIPS decision */
   int64_t fp64_rescored;        /* survivors decided in double precision */
@@ -167,6 +173,7 @@ typedef struct {
   int64_t stage_launches[8];
   double build_gemm_ms;         /* index build, |P'| = n with SAH_BF16: the tcgen05 GEMM's time */
   int64_t build_overflow_rows;  /* users of that GEMM whose candidate list overflowed */
+  int64_t pairs_rescored;       /* pairs the tensor-core user pass left to the FP32 re-score */
 } sah_stats;
 
 sah_status sah_index_stats(const sah_index* index, sah_stats* out);

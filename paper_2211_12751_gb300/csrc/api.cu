@@ -87,7 +87,7 @@ void sah_default_params(sah_params* p) {
   p->probe_radius = 0;
   p->seed = 0;
   p->srp = nullptr;
-  p->tc_user_pass = 0;
+  p->tc_user_pass = 1;
 }
 
 const char* sah_status_string(sah_status s) {

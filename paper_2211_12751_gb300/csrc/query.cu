@@ -13,6 +13,7 @@
 //   A7  answers are set in a per-query bitmap over the caller's user ids and emitted in
 //       ascending id order.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 
@@ -46,15 +47,21 @@ constexpr int kWordsPerChunk = 2048;
 inline unsigned grid_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
 
 // ---------------------------------------------------------------- query preparation
+// A row with an invalid k or mode is counted (the call then fails) and its k set to
+// INT_MAX, which no kernel uses as an index: such a row asks for every user.
 __global__ void prep_queries_kernel(const float* __restrict__ Q, int nq, int d, int dp,
                                     float* __restrict__ Qd, float* __restrict__ qn,
-                                    const int32_t* __restrict__ kk, const int32_t* __restrict__ modes,
+                                    int32_t* __restrict__ kk, const int32_t* __restrict__ modes,
                                     unsigned long long* __restrict__ stats) {
   int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   int lane = threadIdx.x & 31;
   if (j >= nq) return;
-  if (lane == 0 && (kk[j] < 1 || (modes && modes[j] != SAH_EXACT && modes[j] != SAH_SAALSH)))
+  const bool bad_k = kk[j] < 1 || (modes && modes[j] != SAH_EXACT && modes[j] != SAH_SAALSH);
+  __syncwarp();
+  if (lane == 0 && bad_k) {
     atomicAdd(&stats[ST_BAD_K], 1ull);
+    kk[j] = INT_MAX;
+  }
   float s = 0.f;
   bool fin = true;
   for (int i = lane; i < dp; i += 32) {
@@ -86,7 +93,7 @@ __global__ void block_filter_kernel(const float* __restrict__ bcent, const float
                                     const int32_t* __restrict__ kk, int nq, float slack,
                                     PairEntry* __restrict__ pairs, int32_t* __restrict__ pcount,
                                     unsigned long long* __restrict__ stats, uint32_t* __restrict__ kept_mask,
-                                    int mask_words) {
+                                    int mask_words, const int32_t* __restrict__ bstart) {
   extern __shared__ float4 c4s[];   // the leaf's unit centre
   __shared__ int32_t cnt;
   const int B = blockIdx.x;
@@ -156,7 +163,10 @@ __global__ void block_filter_kernel(const float* __restrict__ bcent, const float
   __syncthreads();
   if (threadIdx.x == 0) {
     pcount[B] = cnt;
-    if (cnt) atomicAdd(&stats[ST_PAIRS_KEPT], (unsigned long long)cnt);
+    if (cnt) {
+      atomicAdd(&stats[ST_PAIRS_KEPT], (unsigned long long)cnt);
+      atomicAdd(&stats[ST_KEPT_USERS], (unsigned long long)(bstart[B + 1] - bstart[B]));
+    }
   }
 }
 
@@ -191,7 +201,6 @@ __global__ void user_scan_kernel(const float* __restrict__ Ut, const float* __re
   if (npairs == 0) return;
   const int s = bstart[B], e = bstart[B + 1];
   const int cnt = e - s;
-  if (threadIdx.x == 0) atomicAdd(&stats[ST_KEPT_USERS], (unsigned long long)cnt);
   const int dp4 = dp / 4, stride4 = dp4 | 1;
   PairInfo* pinfo = reinterpret_cast<PairInfo*>(us4 + (stage ? (size_t)blockDim.x * stride4 : 0));
   if (stage) {
@@ -345,7 +354,6 @@ user_scan_reg_kernel(const float* __restrict__ Ut, const float* __restrict__ uno
   if (npairs == 0) return;
   const int s = bstart[B], e = bstart[B + 1];
   const int cnt = e - s;
-  if (threadIdx.x == 0) atomicAdd(&stats[ST_KEPT_USERS], (unsigned long long)cnt);
   const int dp4 = dp / 4;
   float4* qs = sq4;                                              // kQChunk x dp4
   PairInfo* pinfo = reinterpret_cast<PairInfo*>(qs + (size_t)kQChunk * dp4);
@@ -759,7 +767,7 @@ __global__ void bitmap_emit_kernel(const uint32_t* __restrict__ bitmap, int64_t 
 namespace {
 
 struct WsLayout {
-  size_t qd, qb, qn, kk, pairs, pcount, survcnt, bitmap, chunk, offsets, stats, total;
+  size_t qd, qb, qn, kk, pairs, pcount, kmask, tneed, survcnt, bitmap, chunk, offsets, stats, total;
 };
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -770,11 +778,13 @@ WsLayout layout_for(const Index* ix, int qb, int nchunks) {
   auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes); return r; };
   int64_t words = (ix->m + 31) / 32;
   L.qd = take(sizeof(float) * (size_t)qb * ix->dp);
-  L.qb = take(sizeof(uint16_t) * (size_t)qb * std::max(ix->dk, 1));
+  L.qb = take(2 * sizeof(uint16_t) * (size_t)qb * std::max(ix->dk, 1));   // hi and lo parts
   L.qn = take(sizeof(float) * qb);
   L.kk = take(sizeof(int32_t) * qb);
   L.pairs = take(sizeof(PairEntry) * (size_t)std::max(ix->nb, 1) * qb);
   L.pcount = take(sizeof(int32_t) * std::max(ix->nb, 1));
+  L.kmask = take(sizeof(uint32_t) * (size_t)std::max(ix->nb, 1) * ((qb + 31) / 32));
+  L.tneed = take((size_t)std::max<int64_t>((ix->m_nz + 127) / 128, 1));
   L.survcnt = take(3 * sizeof(unsigned long long));
   L.bitmap = take(sizeof(uint32_t) * (size_t)qb * words);
   L.chunk = take(sizeof(int32_t) * (size_t)qb * nchunks);
@@ -930,10 +940,14 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
       tm.end(0, 1);
       if (ix->nb > 0) {
         tm.begin(1);
+        const bool tc_pass = ix->dk > 0 && ix->prm.tc_user_pass && ix->m_nz > 0;
+        const int mask_words = (nqb + 31) / 32;
+        uint32_t* kmask = (uint32_t*)(w + L.kmask);
         block_filter_kernel<<<ix->nb, 128, sizeof(float) * ix->dp, st>>>(ix->bcent, ix->bcos, ix->bsin, ix->LB,
                                                                           ix->nb, ix->kmax, ix->n, ix->dp, Qd, qn,
                                                                           kk, nqb, ix->cone_slack, pairs, pcount,
-                                                                          stats, nullptr, 0);
+                                                                          stats, tc_pass ? kmask : nullptr,
+                                                                          mask_words, ix->bstart);
         SAH_CUDA(cudaGetLastError());
         tm.end(1, 1);
         // ---- A4: register-tiled kernel for d <= 128, the shared-memory one otherwise
@@ -942,10 +956,12 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
         const int reg_variant = dp4 <= 16 ? 16 : (dp4 <= 32 ? 32 : 0);
         tm.begin(2);
         int up_launches = 1;
-        if (ix->dk > 0 && ix->prm.tc_user_pass) {
-          SAH_TRY(run_user_pass_tc(ix, Qd, (uint16_t*)(w + L.qb), qn, kk, modes_q, nqb, pairs, pcount, bitmap, words,
-                                   surv + 2 * surv_cap, survcnt + 2, surv, survcnt, surv_cap, stats, ST_USERS_SCORED,
-                                   ST_YES_EARLY, ST_KEPT_USERS, ST_FP64, st, &up_launches));
+        if (tc_pass) {
+          up_launches = 0;
+          SAH_TRY(run_user_pass_tc(ix, Qd, (uint16_t*)(w + L.qb), qn, kk, modes_q, nqb, kmask, mask_words,
+                                   (uint8_t*)(w + L.tneed), bitmap, words, surv + 2 * surv_cap, survcnt + 2, surv,
+                                   survcnt, surv_cap, stats, ST_USERS_SCORED, ST_YES_EARLY, ST_FP64, st,
+                                   &up_launches));
         } else if (reg_variant) {
           const size_t smem = (size_t)16 * kQChunk * dp4 + sizeof(PairInfo) * kQChunk + sizeof(float) * 64 * threads;
           auto fn = reg_variant == 16 ? user_scan_reg_kernel<16> : user_scan_reg_kernel<32>;
@@ -1089,6 +1105,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
         SAH_CUDA(cudaStreamSynchronize(st));
       }
       agg.survivors += (int64_t)(ns2[0] + ns2[1]);
+      agg.pairs_rescored += (int64_t)ns2[2];
       cx->surv_hint = std::max<int64_t>(1 << 16, 2 * nsmax);
       agg.block_pairs_total += (int64_t)ix->nb * nqb;
       agg.block_pairs_kept += (int64_t)st_h[ST_PAIRS_KEPT];

@@ -104,10 +104,12 @@ struct Index {
 
   // BF16 copies for the tensor-core kMIPS decision (precision SAH_BF16), K padded to dk
   int32_t dk = 0;             // roundup(d, 64); 0 when the tensor-core path is off
-  uint16_t* Ub = nullptr;     // m_nz x dk, leaf order
+  uint16_t* Ub = nullptr;     // m_nz x dk, leaf order: bf16(u)
+  uint16_t* Ulo = nullptr;    // m_nz x dk: bf16(u - bf16(u)), the low part for the user pass
   uint16_t* Pb = nullptr;     // n x dk, descending norm order
   CUtensorMap tmap_P{};       // TMA map of Pb: box 64 x 256, 128-byte swizzle
   CUtensorMap tmap_U{};       // TMA map of Ub: box 64 x 128, 128-byte swizzle
+  CUtensorMap tmap_Ulo{};     // the same for Ulo
   int* dev_timeout = nullptr; // set by a kernel whose bounded wait ran out
 
   // SA-ALSH over the items behind P' (Alg. 1): norm partitions S_j (descending M_j), their
@@ -191,13 +193,16 @@ sah_status build_saalsh(Index* ix, const float* srp_host, cudaStream_t st);
 sah_status run_saalsh(Index* ix, const Survivor* surv, const unsigned long long* count_dev, int64_t cap,
                       const float* Qd, const float* qn, const int32_t* kk, uint32_t* bitmap, int64_t words,
                       unsigned long long* stats, int stat_items, cudaStream_t st, int* launches);
-// user_pass_tc.cu: the user pass on tcgen05 (BF16 copies present); the pairs its bound
-// leaves open go to resc and are re-scored in FP32 by a second kernel.
-sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qb, const float* qn, const int32_t* kk,
-                            const int32_t* modes, int nq, const void* pairs, const int32_t* pcount, uint32_t* bitmap,
-                            int64_t words, Survivor* resc, unsigned long long* resc_count, Survivor* surv,
-                            unsigned long long* surv_count, int64_t surv_cap, unsigned long long* stats,
-                            int st_scored, int st_yes, int st_kept, int st_fp64, cudaStream_t st, int* launches);
+// user_pass_tc.cu: the user pass on tcgen05 over every user tile and the sub-batch's
+// queries (split hi / lo BF16 operands written to Qsplit, 2 nq dk entries), for the
+// (leaf, query) pairs set in kept_mask ([nb][mask_words]); tile_need holds one byte per
+// 128-user tile.  The pairs its band leaves open go to resc and are re-scored in FP32.
+sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, const float* qn, const int32_t* kk,
+                            const int32_t* modes, int nq, const uint32_t* kept_mask, int mask_words,
+                            uint8_t* tile_need, uint32_t* bitmap, int64_t words, Survivor* resc,
+                            unsigned long long* resc_count, Survivor* surv, unsigned long long* surv_count,
+                            int64_t surv_cap, unsigned long long* stats, int st_scored, int st_yes, int st_fp64,
+                            cudaStream_t st, int* launches);
 // topk_tc.cu: the 64 largest FP32 scores of every user over all items, through tcgen05
 sah_status topk_full_tc(Index* ix, float* vlast, int32_t* ids64, cudaStream_t st, double* gemm_ms);
 // verify_tc.cu

@@ -34,6 +34,19 @@ constexpr uint32_t kTmemCols = 512;
 
 enum RowStatus : int32_t { ROW_YES = 1, ROW_NO = 2, ROW_BAND = 3, ROW_FULL = 4 };
 
+// lo = bf16(x - bf16(x)) of every row: the low half of the split operands
+__global__ void f32_to_bf16_lo_rows_kernel(const float* __restrict__ src, int64_t rows, int dp, int d, int dk,
+                                           uint16_t* __restrict__ dst) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * dk) return;
+  int64_t r = i / dk;
+  int c = (int)(i % dk);
+  float v = c < d ? src[r * dp + c] : 0.f;
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+  dst[i] = __bfloat16_as_ushort(l);
+}
+
 __global__ void f32_to_bf16_rows_kernel(const float* __restrict__ src, int64_t rows, int dp, int d, int dk,
                                         uint16_t* __restrict__ dst) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -489,10 +502,14 @@ sah_status build_bf16_copies(Index* ix, cudaStream_t st) {
   ix->dk = ix->d <= 64 ? 64 : 128;
   const int dk = ix->dk;
   SAH_TRY(dev_alloc(ix, (void**)&ix->Ub, sizeof(uint16_t) * (size_t)std::max<int64_t>(ix->m_nz, 1) * dk));
+  SAH_TRY(dev_alloc(ix, (void**)&ix->Ulo, sizeof(uint16_t) * (size_t)std::max<int64_t>(ix->m_nz, 1) * dk));
   SAH_TRY(dev_alloc(ix, (void**)&ix->Pb, sizeof(uint16_t) * (size_t)ix->n * dk));
-  if (ix->m_nz > 0)
+  if (ix->m_nz > 0) {
     f32_to_bf16_rows_kernel<<<grid_for(ix->m_nz * dk, 256), 256, 0, st>>>(ix->Ut, ix->m_nz, ix->dp, ix->d, dk,
                                                                           ix->Ub);
+    f32_to_bf16_lo_rows_kernel<<<grid_for(ix->m_nz * dk, 256), 256, 0, st>>>(ix->Ut, ix->m_nz, ix->dp, ix->d, dk,
+                                                                             ix->Ulo);
+  }
   f32_to_bf16_rows_kernel<<<grid_for(ix->n * dk, 256), 256, 0, st>>>(ix->Ps, ix->n, ix->dp, ix->d, dk, ix->Pb);
   SAH_CUDA(cudaGetLastError());
   auto encode = get_encode_fn();
@@ -519,6 +536,13 @@ sah_status build_bf16_copies(Index* ix, cudaStream_t st) {
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
       set_error("cuTensorMapEncodeTiled (users) failed with code " + std::to_string((int)r));
+      return SAH_ERR_CUDA;
+    }
+    r = encode(&ix->tmap_Ulo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ix->Ulo, udims, strides, ubox, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      set_error("cuTensorMapEncodeTiled (user low parts) failed with code " + std::to_string((int)r));
       return SAH_ERR_CUDA;
     }
   }

@@ -13,6 +13,15 @@ import workload
 pytestmark = pytest.mark.gpu
 
 
+# precision variants: FP32 on the CUDA cores; BF16 copies with the FP32 user pass; BF16
+# copies with the tensor-core user pass (split BF16 operands)
+VARIANTS = {
+    "fp32": dict(precision=0),
+    "bf16-simt": dict(precision=1, tc_user_pass=0),
+    "bf16-tc": dict(precision=1, tc_user_pass=1),
+}
+
+
 def _truth(U, P, q, ks):
     c = oracle.count_above(U, P, q)
     return {int(k): np.flatnonzero(c < k).astype(np.int32) for k in ks}
@@ -29,12 +38,12 @@ def test_c1_every_query_and_k(sah):
             assert np.array_equal(ix.rkmips(q, k), want[k]), (qi, k)
 
 
-@pytest.mark.parametrize("precision", [0, 1])               # FP32 SIMT, BF16 tensor cores
+@pytest.mark.parametrize("variant", list(VARIANTS))
 @pytest.mark.parametrize("leaf", [1, 20, 256])
 @pytest.mark.parametrize("p_prime", [10, 0, 1 << 30])      # small P', 4 k_max, all items
-def test_mf_batch_mixed_k(sah, leaf, p_prime, precision):
+def test_mf_batch_mixed_k(sah, leaf, p_prime, variant):
     W = workload.make("c2", m=6000, n=2500)
-    ix = sah.Index(W.U, W.P, k_max=50, leaf_size=leaf, p_prime=p_prime, seed=7, precision=precision)
+    ix = sah.Index(W.U, W.P, k_max=50, leaf_size=leaf, p_prime=p_prime, seed=7, **VARIANTS[variant])
     ks = [1, 5, 10, 20, 50, 64]
     qidx = W.query_idx[:8]
     Q = np.repeat(W.P[qidx], len(ks), axis=0)
@@ -48,11 +57,11 @@ def test_mf_batch_mixed_k(sah, leaf, p_prime, precision):
     assert st["queries"] == len(Q) and st["results"] == sum(len(g) for g in got)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("variant", list(VARIANTS))
 @pytest.mark.parametrize("seed", range(4))
-def test_integer_ties(sah, seed, precision):
+def test_integer_ties(sah, seed, variant):
     P, U, q = workload.tie_case(40, 300, 3, lo=-2, hi=2, seed=seed)
-    ix = sah.Index(U, P, k_max=8, leaf_size=4, p_prime=6, seed=seed, precision=precision)
+    ix = sah.Index(U, P, k_max=8, leaf_size=4, p_prime=6, seed=seed, **VARIANTS[variant])
     for qq in (q, P[seed]):                                         # q outside and inside P
         want = _truth(U, P, qq, range(1, 42))
         for k in range(1, 42):
@@ -83,16 +92,17 @@ def test_zero_query_and_foreign_query(sah):
             assert np.array_equal(ix.rkmips(q, k), want[k])
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("d", [1, 3, 50, 100, 128, 300])
-def test_dimensions(sah, d, precision):
+@pytest.mark.parametrize("variant", list(VARIANTS))
+@pytest.mark.parametrize("d", [1, 3, 50, 64, 65, 100, 128, 300])
+def test_dimensions(sah, d, variant):
     W = workload.make("c1", m=700, n=600, d=d)
-    if precision == 1 and d > 128:
+    kw = VARIANTS[variant]
+    if kw["precision"] == 1 and d > 128:
         with pytest.raises(sah.SahError) as e:
-            sah.Index(W.U, W.P, k_max=10, leaf_size=32, precision=precision)
+            sah.Index(W.U, W.P, k_max=10, leaf_size=32, **kw)
         assert e.value.status == sah.SAH_ERR_UNSUPPORTED
         return
-    ix = sah.Index(W.U, W.P, k_max=10, leaf_size=32, p_prime=12, precision=precision)
+    ix = sah.Index(W.U, W.P, k_max=10, leaf_size=32, p_prime=12, **kw)
     for qi in W.query_idx[:3]:
         q = W.P[qi]
         want = _truth(W.U, W.P, q, (1, 10, 11))
@@ -172,13 +182,13 @@ def test_empty_batch(sah):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("variant", list(VARIANTS))
 @pytest.mark.parametrize("p_prime", [0, 1 << 30])
-def test_c2_full_size_sampled(sah, p_prime, precision):
+def test_c2_full_size_sampled(sah, p_prime, variant):
     """n = 17,770, m = 480,000, d = 50 (the benchmark's workload): the answers of a fixed
     sample of users, plus every user the GPU returned, agree with the oracle."""
     W = workload.make("c2")
-    ix = sah.Index(W.U, W.P, k_max=50, leaf_size=256, p_prime=p_prime, precision=precision)
+    ix = sah.Index(W.U, W.P, k_max=50, leaf_size=256, p_prime=p_prime, **VARIANTS[variant])
     ks = [int(k) for k in W.ks]
     qidx = W.query_idx[:6]
     Q = np.repeat(W.P[qidx], len(ks), axis=0)
@@ -212,12 +222,12 @@ def test_tensor_core_path_runs_and_counts(sah):
         assert np.array_equal(got[j], np.flatnonzero(c < K[j]))
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_survivor_list_overflow_reruns(sah, precision):
+@pytest.mark.parametrize("variant", list(VARIANTS))
+def test_survivor_list_overflow_reruns(sah, variant):
     """More survivors than the list's first capacity (64k): the call grows the list, runs
     the sub-batch again and still returns the oracle's answers."""
     W = workload.make("c2", m=20000, n=800)
-    ix = sah.Index(W.U, W.P, k_max=50, leaf_size=128, p_prime=5, precision=precision)
+    ix = sah.Index(W.U, W.P, k_max=50, leaf_size=128, p_prime=5, **VARIANTS[variant])
     rng = np.random.default_rng(3)
     rows = rng.integers(0, W.n, 200)
     Q = W.P[rows]
@@ -226,17 +236,3 @@ def test_survivor_list_overflow_reruns(sah, precision):
     assert ix.stats()["survivors"] > (1 << 16)
     for r in (0, 57, 123, 199):
         assert np.array_equal(got[r], _truth(W.U, W.P, Q[r], (30,))[30]), r
-
-
-@pytest.mark.parametrize("p_prime", [10, 1 << 30])
-@pytest.mark.parametrize("d", [50, 100])
-def test_tensor_core_user_pass(sah, p_prime, d):
-    """The opt-in tcgen05 user pass (per-leaf GEMMs with the BF16 bound, FP32 re-score of
-    what it leaves open) gives the oracle's answers."""
-    W = workload.make("c2", m=6000, n=2000, d=d)
-    ix = sah.Index(W.U, W.P, k_max=50, leaf_size=256, p_prime=p_prime, precision=sah.BF16, tc_user_pass=1)
-    Q, K, _ = W.requests()
-    Q, K = Q[:40], K[:40]
-    got = ix.rkmips_batch(Q, K)
-    for j in range(len(K)):
-        assert np.array_equal(got[j], _truth(W.U, W.P, Q[j], (int(K[j]),))[int(K[j])]), j

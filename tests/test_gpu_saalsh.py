@@ -16,17 +16,17 @@ import workload
 pytestmark = pytest.mark.gpu
 
 
-def _setup(sah, probe_radius=0, K=8, bits=6, m=1200, n=900, p_prime=40, precision=0):
+def _setup(sah, probe_radius=0, K=8, bits=6, m=1200, n=900, p_prime=40, precision=0, tc_user_pass=0):
     W = workload.make("c2", m=m, n=n)
     A = workload.srp_matrix(K * bits, W.d + 1, seed=5)
     ix = sah.Index(W.U, W.P, k_max=20, leaf_size=32, p_prime=p_prime, n_tables=K, code_bits=bits,
-                   probe_radius=probe_radius, srp_matrix=A, precision=precision)
+                   probe_radius=probe_radius, srp_matrix=A, precision=precision, tc_user_pass=tc_user_pass)
     return W, A, ix
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_superset_of_exact_and_f1(sah, precision):
-    W, A, ix = _setup(sah, precision=precision)
+@pytest.mark.parametrize("precision,tc", [(0, 0), (1, 0), (1, 1)])
+def test_superset_of_exact_and_f1(sah, precision, tc):
+    W, A, ix = _setup(sah, precision=precision, tc_user_pass=tc)
     f1s = []
     for qi in W.query_idx[:6]:
         q = W.P[qi]
@@ -62,8 +62,9 @@ def test_agrees_with_oracle_alg2(sah):
     assert total == 0 or agree / total >= 0.95
 
 
-def test_mixed_modes_in_one_batch(sah):
-    W, A, ix = _setup(sah)
+@pytest.mark.parametrize("precision,tc", [(0, 0), (1, 1)])
+def test_mixed_modes_in_one_batch(sah, precision, tc):
+    W, A, ix = _setup(sah, precision=precision, tc_user_pass=tc)
     Q = np.repeat(W.P[W.query_idx[:5]], 2, axis=0)
     K = np.array([10] * 10, np.int32)
     modes = np.array([sah.EXACT, sah.SAALSH] * 5, np.int32)
