@@ -93,7 +93,7 @@ __global__ void block_filter_kernel(const float* __restrict__ bcent, const float
                                     const int32_t* __restrict__ kk, int nq, float slack,
                                     PairEntry* __restrict__ pairs, int32_t* __restrict__ pcount,
                                     unsigned long long* __restrict__ stats, uint32_t* __restrict__ kept_mask,
-                                    int mask_words, const int32_t* __restrict__ bstart) {
+                                    int mask_words, const int32_t* __restrict__ bstart, int count_pairs) {
   extern __shared__ float4 c4s[];   // the leaf's unit centre
   __shared__ int32_t cnt;
   const int B = blockIdx.x;
@@ -164,8 +164,11 @@ __global__ void block_filter_kernel(const float* __restrict__ bcent, const float
   if (threadIdx.x == 0) {
     pcount[B] = cnt;
     if (cnt) {
+      const int users = bstart[B + 1] - bstart[B];
       atomicAdd(&stats[ST_PAIRS_KEPT], (unsigned long long)cnt);
-      atomicAdd(&stats[ST_KEPT_USERS], (unsigned long long)(bstart[B + 1] - bstart[B]));
+      atomicAdd(&stats[ST_KEPT_USERS], (unsigned long long)users);
+      // the tensor-core user pass scores every (user, query) pair of the kept leaves
+      if (count_pairs) atomicAdd(&stats[ST_USERS_SCORED], (unsigned long long)cnt * users);
     }
   }
 }
@@ -767,7 +770,7 @@ __global__ void bitmap_emit_kernel(const uint32_t* __restrict__ bitmap, int64_t 
 namespace {
 
 struct WsLayout {
-  size_t qd, qb, qn, kk, pairs, pcount, kmask, tneed, survcnt, bitmap, chunk, offsets, stats, total;
+  size_t qd, qb, qn, kk, pairs, pcount, kmask, tneed, coltab, survcnt, bitmap, chunk, offsets, stats, total;
 };
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -785,6 +788,7 @@ WsLayout layout_for(const Index* ix, int qb, int nchunks) {
   L.pcount = take(sizeof(int32_t) * std::max(ix->nb, 1));
   L.kmask = take(sizeof(uint32_t) * (size_t)std::max(ix->nb, 1) * ((qb + 31) / 32));
   L.tneed = take((size_t)std::max<int64_t>((ix->m_nz + 127) / 128, 1));
+  L.coltab = take(user_pass_tc_scratch_bytes(qb));
   L.survcnt = take(3 * sizeof(unsigned long long));
   L.bitmap = take(sizeof(uint32_t) * (size_t)qb * words);
   L.chunk = take(sizeof(int32_t) * (size_t)qb * nchunks);
@@ -947,7 +951,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
                                                                           ix->nb, ix->kmax, ix->n, ix->dp, Qd, qn,
                                                                           kk, nqb, ix->cone_slack, pairs, pcount,
                                                                           stats, tc_pass ? kmask : nullptr,
-                                                                          mask_words, ix->bstart);
+                                                                          mask_words, ix->bstart, tc_pass ? 1 : 0);
         SAH_CUDA(cudaGetLastError());
         tm.end(1, 1);
         // ---- A4: register-tiled kernel for d <= 128, the shared-memory one otherwise
@@ -958,9 +962,9 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
         int up_launches = 1;
         if (tc_pass) {
           up_launches = 0;
-          SAH_TRY(run_user_pass_tc(ix, Qd, (uint16_t*)(w + L.qb), qn, kk, modes_q, nqb, kmask, mask_words,
-                                   (uint8_t*)(w + L.tneed), bitmap, words, surv + 2 * surv_cap, survcnt + 2, surv,
-                                   survcnt, surv_cap, stats, ST_USERS_SCORED, ST_YES_EARLY, ST_FP64, st,
+          SAH_TRY(run_user_pass_tc(ix, Qd, (uint16_t*)(w + L.qb), w + L.coltab, qn, kk, modes_q, nqb, kmask,
+                                   mask_words, (uint8_t*)(w + L.tneed), bitmap, words, surv + 2 * surv_cap,
+                                   survcnt + 2, surv, survcnt, surv_cap, stats, ST_YES_EARLY, ST_FP64, st,
                                    &up_launches));
         } else if (reg_variant) {
           const size_t smem = (size_t)16 * kQChunk * dp4 + sizeof(PairInfo) * kQChunk + sizeof(float) * 64 * threads;
