@@ -50,15 +50,31 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Non-blocking test of the same condition: returns at once (try_wait may suspend the
+// thread for a while when the phase is still open).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Waits for the phase with the given parity to complete.  Gives up (returns false) as
 // soon as another thread has raised *timeout or *abort, and raises *timeout itself after
-// kSpinLimit polls.
+// kSpinLimit polls.  The flags live in global memory and every waiting warp of the GPU
+// reads them, so they are read once per kFlagEvery polls only: read on every poll, they
+// made one L2 line so hot that every other access of the kernel slowed down.
+constexpr uint32_t kFlagEvery = 256;
+
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* timeout,
                                           const volatile int* abort) {
   const volatile int* tflag = timeout;
   for (uint32_t i = 0; i < kSpinLimit; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((abort && *abort) || *tflag) return false;
+    if ((i % kFlagEvery) == kFlagEvery - 1 && ((abort && *abort) || *tflag)) return false;
     if (i > 32) __nanosleep(i > 4096 ? 256 : 32);
   }
   atomicExch(timeout, 1);

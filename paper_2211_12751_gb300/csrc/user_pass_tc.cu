@@ -32,15 +32,17 @@
 // more than it saves.
 //
 // Kernel shape: one persistent launch per sub-batch, one CTA per SM, 320 threads, looping
-// over chunks of up to 256 columns.  Warp 0 streams 128-user tiles (hi and lo K-blocks)
-// through TMA, warp 1 issues the MMAs, and two groups of four epilogue warps (2-5, 6-9)
-// take alternate tiles; each group owns a TMA stage, an issuing lane in warps 0 and 1 and
-// a TMEM accumulator split in halves, so the two pipelines never wait on each other and
-// the next tile's MMA starts on a half as soon as it has been read.  An epilogue warp (one
-// user per lane) keeps its users' lower bounds for the chunk's distinct k in shared
-// memory and reads its TMEM lanes 32 columns at a time: one fused multiply-add and one
-// compare per column find the users a column can concern; only those take the per-row
-// tests.
+// over chunks of up to 256 columns.  Two groups of four epilogue warps (2-5, 6-9) take
+// alternate 128-user tiles; each group owns a TMA stage and two TMEM slots, so the two
+// pipelines never wait on each other.  One thread of warp 0 streams the tiles (hi and lo
+// K-blocks) for both groups and one thread of warp 1 issues both groups' MMAs, each in a
+// loop that polls the barriers without blocking on either group.  A chunk of up to 128
+// columns puts a group's consecutive tiles into its two slots in turn, so the next tile's
+// MMA runs while the current one is read; a wider chunk uses the two slots as halves of a
+// tile.  An epilogue warp (one user per lane) keeps its users' lower bounds for the
+// chunk's distinct k in shared memory and reads its TMEM lanes 32 columns at a time: one
+// fused multiply-add and one compare per column find the users a column can concern;
+// only those take the per-row tests.
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
@@ -58,7 +60,7 @@ constexpr int kUM = 128;             // users per tile (UMMA M)
 constexpr int kUThreads = 320;       // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr int kEpiWarps = 8;
 constexpr int kMaxTileList = 1024;   // needed tiles per CTA and launch (the host splits longer ranges)
-constexpr int kHalf = 128;           // accumulator columns per half
+constexpr int kRowsSmem = 512;       // rows of a chunk kept in shared memory (more: read from global)
 constexpr int kOpenBuf = 64;         // open pairs an epilogue warp buffers per tile
 constexpr int kMaxRows = 4096;       // rows of a sub-batch the column table takes
 
@@ -237,6 +239,7 @@ struct UpParams {
   const float* unorm;
   const float* Eu;
   const float* Lt;
+  const float* pnorm;
   const int32_t* uid;
   const int32_t* ublock;
   const uint32_t* kept_mask;   // [nb][mask_words]
@@ -271,6 +274,11 @@ __device__ __forceinline__ void tmem_ld32_wait(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// *addr |= v without a returned value (a reduction the thread does not wait for)
+__device__ __forceinline__ void red_or(uint32_t* addr, uint32_t v) {
+  asm volatile("red.global.or.b32 [%0], %1;" ::"l"(addr), "r"(v) : "memory");
+}
+
 // one FP32 column of this thread's TMEM lane, waited for
 __device__ __forceinline__ float tmem_ld1_wait(uint32_t taddr) {
   uint32_t r;
@@ -289,12 +297,15 @@ struct UpSmem {
   static constexpr uint32_t kStage = 2 * KB * kTile;       // hi and lo
   static constexpr uint32_t kBPart = NMAX * 128;           // one K-block of the columns
   static constexpr size_t kOperands = (size_t)STAGES * kStage + 2 * KB * (size_t)kBPart;
-  // + per epilogue warp: (slots + 2) x 32 lower bounds and kOpenBuf open pairs
+  // + per epilogue warp: (slots + 2) x 32 lower bounds, kOpenBuf open pairs, a 32-entry table
   static constexpr size_t bytes(int slots) {
-    return 1024 + kOperands + (size_t)kEpiWarps * (32 * 4 * ((size_t)slots + 2) + 8 * kOpenBuf);
+    return 1024 + kOperands + (size_t)kEpiWarps * (32 * 4 * ((size_t)slots + 2) + 8 * kOpenBuf + 4 * 32);
   }
-  static constexpr uint32_t kTmemCols = 2 * NMAX <= 256 ? 256 : 512;
-  static constexpr uint32_t kAccStride = kTmemCols / 2;
+  // TMEM: two slots of kSW columns per epilogue group.  A chunk of up to kSW columns puts
+  // consecutive tiles of a group into alternate slots (the next tile's MMA runs while the
+  // current one is read); a wider chunk uses both slots of a tile as its halves.
+  static constexpr int kSW = NMAX < 128 ? NMAX : 128;
+  static constexpr uint32_t kTmemCols = 4 * kSW;
 };
 
 template <int KB, int STAGES, int NMAX>
@@ -311,6 +322,10 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
   __shared__ uint32_t tmem_base_sh;
   __shared__ __align__(16) float2 cq[NMAX];         // per column: ||q||, bound-table row of its largest k
   __shared__ int2 crows[NMAX];                      // per column: first row in T.rows, row count
+  // the chunk's rows: {j | sa << 30, bound-table row offset (-1: past the cap, -2: no
+  // bound), bits of ||p_k||, k}
+  __shared__ int4 srows[kRowsSmem];
+  __shared__ int32_t wrow[NMAX / 32];               // per 32 columns: their common bound row, or -1
   __shared__ int32_t kseen[65], kslot[65], klist[64], nsl_sh;
   __shared__ int32_t tlist[kMaxTileList];           // this CTA's needed tiles, in order
   __shared__ int32_t ntl_sh, nopen_sh[kEpiWarps];
@@ -321,6 +336,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
   // +inf) and kOpenBuf open pairs
   float* Lsm = reinterpret_cast<float*>(base + S::kOperands);
   int2* Osm = reinterpret_cast<int2*>(Lsm + kEpiWarps * 32 * (p.slot_cap + 2));
+  int32_t* Ism = reinterpret_cast<int32_t*>(Osm + kEpiWarps * kOpenBuf);   // per warp: 32 entries
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) {
@@ -333,7 +349,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
         tc::mbar_init(&tfull_bar[a][h], 1);
         tc::mbar_init(&tempty_bar[a][h], 4);
       }
-    tc::mbar_init(&done_bar, 2);
+    tc::mbar_init(&done_bar, 1);
     tc::fence_mbar_init();
   }
   if (warp == 0) {
@@ -354,21 +370,23 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
   }
   const int ncol = *p.T.ncol;
   int it_base = 0;     // tiles processed by earlier chunks (all roles count the same)
-  int use[2] = {0, 0}; // uses so far of this group's accumulator halves (MMA lanes, epilogue)
+  int use0 = 0, use1 = 0;   // epilogue: uses so far of its group's two TMEM slots
+  int kt = 0;               // epilogue: tiles of its group so far
+  int mkt[2] = {0, 0}, mu[2][2] = {{0, 0}, {0, 0}};   // the MMA thread's copies, per group
   unsigned long long yes_cnt = 0;
   bool failed = false;
   for (int c0 = 0; c0 < ncol; c0 += NMAX) {
     const int nn = min(NMAX, ncol - c0);
     const int N = (nn + 15) & ~15;
-    const int H = N > kHalf ? 2 : 1;
+    const int H = N > S::kSW ? 2 : 1;   // TMEM slots per tile
     // ---- the chunk's columns: distinct k of their rows, bound-table rows, B operand
     __syncthreads();   // the previous chunk is done with every shared table
     for (int k = tid; k <= 64; k += kUThreads) kseen[k] = 0;
     __syncthreads();
     const int rb = p.T.start[c0], re = p.T.start[c0 + nn];
     for (int i = rb + tid; i < re; i += kUThreads) {
-      const int k = p.T.rows[i].y;
-      if (k >= 1 && k <= p.kmax) kseen[k] = 1;
+      const int4 rw = p.T.rows[i];
+      if (rw.y >= 1 && rw.y <= p.kmax) kseen[rw.y] = 1;
     }
     __syncthreads();
     if (tid == 0) {
@@ -383,6 +401,12 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
       nsl_sh = ns < p.slot_cap ? ns : p.slot_cap;
     }
     __syncthreads();
+    for (int i = rb + tid; i < re && i - rb < kRowsSmem; i += kUThreads) {
+      const int4 rw = p.T.rows[i];
+      const int k = rw.y;
+      const int sl = (k >= 1 && k <= p.kmax) ? kslot[k] : -1;
+      srows[i - rb] = make_int4(rw.x, sl >= 0 ? 32 * sl : (k <= p.kmax ? -1 : -2), rw.z, k);
+    }
     for (int c = tid; c < NMAX; c += kUThreads) {
       float qn = 0.f;
       int row = p.slot_cap + 1;   // past nn: the +inf row, never a candidate
@@ -393,10 +417,22 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
         qn = p.qn[p.T.rep[c0 + c]];
         // no bound row (only k > k_max rows, or past the cap): the -inf row, every user a candidate
         row = sl >= 0 ? sl : p.slot_cap;
-        cr = make_int2(p.T.start[c0 + c], p.T.start[c0 + c + 1] - p.T.start[c0 + c]);
+        cr = make_int2(p.T.start[c0 + c] - rb, p.T.start[c0 + c + 1] - p.T.start[c0 + c]);   // chunk-relative
       }
       cq[c] = make_float2(qn, __int_as_float(32 * row));
       crows[c] = cr;
+    }
+    __syncthreads();
+    if (tid < NMAX / 32) {
+      // the columns < nn of the group share one bound row: the "no" test needs one table read
+      int common = -1;
+      bool same = true;
+      for (int c = 32 * tid; c < min(nn, 32 * tid + 32); ++c) {
+        const int off = __float_as_int(cq[c].y);
+        if (common == -1) common = off;
+        same = same && off == common;
+      }
+      wrow[tid] = same ? common : -1;
     }
     for (int i = tid; i < N * KB * 8; i += kUThreads) {
       const int rr = i / (KB * 8), rem = i % (KB * 8), kb = rem / 8, ch = rem % 8;
@@ -418,42 +454,73 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
     const int ntl = ntl_sh;
 
     if (warp == 0) {
-      if (lane < 2) {   // TMA producers, lane g for the tiles of epilogue group g
-        if (lane == 0 && c0 == 0) {
+      if (lane == 0) {
+        // TMA producer for both groups: one thread that never blocks on either, so a group
+        // whose stage is still busy does not hold up the other
+        if (c0 == 0) {
           tc::prefetch_tensormap(&tmapUhi);
           tc::prefetch_tensormap(&tmapUlo);
         }
-        for (int it = it_base + ((lane - it_base) & 1); it < it_base + ntl; it += 2) {
-          const int t = tlist[it - it_base];
-          const int s = it % STAGES;
-          if (it >= STAGES && !tc::mbar_wait(&empty_bar[s], ((it / STAGES) & 1) ^ 1, p.timeout, nullptr)) break;
-          tc::mbar_arrive_expect_tx(&full_bar[s], S::kStage);
-          uint8_t* dst = sA + s * S::kStage;
-          for (int kb = 0; kb < KB; ++kb) {
-            tc::tma_load_2d(dst + kb * S::kTile, &tmapUhi, &full_bar[s], kb * 64, t * kUM);
-            tc::tma_load_2d(dst + (KB + kb) * S::kTile, &tmapUlo, &full_bar[s], kb * 64, t * kUM);
+        const int end = it_base + ntl;
+        int nx[2] = {it_base + ((0 - it_base) & 1), it_base + ((1 - it_base) & 1)};
+        uint32_t idle = 0;
+        for (;;) {
+          bool any_left = false, progressed = false;
+#pragma unroll
+          for (int g = 0; g < 2; ++g) {
+            if (nx[g] >= end) continue;
+            any_left = true;
+            const int s = nx[g] % STAGES;
+            if (nx[g] >= STAGES && !tc::mbar_test_wait(&empty_bar[s], ((nx[g] / STAGES) & 1) ^ 1)) continue;
+            const int t = tlist[nx[g] - it_base];
+            tc::mbar_arrive_expect_tx(&full_bar[s], S::kStage);
+            uint8_t* dst = sA + s * S::kStage;
+            for (int kb = 0; kb < KB; ++kb) {
+              tc::tma_load_2d(dst + kb * S::kTile, &tmapUhi, &full_bar[s], kb * 64, t * kUM);
+              tc::tma_load_2d(dst + (KB + kb) * S::kTile, &tmapUlo, &full_bar[s], kb * 64, t * kUM);
+            }
+            nx[g] += 2;
+            progressed = true;
           }
+          if (!any_left) break;
+          if (progressed) {
+            idle = 0;
+            continue;
+          }
+          if (++idle % tc::kFlagEvery == 0 && *(volatile int*)p.timeout) break;
+          if (idle > tc::kSpinLimit) {
+            atomicExch(p.timeout, 1);
+            break;
+          }
+          if (idle > 32) __nanosleep(32);
         }
       }
     } else if (warp == 1) {
-      if (lane < 2) {   // MMA issuers, lane g: hi.hi + hi.lo + lo.hi into accumulator g, by halves
+      if (lane == 0) {
+        // MMA issuer for both groups (hi.hi + hi.lo + lo.hi into group g's TMEM slots), one
+        // thread that never blocks on either group
         const uint32_t a0 = tc::smem_addr(sA), b0 = tc::smem_addr(sB);
-        bool ok = true;
-        for (int it = it_base + ((lane - it_base) & 1); ok && it < it_base + ntl; it += 2) {
-          const int s = it % STAGES, a = it & 1;
-          if (!tc::mbar_wait(&full_bar[s], (it / STAGES) & 1, p.timeout, nullptr)) break;
-          const uint32_t aS = a0 + s * S::kStage;
-          for (int h = 0; h < H; ++h) {
-            const int u = use[h]++;
-            if (u >= 1 && !tc::mbar_wait(&tempty_bar[a][h], (u & 1) ^ 1, p.timeout, nullptr)) {
-              ok = false;
-              break;
-            }
+        const int end = it_base + ntl;
+        int nx[2] = {it_base + ((0 - it_base) & 1), it_base + ((1 - it_base) & 1)};
+        int hh[2] = {0, 0};
+        uint32_t idle = 0;
+        for (;;) {
+          bool any_left = false, progressed = false;
+#pragma unroll
+          for (int g = 0; g < 2; ++g) {
+            if (nx[g] >= end) continue;
+            any_left = true;
+            const int s = nx[g] % STAGES;
+            if (hh[g] == 0 && !tc::mbar_test_wait(&full_bar[s], (nx[g] / STAGES) & 1)) continue;
+            const int sl = H == 2 ? hh[g] : (mkt[g] & 1);
+            const int u = mu[g][sl];
+            if (u >= 1 && !tc::mbar_test_wait(&tempty_bar[g][sl], (u & 1) ^ 1)) continue;
             tc::tc_fence_after();
-            const int nh = h == 0 ? (N < kHalf ? N : kHalf) : N - kHalf;
+            const int nh = hh[g] == 0 ? (N < S::kSW ? N : S::kSW) : N - S::kSW;
             const uint32_t idesc = tc::idesc_bf16_f32(kUM, (uint32_t)nh);
-            const uint32_t d = tbase + a * S::kAccStride + h * kHalf;
-            const uint32_t bh = b0 + h * kHalf * 128;   // rows 128 h.. of each B part
+            const uint32_t d = tbase + (2 * g + sl) * S::kSW;
+            const uint32_t bh = b0 + hh[g] * S::kSW * 128;   // rows kSW hh.. of each B part
+            const uint32_t aS = a0 + s * S::kStage;
             uint32_t acc = 0;
 #pragma unroll
             for (int prod = 0; prod < 3; ++prod) {
@@ -469,9 +536,27 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
                   acc = 1;
                 }
             }
-            tc::umma_commit(&tfull_bar[a][h]);
+            tc::umma_commit(&tfull_bar[g][sl]);
+            ++mu[g][sl];
+            if (++hh[g] == H) {
+              tc::umma_commit(&empty_bar[s]);
+              hh[g] = 0;
+              ++mkt[g];
+              nx[g] += 2;
+            }
+            progressed = true;
           }
-          if (ok) tc::umma_commit(&empty_bar[s]);
+          if (!any_left) break;
+          if (progressed) {
+            idle = 0;
+            continue;
+          }
+          if (++idle % tc::kFlagEvery == 0 && *(volatile int*)p.timeout) break;
+          if (idle > tc::kSpinLimit) {
+            atomicExch(p.timeout, 1);
+            break;
+          }
+          if (idle > 32) __nanosleep(32);
         }
       }
     } else {
@@ -482,6 +567,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
       const int inf_row = 32 * p.slot_cap;
       float* Lw = Lsm + ew * 32 * (p.slot_cap + 2);
       int2* Ob = Osm + ew * kOpenBuf;
+      int32_t* Inv = Ism + ew * 32;
       Lw[inf_row + lane] = -INFINITY;
       Lw[inf_row + 32 + lane] = INFINITY;
       const int nsl = nsl_sh;
@@ -491,6 +577,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
       int Bu_n = 0, id_n = 0;
       float nu_n = 0.f, E_n = 0.f;
       float L_n[kPre];
+      uint32_t kw0_n = 0;   // word `lane` of the kept bits of the warp's first leaf
       auto load_user = [&](int li) {
         Bu_n = 0;
         id_n = 0;
@@ -537,15 +624,24 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
           if ((int64_t)gs < p.resc_cap) p.resc[gs] = Survivor{upos, jv, 0.f};
         }
       };
+      // the kept words of the first leaf of the warp's users in the next tile
+      auto load_words = [&](int li) {
+        const int b0 = __shfl_sync(0xffffffffu, Bu_n, 0);
+        kw0_n = 0u;
+        if (li < ntl && lane < p.mask_words) kw0_n = __ldg(&p.kept_mask[(int64_t)b0 * p.mask_words + lane]);
+      };
       if (lane == 0) nopen_sh[ew] = 0;
       __syncwarp();
       const int first = ((g - it_base) & 1);   // local index of the group's first tile
       load_user(first);
+      load_words(first);
       for (int li = first; li < ntl; li += 2) {
         const int a = g;
         const int64_t r = (int64_t)tlist[li] * kUM + quad * 32 + lane;
         const bool valid = r < p.mz;
         const int Bu = Bu_n;
+        const int B0 = __shfl_sync(0xffffffffu, Bu, 0);
+        const uint32_t kw0 = kw0_n;
         const int32_t id = id_n;
         const float nu = nu_n, E = E_n;
         const float cu = __fmul_ru(p.ctc, nu);
@@ -560,10 +656,12 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
           Lw[32 * sl + lane] = Llo;
         }
         __syncwarp();
-        const uint32_t acc_addr = tbase + lane_addr + a * S::kAccStride;
         for (int h = 0; h < H; ++h) {
-          const int u = use[h]++;
-          if (!tc::mbar_wait(&tfull_bar[a][h], u & 1, p.timeout, nullptr)) {
+          const int sl = H == 2 ? h : (kt & 1);
+          const int u = sl ? use1++ : use0++;
+          // TMEM address of column 0 of this chunk, as seen from this half's slot
+          const uint32_t acc_addr = tbase + lane_addr + (2 * a + sl) * S::kSW - h * S::kSW;
+          if (!tc::mbar_wait(&tfull_bar[a][sl], u & 1, p.timeout, nullptr)) {
             failed = true;
             break;
           }
@@ -572,19 +670,36 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
             emit_prev();
             load_user(li + 2);
           }
-          const int wend = h + 1 < H ? 4 * (h + 1) : wc;
-          for (int w = 4 * h; w < wend; ++w) {
+          const int wend = h + 1 < H ? (S::kSW / 32) * (h + 1) : wc;
+          for (int w = (S::kSW / 32) * h; w < wend; ++w) {
             float v[32];
             tmem_ld32_wait(acc_addr + 32 * w, v);
             // "no" unless s + c_tc ||u|| ||q|| (rounded up) reaches the column's lowest L - E
-            bool any = false;
+            bool any0 = false, any1 = false, any2 = false, any3 = false;
+            const int wr = wrow[w];
+            if (wr >= 0) {
+              const float Lg = Lw[wr + lane];
 #pragma unroll
-            for (int i = 0; i < 32; i += 2) {
-              const float4 c4 = *reinterpret_cast<const float4*>(&cq[32 * w + i]);
-              any |= __fmaf_ru(cu, c4.x, v[i]) >= Lw[__float_as_int(c4.y) + lane];
-              any |= __fmaf_ru(cu, c4.z, v[i + 1]) >= Lw[__float_as_int(c4.w) + lane];
+              for (int i = 0; i < 32; i += 4) {
+                const float4 ca = *reinterpret_cast<const float4*>(&cq[32 * w + i]);
+                const float4 cb = *reinterpret_cast<const float4*>(&cq[32 * w + i + 2]);
+                any0 |= __fmaf_ru(cu, ca.x, v[i]) >= Lg;
+                any1 |= __fmaf_ru(cu, ca.z, v[i + 1]) >= Lg;
+                any2 |= __fmaf_ru(cu, cb.x, v[i + 2]) >= Lg;
+                any3 |= __fmaf_ru(cu, cb.z, v[i + 3]) >= Lg;
+              }
+            } else {
+#pragma unroll
+            for (int i = 0; i < 32; i += 4) {
+              const float4 ca = *reinterpret_cast<const float4*>(&cq[32 * w + i]);
+              const float4 cb = *reinterpret_cast<const float4*>(&cq[32 * w + i + 2]);
+              any0 |= __fmaf_ru(cu, ca.x, v[i]) >= Lw[__float_as_int(ca.y) + lane];
+              any1 |= __fmaf_ru(cu, ca.z, v[i + 1]) >= Lw[__float_as_int(ca.w) + lane];
+              any2 |= __fmaf_ru(cu, cb.x, v[i + 2]) >= Lw[__float_as_int(cb.y) + lane];
+              any3 |= __fmaf_ru(cu, cb.z, v[i + 3]) >= Lw[__float_as_int(cb.w) + lane];
             }
-            if (!__any_sync(0xffffffffu, any)) continue;
+            }
+            if (!__any_sync(0xffffffffu, (any0 || any1) || (any2 || any3))) continue;
             uint32_t cand = 0;
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
@@ -601,46 +716,76 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
               const int i = __ffs(uni) - 1;
               uni &= uni - 1;
               const float sv = tmem_ld1_wait(acc_addr + 32 * w + i);
-              if (!valid || !((cand >> i) & 1u)) continue;
+              const bool is_c = valid && ((cand >> i) & 1u);
+              const unsigned cm = __ballot_sync(0xffffffffu, is_c);
+              // candidate rank -> lane, through this warp's 32-entry table
+              __syncwarp();
+              if (is_c) Inv[__popc(cm & ((1u << lane) - 1u))] = lane;
+              __syncwarp();
               const int2 cr = crows[32 * w + i];
               const float qn = cq[32 * w + i].x;
-              const float e = __fmul_ru(cu, qn) + 1e-30f;
-              const float lo = __fsub_rd(sv, e);
-              const float hi_s = __fmaf_ru(cu, qn, sv);
-              for (int q = 0; q < cr.y; ++q) {
-                const int4 rw = p.T.rows[cr.x + q];
-                const int j = rw.x & 0x3fffffff, k = rw.y;
-                if (!((__ldg(&p.kept_mask[(int64_t)Bu * p.mask_words + (j >> 5)]) >> (j & 31)) & 1u)) continue;
-                const int sl = k <= p.kmax ? kslot[k] : -1;
-                float Lq = -INFINITY;   // L - E - 1e-30 rounded down, or -inf without a bound
-                if (sl >= 0) {
-                  Lq = Lw[32 * sl + lane];
-                } else if (k <= p.kmax) {   // past the table's cap
-                  Lq = __fsub_rd(__fsub_rd(__ldg(&p.Lt[(int64_t)(k - 1) * p.mz + r]), E), 1e-30f);
+              // every (candidate user, row) pair of the column on its own lane
+              const int P = __popc(cm) * cr.y;
+              for (int pb = 0; pb < P; pb += 32) {
+                const int pp = pb + lane;
+                const bool act = pp < P;
+                const int ci = act ? pp / cr.y : 0, q = act ? pp % cr.y : 0;
+                const int src = act ? Inv[ci] : lane;
+                const float s_ = __shfl_sync(0xffffffffu, sv, src);
+                const float cu_ = __shfl_sync(0xffffffffu, cu, src);
+                const float nun_ = __shfl_sync(0xffffffffu, nun, src);
+                const float E_ = __shfl_sync(0xffffffffu, E, src);
+                const int Bu_ = __shfl_sync(0xffffffffu, Bu, src);
+                const int id_ = __shfl_sync(0xffffffffu, id, src);
+                const int r_ = __shfl_sync(0xffffffffu, (int)r, src);
+                int4 rw = make_int4(0, -2, 0, 0);
+                if (act) {
+                  if (cr.x + q < kRowsSmem) {
+                    rw = srows[cr.x + q];
+                  } else {
+                    rw = p.T.rows[rb + cr.x + q];
+                    const int sl3 = (rw.y >= 1 && rw.y <= p.kmax) ? kslot[rw.y] : -1;
+                    rw = make_int4(rw.x, sl3 >= 0 ? 32 * sl3 : (rw.y <= p.kmax ? -1 : -2), rw.z, rw.y);
+                  }
                 }
-                if (hi_s < Lq) continue;   // "no"
-                bool yes = lo >= __fmul_ru(nun, __int_as_float(rw.z));
+                const int j = rw.x & 0x3fffffff, k = rw.w;
+                // the kept bit: from the words of leaf B0 spread over the lanes, else memory
+                uint32_t kwv = __shfl_sync(0xffffffffu, kw0, (j >> 5) & 31);
+                if (!act) continue;
+                if (Bu_ != B0 || (j >> 5) >= 32) kwv = __ldg(&p.kept_mask[(int64_t)Bu_ * p.mask_words + (j >> 5)]);
+                if (!((kwv >> (j & 31)) & 1u)) continue;
+                float Lq = -INFINITY;   // L - E - 1e-30 rounded down, or -inf without a bound
+                if (rw.y >= 0) {
+                  Lq = Lw[rw.y + src];
+                } else if (rw.y == -1) {   // past the table's cap
+                  Lq = __fsub_rd(__fsub_rd(__ldg(&p.Lt[(int64_t)(k - 1) * p.mz + r_]), E_), 1e-30f);
+                }
+                if (__fmaf_ru(cu_, qn, s_) < Lq) continue;   // "no"
+                const float lo = __fsub_rd(s_, __fmul_ru(cu_, qn) + 1e-30f);
+                bool yes = lo >= __fmul_ru(nun_, __int_as_float(rw.z));
                 if (!yes && p.l_exact && k <= p.kmax && Lq != -INFINITY)
-                  yes = lo >= __fadd_ru(__fadd_ru(Lq, 2.f * E), __fmaf_ru(fabsf(Lq), 0x1p-21f, 2e-30f));
+                  yes = lo >= __fadd_ru(__fadd_ru(Lq, 2.f * E_), __fmaf_ru(fabsf(Lq), 0x1p-21f, 2e-30f));
                 if (yes) {
                   ++yes_cnt;
-                  atomicOr(&p.bitmap[(int64_t)j * p.words + (id >> 5)], 1u << (id & 31));
+                  red_or(&p.bitmap[(int64_t)j * p.words + (id_ >> 5)], 1u << (id_ & 31));
                 } else {
-                  push_open((int32_t)r, rw.x);
+                  push_open((int32_t)r_, rw.x);
                 }
               }
             }
           }
           tc::tc_fence_before();
           __syncwarp();
-          if (lane == 0) tc::mbar_arrive(&tempty_bar[a][h]);
+          if (lane == 0) tc::mbar_arrive(&tempty_bar[a][sl]);
         }
+        ++kt;
         if (failed) break;
         // claim the re-score slots of this tile's open pairs (written after the next wait)
         __syncwarp();
         const int no = min(nopen_sh[ew], kOpenBuf);
         prev_n = no;
         if (no && lane == 0) prev_base = atomicAdd(p.resc_count, (unsigned long long)no);
+        load_words(li + 2);
       }
       if (!failed) emit_prev();
     }
@@ -655,7 +800,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
     for (int o = 16; o > 0; o >>= 1) yes_cnt += __shfl_xor_sync(0xffffffffu, yes_cnt, o);
     if (lane == 0 && yes_cnt) atomicAdd(&p.stats[p.st_yes], yes_cnt);
   }
-  if (warp == 1 && lane < 2) tc::umma_commit(&done_bar);
+  if (warp == 1 && lane == 0) tc::umma_commit(&done_bar);
   tc::tc_fence_before();
   __syncthreads();
   if (warp == 0) {
@@ -767,7 +912,18 @@ template <int KB, int STAGES, int NMAX>
 sah_status launch_pass(Index* ix, UpParams p, int sms, cudaStream_t st, int* launches) {
   using S = UpSmem<KB, STAGES, NMAX>;
   auto fn = user_pass_tc_kernel<KB, STAGES, NMAX>;
-  p.slot_cap = std::min(ix->kmax, KB == 1 ? 64 : 48);   // what shared memory holds
+  // lower-bound rows per warp: what shared memory holds beside the operands
+  int optin = 0;
+  SAH_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ix->device));
+  cudaFuncAttributes fa{};
+  SAH_CUDA(cudaFuncGetAttributes(&fa, fn));
+  const int64_t spare = (int64_t)optin - (int64_t)fa.sharedSizeBytes - (int64_t)S::bytes(0);
+  const int rows = (int)std::max<int64_t>(0, spare / (kEpiWarps * 32 * 4));
+  p.slot_cap = std::min({ix->kmax, 64, rows});
+  if (p.slot_cap < 1) {
+    set_error("tensor-core user pass: no shared memory left for the lower bounds");
+    return SAH_ERR_UNSUPPORTED;
+  }
   const size_t smem = S::bytes(p.slot_cap);
   SAH_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const unsigned grid = (unsigned)std::max(1, std::min(p.ntiles, sms));
@@ -827,6 +983,7 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
   p.unorm = ix->unorm;
   p.Eu = ix->Eu;
   p.Lt = ix->Lt;
+  p.pnorm = ix->pnorm;
   p.uid = ix->uid;
   p.ublock = ix->ublock;
   p.kept_mask = kept_mask;
@@ -848,7 +1005,7 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
   if (ix->dk == 64) {
-    SAH_TRY((launch_pass<1, 2, 256>(ix, p, sms, st, launches)));
+    SAH_TRY((launch_pass<1, 4, 128>(ix, p, sms, st, launches)));
   } else {
     SAH_TRY((launch_pass<2, 2, 64>(ix, p, sms, st, launches)));
   }

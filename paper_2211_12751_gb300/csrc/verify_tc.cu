@@ -237,7 +237,7 @@ verify_tc_kernel(const __grid_constant__ CUtensorMap tmapP, TcParams prm) {
             finished = true;
             break;
           }
-          if (*(volatile int*)prm.timeout) break;
+          if (i % tc::kFlagEvery == tc::kFlagEvery - 1 && *(volatile int*)prm.timeout) break;
           if (i > 32) __nanosleep(64);
         }
         if (!got) {
