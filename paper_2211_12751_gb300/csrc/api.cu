@@ -144,6 +144,7 @@ sah_status sah_build_index(const float* U, int64_t m, const float* P, int64_t n,
   }
   sah_index* h = new sah_index();
   Index* ix = &h->impl;
+  ix->main_ctx.graphs_allowed = true;   // the blocking calls replay repeated shapes as CUDA graphs
   cudaGetDevice(&ix->device);
   ix->n = n;
   ix->m = m;

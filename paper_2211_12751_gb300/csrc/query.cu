@@ -628,20 +628,6 @@ __global__ void zero_users_kernel(const int32_t* __restrict__ zid, int64_t nz, i
   atomicOr(&bitmap[(int64_t)j * words + (id >> 5)], 1u << (id & 31));
 }
 
-// Queries with k > n: every user answers "yes".
-__global__ void all_users_kernel(const int32_t* __restrict__ kk, int nq, int64_t n, int64_t m,
-                                 uint32_t* __restrict__ bitmap, int64_t words) {
-  int j = blockIdx.y;
-  if (kk[j] <= n) return;
-  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words;
-       w += (int64_t)gridDim.x * blockDim.x) {
-    int64_t lo = w * 32;
-    uint32_t v = 0xffffffffu;
-    if (lo + 32 > m) v = (m - lo) >= 32 ? 0xffffffffu : ((1u << (m - lo)) - 1u);
-    bitmap[(int64_t)j * words + w] = v;
-  }
-}
-
 __device__ inline int block_exclusive_scan(int v, int* total) {
   __shared__ int wsum[32];
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -664,14 +650,28 @@ __device__ inline int block_exclusive_scan(int v, int* total) {
 }
 
 // chunk_cnt[j][c] = answers of query j among the users of chunk c.
-__global__ void bitmap_count_kernel(const uint32_t* __restrict__ bitmap, int64_t words, int nchunks,
-                                    int32_t* __restrict__ chunk_cnt) {
+// Set bits per (chunk, query).  A query with k > n asks for every user: its chunk of the
+// bitmap is filled here.
+__global__ void bitmap_count_kernel(uint32_t* __restrict__ bitmap, int64_t words, int nchunks,
+                                    int32_t* __restrict__ chunk_cnt, const int32_t* __restrict__ kk, int64_t n,
+                                    int64_t m) {
   int c = blockIdx.x, j = blockIdx.y;
   int64_t w0 = (int64_t)c * kWordsPerChunk;
+  const bool all = kk[j] > n;
   int acc = 0;
   for (int w = threadIdx.x; w < kWordsPerChunk; w += blockDim.x) {
     int64_t ww = w0 + w;
-    if (ww < words) acc += __popc(bitmap[(int64_t)j * words + ww]);
+    if (ww < words) {
+      uint32_t v;
+      if (all) {
+        const int64_t lo = ww * 32;
+        v = (m - lo) >= 32 ? 0xffffffffu : ((1u << (m - lo)) - 1u);
+        bitmap[(int64_t)j * words + ww] = v;
+      } else {
+        v = bitmap[(int64_t)j * words + ww];
+      }
+      acc += __popc(v);
+    }
   }
   acc += __shfl_xor_sync(0xffffffffu, acc, 16);
   acc += __shfl_xor_sync(0xffffffffu, acc, 8);
@@ -822,6 +822,57 @@ sah_status ensure_surv(CallCtx* cx, int64_t cap, cudaStream_t st) {
   return ensure_buf(&cx->surv, 3 * sizeof(Survivor) * (size_t)std::max<int64_t>(cap, 1), st);
 }
 
+// Runs a sub-batch's launch sequence (enqueue) for the given key of shapes and buffers: the
+// first time directly, the second time captured into a CUDA graph, which later calls with
+// the same key replay as one launch.  A capture that fails (an operation that cannot be
+// captured) marks the key, which then always runs directly.
+template <class F>
+sah_status run_captured(CallCtx* cx, const std::vector<uint64_t>& key, F&& enqueue, cudaStream_t st) {
+  constexpr size_t kMaxGraphs = 8;
+  GraphEntry* e = nullptr;
+  for (GraphEntry& g : cx->graphs)
+    if (g.key == key) e = &g;
+  ++cx->graph_clock;
+  if (!e) {
+    if (cx->graphs.size() >= kMaxGraphs) {
+      // the least recently used entry makes room
+      size_t lru = 0;
+      for (size_t i = 1; i < cx->graphs.size(); ++i)
+        if (cx->graphs[i].last_use < cx->graphs[lru].last_use) lru = i;
+      if (cx->graphs[lru].exec) cudaGraphExecDestroy(cx->graphs[lru].exec);
+      cx->graphs.erase(cx->graphs.begin() + (std::ptrdiff_t)lru);
+    }
+    GraphEntry g;
+    g.key = key;
+    g.last_use = cx->graph_clock;
+    cx->graphs.push_back(g);
+    return enqueue();   // first sighting: direct (it also sizes every workspace)
+  }
+  e->last_use = cx->graph_clock;
+  if (e->bad) return enqueue();
+  if (!e->exec) {
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      cudaGetLastError();
+      e->bad = true;
+      return enqueue();
+    }
+    const sah_status s = enqueue();
+    const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    cudaError_t ie = cudaErrorUnknown;
+    if (s == SAH_OK && ce == cudaSuccess && graph) ie = cudaGraphInstantiate(&e->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (s != SAH_OK || ce != cudaSuccess || ie != cudaSuccess) {
+      cudaGetLastError();
+      e->exec = nullptr;
+      e->bad = true;
+      return enqueue();
+    }
+  }
+  SAH_CUDA(cudaGraphLaunch(e->exec, st));
+  return SAH_OK;
+}
+
 // CUDA events around each stage, on the call's stream (only when timing is enabled).
 struct StageTimer {
   static constexpr int kStages = 8;
@@ -874,11 +925,17 @@ struct StageTimer {
 // index's internal result buffer first, so the caller's buffer is only written once the
 // total is known to fit.
 void free_ctx(CallCtx* cx) {
+  for (GraphEntry& g : cx->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  cx->graphs.clear();
   for (Workspace* w : {&cx->ws, &cx->surv, &cx->res, &cx->tcws}) {
     if (w->base) cudaFree(w->base);
     w->base = nullptr;
     w->bytes = 0;
   }
+  if (cx->pin) cudaFreeHost(cx->pin);
+  cx->pin = nullptr;
+  cx->pin_bytes = 0;
 }
 
 size_t ctx_bytes(const CallCtx* cx) { return cx->ws.bytes + cx->surv.bytes + cx->res.bytes + cx->tcws.bytes; }
@@ -933,133 +990,157 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
       unsigned long long* stats = (unsigned long long*)(w + L.stats);
       Survivor* surv = (Survivor*)cx->surv.base;
 
-      tm.begin(0);
-      SAH_CUDA(cudaMemsetAsync(stats, 0, sizeof(unsigned long long) * ST_COUNT, st));
-      SAH_CUDA(cudaMemsetAsync(survcnt, 0, 3 * sizeof(unsigned long long), st));
-      SAH_CUDA(cudaMemsetAsync(bitmap, 0, sizeof(uint32_t) * (size_t)nqb * words, st));
-      SAH_CUDA(cudaMemcpyAsync(kk, ks_dev + q0, sizeof(int32_t) * nqb, cudaMemcpyDeviceToDevice, st));
-      prep_queries_kernel<<<grid_for(nqb, 8), 256, 0, st>>>(Q_dev + (int64_t)q0 * ix->d, nqb, ix->d, ix->dp, Qd, qn,
-                                                             kk, modes_q, stats);
-      SAH_CUDA(cudaGetLastError());
-      tm.end(0, 1);
-      if (ix->nb > 0) {
-        tm.begin(1);
-        const bool tc_pass = ix->dk > 0 && ix->prm.tc_user_pass && ix->m_nz > 0;
-        const int mask_words = (nqb + 31) / 32;
-        uint32_t* kmask = (uint32_t*)(w + L.kmask);
-        block_filter_kernel<<<ix->nb, 128, sizeof(float) * ix->dp, st>>>(ix->bcent, ix->bcos, ix->bsin, ix->LB,
-                                                                          ix->nb, ix->kmax, ix->n, ix->dp, Qd, qn,
-                                                                          kk, nqb, ix->cone_slack, pairs, pcount,
-                                                                          stats, tc_pass ? kmask : nullptr,
-                                                                          mask_words, ix->bstart, tc_pass ? 1 : 0);
-        SAH_CUDA(cudaGetLastError());
-        tm.end(1, 1);
-        // ---- A4: register-tiled kernel for d <= 128, the shared-memory one otherwise
-        const int threads = std::max(32, ((ix->prm.leaf_size + 31) / 32) * 32);
-        const int dp4 = ix->dp / 4;
-        const int reg_variant = dp4 <= 16 ? 16 : (dp4 <= 32 ? 32 : 0);
-        tm.begin(2);
-        int up_launches = 1;
-        if (tc_pass) {
-          up_launches = 0;
-          SAH_TRY(run_user_pass_tc(ix, Qd, (uint16_t*)(w + L.qb), w + L.coltab, qn, kk, modes_q, nqb, kmask,
-                                   mask_words, (uint8_t*)(w + L.tneed), bitmap, words, surv + 2 * surv_cap,
-                                   survcnt + 2, surv, survcnt, surv_cap, stats, ST_YES_EARLY, ST_FP64, st,
-                                   &up_launches));
-        } else if (reg_variant) {
-          const size_t smem = (size_t)16 * kQChunk * dp4 + sizeof(PairInfo) * kQChunk + sizeof(float) * 64 * threads;
-          auto fn = reg_variant == 16 ? user_scan_reg_kernel<16> : user_scan_reg_kernel<32>;
-          if (smem > 48 * 1024)
-            SAH_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-          fn<<<ix->nb, threads, smem, st>>>(
-              ix->Ut, ix->unorm, ix->ucos, ix->usin, ix->uid, ix->bstart, ix->Lt, ix->Eu, ix->pnorm, ix->n,
-              ix->m_nz, ix->kmax, ix->l_exact ? 1 : 0, ix->dp, Qd, qn, kk, nqb, pairs, pcount, ix->gamma,
-              ix->cone_slack, bitmap, words, surv, survcnt, surv_cap, stats, modes_q, ix->T64, ix->d);
-        } else {
-          size_t smem = (size_t)16 * threads * ((ix->dp / 4) | 1);
-          const int stage = smem <= 160 * 1024 ? 1 : 0;
-          if (!stage) smem = 0;
-          smem += sizeof(PairInfo) * kPairChunk;
-          if (smem > 48 * 1024)
-            SAH_CUDA(cudaFuncSetAttribute(user_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-          user_scan_kernel<<<ix->nb, threads, smem, st>>>(
-              ix->Ut, ix->unorm, ix->ucos, ix->usin, ix->uid, ix->bstart, ix->Lt, ix->Eu, ix->pnorm, ix->n,
-              ix->m_nz, ix->kmax, ix->l_exact ? 1 : 0, ix->dp, Qd, qn, kk, nqb, pairs, pcount, ix->gamma,
-              ix->cone_slack, bitmap, words, surv, survcnt, surv_cap, stats, stage, modes_q, ix->T64, ix->d);
-        }
-        SAH_CUDA(cudaGetLastError());
-        tm.end(2, up_launches);
-        // ---- A5/A6 on the survivors (their number stays on the device)
-        tm.begin(3);
-        int nl = 0;
-        if (ix->dk > 0) {
-          SAH_TRY(run_verify_tc(ix, cx, surv, survcnt, surv_cap, Qd, qn, kk, bitmap, words, stats, ST_FP64, ST_ITEMS,
-                                st, &nl));
-        } else {
-          const size_t vsmem = (size_t)16 * kVerifyWarps * (ix->dp / 4);
-          if (vsmem > 48 * 1024)
-            SAH_CUDA(cudaFuncSetAttribute(verify_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)vsmem));
-          verify_exact_kernel<<<sms * 8, kVerifyWarps * 32, vsmem, st>>>(
-              surv, survcnt, surv_cap, ix->Ut, ix->unorm, ix->uid, ix->Ps, ix->pnorm, ix->n, ix->d, ix->dp, Qd, qn,
-              kk, ix->gamma, bitmap, words, stats);
-          SAH_CUDA(cudaGetLastError());
-          nl = 1;
-        }
-        tm.end(3, nl);
-        if (modes_q) {
-          int nsa = 0;
-          tm.begin(5);
-          SAH_TRY(run_saalsh(ix, surv + surv_cap, survcnt + 1, surv_cap, Qd, qn, kk, bitmap, words, stats, ST_ITEMS,
-                             st, &nsa));
-          tm.end(5, nsa);
-        }
+      // the pinned host block the results are read back into
+      const size_t pin_need = sizeof(int64_t) * (size_t)(nqb + 1) + sizeof(unsigned long long) * (ST_COUNT + 3) + 16;
+      if (cx->pin_bytes < pin_need) {
+        SAH_CUDA(cudaStreamSynchronize(st));
+        if (cx->pin) cudaFreeHost(cx->pin);
+        cx->pin = nullptr;
+        cx->pin_bytes = 0;
+        SAH_CUDA(cudaMallocHost(&cx->pin, pin_need));
+        cx->pin_bytes = pin_need;
       }
-      tm.begin(4);
-      int n_compact = 4;
-      if (ix->nzero > 0) {
-        zero_users_kernel<<<grid_for(ix->nzero * nqb, 256), 256, 0, st>>>(ix->zero_uid, ix->nzero, nqb, bitmap,
-                                                                           words);
-        ++n_compact;
-      }
-      {
-        dim3 g((unsigned)std::min<int64_t>(grid_for(words, 256), 1024), nqb);
-        all_users_kernel<<<g, 256, 0, st>>>(kk, nqb, ix->n, ix->m, bitmap, words);
-      }
+      int64_t* ob = (int64_t*)cx->pin;
+      unsigned long long* st_h = (unsigned long long*)(ob + nqb + 1);
+      unsigned long long* ns2 = st_h + ST_COUNT;
+      int* timeout_h = (int*)(ns2 + 3);
       const dim3 gc(nchunks, nqb);
-      bitmap_count_kernel<<<gc, 256, 0, st>>>(bitmap, words, nchunks, chunk);
-      offsets_kernel<<<1, 1024, 0, st>>>(chunk, nchunks, nqb, direct ? 0 : res_total, offsets);
-      int32_t* dst;
-      int64_t dst_cap;
-      if (direct) {
-        dst = out_dev;
-        dst_cap = out_cap;
+      // every device operation of the attempt, the readback of its results included
+      auto enqueue = [&]() -> sah_status {
+        tm.begin(0);
+        SAH_CUDA(cudaMemsetAsync(stats, 0, sizeof(unsigned long long) * ST_COUNT, st));
+        SAH_CUDA(cudaMemsetAsync(survcnt, 0, 3 * sizeof(unsigned long long), st));
+        SAH_CUDA(cudaMemsetAsync(bitmap, 0, sizeof(uint32_t) * (size_t)nqb * words, st));
+        SAH_CUDA(cudaMemcpyAsync(kk, ks_dev + q0, sizeof(int32_t) * nqb, cudaMemcpyDeviceToDevice, st));
+        prep_queries_kernel<<<grid_for(nqb, 8), 256, 0, st>>>(Q_dev + (int64_t)q0 * ix->d, nqb, ix->d, ix->dp, Qd, qn,
+                                                               kk, modes_q, stats);
+        SAH_CUDA(cudaGetLastError());
+        tm.end(0, 1);
+        if (ix->nb > 0) {
+          tm.begin(1);
+          const bool tc_pass = ix->dk > 0 && ix->prm.tc_user_pass && ix->m_nz > 0;
+          const int mask_words = (nqb + 31) / 32;
+          uint32_t* kmask = (uint32_t*)(w + L.kmask);
+          block_filter_kernel<<<ix->nb, 128, sizeof(float) * ix->dp, st>>>(ix->bcent, ix->bcos, ix->bsin, ix->LB,
+                                                                            ix->nb, ix->kmax, ix->n, ix->dp, Qd, qn,
+                                                                            kk, nqb, ix->cone_slack, pairs, pcount,
+                                                                            stats, tc_pass ? kmask : nullptr,
+                                                                            mask_words, ix->bstart, tc_pass ? 1 : 0);
+          SAH_CUDA(cudaGetLastError());
+          tm.end(1, 1);
+          // ---- A4: register-tiled kernel for d <= 128, the shared-memory one otherwise
+          const int threads = std::max(32, ((ix->prm.leaf_size + 31) / 32) * 32);
+          const int dp4 = ix->dp / 4;
+          const int reg_variant = dp4 <= 16 ? 16 : (dp4 <= 32 ? 32 : 0);
+          tm.begin(2);
+          int up_launches = 1;
+          if (tc_pass) {
+            up_launches = 0;
+            SAH_TRY(run_user_pass_tc(ix, Qd, (uint16_t*)(w + L.qb), w + L.coltab, qn, kk, modes_q, nqb, kmask,
+                                     mask_words, (uint8_t*)(w + L.tneed), bitmap, words, surv + 2 * surv_cap,
+                                     survcnt + 2, surv, survcnt, surv_cap, stats, ST_YES_EARLY, ST_FP64, st,
+                                     &up_launches));
+          } else if (reg_variant) {
+            const size_t smem = (size_t)16 * kQChunk * dp4 + sizeof(PairInfo) * kQChunk + sizeof(float) * 64 * threads;
+            auto fn = reg_variant == 16 ? user_scan_reg_kernel<16> : user_scan_reg_kernel<32>;
+            if (smem > 48 * 1024)
+              SAH_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            fn<<<ix->nb, threads, smem, st>>>(
+                ix->Ut, ix->unorm, ix->ucos, ix->usin, ix->uid, ix->bstart, ix->Lt, ix->Eu, ix->pnorm, ix->n,
+                ix->m_nz, ix->kmax, ix->l_exact ? 1 : 0, ix->dp, Qd, qn, kk, nqb, pairs, pcount, ix->gamma,
+                ix->cone_slack, bitmap, words, surv, survcnt, surv_cap, stats, modes_q, ix->T64, ix->d);
+          } else {
+            size_t smem = (size_t)16 * threads * ((ix->dp / 4) | 1);
+            const int stage = smem <= 160 * 1024 ? 1 : 0;
+            if (!stage) smem = 0;
+            smem += sizeof(PairInfo) * kPairChunk;
+            if (smem > 48 * 1024)
+              SAH_CUDA(cudaFuncSetAttribute(user_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            user_scan_kernel<<<ix->nb, threads, smem, st>>>(
+                ix->Ut, ix->unorm, ix->ucos, ix->usin, ix->uid, ix->bstart, ix->Lt, ix->Eu, ix->pnorm, ix->n,
+                ix->m_nz, ix->kmax, ix->l_exact ? 1 : 0, ix->dp, Qd, qn, kk, nqb, pairs, pcount, ix->gamma,
+                ix->cone_slack, bitmap, words, surv, survcnt, surv_cap, stats, stage, modes_q, ix->T64, ix->d);
+          }
+          SAH_CUDA(cudaGetLastError());
+          tm.end(2, up_launches);
+          // ---- A5/A6 on the survivors (their number stays on the device)
+          tm.begin(3);
+          int nl = 0;
+          if (ix->dk > 0) {
+            SAH_TRY(run_verify_tc(ix, cx, surv, survcnt, surv_cap, Qd, qn, kk, bitmap, words, stats, ST_FP64, ST_ITEMS,
+                                  st, &nl));
+          } else {
+            const size_t vsmem = (size_t)16 * kVerifyWarps * (ix->dp / 4);
+            if (vsmem > 48 * 1024)
+              SAH_CUDA(cudaFuncSetAttribute(verify_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)vsmem));
+            verify_exact_kernel<<<sms * 8, kVerifyWarps * 32, vsmem, st>>>(
+                surv, survcnt, surv_cap, ix->Ut, ix->unorm, ix->uid, ix->Ps, ix->pnorm, ix->n, ix->d, ix->dp, Qd, qn,
+                kk, ix->gamma, bitmap, words, stats);
+            SAH_CUDA(cudaGetLastError());
+            nl = 1;
+          }
+          tm.end(3, nl);
+          if (modes_q) {
+            int nsa = 0;
+            tm.begin(5);
+            SAH_TRY(run_saalsh(ix, surv + surv_cap, survcnt + 1, surv_cap, Qd, qn, kk, bitmap, words, stats, ST_ITEMS,
+                               st, &nsa));
+            tm.end(5, nsa);
+          }
+        }
+        tm.begin(4);
+        int n_compact = 3;
+        if (ix->nzero > 0) {
+          zero_users_kernel<<<grid_for(ix->nzero * nqb, 256), 256, 0, st>>>(ix->zero_uid, ix->nzero, nqb, bitmap,
+                                                                             words);
+          ++n_compact;
+        }
+        bitmap_count_kernel<<<gc, 256, 0, st>>>(bitmap, words, nchunks, chunk, kk, ix->n, ix->m);
+        offsets_kernel<<<1, 1024, 0, st>>>(chunk, nchunks, nqb, direct ? 0 : res_total, offsets);
+        int32_t* dst;
+        int64_t dst_cap;
+        if (direct) {
+          dst = out_dev;
+          dst_cap = out_cap;
+        } else {
+          dst = (int32_t*)cx->res.base;
+          dst_cap = (int64_t)(cx->res.bytes / sizeof(int32_t));
+        }
+        if (dst) {
+          bitmap_emit_kernel<<<gc, 256, 0, st>>>(bitmap, words, nchunks, chunk, offsets, nqb, dst, dst_cap,
+                                                 &stats[ST_EMIT_OVERFLOW]);
+        } else {
+          SAH_CUDA(cudaMemsetAsync(&stats[ST_EMIT_OVERFLOW], 0xff, sizeof(unsigned long long), st));
+        }
+        if (direct && offsets_dev)
+          SAH_CUDA(cudaMemcpyAsync(offsets_dev, offsets, sizeof(int64_t) * (nqb + 1), cudaMemcpyDeviceToDevice, st));
+        SAH_CUDA(cudaGetLastError());
+        tm.end(4, n_compact);
+        // ---- the one synchronisation of the sub-batch: offsets, counters, survivor counts
+        *timeout_h = 0;
+        SAH_CUDA(cudaMemcpyAsync(ob, offsets, sizeof(int64_t) * (nqb + 1), cudaMemcpyDeviceToHost, st));
+        SAH_CUDA(cudaMemcpyAsync(st_h, stats, sizeof(unsigned long long) * ST_COUNT, cudaMemcpyDeviceToHost, st));
+        SAH_CUDA(cudaMemcpyAsync(ns2, survcnt, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        if (ix->dev_timeout)
+          SAH_CUDA(cudaMemcpyAsync(timeout_h, ix->dev_timeout, sizeof(int), cudaMemcpyDeviceToHost, st));
+        return SAH_OK;
+      };
+      if (tm.on || !ix->use_graphs || !cx->graphs_allowed) {
+        SAH_TRY(enqueue());
       } else {
-        dst = (int32_t*)cx->res.base;
-        dst_cap = (int64_t)(cx->res.bytes / sizeof(int32_t));
+        // the same shapes and buffers as an earlier call: replay its captured graph
+        const std::vector<uint64_t> key = {(uint64_t)Q_dev, (uint64_t)ks_dev, (uint64_t)modes_dev,
+                                           (uint64_t)out_dev, (uint64_t)out_cap, (uint64_t)offsets_dev,
+                                           (uint64_t)nqb, (uint64_t)q0, (uint64_t)surv_cap, (uint64_t)res_total,
+                                           (uint64_t)direct, (uint64_t)cx->ws.base, (uint64_t)cx->surv.base,
+                                           (uint64_t)cx->res.base, (uint64_t)cx->res.bytes, (uint64_t)cx->tcws.base,
+                                           (uint64_t)cx->tcws.bytes, (uint64_t)cx->pin};
+        SAH_TRY(run_captured(cx, key, enqueue, st));
       }
-      if (dst) {
-        bitmap_emit_kernel<<<gc, 256, 0, st>>>(bitmap, words, nchunks, chunk, offsets, nqb, dst, dst_cap,
-                                               &stats[ST_EMIT_OVERFLOW]);
-      } else {
-        SAH_CUDA(cudaMemsetAsync(&stats[ST_EMIT_OVERFLOW], 0xff, sizeof(unsigned long long), st));
-      }
-      if (direct && offsets_dev)
-        SAH_CUDA(cudaMemcpyAsync(offsets_dev, offsets, sizeof(int64_t) * (nqb + 1), cudaMemcpyDeviceToDevice, st));
-      SAH_CUDA(cudaGetLastError());
-      tm.end(4, n_compact);
-      // ---- the one synchronisation of the sub-batch: offsets, counters, survivor counts
-      std::vector<int64_t> ob(nqb + 1);
-      std::vector<unsigned long long> st_h(ST_COUNT);
-      unsigned long long ns2[3] = {0, 0, 0};
-      int timeout = 0;
-      SAH_CUDA(cudaMemcpyAsync(ob.data(), offsets, sizeof(int64_t) * (nqb + 1), cudaMemcpyDeviceToHost, st));
-      SAH_CUDA(cudaMemcpyAsync(st_h.data(), stats, sizeof(unsigned long long) * ST_COUNT, cudaMemcpyDeviceToHost, st));
-      SAH_CUDA(cudaMemcpyAsync(ns2, survcnt, sizeof(ns2), cudaMemcpyDeviceToHost, st));
-      if (ix->dev_timeout) SAH_CUDA(cudaMemcpyAsync(&timeout, ix->dev_timeout, sizeof(int), cudaMemcpyDeviceToHost, st));
       SAH_CUDA(cudaStreamSynchronize(st));
       tm.collect();
-      if (timeout) {
+      if (*timeout_h) {
         SAH_CUDA(cudaMemsetAsync(ix->dev_timeout, 0, sizeof(int), st));
         SAH_CUDA(cudaStreamSynchronize(st));
         set_error("a bounded device-side wait of the tensor-core kMIPS decision ran out");

@@ -50,6 +50,15 @@ struct Workspace {
 // Everything one query call needs besides the index: a caller (the C-ABI's blocking
 // calls, or one worker of the serving loop) owns one of these, so calls with different
 // contexts can run concurrently on different streams.
+// A sub-batch's launch sequence captured as a CUDA graph, for one set of shapes and
+// buffers (the key); captured the second time the key is seen, replayed after that.
+struct GraphEntry {
+  std::vector<uint64_t> key;
+  cudaGraphExec_t exec = nullptr;
+  bool bad = false;          // capture failed: run this key directly
+  uint64_t last_use = 0;
+};
+
 struct CallCtx {
   Workspace ws;      // queries, pair lists, bitmaps, counters
   Workspace surv;    // survivor lists, grown on demand
@@ -57,6 +66,11 @@ struct CallCtx {
   Workspace tcws;    // tensor-core kMIPS decision: sorted rows, statuses, band lists
   int64_t surv_hint = 1 << 16;   // survivor-list capacity for the next call
   sah_stats stats{};
+  void* pin = nullptr;           // pinned host memory for the per-call readback
+  size_t pin_bytes = 0;
+  std::vector<GraphEntry> graphs;
+  uint64_t graph_clock = 0;
+  bool graphs_allowed = false;   // the index's own context; the server's workers run directly
 };
 
 void free_ctx(CallCtx* cx);
@@ -136,6 +150,7 @@ struct Index {
   size_t bytes = 0;
   CallCtx main_ctx;           // context of the blocking C-ABI calls
   bool timing = false;
+  bool use_graphs = true;     // replay a call's launch sequence as a CUDA graph when shapes repeat
 };
 
 sah_status dev_alloc(Index* ix, void** p, size_t bytes);

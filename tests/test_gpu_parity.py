@@ -236,3 +236,30 @@ def test_survivor_list_overflow_reruns(sah, variant):
     assert ix.stats()["survivors"] > (1 << 16)
     for r in (0, 57, 123, 199):
         assert np.array_equal(got[r], _truth(W.U, W.P, Q[r], (30,))[30]), r
+
+
+@pytest.mark.parametrize("variant", list(VARIANTS))
+def test_repeated_calls_same_answers(sah, variant):
+    """A call whose shapes and buffers repeat is captured as a CUDA graph on its second run
+    and replayed after that: every run, host or device buffers, interleaved with other
+    shapes and with per-stage timing on and off, gives the oracle's answers."""
+    import torch
+    W = workload.make("c2", m=5000, n=1500)
+    ix = sah.Index(W.U, W.P, k_max=50, leaf_size=128, p_prime=1 << 30, **VARIANTS[variant])
+    Q, K, rows = W.requests()
+    Q, K, rows = Q[:120], K[:120], rows[:120]
+    counts = {int(r): oracle.count_above(W.U, W.P, W.P[W.query_idx[r]]) for r in np.unique(rows)}
+    want = [np.flatnonzero(counts[int(rows[j])] < K[j]).astype(np.int32) for j in range(len(K))]
+    Qd, Kd = torch.from_numpy(Q).cuda(), torch.from_numpy(K).cuda()
+    out = torch.empty(W.m * len(K), dtype=torch.int32, device="cuda")
+    offs = torch.empty(len(K) + 1, dtype=torch.int64, device="cuda")
+    for it in range(6):
+        ix.set_timing(it == 4)
+        got = ix.rkmips_batch(Q, K)
+        assert all(np.array_equal(g, w) for g, w in zip(got, want)), it
+        total = ix.rkmips_batch_device(Qd, Kd, out, offs)
+        o = offs.cpu().numpy()
+        res = out[:total].cpu().numpy()
+        assert all(np.array_equal(res[o[j]:o[j + 1]], want[j]) for j in range(len(K))), it
+        small = ix.rkmips_batch(Q[:7], K[:7])                 # another shape in between
+        assert all(np.array_equal(g, w) for g, w in zip(small, want[:7])), it
