@@ -428,13 +428,18 @@ def main():
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     kernel = STAGE_KERNELS.get(dom, dom)
     if dom == "user_pass" and tc_main:
-        # one dense GEMM U Q^T over the users of the kept leaves (A8), useful FLOPs only
-        # (the three split-BF16 products count once)
+        # the tcgen05 GEMM kernel of the user pass: HBM-bound (its intensity, about 150 FLOP
+        # per byte with the three split-BF16 products, is below the ridge of about 270).
+        # Algorithmic bytes per launch: every user of the kept leaves once (hi and lo BF16
+        # rows, 4 bytes per padded coordinate) plus its norm, bound error, id, leaf and the
+        # lower bounds of the batch's distinct k; time: the kernel alone (stage slot 6).
         kernel = "user_pass_tc_kernel"
-        fl = 2.0 * W.d * st["users_in_kept_blocks"] * nq
-        roof = {"bound": "tensor", "achieved": fl / (stage_ms[dom_i] / 1e3) / 1e12,
-                "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json bf16_tflops, burst)"}
+        dk = 64 if W.d <= 64 else 128
+        by = st["users_in_kept_blocks"] * (4.0 * dk + 4.0 * (4 + distinct_k))
+        dur_s = stage_ms[6] / 1e3
+        roof = {"bound": "hbm", "achieved": by / dur_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes": by}
     elif dom == "kmips_decision" and args.precision == "bf16":
         # the tcgen05 GEMM: useful BF16 MACs of the rows still open, per launch of the
         # stage's kernels (the GEMM itself is one of them)
@@ -503,6 +508,33 @@ def main():
                 line["variants"][name] = rec
                 if not same:
                     ixv.close()
+
+    if not args.no_variants and rank == 0:
+        # a batch without repeated vectors: 500 distinct item queries at k uniform in 1..50
+        rng = np.random.default_rng(5)
+        rows = rng.choice(W.n, size=nq, replace=False)
+        Qx = np.ascontiguousarray(W.P[rows])
+        Kx = rng.integers(1, 51, size=nq).astype(np.int32)
+        Qxd, Kxd = torch.from_numpy(Qx).to(dev), torch.from_numpy(Kx).to(dev)
+        hx = ix.rkmips_batch(Qx, Kx)
+        outx = torch.empty(max(1, sum(len(h) for h in hx)), dtype=torch.int32, device=dev)
+        offx = torch.empty(nq + 1, dtype=torch.int64, device=dev)
+        for _ in range(3):
+            ix.rkmips_batch_device(Qxd, Kxd, outx, offx, stream=stream)
+        tx = []
+        for _ in range(max(3, args.steps // 2)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ix.rkmips_batch_device(Qxd, Kxd, outx, offx, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tx.append(e0.elapsed_time(e1))
+        line["variants"]["distinct_queries_mixed_k"] = {
+            "value": nq * len(tx) / (sum(tx) / 1e3), "ms_per_step": float(np.mean(tx)),
+            "batch": "%d distinct item queries, k uniform in 1..50, the main index" % nq}
 
     if rank == 0 and not args.no_serving:
         line["serving"] = serve_stream(sah, ix, W, args.serve_rate, args.serve_requests)

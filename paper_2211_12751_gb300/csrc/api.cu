@@ -2,6 +2,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <unordered_map>
 #include <string>
 #include <vector>
 
@@ -14,6 +16,25 @@ thread_local std::string g_last_error;
 }
 
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+// Kernels whose dynamic shared memory depends on the call may be launched from several
+// threads at once (the server's workers): the limit only ever rises, so a launch never
+// finds it lowered under its feet by another thread.
+sah_status raise_smem_limit(const void* fn, size_t bytes) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> limit;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = limit[fn];
+  if (bytes <= cur) return SAH_OK;
+  const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error(std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+    return SAH_ERR_CUDA;
+  }
+  cur = bytes;
+  return SAH_OK;
+}
 
 sah_status cuda_status(cudaError_t e, const char* what) {
   g_last_error = std::string(what) + ": " + cudaGetErrorString(e);

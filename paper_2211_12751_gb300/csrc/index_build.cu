@@ -695,8 +695,7 @@ sah_status build_index_device(Index* ix, const float* U_dev, const float* P_dev,
     int tile_items = 128;
     while (tile_items > 32 && (size_t)tile_items * stride4 * 16 > 96 * 1024) tile_items -= 32;
     size_t smem = ((size_t)tile_items * stride4 + (size_t)kTopkWarps * kUsersPerWarp * (dp / 4)) * 16;
-    SAH_CUDA(cudaFuncSetAttribute(topk_lower_bounds_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+    SAH_TRY(raise_smem_limit((const void*)topk_lower_bounds_kernel, (size_t)((int)smem)));
     unsigned grid = grid_for(mz, kTopkWarps * kUsersPerWarp);
     if (ix->prm.precision == SAH_BF16) SAH_TRY(build_bf16_copies(ix, st));
     if (ix->pp > 0) {

@@ -897,6 +897,15 @@ struct StageTimer {
     }
   }
   void begin(int i) { if (on) cudaEventRecord(b[i], st); }
+  // the begin / end events of slot i for a launcher to record itself (nullptr when off)
+  const cudaEvent_t* slot(int i) {
+    if (!on) return nullptr;
+    used[i] = true;
+    pair[0] = b[i];
+    pair[1] = e[i];
+    return pair;
+  }
+  cudaEvent_t pair[2] = {};
   void end(int i, int nlaunch) {
     launches[i] += nlaunch;
     if (on) {
@@ -910,8 +919,8 @@ struct StageTimer {
     for (int i = 0; i < kStages; ++i)
       if (used[i]) {
         float t = 0.f;
-        cudaEventElapsedTime(&t, b[i], e[i]);
-        ms[i] += t;
+        if (cudaEventElapsedTime(&t, b[i], e[i]) == cudaSuccess) ms[i] += t;
+        else cudaGetLastError();   // a slot whose launcher recorded nothing
         used[i] = false;
       }
   }
@@ -1039,12 +1048,12 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
             SAH_TRY(run_user_pass_tc(ix, Qd, (uint16_t*)(w + L.qb), w + L.coltab, qn, kk, modes_q, nqb, kmask,
                                      mask_words, (uint8_t*)(w + L.tneed), bitmap, words, surv + 2 * surv_cap,
                                      survcnt + 2, surv, survcnt, surv_cap, stats, ST_YES_EARLY, ST_FP64, st,
-                                     &up_launches));
+                                     &up_launches, tm.slot(6)));
           } else if (reg_variant) {
             const size_t smem = (size_t)16 * kQChunk * dp4 + sizeof(PairInfo) * kQChunk + sizeof(float) * 64 * threads;
             auto fn = reg_variant == 16 ? user_scan_reg_kernel<16> : user_scan_reg_kernel<32>;
             if (smem > 48 * 1024)
-              SAH_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+              SAH_TRY(raise_smem_limit((const void*)fn, (size_t)((int)smem)));
             fn<<<ix->nb, threads, smem, st>>>(
                 ix->Ut, ix->unorm, ix->ucos, ix->usin, ix->uid, ix->bstart, ix->Lt, ix->Eu, ix->pnorm, ix->n,
                 ix->m_nz, ix->kmax, ix->l_exact ? 1 : 0, ix->dp, Qd, qn, kk, nqb, pairs, pcount, ix->gamma,
@@ -1055,7 +1064,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
             if (!stage) smem = 0;
             smem += sizeof(PairInfo) * kPairChunk;
             if (smem > 48 * 1024)
-              SAH_CUDA(cudaFuncSetAttribute(user_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+              SAH_TRY(raise_smem_limit((const void*)user_scan_kernel, (size_t)((int)smem)));
             user_scan_kernel<<<ix->nb, threads, smem, st>>>(
                 ix->Ut, ix->unorm, ix->ucos, ix->usin, ix->uid, ix->bstart, ix->Lt, ix->Eu, ix->pnorm, ix->n,
                 ix->m_nz, ix->kmax, ix->l_exact ? 1 : 0, ix->dp, Qd, qn, kk, nqb, pairs, pcount, ix->gamma,
@@ -1072,8 +1081,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
           } else {
             const size_t vsmem = (size_t)16 * kVerifyWarps * (ix->dp / 4);
             if (vsmem > 48 * 1024)
-              SAH_CUDA(cudaFuncSetAttribute(verify_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)vsmem));
+              SAH_TRY(raise_smem_limit((const void*)verify_exact_kernel, (size_t)((int)vsmem)));
             verify_exact_kernel<<<sms * 8, kVerifyWarps * 32, vsmem, st>>>(
                 surv, survcnt, surv_cap, ix->Ut, ix->unorm, ix->uid, ix->Ps, ix->pnorm, ix->n, ix->d, ix->dp, Qd, qn,
                 kk, ix->gamma, bitmap, words, stats);

@@ -502,7 +502,7 @@ sah_status build_saalsh(Index* ix, const float* srp_host, cudaStream_t st) {
     const size_t smem = sizeof(float) * (size_t)(kCodeUsers + kCodeTables * bits) * (d | 1);
     if (smem <= 160 * 1024) {
       if (smem > 48 * 1024)
-        SAH_CUDA(cudaFuncSetAttribute(user_codes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        SAH_TRY(raise_smem_limit((const void*)user_codes_kernel, (size_t)((int)smem)));
       dim3 g(grid_for(ix->m_nz, kCodeUsers), (K + kCodeTables - 1) / kCodeTables);
       user_codes_kernel<<<g, kCodeUsers * kCodeTables, smem, st>>>(ix->Ut, d, dp, ix->m_nz, ix->sa_A, ix->sa_d1p, K,
                                                                   bits, ix->sa_ucode);

@@ -154,6 +154,8 @@ struct Index {
 };
 
 sah_status dev_alloc(Index* ix, void** p, size_t bytes);
+// Raises (never lowers) a kernel's dynamic shared-memory limit; thread-safe.
+sah_status raise_smem_limit(const void* fn, size_t bytes);
 
 // ------------------------------------------------------------------ device helpers
 __host__ __device__ inline uint64_t splitmix64(uint64_t x) {
@@ -219,7 +221,7 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
                             int mask_words, uint8_t* tile_need, uint32_t* bitmap, int64_t words, Survivor* resc,
                             unsigned long long* resc_count, Survivor* surv, unsigned long long* surv_count,
                             int64_t surv_cap, unsigned long long* stats, int st_yes, int st_fp64, cudaStream_t st,
-                            int* launches);
+                            int* launches, const cudaEvent_t* ev = nullptr);   // ev: begin / end of the GEMM kernel
 // topk_tc.cu: the 64 largest FP32 scores of every user over all items, through tcgen05
 sah_status topk_full_tc(Index* ix, float* vlast, int32_t* ids64, cudaStream_t st, double* gemm_ms);
 // verify_tc.cu

@@ -41,6 +41,7 @@ struct Done {
   sah_status status;
   std::vector<int32_t> ids;
   double latency_s;
+  std::string error;   // the worker's error message when the batch failed
 };
 
 struct Worker {
@@ -153,6 +154,7 @@ void worker_loop(sah_server* s, Worker* w) {
         dn.status = st;
         if (st == SAH_OK) dn.ids.assign(w->ids_h + offs[i], w->ids_h + offs[i + 1]);
         dn.latency_s = std::chrono::duration<double>(t1 - batch[i].t0).count();
+        if (st != SAH_OK) dn.error = sah_last_error();
         s->done.emplace(batch[i].ticket, std::move(dn));
         s->inflight.erase(batch[i].ticket);
       }
@@ -253,8 +255,9 @@ sah_status sah_server_poll(sah_server* s, uint64_t ticket, int32_t* out_ids, int
   if (latency_s) *latency_s = dn.latency_s;
   if (dn.status != SAH_OK) {
     const sah_status st = dn.status;
+    const std::string why = dn.error;
     s->done.erase(it);
-    sah::set_error("sah_server_poll: the request's batch failed");
+    sah::set_error("sah_server_poll: the request's batch failed: " + why);
     return st;
   }
   if ((int64_t)dn.ids.size() > cap) return SAH_ERR_BUFFER_TOO_SMALL;

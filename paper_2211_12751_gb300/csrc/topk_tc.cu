@@ -303,11 +303,11 @@ sah_status topk_full_tc(Index* ix, float* vlast, int32_t* ids64, cudaStream_t st
     cudaEventRecord(e0, st);
     if (ix->dk == 64) {
       constexpr size_t smem = topk_smem_bytes<1, 4>();
-      SAH_CUDA(cudaFuncSetAttribute(topk_tc_kernel<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      SAH_TRY(raise_smem_limit((const void*)topk_tc_kernel<1, 4>, smem));
       topk_tc_kernel<1, 4><<<grid, kTThreads, smem, st>>>(ix->tmap_U, ix->tmap_P, p);
     } else {
       constexpr size_t smem = topk_smem_bytes<2, 2>();
-      SAH_CUDA(cudaFuncSetAttribute(topk_tc_kernel<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      SAH_TRY(raise_smem_limit((const void*)topk_tc_kernel<2, 2>, smem));
       topk_tc_kernel<2, 2><<<grid, kTThreads, smem, st>>>(ix->tmap_U, ix->tmap_P, p);
     }
     cudaEventRecord(e1, st);

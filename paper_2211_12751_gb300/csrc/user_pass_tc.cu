@@ -909,7 +909,7 @@ __global__ void split_queries_kernel(const float* __restrict__ Qd, int nq, int d
 inline unsigned grid_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
 
 template <int KB, int STAGES, int NMAX>
-sah_status launch_pass(Index* ix, UpParams p, int sms, cudaStream_t st, int* launches) {
+sah_status launch_pass(Index* ix, UpParams p, int sms, cudaStream_t st, int* launches, const cudaEvent_t* ev) {
   using S = UpSmem<KB, STAGES, NMAX>;
   auto fn = user_pass_tc_kernel<KB, STAGES, NMAX>;
   // lower-bound rows per warp: what shared memory holds beside the operands
@@ -925,13 +925,15 @@ sah_status launch_pass(Index* ix, UpParams p, int sms, cudaStream_t st, int* lau
     return SAH_ERR_UNSUPPORTED;
   }
   const size_t smem = S::bytes(p.slot_cap);
-  SAH_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SAH_TRY(raise_smem_limit((const void*)fn, (size_t)((int)smem)));
   const unsigned grid = (unsigned)std::max(1, std::min(p.ntiles, sms));
   const int64_t seg = (int64_t)kMaxTileList * grid;   // tiles per launch: at most kMaxTileList per CTA
   for (int64_t t0 = 0; t0 < p.ntiles; t0 += seg) {
     p.tile0 = (int)t0;
     p.tile_end = (int)std::min<int64_t>(p.ntiles, t0 + seg);
+    if (ev && t0 == 0) SAH_CUDA(cudaEventRecord(ev[0], st));
     fn<<<grid, kUThreads, smem, st>>>(ix->tmap_U, ix->tmap_Ulo, p);
+    if (ev && t0 + seg >= p.ntiles) SAH_CUDA(cudaEventRecord(ev[1], st));
     SAH_CUDA(cudaGetLastError());
     if (launches) *launches += 1;
   }
@@ -947,7 +949,7 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
                             int mask_words, uint8_t* tile_need, uint32_t* bitmap, int64_t words, Survivor* resc,
                             unsigned long long* resc_count, Survivor* surv, unsigned long long* surv_count,
                             int64_t surv_cap, unsigned long long* stats, int st_yes, int st_fp64, cudaStream_t st,
-                            int* launches) {
+                            int* launches, const cudaEvent_t* ev) {
   if (ix->m_nz == 0 || nq == 0 || ix->dk <= 0) return SAH_OK;
   if (nq > kMaxRows) {
     set_error("tensor-core user pass: sub-batch larger than its column table");
@@ -963,7 +965,7 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
   int ht = 64;
   while (ht < 2 * nq) ht <<= 1;
   const size_t tsmem = sizeof(int32_t) * (2 * (size_t)ht + 4 * (size_t)nq);
-  SAH_CUDA(cudaFuncSetAttribute(column_table_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem));
+  SAH_TRY(raise_smem_limit((const void*)column_table_kernel, (size_t)((int)tsmem)));
   column_table_kernel<<<1, 1024, tsmem, st>>>(Qd, nq, ix->d, ix->dp, kk, modes, ix->kmax, ix->n, ix->pnorm, ht, T);
   SAH_CUDA(cudaGetLastError());
   UpParams p{};
@@ -1005,9 +1007,9 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
   if (ix->dk == 64) {
-    SAH_TRY((launch_pass<1, 4, 128>(ix, p, sms, st, launches)));
+    SAH_TRY((launch_pass<1, 4, 128>(ix, p, sms, st, launches, ev)));
   } else {
-    SAH_TRY((launch_pass<2, 2, 64>(ix, p, sms, st, launches)));
+    SAH_TRY((launch_pass<2, 2, 64>(ix, p, sms, st, launches, ev)));
   }
   pair_rescore_kernel<<<sms * 4, 256, 0, st>>>(resc, resc_count, surv_cap, ix->Ut, ix->unorm, ix->uid, ix->Lt,
                                                ix->Eu, ix->pnorm, ix->n, ix->m_nz, ix->kmax, ix->l_exact ? 1 : 0,

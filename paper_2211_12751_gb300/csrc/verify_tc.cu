@@ -616,11 +616,11 @@ sah_status run_verify_tc(Index* ix, CallCtx* cx, const Survivor* surv, const uns
   const unsigned grid = grid_for(ns, kRows);
   if (ix->dk == 64) {
     constexpr size_t smem = tc_smem_bytes<1, 4>();
-    SAH_CUDA(cudaFuncSetAttribute(verify_tc_kernel<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SAH_TRY(raise_smem_limit((const void*)verify_tc_kernel<1, 4>, smem));
     verify_tc_kernel<1, 4><<<grid, kThreads, smem, st>>>(ix->tmap_P, prm);
   } else {
     constexpr size_t smem = tc_smem_bytes<2, 2>();
-    SAH_CUDA(cudaFuncSetAttribute(verify_tc_kernel<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SAH_TRY(raise_smem_limit((const void*)verify_tc_kernel<2, 2>, smem));
     verify_tc_kernel<2, 2><<<grid, kThreads, smem, st>>>(ix->tmap_P, prm);
   }
   SAH_CUDA(cudaGetLastError());
