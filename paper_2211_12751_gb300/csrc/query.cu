@@ -1030,13 +1030,20 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
           const bool tc_pass = ix->dk > 0 && ix->prm.tc_user_pass && ix->m_nz > 0;
           const int mask_words = (nqb + 31) / 32;
           uint32_t* kmask = (uint32_t*)(w + L.kmask);
-          block_filter_kernel<<<ix->nb, 128, sizeof(float) * ix->dp, st>>>(ix->bcent, ix->bcos, ix->bsin, ix->LB,
-                                                                            ix->nb, ix->kmax, ix->n, ix->dp, Qd, qn,
-                                                                            kk, nqb, ix->cone_slack, pairs, pcount,
-                                                                            stats, tc_pass ? kmask : nullptr,
-                                                                            mask_words, ix->bstart, tc_pass ? 1 : 0);
-          SAH_CUDA(cudaGetLastError());
-          tm.end(1, 1);
+          int bf_launches = 1;
+          if (tc_pass) {
+            // the distinct query vectors first: the block bound is taken once per vector
+            SAH_TRY(prepare_user_pass_tc(ix, Qd, (uint16_t*)(w + L.qb), w + L.coltab, kk, modes_q, nqb, st,
+                                         &bf_launches));
+            SAH_TRY(block_filter_tc(ix, Qd, qn, w + L.coltab, nqb, kmask, mask_words, stats, ST_PAIRS_KEPT,
+                                    ST_KEPT_USERS, ST_USERS_SCORED, st));
+          } else {
+            block_filter_kernel<<<ix->nb, 128, sizeof(float) * ix->dp, st>>>(
+                ix->bcent, ix->bcos, ix->bsin, ix->LB, ix->nb, ix->kmax, ix->n, ix->dp, Qd, qn, kk, nqb,
+                ix->cone_slack, pairs, pcount, stats, nullptr, mask_words, ix->bstart, 0);
+            SAH_CUDA(cudaGetLastError());
+          }
+          tm.end(1, bf_launches);
           // ---- A4: register-tiled kernel for d <= 128, the shared-memory one otherwise
           const int threads = std::max(32, ((ix->prm.leaf_size + 31) / 32) * 32);
           const int dp4 = ix->dp / 4;
@@ -1045,7 +1052,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
           int up_launches = 1;
           if (tc_pass) {
             up_launches = 0;
-            SAH_TRY(run_user_pass_tc(ix, Qd, (uint16_t*)(w + L.qb), w + L.coltab, qn, kk, modes_q, nqb, kmask,
+            SAH_TRY(run_user_pass_tc(ix, Qd, (uint16_t*)(w + L.qb), w + L.coltab, qn, kk, nqb, kmask,
                                      mask_words, (uint8_t*)(w + L.tneed), bitmap, words, surv + 2 * surv_cap,
                                      survcnt + 2, surv, survcnt, surv_cap, stats, ST_YES_EARLY, ST_FP64, st,
                                      &up_launches, tm.slot(6)));

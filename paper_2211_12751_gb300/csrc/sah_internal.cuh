@@ -211,17 +211,25 @@ sah_status run_saalsh(Index* ix, const Survivor* surv, const unsigned long long*
                       const float* Qd, const float* qn, const int32_t* kk, uint32_t* bitmap, int64_t words,
                       unsigned long long* stats, int stat_items, cudaStream_t st, int* launches);
 // user_pass_tc.cu: the user pass on tcgen05 over every user tile and the distinct query
-// vectors of the sub-batch (split hi / lo BF16 operands written to Qsplit, 2 nq dk entries;
-// the column table in scratch, user_pass_tc_scratch_bytes(nq) bytes), for the (leaf,
-// query) pairs set in kept_mask ([nb][mask_words]); tile_need holds one byte per 128-user
-// tile.  The pairs its band leaves open go to resc and are re-scored in FP32.  nq <= 4096.
+// vectors of the sub-batch (nq <= 4096 rows).
+//  prepare_user_pass_tc: split hi / lo BF16 queries into Qsplit (2 nq dk entries) and the
+//    column table (distinct vectors, their rows) into scratch (user_pass_tc_scratch_bytes).
+//  block_filter_tc: A3 per (leaf, column), the rows' decisions into kept_mask
+//    ([nb][mask_words]) and the counters stats[st_pairs], stats[st_users], stats[st_scored].
+//  run_user_pass_tc: the GEMM and its epilogue; tile_need holds one byte per 128-user tile;
+//    the pairs its band leaves open go to resc and are re-scored in FP32.
 size_t user_pass_tc_scratch_bytes(int nq);
+sah_status prepare_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* scratch, const int32_t* kk,
+                                const int32_t* modes, int nq, cudaStream_t st, int* launches);
+sah_status block_filter_tc(Index* ix, const float* Qd, const float* qn, void* scratch, int nq, uint32_t* kept_mask,
+                           int mask_words, unsigned long long* stats, int st_pairs, int st_users, int st_scored,
+                           cudaStream_t st);
 sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* scratch, const float* qn,
-                            const int32_t* kk, const int32_t* modes, int nq, const uint32_t* kept_mask,
-                            int mask_words, uint8_t* tile_need, uint32_t* bitmap, int64_t words, Survivor* resc,
-                            unsigned long long* resc_count, Survivor* surv, unsigned long long* surv_count,
-                            int64_t surv_cap, unsigned long long* stats, int st_yes, int st_fp64, cudaStream_t st,
-                            int* launches, const cudaEvent_t* ev = nullptr);   // ev: begin / end of the GEMM kernel
+                            const int32_t* kk, int nq, const uint32_t* kept_mask, int mask_words, uint8_t* tile_need,
+                            uint32_t* bitmap, int64_t words, Survivor* resc, unsigned long long* resc_count,
+                            Survivor* surv, unsigned long long* surv_count, int64_t surv_cap,
+                            unsigned long long* stats, int st_yes, int st_fp64, cudaStream_t st, int* launches,
+                            const cudaEvent_t* ev = nullptr);   // ev: begin / end of the GEMM kernel
 // topk_tc.cu: the 64 largest FP32 scores of every user over all items, through tcgen05
 sah_status topk_full_tc(Index* ix, float* vlast, int32_t* ids64, cudaStream_t st, double* gemm_ms);
 // verify_tc.cu

@@ -147,14 +147,21 @@ column_table_kernel(const float* __restrict__ Qd, int nq, int d, int dp, const i
     kq[i] = 0;
   }
   __syncthreads();
+  // a thread per row: hash of the row's bits (one multiply per 64 bits), then linear
+  // probing with a bitwise comparison against the slot's owner
   for (int j = tid; j < nq; j += nt) {
     const int k = kk[j];
     colof[j] = -1;
     if (k < 1 || k > n) continue;
     const int cls = k <= kmax ? 0 : 1;
     const uint32_t* q = reinterpret_cast<const uint32_t*>(Qd + (int64_t)j * dp);
-    uint64_t h = splitmix64(0x51ed27ull + cls);
-    for (int i = 0; i < d; ++i) h = splitmix64(h ^ q[i]);
+    uint64_t h = 0x51ed27ull + (uint64_t)cls;
+    for (int i = 0; i < d; i += 2) {
+      const uint64_t x = (uint64_t)q[i] | ((i + 1 < d ? (uint64_t)q[i + 1] : 0ull) << 32);
+      h = (h ^ x) * 0x9E3779B97F4A7C15ull;
+      h ^= h >> 29;
+    }
+    h = splitmix64(h);
     int slot = (int)(h & (uint64_t)(ht - 1));
     for (int probe = 0; probe < ht; ++probe) {
       int cur = owner[slot];
@@ -165,8 +172,12 @@ column_table_kernel(const float* __restrict__ Qd, int nq, int d, int dp, const i
       }
       const int kc = kk[cur];
       bool same = (kc <= kmax ? 0 : 1) == cls;
-      const uint32_t* qc = reinterpret_cast<const uint32_t*>(Qd + (int64_t)cur * dp);
-      for (int i = 0; same && i < d; ++i) same = q[i] == qc[i];
+      const float4* a4 = reinterpret_cast<const float4*>(Qd + (int64_t)j * dp);
+      const float4* c4 = reinterpret_cast<const float4*>(Qd + (int64_t)cur * dp);
+      for (int i = 0; same && i < dp / 4; ++i) {
+        const uint4 x = *reinterpret_cast<const uint4*>(a4 + i), y = *reinterpret_cast<const uint4*>(c4 + i);
+        same = x.x == y.x && x.y == y.y && x.z == y.z && x.w == y.w;
+      }
       if (same) break;
       slot = (slot + 1) & (ht - 1);
     }
@@ -222,6 +233,85 @@ column_table_kernel(const float* __restrict__ Qd, int nq, int d, int dp, const i
     const int sa = (modes != nullptr && modes[j] == SAH_SAALSH && k <= kmax) ? 1 : 0;
     const float pk = k <= n ? pnorm[k - 1] : -INFINITY;
     T.rows[atomicAdd(&cnt[cc], 1)] = make_int4(j | (sa << 30), k, __float_as_int(pk), 0);
+  }
+}
+
+// A3 over the columns: Lemma 2 for every (leaf, distinct query vector) pair, then the bound
+// compared with L^k(B) for each row of the column.  One CTA per leaf; the leaf's decisions
+// go to kept_mask[B] (bit j of word j / 32), as the row-wise block filter writes them.
+// The arithmetic of the bound is the row-wise kernel's.
+__global__ void block_filter_cols_kernel(const float* __restrict__ bcent, const float* __restrict__ bcos,
+                                         const float* __restrict__ bsin, const float* __restrict__ LB, int nb,
+                                         int kmax, int dp, const float* __restrict__ Qd, const float* __restrict__ qn,
+                                         ColTable T, float slack, uint32_t* __restrict__ kept_mask, int mask_words,
+                                         const int32_t* __restrict__ bstart, unsigned long long* __restrict__ stats,
+                                         int st_pairs, int st_users, int st_scored) {
+  extern __shared__ float4 c4s[];   // the leaf's unit centre
+  __shared__ uint32_t kbits[kMaxRows / 32];
+  __shared__ int kept_sh;
+  const int B = blockIdx.x;
+  const int dp4 = dp / 4;
+  for (int i = threadIdx.x; i < dp4; i += blockDim.x)
+    c4s[i] = reinterpret_cast<const float4*>(bcent + (int64_t)B * dp)[i];
+  for (int i = threadIdx.x; i < mask_words; i += blockDim.x) kbits[i] = 0u;
+  if (threadIdx.x == 0) kept_sh = 0;
+  __syncthreads();
+  const float cw = bcos[B], sw = bsin[B];
+  const bool degenerate = cw < -1.5f;
+  const int ncol = *T.ncol;
+  int kept = 0;
+  for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+    const int rep = T.rep[c];
+    const float nrm = qn[rep];
+    float ub = INFINITY;   // no cone bound: every row kept
+    if (!degenerate && nrm > 0.f) {
+      const float4* q4 = reinterpret_cast<const float4*>(Qd + (int64_t)rep * dp);
+      float dq = 0.f;
+      for (int i = 0; i < dp4; ++i) {
+        const float4 a = c4s[i], b = __ldg(q4 + i);
+        dq = fmaf(a.x, b.x, dq);
+        dq = fmaf(a.y, b.y, dq);
+        dq = fmaf(a.z, b.z, dq);
+        dq = fmaf(a.w, b.w, dq);
+      }
+      const float cphi = fminf(1.f, fmaxf(-1.f, dq / nrm));
+      float sphi;
+      if (cphi * cphi <= 0.5f) {
+        sphi = sqrtf(fmaxf(0.f, fmaf(-cphi, cphi, 1.f)));
+      } else {
+        float o2 = 0.f;
+        for (int i = 0; i < dp4; ++i) {
+          const float4 a = c4s[i], b = __ldg(q4 + i);
+          float o;
+          o = fmaf(-dq, a.x, b.x); o2 = fmaf(o, o, o2);
+          o = fmaf(-dq, a.y, b.y); o2 = fmaf(o, o, o2);
+          o = fmaf(-dq, a.z, b.z); o2 = fmaf(o, o, o2);
+          o = fmaf(-dq, a.w, b.w); o2 = fmaf(o, o, o2);
+        }
+        sphi = fminf(1.f, sqrtf(o2) / nrm);
+      }
+      if (cphi >= cw - slack) ub = nrm * (1.f + slack);
+      else ub = nrm * (fmaf(cphi, cw, sphi * sw) + 2.f * slack);
+    }
+    for (int q = T.start[c]; q < T.start[c + 1]; ++q) {
+      const int4 rw = T.rows[q];
+      const int j = rw.x & 0x3fffffff, k = rw.y;
+      const float lb = (k <= kmax) ? LB[(int64_t)(k - 1) * nb + B] : -INFINITY;
+      if (!(ub < lb)) {
+        atomicOr(&kbits[j >> 5], 1u << (j & 31));
+        ++kept;
+      }
+    }
+  }
+  kept = __reduce_add_sync(0xffffffffu, kept);
+  if ((threadIdx.x & 31) == 0 && kept) atomicAdd(&kept_sh, kept);
+  __syncthreads();
+  for (int i = threadIdx.x; i < mask_words; i += blockDim.x) kept_mask[(int64_t)B * mask_words + i] = kbits[i];
+  if (threadIdx.x == 0 && kept_sh) {
+    const int users = bstart[B + 1] - bstart[B];
+    atomicAdd(&stats[st_pairs], (unsigned long long)kept_sh);
+    atomicAdd(&stats[st_users], (unsigned long long)users);
+    atomicAdd(&stats[st_scored], (unsigned long long)kept_sh * users);
   }
 }
 
@@ -944,13 +1034,9 @@ sah_status launch_pass(Index* ix, UpParams p, int sms, cudaStream_t st, int* lau
 
 size_t user_pass_tc_scratch_bytes(int nq) { return col_table_bytes(nq); }
 
-sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* scratch, const float* qn,
-                            const int32_t* kk, const int32_t* modes, int nq, const uint32_t* kept_mask,
-                            int mask_words, uint8_t* tile_need, uint32_t* bitmap, int64_t words, Survivor* resc,
-                            unsigned long long* resc_count, Survivor* surv, unsigned long long* surv_count,
-                            int64_t surv_cap, unsigned long long* stats, int st_yes, int st_fp64, cudaStream_t st,
-                            int* launches, const cudaEvent_t* ev) {
-  if (ix->m_nz == 0 || nq == 0 || ix->dk <= 0) return SAH_OK;
+sah_status prepare_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* scratch, const int32_t* kk,
+                                const int32_t* modes, int nq, cudaStream_t st, int* launches) {
+  if (nq == 0 || ix->dk <= 0) return SAH_OK;
   if (nq > kMaxRows) {
     set_error("tensor-core user pass: sub-batch larger than its column table");
     return SAH_ERR_ARG;
@@ -965,9 +1051,35 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
   int ht = 64;
   while (ht < 2 * nq) ht <<= 1;
   const size_t tsmem = sizeof(int32_t) * (2 * (size_t)ht + 4 * (size_t)nq);
-  SAH_TRY(raise_smem_limit((const void*)column_table_kernel, (size_t)((int)tsmem)));
+  SAH_TRY(raise_smem_limit((const void*)column_table_kernel, tsmem));
   column_table_kernel<<<1, 1024, tsmem, st>>>(Qd, nq, ix->d, ix->dp, kk, modes, ix->kmax, ix->n, ix->pnorm, ht, T);
   SAH_CUDA(cudaGetLastError());
+  if (launches) *launches += 2;
+  return SAH_OK;
+}
+
+sah_status block_filter_tc(Index* ix, const float* Qd, const float* qn, void* scratch, int nq, uint32_t* kept_mask,
+                           int mask_words, unsigned long long* stats, int st_pairs, int st_users, int st_scored,
+                           cudaStream_t st) {
+  if (ix->nb == 0 || nq == 0) return SAH_OK;
+  const ColTable T = col_table_at(scratch, nq);
+  block_filter_cols_kernel<<<ix->nb, 128, sizeof(float) * ix->dp, st>>>(
+      ix->bcent, ix->bcos, ix->bsin, ix->LB, ix->nb, ix->kmax, ix->dp, Qd, qn, T, ix->cone_slack, kept_mask,
+      mask_words, ix->bstart, stats, st_pairs, st_users, st_scored);
+  SAH_CUDA(cudaGetLastError());
+  return SAH_OK;
+}
+
+sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* scratch, const float* qn,
+                            const int32_t* kk, int nq, const uint32_t* kept_mask, int mask_words, uint8_t* tile_need,
+                            uint32_t* bitmap, int64_t words, Survivor* resc, unsigned long long* resc_count,
+                            Survivor* surv, unsigned long long* surv_count, int64_t surv_cap,
+                            unsigned long long* stats, int st_yes, int st_fp64, cudaStream_t st, int* launches,
+                            const cudaEvent_t* ev) {
+  if (ix->m_nz == 0 || nq == 0 || ix->dk <= 0) return SAH_OK;
+  const uint16_t* Qhi = Qsplit;
+  const uint16_t* Qlo = Qsplit + (size_t)nq * ix->dk;
+  const ColTable T = col_table_at(scratch, nq);
   UpParams p{};
   p.mz = ix->m_nz;
   p.n = ix->n;
@@ -1003,7 +1115,7 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
   tile_need_kernel<<<grid_for(p.ntiles, 8), 256, 0, st>>>(ix->ublock, ix->m_nz, kept_mask, mask_words, p.ntiles,
                                                           tile_need);
   SAH_CUDA(cudaGetLastError());
-  if (launches) *launches += 3;
+  if (launches) *launches += 1;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
   if (ix->dk == 64) {
