@@ -538,7 +538,7 @@ verify_exact_kernel(const Survivor* __restrict__ surv, const unsigned long long*
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int dp4 = dp / 4;
   float4* myu = vs4 + warp * dp4;
-  int64_t total = (int64_t)min((unsigned long long)surv_cap, *surv_count);
+  int64_t total = block_count(surv_count, surv_cap);
   int64_t gw = (int64_t)blockIdx.x * kVerifyWarps + warp;
   int64_t nwarps = (int64_t)gridDim.x * kVerifyWarps;
   unsigned long long fp64_cnt = 0, scanned = 0;

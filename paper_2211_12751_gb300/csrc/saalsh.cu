@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kSaWarps * 32) saalsh_decide_kernel(SaParams p
   const int64_t nw = (int64_t)gridDim.x * kSaWarps;
   int32_t* q = queue[warp];
   unsigned long long scored = 0;
-  const int64_t nrows = min((int64_t)*prm.nrows_dev, prm.cap);
+  const int64_t nrows = block_count(prm.nrows_dev, prm.cap);
   for (int64_t r = gw; r < nrows; r += nw) {
     const Survivor S = prm.rows[r];
     const int k = prm.kk[S.j];

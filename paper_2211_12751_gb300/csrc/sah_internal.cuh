@@ -189,6 +189,16 @@ __device__ inline float warp_max(float v) {
   return v;
 }
 
+// A device-side count (a list's length) that the whole block needs, capped at cap: one
+// thread reads it and shares it.  Read by every warp of a large grid, the one word made its
+// L2 line a hot spot.  Every thread of the block must call it (it synchronises the block).
+__device__ inline int64_t block_count(const unsigned long long* c, int64_t cap) {
+  __shared__ long long v;
+  if (threadIdx.x == 0) v = (long long)min((unsigned long long)cap, *c);
+  __syncthreads();
+  return v;
+}
+
 // Sequential double-precision inner product in the order i = 0..d-1.  The product of
 // two floats is exact in double, so this equals the double-precision definition of the
 // count rule bit for bit, whatever the compiler does with the multiply-add.

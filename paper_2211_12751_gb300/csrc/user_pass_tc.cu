@@ -930,8 +930,10 @@ __global__ void pair_rescore_kernel(const Survivor* __restrict__ pairs, const un
                                     int64_t surv_cap, unsigned long long* __restrict__ stats, int st_yes,
                                     int st_fp64, int nq, const int* __restrict__ timeout) {
   // after a timed-out wait of the pass the list may hold unwritten entries: nothing is read
-  if (*(volatile const int*)timeout) return;
-  const int64_t total = min((int64_t)*count, cap);
+  __shared__ int stop;
+  if (threadIdx.x == 0) stop = *(volatile const int*)timeout;
+  const int64_t total = block_count(count, cap);   // synchronises the block
+  if (stop) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const Survivor P = pairs[i];
     const int r = P.upos;

@@ -64,7 +64,7 @@ __global__ void cut_kernel(const Survivor* __restrict__ surv, const unsigned lon
                            int64_t cap, const float* __restrict__ unorm, const float* __restrict__ pnorm, int64_t n,
                            const float* __restrict__ qn, float gamma, int ntiles, int32_t* __restrict__ cut,
                            int32_t* __restrict__ hist) {
-  const int64_t ns = min((int64_t)*count, cap);
+  const int64_t ns = block_count(count, cap);
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ns) return;
   Survivor S = surv[i];
@@ -97,7 +97,7 @@ __global__ void sort_by_cut_kernel(const Survivor* __restrict__ surv, const int3
                                    const unsigned long long* __restrict__ count, int64_t cap,
                                    int32_t* __restrict__ off, Survivor* __restrict__ out_rows,
                                    int32_t* __restrict__ out_cut) {
-  const int64_t ns = min((int64_t)*count, cap);
+  const int64_t ns = block_count(count, cap);
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ns) return;
   int32_t c = cut[i];
@@ -161,7 +161,7 @@ verify_tc_kernel(const __grid_constant__ CUtensorMap tmapP, TcParams prm) {
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t r0 = (int64_t)blockIdx.x * kRows;
-  const int64_t nrows_all = std::min<int64_t>((int64_t)*prm.nrows_dev, prm.cap);
+  const int64_t nrows_all = block_count(prm.nrows_dev, prm.cap);
   if (r0 >= nrows_all) return;                          // the grid is sized for the list's capacity
   const int64_t nrows_cta = std::min<int64_t>(kRows, nrows_all - r0);
   const int T = prm.cut[r0 + nrows_cta - 1];          // rows are sorted by cut: the last needs most
@@ -384,7 +384,7 @@ __global__ void resolve_kernel(const Survivor* __restrict__ rows, const unsigned
                                int64_t words, unsigned long long* __restrict__ fp64_stat,
                                unsigned long long* __restrict__ items_stat) {
   const int lane = threadIdx.x & 31;
-  const int64_t nrows = min((int64_t)*count, cap);
+  const int64_t nrows = block_count(count, cap);
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long fp64 = 0, scanned = 0;
