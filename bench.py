@@ -441,12 +441,17 @@ def main():
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                 "algorithmic_bytes": by}
     elif dom == "kmips_decision" and args.precision == "bf16":
-        # the tcgen05 GEMM: useful BF16 MACs of the rows still open, per launch of the
-        # stage's kernels (the GEMM itself is one of them)
+        # the tcgen05 GEMM of the kMIPS decision: algorithmic flops 2 d per (row, item)
+        # scored before the row was decided (the stage's item count, which also holds the
+        # few FP32 re-scans of rows whose band overflowed); time: the kernel alone (stage
+        # slot 7).  The tensor pipe runs three split-BF16 products over the padded K per
+        # score and whole 128-row tiles, so its own utilisation is higher (ncu).
         kernel = "verify_tc_kernel"
-        roof = {"bound": "tensor", "achieved": per_launch(a["flops"]) / dur_s / 1e12,
+        dur_s = stage_ms[7] / 1e3
+        roof = {"bound": "tensor", "achieved": a["flops"] / dur_s / 1e12,
                 "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json bf16_tflops, burst)"}
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json bf16_tflops, burst)",
+                "algorithmic_flops": a["flops"]}
     else:
         t_alu = a["flops"] / (fp32_peak * 1e12)
         t_hbm = a["bytes"] / (peaks["hbm_gbs"] * 1e9)
@@ -497,6 +502,15 @@ def main():
                     rec.update(value=value, ms_per_step=t_step_ms, user_pass_ms=float(stage_ms[2]),
                                kmips_decision_ms=float(stage_ms[3]), survivors=st["survivors"],
                                items_scanned=st["items_scanned"])
+                if thr == "paper" and prec == "bf16":
+                    # the tcgen05 kMIPS decision kernel alone (stage slot 7): algorithmic
+                    # flops 2 d per (row, item) scored before the row was decided
+                    sm7 = float((stage_ms if same else smv)[7])
+                    items = (st if same else stv)["items_scanned"]
+                    if sm7 > 0:
+                        tf = 2.0 * W.d * items / (sm7 / 1e3) / 1e12
+                        rec["verify_gemm"] = {"kernel": "verify_tc_kernel", "ms": sm7, "tflops_algorithmic": tf,
+                                              "peak_tflops": peaks["bf16_tflops"], "frac": tf / peaks["bf16_tflops"]}
                 if thr == "paper" and not tc:
                     sa_modes = np.full(nq, sah.SAALSH, np.int32)
                     hsa, tsa, _, _, stsa, _ = measure(ixv, vsteps, 3, timing=False, modes=sa_modes)

@@ -169,7 +169,8 @@ typedef struct {
   /* With timing enabled: CUDA-event time (ms) and kernel launches per stage of the last
    * call: [0] query preparation, [1] block pass (A3), [2] user pass (A4), [3] kMIPS
    * decision (A5/A6), [4] answer compaction (A7), [5] SA-ALSH hashing; [6] the tensor-core
-   * user pass's GEMM kernel alone (within [2]). */
+   * user pass's GEMM kernel alone (within [2]); [7] the tensor-core kMIPS decision's GEMM
+   * kernel alone (within [3]). */
   double stage_ms[8];
   int64_t stage_launches[8];
   double build_gemm_ms;         /* index build, |P'| = n with SAH_BF16: the tcgen05 GEMM's time */

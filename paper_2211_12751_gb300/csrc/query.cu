@@ -1084,7 +1084,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
           int nl = 0;
           if (ix->dk > 0) {
             SAH_TRY(run_verify_tc(ix, cx, surv, survcnt, surv_cap, Qd, qn, kk, bitmap, words, stats, ST_FP64, ST_ITEMS,
-                                  st, &nl));
+                                  st, &nl, tm.slot(7)));
           } else {
             const size_t vsmem = (size_t)16 * kVerifyWarps * (ix->dp / 4);
             if (vsmem > 48 * 1024)

@@ -119,9 +119,12 @@ struct Index {
   // BF16 copies for the tensor-core kMIPS decision (precision SAH_BF16), K padded to dk
   int32_t dk = 0;             // roundup(d, 64); 0 when the tensor-core path is off
   uint16_t* Ub = nullptr;     // m_nz x dk, leaf order: bf16(u)
-  uint16_t* Ulo = nullptr;    // m_nz x dk: bf16(u - bf16(u)), the low part for the user pass
+  uint16_t* Ulo = nullptr;    // m_nz x dk: bf16(u - bf16(u)), the low part (user pass, verify)
   uint16_t* Pb = nullptr;     // n x dk, descending norm order
+  uint16_t* Plo = nullptr;    // n x dk: bf16(p - bf16(p)), the low part for the verify pass
   CUtensorMap tmap_P{};       // TMA map of Pb: box 64 x 256, 128-byte swizzle
+  CUtensorMap tmap_Pv{};      // Pb and Plo in the verify pass's tiles: box 64 x 128
+  CUtensorMap tmap_Plo{};
   CUtensorMap tmap_U{};       // TMA map of Ub: box 64 x 128, 128-byte swizzle
   CUtensorMap tmap_Ulo{};     // the same for Ulo
   int* dev_timeout = nullptr; // set by a kernel whose bounded wait ran out
@@ -249,7 +252,7 @@ sah_status build_bf16_copies(Index* ix, cudaStream_t st);
 sah_status run_verify_tc(Index* ix, CallCtx* cx, const Survivor* surv, const unsigned long long* surv_count_dev,
                          int64_t surv_cap, const float* Qd, const float* qn, const int32_t* kk, uint32_t* bitmap,
                          int64_t words, unsigned long long* stats, int stat_fp64, int stat_items,
-                         cudaStream_t st, int* launches);
+                         cudaStream_t st, int* launches, const cudaEvent_t* ev = nullptr);
 // query.cu
 // Alg. 5 for nq queries (Q, ks, modes on the device), with one stream synchronisation
 // per sub-batch.  When out_dev is given and the call fits one sub-batch, the ascending

@@ -934,52 +934,76 @@ __global__ void pair_rescore_kernel(const Survivor* __restrict__ pairs, const un
   if (threadIdx.x == 0) stop = *(volatile const int*)timeout;
   const int64_t total = block_count(count, cap);   // synchronises the block
   if (stop) return;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const Survivor P = pairs[i];
-    const int r = P.upos;
-    const int j = P.j & 0x3fffffff;
-    if (r < 0 || r >= mz || j >= nq) continue;
-    const bool sa_row = (P.j >> 30) & 1;
-    const int k = kk[j];
-    const float4* u4 = reinterpret_cast<const float4*>(Ut + (int64_t)r * dp);
-    const float4* q4 = reinterpret_cast<const float4*>(Qd + (int64_t)j * dp);
+  // warp-strided, so that every lane runs the same iterations and the appends to the
+  // lists and counters go out once per warp
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; w0 < total; w0 += nw * 32) {
+    const int64_t i = w0 + lane;
+    bool yes = false, surv_flag = false, sa_row = false, fp64 = false;
+    int r = 0, j = 0;
     float acc = 0.f;
-    for (int c = 0; c < dp / 4; ++c) {
-      const float4 a = u4[c], b = q4[c];
-      acc = fmaf(a.x, b.x, acc);
-      acc = fmaf(a.y, b.y, acc);
-      acc = fmaf(a.z, b.z, acc);
-      acc = fmaf(a.w, b.w, acc);
-    }
-    const float nu = unorm[r], E = Eu[r];
-    const float L = (k <= kmax) ? Lt[(int64_t)(k - 1) * mz + r] : -INFINITY;
-    const float Llo = (L == -INFINITY) ? -INFINITY : __fsub_rd(L, E);
-    const float eq = __fmul_ru(__fmul_ru(gamma, nu), qn[j]) + 1e-30f;
-    const float hi = __fadd_ru(acc, eq), lo = __fsub_rd(acc, eq);
-    bool yes = false, surv_flag = false;
-    if (hi < Llo) {
-    } else if (l_exact && k <= kmax && lo >= __fadd_ru(L, E)) {
-      yes = true;
-    } else if (lo >= __fmul_ru(__fmul_ru(nu, pnorm[k - 1]), 1.f + 2.f * gamma)) {
-      yes = true;
-    } else if (T64 != nullptr && k <= kmax && !sa_row) {
-      const double t64 = T64[(int64_t)(k - 1) * mz + r];
-      if (t64 == t64) {
-        atomicAdd(&stats[st_fp64], 1ull);
-        yes = dot64_seq(Ut + (int64_t)r * dp, Qd + (int64_t)j * dp, d) >= t64;
-      } else {
-        surv_flag = true;
+    if (i < total) {
+      const Survivor P = pairs[i];
+      r = P.upos;
+      j = P.j & 0x3fffffff;
+      if (r >= 0 && r < mz && j < nq) {
+        sa_row = (P.j >> 30) & 1;
+        const int k = kk[j];
+        const float4* u4 = reinterpret_cast<const float4*>(Ut + (int64_t)r * dp);
+        const float4* q4 = reinterpret_cast<const float4*>(Qd + (int64_t)j * dp);
+        for (int c = 0; c < dp / 4; ++c) {
+          const float4 a = u4[c], b = q4[c];
+          acc = fmaf(a.x, b.x, acc);
+          acc = fmaf(a.y, b.y, acc);
+          acc = fmaf(a.z, b.z, acc);
+          acc = fmaf(a.w, b.w, acc);
+        }
+        const float nu = unorm[r], E = Eu[r];
+        const float L = (k <= kmax) ? Lt[(int64_t)(k - 1) * mz + r] : -INFINITY;
+        const float Llo = (L == -INFINITY) ? -INFINITY : __fsub_rd(L, E);
+        const float eq = __fmul_ru(__fmul_ru(gamma, nu), qn[j]) + 1e-30f;
+        const float hi = __fadd_ru(acc, eq), lo = __fsub_rd(acc, eq);
+        if (hi < Llo) {
+        } else if (l_exact && k <= kmax && lo >= __fadd_ru(L, E)) {
+          yes = true;
+        } else if (lo >= __fmul_ru(__fmul_ru(nu, pnorm[k - 1]), 1.f + 2.f * gamma)) {
+          yes = true;
+        } else if (T64 != nullptr && k <= kmax && !sa_row) {
+          const double t64 = T64[(int64_t)(k - 1) * mz + r];
+          if (t64 == t64) {
+            fp64 = true;
+            yes = dot64_seq(Ut + (int64_t)r * dp, Qd + (int64_t)j * dp, d) >= t64;
+          } else {
+            surv_flag = true;
+          }
+        } else {
+          surv_flag = true;
+        }
       }
-    } else {
-      surv_flag = true;
     }
     if (yes) {
       const int32_t id = uid[r];
       atomicOr(&bitmap[(int64_t)j * words + (id >> 5)], 1u << (id & 31));
-      atomicAdd(&stats[st_yes], 1ull);
-    } else if (surv_flag) {
-      const unsigned long long slot = atomicAdd(surv_count + (sa_row ? 1 : 0), 1ull);
-      if ((int64_t)slot < surv_cap) surv[(sa_row ? surv_cap : 0) + slot] = Survivor{r, j, acc};
+    }
+    const unsigned myes = __ballot_sync(0xffffffffu, yes), mf = __ballot_sync(0xffffffffu, fp64);
+    if (lane == 0) {
+      if (myes) atomicAdd(&stats[st_yes], (unsigned long long)__popc(myes));
+      if (mf) atomicAdd(&stats[st_fp64], (unsigned long long)__popc(mf));
+    }
+#pragma unroll
+    for (int sa = 0; sa < 2; ++sa) {
+      const bool mine = surv_flag && (sa_row == (sa == 1));
+      const unsigned m = __ballot_sync(0xffffffffu, mine);
+      if (m) {
+        unsigned long long b = 0;
+        if (lane == 0) b = atomicAdd(surv_count + sa, (unsigned long long)__popc(m));
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (mine) {
+          const unsigned long long slot = b + __popc(m & ((1u << lane) - 1u));
+          if ((int64_t)slot < surv_cap) surv[(sa ? surv_cap : 0) + slot] = Survivor{r, j, acc};
+        }
+      }
     }
   }
 }
