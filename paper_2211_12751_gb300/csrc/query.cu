@@ -42,7 +42,6 @@ enum StatSlot {
   ST_COUNT
 };
 
-constexpr int kWordsPerChunk = 2048;
 
 inline unsigned grid_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
 
@@ -299,7 +298,7 @@ __global__ void user_scan_kernel(const float* __restrict__ Ut, const float* __re
       }
       if (yes) {
         ++yes_early;
-        atomicOr(&bitmap[(int64_t)j * words + (id >> 5)], 1u << (id & 31));
+        set_answer(bitmap, words, j, id);
       }
       // every record in this loop iteration belongs to one query, so one list per warp step
       const unsigned m = __ballot_sync(0xffffffffu, surv_flag);
@@ -489,7 +488,7 @@ user_scan_reg_kernel(const float* __restrict__ Ut, const float* __restrict__ uno
         }
         if (yes) {
           ++yes_early;
-          atomicOr(&bitmap[(int64_t)j * words + (id >> 5)], 1u << (id & 31));
+          set_answer(bitmap, words, j, id);
         }
         const unsigned m = __ballot_sync(0xffffffffu, surv_flag);
         if (m) {
@@ -610,7 +609,7 @@ verify_exact_kernel(const Survivor* __restrict__ surv, const unsigned long long*
     }
     if (yes && lane == 0) {
       int32_t id = uid[S.upos];
-      atomicOr(&bitmap[(int64_t)S.j * words + (id >> 5)], 1u << (id & 31));
+      set_answer(bitmap, words, S.j, id);
     }
     __syncwarp();
   }
@@ -625,7 +624,7 @@ __global__ void zero_users_kernel(const int32_t* __restrict__ zid, int64_t nz, i
   if (t >= nz * nq) return;
   int j = (int)(t / nz);
   int32_t id = zid[t % nz];
-  atomicOr(&bitmap[(int64_t)j * words + (id >> 5)], 1u << (id & 31));
+  set_answer(bitmap, words, j, id);
 }
 
 __device__ inline int block_exclusive_scan(int v, int* total) {
@@ -649,49 +648,52 @@ __device__ inline int block_exclusive_scan(int v, int* total) {
   return before + x - v;
 }
 
-// chunk_cnt[j][c] = answers of query j among the users of chunk c.
-// Set bits per (chunk, query).  A query with k > n asks for every user: its chunk of the
-// bitmap is filled here.
-__global__ void bitmap_count_kernel(uint32_t* __restrict__ bitmap, int64_t words, int nchunks,
-                                    int32_t* __restrict__ chunk_cnt, const int32_t* __restrict__ kk, int64_t n,
-                                    int64_t m) {
-  int c = blockIdx.x, j = blockIdx.y;
-  int64_t w0 = (int64_t)c * kWordsPerChunk;
-  const bool all = kk[j] > n;
-  int acc = 0;
-  for (int w = threadIdx.x; w < kWordsPerChunk; w += blockDim.x) {
-    int64_t ww = w0 + w;
-    if (ww < words) {
-      uint32_t v;
-      if (all) {
-        const int64_t lo = ww * 32;
-        v = (m - lo) >= 32 ? 0xffffffffu : ((1u << (m - lo)) - 1u);
-        bitmap[(int64_t)j * words + ww] = v;
-      } else {
-        v = bitmap[(int64_t)j * words + ww];
-      }
-      acc += __popc(v);
+// Answers per summary word: one thread per (query j, summary word sw), reading the
+// bitmap words the summary marks (independent loads, all in flight at once).  A query
+// with k > n asks for every user: its words count as full.
+__global__ void answer_count_kernel(const uint32_t* __restrict__ bitmap, int64_t stride, int nq,
+                                    const int32_t* __restrict__ kk, int64_t n, int64_t m,
+                                    int32_t* __restrict__ wcnt) {
+  const int64_t w = answer_words(stride);
+  const int nsw = (int)(w / 32);
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nsw * nq) return;
+  const int j = g / nsw, sw = g - j * nsw;
+  int c = 0;
+  if (kk[j] > n) {
+    c = (int)std::max<int64_t>(0, std::min<int64_t>(1024, m - (int64_t)sw * 1024));
+  } else {
+    const uint32_t* row = bitmap + (int64_t)j * stride;
+    const uint32_t sm = row[w + sw];
+    if (sm) {
+#pragma unroll
+      for (int b = 0; b < 32; ++b)
+        if ((sm >> b) & 1u) c += __popc(row[sw * 32 + b]);
     }
   }
-  acc += __shfl_xor_sync(0xffffffffu, acc, 16);
-  acc += __shfl_xor_sync(0xffffffffu, acc, 8);
-  acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-  __shared__ int ws[32];
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int t = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
-    chunk_cnt[(int64_t)j * nchunks + c] = t;
-  }
+  wcnt[g] = c;
 }
 
-// Per query: exclusive scan over its chunks (one thread per query), then an exclusive
-// scan of the query totals across the CTA; offsets over queries start at base.  One CTA
+// Per query (one CTA): exclusive scan of its summary-word counts in place, total to cnt[j].
+__global__ void answer_scan_kernel(int32_t* __restrict__ wcnt, int64_t nsw, int32_t* __restrict__ cnt) {
+  int32_t* v = wcnt + (int64_t)blockIdx.x * nsw;
+  const int64_t per = (nsw + blockDim.x - 1) / blockDim.x;
+  const int64_t b = std::min<int64_t>((int64_t)threadIdx.x * per, nsw), e = std::min<int64_t>(b + per, nsw);
+  int s = 0;
+  for (int64_t i = b; i < e; ++i) s += v[i];
+  int total;
+  int acc = block_exclusive_scan(s, &total);
+  for (int64_t i = b; i < e; ++i) {
+    const int x = v[i];
+    v[i] = acc;
+    acc += x;
+  }
+  if (threadIdx.x == 0) cnt[blockIdx.x] = total;
+}
+
+// offsets[j] = base + the answers of the queries before j, offsets[nq] the end.  One CTA
 // of 1024 threads.
-__global__ void offsets_kernel(int32_t* __restrict__ chunk_cnt, int nchunks, int nq, int64_t base,
+__global__ void offsets_kernel(const int32_t* __restrict__ cnt, int nq, int64_t base,
                                int64_t* __restrict__ offsets) {
   __shared__ long long warp_tot[32];
   __shared__ long long carry;
@@ -700,14 +702,7 @@ __global__ void offsets_kernel(int32_t* __restrict__ chunk_cnt, int nchunks, int
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int j0 = 0; j0 < nq; j0 += blockDim.x) {
     const int j = j0 + threadIdx.x;
-    long long tot = 0;
-    if (j < nq) {
-      for (int c = 0; c < nchunks; ++c) {
-        const int v = chunk_cnt[(int64_t)j * nchunks + c];
-        chunk_cnt[(int64_t)j * nchunks + c] = (int)tot;
-        tot += v;
-      }
-    }
+    const long long tot = j < nq ? cnt[j] : 0;
     long long x = tot;
     for (int o = 1; o < 32; o <<= 1) {
       const long long y = __shfl_up_sync(0xffffffffu, x, o);
@@ -728,38 +723,48 @@ __global__ void offsets_kernel(int32_t* __restrict__ chunk_cnt, int nchunks, int
   if (threadIdx.x == 0) offsets[nq] = carry;
 }
 
-// Writes the ids only if the call's total fits in out_cap; otherwise raises *overflow.
-__global__ void bitmap_emit_kernel(const uint32_t* __restrict__ bitmap, int64_t words, int nchunks,
-                                   const int32_t* __restrict__ chunk_off, const int64_t* __restrict__ offsets,
-                                   int nq, int32_t* __restrict__ out, int64_t out_cap,
+// Writes the ids of summary word sw of query j (one thread each) at offsets[j] plus the
+// scanned count before it, in ascending order, and clears the words it read, leaving the
+// bitmap zero for the next call.  Only if the call's total fits in out_cap; otherwise it
+// raises *overflow and leaves the bitmap as it is.
+__global__ void answer_emit_kernel(uint32_t* __restrict__ bitmap, int64_t stride, int nq,
+                                   const int32_t* __restrict__ kk, int64_t n, int64_t m,
+                                   const int32_t* __restrict__ wpre, const int64_t* __restrict__ offsets,
+                                   int32_t* __restrict__ out, int64_t out_cap,
                                    unsigned long long* __restrict__ overflow) {
-  int c = blockIdx.x, j = blockIdx.y;
+  const int64_t w = answer_words(stride);
+  const int nsw = (int)(w / 32);
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (offsets[nq] > out_cap) {
-    if (c == 0 && j == 0 && threadIdx.x == 0) atomicExch(overflow, 1ull);
+    if (g == 0) atomicExch(overflow, 1ull);
     return;
   }
-  int64_t w0 = (int64_t)c * kWordsPerChunk;
-  int64_t dst0 = offsets[j] + chunk_off[(int64_t)j * nchunks + c];
-  const int per = kWordsPerChunk / 256;   // words per thread, blockDim = 256
-  uint32_t wv[per];
-  int cnt = 0;
+  if (g >= nsw * nq) return;
+  const int j = g / nsw, sw = g - j * nsw;
+  uint32_t* row = bitmap + (int64_t)j * stride;
+  int64_t dst = offsets[j] + wpre[g];
+  const bool all = kk[j] > n;
+  if (all)
+    for (int64_t i = (int64_t)sw * 1024; i < std::min<int64_t>(m, (int64_t)sw * 1024 + 1024); ++i)
+      out[dst++] = (int32_t)i;
+  const uint32_t sm = row[w + sw];
+  if (!sm) return;
+  uint32_t v[32];
 #pragma unroll
-  for (int q = 0; q < per; ++q) {
-    int64_t ww = w0 + (int64_t)threadIdx.x * per + q;
-    wv[q] = (ww < words) ? bitmap[(int64_t)j * words + ww] : 0u;
-    cnt += __popc(wv[q]);
-  }
-  int total;
-  int pre = block_exclusive_scan(cnt, &total);
-  int64_t dst = dst0 + pre;
+  for (int b = 0; b < 32; ++b) v[b] = ((sm >> b) & 1u) ? row[sw * 32 + b] : 0u;
 #pragma unroll
-  for (int q = 0; q < per; ++q) {
-    uint32_t v = wv[q];
-    int64_t idbase = (w0 + (int64_t)threadIdx.x * per + q) * 32;
-    while (v) {
-      int b = __ffs(v) - 1;
-      out[dst++] = (int32_t)(idbase + b);
-      v &= v - 1;
+  for (int b = 0; b < 32; ++b)
+    if ((sm >> b) & 1u) row[sw * 32 + b] = 0u;
+  row[w + sw] = 0u;
+  if (all) return;
+#pragma unroll
+  for (int b = 0; b < 32; ++b) {
+    uint32_t x = v[b];
+    const int64_t base_id = ((int64_t)sw * 32 + b) * 32;
+    while (x) {
+      const int i = __ffs(x) - 1;
+      x &= x - 1;
+      out[dst++] = (int32_t)(base_id + i);
     }
   }
 }
@@ -775,11 +780,12 @@ struct WsLayout {
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
-WsLayout layout_for(const Index* ix, int qb, int nchunks) {
+WsLayout layout_for(const Index* ix, int qb) {
   WsLayout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes); return r; };
-  int64_t words = (ix->m + 31) / 32;
+  // the answer bitmaps first: the part of the workspace that stays zero between calls
+  L.bitmap = take(sizeof(uint32_t) * (size_t)qb * answer_stride(ix->m));
   L.qd = take(sizeof(float) * (size_t)qb * ix->dp);
   L.qb = take(2 * sizeof(uint16_t) * (size_t)qb * std::max(ix->dk, 1));   // hi and lo parts
   L.qn = take(sizeof(float) * qb);
@@ -790,8 +796,7 @@ WsLayout layout_for(const Index* ix, int qb, int nchunks) {
   L.tneed = take((size_t)std::max<int64_t>((ix->m_nz + 127) / 128, 1));
   L.coltab = take(user_pass_tc_scratch_bytes(qb));
   L.survcnt = take(3 * sizeof(unsigned long long));
-  L.bitmap = take(sizeof(uint32_t) * (size_t)qb * words);
-  L.chunk = take(sizeof(int32_t) * (size_t)qb * nchunks);
+  L.chunk = take(sizeof(int32_t) * (size_t)qb * (answer_words(answer_stride(ix->m)) / 32 + 1));
   L.offsets = take(sizeof(int64_t) * (size_t)(qb + 1));
   L.stats = take(sizeof(unsigned long long) * ST_COUNT);
   L.total = o;
@@ -950,19 +955,18 @@ void free_ctx(CallCtx* cx) {
 size_t ctx_bytes(const CallCtx* cx) { return cx->ws.bytes + cx->surv.bytes + cx->res.bytes + cx->tcws.bytes; }
 
 size_t batch_workspace_bytes(const Index* ix, int32_t nq) {
-  const int64_t words = (ix->m + 31) / 32;
-  const int nchunks = (int)((words + kWordsPerChunk - 1) / kWordsPerChunk);
-  return layout_for(ix, std::max(nq, 1), nchunks).total;
+  return layout_for(ix, std::max(nq, 1)).total;
 }
 
 sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, const int32_t* ks_dev,
                      const int32_t* modes_dev, int32_t* out_dev, int64_t out_cap, int64_t* offsets_dev,
                      int64_t* offsets_host, bool* wrote_out, cudaStream_t st) {
-  const int64_t words = (ix->m + 31) / 32;
-  const int nchunks = (int)((words + kWordsPerChunk - 1) / kWordsPerChunk);
+  // row stride of the answer bitmaps (the kernels that set answers take it as "words")
+  const int64_t words = answer_stride(ix->m);
+  const int64_t nsw = answer_words(words) / 32;   // summary words per query
   // sub-batch size: bounded pair list and bitmap (about 1 GiB together)
   const size_t per_q = sizeof(PairEntry) * (size_t)std::max(ix->nb, 1) + sizeof(uint32_t) * words +
-                       sizeof(int32_t) * nchunks + sizeof(float) * ix->dp + 16;
+                       sizeof(int32_t) * (nsw + 1) + sizeof(float) * ix->dp + 16;
   int qb = (int)std::max<size_t>(1, std::min<size_t>((size_t)nq, (size_t(1) << 30) / per_q));
   qb = std::min(qb, 4096);
   const bool direct = out_dev != nullptr && qb >= nq;   // one sub-batch: emit into the caller's buffer
@@ -983,8 +987,19 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
     const int nqb = std::min(qb, nq - q0);
     const int32_t* modes_q = modes_dev ? modes_dev + q0 : nullptr;
     for (int attempt = 0;; ++attempt) {
-      WsLayout L = layout_for(ix, nqb, nchunks);
+      WsLayout L = layout_for(ix, nqb);
       SAH_TRY(ensure_ws(cx, L.total, st));
+      // the answer bitmaps must start zero: the emit pass of a completed call leaves them
+      // so; after a reallocation, a larger sub-batch or a call that stopped early, clear them
+      const size_t bm_bytes = sizeof(uint32_t) * (size_t)nqb * words;
+      const unsigned ans_grid = (unsigned)((nqb * nsw + 255) / 256);   // a thread per summary word
+      if (cx->bm_clean_base != cx->ws.base || cx->bm_clean_bytes < bm_bytes) {
+        SAH_CUDA(cudaMemsetAsync((char*)cx->ws.base + L.bitmap, 0, bm_bytes, st));
+        cx->bm_clean_base = cx->ws.base;
+        cx->bm_clean_bytes = bm_bytes;
+      }
+      // until this sub-batch has emitted (and so cleared) its answers, nothing is clean
+      cx->bm_clean_bytes = 0;
       SAH_TRY(ensure_surv(cx, surv_cap, st));
       char* w = (char*)cx->ws.base;
       float* Qd = (float*)(w + L.qd);
@@ -1013,13 +1028,11 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
       unsigned long long* st_h = (unsigned long long*)(ob + nqb + 1);
       unsigned long long* ns2 = st_h + ST_COUNT;
       int* timeout_h = (int*)(ns2 + 3);
-      const dim3 gc(nchunks, nqb);
       // every device operation of the attempt, the readback of its results included
       auto enqueue = [&]() -> sah_status {
         tm.begin(0);
         SAH_CUDA(cudaMemsetAsync(stats, 0, sizeof(unsigned long long) * ST_COUNT, st));
         SAH_CUDA(cudaMemsetAsync(survcnt, 0, 3 * sizeof(unsigned long long), st));
-        SAH_CUDA(cudaMemsetAsync(bitmap, 0, sizeof(uint32_t) * (size_t)nqb * words, st));
         SAH_CUDA(cudaMemcpyAsync(kk, ks_dev + q0, sizeof(int32_t) * nqb, cudaMemcpyDeviceToDevice, st));
         prep_queries_kernel<<<grid_for(nqb, 8), 256, 0, st>>>(Q_dev + (int64_t)q0 * ix->d, nqb, ix->d, ix->dp, Qd, qn,
                                                                kk, modes_q, stats);
@@ -1105,14 +1118,17 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
           }
         }
         tm.begin(4);
-        int n_compact = 3;
+        int n_compact = 4;
         if (ix->nzero > 0) {
           zero_users_kernel<<<grid_for(ix->nzero * nqb, 256), 256, 0, st>>>(ix->zero_uid, ix->nzero, nqb, bitmap,
                                                                              words);
           ++n_compact;
         }
-        bitmap_count_kernel<<<gc, 256, 0, st>>>(bitmap, words, nchunks, chunk, kk, ix->n, ix->m);
-        offsets_kernel<<<1, 1024, 0, st>>>(chunk, nchunks, nqb, direct ? 0 : res_total, offsets);
+        // the per-query answer counts go after the per-word counts
+        int32_t* qcnt = chunk + (int64_t)nqb * nsw;
+        answer_count_kernel<<<ans_grid, 256, 0, st>>>(bitmap, words, nqb, kk, ix->n, ix->m, chunk);
+        answer_scan_kernel<<<nqb, 256, 0, st>>>(chunk, nsw, qcnt);
+        offsets_kernel<<<1, 1024, 0, st>>>(qcnt, nqb, direct ? 0 : res_total, offsets);
         int32_t* dst;
         int64_t dst_cap;
         if (direct) {
@@ -1123,8 +1139,8 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
           dst_cap = (int64_t)(cx->res.bytes / sizeof(int32_t));
         }
         if (dst) {
-          bitmap_emit_kernel<<<gc, 256, 0, st>>>(bitmap, words, nchunks, chunk, offsets, nqb, dst, dst_cap,
-                                                 &stats[ST_EMIT_OVERFLOW]);
+          answer_emit_kernel<<<ans_grid, 256, 0, st>>>(bitmap, words, nqb, kk, ix->n, ix->m, chunk, offsets, dst,
+                                                       dst_cap, &stats[ST_EMIT_OVERFLOW]);
         } else {
           SAH_CUDA(cudaMemsetAsync(&stats[ST_EMIT_OVERFLOW], 0xff, sizeof(unsigned long long), st));
         }
@@ -1199,11 +1215,16 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
         if (cx->res.base) cudaFree(cx->res.base);
         cx->res = nr;
         SAH_CUDA(cudaMemsetAsync(&stats[ST_EMIT_OVERFLOW], 0, sizeof(unsigned long long), st));
-        bitmap_emit_kernel<<<gc, 256, 0, st>>>(bitmap, words, nchunks, chunk, offsets, nqb, (int32_t*)cx->res.base,
-                                               (int64_t)(cx->res.bytes / sizeof(int32_t)), &stats[ST_EMIT_OVERFLOW]);
+        answer_emit_kernel<<<ans_grid, 256, 0, st>>>(bitmap, words, nqb, kk, ix->n, ix->m, chunk, offsets,
+                                                     (int32_t*)cx->res.base,
+                                                     (int64_t)(cx->res.bytes / sizeof(int32_t)),
+                                                     &stats[ST_EMIT_OVERFLOW]);
         SAH_CUDA(cudaGetLastError());
         SAH_CUDA(cudaStreamSynchronize(st));
       }
+      // the emit pass has read and cleared every answer of the sub-batch
+      cx->bm_clean_base = cx->ws.base;
+      cx->bm_clean_bytes = bm_bytes;
       agg.survivors += (int64_t)(ns2[0] + ns2[1]);
       agg.pairs_rescored += (int64_t)ns2[2];
       cx->surv_hint = std::max<int64_t>(1 << 16, 2 * nsmax);

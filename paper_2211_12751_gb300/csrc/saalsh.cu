@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(kSaWarps * 32) saalsh_decide_kernel(SaParams p
     }
     if (yes && lane == 0) {
       const int32_t id = prm.uid[S.upos];
-      atomicOr(&prm.bitmap[(int64_t)S.j * prm.words + (id >> 5)], 1u << (id & 31));
+      set_answer(prm.bitmap, prm.words, S.j, id);
     }
   }
   for (int o = 16; o > 0; o >>= 1) scored += __shfl_xor_sync(0xffffffffu, scored, o);

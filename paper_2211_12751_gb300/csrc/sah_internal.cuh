@@ -71,6 +71,10 @@ struct CallCtx {
   std::vector<GraphEntry> graphs;
   uint64_t graph_clock = 0;
   bool graphs_allowed = false;   // the index's own context; the server's workers run directly
+  // the answer bitmaps sit at the start of ws; this many bytes of it are known to be zero
+  // (the emit pass clears what it reads), valid while ws.base equals bm_clean_base
+  void* bm_clean_base = nullptr;
+  size_t bm_clean_bytes = 0;
 };
 
 void free_ctx(CallCtx* cx);
@@ -200,6 +204,24 @@ __device__ inline int64_t block_count(const unsigned long long* c, int64_t cap) 
   if (threadIdx.x == 0) v = (long long)min((unsigned long long)cap, *c);
   __syncthreads();
   return v;
+}
+
+// Answer bitmaps.  Per query one row of answer_stride(m) 32-bit words: w = ceil(m / 32)
+// rounded up to a multiple of 32 words whose bit (id & 31) of word (id >> 5) marks user id,
+// then w / 32 summary words whose bit i marks a nonzero word i, so that counting and
+// emitting visit only the words that hold answers.
+__host__ __device__ inline int64_t answer_stride(int64_t m) {
+  const int64_t w = ((m + 31) / 32 + 31) / 32 * 32;
+  return w + w / 32;
+}
+__host__ __device__ inline int64_t answer_words(int64_t stride) { return (int64_t)((uint64_t)stride / 33 * 32); }
+
+// Both ORs are reductions the thread does not wait for.
+__device__ __forceinline__ void set_answer(uint32_t* bitmap, int64_t stride, int j, int32_t id) {
+  uint32_t* row = bitmap + (int64_t)j * stride;
+  const int wi = id >> 5;
+  atomicOr(&row[wi], 1u << (id & 31));
+  atomicOr(&row[answer_words(stride) + (wi >> 5)], 1u << (wi & 31));
 }
 
 // Sequential double-precision inner product in the order i = 0..d-1.  The product of

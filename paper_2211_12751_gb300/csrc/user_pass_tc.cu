@@ -364,11 +364,6 @@ __device__ __forceinline__ void tmem_ld32_wait(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// *addr |= v without a returned value (a reduction the thread does not wait for)
-__device__ __forceinline__ void red_or(uint32_t* addr, uint32_t v) {
-  asm volatile("red.global.or.b32 [%0], %1;" ::"l"(addr), "r"(v) : "memory");
-}
-
 // one FP32 column of this thread's TMEM lane, waited for
 __device__ __forceinline__ float tmem_ld1_wait(uint32_t taddr) {
   uint32_t r;
@@ -857,7 +852,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
                   yes = lo >= __fadd_ru(__fadd_ru(Lq, 2.f * E_), __fmaf_ru(fabsf(Lq), 0x1p-21f, 2e-30f));
                 if (yes) {
                   ++yes_cnt;
-                  red_or(&p.bitmap[(int64_t)j * p.words + (id_ >> 5)], 1u << (id_ & 31));
+                  set_answer(p.bitmap, p.words, j, id_);
                 } else {
                   push_open((int32_t)r_, rw.x);
                 }
@@ -984,7 +979,7 @@ __global__ void pair_rescore_kernel(const Survivor* __restrict__ pairs, const un
     }
     if (yes) {
       const int32_t id = uid[r];
-      atomicOr(&bitmap[(int64_t)j * words + (id >> 5)], 1u << (id & 31));
+      set_answer(bitmap, words, j, id);
     }
     const unsigned myes = __ballot_sync(0xffffffffu, yes), mf = __ballot_sync(0xffffffffu, fp64);
     if (lane == 0) {

@@ -228,23 +228,33 @@ struct TcParams {
   int32_t* band_items;
   unsigned long long* items_stat;
   int* timeout;
+  // phase of the scan: tiles [t_begin, t_end) for the rows of list (positions in the
+  // cut-sorted rows; all rows in order when list is null).  A row that is still open at
+  // t_end keeps its counts in certain_out / band_out and sets its flag.
+  const int32_t* list;
+  int t_begin, t_end;
+  uint8_t* flags;
 };
 
-// One CTA per 128 survivor rows.  Warp 0 (one thread) streams the item tiles by TMA,
-// warp 1 (one thread) issues the MMAs, warps 2-5 read the scores from TMEM, one thread
-// per row.  Operands are split: A = (u_hi, u_lo) gathered from the BF16 copies of the
-// users, B = (p_hi, p_lo) tiles of the items, and every K block accumulates
-// u_hi p_hi + u_hi p_lo + u_lo p_hi into the tile's TMEM slot (two slots alternate, so
-// the MMAs of tile t+1 run while tile t is read).
+// Persistent: a CTA takes row blocks blockIdx.x, blockIdx.x + gridDim.x, ... (128 survivor
+// rows each).  Warp 0 (one thread) streams the item tiles by TMA, warp 1 (one thread)
+// issues the MMAs, warps 2-5 read the scores from TMEM, one thread per row.  Operands are
+// split: A = (u_hi, u_lo) gathered from the BF16 copies of the users, B = (p_hi, p_lo)
+// tiles of the items, and every K block accumulates u_hi p_hi + u_hi p_lo + u_lo p_hi into
+// the tile's TMEM slot (two slots alternate, so the MMAs of tile t+1 run while tile t is
+// read).  The barriers are set up once; stages and slots run on counters across blocks
+// (P tiles streamed, M tiles consumed, C tiles computed, E tiles read), and at the end of a
+// block the epilogue also takes the (at most two) computed tiles it did not need, so the
+// counters stay in step and the A buffer is free for the next block.
 template <int KB, int STAGES, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB)
 verify_tc_kernel(const __grid_constant__ CUtensorMap tmapPhi, const __grid_constant__ CUtensorMap tmapPlo,
                  TcParams prm) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], tfull_bar[2], tempty_bar[2], done_bar,
-      a_bar;
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], tfull_bar[2], tempty_bar[2], a_bar;
   __shared__ uint32_t tmem_base_sh;
-  __shared__ volatile int stop_flag, p_issued, p_done;
+  __shared__ volatile int stop_flag, p_issued, p_done, quit_sh;
+  __shared__ volatile uint32_t c_sh;
 
   constexpr uint32_t kABytes = kRows * 128;          // one 64-wide K block of A (hi or lo)
   constexpr uint32_t kBBytes = kTileN * 128;         // one 64-wide K block of a B tile (hi or lo)
@@ -253,11 +263,8 @@ verify_tc_kernel(const __grid_constant__ CUtensorMap tmapPhi, const __grid_const
   uint8_t* sB = base + 2 * KB * kABytes;             // [stage][hi | lo][KB]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t r0 = (int64_t)blockIdx.x * kRows;
   const int64_t nrows_all = block_count(prm.nrows_dev, prm.cap);
-  if (r0 >= nrows_all) return;                          // the grid is sized for the list's capacity
-  const int64_t nrows_cta = std::min<int64_t>(kRows, nrows_all - r0);
-  const int T = prm.cut[r0 + nrows_cta - 1];          // rows are sorted by cut: the last needs most
+  if ((int64_t)blockIdx.x * kRows >= nrows_all) return;   // no block for this CTA
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -268,241 +275,397 @@ verify_tc_kernel(const __grid_constant__ CUtensorMap tmapPhi, const __grid_const
       tc::mbar_init(&tfull_bar[a], 1);
       tc::mbar_init(&tempty_bar[a], 4);
     }
-    tc::mbar_init(&done_bar, 1);
     tc::mbar_init(&a_bar, 128);                      // every epilogue thread, once its row is in place
     stop_flag = 0;
     p_issued = 0;
     p_done = 0;
+    quit_sh = 0;
+    c_sh = 0;
     tc::fence_mbar_init();
   }
   if (warp == 0) {
     tc::tmem_alloc(&tmem_base_sh, kTmemCols);
     tc::tmem_relinquish();
   }
-  // The item tiles do not depend on the rows: the producer starts streaming them while
-  // the epilogue warps gather the A operand.
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tbase = tmem_base_sh;
+  if (warp == 0 && lane == 0) {
+    tc::prefetch_tensormap(&tmapPhi);
+    tc::prefetch_tensormap(&tmapPlo);
+  }
 
-  if (warp == 0) {
-    // ------------------------------------------------ TMA producer
-    if (lane == 0) {
-      tc::prefetch_tensormap(&tmapPhi);
-      tc::prefetch_tensormap(&tmapPlo);
-      int issued = 0;
-      for (int t = 0; t < T; ++t) {
-        const int s = t % STAGES;
-        if (t >= STAGES && !tc::mbar_wait(&empty_bar[s], ((t / STAGES) & 1) ^ 1, prm.timeout, nullptr)) break;
-        if (stop_flag) break;
-        tc::mbar_arrive_expect_tx(&full_bar[s], 2 * KB * kBBytes);
-        uint8_t* dst = sB + (size_t)s * 2 * KB * kBBytes;
-        for (int kb = 0; kb < KB; ++kb) {
-          tc::tma_load_2d(dst + kb * kBBytes, &tmapPhi, &full_bar[s], kb * 64, t * kTileN);
-          tc::tma_load_2d(dst + (KB + kb) * kBBytes, &tmapPlo, &full_bar[s], kb * 64, t * kTileN);
+  uint32_t P = 0, M = 0, C = 0, E = 0;               // running counters (each kept by its role)
+  int it = 0;                                        // blocks done by this CTA
+  const int t0 = prm.t_begin;
+  for (int64_t blk = blockIdx.x; blk * kRows < nrows_all; blk += gridDim.x, ++it) {
+    const int64_t r0 = blk * kRows;
+    const int64_t nrows_cta = std::min<int64_t>(kRows, nrows_all - r0);
+    // rows are sorted by cut (lists keep that order): the last needs most
+    const int64_t last = prm.list ? prm.list[r0 + nrows_cta - 1] : r0 + nrows_cta - 1;
+    const int T = std::max(t0, std::min(prm.cut[last], prm.t_end));
+
+    // The item tiles do not depend on the rows: the producer streams them while the
+    // epilogue warps gather the A operand.
+    if (warp == 0) {
+      // ------------------------------------------------ TMA producer
+      if (lane == 0) {
+        int issued = 0;
+        for (int i = 0; i < T - t0; ++i, ++P) {       // item tile t0 + i
+          const uint32_t s = P % STAGES;
+          if (P >= STAGES && !tc::mbar_wait(&empty_bar[s], ((P / STAGES) & 1) ^ 1, prm.timeout, nullptr)) break;
+          if (stop_flag) break;
+          tc::mbar_arrive_expect_tx(&full_bar[s], 2 * KB * kBBytes);
+          uint8_t* dst = sB + (size_t)s * 2 * KB * kBBytes;
+          const int y = (t0 + i) * kTileN;
+          for (int kb = 0; kb < KB; ++kb) {
+            tc::tma_load_2d(dst + kb * kBBytes, &tmapPhi, &full_bar[s], kb * 64, y);
+            tc::tma_load_2d(dst + (KB + kb) * kBBytes, &tmapPlo, &full_bar[s], kb * 64, y);
+          }
+          issued = i + 1;
         }
-        issued = t + 1;
+        p_issued = issued;
+        __threadfence_block();
+        p_done = 1;
       }
-      p_issued = issued;
-      __threadfence_block();
-      p_done = 1;
-    }
-  } else if (warp == 1) {
-    // ------------------------------------------------ MMA issuer
-    if (lane == 0) {
-      constexpr uint32_t idesc = tc::idesc_bf16_f32(kRows, kTileN);
-      const uint32_t a_addr = tc::smem_addr(sA);
-      const uint32_t b_addr = tc::smem_addr(sB);
-      if (!tc::mbar_wait(&a_bar, 0, prm.timeout, nullptr)) stop_flag = 1;
-      for (int t = 0;; ++t) {
-        const int s = t % STAGES, a = t & 1;
-        bool got = false, finished = false;
-        for (uint32_t i = 0; i < tc::kSpinLimit; ++i) {
-          if (tc::mbar_try_wait(&full_bar[s], (t / STAGES) & 1)) {
-            got = true;
+    } else if (warp == 1) {
+      // ------------------------------------------------ MMA issuer
+      if (lane == 0) {
+        constexpr uint32_t idesc = tc::idesc_bf16_f32(kRows, kTileN);
+        const uint32_t a_addr = tc::smem_addr(sA);
+        const uint32_t b_addr = tc::smem_addr(sB);
+        if (!tc::mbar_wait(&a_bar, it & 1, prm.timeout, nullptr)) stop_flag = 1;
+        for (int i = 0;; ++i) {                       // the block's i-th tile
+          const uint32_t s = M % STAGES;
+          bool got = false, finished = false;
+          for (uint32_t w = 0; w < tc::kSpinLimit; ++w) {
+            if (tc::mbar_try_wait(&full_bar[s], (M / STAGES) & 1)) {
+              got = true;
+              break;
+            }
+            if (p_done && i >= p_issued) {
+              finished = true;
+              break;
+            }
+            if (w % tc::kFlagEvery == tc::kFlagEvery - 1 && *(volatile int*)prm.timeout) break;
+            if (w > 32) __nanosleep(32);
+          }
+          if (!got) {
+            if (!finished && !*(volatile int*)prm.timeout) atomicExch(prm.timeout, 1);
             break;
           }
-          if (p_done && t >= p_issued) {
-            finished = true;
-            break;
+          ++M;
+          const uint32_t a = C & 1;
+          bool do_mma = !stop_flag;
+          if (do_mma && C >= 2)
+            do_mma = tc::mbar_wait(&tempty_bar[a], ((C >> 1) & 1) ^ 1, prm.timeout, &stop_flag);
+          if (do_mma) {
+            tc::tc_fence_after();
+            const uint32_t bs = b_addr + s * 2 * KB * kBBytes;
+#pragma unroll
+            for (int kb = 0; kb < KB; ++kb)
+#pragma unroll
+              for (int k16 = 0; k16 < 4; ++k16) {
+                const uint64_t ah = tc::sw128_kmajor_desc(a_addr + kb * kABytes + k16 * 32);
+                const uint64_t al = tc::sw128_kmajor_desc(a_addr + (KB + kb) * kABytes + k16 * 32);
+                const uint64_t bh = tc::sw128_kmajor_desc(bs + kb * kBBytes + k16 * 32);
+                const uint64_t bl = tc::sw128_kmajor_desc(bs + (KB + kb) * kBBytes + k16 * 32);
+                const uint32_t d = tbase + a * kTileN;
+                tc::umma_bf16(d, ah, bh, idesc, (kb | k16) ? 1u : 0u);
+                tc::umma_bf16(d, ah, bl, idesc, 1u);
+                tc::umma_bf16(d, al, bh, idesc, 1u);
+              }
+            tc::umma_commit(&empty_bar[s]);
+            tc::umma_commit(&tfull_bar[a]);
+            ++C;
+          } else {
+            tc::mbar_arrive(&empty_bar[s]);
           }
-          if (i % tc::kFlagEvery == tc::kFlagEvery - 1 && *(volatile int*)prm.timeout) break;
-          if (i > 32) __nanosleep(32);
         }
-        if (!got) {
-          if (!finished && !*(volatile int*)prm.timeout) atomicExch(prm.timeout, 1);
+        c_sh = C;
+      }
+    } else {
+      // ------------------------------------------------ epilogue: one thread per row
+      const int quad = warp & 3;                  // TMEM lanes this warp may read
+      const int row = quad * 32 + lane;
+      const bool valid = row < nrows_cta;
+      const int64_t gi = !valid ? 0 : prm.list ? (int64_t)prm.list[r0 + row] : r0 + row;
+      Survivor S{};
+      if (valid) S = prm.rows[gi];
+      {
+        // A operand: this thread's survivor row (high and low parts) into the
+        // 128-byte-swizzled K-major layout
+        uint4 vh[KB * 8], vl[KB * 8];
+        const int64_t off = (int64_t)S.upos * prm.dk;
+#pragma unroll
+        for (int c = 0; c < KB * 8; ++c) {
+          vh[c] = valid ? *reinterpret_cast<const uint4*>(prm.Ub + off + c * 8) : make_uint4(0u, 0u, 0u, 0u);
+          vl[c] = valid ? *reinterpret_cast<const uint4*>(prm.Ulo + off + c * 8) : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int c = 0; c < KB * 8; ++c) {
+          const int kb = c / 8;
+          *reinterpret_cast<uint4*>(sA + kb * kABytes + tc::sw128_offset(row, c % 8)) = vh[c];
+          *reinterpret_cast<uint4*>(sA + (KB + kb) * kABytes + tc::sw128_offset(row, c % 8)) = vl[c];
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc::mbar_arrive(&a_bar);
+      }
+      int k = 0, cut_r = 0;
+      float nu = 0.f, hi = 0.f, lo = 0.f;
+      if (valid) {
+        k = prm.kk[S.j];
+        cut_r = prm.cut[gi];
+        nu = prm.unorm[S.upos];
+        float eq = __fmul_ru(__fmul_ru(prm.gamma, nu), prm.qn[S.j]) + 1e-30f;
+        hi = __fadd_ru(S.sq, eq);
+        lo = __fsub_rd(S.sq, eq);
+      }
+      const float cbu = __fmul_ru(prm.cbf, nu);
+      float pn_next = T > t0 ? prm.pnorm[(int64_t)t0 * kTileN] : 0.f;
+      int certain = 0, band = 0;
+      if (valid && prm.list) {
+        certain = prm.certain_out[gi];
+        band = prm.band_out[gi];
+      }
+      bool decided = !valid || band > kBandCap, failed = false;
+      unsigned long long scanned = 0;
+      for (int t = t0; t < T; ++t) {
+        const uint32_t a = E & 1;
+        if (!failed && !tc::mbar_wait(&tfull_bar[a], (E >> 1) & 1, prm.timeout, nullptr)) {
+          failed = true;
+          stop_flag = 1;
+        }
+        ++E;
+        tc::tc_fence_after();
+        const bool need = !failed && !decided && t < cut_r;
+        const float pn_tile = pn_next;                       // ||p|| of the tile's first (largest) item
+        if (t + 1 < T) pn_next = prm.pnorm[(int64_t)(t + 1) * kTileN];
+        if (__any_sync(0xffffffffu, need)) {
+          // every item of the tile has ||p|| <= pn_tile, so E_t bounds its score error
+          const float Et = __fmul_ru(cbu, pn_tile) + 1e-30f;
+          const float thb = __fsub_rd(lo, Et);               // at or below: certainly not above <u,q>
+          const float thc = __fadd_ru(hi, Et);               // above: certainly above <u,q>
+          const int ncols = (int)std::min<int64_t>(kTileN, prm.n - (int64_t)t * kTileN);
+          if (need) scanned += ncols;
+          const uint32_t taddr = tbase + ((uint32_t)(quad * 32) << 16) + a * kTileN;
+          // the maximum of every group of 32 items: a group whose maximum is at or below
+          // the band holds no item that counts
+          float gmax[kTileN / 32];
+          {
+            float v[kTileN];
+            tc::tmem_ld128(taddr, v);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int c0 = 0; c0 < kTileN; c0 += 32) {
+              float g[11];
+#pragma unroll
+              for (int i = 0; i < 10; ++i) g[i] = max3(v[c0 + 3 * i], v[c0 + 3 * i + 1], v[c0 + 3 * i + 2]);
+              g[10] = fmaxf(v[c0 + 30], v[c0 + 31]);
+              gmax[c0 / 32] = max3(max3(g[0], g[1], g[2]), max3(g[3], g[4], g[5]),
+                                   max3(max3(g[6], g[7], g[8]), g[9], g[10]));
+            }
+          }
+          // the few groups that hold such an item (for some row of the warp) are read
+          // again from TMEM under a warp-uniform branch; items are classified into masks
+          uint32_t mine = 0;
+#pragma unroll
+          for (int j = 0; j < kTileN / 32; ++j) mine |= (need && gmax[j] > thb) ? 1u << j : 0u;
+          uint32_t todo = __reduce_or_sync(0xffffffffu, mine);
+          while (todo) {
+            const int gi32 = __ffs(todo) - 1;
+            todo &= todo - 1;
+            float w[32];
+            tc::tmem_ld32(taddr + gi32 * 32, w);
+            tc::tmem_ld_wait();
+            if ((mine >> gi32) & 1u) {
+              uint32_t above = 0, inband = 0;
+#pragma unroll
+              for (int i = 0; i < 32; ++i) {
+                above |= (w[i] > thc) ? 1u << i : 0u;
+                inband |= (w[i] > thb) ? 1u << i : 0u;
+              }
+              const int left = ncols - gi32 * 32;           // items of the group inside P
+              const uint32_t inside = left >= 32 ? 0xffffffffu : left <= 0 ? 0u : (1u << left) - 1u;
+              above &= inside;
+              inband &= inside & ~above;
+              certain += __popc(above);
+              while (inband) {
+                const int i = __ffs(inband) - 1;
+                inband &= inband - 1;
+                if (band < kBandCap) prm.band_items[gi * kBandCap + band] = t * kTileN + gi32 * 32 + i;
+                ++band;
+              }
+            }
+          }
+          // a row whose band overflowed is re-scanned whole by the resolve pass
+          if (need && (certain >= k || band > kBandCap)) decided = true;
+        }
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&tempty_bar[a]);
+        const bool row_done = failed || decided || (t + 1 >= cut_r);
+        if (epilogue_all(row_done)) {
+          if (t + 1 < T) stop_flag = 1;
           break;
         }
-        bool do_mma = !stop_flag;
-        if (do_mma && t >= 2)
-          do_mma = tc::mbar_wait(&tempty_bar[a], ((t >> 1) & 1) ^ 1, prm.timeout, &stop_flag);
-        if (do_mma) {
-          tc::tc_fence_after();
-          const uint32_t bs = b_addr + (uint32_t)s * 2 * KB * kBBytes;
-#pragma unroll
-          for (int kb = 0; kb < KB; ++kb)
-#pragma unroll
-            for (int k16 = 0; k16 < 4; ++k16) {
-              const uint64_t ah = tc::sw128_kmajor_desc(a_addr + kb * kABytes + k16 * 32);
-              const uint64_t al = tc::sw128_kmajor_desc(a_addr + (KB + kb) * kABytes + k16 * 32);
-              const uint64_t bh = tc::sw128_kmajor_desc(bs + kb * kBBytes + k16 * 32);
-              const uint64_t bl = tc::sw128_kmajor_desc(bs + (KB + kb) * kBBytes + k16 * 32);
-              const uint32_t d = tbase + a * kTileN;
-              tc::umma_bf16(d, ah, bh, idesc, (kb | k16) ? 1u : 0u);
-              tc::umma_bf16(d, ah, bl, idesc, 1u);
-              tc::umma_bf16(d, al, bh, idesc, 1u);
-            }
-          tc::umma_commit(&empty_bar[s]);
-          tc::umma_commit(&tfull_bar[a]);
-        } else {
-          tc::mbar_arrive(&empty_bar[s]);
+      }
+      if (valid) {
+        // open: not decided, and items before the row's cut lie beyond this phase
+        const bool open = !failed && certain < k && band <= kBandCap && cut_r > prm.t_end;
+        if (!open) {
+          int32_t st;
+          if (certain >= k) st = ROW_NO;
+          else if (failed) st = ROW_FULL;
+          else if (certain + band < k) st = ROW_YES;
+          else if (band <= kBandCap) st = ROW_BAND;
+          else st = ROW_FULL;
+          prm.status[gi] = st;
         }
+        prm.certain_out[gi] = certain;
+        prm.band_out[gi] = band;
+        prm.flags[gi] = open ? 1 : 0;
       }
-      tc::umma_commit(&done_bar);
+      for (int o = 16; o > 0; o >>= 1) scanned += __shfl_xor_sync(0xffffffffu, scanned, o);
+      if (lane == 0 && scanned) atomicAdd(prm.items_stat, scanned);
     }
-  } else {
-    // ------------------------------------------------ epilogue: one thread per row
-    const int quad = warp & 3;                  // TMEM lanes this warp may read
-    const int row = quad * 32 + lane;
-    const int64_t gi = r0 + row;
-    const bool valid = row < nrows_cta;
-    Survivor S{};
-    if (valid) S = prm.rows[gi];
-    {
-      // A operand: this thread's survivor row (high and low parts) into the
-      // 128-byte-swizzled K-major layout
-      uint4 vh[KB * 8], vl[KB * 8];
-      const int64_t off = (int64_t)S.upos * prm.dk;
-#pragma unroll
-      for (int c = 0; c < KB * 8; ++c) {
-        vh[c] = valid ? *reinterpret_cast<const uint4*>(prm.Ub + off + c * 8) : make_uint4(0u, 0u, 0u, 0u);
-        vl[c] = valid ? *reinterpret_cast<const uint4*>(prm.Ulo + off + c * 8) : make_uint4(0u, 0u, 0u, 0u);
-      }
-#pragma unroll
-      for (int c = 0; c < KB * 8; ++c) {
-        const int kb = c / 8;
-        *reinterpret_cast<uint4*>(sA + kb * kABytes + tc::sw128_offset(row, c % 8)) = vh[c];
-        *reinterpret_cast<uint4*>(sA + (KB + kb) * kABytes + tc::sw128_offset(row, c % 8)) = vl[c];
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      tc::mbar_arrive(&a_bar);
-    }
-    int k = 0, cut_r = 0;
-    float nu = 0.f, hi = 0.f, lo = 0.f;
-    if (valid) {
-      k = prm.kk[S.j];
-      cut_r = prm.cut[gi];
-      nu = prm.unorm[S.upos];
-      float eq = __fmul_ru(__fmul_ru(prm.gamma, nu), prm.qn[S.j]) + 1e-30f;
-      hi = __fadd_ru(S.sq, eq);
-      lo = __fsub_rd(S.sq, eq);
-    }
-    const float cbu = __fmul_ru(prm.cbf, nu);
-    float pn_next = T > 0 ? prm.pnorm[0] : 0.f;
-    int certain = 0, band = 0;
-    bool decided = !valid, failed = false;
-    unsigned long long scanned = 0;
-    for (int t = 0; t < T; ++t) {
-      const int a = t & 1;
-      if (!failed && !tc::mbar_wait(&tfull_bar[a], (t >> 1) & 1, prm.timeout, nullptr)) {
-        failed = true;
-        stop_flag = 1;
-      }
-      tc::tc_fence_after();
-      const bool need = !failed && !decided && t < cut_r;
-      const float pn_tile = pn_next;                       // ||p|| of the tile's first (largest) item
-      if (t + 1 < T) pn_next = prm.pnorm[(int64_t)(t + 1) * kTileN];
-      if (__any_sync(0xffffffffu, need)) {
-        // every item of the tile has ||p|| <= pn_tile, so E bounds its score error
-        const float E = __fmul_ru(cbu, pn_tile) + 1e-30f;
-        const float thb = __fsub_rd(lo, E);                // at or below: certainly not above <u,q>
-        const float thc = __fadd_ru(hi, E);                // above: certainly above <u,q>
-        const int ncols = (int)std::min<int64_t>(kTileN, prm.n - (int64_t)t * kTileN);
-        if (need) scanned += ncols;
-        const uint32_t taddr = tbase + ((uint32_t)(quad * 32) << 16) + a * kTileN;
-        // the maximum of every group of 32 items: a group whose maximum is at or below
-        // the band holds no item that counts
-        float gmax[kTileN / 32];
-        {
-          float v[kTileN];
-          tc::tmem_ld128(taddr, v);
-          tc::tmem_ld_wait();
-#pragma unroll
-          for (int c0 = 0; c0 < kTileN; c0 += 32) {
-            float g[11];
-#pragma unroll
-            for (int i = 0; i < 10; ++i) g[i] = max3(v[c0 + 3 * i], v[c0 + 3 * i + 1], v[c0 + 3 * i + 2]);
-            g[10] = fmaxf(v[c0 + 30], v[c0 + 31]);
-            gmax[c0 / 32] = max3(max3(g[0], g[1], g[2]), max3(g[3], g[4], g[5]),
-                                 max3(max3(g[6], g[7], g[8]), g[9], g[10]));
-          }
+    tc::tc_fence_before();
+    __syncthreads();
+    // every role is done with the block: the epilogue takes the tiles computed after its
+    // rows had finished (their MMAs complete before the next block's rows replace A), and
+    // the per-block flags are reset
+    if (warp >= 2) {
+      const uint32_t c = c_sh;
+      if (lane == 0)
+        for (uint32_t e = E; e < c; ++e) {
+          if (!tc::mbar_wait(&tfull_bar[e & 1], (e >> 1) & 1, prm.timeout, nullptr)) break;
+          tc::mbar_arrive(&tempty_bar[e & 1]);
         }
-        // the few groups that hold such an item (for some row of the warp) are read again
-        // from TMEM under a warp-uniform branch; the items are classified into bit masks
-        uint32_t mine = 0;
-#pragma unroll
-        for (int j = 0; j < kTileN / 32; ++j) mine |= (need && gmax[j] > thb) ? 1u << j : 0u;
-        uint32_t todo = __reduce_or_sync(0xffffffffu, mine);
-        while (todo) {
-          const int gi32 = __ffs(todo) - 1;
-          todo &= todo - 1;
-          float w[32];
-          tc::tmem_ld32(taddr + gi32 * 32, w);
-          tc::tmem_ld_wait();
-          if ((mine >> gi32) & 1u) {
-            uint32_t above = 0, inband = 0;
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              above |= (w[i] > thc) ? 1u << i : 0u;
-              inband |= (w[i] > thb) ? 1u << i : 0u;
-            }
-            const int left = ncols - gi32 * 32;           // items of the group inside P
-            const uint32_t valid = left >= 32 ? 0xffffffffu : left <= 0 ? 0u : (1u << left) - 1u;
-            above &= valid;
-            inband &= valid & ~above;
-            certain += __popc(above);
-            while (inband) {
-              const int i = __ffs(inband) - 1;
-              inband &= inband - 1;
-              if (band < kBandCap) prm.band_items[gi * kBandCap + band] = t * kTileN + gi32 * 32 + i;
-              ++band;
-            }
-          }
-        }
-        if (need && certain >= k) decided = true;
-      }
-      tc::tc_fence_before();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&tempty_bar[a]);
-      const bool row_done = failed || decided || (t + 1 >= cut_r);
-      if (epilogue_all(row_done)) {
-        if (t + 1 < T) stop_flag = 1;
-        break;
-      }
+      E = c;
     }
-    if (valid) {
-      int32_t st;
-      if (certain >= k) st = ROW_NO;
-      else if (failed) st = ROW_FULL;
-      else if (certain + band < k) st = ROW_YES;
-      else if (band <= kBandCap) st = ROW_BAND;
-      else st = ROW_FULL;
-      prm.status[gi] = st;
-      prm.certain_out[gi] = certain;
-      prm.band_out[gi] = band;
+    if (threadIdx.x == 0) {
+      stop_flag = 0;
+      p_issued = 0;
+      p_done = 0;
+      quit_sh = *(volatile int*)prm.timeout;
     }
-    for (int o = 16; o > 0; o >>= 1) scanned += __shfl_xor_sync(0xffffffffu, scanned, o);
-    if (lane == 0 && scanned) atomicAdd(prm.items_stat, scanned);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    if (quit_sh) break;
   }
-  tc::tc_fence_before();
-  __syncthreads();
   if (warp == 0) {
-    if (lane == 0) tc::mbar_wait(&done_bar, 0, prm.timeout, nullptr);
-    __syncwarp();
     tc::tc_fence_after();
     tc::tmem_dealloc(tbase, kTmemCols);
   }
+}
+
+// Positions (in the cut-sorted rows) of the rows whose flag is set, in ascending order,
+// so that the next phase's list stays sorted by cut: per-block counts, then each block
+// places its rows after those of the blocks before it.
+constexpr int kCompactPer = 8192;   // rows per block: 8 consecutive rows per thread
+
+__device__ __forceinline__ int32_t block_sum_1024(int32_t v, int32_t* sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  int32_t t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  __syncthreads();
+  return t;
+}
+
+__device__ __forceinline__ uint32_t flags8(const uint8_t* __restrict__ flags, int64_t r, int64_t ns) {
+  uint32_t m = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) m |= (r + i < ns && flags[r + i]) ? 1u << i : 0u;
+  return m;
+}
+
+__global__ void __launch_bounds__(1024) flag_count_kernel(const uint8_t* __restrict__ flags,
+                                                          const unsigned long long* __restrict__ count, int64_t cap,
+                                                          int32_t* __restrict__ bcount) {
+  __shared__ int32_t sh[32];
+  const int64_t ns = block_count(count, cap);
+  const int64_t r = (int64_t)blockIdx.x * kCompactPer + threadIdx.x * 8;
+  const int32_t c = block_sum_1024(__popc(flags8(flags, r, ns)), sh);
+  if (threadIdx.x == 0) bcount[blockIdx.x] = c;
+}
+
+__global__ void __launch_bounds__(1024) flag_scatter_kernel(const uint8_t* __restrict__ flags,
+                                                            const unsigned long long* __restrict__ count,
+                                                            int64_t cap, const int32_t* __restrict__ bcount,
+                                                            int32_t* __restrict__ list,
+                                                            unsigned long long* __restrict__ list_count) {
+  __shared__ int32_t sh[32];
+  const int64_t ns = block_count(count, cap);
+  int32_t before = 0;
+  for (int b = threadIdx.x; b < (int)blockIdx.x; b += blockDim.x) before += bcount[b];
+  before = block_sum_1024(before, sh);
+  const int64_t r = (int64_t)blockIdx.x * kCompactPer + threadIdx.x * 8;
+  const uint32_t m = flags8(flags, r, ns);
+  // exclusive scan of the per-thread counts over the block
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int32_t c = __popc(m);
+  int32_t x = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int32_t t = sh[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    sh[lane] = t;
+  }
+  __syncthreads();
+  int32_t pos = before + x - c + (w > 0 ? sh[w - 1] : 0);
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    if ((m >> i) & 1u) list[pos++] = (int32_t)(r + i);
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *list_count = (unsigned long long)(before + sh[31]);
+}
+
+// FP32 inner product of two padded rows (dp a multiple of 4, 16-byte aligned): four
+// partial sums over float4 loads.  Its error is within gamma_d sum |u_i p_i| whatever the
+// order of the additions.
+__device__ __forceinline__ float dot32_rows(const float* __restrict__ u, const float* __restrict__ p, int dp) {
+  const float4* u4 = reinterpret_cast<const float4*>(u);
+  const float4* p4 = reinterpret_cast<const float4*>(p);
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll 4
+  for (int c = 0; c < dp / 4; ++c) {
+    const float4 a = u4[c], b = p4[c];
+    s0 = fmaf(a.x, b.x, s0);
+    s1 = fmaf(a.y, b.y, s1);
+    s2 = fmaf(a.z, b.z, s2);
+    s3 = fmaf(a.w, b.w, s3);
+  }
+  return (s0 + s1) + (s2 + s3);
+}
+
+// Whether two rows hold the same d floats bit for bit.  An item equal to the query
+// vector scores exactly <u,q>, which is not above it: no double-precision score needed.
+__device__ __forceinline__ bool same_vector(const float* __restrict__ a, const float* __restrict__ b, int d) {
+  bool eq = true;
+  int i = 0;
+  for (; i + 4 <= d; i += 4) {
+    const uint4 x = *reinterpret_cast<const uint4*>(a + i), y = *reinterpret_cast<const uint4*>(b + i);
+    eq &= x.x == y.x && x.y == y.y && x.z == y.z && x.w == y.w;
+  }
+  for (; i < d; ++i) eq &= __float_as_uint(a[i]) == __float_as_uint(b[i]);
+  return eq;
 }
 
 // Decides every row of the tensor-core pass: "yes"/"no" as found, band items (or, when
@@ -523,12 +686,23 @@ __global__ void resolve_kernel(const Survivor* __restrict__ rows, const unsigned
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long fp64 = 0, scanned = 0;
-  for (int64_t r = gw; r < nrows; r += nw) {
-    const int32_t st = status[r];
-    if (st == ROW_NO) continue;
-    const Survivor S = rows[r];
-    bool yes = st == ROW_YES;
-    if (st == ROW_BAND || st == ROW_FULL) {
+  // 32 rows per warp step: statuses and "yes" rows lane-parallel, rows with band items
+  // (or a whole-row re-scan) one after another with the whole warp
+  for (int64_t r0 = gw * 32; r0 < nrows; r0 += nw * 32) {
+    const int64_t rl = r0 + lane;
+    const int32_t st_l = rl < nrows ? status[rl] : (int32_t)ROW_NO;
+    if (st_l == ROW_YES) {
+      const Survivor S = rows[rl];
+      const int32_t id = uid[S.upos];
+      set_answer(bitmap, words, S.j, id);
+    }
+    uint32_t open = __ballot_sync(0xffffffffu, st_l == ROW_BAND || st_l == ROW_FULL);
+    while (open) {
+      const int src = __ffs(open) - 1;
+      open &= open - 1;
+      const int64_t r = r0 + src;
+      const int32_t st = __shfl_sync(0xffffffffu, st_l, src);
+      const Survivor S = rows[r];
       const int k = kk[S.j];
       const float* u = Ut + (int64_t)S.upos * dp;
       const float nu = unorm[S.upos];
@@ -555,11 +729,10 @@ __global__ void resolve_kernel(const Survivor* __restrict__ rows, const unsigned
         if (lane < nb) {
           const int64_t it = band_items[r * kBandCap + lane];
           p = Ps + it * dp;
-          float s = 0.f;
-          for (int i = 0; i < dp; ++i) s = fmaf(u[i], p[i], s);
+          const float s = dot32_rows(u, p, dp);
           const float ep = __fmul_ru(gnu, pnorm[it]) + 1e-30f;
           if (__fsub_rd(s, ep) > hi) gt = true;
-          else amb = __fadd_ru(s, ep) > lo;
+          else amb = __fadd_ru(s, ep) > lo && !same_vector(p, Qd + (int64_t)S.j * dp, d);
         }
         need64(__any_sync(0xffffffffu, amb));
         if (amb) gt = dot64_seq(u, p, d) > s64q;
@@ -575,11 +748,10 @@ __global__ void resolve_kernel(const Survivor* __restrict__ rows, const unsigned
           bool gt = false, amb = false;
           const float* p = Ps + i * dp;
           if (i < n) {
-            float s = 0.f;
-            for (int e = 0; e < dp; ++e) s = fmaf(u[e], p[e], s);
+            const float s = dot32_rows(u, p, dp);
             const float ep = __fmul_ru(gnu, pnorm[i]) + 1e-30f;
             if (__fsub_rd(s, ep) > hi) gt = true;
-            else amb = __fadd_ru(s, ep) > lo;
+            else amb = __fadd_ru(s, ep) > lo && !same_vector(p, Qd + (int64_t)S.j * dp, d);
           }
           need64(__any_sync(0xffffffffu, amb));
           if (amb) gt = dot64_seq(u, p, d) > s64q;
@@ -588,11 +760,10 @@ __global__ void resolve_kernel(const Survivor* __restrict__ rows, const unsigned
         }
         ++fp64;
       }
-      yes = c < k;
-    }
-    if (yes && lane == 0) {
-      const int32_t id = uid[S.upos];
-      atomicOr(&bitmap[(int64_t)S.j * words + (id >> 5)], 1u << (id & 31));
+      if (c < k && lane == 0) {
+        const int32_t id = uid[S.upos];
+        set_answer(bitmap, words, S.j, id);
+      }
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -713,6 +884,9 @@ sah_status run_verify_tc(Index* ix, CallCtx* cx, const Survivor* surv, const uns
                o_rows = take(sizeof(Survivor) * ns), o_scut = take(sizeof(int32_t) * ns),
                o_stat = take(sizeof(int32_t) * ns), o_cert = take(sizeof(int32_t) * ns),
                o_band = take(sizeof(int32_t) * ns), o_items = take(sizeof(int32_t) * ns * kBandCap);
+  const int64_t nbc = (ns + kCompactPer - 1) / kCompactPer;
+  const size_t o_flags = take(ns), o_lists = take(sizeof(int32_t) * 2 * ns), o_bcount = take(sizeof(int32_t) * nbc),
+               o_lcount = take(sizeof(unsigned long long) * 2);
   if (cx->tcws.bytes < need) {
     SAH_CUDA(cudaStreamSynchronize(st));
     if (cx->tcws.base) cudaFree(cx->tcws.base);
@@ -735,6 +909,10 @@ sah_status run_verify_tc(Index* ix, CallCtx* cx, const Survivor* surv, const uns
   int32_t* cert = (int32_t*)(w + o_cert);
   int32_t* band = (int32_t*)(w + o_band);
   int32_t* items = (int32_t*)(w + o_items);
+  uint8_t* flags = (uint8_t*)(w + o_flags);
+  int32_t* lists = (int32_t*)(w + o_lists);
+  int32_t* bcount = (int32_t*)(w + o_bcount);
+  unsigned long long* lcount = (unsigned long long*)(w + o_lcount);
 
   SAH_CUDA(cudaMemsetAsync(hist, 0, sizeof(int32_t) * (ntiles + 2), st));
   {
@@ -782,19 +960,48 @@ sah_status run_verify_tc(Index* ix, CallCtx* cx, const Survivor* surv, const uns
   prm.band_items = items;
   prm.items_stat = stats + stat_items;
   prm.timeout = ix->dev_timeout;
-  const unsigned grid = grid_for(ns, kRows);
+  prm.flags = flags;
+  // Two phases of the scan over item tiles, [0,8) and [8, end): rows still open after the
+  // first go on, compacted, to the second, so that its (longer) CTAs hold only rows that
+  // still need the items.  Every phase boundary costs a fill and drain of the CTAs and
+  // the gather of their rows: with more phases ([4,8,16,32] was tried) that cost exceeds
+  // the saving.  With exact thresholds (|P'| = n) the user pass decides nearly every pair,
+  // the list is short or empty, and one phase costs fewer launches.
+  std::vector<int> bounds{0};
+  if (!ix->l_exact && 8 < ntiles) bounds.push_back(8);
+  bounds.push_back(ntiles);
+  int nsm = 152;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ix->device);
+  // persistent CTAs (two per SM when they fit), each over several row blocks
+  const unsigned grid = (unsigned)std::min<int64_t>(grid_for(ns, kRows), (ix->dk == 64 ? 2 : 1) * (int64_t)nsm);
   if (ev) SAH_CUDA(cudaEventRecord(ev[0], st));
-  if (ix->dk == 64) {
-    // 97 KB of shared memory and 256 TMEM columns: two CTAs per SM
-    constexpr size_t smem = tc_smem_bytes<1, 2>();
-    SAH_TRY(raise_smem_limit((const void*)verify_tc_kernel<1, 2, 2>, smem));
-    verify_tc_kernel<1, 2, 2><<<grid, kThreads, smem, st>>>(ix->tmap_Pv, ix->tmap_Plo, prm);
-  } else {
-    constexpr size_t smem = tc_smem_bytes<2, 2>();
-    SAH_TRY(raise_smem_limit((const void*)verify_tc_kernel<2, 2, 1>, smem));
-    verify_tc_kernel<2, 2, 1><<<grid, kThreads, smem, st>>>(ix->tmap_Pv, ix->tmap_Plo, prm);
+  int nlaunch = 0;
+  for (size_t ph = 0; ph + 1 < bounds.size(); ++ph) {
+    prm.t_begin = bounds[ph];
+    prm.t_end = bounds[ph + 1];
+    prm.list = ph == 0 ? nullptr : lists + (ph & 1) * ns;
+    prm.nrows_dev = ph == 0 ? count_dev : lcount + (ph & 1);
+    if (ix->dk == 64) {
+      // 97 KB of shared memory and 256 TMEM columns: two CTAs per SM
+      constexpr size_t smem = tc_smem_bytes<1, 2>();
+      SAH_TRY(raise_smem_limit((const void*)verify_tc_kernel<1, 2, 2>, smem));
+      verify_tc_kernel<1, 2, 2><<<grid, kThreads, smem, st>>>(ix->tmap_Pv, ix->tmap_Plo, prm);
+    } else {
+      constexpr size_t smem = tc_smem_bytes<2, 2>();
+      SAH_TRY(raise_smem_limit((const void*)verify_tc_kernel<2, 2, 1>, smem));
+      verify_tc_kernel<2, 2, 1><<<grid, kThreads, smem, st>>>(ix->tmap_Pv, ix->tmap_Plo, prm);
+    }
+    SAH_CUDA(cudaGetLastError());
+    ++nlaunch;
+    if (ph + 2 < bounds.size()) {
+      const int nx = (int)((ph + 1) & 1);
+      flag_count_kernel<<<(unsigned)nbc, 1024, 0, st>>>(flags, count_dev, ns, bcount);
+      flag_scatter_kernel<<<(unsigned)nbc, 1024, 0, st>>>(flags, count_dev, ns, bcount, lists + nx * ns,
+                                                          lcount + nx);
+      SAH_CUDA(cudaGetLastError());
+      nlaunch += 2;
+    }
   }
-  SAH_CUDA(cudaGetLastError());
   if (ev) SAH_CUDA(cudaEventRecord(ev[1], st));
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
@@ -802,7 +1009,7 @@ sah_status run_verify_tc(Index* ix, CallCtx* cx, const Survivor* surv, const uns
                                           ix->pnorm, ix->n, ix->d, ix->dp, Qd, qn, kk, ix->gamma, bitmap, words,
                                           stats + stat_fp64, stats + stat_items);
   SAH_CUDA(cudaGetLastError());
-  if (launches) *launches += 6;
+  if (launches) *launches += 4 + nlaunch;
   return SAH_OK;
 }
 
