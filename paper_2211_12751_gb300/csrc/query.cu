@@ -650,28 +650,39 @@ __device__ inline int block_exclusive_scan(int v, int* total) {
 
 // Answers per summary word: one thread per (query j, summary word sw), reading the
 // bitmap words the summary marks (independent loads, all in flight at once).  A query
-// with k > n asks for every user: its words count as full.
+// with k > n asks for every user: its words count as full.  The words with answers are
+// listed (in no particular order) for the emission.
 __global__ void answer_count_kernel(const uint32_t* __restrict__ bitmap, int64_t stride, int nq,
                                     const int32_t* __restrict__ kk, int64_t n, int64_t m,
-                                    int32_t* __restrict__ wcnt) {
+                                    int32_t* __restrict__ wcnt, int32_t* __restrict__ list,
+                                    unsigned int* __restrict__ list_count) {
   const int64_t w = answer_words(stride);
   const int nsw = (int)(w / 32);
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= nsw * nq) return;
-  const int j = g / nsw, sw = g - j * nsw;
+  const int lane = threadIdx.x & 31;
   int c = 0;
-  if (kk[j] > n) {
-    c = (int)std::max<int64_t>(0, std::min<int64_t>(1024, m - (int64_t)sw * 1024));
-  } else {
-    const uint32_t* row = bitmap + (int64_t)j * stride;
-    const uint32_t sm = row[w + sw];
-    if (sm) {
+  if (g < nsw * nq) {
+    const int j = g / nsw, sw = g - j * nsw;
+    if (kk[j] > n) {
+      c = (int)std::max<int64_t>(0, std::min<int64_t>(1024, m - (int64_t)sw * 1024));
+    } else {
+      const uint32_t* row = bitmap + (int64_t)j * stride;
+      const uint32_t sm = row[w + sw];
+      if (sm) {
 #pragma unroll
-      for (int b = 0; b < 32; ++b)
-        if ((sm >> b) & 1u) c += __popc(row[sw * 32 + b]);
+        for (int b = 0; b < 32; ++b)
+          if ((sm >> b) & 1u) c += __popc(row[sw * 32 + b]);
+      }
     }
+    wcnt[g] = c;
   }
-  wcnt[g] = c;
+  const unsigned mk = __ballot_sync(0xffffffffu, c > 0);
+  if (mk) {
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(list_count, (unsigned)__popc(mk));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (c > 0) list[base + __popc(mk & ((1u << lane) - 1u))] = g;
+  }
 }
 
 // Per query (one CTA): exclusive scan of its summary-word counts in place, total to cnt[j].
@@ -723,48 +734,58 @@ __global__ void offsets_kernel(const int32_t* __restrict__ cnt, int nq, int64_t 
   if (threadIdx.x == 0) offsets[nq] = carry;
 }
 
-// Writes the ids of summary word sw of query j (one thread each) at offsets[j] plus the
-// scanned count before it, in ascending order, and clears the words it read, leaving the
-// bitmap zero for the next call.  Only if the call's total fits in out_cap; otherwise it
-// raises *overflow and leaves the bitmap as it is.
-__global__ void answer_emit_kernel(uint32_t* __restrict__ bitmap, int64_t stride, int nq,
+// Emission, one warp per listed summary word (query j, word sw): lane l takes bitmap
+// word 32 sw + l and writes its ids at offsets[j] plus the scanned count before the
+// summary word plus the lane's share, in ascending order, and clears the words it read,
+// leaving the bitmap zero for the next call.  A row with k > n writes the summary word's
+// 1024 users.  Only if the call's total fits in out_cap; otherwise it raises *overflow and
+// leaves the bitmap as it is.
+__global__ void answer_emit_kernel(uint32_t* __restrict__ bitmap, int64_t stride,
                                    const int32_t* __restrict__ kk, int64_t n, int64_t m,
-                                   const int32_t* __restrict__ wpre, const int64_t* __restrict__ offsets,
-                                   int32_t* __restrict__ out, int64_t out_cap,
-                                   unsigned long long* __restrict__ overflow) {
+                                   const int32_t* __restrict__ wpre, const int32_t* __restrict__ list,
+                                   const unsigned int* __restrict__ list_count,
+                                   const int64_t* __restrict__ offsets, int nq, int32_t* __restrict__ out,
+                                   int64_t out_cap, unsigned long long* __restrict__ overflow) {
+  const int lane = threadIdx.x & 31;
   const int64_t w = answer_words(stride);
   const int nsw = (int)(w / 32);
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   if (offsets[nq] > out_cap) {
-    if (g == 0) atomicExch(overflow, 1ull);
+    if (gw == 0 && lane == 0) atomicExch(overflow, 1ull);
     return;
   }
-  if (g >= nsw * nq) return;
-  const int j = g / nsw, sw = g - j * nsw;
-  uint32_t* row = bitmap + (int64_t)j * stride;
-  int64_t dst = offsets[j] + wpre[g];
-  const bool all = kk[j] > n;
-  if (all)
-    for (int64_t i = (int64_t)sw * 1024; i < std::min<int64_t>(m, (int64_t)sw * 1024 + 1024); ++i)
-      out[dst++] = (int32_t)i;
-  const uint32_t sm = row[w + sw];
-  if (!sm) return;
-  uint32_t v[32];
+  const unsigned nl = *list_count;
+  for (int64_t e = gw; e < nl; e += nwarps) {
+    const int g = list[e];
+    const int j = g / nsw, sw = g - j * nsw;
+    uint32_t* row = bitmap + (int64_t)j * stride;
+    const uint32_t sm = row[w + sw];
+    uint32_t v = 0;
+    if ((sm >> lane) & 1u) {
+      v = row[sw * 32 + lane];
+      row[sw * 32 + lane] = 0u;
+    }
+    if (lane == 0 && sm) row[w + sw] = 0u;
+    const int64_t dst = offsets[j] + wpre[g];
+    if (kk[j] > n) {
+      const int64_t lo = (int64_t)sw * 1024, hi = std::min<int64_t>(m, lo + 1024);
+      for (int64_t i = lo + lane; i < hi; i += 32) out[dst + (i - lo)] = (int32_t)i;
+      continue;
+    }
+    const int pc = __popc(v);
+    int x = pc;   // inclusive scan over the lanes
 #pragma unroll
-  for (int b = 0; b < 32; ++b) v[b] = ((sm >> b) & 1u) ? row[sw * 32 + b] : 0u;
-#pragma unroll
-  for (int b = 0; b < 32; ++b)
-    if ((sm >> b) & 1u) row[sw * 32 + b] = 0u;
-  row[w + sw] = 0u;
-  if (all) return;
-#pragma unroll
-  for (int b = 0; b < 32; ++b) {
-    uint32_t x = v[b];
-    const int64_t base_id = ((int64_t)sw * 32 + b) * 32;
-    while (x) {
-      const int i = __ffs(x) - 1;
-      x &= x - 1;
-      out[dst++] = (int32_t)(base_id + i);
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    int64_t p = dst + x - pc;
+    const int32_t base_id = (int32_t)(((int64_t)sw * 32 + lane) * 32);
+    while (v) {
+      const int i = __ffs(v) - 1;
+      v &= v - 1;
+      out[p++] = base_id + i;
     }
   }
 }
@@ -796,7 +817,7 @@ WsLayout layout_for(const Index* ix, int qb) {
   L.tneed = take((size_t)std::max<int64_t>((ix->m_nz + 127) / 128, 1));
   L.coltab = take(user_pass_tc_scratch_bytes(qb));
   L.survcnt = take(3 * sizeof(unsigned long long));
-  L.chunk = take(sizeof(int32_t) * (size_t)qb * (answer_words(answer_stride(ix->m)) / 32 + 1));
+  L.chunk = take(sizeof(int32_t) * ((size_t)qb * (2 * (answer_words(answer_stride(ix->m)) / 32) + 1) + 4));
   L.offsets = take(sizeof(int64_t) * (size_t)(qb + 1));
   L.stats = take(sizeof(unsigned long long) * ST_COUNT);
   L.total = o;
@@ -993,6 +1014,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
       // so; after a reallocation, a larger sub-batch or a call that stopped early, clear them
       const size_t bm_bytes = sizeof(uint32_t) * (size_t)nqb * words;
       const unsigned ans_grid = (unsigned)((nqb * nsw + 255) / 256);   // a thread per summary word
+      const unsigned emit_grid = (unsigned)std::max(1, sms * 8);             // warps over the listed words
       if (cx->bm_clean_base != cx->ws.base || cx->bm_clean_bytes < bm_bytes) {
         SAH_CUDA(cudaMemsetAsync((char*)cx->ws.base + L.bitmap, 0, bm_bytes, st));
         cx->bm_clean_base = cx->ws.base;
@@ -1124,9 +1146,13 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
                                                                              words);
           ++n_compact;
         }
-        // the per-query answer counts go after the per-word counts
+        // after the per-word counts: the per-query counts, the list of words with answers
+        // and its length
         int32_t* qcnt = chunk + (int64_t)nqb * nsw;
-        answer_count_kernel<<<ans_grid, 256, 0, st>>>(bitmap, words, nqb, kk, ix->n, ix->m, chunk);
+        int32_t* alist = qcnt + nqb;
+        unsigned int* alist_n = (unsigned int*)(alist + (int64_t)nqb * nsw);
+        SAH_CUDA(cudaMemsetAsync(alist_n, 0, sizeof(unsigned int), st));
+        answer_count_kernel<<<ans_grid, 256, 0, st>>>(bitmap, words, nqb, kk, ix->n, ix->m, chunk, alist, alist_n);
         answer_scan_kernel<<<nqb, 256, 0, st>>>(chunk, nsw, qcnt);
         offsets_kernel<<<1, 1024, 0, st>>>(qcnt, nqb, direct ? 0 : res_total, offsets);
         int32_t* dst;
@@ -1139,8 +1165,8 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
           dst_cap = (int64_t)(cx->res.bytes / sizeof(int32_t));
         }
         if (dst) {
-          answer_emit_kernel<<<ans_grid, 256, 0, st>>>(bitmap, words, nqb, kk, ix->n, ix->m, chunk, offsets, dst,
-                                                       dst_cap, &stats[ST_EMIT_OVERFLOW]);
+          answer_emit_kernel<<<emit_grid, 256, 0, st>>>(bitmap, words, kk, ix->n, ix->m, chunk, alist, alist_n,
+                                                        offsets, nqb, dst, dst_cap, &stats[ST_EMIT_OVERFLOW]);
         } else {
           SAH_CUDA(cudaMemsetAsync(&stats[ST_EMIT_OVERFLOW], 0xff, sizeof(unsigned long long), st));
         }
@@ -1215,10 +1241,15 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
         if (cx->res.base) cudaFree(cx->res.base);
         cx->res = nr;
         SAH_CUDA(cudaMemsetAsync(&stats[ST_EMIT_OVERFLOW], 0, sizeof(unsigned long long), st));
-        answer_emit_kernel<<<ans_grid, 256, 0, st>>>(bitmap, words, nqb, kk, ix->n, ix->m, chunk, offsets,
-                                                     (int32_t*)cx->res.base,
-                                                     (int64_t)(cx->res.bytes / sizeof(int32_t)),
-                                                     &stats[ST_EMIT_OVERFLOW]);
+        {
+          int32_t* qcnt = (int32_t*)(w + L.chunk) + (int64_t)nqb * nsw;
+          int32_t* alist = qcnt + nqb;
+          const unsigned int* alist_n = (const unsigned int*)(alist + (int64_t)nqb * nsw);
+          answer_emit_kernel<<<emit_grid, 256, 0, st>>>(bitmap, words, kk, ix->n, ix->m, chunk, alist, alist_n,
+                                                        offsets, nqb, (int32_t*)cx->res.base,
+                                                        (int64_t)(cx->res.bytes / sizeof(int32_t)),
+                                                        &stats[ST_EMIT_OVERFLOW]);
+        }
         SAH_CUDA(cudaGetLastError());
         SAH_CUDA(cudaStreamSynchronize(st));
       }
