@@ -914,6 +914,9 @@ __global__ void tile_need_kernel(const int32_t* __restrict__ ublock, int64_t mz,
 
 // FP32 re-score of the pairs the tensor-core band left open; the same decisions as the
 // FP32 user pass.  Grid-stride, one thread per pair.
+// DP4 > 0: rows of at most 4 DP4 floats, held in registers for both the FP32 and the
+// double-precision dot (no second pass over memory); DP4 = 0: any width, read as needed.
+template <int DP4>
 __global__ void pair_rescore_kernel(const Survivor* __restrict__ pairs, const unsigned long long* __restrict__ count,
                                     int64_t cap, const float* __restrict__ Ut, const float* __restrict__ unorm,
                                     const int32_t* __restrict__ uid, const float* __restrict__ Lt,
@@ -947,12 +950,28 @@ __global__ void pair_rescore_kernel(const Survivor* __restrict__ pairs, const un
         const int k = kk[j];
         const float4* u4 = reinterpret_cast<const float4*>(Ut + (int64_t)r * dp);
         const float4* q4 = reinterpret_cast<const float4*>(Qd + (int64_t)j * dp);
-        for (int c = 0; c < dp / 4; ++c) {
-          const float4 a = u4[c], b = q4[c];
-          acc = fmaf(a.x, b.x, acc);
-          acc = fmaf(a.y, b.y, acc);
-          acc = fmaf(a.z, b.z, acc);
-          acc = fmaf(a.w, b.w, acc);
+        float4 ur[DP4 > 0 ? DP4 : 1], qr[DP4 > 0 ? DP4 : 1];
+        if (DP4 > 0) {
+#pragma unroll
+          for (int c = 0; c < DP4; ++c) {
+            ur[c] = c < dp / 4 ? u4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+            qr[c] = c < dp / 4 ? q4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+#pragma unroll
+          for (int c = 0; c < DP4; ++c) {
+            acc = fmaf(ur[c].x, qr[c].x, acc);
+            acc = fmaf(ur[c].y, qr[c].y, acc);
+            acc = fmaf(ur[c].z, qr[c].z, acc);
+            acc = fmaf(ur[c].w, qr[c].w, acc);
+          }
+        } else {
+          for (int c = 0; c < dp / 4; ++c) {
+            const float4 a = u4[c], b = q4[c];
+            acc = fmaf(a.x, b.x, acc);
+            acc = fmaf(a.y, b.y, acc);
+            acc = fmaf(a.z, b.z, acc);
+            acc = fmaf(a.w, b.w, acc);
+          }
         }
         const float nu = unorm[r], E = Eu[r];
         const float L = (k <= kmax) ? Lt[(int64_t)(k - 1) * mz + r] : -INFINITY;
@@ -968,7 +987,21 @@ __global__ void pair_rescore_kernel(const Survivor* __restrict__ pairs, const un
           const double t64 = T64[(int64_t)(k - 1) * mz + r];
           if (t64 == t64) {
             fp64 = true;
-            yes = dot64_seq(Ut + (int64_t)r * dp, Qd + (int64_t)j * dp, d) >= t64;
+            double s64 = 0.0;
+            if (DP4 > 0) {
+              // the sequential double-precision sum i = 0..d-1 over the registers
+#pragma unroll
+              for (int c = 0; c < DP4; ++c) {
+                const float a4[4] = {ur[c].x, ur[c].y, ur[c].z, ur[c].w};
+                const float b4[4] = {qr[c].x, qr[c].y, qr[c].z, qr[c].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                  if (4 * c + e < d) s64 = __fma_rn((double)a4[e], (double)b4[e], s64);
+              }
+            } else {
+              s64 = dot64_seq(Ut + (int64_t)r * dp, Qd + (int64_t)j * dp, d);
+            }
+            yes = s64 >= t64;
           } else {
             surv_flag = true;
           }
@@ -1144,10 +1177,11 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
   } else {
     SAH_TRY((launch_pass<2, 2, 64>(ix, p, sms, st, launches, ev)));
   }
-  pair_rescore_kernel<<<sms * 4, 256, 0, st>>>(resc, resc_count, surv_cap, ix->Ut, ix->unorm, ix->uid, ix->Lt,
-                                               ix->Eu, ix->pnorm, ix->n, ix->m_nz, ix->kmax, ix->l_exact ? 1 : 0,
-                                               ix->d, ix->dp, Qd, qn, kk, ix->gamma, ix->T64, bitmap, words, surv,
-                                               surv_count, surv_cap, stats, st_yes, st_fp64, nq, ix->dev_timeout);
+  auto rescore = ix->dp <= 64 ? pair_rescore_kernel<16> : pair_rescore_kernel<0>;
+  rescore<<<sms * 4, 256, 0, st>>>(resc, resc_count, surv_cap, ix->Ut, ix->unorm, ix->uid, ix->Lt, ix->Eu, ix->pnorm,
+                                   ix->n, ix->m_nz, ix->kmax, ix->l_exact ? 1 : 0, ix->d, ix->dp, Qd, qn, kk,
+                                   ix->gamma, ix->T64, bitmap, words, surv, surv_count, surv_cap, stats, st_yes,
+                                   st_fp64, nq, ix->dev_timeout);
   SAH_CUDA(cudaGetLastError());
   if (launches) *launches += 1;
   return SAH_OK;
