@@ -50,16 +50,16 @@ inline unsigned grid_for(int64_t n, int per) { return (unsigned)((n + per - 1) /
 // INT_MAX, which no kernel uses as an index: such a row asks for every user.
 __global__ void prep_queries_kernel(const float* __restrict__ Q, int nq, int d, int dp,
                                     float* __restrict__ Qd, float* __restrict__ qn,
-                                    int32_t* __restrict__ kk, const int32_t* __restrict__ modes,
-                                    unsigned long long* __restrict__ stats) {
+                                    const int32_t* __restrict__ ks, int32_t* __restrict__ kk,
+                                    const int32_t* __restrict__ modes, unsigned long long* __restrict__ stats) {
   int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   int lane = threadIdx.x & 31;
   if (j >= nq) return;
-  const bool bad_k = kk[j] < 1 || (modes && modes[j] != SAH_EXACT && modes[j] != SAH_SAALSH);
-  __syncwarp();
-  if (lane == 0 && bad_k) {
-    atomicAdd(&stats[ST_BAD_K], 1ull);
-    kk[j] = INT_MAX;
+  const int32_t kj = ks[j];
+  const bool bad_k = kj < 1 || (modes && modes[j] != SAH_EXACT && modes[j] != SAH_SAALSH);
+  if (lane == 0) {
+    kk[j] = bad_k ? INT_MAX : kj;
+    if (bad_k) atomicAdd(&stats[ST_BAD_K], 1ull);
   }
   float s = 0.f;
   bool fin = true;
@@ -705,7 +705,7 @@ __global__ void answer_scan_kernel(int32_t* __restrict__ wcnt, int64_t nsw, int3
 // offsets[j] = base + the answers of the queries before j, offsets[nq] the end.  One CTA
 // of 1024 threads.
 __global__ void offsets_kernel(const int32_t* __restrict__ cnt, int nq, int64_t base,
-                               int64_t* __restrict__ offsets) {
+                               int64_t* __restrict__ offsets, int64_t* __restrict__ offsets2) {
   __shared__ long long warp_tot[32];
   __shared__ long long carry;
   if (threadIdx.x == 0) carry = base;
@@ -726,12 +726,18 @@ __global__ void offsets_kernel(const int32_t* __restrict__ cnt, int nq, int64_t 
       if (w < warp) before += warp_tot[w];
       all += warp_tot[w];
     }
-    if (j < nq) offsets[j] = before + x - tot;
+    if (j < nq) {
+      offsets[j] = before + x - tot;
+      if (offsets2) offsets2[j] = before + x - tot;
+    }
     __syncthreads();
     if (threadIdx.x == 0) carry += all;
     __syncthreads();
   }
-  if (threadIdx.x == 0) offsets[nq] = carry;
+  if (threadIdx.x == 0) {
+    offsets[nq] = carry;
+    if (offsets2) offsets2[nq] = carry;
+  }
 }
 
 // Emission, one warp per listed summary word (query j, word sw): lane l takes bitmap
@@ -796,7 +802,7 @@ __global__ void answer_emit_kernel(uint32_t* __restrict__ bitmap, int64_t stride
 namespace {
 
 struct WsLayout {
-  size_t qd, qb, qn, kk, pairs, pcount, kmask, tneed, coltab, survcnt, bitmap, chunk, offsets, stats, total;
+  size_t qd, qb, qn, kk, pairs, pcount, kmask, tneed, coltab, survcnt, alist_n, bitmap, chunk, offsets, stats, total;
 };
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -816,10 +822,14 @@ WsLayout layout_for(const Index* ix, int qb) {
   L.kmask = take(sizeof(uint32_t) * (size_t)std::max(ix->nb, 1) * ((qb + 31) / 32));
   L.tneed = take((size_t)std::max<int64_t>((ix->m_nz + 127) / 128, 1));
   L.coltab = take(user_pass_tc_scratch_bytes(qb));
-  L.survcnt = take(3 * sizeof(unsigned long long));
-  L.chunk = take(sizeof(int32_t) * ((size_t)qb * (2 * (answer_words(answer_stride(ix->m)) / 32) + 1) + 4));
-  L.offsets = take(sizeof(int64_t) * (size_t)(qb + 1));
-  L.stats = take(sizeof(unsigned long long) * ST_COUNT);
+  L.chunk = take(sizeof(int32_t) * ((size_t)qb * (2 * (answer_words(answer_stride(ix->m)) / 32) + 1)));
+  // the control block, contiguous so that one memset clears its counters and one copy
+  // reads it back: stats[ST_COUNT] | survivor counts[3] | answer-list length (u64) |
+  // offsets[qb + 1]
+  L.stats = take(sizeof(unsigned long long) * (ST_COUNT + 4) + sizeof(int64_t) * (size_t)(qb + 1));
+  L.survcnt = L.stats + sizeof(unsigned long long) * ST_COUNT;
+  L.alist_n = L.survcnt + 3 * sizeof(unsigned long long);
+  L.offsets = L.alist_n + sizeof(unsigned long long);
   L.total = o;
   return L;
 }
@@ -1037,7 +1047,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
       Survivor* surv = (Survivor*)cx->surv.base;
 
       // the pinned host block the results are read back into
-      const size_t pin_need = sizeof(int64_t) * (size_t)(nqb + 1) + sizeof(unsigned long long) * (ST_COUNT + 3) + 16;
+      const size_t pin_need = sizeof(int64_t) * (size_t)(nqb + 1) + sizeof(unsigned long long) * (ST_COUNT + 4) + 16;
       if (cx->pin_bytes < pin_need) {
         SAH_CUDA(cudaStreamSynchronize(st));
         if (cx->pin) cudaFreeHost(cx->pin);
@@ -1046,18 +1056,18 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
         SAH_CUDA(cudaMallocHost(&cx->pin, pin_need));
         cx->pin_bytes = pin_need;
       }
-      int64_t* ob = (int64_t*)cx->pin;
-      unsigned long long* st_h = (unsigned long long*)(ob + nqb + 1);
+      // the same layout as the control block: stats, survivor counts, list length, offsets
+      unsigned long long* st_h = (unsigned long long*)cx->pin;
       unsigned long long* ns2 = st_h + ST_COUNT;
-      int* timeout_h = (int*)(ns2 + 3);
+      int64_t* ob = (int64_t*)(st_h + ST_COUNT + 4);
+      int* timeout_h = (int*)(ob + nqb + 1);
       // every device operation of the attempt, the readback of its results included
       auto enqueue = [&]() -> sah_status {
         tm.begin(0);
-        SAH_CUDA(cudaMemsetAsync(stats, 0, sizeof(unsigned long long) * ST_COUNT, st));
-        SAH_CUDA(cudaMemsetAsync(survcnt, 0, 3 * sizeof(unsigned long long), st));
-        SAH_CUDA(cudaMemcpyAsync(kk, ks_dev + q0, sizeof(int32_t) * nqb, cudaMemcpyDeviceToDevice, st));
+        // the counters of the control block (stats, survivor counts, answer-list length)
+        SAH_CUDA(cudaMemsetAsync(stats, 0, sizeof(unsigned long long) * (ST_COUNT + 4), st));
         prep_queries_kernel<<<grid_for(nqb, 8), 256, 0, st>>>(Q_dev + (int64_t)q0 * ix->d, nqb, ix->d, ix->dp, Qd, qn,
-                                                               kk, modes_q, stats);
+                                                               ks_dev + q0, kk, modes_q, stats);
         SAH_CUDA(cudaGetLastError());
         tm.end(0, 1);
         if (ix->nb > 0) {
@@ -1150,11 +1160,11 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
         // and its length
         int32_t* qcnt = chunk + (int64_t)nqb * nsw;
         int32_t* alist = qcnt + nqb;
-        unsigned int* alist_n = (unsigned int*)(alist + (int64_t)nqb * nsw);
-        SAH_CUDA(cudaMemsetAsync(alist_n, 0, sizeof(unsigned int), st));
+        unsigned int* alist_n = (unsigned int*)(w + L.alist_n);
         answer_count_kernel<<<ans_grid, 256, 0, st>>>(bitmap, words, nqb, kk, ix->n, ix->m, chunk, alist, alist_n);
         answer_scan_kernel<<<nqb, 256, 0, st>>>(chunk, nsw, qcnt);
-        offsets_kernel<<<1, 1024, 0, st>>>(qcnt, nqb, direct ? 0 : res_total, offsets);
+        offsets_kernel<<<1, 1024, 0, st>>>(qcnt, nqb, direct ? 0 : res_total, offsets,
+                                           direct ? offsets_dev : nullptr);
         int32_t* dst;
         int64_t dst_cap;
         if (direct) {
@@ -1170,15 +1180,12 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
         } else {
           SAH_CUDA(cudaMemsetAsync(&stats[ST_EMIT_OVERFLOW], 0xff, sizeof(unsigned long long), st));
         }
-        if (direct && offsets_dev)
-          SAH_CUDA(cudaMemcpyAsync(offsets_dev, offsets, sizeof(int64_t) * (nqb + 1), cudaMemcpyDeviceToDevice, st));
         SAH_CUDA(cudaGetLastError());
         tm.end(4, n_compact);
         // ---- the one synchronisation of the sub-batch: offsets, counters, survivor counts
         *timeout_h = 0;
-        SAH_CUDA(cudaMemcpyAsync(ob, offsets, sizeof(int64_t) * (nqb + 1), cudaMemcpyDeviceToHost, st));
-        SAH_CUDA(cudaMemcpyAsync(st_h, stats, sizeof(unsigned long long) * ST_COUNT, cudaMemcpyDeviceToHost, st));
-        SAH_CUDA(cudaMemcpyAsync(ns2, survcnt, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        SAH_CUDA(cudaMemcpyAsync(st_h, stats, sizeof(unsigned long long) * (ST_COUNT + 4) + sizeof(int64_t) * (nqb + 1),
+                                 cudaMemcpyDeviceToHost, st));
         if (ix->dev_timeout)
           SAH_CUDA(cudaMemcpyAsync(timeout_h, ix->dev_timeout, sizeof(int), cudaMemcpyDeviceToHost, st));
         return SAH_OK;
@@ -1244,7 +1251,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
         {
           int32_t* qcnt = (int32_t*)(w + L.chunk) + (int64_t)nqb * nsw;
           int32_t* alist = qcnt + nqb;
-          const unsigned int* alist_n = (const unsigned int*)(alist + (int64_t)nqb * nsw);
+          const unsigned int* alist_n = (const unsigned int*)(w + L.alist_n);
           answer_emit_kernel<<<emit_grid, 256, 0, st>>>(bitmap, words, kk, ix->n, ix->m, chunk, alist, alist_n,
                                                         offsets, nqb, (int32_t*)cx->res.base,
                                                         (int64_t)(cx->res.bytes / sizeof(int32_t)),
