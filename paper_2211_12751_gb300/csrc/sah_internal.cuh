@@ -271,6 +271,13 @@ sah_status topk_full_tc(Index* ix, float* vlast, int32_t* ids64, cudaStream_t st
 sah_status build_bf16_copies(Index* ix, cudaStream_t st);
 // Decides every survivor with the tcgen05 kernel and sets the answer bits; the counters
 // of double-precision decisions and scanned items go to stats[stat_fp64], stats[stat_items].
+// rescore.cu
+// FP32 (and, with exact thresholds, double-precision) re-score of the pairs listed in
+// pairs[0, *count) (at most cap): "yes" pairs set their answer bit, open ones go to surv.
+sah_status launch_pair_rescore(Index* ix, const Survivor* pairs, const unsigned long long* count, int64_t cap,
+                               const float* Qd, const float* qn, const int32_t* kk, uint32_t* bitmap, int64_t words,
+                               Survivor* surv, unsigned long long* surv_count, unsigned long long* stats, int st_yes,
+                               int st_fp64, int nq, int sms, cudaStream_t st);
 sah_status run_verify_tc(Index* ix, CallCtx* cx, const Survivor* surv, const unsigned long long* surv_count_dev,
                          int64_t surv_cap, const float* Qd, const float* qn, const int32_t* kk, uint32_t* bitmap,
                          int64_t words, unsigned long long* stats, int stat_fp64, int stat_items,

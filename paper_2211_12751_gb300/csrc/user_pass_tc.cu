@@ -912,130 +912,6 @@ __global__ void tile_need_kernel(const int32_t* __restrict__ ublock, int64_t mz,
   if (lane == 0) need[t] = any ? 1 : 0;
 }
 
-// FP32 re-score of the pairs the tensor-core band left open; the same decisions as the
-// FP32 user pass.  Grid-stride, one thread per pair.
-// DP4 > 0: rows of at most 4 DP4 floats, held in registers for both the FP32 and the
-// double-precision dot (no second pass over memory); DP4 = 0: any width, read as needed.
-template <int DP4>
-__global__ void pair_rescore_kernel(const Survivor* __restrict__ pairs, const unsigned long long* __restrict__ count,
-                                    int64_t cap, const float* __restrict__ Ut, const float* __restrict__ unorm,
-                                    const int32_t* __restrict__ uid, const float* __restrict__ Lt,
-                                    const float* __restrict__ Eu, const float* __restrict__ pnorm, int64_t n,
-                                    int64_t mz, int kmax, int l_exact, int d, int dp, const float* __restrict__ Qd,
-                                    const float* __restrict__ qn, const int32_t* __restrict__ kk, float gamma,
-                                    const double* __restrict__ T64, uint32_t* __restrict__ bitmap, int64_t words,
-                                    Survivor* __restrict__ surv, unsigned long long* __restrict__ surv_count,
-                                    int64_t surv_cap, unsigned long long* __restrict__ stats, int st_yes,
-                                    int st_fp64, int nq, const int* __restrict__ timeout) {
-  // after a timed-out wait of the pass the list may hold unwritten entries: nothing is read
-  __shared__ int stop;
-  if (threadIdx.x == 0) stop = *(volatile const int*)timeout;
-  const int64_t total = block_count(count, cap);   // synchronises the block
-  if (stop) return;
-  // warp-strided, so that every lane runs the same iterations and the appends to the
-  // lists and counters go out once per warp
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t w0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; w0 < total; w0 += nw * 32) {
-    const int64_t i = w0 + lane;
-    bool yes = false, surv_flag = false, sa_row = false, fp64 = false;
-    int r = 0, j = 0;
-    float acc = 0.f;
-    if (i < total) {
-      const Survivor P = pairs[i];
-      r = P.upos;
-      j = P.j & 0x3fffffff;
-      if (r >= 0 && r < mz && j < nq) {
-        sa_row = (P.j >> 30) & 1;
-        const int k = kk[j];
-        const float4* u4 = reinterpret_cast<const float4*>(Ut + (int64_t)r * dp);
-        const float4* q4 = reinterpret_cast<const float4*>(Qd + (int64_t)j * dp);
-        float4 ur[DP4 > 0 ? DP4 : 1], qr[DP4 > 0 ? DP4 : 1];
-        if (DP4 > 0) {
-#pragma unroll
-          for (int c = 0; c < DP4; ++c) {
-            ur[c] = c < dp / 4 ? u4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
-            qr[c] = c < dp / 4 ? q4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
-          }
-#pragma unroll
-          for (int c = 0; c < DP4; ++c) {
-            acc = fmaf(ur[c].x, qr[c].x, acc);
-            acc = fmaf(ur[c].y, qr[c].y, acc);
-            acc = fmaf(ur[c].z, qr[c].z, acc);
-            acc = fmaf(ur[c].w, qr[c].w, acc);
-          }
-        } else {
-          for (int c = 0; c < dp / 4; ++c) {
-            const float4 a = u4[c], b = q4[c];
-            acc = fmaf(a.x, b.x, acc);
-            acc = fmaf(a.y, b.y, acc);
-            acc = fmaf(a.z, b.z, acc);
-            acc = fmaf(a.w, b.w, acc);
-          }
-        }
-        const float nu = unorm[r], E = Eu[r];
-        const float L = (k <= kmax) ? Lt[(int64_t)(k - 1) * mz + r] : -INFINITY;
-        const float Llo = (L == -INFINITY) ? -INFINITY : __fsub_rd(L, E);
-        const float eq = __fmul_ru(__fmul_ru(gamma, nu), qn[j]) + 1e-30f;
-        const float hi = __fadd_ru(acc, eq), lo = __fsub_rd(acc, eq);
-        if (hi < Llo) {
-        } else if (l_exact && k <= kmax && lo >= __fadd_ru(L, E)) {
-          yes = true;
-        } else if (lo >= __fmul_ru(__fmul_ru(nu, pnorm[k - 1]), 1.f + 2.f * gamma)) {
-          yes = true;
-        } else if (T64 != nullptr && k <= kmax && !sa_row) {
-          const double t64 = T64[(int64_t)(k - 1) * mz + r];
-          if (t64 == t64) {
-            fp64 = true;
-            double s64 = 0.0;
-            if (DP4 > 0) {
-              // the sequential double-precision sum i = 0..d-1 over the registers
-#pragma unroll
-              for (int c = 0; c < DP4; ++c) {
-                const float a4[4] = {ur[c].x, ur[c].y, ur[c].z, ur[c].w};
-                const float b4[4] = {qr[c].x, qr[c].y, qr[c].z, qr[c].w};
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                  if (4 * c + e < d) s64 = __fma_rn((double)a4[e], (double)b4[e], s64);
-              }
-            } else {
-              s64 = dot64_seq(Ut + (int64_t)r * dp, Qd + (int64_t)j * dp, d);
-            }
-            yes = s64 >= t64;
-          } else {
-            surv_flag = true;
-          }
-        } else {
-          surv_flag = true;
-        }
-      }
-    }
-    if (yes) {
-      const int32_t id = uid[r];
-      set_answer(bitmap, words, j, id);
-    }
-    const unsigned myes = __ballot_sync(0xffffffffu, yes), mf = __ballot_sync(0xffffffffu, fp64);
-    if (lane == 0) {
-      if (myes) atomicAdd(&stats[st_yes], (unsigned long long)__popc(myes));
-      if (mf) atomicAdd(&stats[st_fp64], (unsigned long long)__popc(mf));
-    }
-#pragma unroll
-    for (int sa = 0; sa < 2; ++sa) {
-      const bool mine = surv_flag && (sa_row == (sa == 1));
-      const unsigned m = __ballot_sync(0xffffffffu, mine);
-      if (m) {
-        unsigned long long b = 0;
-        if (lane == 0) b = atomicAdd(surv_count + sa, (unsigned long long)__popc(m));
-        b = __shfl_sync(0xffffffffu, b, 0);
-        if (mine) {
-          const unsigned long long slot = b + __popc(m & ((1u << lane) - 1u));
-          if ((int64_t)slot < surv_cap) surv[(sa ? surv_cap : 0) + slot] = Survivor{r, j, acc};
-        }
-      }
-    }
-  }
-}
-
 // hi = bf16(x), lo = bf16(x - hi) of the queries, K padded to dk with zeros
 __global__ void split_queries_kernel(const float* __restrict__ Qd, int nq, int d, int dp, int dk,
                                      uint16_t* __restrict__ Qhi, uint16_t* __restrict__ Qlo) {
@@ -1177,11 +1053,8 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
   } else {
     SAH_TRY((launch_pass<2, 2, 64>(ix, p, sms, st, launches, ev)));
   }
-  auto rescore = ix->dp <= 64 ? pair_rescore_kernel<16> : pair_rescore_kernel<0>;
-  rescore<<<sms * 4, 256, 0, st>>>(resc, resc_count, surv_cap, ix->Ut, ix->unorm, ix->uid, ix->Lt, ix->Eu, ix->pnorm,
-                                   ix->n, ix->m_nz, ix->kmax, ix->l_exact ? 1 : 0, ix->d, ix->dp, Qd, qn, kk,
-                                   ix->gamma, ix->T64, bitmap, words, surv, surv_count, surv_cap, stats, st_yes,
-                                   st_fp64, nq, ix->dev_timeout);
+  SAH_TRY(launch_pair_rescore(ix, resc, resc_count, surv_cap, Qd, qn, kk, bitmap, words, surv, surv_count, stats,
+                               st_yes, st_fp64, nq, sms, st));
   SAH_CUDA(cudaGetLastError());
   if (launches) *launches += 1;
   return SAH_OK;
