@@ -12,6 +12,8 @@
 //   A6  the open cases are decided in double precision, summed i = 0..d-1.
 //   A7  answers are set in a per-query bitmap over the caller's user ids and emitted in
 //       ascending id order.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -48,10 +50,13 @@ inline unsigned grid_for(int64_t n, int per) { return (unsigned)((n + per - 1) /
 // ---------------------------------------------------------------- query preparation
 // A row with an invalid k or mode is counted (the call then fails) and its k set to
 // INT_MAX, which no kernel uses as an index: such a row asks for every user.
+// (with Qhi non-null, also the split BF16 copy of the tensor-core user pass: hi = bf16(x),
+// lo = bf16(x - hi), K padded to dk with zeros, lo at Qhi + nq dk)
 __global__ void prep_queries_kernel(const float* __restrict__ Q, int nq, int d, int dp,
                                     float* __restrict__ Qd, float* __restrict__ qn,
                                     const int32_t* __restrict__ ks, int32_t* __restrict__ kk,
-                                    const int32_t* __restrict__ modes, unsigned long long* __restrict__ stats) {
+                                    const int32_t* __restrict__ modes, unsigned long long* __restrict__ stats,
+                                    uint16_t* __restrict__ Qhi, int dk) {
   int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   int lane = threadIdx.x & 31;
   if (j >= nq) return;
@@ -68,6 +73,16 @@ __global__ void prep_queries_kernel(const float* __restrict__ Q, int nq, int d, 
     fin &= isfinite(v);
     Qd[(int64_t)j * dp + i] = v;
     s = fmaf(v, v, s);
+  }
+  if (Qhi) {
+    uint16_t* Qlo = Qhi + (int64_t)nq * dk;
+    for (int i = lane; i < dk; i += 32) {
+      const float v = (i < d) ? Q[(int64_t)j * d + i] : 0.f;
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+      Qhi[(int64_t)j * dk + i] = __bfloat16_as_ushort(h);
+      Qlo[(int64_t)j * dk + i] = __bfloat16_as_ushort(l);
+    }
   }
   s = warp_sum(s);
   bool ok = __all_sync(0xffffffffu, fin);
@@ -686,7 +701,12 @@ __global__ void answer_count_kernel(const uint32_t* __restrict__ bitmap, int64_t
 }
 
 // Per query (one CTA): exclusive scan of its summary-word counts in place, total to cnt[j].
-__global__ void answer_scan_kernel(int32_t* __restrict__ wcnt, int64_t nsw, int32_t* __restrict__ cnt) {
+// The last CTA to finish (a ticket taken after a fence) then turns the totals into the
+// offsets: offsets[j] = base + the answers of the queries before j, offsets[nq] the end
+// (also into offsets2 when given).
+__global__ void answer_scan_kernel(int32_t* __restrict__ wcnt, int64_t nsw, int32_t* __restrict__ cnt, int nq,
+                                   int64_t base, int64_t* __restrict__ offsets, int64_t* __restrict__ offsets2,
+                                   unsigned int* __restrict__ ticket) {
   int32_t* v = wcnt + (int64_t)blockIdx.x * nsw;
   const int64_t per = (nsw + blockDim.x - 1) / blockDim.x;
   const int64_t b = std::min<int64_t>((int64_t)threadIdx.x * per, nsw), e = std::min<int64_t>(b + per, nsw);
@@ -699,44 +719,43 @@ __global__ void answer_scan_kernel(int32_t* __restrict__ wcnt, int64_t nsw, int3
     v[i] = acc;
     acc += x;
   }
-  if (threadIdx.x == 0) cnt[blockIdx.x] = total;
-}
-
-// offsets[j] = base + the answers of the queries before j, offsets[nq] the end.  One CTA
-// of 1024 threads.
-__global__ void offsets_kernel(const int32_t* __restrict__ cnt, int nq, int64_t base,
-                               int64_t* __restrict__ offsets, int64_t* __restrict__ offsets2) {
-  __shared__ long long warp_tot[32];
-  __shared__ long long carry;
-  if (threadIdx.x == 0) carry = base;
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    cnt[blockIdx.x] = total;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int j0 = 0; j0 < nq; j0 += blockDim.x) {
-    const int j = j0 + threadIdx.x;
-    const long long tot = j < nq ? cnt[j] : 0;
-    long long x = tot;
-    for (int o = 1; o < 32; o <<= 1) {
-      const long long y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_tot[warp] = x;
-    __syncthreads();
-    long long before = carry, all = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      if (w < warp) before += warp_tot[w];
-      all += warp_tot[w];
-    }
-    if (j < nq) {
-      offsets[j] = before + x - tot;
-      if (offsets2) offsets2[j] = before + x - tot;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) carry += all;
-    __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // the query offsets, in 64 bits: a contiguous run of queries per thread, then a block scan
+  __shared__ long long wtot[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int qper = (nq + blockDim.x - 1) / blockDim.x;
+  const int q0 = min((int)threadIdx.x * qper, nq), q1 = min(q0 + qper, nq);
+  long long t = 0;
+  for (int j = q0; j < q1; ++j) t += *(volatile int32_t*)&cnt[j];
+  long long x = t;
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wtot[warp] = x;
+  __syncthreads();
+  long long before = base, all = base;
+  for (int w = 0; w < nw; ++w) {
+    if (w < warp) before += wtot[w];
+    all += wtot[w];
+  }
+  long long o = before + x - t;
+  for (int j = q0; j < q1; ++j) {
+    offsets[j] = o;
+    if (offsets2) offsets2[j] = o;
+    o += *(volatile int32_t*)&cnt[j];
   }
   if (threadIdx.x == 0) {
-    offsets[nq] = carry;
-    if (offsets2) offsets2[nq] = carry;
+    offsets[nq] = all;
+    if (offsets2) offsets2[nq] = all;
   }
 }
 
@@ -801,8 +820,11 @@ __global__ void answer_emit_kernel(uint32_t* __restrict__ bitmap, int64_t stride
 // ---------------------------------------------------------------- workspace
 namespace {
 
+constexpr int kCtlCounters = 5;   // survivor counts (3), answer-list length, scan ticket
+
 struct WsLayout {
-  size_t qd, qb, qn, kk, pairs, pcount, kmask, tneed, coltab, survcnt, alist_n, bitmap, chunk, offsets, stats, total;
+  size_t qd, qb, qn, kk, pairs, pcount, kmask, tneed, coltab, survcnt, alist_n, ticket, bitmap, chunk, offsets, stats,
+      total;
 };
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -825,11 +847,12 @@ WsLayout layout_for(const Index* ix, int qb) {
   L.chunk = take(sizeof(int32_t) * ((size_t)qb * (2 * (answer_words(answer_stride(ix->m)) / 32) + 1)));
   // the control block, contiguous so that one memset clears its counters and one copy
   // reads it back: stats[ST_COUNT] | survivor counts[3] | answer-list length (u64) |
-  // offsets[qb + 1]
-  L.stats = take(sizeof(unsigned long long) * (ST_COUNT + 4) + sizeof(int64_t) * (size_t)(qb + 1));
+  // scan ticket (u64) | offsets[qb + 1]
+  L.stats = take(sizeof(unsigned long long) * (ST_COUNT + kCtlCounters) + sizeof(int64_t) * (size_t)(qb + 1));
   L.survcnt = L.stats + sizeof(unsigned long long) * ST_COUNT;
   L.alist_n = L.survcnt + 3 * sizeof(unsigned long long);
-  L.offsets = L.alist_n + sizeof(unsigned long long);
+  L.ticket = L.alist_n + sizeof(unsigned long long);
+  L.offsets = L.ticket + sizeof(unsigned long long);
   L.total = o;
   return L;
 }
@@ -1047,7 +1070,8 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
       Survivor* surv = (Survivor*)cx->surv.base;
 
       // the pinned host block the results are read back into
-      const size_t pin_need = sizeof(int64_t) * (size_t)(nqb + 1) + sizeof(unsigned long long) * (ST_COUNT + 4) + 16;
+      const size_t pin_need =
+          sizeof(int64_t) * (size_t)(nqb + 1) + sizeof(unsigned long long) * (ST_COUNT + kCtlCounters) + 16;
       if (cx->pin_bytes < pin_need) {
         SAH_CUDA(cudaStreamSynchronize(st));
         if (cx->pin) cudaFreeHost(cx->pin);
@@ -1059,27 +1083,28 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
       // the same layout as the control block: stats, survivor counts, list length, offsets
       unsigned long long* st_h = (unsigned long long*)cx->pin;
       unsigned long long* ns2 = st_h + ST_COUNT;
-      int64_t* ob = (int64_t*)(st_h + ST_COUNT + 4);
+      int64_t* ob = (int64_t*)(st_h + ST_COUNT + kCtlCounters);
       int* timeout_h = (int*)(ob + nqb + 1);
       // every device operation of the attempt, the readback of its results included
       auto enqueue = [&]() -> sah_status {
         tm.begin(0);
         // the counters of the control block (stats, survivor counts, answer-list length)
-        SAH_CUDA(cudaMemsetAsync(stats, 0, sizeof(unsigned long long) * (ST_COUNT + 4), st));
+        SAH_CUDA(cudaMemsetAsync(stats, 0, sizeof(unsigned long long) * (ST_COUNT + kCtlCounters), st));
+        // with the tensor-core user pass the preparation also writes the split BF16 queries
+        const bool tc_pass = ix->nb > 0 && ix->dk > 0 && ix->prm.tc_user_pass && ix->m_nz > 0;
         prep_queries_kernel<<<grid_for(nqb, 8), 256, 0, st>>>(Q_dev + (int64_t)q0 * ix->d, nqb, ix->d, ix->dp, Qd, qn,
-                                                               ks_dev + q0, kk, modes_q, stats);
+                                                               ks_dev + q0, kk, modes_q, stats,
+                                                               tc_pass ? (uint16_t*)(w + L.qb) : nullptr, ix->dk);
         SAH_CUDA(cudaGetLastError());
         tm.end(0, 1);
         if (ix->nb > 0) {
           tm.begin(1);
-          const bool tc_pass = ix->dk > 0 && ix->prm.tc_user_pass && ix->m_nz > 0;
           const int mask_words = (nqb + 31) / 32;
           uint32_t* kmask = (uint32_t*)(w + L.kmask);
           int bf_launches = 1;
           if (tc_pass) {
             // the distinct query vectors first: the block bound is taken once per vector
-            SAH_TRY(prepare_user_pass_tc(ix, Qd, (uint16_t*)(w + L.qb), w + L.coltab, kk, modes_q, nqb, st,
-                                         &bf_launches));
+            SAH_TRY(prepare_user_pass_tc(ix, Qd, w + L.coltab, kk, modes_q, nqb, st, &bf_launches));
             SAH_TRY(block_filter_tc(ix, Qd, qn, w + L.coltab, nqb, kmask, mask_words, stats, ST_PAIRS_KEPT,
                                     ST_KEPT_USERS, ST_USERS_SCORED, st));
           } else {
@@ -1150,7 +1175,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
           }
         }
         tm.begin(4);
-        int n_compact = 4;
+        int n_compact = 3;
         if (ix->nzero > 0) {
           zero_users_kernel<<<grid_for(ix->nzero * nqb, 256), 256, 0, st>>>(ix->zero_uid, ix->nzero, nqb, bitmap,
                                                                              words);
@@ -1162,9 +1187,8 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
         int32_t* alist = qcnt + nqb;
         unsigned int* alist_n = (unsigned int*)(w + L.alist_n);
         answer_count_kernel<<<ans_grid, 256, 0, st>>>(bitmap, words, nqb, kk, ix->n, ix->m, chunk, alist, alist_n);
-        answer_scan_kernel<<<nqb, 256, 0, st>>>(chunk, nsw, qcnt);
-        offsets_kernel<<<1, 1024, 0, st>>>(qcnt, nqb, direct ? 0 : res_total, offsets,
-                                           direct ? offsets_dev : nullptr);
+        answer_scan_kernel<<<nqb, 256, 0, st>>>(chunk, nsw, qcnt, nqb, direct ? 0 : res_total, offsets,
+                                                direct ? offsets_dev : nullptr, (unsigned int*)(w + L.ticket));
         int32_t* dst;
         int64_t dst_cap;
         if (direct) {
@@ -1184,7 +1208,8 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
         tm.end(4, n_compact);
         // ---- the one synchronisation of the sub-batch: offsets, counters, survivor counts
         *timeout_h = 0;
-        SAH_CUDA(cudaMemcpyAsync(st_h, stats, sizeof(unsigned long long) * (ST_COUNT + 4) + sizeof(int64_t) * (nqb + 1),
+        SAH_CUDA(cudaMemcpyAsync(st_h, stats,
+                                 sizeof(unsigned long long) * (ST_COUNT + kCtlCounters) + sizeof(int64_t) * (nqb + 1),
                                  cudaMemcpyDeviceToHost, st));
         if (ix->dev_timeout)
           SAH_CUDA(cudaMemcpyAsync(timeout_h, ix->dev_timeout, sizeof(int), cudaMemcpyDeviceToHost, st));

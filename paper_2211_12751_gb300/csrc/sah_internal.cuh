@@ -247,15 +247,16 @@ sah_status run_saalsh(Index* ix, const Survivor* surv, const unsigned long long*
                       unsigned long long* stats, int stat_items, cudaStream_t st, int* launches);
 // user_pass_tc.cu: the user pass on tcgen05 over every user tile and the distinct query
 // vectors of the sub-batch (nq <= 4096 rows).
-//  prepare_user_pass_tc: split hi / lo BF16 queries into Qsplit (2 nq dk entries) and the
-//    column table (distinct vectors, their rows) into scratch (user_pass_tc_scratch_bytes).
+//  prepare_user_pass_tc: the column table (distinct vectors, their rows) into scratch
+//    (user_pass_tc_scratch_bytes); the split hi / lo BF16 queries (2 nq dk entries) are
+//    written by the query preparation.
 //  block_filter_tc: A3 per (leaf, column), the rows' decisions into kept_mask
 //    ([nb][mask_words]) and the counters stats[st_pairs], stats[st_users], stats[st_scored].
 //  run_user_pass_tc: the GEMM and its epilogue; tile_need holds one byte per 128-user tile;
 //    the pairs its band leaves open go to resc and are re-scored in FP32.
 size_t user_pass_tc_scratch_bytes(int nq);
-sah_status prepare_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* scratch, const int32_t* kk,
-                                const int32_t* modes, int nq, cudaStream_t st, int* launches);
+sah_status prepare_user_pass_tc(Index* ix, const float* Qd, void* scratch, const int32_t* kk, const int32_t* modes,
+                                int nq, cudaStream_t st, int* launches);
 sah_status block_filter_tc(Index* ix, const float* Qd, const float* qn, void* scratch, int nq, uint32_t* kept_mask,
                            int mask_words, unsigned long long* stats, int st_pairs, int st_users, int st_scored,
                            cudaStream_t st);

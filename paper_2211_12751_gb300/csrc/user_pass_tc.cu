@@ -248,11 +248,13 @@ __global__ void block_filter_cols_kernel(const float* __restrict__ bcent, const 
                                          int st_pairs, int st_users, int st_scored) {
   extern __shared__ float4 c4s[];   // the leaf's unit centre
   __shared__ uint32_t kbits[kMaxRows / 32];
+  __shared__ float lbs[65];           // the leaf's lower bounds L^k(B), k = 1..k_max
   __shared__ int kept_sh;
   const int B = blockIdx.x;
   const int dp4 = dp / 4;
   for (int i = threadIdx.x; i < dp4; i += blockDim.x)
     c4s[i] = reinterpret_cast<const float4*>(bcent + (int64_t)B * dp)[i];
+  for (int k = threadIdx.x + 1; k <= kmax && k <= 64; k += blockDim.x) lbs[k] = LB[(int64_t)(k - 1) * nb + B];
   for (int i = threadIdx.x; i < mask_words; i += blockDim.x) kbits[i] = 0u;
   if (threadIdx.x == 0) kept_sh = 0;
   __syncthreads();
@@ -266,14 +268,16 @@ __global__ void block_filter_cols_kernel(const float* __restrict__ bcent, const 
     float ub = INFINITY;   // no cone bound: every row kept
     if (!degenerate && nrm > 0.f) {
       const float4* q4 = reinterpret_cast<const float4*>(Qd + (int64_t)rep * dp);
-      float dq = 0.f;
+      float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+#pragma unroll 4
       for (int i = 0; i < dp4; ++i) {
         const float4 a = c4s[i], b = __ldg(q4 + i);
-        dq = fmaf(a.x, b.x, dq);
-        dq = fmaf(a.y, b.y, dq);
-        dq = fmaf(a.z, b.z, dq);
-        dq = fmaf(a.w, b.w, dq);
+        d0 = fmaf(a.x, b.x, d0);
+        d1 = fmaf(a.y, b.y, d1);
+        d2 = fmaf(a.z, b.z, d2);
+        d3 = fmaf(a.w, b.w, d3);
       }
+      const float dq = (d0 + d1) + (d2 + d3);
       const float cphi = fminf(1.f, fmaxf(-1.f, dq / nrm));
       float sphi;
       if (cphi * cphi <= 0.5f) {
@@ -296,7 +300,7 @@ __global__ void block_filter_cols_kernel(const float* __restrict__ bcent, const 
     for (int q = T.start[c]; q < T.start[c + 1]; ++q) {
       const int4 rw = T.rows[q];
       const int j = rw.x & 0x3fffffff, k = rw.y;
-      const float lb = (k <= kmax) ? LB[(int64_t)(k - 1) * nb + B] : -INFINITY;
+      const float lb = (k <= kmax) ? (k <= 64 ? lbs[k] : LB[(int64_t)(k - 1) * nb + B]) : -INFINITY;
       if (!(ub < lb)) {
         atomicOr(&kbits[j >> 5], 1u << (j & 31));
         ++kept;
@@ -912,20 +916,6 @@ __global__ void tile_need_kernel(const int32_t* __restrict__ ublock, int64_t mz,
   if (lane == 0) need[t] = any ? 1 : 0;
 }
 
-// hi = bf16(x), lo = bf16(x - hi) of the queries, K padded to dk with zeros
-__global__ void split_queries_kernel(const float* __restrict__ Qd, int nq, int d, int dp, int dk,
-                                     uint16_t* __restrict__ Qhi, uint16_t* __restrict__ Qlo) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (int64_t)nq * dk) return;
-  const int64_t j = i / dk;
-  const int c = (int)(i % dk);
-  const float v = c < d ? Qd[j * dp + c] : 0.f;
-  const __nv_bfloat16 h = __float2bfloat16_rn(v);
-  const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
-  Qhi[i] = __bfloat16_as_ushort(h);
-  Qlo[i] = __bfloat16_as_ushort(l);
-}
-
 inline unsigned grid_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
 
 template <int KB, int STAGES, int NMAX>
@@ -964,18 +954,13 @@ sah_status launch_pass(Index* ix, UpParams p, int sms, cudaStream_t st, int* lau
 
 size_t user_pass_tc_scratch_bytes(int nq) { return col_table_bytes(nq); }
 
-sah_status prepare_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* scratch, const int32_t* kk,
-                                const int32_t* modes, int nq, cudaStream_t st, int* launches) {
+sah_status prepare_user_pass_tc(Index* ix, const float* Qd, void* scratch, const int32_t* kk, const int32_t* modes,
+                                int nq, cudaStream_t st, int* launches) {
   if (nq == 0 || ix->dk <= 0) return SAH_OK;
   if (nq > kMaxRows) {
     set_error("tensor-core user pass: sub-batch larger than its column table");
     return SAH_ERR_ARG;
   }
-  uint16_t* Qhi = Qsplit;
-  uint16_t* Qlo = Qsplit + (size_t)nq * ix->dk;
-  split_queries_kernel<<<grid_for((int64_t)nq * ix->dk, 256), 256, 0, st>>>(Qd, nq, ix->d, ix->dp, ix->dk, Qhi,
-                                                                           Qlo);
-  SAH_CUDA(cudaGetLastError());
   // the distinct query vectors of the sub-batch
   const ColTable T = col_table_at(scratch, nq);
   int ht = 64;
@@ -984,7 +969,7 @@ sah_status prepare_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, vo
   SAH_TRY(raise_smem_limit((const void*)column_table_kernel, tsmem));
   column_table_kernel<<<1, 1024, tsmem, st>>>(Qd, nq, ix->d, ix->dp, kk, modes, ix->kmax, ix->n, ix->pnorm, ht, T);
   SAH_CUDA(cudaGetLastError());
-  if (launches) *launches += 2;
+  if (launches) *launches += 1;
   return SAH_OK;
 }
 
