@@ -450,8 +450,13 @@ sah_status build_saalsh(Index* ix, const float* srp_host, cudaStream_t st) {
   const int64_t ni = n - first;
   uint16_t* icodes = nullptr;
   SAH_CUDA(cudaMallocAsync((void**)&icodes, sizeof(uint16_t) * ni * K, st));
-  item_codes_kernel<<<grid_for(ni * K, 256), 256, 0, st>>>(ix->Ps, d, dp, first, n, part_of_d, ix->sa_cent,
-                                                           ix->sa_R, ix->sa_A, ix->sa_d1p, K, bits, icodes);
+  if (ix->dk > 0 && d + 1 <= 128) {
+    // BF16 precision: the projections on the tensor cores
+    SAH_TRY(item_codes_tc(ix, first, part_of_d, A_pad.data(), ix->sa_d1p, K, bits, icodes, st));
+  } else {
+    item_codes_kernel<<<grid_for(ni * K, 256), 256, 0, st>>>(ix->Ps, d, dp, first, n, part_of_d, ix->sa_cent,
+                                                             ix->sa_R, ix->sa_A, ix->sa_d1p, K, bits, icodes);
+  }
   SAH_CUDA(cudaGetLastError());
   std::vector<uint16_t> ic((size_t)ni * K);
   SAH_CUDA(cudaMemcpyAsync(ic.data(), icodes, sizeof(uint16_t) * ic.size(), cudaMemcpyDeviceToHost, st));
@@ -500,7 +505,10 @@ sah_status build_saalsh(Index* ix, const float* srp_host, cudaStream_t st) {
   if (ix->m_nz > 0) {
     SAH_TRY(dev_alloc(ix, (void**)&ix->sa_ucode, sizeof(uint16_t) * (size_t)ix->m_nz * K));
     const size_t smem = sizeof(float) * (size_t)(kCodeUsers + kCodeTables * bits) * (d | 1);
-    if (smem <= 160 * 1024) {
+    if (ix->dk == 64 || ix->dk == 128) {
+      // BF16 precision: the projections on the tensor cores
+      SAH_TRY(user_codes_tc(ix, A_pad.data(), ix->sa_d1p, K, bits, ix->sa_ucode, st));
+    } else if (smem <= 160 * 1024) {
       if (smem > 48 * 1024)
         SAH_TRY(raise_smem_limit((const void*)user_codes_kernel, (size_t)((int)smem)));
       dim3 g(grid_for(ix->m_nz, kCodeUsers), (K + kCodeTables - 1) / kCodeTables);

@@ -272,6 +272,16 @@ sah_status topk_full_tc(Index* ix, float* vlast, int32_t* ids64, cudaStream_t st
 sah_status build_bf16_copies(Index* ix, cudaStream_t st);
 // Decides every survivor with the tcgen05 kernel and sets the answer bits; the counters
 // of double-precision decisions and scanned items go to stats[stat_fp64], stats[stat_items].
+// codes_tc.cu
+// SA-ALSH user codes ([m_nz][K], bits per table) on the tensor cores from the BF16 user
+// copies; A_host is the SRP matrix (K * bits rows of stride a_stride, the first d
+// coordinates used).  Synchronous with respect to the host matrix (copied before return).
+sah_status user_codes_tc(Index* ix, const float* A_host, int a_stride, int K, int bits, uint16_t* codes,
+                         cudaStream_t st);
+// The same for the items from `first` on ([n - first][K]), transformed for their
+// partitions (part_of[i - first], the partition centres and radii of the index), d < 128.
+sah_status item_codes_tc(Index* ix, int64_t first, const int32_t* part_of, const float* A_host, int a_stride, int K,
+                         int bits, uint16_t* codes, cudaStream_t st);
 // rescore.cu
 // FP32 (and, with exact thresholds, double-precision) re-score of the pairs listed in
 // pairs[0, *count) (at most cap): "yes" pairs set their answer bit, open ones go to surv.

@@ -47,8 +47,9 @@ def test_full_probe_is_exact(sah):
             assert np.array_equal(ix.rkmips(q, k, mode=sah.SAALSH), oracle.rkmips(W.U, W.P, q, k))
 
 
-def test_agrees_with_oracle_alg2(sah):
-    W, A, ix = _setup(sah, m=500, n=600)
+@pytest.mark.parametrize("precision", [0, 1])   # FP32 codes; tensor-core (split BF16) codes
+def test_agrees_with_oracle_alg2(sah, precision):
+    W, A, ix = _setup(sah, m=500, n=600, precision=precision)
     rix = ref.sah_index(W.P, W.U, kmax=20, N0=32, p_prime=40, A=A.astype(np.float64), n_tables=8,
                         code_bits=6, b=0.5)
     agree, total = 0, 0
