@@ -317,7 +317,7 @@ def main():
 
     def build(threshold, precision, tc_user_pass=0):
         pp = (1 << 30) if threshold == "full" else 0
-        prec = sah.BF16 if precision == "bf16" else sah.FP32
+        prec = {"bf16": sah.BF16, "fp8": sah.FP8}.get(precision, sah.FP32)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ix = sah.Index(W.U, W.P, k_max=50, leaf_size=args.leaf_size, p_prime=pp, seed=0, precision=prec,
@@ -488,7 +488,9 @@ def main():
         line["variants"] = {}
         vsteps = max(3, args.steps // 2)
         for thr in ("full", "paper"):
-            for prec, tc in (("fp32", 0), ("bf16", 0), ("bf16", 1)):
+            for prec, tc in (("fp32", 0), ("bf16", 0), ("bf16", 1), ("fp8", 1)):
+                if prec == "fp8" and thr == "full":
+                    continue   # FP8 changes only the SA-ALSH codes, measured with the paper's |P'|
                 name = f"{thr}_{prec}" + ("_tc_user_pass" if tc else "")
                 same = thr == args.threshold and prec == args.precision and tc == tc_main
                 ixv, bv = (ix, build_s) if same else build(thr, prec, tc_user_pass=tc)
@@ -511,7 +513,7 @@ def main():
                         tf = 2.0 * W.d * items / (sm7 / 1e3) / 1e12
                         rec["verify_gemm"] = {"kernel": "verify_tc_kernel", "ms": sm7, "tflops_algorithmic": tf,
                                               "peak_tflops": peaks["bf16_tflops"], "frac": tf / peaks["bf16_tflops"]}
-                if thr == "paper" and not tc:
+                if thr == "paper" and (not tc or prec == "fp8"):
                     sa_modes = np.full(nq, sah.SAALSH, np.int32)
                     hsa, tsa, _, _, stsa, _ = measure(ixv, vsteps, 3, timing=False, modes=sa_modes)
                     exact_sets = host if same else ixv.rkmips_batch(Q, K)

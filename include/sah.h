@@ -54,7 +54,10 @@ typedef enum {
 typedef enum { SAH_EXACT = 0, SAH_SAALSH = 1 } sah_mode;
 
 /* Working precision of the user x query and user x item scores.  Every mode is exact
- * in SAH_EXACT: a lower precision only widens the error band that is re-scored. */
+ * in SAH_EXACT: a lower precision only widens the error band that is re-scored.
+ * SAH_FP8: the scores as with SAH_BF16, and the SA-ALSH projections (item and user codes)
+ * in FP8 E4M3 on the tensor cores, every vector scaled by its own max |x| / 448 (a code
+ * bit can differ from the exact sign only near zero); d <= 127. */
 typedef enum { SAH_FP32 = 0, SAH_BF16 = 1, SAH_FP8 = 2 } sah_precision;
 
 typedef struct {

@@ -148,12 +148,16 @@ sah_status sah_build_index(const float* U, int64_t m, const float* P, int64_t n,
     sah::set_error("sah_build_index: parameter out of range");
     return SAH_ERR_ARG;
   }
-  if (prm.precision != SAH_FP32 && prm.precision != SAH_BF16) {
-    sah::set_error("sah_build_index: precision must be SAH_FP32 or SAH_BF16 in this build");
-    return SAH_ERR_UNSUPPORTED;
+  if (prm.precision != SAH_FP32 && prm.precision != SAH_BF16 && prm.precision != SAH_FP8) {
+    sah::set_error("sah_build_index: precision must be SAH_FP32, SAH_BF16 or SAH_FP8");
+    return SAH_ERR_ARG;
   }
   if (prm.precision == SAH_BF16 && d > 128) {
     sah::set_error("sah_build_index: the BF16 tensor-core path supports d <= 128");
+    return SAH_ERR_UNSUPPORTED;
+  }
+  if (prm.precision == SAH_FP8 && d > 127) {
+    sah::set_error("sah_build_index: SAH_FP8 supports d <= 127 (item codes use d + 1 coordinates)");
     return SAH_ERR_UNSUPPORTED;
   }
   cudaStream_t st = (cudaStream_t)cuda_stream;

@@ -450,7 +450,10 @@ sah_status build_saalsh(Index* ix, const float* srp_host, cudaStream_t st) {
   const int64_t ni = n - first;
   uint16_t* icodes = nullptr;
   SAH_CUDA(cudaMallocAsync((void**)&icodes, sizeof(uint16_t) * ni * K, st));
-  if (ix->dk > 0 && d + 1 <= 128) {
+  if (ix->prm.precision == SAH_FP8) {
+    // FP8 E4M3 projections on the tensor cores
+    SAH_TRY(codes_f8(ix, ix->Ps, first, n, part_of_d, A_pad.data(), ix->sa_d1p, K, bits, icodes, st));
+  } else if (ix->dk > 0 && d + 1 <= 128) {
     // BF16 precision: the projections on the tensor cores
     SAH_TRY(item_codes_tc(ix, first, part_of_d, A_pad.data(), ix->sa_d1p, K, bits, icodes, st));
   } else {
@@ -505,7 +508,9 @@ sah_status build_saalsh(Index* ix, const float* srp_host, cudaStream_t st) {
   if (ix->m_nz > 0) {
     SAH_TRY(dev_alloc(ix, (void**)&ix->sa_ucode, sizeof(uint16_t) * (size_t)ix->m_nz * K));
     const size_t smem = sizeof(float) * (size_t)(kCodeUsers + kCodeTables * bits) * (d | 1);
-    if (ix->dk == 64 || ix->dk == 128) {
+    if (ix->prm.precision == SAH_FP8) {
+      SAH_TRY(codes_f8(ix, ix->Ut, 0, ix->m_nz, nullptr, A_pad.data(), ix->sa_d1p, K, bits, ix->sa_ucode, st));
+    } else if (ix->dk == 64 || ix->dk == 128) {
       // BF16 precision: the projections on the tensor cores
       SAH_TRY(user_codes_tc(ix, A_pad.data(), ix->sa_d1p, K, bits, ix->sa_ucode, st));
     } else if (smem <= 160 * 1024) {

@@ -282,6 +282,10 @@ sah_status user_codes_tc(Index* ix, const float* A_host, int a_stride, int K, in
 // partitions (part_of[i - first], the partition centres and radii of the index), d < 128.
 sah_status item_codes_tc(Index* ix, int64_t first, const int32_t* part_of, const float* A_host, int a_stride, int K,
                          int bits, uint16_t* codes, cudaStream_t st);
+// FP8 E4M3 codes (precision SAH_FP8): the rows X[first, n) of stride dp, as users
+// (part_of null, d coordinates) or as items transformed for their partitions (d + 1).
+sah_status codes_f8(Index* ix, const float* X, int64_t first, int64_t n, const int32_t* part_of, const float* A_host,
+                    int a_stride, int K, int bits, uint16_t* codes, cudaStream_t st);
 // rescore.cu
 // FP32 (and, with exact thresholds, double-precision) re-score of the pairs listed in
 // pairs[0, *count) (at most cap): "yes" pairs set their answer bit, open ones go to surv.

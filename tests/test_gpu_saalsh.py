@@ -24,7 +24,7 @@ def _setup(sah, probe_radius=0, K=8, bits=6, m=1200, n=900, p_prime=40, precisio
     return W, A, ix
 
 
-@pytest.mark.parametrize("precision,tc", [(0, 0), (1, 0), (1, 1)])
+@pytest.mark.parametrize("precision,tc", [(0, 0), (1, 0), (1, 1), (2, 1)])
 def test_superset_of_exact_and_f1(sah, precision, tc):
     W, A, ix = _setup(sah, precision=precision, tc_user_pass=tc)
     f1s = []
@@ -39,16 +39,19 @@ def test_superset_of_exact_and_f1(sah, precision, tc):
     assert np.mean(f1s) > 0.5
 
 
-def test_full_probe_is_exact(sah):
-    W, A, ix = _setup(sah, probe_radius=6)
+@pytest.mark.parametrize("precision", [0, 2])
+def test_full_probe_is_exact(sah, precision):
+    W, A, ix = _setup(sah, probe_radius=6, precision=precision)
     for qi in W.query_idx[:4]:
         q = W.P[qi]
         for k in (1, 10, 20):
             assert np.array_equal(ix.rkmips(q, k, mode=sah.SAALSH), oracle.rkmips(W.U, W.P, q, k))
 
 
-@pytest.mark.parametrize("precision", [0, 1])   # FP32 codes; tensor-core (split BF16) codes
-def test_agrees_with_oracle_alg2(sah, precision):
+# FP32 codes; tensor-core codes with split BF16 and with FP8 E4M3 operands (more code bits
+# fall on the other side of zero with FP8: a looser bar)
+@pytest.mark.parametrize("precision,bar", [(0, 0.95), (1, 0.95), (2, 0.8)])
+def test_agrees_with_oracle_alg2(sah, precision, bar):
     W, A, ix = _setup(sah, m=500, n=600, precision=precision)
     rix = ref.sah_index(W.P, W.U, kmax=20, N0=32, p_prime=40, A=A.astype(np.float64), n_tables=8,
                         code_bits=6, b=0.5)
@@ -60,10 +63,10 @@ def test_agrees_with_oracle_alg2(sah, precision):
             want = set(ref.sah_query(rix, q, k, "saalsh", probe_radius=0).tolist())
             agree += len(got & want)
             total += len(got | want)
-    assert total == 0 or agree / total >= 0.95
+    assert total == 0 or agree / total >= bar
 
 
-@pytest.mark.parametrize("precision,tc", [(0, 0), (1, 1)])
+@pytest.mark.parametrize("precision,tc", [(0, 0), (1, 1), (2, 1)])
 def test_mixed_modes_in_one_batch(sah, precision, tc):
     W, A, ix = _setup(sah, precision=precision, tc_user_pass=tc)
     Q = np.repeat(W.P[W.query_idx[:5]], 2, axis=0)
@@ -78,3 +81,10 @@ def test_mixed_modes_in_one_batch(sah, precision, tc):
         else:
             assert set(exact.tolist()) <= set(got[r].tolist())
             assert np.array_equal(got[r], ix.rkmips(Q[r], 10, mode=sah.SAALSH))
+
+
+def test_fp8_dimension_limit(sah):
+    W = workload.make("c1", m=300, n=200, d=128)
+    with pytest.raises(sah.SahError) as e:
+        sah.Index(W.U, W.P, k_max=10, leaf_size=32, precision=2)
+    assert e.value.status == sah.SAH_ERR_UNSUPPORTED
