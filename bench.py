@@ -176,16 +176,39 @@ STAGE_KERNELS = {"block_pass": "block_filter_kernel", "user_pass": "user_scan_re
                  "saalsh": "saalsh_decide_kernel"}
 
 
+def kernel_source_hash(path: str, kernel: str):
+    """sha256 (16 hex digits) of a kernel's definition text: from the line that starts its
+    declaration (a template line, or the __global__ line) to the brace that closes its body."""
+    lines = open(path).read().split("\n")
+    for i, line in enumerate(lines):
+        if kernel + "(" in line and "<<<" not in line and not line.lstrip().startswith("//"):
+            j = i
+            while j > 0 and "__global__" not in lines[j]:
+                j -= 1
+            if "__global__" not in lines[j]:
+                continue
+            if j > 0 and lines[j - 1].startswith("template"):
+                j -= 1
+            depth, started, k = 0, False, i
+            while k < len(lines):
+                depth += lines[k].count("{") - lines[k].count("}")
+                started = started or "{" in lines[k]
+                if started and depth == 0:
+                    break
+                k += 1
+            return hashlib.sha256("\n".join(lines[j:k + 1]).encode()).hexdigest()[:16]
+    return None
+
+
 def kernel_traffic(kernel: str):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel's source is
-    unchanged since it was taken (matched by the source file's hash)."""
+    """DRAM bytes per launch from a committed ncu summary, if the kernel's definition is
+    unchanged since it was taken (matched by the hash of its source text)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f).get(kernel)
         src = os.path.join(ROOT, "paper_2211_12751_gb300", "csrc", rec["source"])
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if h == rec["source_sha256_16"]:
+        if kernel_source_hash(src, kernel) == rec["kernel_sha256_16"]:
             return rec["dram_bytes_per_launch"]
     except Exception:
         pass

@@ -219,6 +219,8 @@ struct SaParams {
   const float* R;
   const uint16_t* ucode;
   const int32_t* boff;
+  const int32_t* rbin;
+  int nbin, rshift;
   const uint16_t* bcode;
   const int32_t* bitem;
   const uint32_t* probes;
@@ -282,9 +284,13 @@ __global__ void __launch_bounds__(kSaWarps * 32) saalsh_decide_kernel(SaParams p
               const int t = task / prm.nprobes, pr = task % prm.nprobes;
               const uint32_t code = prm.ucode[(int64_t)S.upos * prm.K + t] ^ prm.probes[pr];
               const int seg = j * prm.K + t;
-              const int b0 = prm.boff[seg], b1 = prm.boff[seg + 1];
-              const int l = lower_bound_u16(prm.bcode, b0, b1, code);
-              const int h = lower_bound_u16(prm.bcode, l, b1, code + 1);
+              const int b0 = prm.boff[seg];
+              // the codes with the same top bits first (radix index), then a short search
+              const int32_t* rb = prm.rbin + (int64_t)seg * (prm.nbin + 1);
+              const int c8 = (int)(code >> prm.rshift);
+              const int lo8 = b0 + rb[c8], hi8 = b0 + rb[c8 + 1];
+              const int l = lower_bound_u16(prm.bcode, lo8, hi8, code);
+              const int h = lower_bound_u16(prm.bcode, l, hi8, code + 1);
               lo = l;
               len = h - l;
             }
@@ -309,10 +315,18 @@ __global__ void __launch_bounds__(kSaWarps * 32) saalsh_decide_kernel(SaParams p
               int id = -1;
               if (c < qn_) {
                 id = q[c];
-                const float* p = prm.Ps + (int64_t)id * prm.dp;
-                float s = 0.f;
-                for (int e = 0; e < prm.dp; ++e) s = fmaf(u[e], p[e], s);
-                v = s;
+                const float4* p4 = reinterpret_cast<const float4*>(prm.Ps + (int64_t)id * prm.dp);
+                const float4* u4 = reinterpret_cast<const float4*>(u);
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll 4
+                for (int e = 0; e < prm.dp / 4; ++e) {
+                  const float4 pa = p4[e], ua = u4[e];
+                  s0 = fmaf(ua.x, pa.x, s0);
+                  s1 = fmaf(ua.y, pa.y, s1);
+                  s2 = fmaf(ua.z, pa.z, s2);
+                  s3 = fmaf(ua.w, pa.w, s3);
+                }
+                v = (s0 + s1) + (s2 + s3);
               }
               scored += (c < qn_) ? 1 : 0;
               unsigned cand = __ballot_sync(0xffffffffu, v > phi);
@@ -497,6 +511,22 @@ sah_status build_saalsh(Index* ix, const float* srp_host, cudaStream_t st) {
     }
     for (auto& th : pool) th.join();
   }
+  // radix index of every segment on the codes' top bits (at most 8 of them)
+  ix->sa_rshift = bits > 8 ? bits - 8 : 0;
+  ix->sa_nbin = 1 << (bits - ix->sa_rshift);
+  std::vector<int32_t> rbin((size_t)t * K * (ix->sa_nbin + 1));
+  for (int seg = 0; seg < t * K; ++seg) {
+    int32_t* rb = rbin.data() + (size_t)seg * (ix->sa_nbin + 1);
+    const int32_t b0 = boff[seg], b1 = boff[seg + 1];
+    int32_t o = b0;
+    for (int c = 0; c <= ix->sa_nbin; ++c) {
+      // first position of the segment whose code's top bits are >= c
+      while (o < b1 && (int)(bcode[o] >> ix->sa_rshift) < c) ++o;
+      rb[c] = o - b0;
+    }
+  }
+  SAH_TRY(dev_alloc(ix, (void**)&ix->sa_rbin, sizeof(int32_t) * rbin.size()));
+  SAH_CUDA(cudaMemcpyAsync(ix->sa_rbin, rbin.data(), sizeof(int32_t) * rbin.size(), cudaMemcpyHostToDevice, st));
   SAH_TRY(dev_alloc(ix, (void**)&ix->sa_boff, sizeof(int32_t) * boff.size()));
   SAH_TRY(dev_alloc(ix, (void**)&ix->sa_bcode, sizeof(uint16_t) * bcode.size()));
   SAH_TRY(dev_alloc(ix, (void**)&ix->sa_bitem, sizeof(int32_t) * bitem.size()));
@@ -573,6 +603,9 @@ sah_status run_saalsh(Index* ix, const Survivor* surv, const unsigned long long*
   p.R = ix->sa_R;
   p.ucode = ix->sa_ucode;
   p.boff = ix->sa_boff;
+  p.rbin = ix->sa_rbin;
+  p.nbin = ix->sa_nbin;
+  p.rshift = ix->sa_rshift;
   p.bcode = ix->sa_bcode;
   p.bitem = ix->sa_bitem;
   p.probes = ix->sa_probes;

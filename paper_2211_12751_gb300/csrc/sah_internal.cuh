@@ -146,6 +146,9 @@ struct Index {
   float* sa_A = nullptr;             // (K * bits) x d1p SRP projection vectors
   uint16_t* sa_ucode = nullptr;      // m_nz x K user codes (leaf order)
   int32_t* sa_boff = nullptr;        // t * K + 1 bucket-array offsets
+  int32_t* sa_rbin = nullptr;        // per (partition, table): sa_nbin + 1 offsets (relative to the
+                                     // segment) of the codes by their top bits: a radix index
+  int32_t sa_nbin = 0, sa_rshift = 0;
   uint16_t* sa_bcode = nullptr;      // codes, sorted within each (partition, table)
   int32_t* sa_bitem = nullptr;       // matching item positions
   uint32_t* sa_probes = nullptr;     // XOR masks with popcount <= probe_radius
