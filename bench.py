@@ -504,7 +504,7 @@ def main():
             "roofline": roof,
             "stages_ms": {nm: float(stage_ms[i]) for i, nm in enumerate(STAGE_NAMES)},
             "stage_counts": {k: st[k] for k in ("block_pairs_total", "block_pairs_kept", "users_in_kept_blocks",
-                                                "users_scored", "users_yes_early", "survivors", "fp64_rescored",
+                                                "users_scored", "users_yes_early", "pairs_rescored", "survivors", "fp64_rescored",
                                                 "items_scanned", "results")},
             "index_build_s": build_s, "index_gemm": index_gemm, "clocks": clocks,
             "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99)),

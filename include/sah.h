@@ -224,6 +224,15 @@ sah_status sah_rkmips_bruteforce_noalloc(const float* U, int64_t m, const float*
                                          int32_t d, const float* q, int32_t k, int32_t* out_ids,
                                          int64_t cap, int64_t* out_count, void* cuda_stream);
 
+/* Self-check of the exact float -> double widening that every double-precision inner
+ * product of the count rule (Definition 1, the exact mode above) uses on the GPU: the library's
+ * own conversion (field by field, IEEE 754 binary32 -> binary64) is compared bit for bit
+ * with the GPU's conversion for all 2^32 float bit patterns on the current device (two
+ * NaNs count as equal).  *mismatches receives the number that differ (0 expected).
+ * Synchronous, about 4.3e9 conversions; needs no index.
+ * Errors: SAH_ERR_ARG (mismatches NULL), SAH_ERR_CUDA. */
+sah_status sah_selftest_f2d(uint64_t* mismatches);
+
 /* Frees the index and every device buffer it owns.  NULL is ignored. */
 void sah_free_index(sah_index* index);
 

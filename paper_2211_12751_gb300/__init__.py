@@ -115,6 +115,8 @@ def load(path: Optional[str] = None):
     lib.sah_server_info.restype = I32
     lib.sah_server_stop.argtypes = [P]
     lib.sah_server_stop.restype = I32
+    lib.sah_selftest_f2d.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
+    lib.sah_selftest_f2d.restype = I32
     lib.sah_free_index.argtypes = [P]
     lib.sah_free_index.restype = None
     lib.sah_status_string.argtypes = [I32]
@@ -171,6 +173,14 @@ def rkmips_bruteforce_noalloc(U, P, q, k: int, out_ids, out_count, m: Optional[i
     _check(lib.sah_rkmips_bruteforce_noalloc(U.data_ptr(), m, P.data_ptr(), P.shape[0], U.shape[1],
                                              q.data_ptr(), int(k), out_ids.data_ptr(), out_ids.numel(),
                                              out_count.data_ptr(), _stream_handle(stream)))
+
+
+def selftest_f2d() -> int:
+    """sah_selftest_f2d: the number of float bit patterns whose double widening by the
+    library differs from the GPU's own conversion (0 expected)."""
+    n = ctypes.c_uint64(0)
+    _check(load().sah_selftest_f2d(ctypes.byref(n)))
+    return int(n.value)
 
 
 class Index:

@@ -36,6 +36,21 @@ sah_status raise_smem_limit(const void* fn, size_t bytes) {
   return SAH_OK;
 }
 
+namespace {
+// Every float bit pattern x = base + i: f2d_bits(x) against the hardware conversion, bit
+// for bit (two NaNs count as equal).
+__global__ void selftest_f2d_kernel(uint64_t base, uint64_t count, unsigned long long* bad) {
+  unsigned long long local = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x) {
+    const float x = __uint_as_float((uint32_t)(base + i));
+    const double a = f2d_bits(x), h = (double)x;
+    const bool same = (a != a && h != h) || __double_as_longlong(a) == __double_as_longlong(h);
+    local += same ? 0ull : 1ull;
+  }
+  if (local) atomicAdd(bad, local);
+}
+}  // namespace
+
 sah_status cuda_status(cudaError_t e, const char* what) {
   g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
   cudaGetLastError();   // clear a non-sticky error so the index stays usable
@@ -339,6 +354,27 @@ sah_status sah_index_stats(const sah_index* index, sah_stats* out) {
 }
 
 void sah_free_index(sah_index* index) { destroy_index(index); }
+
+sah_status sah_selftest_f2d(uint64_t* mismatches) {
+  if (!mismatches) {
+    sah::set_error("sah_selftest_f2d: mismatches is NULL");
+    return SAH_ERR_ARG;
+  }
+  unsigned long long* bad = nullptr;
+  SAH_CUDA(cudaMalloc((void**)&bad, sizeof(unsigned long long)));
+  cudaError_t e = cudaMemset(bad, 0, sizeof(unsigned long long));
+  // four launches of 2^30 patterns each
+  for (uint64_t b = 0; e == cudaSuccess && b < (1ull << 32); b += (1ull << 30)) {
+    sah::selftest_f2d_kernel<<<4096, 256>>>(b, 1ull << 30, bad);
+    e = cudaGetLastError();
+  }
+  unsigned long long h = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&h, bad, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(bad);
+  if (e != cudaSuccess) return sah::cuda_status(e, "sah_selftest_f2d");
+  *mismatches = (uint64_t)h;
+  return SAH_OK;
+}
 
 sah_status sah_index_blocks(const sah_index* index, int64_t* m_nz, int32_t* nb, int32_t* ids, int32_t* starts,
                             float* cos_theta, float* cos_omega) {

@@ -56,7 +56,7 @@ __global__ void prep_queries_kernel(const float* __restrict__ Q, int nq, int d, 
                                     float* __restrict__ Qd, float* __restrict__ qn,
                                     const int32_t* __restrict__ ks, int32_t* __restrict__ kk,
                                     const int32_t* __restrict__ modes, unsigned long long* __restrict__ stats,
-                                    uint16_t* __restrict__ Qhi, int dk) {
+                                    uint16_t* __restrict__ Qhi, int dk, uint64_t* __restrict__ qh) {
   int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   int lane = threadIdx.x & 31;
   if (j >= nq) return;
@@ -68,11 +68,18 @@ __global__ void prep_queries_kernel(const float* __restrict__ Q, int nq, int d, 
   }
   float s = 0.f;
   bool fin = true;
+  uint64_t h = 0;   // sum over i of a mix of (i, bits of the padded row's element i)
   for (int i = lane; i < dp; i += 32) {
     float v = (i < d) ? Q[(int64_t)j * d + i] : 0.f;
     fin &= isfinite(v);
     Qd[(int64_t)j * dp + i] = v;
     s = fmaf(v, v, s);
+    h += splitmix64(((uint64_t)i << 32) | __float_as_uint(v));
+  }
+  if (qh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+    if (lane == 0) qh[j] = h;
   }
   if (Qhi) {
     uint16_t* Qlo = Qhi + (int64_t)nq * dk;
@@ -663,65 +670,58 @@ __device__ inline int block_exclusive_scan(int v, int* total) {
   return before + x - v;
 }
 
-// Answers per summary word: one thread per (query j, summary word sw), reading the
-// bitmap words the summary marks (independent loads, all in flight at once).  A query
-// with k > n asks for every user: its words count as full.  The words with answers are
-// listed (in no particular order) for the emission.
-__global__ void answer_count_kernel(const uint32_t* __restrict__ bitmap, int64_t stride, int nq,
-                                    const int32_t* __restrict__ kk, int64_t n, int64_t m,
-                                    int32_t* __restrict__ wcnt, int32_t* __restrict__ list,
-                                    unsigned int* __restrict__ list_count) {
+// Answers per summary word, then their scan, one CTA per query j: a thread per summary
+// word sw reads the bitmap words the summary marks (independent loads, all in flight at
+// once) and counts their bits; a row with k > n counts the summary word's users.  The
+// block scans the counts in chunks of blockDim words and writes each word's exclusive
+// prefix to wpre[j * nsw + sw], appends the words with answers to list (one atomic per
+// warp), and writes the query's total to cnt[j].  The last CTA to finish (a ticket taken
+// after a fence) then turns the totals into the offsets: offsets[j] = base + the answers
+// of the queries before j, offsets[nq] the end (also into offsets2 when given).
+__global__ void answer_count_scan_kernel(const uint32_t* __restrict__ bitmap, int64_t stride,
+                                         const int32_t* __restrict__ kk, int64_t n, int64_t m,
+                                         int32_t* __restrict__ wpre, int32_t* __restrict__ list,
+                                         unsigned int* __restrict__ list_count, int32_t* __restrict__ cnt, int nq,
+                                         int64_t base, int64_t* __restrict__ offsets, int64_t* __restrict__ offsets2,
+                                         unsigned int* __restrict__ ticket) {
   const int64_t w = answer_words(stride);
   const int nsw = (int)(w / 32);
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.x;
   const int lane = threadIdx.x & 31;
-  int c = 0;
-  if (g < nsw * nq) {
-    const int j = g / nsw, sw = g - j * nsw;
-    if (kk[j] > n) {
-      c = (int)std::max<int64_t>(0, std::min<int64_t>(1024, m - (int64_t)sw * 1024));
-    } else {
-      const uint32_t* row = bitmap + (int64_t)j * stride;
-      const uint32_t sm = row[w + sw];
-      if (sm) {
+  const bool all_users = kk[j] > n;
+  const uint32_t* row = bitmap + (int64_t)j * stride;
+  int carry = 0;
+  for (int c0 = 0; c0 < nsw; c0 += blockDim.x) {
+    const int sw = c0 + threadIdx.x;
+    int c = 0;
+    if (sw < nsw) {
+      if (all_users) {
+        c = (int)std::max<int64_t>(0, std::min<int64_t>(1024, m - (int64_t)sw * 1024));
+      } else {
+        const uint32_t sm = row[w + sw];
+        if (sm) {
 #pragma unroll
-        for (int b = 0; b < 32; ++b)
-          if ((sm >> b) & 1u) c += __popc(row[sw * 32 + b]);
+          for (int b = 0; b < 32; ++b)
+            if ((sm >> b) & 1u) c += __popc(row[sw * 32 + b]);
+        }
       }
     }
-    wcnt[g] = c;
-  }
-  const unsigned mk = __ballot_sync(0xffffffffu, c > 0);
-  if (mk) {
-    unsigned base = 0;
-    if (lane == 0) base = atomicAdd(list_count, (unsigned)__popc(mk));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (c > 0) list[base + __popc(mk & ((1u << lane) - 1u))] = g;
-  }
-}
-
-// Per query (one CTA): exclusive scan of its summary-word counts in place, total to cnt[j].
-// The last CTA to finish (a ticket taken after a fence) then turns the totals into the
-// offsets: offsets[j] = base + the answers of the queries before j, offsets[nq] the end
-// (also into offsets2 when given).
-__global__ void answer_scan_kernel(int32_t* __restrict__ wcnt, int64_t nsw, int32_t* __restrict__ cnt, int nq,
-                                   int64_t base, int64_t* __restrict__ offsets, int64_t* __restrict__ offsets2,
-                                   unsigned int* __restrict__ ticket) {
-  int32_t* v = wcnt + (int64_t)blockIdx.x * nsw;
-  const int64_t per = (nsw + blockDim.x - 1) / blockDim.x;
-  const int64_t b = std::min<int64_t>((int64_t)threadIdx.x * per, nsw), e = std::min<int64_t>(b + per, nsw);
-  int s = 0;
-  for (int64_t i = b; i < e; ++i) s += v[i];
-  int total;
-  int acc = block_exclusive_scan(s, &total);
-  for (int64_t i = b; i < e; ++i) {
-    const int x = v[i];
-    v[i] = acc;
-    acc += x;
+    int chunk_total;
+    const int pre = block_exclusive_scan(c, &chunk_total);
+    const int g = j * nsw + sw;
+    if (sw < nsw) wpre[g] = carry + pre;
+    carry += chunk_total;
+    const unsigned mk = __ballot_sync(0xffffffffu, c > 0);
+    if (mk) {
+      unsigned b0 = 0;
+      if (lane == 0) b0 = atomicAdd(list_count, (unsigned)__popc(mk));
+      b0 = __shfl_sync(0xffffffffu, b0, 0);
+      if (c > 0) list[b0 + __popc(mk & ((1u << lane) - 1u))] = g;
+    }
   }
   __shared__ bool last;
   if (threadIdx.x == 0) {
-    cnt[blockIdx.x] = total;
+    cnt[j] = carry;
     __threadfence();
     last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   }
@@ -730,11 +730,11 @@ __global__ void answer_scan_kernel(int32_t* __restrict__ wcnt, int64_t nsw, int3
   __threadfence();
   // the query offsets, in 64 bits: a contiguous run of queries per thread, then a block scan
   __shared__ long long wtot[32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int qper = (nq + blockDim.x - 1) / blockDim.x;
   const int q0 = min((int)threadIdx.x * qper, nq), q1 = min(q0 + qper, nq);
   long long t = 0;
-  for (int j = q0; j < q1; ++j) t += *(volatile int32_t*)&cnt[j];
+  for (int q = q0; q < q1; ++q) t += *(volatile int32_t*)&cnt[q];
   long long x = t;
   for (int o = 1; o < 32; o <<= 1) {
     const long long y = __shfl_up_sync(0xffffffffu, x, o);
@@ -743,15 +743,15 @@ __global__ void answer_scan_kernel(int32_t* __restrict__ wcnt, int64_t nsw, int3
   if (lane == 31) wtot[warp] = x;
   __syncthreads();
   long long before = base, all = base;
-  for (int w = 0; w < nw; ++w) {
-    if (w < warp) before += wtot[w];
-    all += wtot[w];
+  for (int v = 0; v < nw; ++v) {
+    if (v < warp) before += wtot[v];
+    all += wtot[v];
   }
   long long o = before + x - t;
-  for (int j = q0; j < q1; ++j) {
-    offsets[j] = o;
-    if (offsets2) offsets2[j] = o;
-    o += *(volatile int32_t*)&cnt[j];
+  for (int q = q0; q < q1; ++q) {
+    offsets[q] = o;
+    if (offsets2) offsets2[q] = o;
+    o += *(volatile int32_t*)&cnt[q];
   }
   if (threadIdx.x == 0) {
     offsets[nq] = all;
@@ -759,12 +759,15 @@ __global__ void answer_scan_kernel(int32_t* __restrict__ wcnt, int64_t nsw, int3
   }
 }
 
-// Emission, one warp per listed summary word (query j, word sw): lane l takes bitmap
-// word 32 sw + l and writes its ids at offsets[j] plus the scanned count before the
-// summary word plus the lane's share, in ascending order, and clears the words it read,
-// leaving the bitmap zero for the next call.  A row with k > n writes the summary word's
-// 1024 users.  Only if the call's total fits in out_cap; otherwise it raises *overflow and
-// leaves the bitmap as it is.
+// Emission, a warp per batch of kEmitBatch listed summary words (query j, word sw): lanes
+// 0..kEmitBatch-1 read the words' list entries, summaries and output positions, then every
+// lane l reads bitmap word 32 sw + l of each listed word (all loads in flight at once) and
+// writes its ids at offsets[j] plus the scanned count before the summary word plus the
+// lane's share, in ascending order, clearing the words it read so that the bitmap is zero
+// for the next call.  A row with k > n writes the summary word's 1024 users.  Only if the
+// call's total fits in out_cap; otherwise it raises *overflow and leaves the bitmap as it is.
+constexpr int kEmitBatch = 8;
+
 __global__ void answer_emit_kernel(uint32_t* __restrict__ bitmap, int64_t stride,
                                    const int32_t* __restrict__ kk, int64_t n, int64_t m,
                                    const int32_t* __restrict__ wpre, const int32_t* __restrict__ list,
@@ -780,37 +783,61 @@ __global__ void answer_emit_kernel(uint32_t* __restrict__ bitmap, int64_t stride
     if (gw == 0 && lane == 0) atomicExch(overflow, 1ull);
     return;
   }
-  const unsigned nl = *list_count;
-  for (int64_t e = gw; e < nl; e += nwarps) {
-    const int g = list[e];
-    const int j = g / nsw, sw = g - j * nsw;
-    uint32_t* row = bitmap + (int64_t)j * stride;
-    const uint32_t sm = row[w + sw];
-    uint32_t v = 0;
-    if ((sm >> lane) & 1u) {
-      v = row[sw * 32 + lane];
-      row[sw * 32 + lane] = 0u;
+  const int64_t nl = *list_count;
+  for (int64_t e0 = gw * kEmitBatch; e0 < nl; e0 += nwarps * kEmitBatch) {
+    int g = -1;
+    uint32_t sm = 0;
+    int64_t dst = 0;
+    int all = 0;
+    if (lane < kEmitBatch && e0 + lane < nl) {
+      g = list[e0 + lane];
+      const int j = g / nsw, sw = g - j * nsw;
+      sm = bitmap[(int64_t)j * stride + w + sw];
+      dst = offsets[j] + wpre[g];
+      all = kk[j] > n ? 1 : 0;
     }
-    if (lane == 0 && sm) row[w + sw] = 0u;
-    const int64_t dst = offsets[j] + wpre[g];
-    if (kk[j] > n) {
-      const int64_t lo = (int64_t)sw * 1024, hi = std::min<int64_t>(m, lo + 1024);
-      for (int64_t i = lo + lane; i < hi; i += 32) out[dst + (i - lo)] = (int32_t)i;
-      continue;
-    }
-    const int pc = __popc(v);
-    int x = pc;   // inclusive scan over the lanes
+    uint32_t v[kEmitBatch];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+    for (int e = 0; e < kEmitBatch; ++e) {
+      const int ge = __shfl_sync(0xffffffffu, g, e);
+      const uint32_t se = __shfl_sync(0xffffffffu, sm, e);
+      v[e] = 0u;
+      if (ge >= 0 && ((se >> lane) & 1u)) {
+        const int je = ge / nsw, swe = ge - je * nsw;
+        v[e] = bitmap[(int64_t)je * stride + (int64_t)swe * 32 + lane];
+      }
     }
-    int64_t p = dst + x - pc;
-    const int32_t base_id = (int32_t)(((int64_t)sw * 32 + lane) * 32);
-    while (v) {
-      const int i = __ffs(v) - 1;
-      v &= v - 1;
-      out[p++] = base_id + i;
+#pragma unroll
+    for (int e = 0; e < kEmitBatch; ++e) {
+      const int ge = __shfl_sync(0xffffffffu, g, e);
+      const uint32_t se = __shfl_sync(0xffffffffu, sm, e);
+      const int64_t de = __shfl_sync(0xffffffffu, dst, e);
+      const int ae = __shfl_sync(0xffffffffu, all, e);
+      if (ge < 0) continue;   // warp-uniform
+      const int je = ge / nsw, swe = ge - je * nsw;
+      uint32_t* row = bitmap + (int64_t)je * stride;
+      if ((se >> lane) & 1u) row[(int64_t)swe * 32 + lane] = 0u;
+      if (lane == 0 && se) row[w + swe] = 0u;
+      if (ae) {
+        const int64_t lo = (int64_t)swe * 1024, hi = std::min<int64_t>(m, lo + 1024);
+        for (int64_t i = lo + lane; i < hi; i += 32) out[de + (i - lo)] = (int32_t)i;
+        continue;
+      }
+      uint32_t x = v[e];
+      const int pc = __popc(x);
+      int incl = pc;   // inclusive scan over the lanes
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      int64_t p = de + incl - pc;
+      const int32_t base_id = (int32_t)(((int64_t)swe * 32 + lane) * 32);
+      while (x) {
+        const int i = __ffs(x) - 1;
+        x &= x - 1;
+        out[p++] = base_id + i;
+      }
     }
   }
 }
@@ -820,10 +847,11 @@ __global__ void answer_emit_kernel(uint32_t* __restrict__ bitmap, int64_t stride
 // ---------------------------------------------------------------- workspace
 namespace {
 
+constexpr int kAnswerThreads = 512;   // summary words counted and scanned per step of a query's CTA
 constexpr int kCtlCounters = 5;   // survivor counts (3), answer-list length, scan ticket
 
 struct WsLayout {
-  size_t qd, qb, qn, kk, pairs, pcount, kmask, tneed, coltab, survcnt, alist_n, ticket, bitmap, chunk, offsets, stats,
+  size_t qd, qb, qn, qh, kk, pairs, pcount, kmask, tneed, coltab, survcnt, alist_n, ticket, bitmap, chunk, offsets, stats,
       total;
 };
 
@@ -838,12 +866,13 @@ WsLayout layout_for(const Index* ix, int qb) {
   L.qd = take(sizeof(float) * (size_t)qb * ix->dp);
   L.qb = take(2 * sizeof(uint16_t) * (size_t)qb * std::max(ix->dk, 1));   // hi and lo parts
   L.qn = take(sizeof(float) * qb);
+  L.qh = take(sizeof(uint64_t) * qb);
   L.kk = take(sizeof(int32_t) * qb);
   L.pairs = take(sizeof(PairEntry) * (size_t)std::max(ix->nb, 1) * qb);
   L.pcount = take(sizeof(int32_t) * std::max(ix->nb, 1));
   L.kmask = take(sizeof(uint32_t) * (size_t)std::max(ix->nb, 1) * ((qb + 31) / 32));
   L.tneed = take((size_t)std::max<int64_t>((ix->m_nz + 127) / 128, 1));
-  L.coltab = take(user_pass_tc_scratch_bytes(qb));
+  L.coltab = take(user_pass_tc_scratch_bytes(qb, ix->dp));
   L.chunk = take(sizeof(int32_t) * ((size_t)qb * (2 * (answer_words(answer_stride(ix->m)) / 32) + 1)));
   // the control block, contiguous so that one memset clears its counters and one copy
   // reads it back: stats[ST_COUNT] | survivor counts[3] | answer-list length (u64) |
@@ -1046,7 +1075,6 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
       // the answer bitmaps must start zero: the emit pass of a completed call leaves them
       // so; after a reallocation, a larger sub-batch or a call that stopped early, clear them
       const size_t bm_bytes = sizeof(uint32_t) * (size_t)nqb * words;
-      const unsigned ans_grid = (unsigned)((nqb * nsw + 255) / 256);   // a thread per summary word
       const unsigned emit_grid = (unsigned)std::max(1, sms * 8);             // warps over the listed words
       if (cx->bm_clean_base != cx->ws.base || cx->bm_clean_bytes < bm_bytes) {
         SAH_CUDA(cudaMemsetAsync((char*)cx->ws.base + L.bitmap, 0, bm_bytes, st));
@@ -1094,7 +1122,8 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
         const bool tc_pass = ix->nb > 0 && ix->dk > 0 && ix->prm.tc_user_pass && ix->m_nz > 0;
         prep_queries_kernel<<<grid_for(nqb, 8), 256, 0, st>>>(Q_dev + (int64_t)q0 * ix->d, nqb, ix->d, ix->dp, Qd, qn,
                                                                ks_dev + q0, kk, modes_q, stats,
-                                                               tc_pass ? (uint16_t*)(w + L.qb) : nullptr, ix->dk);
+                                                               tc_pass ? (uint16_t*)(w + L.qb) : nullptr, ix->dk,
+                                                               tc_pass ? (uint64_t*)(w + L.qh) : nullptr);
         SAH_CUDA(cudaGetLastError());
         tm.end(0, 1);
         if (ix->nb > 0) {
@@ -1104,8 +1133,9 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
           int bf_launches = 1;
           if (tc_pass) {
             // the distinct query vectors first: the block bound is taken once per vector
-            SAH_TRY(prepare_user_pass_tc(ix, Qd, w + L.coltab, kk, modes_q, nqb, st, &bf_launches));
-            SAH_TRY(block_filter_tc(ix, Qd, qn, w + L.coltab, nqb, kmask, mask_words, stats, ST_PAIRS_KEPT,
+            SAH_TRY(prepare_user_pass_tc(ix, Qd, qn, (const uint64_t*)(w + L.qh), w + L.coltab, kk, modes_q, nqb,
+                                         st, &bf_launches));
+            SAH_TRY(block_filter_tc(ix, w + L.coltab, nqb, kmask, mask_words, stats, ST_PAIRS_KEPT,
                                     ST_KEPT_USERS, ST_USERS_SCORED, st));
           } else {
             block_filter_kernel<<<ix->nb, 128, sizeof(float) * ix->dp, st>>>(
@@ -1175,7 +1205,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
           }
         }
         tm.begin(4);
-        int n_compact = 3;
+        int n_compact = 2;
         if (ix->nzero > 0) {
           zero_users_kernel<<<grid_for(ix->nzero * nqb, 256), 256, 0, st>>>(ix->zero_uid, ix->nzero, nqb, bitmap,
                                                                              words);
@@ -1186,9 +1216,9 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
         int32_t* qcnt = chunk + (int64_t)nqb * nsw;
         int32_t* alist = qcnt + nqb;
         unsigned int* alist_n = (unsigned int*)(w + L.alist_n);
-        answer_count_kernel<<<ans_grid, 256, 0, st>>>(bitmap, words, nqb, kk, ix->n, ix->m, chunk, alist, alist_n);
-        answer_scan_kernel<<<nqb, 256, 0, st>>>(chunk, nsw, qcnt, nqb, direct ? 0 : res_total, offsets,
-                                                direct ? offsets_dev : nullptr, (unsigned int*)(w + L.ticket));
+        answer_count_scan_kernel<<<nqb, kAnswerThreads, 0, st>>>(
+            bitmap, words, kk, ix->n, ix->m, chunk, alist, alist_n, qcnt, nqb, direct ? 0 : res_total, offsets,
+            direct ? offsets_dev : nullptr, (unsigned int*)(w + L.ticket));
         int32_t* dst;
         int64_t dst_cap;
         if (direct) {

@@ -11,8 +11,9 @@
 namespace sah {
 namespace {
 
-// DP4 > 0: rows of at most 4 DP4 floats, held in registers for both the FP32 and the
-// double-precision dot (no second pass over memory); DP4 = 0: any width, read as needed.
+// DP4 > 0: user rows of at most 4 DP4 floats, held in registers for both the FP32 and the
+// double-precision dot (the query row is read twice, the second time from L1); DP4 = 0:
+// any width, read as needed.
 template <int DP4>
 __global__ void pair_rescore_kernel(const Survivor* __restrict__ pairs, const unsigned long long* __restrict__ count,
                                     int64_t cap, const float* __restrict__ Ut, const float* __restrict__ unorm,
@@ -30,10 +31,12 @@ __global__ void pair_rescore_kernel(const Survivor* __restrict__ pairs, const un
   const int64_t total = block_count(count, cap);   // synchronises the block
   if (stop) return;
   // warp-strided, so that every lane runs the same iterations and the appends to the
-  // lists and counters go out once per warp
+  // lists and counters go out once per warp; consecutive 32-pair chunks go to warps of
+  // different CTAs, so that a short list still spreads over the SMs
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t w0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; w0 < total; w0 += nw * 32) {
+  const int64_t wid = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+  for (int64_t w0 = wid * 32; w0 < total; w0 += nw * 32) {
     const int64_t i = w0 + lane;
     bool yes = false, surv_flag = false, sa_row = false, fp64 = false;
     int r = 0, j = 0;
@@ -47,19 +50,17 @@ __global__ void pair_rescore_kernel(const Survivor* __restrict__ pairs, const un
         const int k = kk[j];
         const float4* u4 = reinterpret_cast<const float4*>(Ut + (int64_t)r * dp);
         const float4* q4 = reinterpret_cast<const float4*>(Qd + (int64_t)j * dp);
-        float4 ur[DP4 > 0 ? DP4 : 1], qr[DP4 > 0 ? DP4 : 1];
+        float4 ur[DP4 > 0 ? DP4 : 1];
         if (DP4 > 0) {
 #pragma unroll
-          for (int c = 0; c < DP4; ++c) {
-            ur[c] = c < dp / 4 ? u4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
-            qr[c] = c < dp / 4 ? q4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
-          }
+          for (int c = 0; c < DP4; ++c) ur[c] = c < dp / 4 ? u4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
           for (int c = 0; c < DP4; ++c) {
-            acc = fmaf(ur[c].x, qr[c].x, acc);
-            acc = fmaf(ur[c].y, qr[c].y, acc);
-            acc = fmaf(ur[c].z, qr[c].z, acc);
-            acc = fmaf(ur[c].w, qr[c].w, acc);
+            const float4 b = c < dp / 4 ? __ldg(q4 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+            acc = fmaf(ur[c].x, b.x, acc);
+            acc = fmaf(ur[c].y, b.y, acc);
+            acc = fmaf(ur[c].z, b.z, acc);
+            acc = fmaf(ur[c].w, b.w, acc);
           }
         } else {
           for (int c = 0; c < dp / 4; ++c) {
@@ -89,11 +90,12 @@ __global__ void pair_rescore_kernel(const Survivor* __restrict__ pairs, const un
               // the sequential double-precision sum i = 0..d-1 over the registers
 #pragma unroll
               for (int c = 0; c < DP4; ++c) {
+                const float4 b = c < dp / 4 ? __ldg(q4 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
                 const float a4[4] = {ur[c].x, ur[c].y, ur[c].z, ur[c].w};
-                const float b4[4] = {qr[c].x, qr[c].y, qr[c].z, qr[c].w};
+                const float b4[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
-                  if (4 * c + e < d) s64 = __fma_rn((double)a4[e], (double)b4[e], s64);
+                  if (4 * c + e < d) s64 = __fma_rn(f2d_bits(a4[e]), f2d_bits(b4[e]), s64);
               }
             } else {
               s64 = dot64_seq(Ut + (int64_t)r * dp, Qd + (int64_t)j * dp, d);
@@ -142,7 +144,12 @@ sah_status launch_pair_rescore(Index* ix, const Survivor* pairs, const unsigned 
   // rows in registers pay off where most pairs also take the double-precision dot (exact
   // thresholds); otherwise the narrower kernel keeps more warps in flight
   auto fn = (ix->T64 != nullptr && ix->dp <= 64) ? pair_rescore_kernel<16> : pair_rescore_kernel<0>;
-  fn<<<sms * 4, 256, 0, st>>>(pairs, count, cap, ix->Ut, ix->unorm, ix->uid, ix->Lt, ix->Eu, ix->pnorm, ix->n,
+  // one wave: the CTAs that fit on an SM at once (the register-resident rows allow fewer),
+  // each warp taking its pairs in one or a few strides; CTAs of a second wave would only
+  // find the list already done
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+  fn<<<sms * per_sm, 256, 0, st>>>(pairs, count, cap, ix->Ut, ix->unorm, ix->uid, ix->Lt, ix->Eu, ix->pnorm, ix->n,
                               ix->m_nz, ix->kmax, ix->l_exact ? 1 : 0, ix->d, ix->dp, Qd, qn, kk, ix->gamma, ix->T64,
                               bitmap, words, surv, surv_count, cap, stats, st_yes, st_fp64, nq, ix->dev_timeout);
   SAH_CUDA(cudaGetLastError());

@@ -227,13 +227,40 @@ __device__ __forceinline__ void set_answer(uint32_t* bitmap, int64_t stride, int
   atomicOr(&row[answer_words(stride) + (wi >> 5)], 1u << (wi & 31));
 }
 
+// A float widened to double by rewriting its fields (IEEE 754 binary32 -> binary64, exact
+// for every value): the sign stays, a normal number's exponent is re-biased (+1023 - 127)
+// and its 23-bit fraction moves to the top of the 52-bit one; a subnormal m * 2^-149 is
+// normalised around its leading bit p; zeros, infinities and NaNs keep their class.  On
+// GPUs whose double-precision pipe is narrow this keeps the conversions on the integer
+// units, leaving the double pipe to the multiply-adds.  sah_selftest_f2d checks it
+// against the hardware conversion over every float.
+__device__ __forceinline__ double f2d_bits(float x) {
+  const uint32_t b = __float_as_uint(x);
+  const uint64_t sgn = (uint64_t)(b >> 31) << 63;
+  const uint32_t e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+  uint64_t r;
+  if (e - 1u < 254u) {
+    r = sgn | ((uint64_t)(e + 896u) << 52) | ((uint64_t)m << 29);
+  } else if (e == 0u) {
+    if (m == 0u) {
+      r = sgn;
+    } else {
+      const int p = 31 - __clz(m);   // m = 2^p (1 + f), value 2^(p - 149) (1 + f)
+      r = sgn | ((uint64_t)(p + 874) << 52) | (((uint64_t)m << (52 - p)) & 0xFFFFFFFFFFFFFull);
+    }
+  } else {
+    r = sgn | (0x7FFull << 52) | ((uint64_t)m << 29);
+  }
+  return __longlong_as_double((long long)r);
+}
+
 // Sequential double-precision inner product in the order i = 0..d-1.  The product of
 // two floats is exact in double, so this equals the double-precision definition of the
 // count rule bit for bit, whatever the compiler does with the multiply-add.
 __device__ inline double dot64_seq(const float* __restrict__ a, const float* __restrict__ b,
                                    int d) {
   double s = 0.0;
-  for (int i = 0; i < d; ++i) s = __fma_rn((double)a[i], (double)b[i], s);
+  for (int i = 0; i < d; ++i) s = __fma_rn(f2d_bits(a[i]), f2d_bits(b[i]), s);
   return s;
 }
 
@@ -251,17 +278,18 @@ sah_status run_saalsh(Index* ix, const Survivor* surv, const unsigned long long*
 // user_pass_tc.cu: the user pass on tcgen05 over every user tile and the distinct query
 // vectors of the sub-batch (nq <= 4096 rows).
 //  prepare_user_pass_tc: the column table (distinct vectors, their rows) into scratch
-//    (user_pass_tc_scratch_bytes); the split hi / lo BF16 queries (2 nq dk entries) are
-//    written by the query preparation.
+//    (user_pass_tc_scratch_bytes); the split hi / lo BF16 queries (2 nq dk entries) and
+//    qh, a 64-bit hash of each padded query row's bits, are written by the query
+//    preparation.
 //  block_filter_tc: A3 per (leaf, column), the rows' decisions into kept_mask
 //    ([nb][mask_words]) and the counters stats[st_pairs], stats[st_users], stats[st_scored].
 //  run_user_pass_tc: the GEMM and its epilogue; tile_need holds one byte per 128-user tile;
 //    the pairs its band leaves open go to resc and are re-scored in FP32.
-size_t user_pass_tc_scratch_bytes(int nq);
-sah_status prepare_user_pass_tc(Index* ix, const float* Qd, void* scratch, const int32_t* kk, const int32_t* modes,
-                                int nq, cudaStream_t st, int* launches);
-sah_status block_filter_tc(Index* ix, const float* Qd, const float* qn, void* scratch, int nq, uint32_t* kept_mask,
-                           int mask_words, unsigned long long* stats, int st_pairs, int st_users, int st_scored,
+size_t user_pass_tc_scratch_bytes(int nq, int dp);
+sah_status prepare_user_pass_tc(Index* ix, const float* Qd, const float* qn, const uint64_t* qh, void* scratch,
+                                const int32_t* kk, const int32_t* modes, int nq, cudaStream_t st, int* launches);
+sah_status block_filter_tc(Index* ix, void* scratch, int nq, uint32_t* kept_mask, int mask_words,
+                           unsigned long long* stats, int st_pairs, int st_users, int st_scored,
                            cudaStream_t st);
 sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* scratch, const float* qn,
                             const int32_t* kk, int nq, const uint32_t* kept_mask, int mask_words, uint8_t* tile_need,

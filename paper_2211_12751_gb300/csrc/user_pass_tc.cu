@@ -5,7 +5,8 @@
 // Columns.  The rows of a sub-batch are (q, k) requests; rows asking for the same vector q
 // (with k <= k_max) share one GEMM column, so a batch that asks each item at several k
 // costs one column per item.  column_table_kernel finds the distinct vectors (hash table in
-// shared memory, bitwise comparison of the rows) and lists each column's rows.
+// shared memory on a hash of each row's bits, then a bitwise check of the rows) and lists
+// each column's rows.
 //
 // Operands.  BF16 alone carries 8 significant bits, which makes the score's error band
 // (about 2^-7 ||u|| ||q||) so wide that many pairs would stay open.  Every FP32 vector x
@@ -71,11 +72,14 @@ struct ColTable {
   int32_t* kq;        // [nq]: largest k <= k_max among the column's rows (0: none)
   int32_t* start;     // [nq + 1]: the column's rows in rows[start[c], start[c + 1])
   int4* rows;         // [nq]: {j | sa << 30, k, bits of ||p_k|| (-inf past n), 0}
+  float* qnc;         // [nq]: ||q|| of each column
+  float4* qt;         // [dp / 4][nq]: the columns' vectors, transposed (16-byte words)
 };
 
-size_t col_table_bytes(int nq) {
+size_t col_table_bytes(int nq, int dp) {
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  return up(sizeof(int32_t)) + 3 * up(sizeof(int32_t) * (nq + 1)) + up(sizeof(int4) * (nq + 1));
+  return up(sizeof(int32_t)) + 3 * up(sizeof(int32_t) * (nq + 1)) + up(sizeof(int4) * (nq + 1)) +
+         up(sizeof(float) * nq) + up(sizeof(float4) * (size_t)(dp / 4) * nq);
 }
 
 ColTable col_table_at(void* base, int nq) {
@@ -91,6 +95,10 @@ ColTable col_table_at(void* base, int nq) {
   T.start = (int32_t*)p;
   p += up(sizeof(int32_t) * (nq + 1));
   T.rows = (int4*)p;
+  p += up(sizeof(int4) * (nq + 1));
+  T.qnc = (float*)p;
+  p += up(sizeof(float) * nq);
+  T.qt = (float4*)p;
   return T;
 }
 
@@ -124,19 +132,20 @@ __device__ int block_exclusive_scan(int v, int* wsum, int* total) {
 }
 
 // One CTA of 1024 threads.  Rows with k > n ask for every user and get no column.
-__global__ void __launch_bounds__(1024)
-column_table_kernel(const float* __restrict__ Qd, int nq, int d, int dp, const int32_t* __restrict__ kk,
-                    const int32_t* __restrict__ modes, int kmax, int64_t n, const float* __restrict__ pnorm,
-                    int ht, ColTable T) {
+__global__ void __launch_bounds__(1024, 1)
+column_table_kernel(const float* __restrict__ Qd, const float* __restrict__ qn, const uint64_t* __restrict__ qh,
+                    int nq, int dp, const int32_t* __restrict__ kk, const int32_t* __restrict__ modes, int kmax,
+                    int64_t n, const float* __restrict__ pnorm, int ht, ColTable T) {
   extern __shared__ int32_t sm[];
   __shared__ int wsum[32];
-  __shared__ int total_sh;
+  __shared__ int total_sh, collide_sh;
   int32_t* owner = sm;             // [ht] a row of the slot's vector, -1 empty
   int32_t* minrow = owner + ht;    // [ht] the first row of the slot's vector
   int32_t* colof = minrow + ht;    // [nq] slot, then column, of each row (-1: none)
   int32_t* cid = colof + nq;       // [nq] column of each first row
   int32_t* cnt = cid + nq;         // [nq] rows per column, then the scatter cursor
   int32_t* kq = cnt + nq;          // [nq] largest k <= k_max per column
+  int32_t* crep = kq + nq;         // [nq] the first row of each column
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int i = tid; i < ht; i += nt) {
     owner[i] = -1;
@@ -147,44 +156,78 @@ column_table_kernel(const float* __restrict__ Qd, int nq, int d, int dp, const i
     kq[i] = 0;
   }
   __syncthreads();
-  // a thread per row: hash of the row's bits (one multiply per 64 bits), then linear
-  // probing with a bitwise comparison against the slot's owner
-  for (int j = tid; j < nq; j += nt) {
-    const int k = kk[j];
-    colof[j] = -1;
-    if (k < 1 || k > n) continue;
-    const int cls = k <= kmax ? 0 : 1;
-    const uint32_t* q = reinterpret_cast<const uint32_t*>(Qd + (int64_t)j * dp);
-    uint64_t h = 0x51ed27ull + (uint64_t)cls;
-    for (int i = 0; i < d; i += 2) {
-      const uint64_t x = (uint64_t)q[i] | ((i + 1 < d ? (uint64_t)q[i + 1] : 0ull) << 32);
-      h = (h ^ x) * 0x9E3779B97F4A7C15ull;
-      h ^= h >> 29;
-    }
-    h = splitmix64(h);
-    int slot = (int)(h & (uint64_t)(ht - 1));
-    for (int probe = 0; probe < ht; ++probe) {
-      int cur = owner[slot];
-      if (cur == -1) {
-        const int prev = atomicCAS(&owner[slot], -1, j);
-        if (prev == -1) break;
-        cur = prev;
+  // a thread per row: linear probing on (hash of the padded row's bits, k <= k_max); a
+  // slot's owner is a row of its vector.  Equal hashes are then checked bitwise (a 16-byte
+  // word per thread and step, so that the loads coalesce); should two different vectors
+  // share a hash, the table is built again with every probe comparing the rows bitwise.
+  const int dp4 = dp / 4;
+  if (tid == 0) collide_sh = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1) {
+      for (int i = tid; i < ht; i += nt) {
+        owner[i] = -1;
+        minrow[i] = INT_MAX;
       }
-      const int kc = kk[cur];
-      bool same = (kc <= kmax ? 0 : 1) == cls;
-      const float4* a4 = reinterpret_cast<const float4*>(Qd + (int64_t)j * dp);
-      const float4* c4 = reinterpret_cast<const float4*>(Qd + (int64_t)cur * dp);
-      for (int i = 0; same && i < dp / 4; ++i) {
-        const uint4 x = *reinterpret_cast<const uint4*>(a4 + i), y = *reinterpret_cast<const uint4*>(c4 + i);
-        same = x.x == y.x && x.y == y.y && x.z == y.z && x.w == y.w;
-      }
-      if (same) break;
-      slot = (slot + 1) & (ht - 1);
+      __syncthreads();
     }
-    colof[j] = slot;
-    atomicMin(&minrow[slot], j);
+    for (int j = tid; j < nq; j += nt) {
+      const int k = kk[j];
+      colof[j] = -1;
+      if (k < 1 || k > n) continue;
+      const int cls = k <= kmax ? 0 : 1;
+      const uint64_t key = qh[j];
+      int slot = (int)(splitmix64(key + (uint64_t)cls) & (uint64_t)(ht - 1));
+      for (int probe = 0; probe < ht; ++probe) {
+        int cur = owner[slot];
+        if (cur == -1) {
+          const int prev = atomicCAS(&owner[slot], -1, j);
+          if (prev == -1) break;
+          cur = prev;
+        }
+        bool same = qh[cur] == key && (kk[cur] <= kmax ? 0 : 1) == cls;
+        if (same && pass == 1) {
+          const uint4* a4 = reinterpret_cast<const uint4*>(Qd + (int64_t)j * dp);
+          const uint4* c4 = reinterpret_cast<const uint4*>(Qd + (int64_t)cur * dp);
+          for (int i = 0; same && i < dp4; ++i) {
+            const uint4 x = a4[i], y = c4[i];
+            same = x.x == y.x && x.y == y.y && x.z == y.z && x.w == y.w;
+          }
+        }
+        if (same) break;
+        slot = (slot + 1) & (ht - 1);
+      }
+      colof[j] = slot;
+      atomicMin(&minrow[slot], j);
+    }
+    __syncthreads();
+    if (pass == 1) break;
+    for (int x0 = tid; x0 < nq * dp4; x0 += 4 * nt) {
+      uint4 a[4], b[4];
+      bool chk[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int x = x0 + e * nt;
+        chk[e] = false;
+        a[e] = b[e] = make_uint4(0u, 0u, 0u, 0u);
+        if (x < nq * dp4) {
+          const int j = x / dp4, i = x - j * dp4;
+          const int sl = colof[j];
+          const int o = sl >= 0 ? owner[sl] : j;
+          if (o != j) {
+            chk[e] = true;
+            a[e] = __ldcg(reinterpret_cast<const uint4*>(Qd + (int64_t)j * dp) + i);
+            b[e] = __ldcg(reinterpret_cast<const uint4*>(Qd + (int64_t)o * dp) + i);
+          }
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (chk[e] && (a[e].x != b[e].x || a[e].y != b[e].y || a[e].z != b[e].z || a[e].w != b[e].w))
+          collide_sh = 1;
+    }
+    __syncthreads();
+    if (!collide_sh) break;
   }
-  __syncthreads();
   // columns numbered by their first rows, in row order
   const int per = (nq + nt - 1) / nt;
   const int j0 = tid * per, j1 = min(nq, j0 + per);
@@ -196,6 +239,7 @@ column_table_kernel(const float* __restrict__ Qd, int nq, int d, int dp, const i
     if (colof[j] >= 0 && minrow[colof[j]] == j) {
       cid[j] = c;
       T.rep[c] = j;
+      crep[c] = j;
       ++c;
     }
   __syncthreads();
@@ -234,88 +278,143 @@ column_table_kernel(const float* __restrict__ Qd, int nq, int d, int dp, const i
     const float pk = k <= n ? pnorm[k - 1] : -INFINITY;
     T.rows[atomicAdd(&cnt[cc], 1)] = make_int4(j | (sa << 30), k, __float_as_int(pk), 0);
   }
+  // the columns' vectors transposed (read row by row, so that the loads coalesce) and
+  // their norms, for the block filter's thread-per-column reads
+  const float4* Q4 = reinterpret_cast<const float4*>(Qd);
+  for (int x = tid; x < ncol * dp4; x += nt) {
+    const int c = x / dp4, i = x - c * dp4;
+    T.qt[(int64_t)i * nq + c] = Q4[(int64_t)crep[c] * dp4 + i];
+  }
+  for (int c = tid; c < ncol; c += nt) T.qnc[c] = qn[crep[c]];
 }
 
 // A3 over the columns: Lemma 2 for every (leaf, distinct query vector) pair, then the bound
-// compared with L^k(B) for each row of the column.  One CTA per leaf; the leaf's decisions
-// go to kept_mask[B] (bit j of word j / 32), as the row-wise block filter writes them.
-// The arithmetic of the bound is the row-wise kernel's.
-__global__ void block_filter_cols_kernel(const float* __restrict__ bcent, const float* __restrict__ bcos,
-                                         const float* __restrict__ bsin, const float* __restrict__ LB, int nb,
-                                         int kmax, int dp, const float* __restrict__ Qd, const float* __restrict__ qn,
-                                         ColTable T, float slack, uint32_t* __restrict__ kept_mask, int mask_words,
-                                         const int32_t* __restrict__ bstart, unsigned long long* __restrict__ stats,
-                                         int st_pairs, int st_users, int st_scored) {
-  extern __shared__ float4 c4s[];   // the leaf's unit centre
-  __shared__ uint32_t kbits[kMaxRows / 32];
-  __shared__ float lbs[65];           // the leaf's lower bounds L^k(B), k = 1..k_max
-  __shared__ int kept_sh;
-  const int B = blockIdx.x;
+// compared with L^k(B) for each row of the column.  A CTA takes kFilterLeaves consecutive
+// leaves (centres, cone angles and lower bounds staged in shared memory) and a thread a
+// column, which it tests against each leaf in turn; the column vectors come from the
+// column table's transposed copy, so that a warp's loads of a 16-byte word of 32 columns
+// coalesce, and the (j, k) of the rows are staged in shared memory.  The leaf's decisions
+// go to kept_mask[B] (bit j of word j / 32), as the row-wise block filter writes them.  The
+// arithmetic of the bound is the row-wise kernel's.
+constexpr int kFilterLeaves = 4;
+constexpr int kFilterRows = 1024;   // rows staged in shared memory (the rest read from memory)
+
+__global__ void __launch_bounds__(128)
+block_filter_cols_kernel(const float* __restrict__ bcent, const float* __restrict__ bcos,
+                         const float* __restrict__ bsin, const float* __restrict__ LB, int nb, int kmax, int dp,
+                         int nq, ColTable T, float slack, uint32_t* __restrict__ kept_mask, int mask_words,
+                         const int32_t* __restrict__ bstart, unsigned long long* __restrict__ stats, int st_pairs,
+                         int st_users, int st_scored) {
+  extern __shared__ float4 cen[];   // [kFilterLeaves][dp / 4] the leaves' unit centres
+  __shared__ int2 rs[kFilterRows];   // (j, k) of the rows
+  __shared__ uint32_t kbits[kFilterLeaves][kMaxRows / 32];
+  __shared__ float lbs[kFilterLeaves][65];   // the leaves' lower bounds L^k(B), k = 1..64
+  __shared__ float cws[kFilterLeaves], sws[kFilterLeaves];
+  __shared__ int kept_sh[kFilterLeaves];
   const int dp4 = dp / 4;
-  for (int i = threadIdx.x; i < dp4; i += blockDim.x)
-    c4s[i] = reinterpret_cast<const float4*>(bcent + (int64_t)B * dp)[i];
-  for (int k = threadIdx.x + 1; k <= kmax && k <= 64; k += blockDim.x) lbs[k] = LB[(int64_t)(k - 1) * nb + B];
-  for (int i = threadIdx.x; i < mask_words; i += blockDim.x) kbits[i] = 0u;
-  if (threadIdx.x == 0) kept_sh = 0;
-  __syncthreads();
-  const float cw = bcos[B], sw = bsin[B];
-  const bool degenerate = cw < -1.5f;
+  const int B0 = blockIdx.x * kFilterLeaves;
+  const int nl = min(kFilterLeaves, nb - B0);
+  const int tid = threadIdx.x, nt = blockDim.x;
   const int ncol = *T.ncol;
-  int kept = 0;
-  for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
-    const int rep = T.rep[c];
-    const float nrm = qn[rep];
-    float ub = INFINITY;   // no cone bound: every row kept
-    if (!degenerate && nrm > 0.f) {
-      const float4* q4 = reinterpret_cast<const float4*>(Qd + (int64_t)rep * dp);
-      float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+  const int nrows = T.start[ncol];
+  const float4* cg = reinterpret_cast<const float4*>(bcent + (int64_t)B0 * dp);
+  for (int i = tid; i < nl * dp4; i += nt) cen[i] = cg[i];
+  const int k64 = min(kmax, 64);
+  for (int i = tid; i < nl * k64; i += nt) {
+    const int k = i / nl + 1, l = i - (k - 1) * nl;   // consecutive threads, consecutive leaves
+    lbs[l][k] = LB[(int64_t)(k - 1) * nb + B0 + l];
+  }
+  for (int q = tid; q < min(nrows, kFilterRows); q += nt) {
+    const int4 rw = T.rows[q];
+    rs[q] = make_int2(rw.x & 0x3fffffff, rw.y);
+  }
+  for (int i = tid; i < nl * mask_words; i += nt) kbits[i / mask_words][i % mask_words] = 0u;
+  if (tid < nl) {
+    cws[tid] = bcos[B0 + tid];
+    sws[tid] = bsin[B0 + tid];
+    kept_sh[tid] = 0;
+  }
+  __syncthreads();
+  int kept[kFilterLeaves] = {};
+  for (int c = tid; c < ncol; c += nt) {
+    const float nrm = T.qnc[c];
+    const int r0 = T.start[c], r1 = T.start[c + 1];
+    const float4* qc = T.qt + c;   // word i at qc[i * nq]
+#pragma unroll
+    for (int l = 0; l < kFilterLeaves; ++l) {
+      if (l >= nl) break;
+      const float cw = cws[l], sw = sws[l];
+      const float4* cl = cen + l * dp4;
+      float ub = INFINITY;   // no cone bound: every row kept
+      if (!(cw < -1.5f) && nrm > 0.f) {
+        float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
 #pragma unroll 4
-      for (int i = 0; i < dp4; ++i) {
-        const float4 a = c4s[i], b = __ldg(q4 + i);
-        d0 = fmaf(a.x, b.x, d0);
-        d1 = fmaf(a.y, b.y, d1);
-        d2 = fmaf(a.z, b.z, d2);
-        d3 = fmaf(a.w, b.w, d3);
-      }
-      const float dq = (d0 + d1) + (d2 + d3);
-      const float cphi = fminf(1.f, fmaxf(-1.f, dq / nrm));
-      float sphi;
-      if (cphi * cphi <= 0.5f) {
-        sphi = sqrtf(fmaxf(0.f, fmaf(-cphi, cphi, 1.f)));
-      } else {
-        float o2 = 0.f;
         for (int i = 0; i < dp4; ++i) {
-          const float4 a = c4s[i], b = __ldg(q4 + i);
-          float o;
-          o = fmaf(-dq, a.x, b.x); o2 = fmaf(o, o, o2);
-          o = fmaf(-dq, a.y, b.y); o2 = fmaf(o, o, o2);
-          o = fmaf(-dq, a.z, b.z); o2 = fmaf(o, o, o2);
-          o = fmaf(-dq, a.w, b.w); o2 = fmaf(o, o, o2);
+          const float4 a = cl[i], b = __ldg(qc + (int64_t)i * nq);
+          d0 = fmaf(a.x, b.x, d0);
+          d1 = fmaf(a.y, b.y, d1);
+          d2 = fmaf(a.z, b.z, d2);
+          d3 = fmaf(a.w, b.w, d3);
         }
-        sphi = fminf(1.f, sqrtf(o2) / nrm);
+        const float dq = (d0 + d1) + (d2 + d3);
+        const float cphi = fminf(1.f, fmaxf(-1.f, dq / nrm));
+        float sphi;
+        if (cphi * cphi <= 0.5f) {
+          sphi = sqrtf(fmaxf(0.f, fmaf(-cphi, cphi, 1.f)));
+        } else {
+          float o2 = 0.f;
+          for (int i = 0; i < dp4; ++i) {
+            const float4 a = cl[i], b = __ldg(qc + (int64_t)i * nq);
+            float o;
+            o = fmaf(-dq, a.x, b.x); o2 = fmaf(o, o, o2);
+            o = fmaf(-dq, a.y, b.y); o2 = fmaf(o, o, o2);
+            o = fmaf(-dq, a.z, b.z); o2 = fmaf(o, o, o2);
+            o = fmaf(-dq, a.w, b.w); o2 = fmaf(o, o, o2);
+          }
+          sphi = fminf(1.f, sqrtf(o2) / nrm);
+        }
+        if (cphi >= cw - slack) ub = nrm * (1.f + slack);
+        else ub = nrm * (fmaf(cphi, cw, sphi * sw) + 2.f * slack);
       }
-      if (cphi >= cw - slack) ub = nrm * (1.f + slack);
-      else ub = nrm * (fmaf(cphi, cw, sphi * sw) + 2.f * slack);
-    }
-    for (int q = T.start[c]; q < T.start[c + 1]; ++q) {
-      const int4 rw = T.rows[q];
-      const int j = rw.x & 0x3fffffff, k = rw.y;
-      const float lb = (k <= kmax) ? (k <= 64 ? lbs[k] : LB[(int64_t)(k - 1) * nb + B]) : -INFINITY;
-      if (!(ub < lb)) {
-        atomicOr(&kbits[j >> 5], 1u << (j & 31));
-        ++kept;
+      for (int q = r0; q < r1; ++q) {
+        int2 jk;
+        if (q < kFilterRows) {
+          jk = rs[q];
+        } else {
+          const int4 rw = T.rows[q];
+          jk = make_int2(rw.x & 0x3fffffff, rw.y);
+        }
+        const int j = jk.x, k = jk.y;
+        const float lb = (k <= kmax) ? (k <= 64 ? lbs[l][k] : LB[(int64_t)(k - 1) * nb + B0 + l]) : -INFINITY;
+        if (!(ub < lb)) {
+          atomicOr(&kbits[l][j >> 5], 1u << (j & 31));
+          ++kept[l];
+        }
       }
     }
   }
-  kept = __reduce_add_sync(0xffffffffu, kept);
-  if ((threadIdx.x & 31) == 0 && kept) atomicAdd(&kept_sh, kept);
+#pragma unroll
+  for (int l = 0; l < kFilterLeaves; ++l) {
+    const int v = __reduce_add_sync(0xffffffffu, kept[l]);
+    if ((tid & 31) == 0 && v) atomicAdd(&kept_sh[l], v);
+  }
   __syncthreads();
-  for (int i = threadIdx.x; i < mask_words; i += blockDim.x) kept_mask[(int64_t)B * mask_words + i] = kbits[i];
-  if (threadIdx.x == 0 && kept_sh) {
-    const int users = bstart[B + 1] - bstart[B];
-    atomicAdd(&stats[st_pairs], (unsigned long long)kept_sh);
-    atomicAdd(&stats[st_users], (unsigned long long)users);
-    atomicAdd(&stats[st_scored], (unsigned long long)kept_sh * users);
+  for (int i = tid; i < nl * mask_words; i += nt)
+    kept_mask[(int64_t)B0 * mask_words + i] = kbits[i / mask_words][i % mask_words];
+  if (tid == 0) {
+    unsigned long long pairs = 0, users = 0, scored = 0;
+    for (int l = 0; l < nl; ++l) {
+      if (!kept_sh[l]) continue;
+      const unsigned long long u = (unsigned long long)(bstart[B0 + l + 1] - bstart[B0 + l]);
+      pairs += kept_sh[l];
+      users += u;
+      scored += (unsigned long long)kept_sh[l] * u;
+    }
+    if (pairs) {
+      atomicAdd(&stats[st_pairs], pairs);
+      atomicAdd(&stats[st_users], users);
+      atomicAdd(&stats[st_scored], scored);
+    }
   }
 }
 
@@ -952,10 +1051,10 @@ sah_status launch_pass(Index* ix, UpParams p, int sms, cudaStream_t st, int* lau
 
 }  // namespace
 
-size_t user_pass_tc_scratch_bytes(int nq) { return col_table_bytes(nq); }
+size_t user_pass_tc_scratch_bytes(int nq, int dp) { return col_table_bytes(nq, dp); }
 
-sah_status prepare_user_pass_tc(Index* ix, const float* Qd, void* scratch, const int32_t* kk, const int32_t* modes,
-                                int nq, cudaStream_t st, int* launches) {
+sah_status prepare_user_pass_tc(Index* ix, const float* Qd, const float* qn, const uint64_t* qh, void* scratch,
+                                const int32_t* kk, const int32_t* modes, int nq, cudaStream_t st, int* launches) {
   if (nq == 0 || ix->dk <= 0) return SAH_OK;
   if (nq > kMaxRows) {
     set_error("tensor-core user pass: sub-batch larger than its column table");
@@ -965,22 +1064,24 @@ sah_status prepare_user_pass_tc(Index* ix, const float* Qd, void* scratch, const
   const ColTable T = col_table_at(scratch, nq);
   int ht = 64;
   while (ht < 2 * nq) ht <<= 1;
-  const size_t tsmem = sizeof(int32_t) * (2 * (size_t)ht + 4 * (size_t)nq);
+  const size_t tsmem = sizeof(int32_t) * (2 * (size_t)ht + 5 * (size_t)nq);
   SAH_TRY(raise_smem_limit((const void*)column_table_kernel, tsmem));
-  column_table_kernel<<<1, 1024, tsmem, st>>>(Qd, nq, ix->d, ix->dp, kk, modes, ix->kmax, ix->n, ix->pnorm, ht, T);
+  column_table_kernel<<<1, 1024, tsmem, st>>>(Qd, qn, qh, nq, ix->dp, kk, modes, ix->kmax, ix->n, ix->pnorm, ht,
+                                               T);
   SAH_CUDA(cudaGetLastError());
   if (launches) *launches += 1;
   return SAH_OK;
 }
 
-sah_status block_filter_tc(Index* ix, const float* Qd, const float* qn, void* scratch, int nq, uint32_t* kept_mask,
-                           int mask_words, unsigned long long* stats, int st_pairs, int st_users, int st_scored,
+sah_status block_filter_tc(Index* ix, void* scratch, int nq, uint32_t* kept_mask, int mask_words,
+                           unsigned long long* stats, int st_pairs, int st_users, int st_scored,
                            cudaStream_t st) {
   if (ix->nb == 0 || nq == 0) return SAH_OK;
   const ColTable T = col_table_at(scratch, nq);
-  block_filter_cols_kernel<<<ix->nb, 128, sizeof(float) * ix->dp, st>>>(
-      ix->bcent, ix->bcos, ix->bsin, ix->LB, ix->nb, ix->kmax, ix->dp, Qd, qn, T, ix->cone_slack, kept_mask,
-      mask_words, ix->bstart, stats, st_pairs, st_users, st_scored);
+  block_filter_cols_kernel<<<(ix->nb + kFilterLeaves - 1) / kFilterLeaves, 128,
+                             sizeof(float) * ix->dp * kFilterLeaves, st>>>(
+      ix->bcent, ix->bcos, ix->bsin, ix->LB, ix->nb, ix->kmax, ix->dp, nq, T, ix->cone_slack, kept_mask, mask_words,
+      ix->bstart, stats, st_pairs, st_users, st_scored);
   SAH_CUDA(cudaGetLastError());
   return SAH_OK;
 }
