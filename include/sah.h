@@ -108,7 +108,10 @@ sah_status sah_rkmips(sah_index* index, const float* q, int32_t k, int32_t mode,
  * out_offsets: nq + 1 entries, query j's ids are out_ids[out_offsets[j] .. out_offsets[j+1]).
  * If buffers_on_device != 0, Q, ks, modes, out_ids and out_offsets are device pointers
  * (the call still synchronises the stream once, to size the output); otherwise host
- * pointers, and the host <-> device copies happen inside the call.  modes may be NULL
+ * pointers.  Host buffers that are all pinned and mapped into the device's address space
+ * (cudaHostAlloc, cudaMallocHost, cudaHostRegister with mapping; cap > 0) are read and
+ * written in place by the kernels, with one synchronisation and no staging copy; other
+ * host buffers are copied to and from the device inside the call.  modes may be NULL
  * (all exact).  If the total exceeds cap, out_offsets[nq] is set to the required total
  * (and, for host buffers, out_offsets[0..nq] are filled), no id is written and
  * SAH_ERR_BUFFER_TOO_SMALL is returned. */

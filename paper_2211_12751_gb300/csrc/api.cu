@@ -233,6 +233,19 @@ sah_status sah_build_index(const float* U, int64_t m, const float* P, int64_t n,
   return SAH_OK;
 }
 
+// The address under which the current device reaches host memory p: pinned memory mapped
+// into the device's address space (as pinned memory is under unified addressing).
+static bool device_view(const void* p, const void** out) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type != cudaMemoryTypeHost || a.devicePointer == nullptr) return false;
+  *out = a.devicePointer;
+  return true;
+}
+
 static sah_status batch_impl(sah_index* index, const float* Q, int32_t nq, const int32_t* ks,
                              const int32_t* modes, int32_t on_dev, int32_t* out_ids, int64_t cap,
                              int64_t* out_offsets, cudaStream_t st) {
@@ -248,7 +261,25 @@ static sah_status batch_impl(sah_index* index, const float* Q, int32_t nq, const
     }
     return SAH_OK;
   }
-  // host buffers are checked here; device buffers (k, mode, finiteness) on the device
+  // Host buffers that the GPU addresses directly: the kernels read the requests and write
+  // the answers in place, so the call makes no staging copy and synchronises once; k, the
+  // modes and the vectors are then checked on the device, as for device buffers.
+  bool mapped = false;
+  int64_t* host_offsets = out_offsets;
+  if (!on_dev && cap > 0) {
+    const void *q2 = nullptr, *k2 = nullptr, *m2 = nullptr, *o2 = nullptr, *f2 = nullptr;
+    if (device_view(Q, &q2) && device_view(ks, &k2) && (!modes || device_view(modes, &m2)) &&
+        device_view(out_ids, &o2) && device_view(out_offsets, &f2)) {
+      Q = (const float*)q2;
+      ks = (const int32_t*)k2;
+      modes = (const int32_t*)m2;
+      out_ids = (int32_t*)o2;
+      out_offsets = (int64_t*)f2;
+      on_dev = 1;
+      mapped = true;
+    }
+  }
+  // other host buffers are checked here; device buffers (k, mode, finiteness) on the device
   if (!on_dev) {
     for (int j = 0; j < nq; ++j) {
       if (ks[j] < 1) {
@@ -290,11 +321,11 @@ static sah_status batch_impl(sah_index* index, const float* Q, int32_t nq, const
   const int64_t total = offs[nq];
   if (s == SAH_ERR_BUFFER_TOO_SMALL || (s == SAH_OK && total > cap)) {
     if (out_offsets) {
-      if (on_dev) {
+      if (on_dev && !mapped) {
         cudaMemcpyAsync(out_offsets + nq, &total, sizeof(int64_t), cudaMemcpyHostToDevice, st);
         cudaStreamSynchronize(st);
       } else {
-        std::memcpy(out_offsets, offs.data(), sizeof(int64_t) * (nq + 1));
+        std::memcpy(host_offsets, offs.data(), sizeof(int64_t) * (nq + 1));
       }
     }
     sah::set_error("result buffer too small: " + std::to_string(total) + " ids needed");
@@ -304,12 +335,13 @@ static sah_status batch_impl(sah_index* index, const float* Q, int32_t nq, const
   if (!wrote) {
     if (total > 0)
       SAH_CUDA(cudaMemcpyAsync(out_ids, cx->res.base, sizeof(int32_t) * total,
-                               on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-    if (on_dev)
+                               mapped ? cudaMemcpyDefault
+                                      : (on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost), st));
+    if (on_dev && !mapped)
       SAH_CUDA(cudaMemcpyAsync(out_offsets, offs.data(), sizeof(int64_t) * (nq + 1), cudaMemcpyHostToDevice, st));
     SAH_CUDA(cudaStreamSynchronize(st));
   }
-  if (!on_dev) std::memcpy(out_offsets, offs.data(), sizeof(int64_t) * (nq + 1));
+  if (!on_dev || mapped) std::memcpy(host_offsets, offs.data(), sizeof(int64_t) * (nq + 1));
   return SAH_OK;
 }
 
