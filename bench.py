@@ -64,6 +64,10 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--saalsh", action="store_true",
                     help="time every request in SA-ALSH mode (approximate; for profiling that mode)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="instead of the bench line, one JSON line of parameter sweeps on the workload: "
+                         "leaf size N_0 (exact mode), and for SA-ALSH mode the probe radius (k = 10), "
+                         "the interval ratio b and the table count K, each with its F1 against the exact answers")
     ap.add_argument("--serve-rate", type=float, default=20000.0, help="Poisson arrival rate (requests/s)")
     ap.add_argument("--serve-requests", type=int, default=6000)
     return ap.parse_args()
@@ -320,6 +324,79 @@ def config_block(W, args):
 
 
 # ---------------------------------------------------------------- our arm
+def run_sweeps(sah, W, Q, K, dev, stream, flush, args, steps=5):
+    """Parameter sweeps on the workload (the paper's Fig. 1 row 3 and Figs. 3-5, on synthetic
+    data): index with the paper's |P'| = 200, BF16 with the tensor-core user pass, 128 tables
+    of 16-bit codes, b = 0.5, probe radius 0, leaf size from --leaf-size, unless swept.
+    Every point times `steps` batches (CUDA events, L2 flushed before each) after 3 warm-up
+    calls; SA-ALSH points report their F1 against the exact answers of the same index."""
+    import torch
+    base = dict(k_max=50, leaf_size=args.leaf_size, p_prime=0, seed=0, precision=sah.BF16, n_tables=128,
+                code_bits=16, tc_user_pass=1, b=0.5, probe_radius=0)
+
+    def time_batch(ix, Qs, Ks, modes=None):
+        Qsd = torch.from_numpy(np.ascontiguousarray(Qs)).to(dev)
+        Ksd = torch.from_numpy(np.ascontiguousarray(Ks, dtype=np.int32)).to(dev)
+        Msd = None if modes is None else torch.from_numpy(modes).to(dev)
+        host = ix.rkmips_batch(Qs, Ks, modes=modes)
+        out = torch.empty(max(1, sum(len(h) for h in host)), dtype=torch.int32, device=dev)
+        offs = torch.empty(len(Ks) + 1, dtype=torch.int64, device=dev)
+        mptr = Msd.data_ptr() if Msd is not None else None
+
+        def call():
+            s = ix.raw_batch(Qsd.data_ptr(), len(Ks), Ksd.data_ptr(), mptr, 1, out.data_ptr(), out.numel(),
+                             offs.data_ptr(), stream=stream)
+            assert s == 0, s
+
+        for _ in range(3):
+            call()
+        times = []
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            call()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return host, len(Ks) / (float(np.mean(times)) / 1e3), float(np.mean(times))
+
+    def f1(got, exact):
+        vals = [2 * len(set(a.tolist()) & set(b.tolist())) / max(1, len(a) + len(b)) if (len(a) + len(b)) else 1.0
+                for a, b in zip(got, exact)]
+        return float(np.mean(vals)), float(np.min(vals))
+
+    def point(Qs, Ks, saalsh, **over):
+        prm = dict(base, **over)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ix = sah.Index(W.U, W.P, stream=stream, **prm)
+        torch.cuda.synchronize()
+        rec = {k: over[k] for k in over}
+        rec["index_build_s"] = time.perf_counter() - t0
+        exact, qps, ms = time_batch(ix, Qs, Ks)
+        rec["exact"] = {"queries_per_s": qps, "ms_per_batch": ms}
+        if saalsh:
+            got, qps_sa, ms_sa = time_batch(ix, Qs, Ks, modes=np.full(len(Ks), sah.SAALSH, np.int32))
+            mean_f1, min_f1 = f1(got, exact)
+            rec["saalsh"] = {"queries_per_s": qps_sa, "ms_per_batch": ms_sa, "f1_vs_exact": mean_f1, "min_f1": min_f1}
+        ix.close()
+        return rec
+
+    k10 = K == 10
+    out = {"workload": config_block(W, args)["workload"],
+           "batch": "%d queries (%d items x k in %s); the probe radius at k = 10 only"
+           % (len(K), len(W.query_idx), sorted(set(int(k) for k in K.tolist()))),
+           "base": {k: (int(v) if not isinstance(v, float) else v) for k, v in base.items()},
+           "leaf_size": [point(Q, K, False, leaf_size=v) for v in (32, 64, 128, 256)],
+           "probe_radius": [point(Q[k10], K[k10], True, probe_radius=v) for v in (0, 1, 2)],
+           "b": [point(Q, K, True, b=v) for v in (0.3, 0.5, 0.7, 0.9)],
+           "n_tables": [point(Q, K, True, n_tables=v) for v in (32, 64, 128)]}
+    return {"sweep": out}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -402,6 +479,13 @@ def main():
             launches /= reps
             ix.set_timing(False)
         return host, times, stage_ms, launches, st_last, total
+
+    if args.sweep:
+        if rank == 0:
+            print(json.dumps(run_sweeps(sah, W, Q, K, dev, stream, flush, args)), flush=True)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
 
     tc_main = int(args.tc_user_pass and args.precision == "bf16")
     ix, build_s = build(args.threshold, args.precision, tc_user_pass=tc_main)
