@@ -86,3 +86,28 @@ def test_pinned_inputs_pageable_output(sah):
     assert st == 0
     for i in range(3):
         assert np.array_equal(out[offs[i]:offs[i + 1]], ref[i])
+
+
+def test_pinned_two_sub_batches(sah):
+    """More rows than one sub-batch holds (4096): the answers gather in the library's
+    buffer and are copied into the pinned output at the end."""
+    torch = pytest.importorskip("torch")
+    W = workload.make("c1", m=700, n=400)
+    ix = sah.Index(W.U, W.P, k_max=10, leaf_size=16, p_prime=0, precision=1, tc_user_pass=1)
+    rng = np.random.default_rng(11)
+    nq = 4500
+    Q = np.ascontiguousarray(W.P[rng.integers(0, W.n, nq)])
+    K = rng.integers(1, 13, nq).astype(np.int32)
+    ref = ix.rkmips_batch(Q, K)
+    total = sum(len(r) for r in ref)
+    Qp, Kp = _pinned(Q), _pinned(K)
+    out = torch.empty(max(total, 1), dtype=torch.int32).pin_memory()
+    offs = torch.empty(nq + 1, dtype=torch.int64).pin_memory()
+    assert _call(ix, Qp, Kp, out, offs) == 0
+    o = offs.numpy()
+    assert o[-1] == total
+    for i in range(nq):
+        assert np.array_equal(out.numpy()[o[i]:o[i + 1]], ref[i]), i
+    for i in range(0, nq, 450):
+        want = np.flatnonzero(oracle.count_above(W.U, W.P, Q[i]) < K[i]).astype(np.int32)
+        assert np.array_equal(out.numpy()[o[i]:o[i + 1]], want), i
