@@ -11,9 +11,8 @@
 namespace sah {
 namespace {
 
-// DP4 > 0: user rows of at most 4 DP4 floats, held in registers for both the FP32 and the
-// double-precision dot (the query row is read twice, the second time from L1); DP4 = 0:
-// any width, read as needed.
+// DP4 > 0: user rows of at most 4 DP4 floats, held in registers for the FP32 dot; DP4 = 0:
+// any width, read as needed.  The double-precision dot reads both rows again (from L1).
 template <int DP4>
 __global__ void pair_rescore_kernel(const Survivor* __restrict__ pairs, const unsigned long long* __restrict__ count,
                                     int64_t cap, const float* __restrict__ Ut, const float* __restrict__ unorm,
@@ -85,21 +84,10 @@ __global__ void pair_rescore_kernel(const Survivor* __restrict__ pairs, const un
           const double t64 = T64[(int64_t)(k - 1) * mz + r];
           if (t64 == t64) {
             fp64 = true;
-            double s64 = 0.0;
-            if (DP4 > 0) {
-              // the sequential double-precision sum i = 0..d-1 over the registers
-#pragma unroll
-              for (int c = 0; c < DP4; ++c) {
-                const float4 b = c < dp / 4 ? __ldg(q4 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
-                const float a4[4] = {ur[c].x, ur[c].y, ur[c].z, ur[c].w};
-                const float b4[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                  if (4 * c + e < d) s64 = __fma_rn(f2d_bits(a4[e]), f2d_bits(b4[e]), s64);
-              }
-            } else {
-              s64 = dot64_seq(Ut + (int64_t)r * dp, Qd + (int64_t)j * dp, d);
-            }
+            // the sequential double-precision sum i = 0..d-1, as a rolled loop (the rows
+            // are in L1 by now): unrolled over the registers it was so long that the warps
+            // waited on instruction fetch
+            const double s64 = dot64_seq(Ut + (int64_t)r * dp, Qd + (int64_t)j * dp, d);
             yes = s64 >= t64;
           } else {
             surv_flag = true;

@@ -260,6 +260,7 @@ __device__ __forceinline__ double f2d_bits(float x) {
 __device__ inline double dot64_seq(const float* __restrict__ a, const float* __restrict__ b,
                                    int d) {
   double s = 0.0;
+#pragma unroll 2
   for (int i = 0; i < d; ++i) s = __fma_rn(f2d_bits(a[i]), f2d_bits(b[i]), s);
   return s;
 }
