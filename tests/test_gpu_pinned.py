@@ -111,3 +111,28 @@ def test_pinned_two_sub_batches(sah):
     for i in range(0, nq, 450):
         want = np.flatnonzero(oracle.count_above(W.U, W.P, Q[i]) < K[i]).astype(np.int32)
         assert np.array_equal(out.numpy()[o[i]:o[i + 1]], want), i
+
+
+def test_pinned_mixed_modes(sah):
+    """Pinned requests with a pinned modes array (half the rows in SA-ALSH mode): the same
+    answers as the call on pageable buffers; the exact rows equal the oracle's."""
+    torch = pytest.importorskip("torch")
+    W = workload.make("c1", m=1200, n=800)
+    ix = sah.Index(W.U, W.P, k_max=20, leaf_size=32, p_prime=0, precision=1, tc_user_pass=1, n_tables=16,
+                   code_bits=8)
+    rows = W.query_idx[:10]
+    Q = np.ascontiguousarray(np.repeat(W.P[rows], 2, axis=0))
+    K = np.tile(np.array([4, 15], np.int32), len(rows))
+    modes = np.tile(np.array([sah.SAALSH, sah.EXACT], np.int32), len(rows))
+    ref = ix.rkmips_batch(Q, K, modes=modes)
+    Qp, Kp, Mp = _pinned(Q), _pinned(K), _pinned(modes)
+    out = torch.empty(sum(len(r) for r in ref) + 1, dtype=torch.int32).pin_memory()
+    offs = torch.empty(len(K) + 1, dtype=torch.int64).pin_memory()
+    assert _call(ix, Qp, Kp, out, offs, modes=Mp) == 0
+    o = offs.numpy()
+    for i in range(len(K)):
+        got = out.numpy()[o[i]:o[i + 1]]
+        assert np.array_equal(got, ref[i]), i
+        if modes[i] == sah.EXACT:
+            want = np.flatnonzero(oracle.count_above(W.U, W.P, Q[i]) < K[i]).astype(np.int32)
+            assert np.array_equal(got, want), i
