@@ -851,7 +851,7 @@ constexpr int kAnswerThreads = 512;   // summary words counted and scanned per s
 constexpr int kCtlCounters = 5;   // survivor counts (3), answer-list length, scan ticket
 
 struct WsLayout {
-  size_t qd, qb, qn, qh, kk, pairs, pcount, kmask, tneed, coltab, survcnt, alist_n, ticket, bitmap, chunk, offsets, stats,
+  size_t qd, qb, qn, qh, kk, pairs, pcount, kmask, tneed, tneed_end, coltab, survcnt, alist_n, ticket, bitmap, chunk, offsets, stats,
       total;
 };
 
@@ -871,17 +871,20 @@ WsLayout layout_for(const Index* ix, int qb) {
   L.pairs = take(sizeof(PairEntry) * (size_t)std::max(ix->nb, 1) * qb);
   L.pcount = take(sizeof(int32_t) * std::max(ix->nb, 1));
   L.kmask = take(sizeof(uint32_t) * (size_t)std::max(ix->nb, 1) * ((qb + 31) / 32));
-  L.tneed = take((size_t)std::max<int64_t>((ix->m_nz + 127) / 128, 1));
   L.coltab = take(user_pass_tc_scratch_bytes(qb, ix->dp));
   L.chunk = take(sizeof(int32_t) * ((size_t)qb * (2 * (answer_words(answer_stride(ix->m)) / 32) + 1)));
-  // the control block, contiguous so that one memset clears its counters and one copy
-  // reads it back: stats[ST_COUNT] | survivor counts[3] | answer-list length (u64) |
-  // scan ticket (u64) | offsets[qb + 1]
-  L.stats = take(sizeof(unsigned long long) * (ST_COUNT + kCtlCounters) + sizeof(int64_t) * (size_t)(qb + 1));
+  // the control block, contiguous so that one memset clears its counters (and, with the
+  // tensor-core user pass, the tile flags) and one copy reads it back: stats[ST_COUNT] |
+  // survivor counts[3] | answer-list length (u64) | scan ticket (u64) | offsets[qb + 1] |
+  // one byte per 128-user tile (set by the block filter for the tiles of kept leaves)
+  const size_t ntiles = (size_t)std::max<int64_t>((ix->m_nz + 127) / 128, 1);
+  L.stats = take(sizeof(unsigned long long) * (ST_COUNT + kCtlCounters) + sizeof(int64_t) * (size_t)(qb + 1) + ntiles);
   L.survcnt = L.stats + sizeof(unsigned long long) * ST_COUNT;
   L.alist_n = L.survcnt + 3 * sizeof(unsigned long long);
   L.ticket = L.alist_n + sizeof(unsigned long long);
   L.offsets = L.ticket + sizeof(unsigned long long);
+  L.tneed = L.offsets + sizeof(int64_t) * (size_t)(qb + 1);
+  L.tneed_end = L.tneed + ntiles;
   L.total = o;
   return L;
 }
@@ -1116,10 +1119,14 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
       // every device operation of the attempt, the readback of its results included
       auto enqueue = [&]() -> sah_status {
         tm.begin(0);
-        // the counters of the control block (stats, survivor counts, answer-list length)
-        SAH_CUDA(cudaMemsetAsync(stats, 0, sizeof(unsigned long long) * (ST_COUNT + kCtlCounters), st));
         // with the tensor-core user pass the preparation also writes the split BF16 queries
         const bool tc_pass = ix->nb > 0 && ix->dk > 0 && ix->prm.tc_user_pass && ix->m_nz > 0;
+        // the counters of the control block (stats, survivor counts, answer-list length),
+        // through the tile flags when the tensor-core user pass reads them
+        SAH_CUDA(cudaMemsetAsync(stats, 0,
+                                 tc_pass ? L.tneed_end - L.stats
+                                         : sizeof(unsigned long long) * (ST_COUNT + kCtlCounters),
+                                 st));
         prep_queries_kernel<<<grid_for(nqb, 8), 256, 0, st>>>(Q_dev + (int64_t)q0 * ix->d, nqb, ix->d, ix->dp, Qd, qn,
                                                                ks_dev + q0, kk, modes_q, stats,
                                                                tc_pass ? (uint16_t*)(w + L.qb) : nullptr, ix->dk,
@@ -1135,8 +1142,8 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
             // the distinct query vectors first: the block bound is taken once per vector
             SAH_TRY(prepare_user_pass_tc(ix, Qd, qn, (const uint64_t*)(w + L.qh), w + L.coltab, kk, modes_q, nqb,
                                          st, &bf_launches));
-            SAH_TRY(block_filter_tc(ix, w + L.coltab, nqb, kmask, mask_words, stats, ST_PAIRS_KEPT,
-                                    ST_KEPT_USERS, ST_USERS_SCORED, st));
+            SAH_TRY(block_filter_tc(ix, w + L.coltab, nqb, kmask, mask_words, (uint8_t*)(w + L.tneed), stats,
+                                    ST_PAIRS_KEPT, ST_KEPT_USERS, ST_USERS_SCORED, st));
           } else {
             block_filter_kernel<<<ix->nb, 128, sizeof(float) * ix->dp, st>>>(
                 ix->bcent, ix->bcos, ix->bsin, ix->LB, ix->nb, ix->kmax, ix->n, ix->dp, Qd, qn, kk, nqb,

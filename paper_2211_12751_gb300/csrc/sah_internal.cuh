@@ -283,13 +283,15 @@ sah_status run_saalsh(Index* ix, const Survivor* surv, const unsigned long long*
 //    qh, a 64-bit hash of each padded query row's bits, are written by the query
 //    preparation.
 //  block_filter_tc: A3 per (leaf, column), the rows' decisions into kept_mask
-//    ([nb][mask_words]) and the counters stats[st_pairs], stats[st_users], stats[st_scored].
-//  run_user_pass_tc: the GEMM and its epilogue; tile_need holds one byte per 128-user tile;
+//    ([nb][mask_words]), a 1 into tile_need (one byte per 128-user tile, zero on entry) for
+//    every tile holding a user of a leaf with a kept row, and the counters stats[st_pairs],
+//    stats[st_users], stats[st_scored].
+//  run_user_pass_tc: the GEMM and its epilogue over the tiles tile_need marks;
 //    the pairs its band leaves open go to resc and are re-scored in FP32.
 size_t user_pass_tc_scratch_bytes(int nq, int dp);
 sah_status prepare_user_pass_tc(Index* ix, const float* Qd, const float* qn, const uint64_t* qh, void* scratch,
                                 const int32_t* kk, const int32_t* modes, int nq, cudaStream_t st, int* launches);
-sah_status block_filter_tc(Index* ix, void* scratch, int nq, uint32_t* kept_mask, int mask_words,
+sah_status block_filter_tc(Index* ix, void* scratch, int nq, uint32_t* kept_mask, int mask_words, uint8_t* tile_need,
                            unsigned long long* stats, int st_pairs, int st_users, int st_scored,
                            cudaStream_t st);
 sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* scratch, const float* qn,

@@ -303,8 +303,8 @@ __global__ void __launch_bounds__(128)
 block_filter_cols_kernel(const float* __restrict__ bcent, const float* __restrict__ bcos,
                          const float* __restrict__ bsin, const float* __restrict__ LB, int nb, int kmax, int dp,
                          int nq, ColTable T, float slack, uint32_t* __restrict__ kept_mask, int mask_words,
-                         const int32_t* __restrict__ bstart, unsigned long long* __restrict__ stats, int st_pairs,
-                         int st_users, int st_scored) {
+                         const int32_t* __restrict__ bstart, uint8_t* __restrict__ tile_need,
+                         unsigned long long* __restrict__ stats, int st_pairs, int st_users, int st_scored) {
   extern __shared__ float4 cen[];   // [kFilterLeaves][dp / 4] the leaves' unit centres
   __shared__ int2 rs[kFilterRows];   // (j, k) of the rows
   __shared__ uint32_t kbits[kFilterLeaves][kMaxRows / 32];
@@ -401,6 +401,11 @@ block_filter_cols_kernel(const float* __restrict__ bcent, const float* __restric
   __syncthreads();
   for (int i = tid; i < nl * mask_words; i += nt)
     kept_mask[(int64_t)B0 * mask_words + i] = kbits[i / mask_words][i % mask_words];
+  // the user pass streams the 128-user tiles that hold a user of a leaf with a kept row
+  if (tid < nl && kept_sh[tid] > 0) {
+    const int t0 = bstart[B0 + tid] / kUM, t1 = (bstart[B0 + tid + 1] - 1) / kUM;
+    for (int t = t0; t <= t1; ++t) tile_need[t] = 1;
+  }
   if (tid == 0) {
     unsigned long long pairs = 0, users = 0, scored = 0;
     for (int l = 0; l < nl; ++l) {
@@ -999,23 +1004,6 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
   }
 }
 
-// Which 128-user tiles hold a user of a leaf with a kept pair (one warp per tile).
-__global__ void tile_need_kernel(const int32_t* __restrict__ ublock, int64_t mz,
-                                 const uint32_t* __restrict__ kept_mask, int mask_words, int ntiles,
-                                 uint8_t* __restrict__ need) {
-  const int t = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  const int lane = threadIdx.x & 31;
-  if (t >= ntiles) return;
-  const int64_t r0 = (int64_t)t * kUM;
-  const int64_t r1 = (r0 + kUM < mz ? r0 + kUM : mz) - 1;
-  const int Bf = ublock[r0], Bl = ublock[r1];
-  bool any = false;
-  for (int64_t i = lane; i < (int64_t)(Bl - Bf + 1) * mask_words; i += 32) any |= kept_mask[Bf * (int64_t)mask_words + i] != 0u;
-  any = __any_sync(0xffffffffu, any);
-  if (lane == 0) need[t] = any ? 1 : 0;
-}
-
-inline unsigned grid_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
 
 template <int KB, int STAGES, int NMAX>
 sah_status launch_pass(Index* ix, UpParams p, int sms, cudaStream_t st, int* launches, const cudaEvent_t* ev) {
@@ -1073,7 +1061,7 @@ sah_status prepare_user_pass_tc(Index* ix, const float* Qd, const float* qn, con
   return SAH_OK;
 }
 
-sah_status block_filter_tc(Index* ix, void* scratch, int nq, uint32_t* kept_mask, int mask_words,
+sah_status block_filter_tc(Index* ix, void* scratch, int nq, uint32_t* kept_mask, int mask_words, uint8_t* tile_need,
                            unsigned long long* stats, int st_pairs, int st_users, int st_scored,
                            cudaStream_t st) {
   if (ix->nb == 0 || nq == 0) return SAH_OK;
@@ -1081,7 +1069,7 @@ sah_status block_filter_tc(Index* ix, void* scratch, int nq, uint32_t* kept_mask
   block_filter_cols_kernel<<<(ix->nb + kFilterLeaves - 1) / kFilterLeaves, 128,
                              sizeof(float) * ix->dp * kFilterLeaves, st>>>(
       ix->bcent, ix->bcos, ix->bsin, ix->LB, ix->nb, ix->kmax, ix->dp, nq, T, ix->cone_slack, kept_mask, mask_words,
-      ix->bstart, stats, st_pairs, st_users, st_scored);
+      ix->bstart, tile_need, stats, st_pairs, st_users, st_scored);
   SAH_CUDA(cudaGetLastError());
   return SAH_OK;
 }
@@ -1128,10 +1116,6 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
   p.stats = stats;
   p.st_yes = st_yes;
   p.timeout = ix->dev_timeout;
-  tile_need_kernel<<<grid_for(p.ntiles, 8), 256, 0, st>>>(ix->ublock, ix->m_nz, kept_mask, mask_words, p.ntiles,
-                                                          tile_need);
-  SAH_CUDA(cudaGetLastError());
-  if (launches) *launches += 1;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
   if (ix->dk == 64) {
