@@ -314,7 +314,8 @@ def run_reference(args):
 
 
 def config_block(W, args):
-    return {"mode": "saalsh" if getattr(args, "saalsh", False) else "exact","workload": f"{W.name}: n={W.n} items, m={W.m} users, d={W.d}, mf rank-50 lognormal(0,0.7), "
+    return {"mode": "saalsh" if getattr(args, "saalsh", False) else "exact",
+            "workload": f"{W.name}: n={W.n} items, m={W.m} users, d={W.d}, mf rank-50 lognormal(0,0.7), "
                         f"5% items x3, seed 0; {len(W.query_idx)} item queries x k in {list(map(int, W.ks))}",
             "queries_per_step": int(len(W.query_idx) * (len(W.ks) if W.every_k else 1)),
             "threshold_mode": args.threshold, "precision": args.precision, "leaf_size": args.leaf_size,
@@ -596,8 +597,8 @@ def main():
             "roofline": roof,
             "stages_ms": {nm: float(stage_ms[i]) for i, nm in enumerate(STAGE_NAMES)},
             "stage_counts": {k: st[k] for k in ("block_pairs_total", "block_pairs_kept", "users_in_kept_blocks",
-                                                "users_scored", "users_yes_early", "pairs_rescored", "survivors", "fp64_rescored",
-                                                "items_scanned", "results")},
+                                                "users_scored", "users_yes_early", "pairs_rescored", "survivors",
+                                                "fp64_rescored", "items_scanned", "results")},
             "index_build_s": build_s, "index_gemm": index_gemm, "clocks": clocks,
             "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99)),
                            "per": "batch of %d queries" % nq}}

@@ -851,8 +851,8 @@ constexpr int kAnswerThreads = 512;   // summary words counted and scanned per s
 constexpr int kCtlCounters = 5;   // survivor counts (3), answer-list length, scan ticket
 
 struct WsLayout {
-  size_t qd, qb, qn, qh, kk, pairs, pcount, kmask, tneed, tneed_end, coltab, survcnt, alist_n, ticket, bitmap, chunk, offsets, stats,
-      total;
+  size_t qd, qb, qn, qh, kk, pairs, pcount, kmask, tneed, tneed_end, coltab, survcnt, alist_n, ticket, bitmap, chunk,
+      offsets, stats, total;
 };
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
