@@ -65,10 +65,14 @@ def pivot_position(seed: int, key: int, size: int) -> int:
 
 
 # ----------------------------------------------------------------------------- SRP / SAT
+def sign_bits(proj: np.ndarray) -> np.ndarray:
+    """Eq. 1's sign as a bit: 1 where sgn(projection) = +1, with sgn(0) := +1."""
+    return (np.asarray(proj, np.float64) >= 0.0).astype(np.uint8)
+
+
 def srp_bits(A: np.ndarray, x: np.ndarray) -> np.ndarray:
     """Eq. 1 for every row of A: bit 1 where sgn(<a, x>) = +1 (sgn(0) := +1)."""
-    proj = np.asarray(A, np.float64) @ np.asarray(x, np.float64)
-    return (proj >= 0.0).astype(np.uint8)
+    return sign_bits(np.asarray(A, np.float64) @ np.asarray(x, np.float64))
 
 
 def srp_projections(A: np.ndarray, X: np.ndarray) -> np.ndarray:
@@ -143,7 +147,7 @@ def sa_alsh_index(P_sorted: np.ndarray, norms_sorted: np.ndarray, first: int, b:
         c = X.mean(axis=0)
         R = float(np.max(np.sqrt(((X - c) ** 2).sum(axis=1))))
         I = np.stack([sat_item(x, c, R) for x in X])
-        bits = (srp_projections(A, I) >= 0.0).astype(np.uint8)
+        bits = sign_bits(srp_projections(A, I))
         cd = pack_codes(bits, n_tables, code_bits)
         tab = []
         for t in range(n_tables):
@@ -185,23 +189,33 @@ def kth_largest(values: np.ndarray, k: int) -> float:
 
 
 def sa_alsh_decide(index: SAALSHIndex, P_sorted: np.ndarray, u: np.ndarray, q: np.ndarray,
-                   k: int, seed_items: np.ndarray, probe_radius: int) -> bool:
-    """Alg. 2: does q stay in u's kMIPS answer?  C starts as ``seed_items`` (P')."""
+                   k: int, seed_items: np.ndarray, probe_radius: int,
+                   trace: Optional[list] = None) -> bool:
+    """Alg. 2: does q stay in u's kMIPS answer?  C starts as ``seed_items`` (P').
+
+    ``trace`` (optional) receives every comparison the decision makes, in order, as
+    ("phi", <u,q>, phi) and ("mu", phi, mu_j); it changes nothing in the decision."""
     u = np.asarray(u, np.float64)
     P64 = np.asarray(P_sorted, np.float64)
     sq = float(ips(np.asarray(q, np.float64), u)[0])
     nu = float(np.sqrt(u @ u))
     C = set(int(i) for i in seed_items)
     phi = kth_largest(ips(P64[sorted(C)], u), k) if C else -np.inf
+    if trace is not None:
+        trace.append(("phi", sq, phi))
     if sq < phi:
         return False
     for j in range(len(index.items)):
         mu = index.M[j] * nu
+        if trace is not None:
+            trace.append(("mu", phi, mu))
         if phi > mu:
             return True
         ucodes = user_codes(index, u, float(index.radii[j]))
         C |= simhash_candidates(index, j, ucodes, probe_radius)
         phi = kth_largest(ips(P64[sorted(C)], u), k)
+        if trace is not None:
+            trace.append(("phi", sq, phi))
         if sq < phi:
             return False
     return True
@@ -315,9 +329,14 @@ def sah_index(P, U, kmax: int = 50, N0: int = 20, p_prime: Optional[int] = None,
                     blocks=blocks, LB=LB, Uhat=Uhat, zero_users=zero, saalsh=sa)
 
 
-def sah_query(ix: SAHIndex, q, k: int, mode: str = "exact", probe_radius: int = 0) -> np.ndarray:
+def sah_query(ix: SAHIndex, q, k: int, mode: str = "exact", probe_radius: int = 0,
+              trace: Optional[Dict[int, list]] = None) -> np.ndarray:
     """Alg. 5: block test (Lemma 2), user test (Lemma 3), <u,q> vs L_i^k, ||p_k|| test, and
-    the kMIPS decision (``exact``: the count rule; ``saalsh``: Alg. 2).  Ascending ids."""
+    the kMIPS decision (``exact``: the count rule; ``saalsh``: Alg. 2).  Ascending ids.
+
+    ``trace`` (optional) receives, per user that reaches the <u,q> tests, every comparison
+    its decision makes: ("L", <u,q>, L_u^k), ("pk", <u,q>, ||p_k||), then those of
+    ``sa_alsh_decide``; it changes no decision."""
     q = np.asarray(q, np.float64)
     n = ix.P_sorted.shape[0]
     nq = float(np.sqrt(q @ q))
@@ -334,6 +353,11 @@ def sah_query(ix: SAHIndex, q, k: int, mode: str = "exact", probe_radius: int = 
                 continue
             uh = ix.Uhat[u]
             s = float(ips(q, uh)[0])
+            tr = None
+            if trace is not None:
+                tr = trace.setdefault(int(u), [])
+                tr.append(("L", s, Lk))
+                tr.append(("pk", s, pk))
             if s < Lk:
                 continue
             if pk > s:
@@ -341,7 +365,7 @@ def sah_query(ix: SAHIndex, q, k: int, mode: str = "exact", probe_radius: int = 
                     yes = int(np.count_nonzero(ips(ix.P_sorted, uh) > s)) < k
                 else:
                     yes = sa_alsh_decide(ix.saalsh, ix.P_sorted, uh, q, k,
-                                         np.arange(ix.p_prime), probe_radius)
+                                         np.arange(ix.p_prime), probe_radius, trace=tr)
                 if yes:
                     out.append(int(u))
             else:

@@ -88,3 +88,107 @@ def test_fp8_dimension_limit(sah):
     with pytest.raises(sah.SahError) as e:
         sah.Index(W.U, W.P, k_max=10, leaf_size=32, precision=2)
     assert e.value.status == sah.SAH_ERR_UNSUPPORTED
+
+
+def _user_code_rows(rix, Uhat):
+    """Every user's code per table (partition-independent for R_j > 0)."""
+    return np.stack([ref.user_codes(rix.saalsh, u, 1.0) for u in Uhat]).astype(np.int64)
+
+
+def _ambiguous_item_bits(A, rix, tol_code):
+    """(partition, item position, table) of every item SRP projection within rounding of
+    zero: tol_code of ||a|| R (the product's rounding), the rounding of p - c, and the
+    rounding of the SAT's last coordinate sqrt(R^2 - ||p - c||^2), largest where the
+    radicand is small."""
+    d = A.shape[1] - 1
+    sa = rix.saalsh
+    An = np.linalg.norm(A, axis=1)
+    out = []
+    for j, S in enumerate(sa.items):
+        X = rix.P_sorted[S]
+        c, R = sa.centroids[j], float(sa.radii[j])
+        diff = X - c
+        rad = R * R - (diff * diff).sum(axis=1)
+        last = np.sqrt(np.maximum(rad, 0.0))
+        proj = np.concatenate([diff, last[:, None]], axis=1) @ A.T
+        delta = 1e-5 * R * R
+        dlast = np.where(last > 0, np.minimum(delta / (2 * np.maximum(last, 1e-300)), np.sqrt(delta)),
+                         np.sqrt(delta))
+        tol = (An[None, :] * (tol_code * R + 1e-6 * np.linalg.norm(c))
+               + np.abs(A[:, d])[None, :] * dlast[:, None])
+        for row, col in zip(*np.nonzero(np.abs(proj) < tol)):
+            out.append((j, int(S[row]), int(row), int(col // sa.code_bits)))
+    return out
+
+
+def _excluded_users(A, rix, probe_radius, tol_code, tol_score, traces, q, codes_u, amb_items):
+    """Users whose decision may legitimately differ between the GPU and the oracle:
+    * a comparison of the decision (<u,q> vs L, ||p_k|| or phi; phi vs mu_j) within
+      rounding of a tie;
+    * for users that reach Alg. 2: an SRP projection of the user within rounding of zero
+      (a code bit may flip), or an item projection within rounding of zero in a table
+      where the flip can change the item's candidacy for the user (Hamming distance
+      probe_radius or probe_radius + 1), for an item of a partition the user's Alg. 2
+      reached and whose score reaches the phi after that partition (an item below it
+      cannot move the k-th largest score of C)."""
+    d = A.shape[1] - 1
+    An = np.linalg.norm(A[:, :d], axis=1)
+    Uhat = rix.Uhat
+    scale = max(float(np.linalg.norm(q)), float(rix.norms[0]))
+    slack = tol_score * scale
+    excl = set()
+    for u, tr in traces.items():
+        if any(abs(a - b) < slack for _, a, b in tr if np.isfinite(a) and np.isfinite(b)):
+            excl.add(u)
+            continue
+        phis = [b for tag, _, b in tr if tag == "phi"]
+        if not phis:
+            continue                       # decided before Alg. 2: codes play no part
+        if np.any(np.abs(A[:, :d] @ Uhat[u]) < tol_code * An):
+            excl.add(u)
+            continue
+        after = phis[1:]                   # phi after partition j, for the partitions reached
+        for j, item, row, t in amb_items:
+            if j >= len(after):
+                continue
+            h = bin(int(codes_u[u, t]) ^ int(rix.saalsh.codes[j][row, t])).count("1")
+            if h in (probe_radius, probe_radius + 1) and float(rix.P_sorted[item] @ Uhat[u]) >= after[j] - slack:
+                excl.add(u)
+                break
+    return excl
+
+
+# FP32 codes (error below 1e-5 of ||a|| ||x||) and tensor-core codes with split BF16
+# operands (below 1e-4: 1.01 (3 2^-16 + (6 K + 16) 2^-23) with K = 64); the FP8 codes flip
+# too many bits near zero for a set comparison
+@pytest.mark.parametrize("probe_radius", [1, 2])
+@pytest.mark.parametrize("precision,tc,tol_code", [(0, 0, 1e-5), (1, 1, 1e-4)])
+def test_equals_oracle_alg2_at_probe_radius(sah, probe_radius, precision, tc, tol_code):
+    """SA-ALSH mode at Hamming probe radius 1 and 2 returns the oracle's Alg. 2 answer for
+    every user whose decision is not within rounding of a code bit or of a tie."""
+    W, A, ix = _setup(sah, probe_radius=probe_radius, m=500, n=600, p_prime=20, precision=precision,
+                      tc_user_pass=tc)
+    A64 = A.astype(np.float64)
+    rix = ref.sah_index(W.P, W.U, kmax=20, N0=32, p_prime=20, A=A64, n_tables=8, code_bits=6, b=0.5)
+    # the index's item order and partition bounds must not sit on a rounding boundary
+    nrm = rix.norms
+    assert abs(nrm[19] - nrm[20]) > 1e-6 * nrm[0]
+    for S, M in zip(rix.saalsh.items, rix.saalsh.M):
+        assert np.all(np.abs(nrm[S] - 0.5 * M) > 1e-6 * M)
+    codes_u = _user_code_rows(rix, rix.Uhat)
+    amb = _ambiguous_item_bits(A64, rix, tol_code)
+    compared = excluded = in_alg2 = 0
+    for qi in W.query_idx[:6]:
+        q = W.P[qi]
+        for k in (1, 10, 20):
+            traces = {}
+            want = set(ref.sah_query(rix, q, k, "saalsh", probe_radius=probe_radius, trace=traces).tolist())
+            got = set(ix.rkmips(q, k, mode=sah.SAALSH).tolist())
+            excl = _excluded_users(A64, rix, probe_radius, tol_code, 1e-4, traces, q, codes_u, amb)
+            keep = set(range(W.m)) - excl
+            assert got & keep == want & keep, (qi, k, sorted((got ^ want) & keep)[:10])
+            compared += len(keep)
+            excluded += len(excl)
+            in_alg2 += sum(1 for u, tr in traces.items() if u not in excl and any(x[0] == "phi" for x in tr))
+    assert excluded <= 0.2 * (compared + excluded), (excluded, compared)
+    assert in_alg2 >= 1000, in_alg2      # the comparison reaches Alg. 2 for many users

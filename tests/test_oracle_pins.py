@@ -204,3 +204,50 @@ def test_pins_catch_planted_mistakes():
         diffs += _mutant_nonstrict(U, P, q, k) != _enumeration_answer(
             P.astype(int).tolist(), U.astype(int).tolist(), q.astype(int).tolist(), 0, k)
     assert diffs > 0
+
+
+# ------------------------------------------------------------------ margins
+def test_golden_margins_and_planted_mistakes():
+    """margin_u = |<u,q> - tau_u(k)| / (||u|| ||q||), the distance of a user's decision from
+    a tie, against values worked by hand; a wrong k index or a missing norm in the
+    denominator changes at least one of them."""
+    g = _load("rkmips_2d.json")
+    P = np.array(g["P"], np.float32)
+    U = np.array(g["U"], np.float32)
+    mg = g["margins"]
+    q = np.array(mg["q"], np.float32)
+    users = np.arange(U.shape[0])
+    T = oracle.tau(U, P, 4, users)
+    want = {(c["user"], c["k"]): float(c["margin"]) for c in mg["cases"]}
+    for (u, k), m in want.items():
+        got = oracle.margins(U, T[[u]], q, k, np.array([u]))[0]
+        assert got == m if np.isinf(m) else np.isclose(got, m, rtol=1e-15, atol=0.0), (u, k, got, m)
+
+    def mutant(kind, u, k):
+        U64, q64 = U.astype(np.float64), q.astype(np.float64)
+        sq = U64[u] @ q64
+        t = T[u, k if kind == "k_index" else k - 1]
+        den = {"no_q_norm": np.linalg.norm(U64[u]), "no_u_norm": np.linalg.norm(q64)}.get(
+            kind, np.linalg.norm(U64[u]) * np.linalg.norm(q64))
+        return abs(sq - t) / den if den > 0 else np.inf
+
+    for kind in ("k_index", "no_q_norm", "no_u_norm"):
+        assert any(not np.isclose(mutant(kind, u, k), m) for (u, k), m in want.items()
+                   if np.isfinite(m) and k < 4), kind
+
+
+def test_margin_scale_invariance_and_zero_at_ties():
+    W = workload.make("c2", m=200, n=300)
+    users = workload.sample_rows(W.m, 40, seed=4)
+    q = W.P[W.query_idx[0]]
+    T = oracle.tau(W.U, W.P, 10, users)
+    m1 = oracle.margins(W.U, T, q, 10, users)
+    T2 = oracle.tau(W.U * 4.0, W.P, 10, users)            # power-of-two scaling is exact
+    m2 = oracle.margins(W.U * 4.0, T2, q, 10, users)
+    np.testing.assert_allclose(m1, m2, rtol=1e-12)
+    # q equal to a user's k-th item: margin 0 for that user at that k
+    u = int(users[0])
+    s = W.U[u].astype(np.float64) @ W.P.astype(np.float64).T
+    kth = int(np.argsort(-s, kind="stable")[2])
+    m3 = oracle.margins(W.U, oracle.tau(W.U, W.P, 3, np.array([u])), W.P[kth], 3, np.array([u]))
+    assert m3[0] == 0.0

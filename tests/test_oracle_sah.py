@@ -214,3 +214,110 @@ def test_splitmix64_reference_values():
     assert sah.splitmix64(0) == 0xE220A8397B1DCDAF
     # second output: state advanced by the golden gamma once more
     assert sah.splitmix64(0x9E3779B97F4A7C15) == 0x6E789E6AA1B965F4
+
+
+# ------------------------------------------------------------------ SimHash candidate rule
+def _simhash_golden():
+    with open(os.path.join(GOLDEN, "simhash_2x3.json")) as f:
+        return json.load(f)
+
+
+def _simhash_state(g):
+    P = np.array(g["P"], float)
+    norms = np.linalg.norm(P, axis=1)
+    A = np.array(g["A"], float)
+    ix = sah.sa_alsh_index(P, norms, 0, g["b"], A, g["n_tables"], g["code_bits"])
+    uc = sah.user_codes(ix, np.array(g["u"], float), float(ix.radii[0]))
+    cands = {r: sorted(sah.simhash_candidates(ix, 0, uc, int(r))) for r in g["candidates"]}
+    return P, ix, uc, cands
+
+
+def _simhash_matches(g, state):
+    P, ix, uc, cands = state
+    return (len(ix.items) == 1 and ix.codes[0].tolist() == g["item_codes"]
+            and uc.tolist() == g["user_codes"]
+            and all(cands[r] == g["candidates"][r] for r in g["candidates"]))
+
+
+def test_golden_simhash_codes_and_candidates():
+    """Eq. 1, Eq. 9 and Alg. 1's K tables of code_bits SRP bits, against a case worked by
+    hand: the partition, its centroid and radius, every item's and the user's code per
+    table, and the candidate set at probe radius 0, 1, 2 and 3."""
+    g = _simhash_golden()
+    P, ix, uc, cands = state = _simhash_state(g)
+    assert [len(s) for s in ix.items] == [6]
+    assert np.allclose(ix.centroids[0], g["centroid"]) and np.isclose(ix.radii[0], g["R"])
+    assert ix.codes[0].tolist() == g["item_codes"]
+    assert uc.tolist() == g["user_codes"]
+    for r, want in g["candidates"].items():
+        assert cands[r] == want, r
+    assert _simhash_matches(g, state)
+    # buckets: each table maps a code to the items that carry it
+    for t in range(g["n_tables"]):
+        for code, members in ix.tables[0][t].items():
+            assert all(g["item_codes"][i][t] == code for i in members)
+
+
+def test_golden_alg2_decisions_by_probe_radius():
+    """Alg. 2 on the hand-worked index: a radius-0 probe misses an item that beats <u,q>
+    and answers "yes" where the definition says "no"; radius 1 finds it."""
+    g = _simhash_golden()
+    P, ix, _, _ = _simhash_state(g)
+    u = np.array(g["u"], float)
+    a2 = g["alg2"]
+    q = P[a2["q_item"]]
+    assert int(np.count_nonzero(P @ u > q @ u)) == a2["exact_count_above"]
+    for c in a2["cases"]:
+        got = sah.sa_alsh_decide(ix, P, u, q, c["k"], np.array([], dtype=int), c["probe_radius"])
+        assert got == c["yes"], c
+
+
+def test_simhash_pins_catch_planted_mistakes(monkeypatch):
+    """Each plausible slip in the candidate rule fails the golden case: a strict Hamming
+    test, bits assigned to tables column-wise instead of row-wise, sgn(0) read as -1, and
+    the bits of a code packed in reverse order."""
+    g = _simhash_golden()
+    orig_pack, orig_bits, orig_cand = sah.pack_codes, sah.sign_bits, sah.simhash_candidates
+
+    def strict_candidates(index, j, ucodes, probe_radius):
+        out = set()
+        for t in range(index.n_tables):
+            for code, members in index.tables[j][t].items():
+                if bin(code ^ int(ucodes[t])).count("1") < probe_radius:
+                    out.update(members)
+        return out
+
+    def transposed_pack(bits, n_tables, code_bits):
+        bits = np.atleast_2d(bits).astype(np.uint64)
+        out = np.zeros((bits.shape[0], n_tables), dtype=np.uint64)
+        for t in range(n_tables):
+            for b in range(code_bits):
+                out[:, t] |= bits[:, b * n_tables + t] << np.uint64(b)
+        return out
+
+    def reversed_pack(bits, n_tables, code_bits):
+        bits = np.atleast_2d(bits).astype(np.uint64)
+        out = np.zeros((bits.shape[0], n_tables), dtype=np.uint64)
+        for t in range(n_tables):
+            for b in range(code_bits):
+                out[:, t] |= bits[:, t * code_bits + b] << np.uint64(code_bits - 1 - b)
+        return out
+
+    def negative_zero_bits(proj):
+        return (np.asarray(proj, np.float64) > 0.0).astype(np.uint8)
+
+    caught = {}
+    with monkeypatch.context() as mp:
+        mp.setattr(sah, "simhash_candidates", strict_candidates)
+        caught["strict_hamming"] = not _simhash_matches(g, _simhash_state(g))
+    with monkeypatch.context() as mp:
+        mp.setattr(sah, "pack_codes", transposed_pack)
+        caught["table_bit_mixup"] = not _simhash_matches(g, _simhash_state(g))
+    with monkeypatch.context() as mp:
+        mp.setattr(sah, "pack_codes", reversed_pack)
+        caught["reversed_bits"] = not _simhash_matches(g, _simhash_state(g))
+    with monkeypatch.context() as mp:
+        mp.setattr(sah, "sign_bits", negative_zero_bits)
+        caught["sgn0_minus"] = not _simhash_matches(g, _simhash_state(g))
+    assert sah.pack_codes is orig_pack and sah.sign_bits is orig_bits and sah.simhash_candidates is orig_cand
+    assert all(caught.values()), caught
