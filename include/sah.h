@@ -199,6 +199,22 @@ sah_status sah_index_blocks(const sah_index* index, int64_t* m_nz, int32_t* nb, 
  * sah_stats.stage_ms after the call. */
 sah_status sah_index_set_timing(sah_index* index, int32_t enable);
 
+/* Test hook for the failure path of the bounded device-side waits (the paper has no
+ * counterpart; Alg. 5's steps run unchanged).  Every wait inside a tensor-core kernel is
+ * bounded; this hook makes one run out without faulting or hanging the GPU.  site 1: in the
+ * next query call on this index (sah_rkmips or sah_rkmips_batch), the thread that issues the
+ * tensor-core user pass's MMAs (precision SAH_BF16 with tc_user_pass) stops after its first
+ * accumulator tile, as a lost pipeline partner would; site 2: the same in the tensor-core
+ * kMIPS decision (SAH_BF16, |P'| < n, survivors present).  The waiting epilogue gives up
+ * after its bounded spin (about a second), raises the index's device flag, every CTA waits
+ * for its own TMA loads and MMAs, frees its tensor memory and returns, and the call returns
+ * SAH_ERR_DEVICE_TIMEOUT with no valid result.  If the pass does not run (or finishes its
+ * work within one tile) the call succeeds as usual.  The hook applies to one call, which
+ * runs its launch sequence directly (never a replayed CUDA graph), then clears itself; the
+ * index stays usable.  site 0 clears it.  Not for use with a running server.
+ * Errors: SAH_ERR_ARG (NULL index, site outside 0..2). */
+sah_status sah_index_inject_stall(sah_index* index, int32_t site);
+
 /* Exact RkMIPS for one query without allocating any memory (the paper has no
  * counterpart; it exists for callers that may not allocate).
  *

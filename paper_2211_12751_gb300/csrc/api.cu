@@ -352,8 +352,10 @@ sah_status sah_rkmips_batch(sah_index* index, const float* Q, int32_t nq, const 
     sah::set_error("sah_rkmips_batch: invalid argument");
     return SAH_ERR_ARG;
   }
-  return batch_impl(index, Q, nq, ks, modes, buffers_on_device, out_ids, cap, out_offsets,
-                    (cudaStream_t)cuda_stream);
+  const sah_status s = batch_impl(index, Q, nq, ks, modes, buffers_on_device, out_ids, cap, out_offsets,
+                                  (cudaStream_t)cuda_stream);
+  index->impl.inject_site = 0;   // the test hook applies to one call
+  return s;
 }
 
 sah_status sah_rkmips(sah_index* index, const float* q, int32_t k, int32_t mode, int32_t* out_ids,
@@ -364,6 +366,7 @@ sah_status sah_rkmips(sah_index* index, const float* q, int32_t k, int32_t mode,
   }
   int64_t offs[2] = {0, 0};
   sah_status s = batch_impl(index, q, 1, &k, &mode, 0, out_ids, cap, offs, (cudaStream_t)cuda_stream);
+  index->impl.inject_site = 0;   // the test hook applies to one call
   *out_count = offs[1];
   return s;
 }
@@ -422,6 +425,15 @@ sah_status sah_index_blocks(const sah_index* index, int64_t* m_nz, int32_t* nb, 
   if (cos_theta && ix->m_nz)
     SAH_CUDA(cudaMemcpy(cos_theta, ix->ucos, sizeof(float) * ix->m_nz, cudaMemcpyDeviceToHost));
   if (cos_omega && ix->nb) SAH_CUDA(cudaMemcpy(cos_omega, ix->bcos, sizeof(float) * ix->nb, cudaMemcpyDeviceToHost));
+  return SAH_OK;
+}
+
+sah_status sah_index_inject_stall(sah_index* index, int32_t site) {
+  if (!index || site < 0 || site > sah::SAH_INJECT_VERIFY) {
+    sah::set_error("sah_index_inject_stall: NULL index or site outside 0..2");
+    return SAH_ERR_ARG;
+  }
+  index->impl.inject_site = site;
   return SAH_OK;
 }
 

@@ -108,7 +108,9 @@ codes_tc_kernel(const __grid_constant__ CUtensorMap tmUhi, const __grid_constant
       ok_sh = 1;
       tc::mbar_arrive(&mma_bar);
     } else {
-      // the loads did not arrive in time: nothing was issued, nothing to wait for
+      // the loads did not arrive in time: no MMA was issued; the loads themselves are
+      // waited for before the CTA can exit
+      tc::mbar_wait_drain(&load_bar, 0);
       tc::mbar_arrive(&mma_bar);
       tc::mbar_arrive(&mma_bar);
     }
@@ -142,6 +144,9 @@ codes_tc_kernel(const __grid_constant__ CUtensorMap tmUhi, const __grid_constant
   tc::tc_fence_before();
   __syncthreads();
   if (warp == 0) {
+    // the MMAs complete before TMEM is freed, also when a thread's wait gave up early
+    if (lane == 0) tc::mbar_wait_drain(&mma_bar, 0);
+    __syncwarp();
     tc::tc_fence_after();
     tc::tmem_dealloc(tbase, kCMaxN);
   }
@@ -266,6 +271,7 @@ codes_f8_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__
       ok_sh = 1;
       tc::mbar_arrive(&mma_bar);
     } else {
+      tc::mbar_wait_drain(&load_bar, 0);   // the loads, before the CTA can exit
       tc::mbar_arrive(&mma_bar);
       tc::mbar_arrive(&mma_bar);
     }
@@ -298,6 +304,9 @@ codes_f8_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__
   tc::tc_fence_before();
   __syncthreads();
   if (warp == 0) {
+    // the MMAs complete before TMEM is freed, also when a thread's wait gave up early
+    if (lane == 0) tc::mbar_wait_drain(&mma_bar, 0);
+    __syncwarp();
     tc::tc_fence_after();
     tc::tmem_dealloc(tbase, kCMaxN);
   }

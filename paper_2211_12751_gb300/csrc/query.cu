@@ -1252,7 +1252,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
           SAH_CUDA(cudaMemcpyAsync(timeout_h, ix->dev_timeout, sizeof(int), cudaMemcpyDeviceToHost, st));
         return SAH_OK;
       };
-      if (tm.on || !ix->use_graphs || !cx->graphs_allowed) {
+      if (tm.on || !ix->use_graphs || !cx->graphs_allowed || ix->inject_site) {
         SAH_TRY(enqueue());
       } else {
         // the same shapes and buffers as an earlier call: replay its captured graph
@@ -1269,7 +1269,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
       if (*timeout_h) {
         SAH_CUDA(cudaMemsetAsync(ix->dev_timeout, 0, sizeof(int), st));
         SAH_CUDA(cudaStreamSynchronize(st));
-        set_error("a bounded device-side wait of the tensor-core kMIPS decision ran out");
+        set_error("a bounded device-side wait of a tensor-core pass ran out");
         return SAH_ERR_DEVICE_TIMEOUT;
       }
       if (st_h[ST_BAD_Q]) {

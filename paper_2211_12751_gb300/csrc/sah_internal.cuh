@@ -80,6 +80,11 @@ struct CallCtx {
 void free_ctx(CallCtx* cx);
 size_t ctx_bytes(const CallCtx* cx);
 
+// Test hook sites of sah_index_inject_stall: the pipeline whose MMA thread stops after its
+// first accumulator tile in the next query call.
+constexpr int SAH_INJECT_USER_PASS = 1;   // the tensor-core user pass (A4/A8)
+constexpr int SAH_INJECT_VERIFY = 2;      // the tensor-core kMIPS decision (A5)
+
 struct Index {
   int device = 0;
   int64_t n = 0, m = 0, m_nz = 0;
@@ -132,6 +137,7 @@ struct Index {
   CUtensorMap tmap_U{};       // TMA map of Ub: box 64 x 128, 128-byte swizzle
   CUtensorMap tmap_Ulo{};     // the same for Ulo
   int* dev_timeout = nullptr; // set by a kernel whose bounded wait ran out
+  int inject_site = 0;        // test hook for the next query call (SAH_INJECT_*), 0: none
 
   // SA-ALSH over the items behind P' (Alg. 1): norm partitions S_j (descending M_j), their
   // centroids and radii, SRP codes of the SAT-transformed items (Eq. 6, Eq. 9) sorted

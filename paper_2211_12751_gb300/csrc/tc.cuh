@@ -81,6 +81,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* t
   return false;
 }
 
+// Teardown wait for this CTA's own asynchronous work (TMA loads, MMAs) before it frees
+// TMEM or exits: the same bounded poll, but it does not give up on the flags, because the
+// work it waits for was issued by this CTA and completes on its own.
+__device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (i > 32) __nanosleep(i > 4096 ? 256 : 32);
+  }
+  return false;
+}
+
 // ---------------------------------------------------------------- TMA
 // 2-D tiled load of box {inner, outer} at element coordinates (x = inner, y = outer)
 // into shared memory; completion is signalled on bar as transaction bytes.

@@ -11,8 +11,13 @@
 //    where ||p_t|| is the largest norm of the tile (items arrive in descending norm order)
 //    and the two terms bound the BF16 and the FP32 errors of those items' scores.
 //    Every item whose FP32 score is >= V_u is kept, so the kept set holds the 64 largest.
+//    Items arrive in descending norm order, so a tile whose largest norm ||p_t|| gives
+//    ||u|| ||p_t|| (1 + 2 (c_bf + gamma)) < V_u holds no item that can be kept, and neither
+//    does any later tile (the mu_j rule of Alg. 2): a user's scan ends at its cut, the first
+//    such tile, and a CTA streams the tiles up to the largest cut of its 128 users.
 // 3. topk_refine_kernel: the kept items re-scored in FP32 and ranked (64 slots per user
-//    spread over a warp); a user whose candidate list overflowed is scanned in full.
+//    spread over a warp); a user whose candidate list overflowed is scanned in full up to
+//    its cut (every item after it scores below V_u in FP32 too).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -37,6 +42,8 @@ struct TopkParams {
   float cb;                // c_bf + gamma
   int32_t* cand;           // [users in chunk][cap]
   int32_t* cand_cnt;       // [users in chunk]
+  int32_t* cut_out;        // [users in chunk]: the user's cut (tiles of kTN items)
+  float cut_factor;        // 1 + 2 (c_bf + gamma), rounded up, with room for the norms' rounding
   int32_t cap;
   int64_t u_first;         // first user of this launch
   int64_t u_count;         // users in this launch
@@ -55,13 +62,40 @@ topk_tc_kernel(const __grid_constant__ CUtensorMap tmapU, const __grid_constant_
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], tfull_bar[2], tempty_bar[2], a_bar, done_bar;
   __shared__ uint32_t tmem_base_sh;
+  __shared__ int tcut_sh;
   constexpr uint32_t kABytes = kTM * 128, kBBytes = kTN * 128;
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = base;
   uint8_t* sB = base + KB * kABytes;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t r0 = p.u_first + (int64_t)blockIdx.x * kTM;
-  const int T = (int)((p.n + kTN - 1) / kTN);
+  const int T_all = (int)((p.n + kTN - 1) / kTN);
+  // each user's cut: the first tile t with ||u|| ||p_t|| cut_factor < V_u (binary search
+  // over the descending tile norms); the CTA streams tiles [0, largest cut)
+  int my_cut = 0;
+  if (threadIdx.x == 0) tcut_sh = 0;
+  if (warp >= 2) {
+    const int64_t r = r0 + (warp & 3) * 32 + lane;
+    if ((r - p.u_first) < p.u_count && r < p.mz) {
+      const float V = p.vfloor[r];
+      const float nu = p.unorm[r];
+      int lo = 0, hi = T_all;   // tiles [0, lo) may hold a kept item; [hi, T_all) hold none
+      if (V == -INFINITY || !(nu > 0.f)) {
+        lo = T_all;
+      } else {
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          const float bound = __fmul_ru(__fmul_ru(nu, p.pnorm[(int64_t)mid * kTN]), p.cut_factor);
+          if (bound >= V) lo = mid + 1;
+          else hi = mid;
+        }
+      }
+      my_cut = lo;
+      p.cut_out[r - p.u_first] = lo;
+    }
+  }
+  __syncthreads();
+  if (warp >= 2) atomicMax(&tcut_sh, my_cut);
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       tc::mbar_init(&full_bar[s], 1);
@@ -83,7 +117,9 @@ topk_tc_kernel(const __grid_constant__ CUtensorMap tmapU, const __grid_constant_
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tbase = tmem_base_sh;
+  const int T = tcut_sh;
 
+  int tiles_issued = 0;   // the producer: item tiles loaded (teardown drain)
   if (warp == 0) {
     if (lane == 0) {   // TMA producer: the users once, then the item tiles
       tc::prefetch_tensormap(&tmapU);
@@ -96,6 +132,7 @@ topk_tc_kernel(const __grid_constant__ CUtensorMap tmapU, const __grid_constant_
         tc::mbar_arrive_expect_tx(&full_bar[s], KB * kBBytes);
         for (int kb = 0; kb < KB; ++kb)
           tc::tma_load_2d(sB + (s * KB + kb) * kBBytes, &tmapP, &full_bar[s], kb * 64, t * kTN);
+        tiles_issued = t + 1;
       }
     }
   } else if (warp == 1) {
@@ -130,7 +167,7 @@ topk_tc_kernel(const __grid_constant__ CUtensorMap tmapU, const __grid_constant_
     const float cbu = valid ? __fmul_ru(p.cb, p.unorm[r]) : 0.f;
     const int64_t slot0 = (r - p.u_first) * p.cap;
     int cnt = 0;
-    float pn_next = p.pnorm[0];
+    float pn_next = T > 0 ? p.pnorm[0] : 0.f;
     for (int t = 0; t < T; ++t) {
       const int a = t & 1;
       // keep threshold of this tile: V_u minus the BF16 and FP32 bounds for its largest norm
@@ -173,7 +210,16 @@ topk_tc_kernel(const __grid_constant__ CUtensorMap tmapU, const __grid_constant_
   tc::tc_fence_before();
   __syncthreads();
   if (warp == 0) {
-    if (lane == 0) tc::mbar_wait(&done_bar, 0, p.timeout, nullptr);
+    if (lane == 0) {
+      // every MMA and every TMA load of the CTA completes before TMEM is freed and the CTA
+      // exits, also when a bounded wait gave up early
+      tc::mbar_wait_drain(&done_bar, 0);
+      tc::mbar_wait_drain(&a_bar, 0);
+      for (int s = 0; s < STAGES && s < tiles_issued; ++s) {
+        const int issued = tiles_issued / STAGES + (s < tiles_issued % STAGES ? 1 : 0);
+        tc::mbar_wait_drain(&full_bar[s], (uint32_t)((issued - 1) & 1));
+      }
+    }
     __syncwarp();
     tc::tc_fence_after();
     tc::tmem_dealloc(tbase, kTTmem);
@@ -219,7 +265,8 @@ __device__ __forceinline__ float dot_f32(const float* __restrict__ u, const floa
 // overflowed), the 64 largest with their ids, written like the FP32 top-k pass writes them.
 __global__ void topk_refine_kernel(const float* __restrict__ Ut, const float* __restrict__ Ps, int dp, int64_t n,
                                    int64_t mz, int kmax, int64_t u_first, int64_t u_count,
-                                   const int32_t* __restrict__ cand, const int32_t* __restrict__ cand_cnt, int cap,
+                                   const int32_t* __restrict__ cand, const int32_t* __restrict__ cand_cnt,
+                                   const int32_t* __restrict__ cut, int cap,
                                    float* __restrict__ Lt, int32_t* __restrict__ ids_out, float* __restrict__ vlast_out,
                                    unsigned long long* __restrict__ overflow_rows) {
   const int lane = threadIdx.x & 31;
@@ -233,7 +280,7 @@ __global__ void topk_refine_kernel(const float* __restrict__ Ut, const float* __
   const int cnt = cand_cnt[w];
   const bool full = cnt > cap;
   if (full && lane == 0) atomicAdd(overflow_rows, 1ull);
-  const int64_t total = full ? n : cnt;
+  const int64_t total = full ? std::min<int64_t>(n, (int64_t)cut[w] * kTN) : cnt;
   for (int64_t base = 0; base < total; base += 32) {
     const int64_t i = base + lane;
     float s = -INFINITY;
@@ -284,10 +331,11 @@ sah_status topk_full_tc(Index* ix, float* vlast, int32_t* ids64, cudaStream_t st
   const int cap = 256;
   const int64_t chunk = std::min<int64_t>(mz, (int64_t)1 << 18);   // users per launch (candidate buffer 256 MiB)
   const int64_t chunk_rows = (chunk + kTM - 1) / kTM * kTM;
-  int32_t *cand = nullptr, *cnt = nullptr;
+  int32_t *cand = nullptr, *cnt = nullptr, *cut = nullptr;
   unsigned long long* ovf = nullptr;
   SAH_CUDA(cudaMallocAsync((void**)&cand, sizeof(int32_t) * (size_t)chunk_rows * cap, st));
   SAH_CUDA(cudaMallocAsync((void**)&cnt, sizeof(int32_t) * (size_t)chunk_rows, st));
+  SAH_CUDA(cudaMallocAsync((void**)&cut, sizeof(int32_t) * (size_t)chunk_rows, st));
   SAH_CUDA(cudaMallocAsync((void**)&ovf, sizeof(unsigned long long), st));
   SAH_CUDA(cudaMemsetAsync(ovf, 0, sizeof(unsigned long long), st));
   cudaEvent_t e0, e1;
@@ -298,7 +346,10 @@ sah_status topk_full_tc(Index* ix, float* vlast, int32_t* ids64, cudaStream_t st
     const int64_t uc = std::min(chunk, mz - u0);
     // c_bf + gamma, rounded up on the host (one ulp up covers the float rounding of the sum)
     const float cb = std::nextafter(cbf + ix->gamma, INFINITY);
-    TopkParams p{mz, n, vfloor, ix->unorm, ix->pnorm, cb, cand, cnt, cap, u0, uc, ix->dev_timeout};
+    // the cut's factor: 1 + 2 cb, rounded up, plus 2^-20 for the rounding of ||u|| and ||p||
+    const float cut_factor = std::nextafter(1.f + 2.f * cb + 0x1p-20f, INFINITY);
+    TopkParams p{mz, n, vfloor, ix->unorm, ix->pnorm, cb, cand, cnt, cut, cut_factor, cap, u0, uc,
+                 ix->dev_timeout};
     const unsigned grid = grid_for(uc, kTM);
     cudaEventRecord(e0, st);
     if (ix->dk == 64) {
@@ -313,7 +364,7 @@ sah_status topk_full_tc(Index* ix, float* vlast, int32_t* ids64, cudaStream_t st
     cudaEventRecord(e1, st);
     SAH_CUDA(cudaGetLastError());
     topk_refine_kernel<<<grid_for(uc * 32, 256), 256, 0, st>>>(ix->Ut, ix->Ps, ix->dp, n, mz, ix->kmax, u0, uc, cand,
-                                                               cnt, cap, ix->Lt, ids64, vlast, ovf);
+                                                               cnt, cut, cap, ix->Lt, ids64, vlast, ovf);
     SAH_CUDA(cudaGetLastError());
     SAH_CUDA(cudaEventSynchronize(e1));
     float ms = 0.f;
@@ -328,6 +379,7 @@ sah_status topk_full_tc(Index* ix, float* vlast, int32_t* ids64, cudaStream_t st
   cudaFreeAsync(vfloor, st);
   cudaFreeAsync(cand, st);
   cudaFreeAsync(cnt, st);
+  cudaFreeAsync(cut, st);
   cudaFreeAsync(ovf, st);
   ix->build_gemm_ms = ms_total;
   ix->build_overflow_rows = (int64_t)ovf_h;

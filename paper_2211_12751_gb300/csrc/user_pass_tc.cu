@@ -451,6 +451,7 @@ struct UpParams {
   unsigned long long* stats;
   int st_yes;
   int* timeout;
+  int inject_stall;            // test hook: the MMA thread stops after its first tile
 };
 
 // 32 consecutive FP32 columns of this thread's TMEM lane, waited for; the wait names the
@@ -522,6 +523,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
   __shared__ int32_t kseen[65], kslot[65], klist[64], nsl_sh;
   __shared__ int32_t tlist[kMaxTileList];           // this CTA's needed tiles, in order
   __shared__ int32_t ntl_sh, nopen_sh[kEpiWarps];
+  __shared__ uint32_t tma_issued[STAGES];            // TMA loads issued per stage (teardown drain)
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = base;                               // [STAGES][hi kb.. | lo kb..]
   uint8_t* sB = base + STAGES * S::kStage;          // [hi kb.. | lo kb..]
@@ -543,6 +545,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
         tc::mbar_init(&tempty_bar[a][h], 4);
       }
     tc::mbar_init(&done_bar, 1);
+    for (int s = 0; s < STAGES; ++s) tma_issued[s] = 0;
     tc::fence_mbar_init();
   }
   if (warp == 0) {
@@ -566,6 +569,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
   int use0 = 0, use1 = 0;   // epilogue: uses so far of its group's two TMEM slots
   int kt = 0;               // epilogue: tiles of its group so far
   int mkt[2] = {0, 0}, mu[2][2] = {{0, 0}, {0, 0}};   // the MMA thread's copies, per group
+  int mma_tiles = 0;        // the MMA thread: accumulator slots committed so far
   unsigned long long yes_cnt = 0;
   bool failed = false;
   for (int c0 = 0; c0 < ncol; c0 += NMAX) {
@@ -672,6 +676,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
               tc::tma_load_2d(dst + kb * S::kTile, &tmapUhi, &full_bar[s], kb * 64, t * kUM);
               tc::tma_load_2d(dst + (KB + kb) * S::kTile, &tmapUlo, &full_bar[s], kb * 64, t * kUM);
             }
+            ++tma_issued[s];
             nx[g] += 2;
             progressed = true;
           }
@@ -698,6 +703,8 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
         int hh[2] = {0, 0};
         uint32_t idle = 0;
         for (;;) {
+          // test hook: a partner that stops working; the epilogue's bounded wait runs out
+          if (p.inject_stall && mma_tiles >= 1) break;
           bool any_left = false, progressed = false;
 #pragma unroll
           for (int g = 0; g < 2; ++g) {
@@ -731,6 +738,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
             }
             tc::umma_commit(&tfull_bar[g][sl]);
             ++mu[g][sl];
+            ++mma_tiles;
             if (++hh[g] == H) {
               tc::umma_commit(&empty_bar[s]);
               hh[g] = 0;
@@ -997,7 +1005,13 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
   tc::tc_fence_before();
   __syncthreads();
   if (warp == 0) {
-    if (lane == 0) tc::mbar_wait(&done_bar, 0, p.timeout, nullptr);
+    if (lane == 0) {
+      // every MMA this CTA issued, and every TMA load (a pass that stopped early may leave
+      // loads that no MMA consumed), completes before TMEM is freed and the CTA exits
+      tc::mbar_wait_drain(&done_bar, 0);
+      for (int s = 0; s < STAGES; ++s)
+        if (tma_issued[s] > 0) tc::mbar_wait_drain(&full_bar[s], (tma_issued[s] - 1) & 1);
+    }
     __syncwarp();
     tc::tc_fence_after();
     tc::tmem_dealloc(tmem_base_sh, S::kTmemCols);
@@ -1116,6 +1130,7 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
   p.stats = stats;
   p.st_yes = st_yes;
   p.timeout = ix->dev_timeout;
+  p.inject_stall = ix->inject_site == SAH_INJECT_USER_PASS ? 1 : 0;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
   if (ix->dk == 64) {

@@ -234,6 +234,7 @@ struct TcParams {
   const int32_t* list;
   int t_begin, t_end;
   uint8_t* flags;
+  int inject_stall;   // test hook: the MMA thread stops after its first tile
 };
 
 // Persistent: a CTA takes row blocks blockIdx.x, blockIdx.x + gridDim.x, ... (128 survivor
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
 verify_tc_kernel(const __grid_constant__ CUtensorMap tmapPhi, const __grid_constant__ CUtensorMap tmapPlo,
                  TcParams prm) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], tfull_bar[2], tempty_bar[2], a_bar;
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], tfull_bar[2], tempty_bar[2], a_bar, done_bar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int stop_flag, p_issued, p_done, quit_sh;
   __shared__ volatile uint32_t c_sh;
@@ -276,6 +277,7 @@ verify_tc_kernel(const __grid_constant__ CUtensorMap tmapPhi, const __grid_const
       tc::mbar_init(&tempty_bar[a], 4);
     }
     tc::mbar_init(&a_bar, 128);                      // every epilogue thread, once its row is in place
+    tc::mbar_init(&done_bar, 1);                     // teardown: every MMA of the CTA has completed
     stop_flag = 0;
     p_issued = 0;
     p_done = 0;
@@ -337,6 +339,8 @@ verify_tc_kernel(const __grid_constant__ CUtensorMap tmapPhi, const __grid_const
         const uint32_t b_addr = tc::smem_addr(sB);
         if (!tc::mbar_wait(&a_bar, it & 1, prm.timeout, nullptr)) stop_flag = 1;
         for (int i = 0;; ++i) {                       // the block's i-th tile
+          // test hook: a partner that stops working; the epilogue's bounded wait runs out
+          if (prm.inject_stall && C >= 1) break;
           const uint32_t s = M % STAGES;
           bool got = false, finished = false;
           for (uint32_t w = 0; w < tc::kSpinLimit; ++w) {
@@ -556,7 +560,20 @@ verify_tc_kernel(const __grid_constant__ CUtensorMap tmapPhi, const __grid_const
     tc::tc_fence_after();
     if (quit_sh) break;
   }
+  // teardown: every MMA this CTA issued, and every TMA load (a block that stopped early may
+  // leave loads that no MMA consumed), completes before TMEM is freed and the CTA exits
+  if (warp == 1 && lane == 0) tc::umma_commit(&done_bar);
+  tc::tc_fence_before();
+  __syncthreads();
   if (warp == 0) {
+    if (lane == 0) {
+      tc::mbar_wait_drain(&done_bar, 0);
+      for (uint32_t s = 0; s < STAGES && s < P; ++s) {
+        const uint32_t issued = P / STAGES + (s < P % STAGES ? 1u : 0u);   // loads on stage s
+        tc::mbar_wait_drain(&full_bar[s], (issued - 1) & 1);
+      }
+    }
+    __syncwarp();
     tc::tc_fence_after();
     tc::tmem_dealloc(tbase, kTmemCols);
   }
@@ -961,6 +978,7 @@ sah_status run_verify_tc(Index* ix, CallCtx* cx, const Survivor* surv, const uns
   prm.items_stat = stats + stat_items;
   prm.timeout = ix->dev_timeout;
   prm.flags = flags;
+  prm.inject_stall = ix->inject_site == SAH_INJECT_VERIFY ? 1 : 0;
   // Two phases of the scan over item tiles, [0,8) and [8, end): rows still open after the
   // first go on, compacted, to the second, so that its (longer) CTAs hold only rows that
   // still need the items.  Every phase boundary costs a fill and drain of the CTAs and
