@@ -703,10 +703,12 @@ sah_status build_index_device(Index* ix, const float* U_dev, const float* P_dev,
         SAH_CUDA(cudaMallocAsync((void**)&ids64, sizeof(int32_t) * 64 * (size_t)mz, st));
         SAH_CUDA(cudaMallocAsync((void**)&vlast, sizeof(float) * (size_t)mz, st));
       }
-      if (ix->l_exact && ix->dk > 0 && ix->n > 256) {
-        // tensor cores: a floor from the first 256 items, then every item through tcgen05
-        topk_lower_bounds_kernel<<<grid, kTopkWarps * 32, smem, st>>>(ix->Ut, ix->Ps, dp, mz, 256, kmax, tile_items,
-                                                                      stride4, ix->Lt, ids64, vlast);
+      // tensor cores: a floor from the largest-norm items, then the items up to each user's
+      // cut through tcgen05 (a higher floor keeps fewer candidates and ends the scans sooner)
+      const int kFloorItems = (int)std::min<int64_t>(2048, std::max<int64_t>(256, ix->n / 8));
+      if (ix->l_exact && ix->dk > 0 && ix->n > kFloorItems) {
+        topk_lower_bounds_kernel<<<grid, kTopkWarps * 32, smem, st>>>(ix->Ut, ix->Ps, dp, mz, kFloorItems, kmax,
+                                                                      tile_items, stride4, ix->Lt, ids64, vlast);
         SAH_CUDA(cudaGetLastError());
         SAH_TRY(topk_full_tc(ix, vlast, ids64, st, nullptr));
       } else {
