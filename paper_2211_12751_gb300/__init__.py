@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libsah.so")
 SAH_OK, SAH_ERR_ARG, SAH_ERR_OOM, SAH_ERR_CUDA = 0, 1, 2, 3
 SAH_ERR_BUFFER_TOO_SMALL, SAH_ERR_DEVICE_TIMEOUT, SAH_ERR_BUSY, SAH_ERR_UNSUPPORTED = 4, 5, 6, 7
 EXACT, SAALSH = 0, 1
+INJECT_USER_PASS, INJECT_VERIFY = 1, 2
 FP32, BF16, FP8 = 0, 1, 2
 
 _lib = None
@@ -102,6 +103,8 @@ def load(path: Optional[str] = None):
     lib.sah_index_blocks.restype = I32
     lib.sah_index_set_timing.argtypes = [P, I32]
     lib.sah_index_set_timing.restype = I32
+    lib.sah_index_inject_stall.argtypes = [P, I32]
+    lib.sah_index_inject_stall.restype = I32
     lib.sah_rkmips_bruteforce_noalloc.argtypes = [P, I64, P, I64, I32, P, I32, P, I64, P, P]
     lib.sah_rkmips_bruteforce_noalloc.restype = I32
     lib.sah_server_start.argtypes = [P, I32, I32, I32, I64, ctypes.POINTER(P)]
@@ -167,10 +170,38 @@ NOALLOC_MAX_USERS = 1 << 22
 def rkmips_bruteforce_noalloc(U, P, q, k: int, out_ids, out_count, m: Optional[int] = None, stream=None):
     """Exact RkMIPS for one query with no allocation anywhere (device tensors in and out):
     U (m x d), P (n x d), q (d) float32; out_ids int32 (capacity = numel); out_count int64
-    (one element).  Queued on the stream; read out_count after synchronising."""
+    (one element).  Queued on the stream; read out_count after synchronising.  The tensors
+    are only checked here (dtype, layout, device, shapes), never copied or converted: a
+    mismatch raises SahError(SAH_ERR_ARG).  ``m`` overrides the user count (at most
+    U.shape[0]), e.g. to probe the size limit."""
+    import torch
+
+    def bad(msg):
+        raise SahError(SAH_ERR_ARG, "rkmips_bruteforce_noalloc: " + msg)
+
+    for name, t, dt in (("U", U, torch.float32), ("P", P, torch.float32), ("q", q, torch.float32),
+                        ("out_ids", out_ids, torch.int32), ("out_count", out_count, torch.int64)):
+        if not _is_torch(t) or not t.is_cuda:
+            bad(f"{name} must be a CUDA tensor")
+        if t.dtype != dt:
+            bad(f"{name} must be {dt}, not {t.dtype}")
+        if not t.is_contiguous():
+            bad(f"{name} must be contiguous")
+    if U.dim() != 2 or P.dim() != 2 or P.shape[1] != U.shape[1]:
+        bad("U and P must be 2-D with the same number of columns")
+    d = U.shape[1]
+    if q.numel() != d:
+        bad("q must hold d values")
+    if out_count.numel() < 1:
+        bad("out_count must hold one value")
+    if len({U.device, P.device, q.device, out_ids.device, out_count.device}) != 1:
+        bad("all tensors must be on one device")
     lib = load()
-    m = U.shape[0] if m is None else m
-    _check(lib.sah_rkmips_bruteforce_noalloc(U.data_ptr(), m, P.data_ptr(), P.shape[0], U.shape[1],
+    if m is None:
+        m = U.shape[0]
+    elif m > U.shape[0] and m <= NOALLOC_MAX_USERS:
+        bad("m exceeds the rows of U")
+    _check(lib.sah_rkmips_bruteforce_noalloc(U.data_ptr(), m, P.data_ptr(), P.shape[0], d,
                                              q.data_ptr(), int(k), out_ids.data_ptr(), out_ids.numel(),
                                              out_count.data_ptr(), _stream_handle(stream)))
 
@@ -282,6 +313,11 @@ class Index:
         _check(lib.sah_index_blocks(self._h, ctypes.byref(mnz), ctypes.byref(nb), ids.ctypes.data,
                                     starts.ctypes.data, ct.ctypes.data, cw.ctypes.data))
         return ids, starts, ct, cw
+
+    def inject_stall(self, site: int):
+        """sah_index_inject_stall: the next query call's MMA thread at `site` (1: user pass,
+        2: kMIPS decision) stops after one tile, so the call returns SAH_ERR_DEVICE_TIMEOUT."""
+        _check(load().sah_index_inject_stall(self._h, int(site)))
 
     def set_timing(self, enable: bool = True):
         _check(load().sah_index_set_timing(self._h, 1 if enable else 0))
