@@ -848,7 +848,7 @@ __global__ void answer_emit_kernel(uint32_t* __restrict__ bitmap, int64_t stride
 namespace {
 
 constexpr int kAnswerThreads = 512;   // summary words counted and scanned per step of a query's CTA
-constexpr int kCtlCounters = 5;   // survivor counts (3), answer-list length, scan ticket
+constexpr int kCtlCounters = 6;   // survivor counts (4), answer-list length, scan ticket
 
 struct WsLayout {
   size_t qd, qb, qn, qh, kk, pairs, pcount, kmask, tneed, tneed_end, coltab, survcnt, alist_n, ticket, bitmap, chunk,
@@ -868,7 +868,9 @@ WsLayout layout_for(const Index* ix, int qb) {
   L.qn = take(sizeof(float) * qb);
   L.qh = take(sizeof(uint64_t) * qb);
   L.kk = take(sizeof(int32_t) * qb);
-  L.pairs = take(sizeof(PairEntry) * (size_t)std::max(ix->nb, 1) * qb);
+  // the per-leaf pair lists of the CUDA-core user pass (the tensor-core pass keeps a bitmask)
+  const bool tc_pass = ix->nb > 0 && ix->dk > 0 && ix->prm.tc_user_pass && ix->m_nz > 0;
+  L.pairs = take(tc_pass ? 0 : sizeof(PairEntry) * (size_t)std::max(ix->nb, 1) * qb);
   L.pcount = take(sizeof(int32_t) * std::max(ix->nb, 1));
   L.kmask = take(sizeof(uint32_t) * (size_t)std::max(ix->nb, 1) * ((qb + 31) / 32));
   L.coltab = take(user_pass_tc_scratch_bytes(qb, ix->dp));
@@ -880,7 +882,7 @@ WsLayout layout_for(const Index* ix, int qb) {
   const size_t ntiles = (size_t)std::max<int64_t>((ix->m_nz + 127) / 128, 1);
   L.stats = take(sizeof(unsigned long long) * (ST_COUNT + kCtlCounters) + sizeof(int64_t) * (size_t)(qb + 1) + ntiles);
   L.survcnt = L.stats + sizeof(unsigned long long) * ST_COUNT;
-  L.alist_n = L.survcnt + 3 * sizeof(unsigned long long);
+  L.alist_n = L.survcnt + 4 * sizeof(unsigned long long);
   L.ticket = L.alist_n + sizeof(unsigned long long);
   L.offsets = L.ticket + sizeof(unsigned long long);
   L.tneed = L.offsets + sizeof(int64_t) * (size_t)(qb + 1);
@@ -910,7 +912,9 @@ sah_status ensure_ws(CallCtx* cx, size_t bytes, cudaStream_t st) { return ensure
 // three lists of cap entries: exact-mode survivors, SA-ALSH survivors, and the pairs the
 // tensor-core user pass leaves to the FP32 re-score
 sah_status ensure_surv(CallCtx* cx, int64_t cap, cudaStream_t st) {
-  return ensure_buf(&cx->surv, 3 * sizeof(Survivor) * (size_t)std::max<int64_t>(cap, 1), st);
+  // exact survivors, SA-ALSH survivors, open pairs of the tensor-core user pass (cap entries
+  // each), then its candidate blocks (cap blocks of 144 bytes)
+  return ensure_buf(&cx->surv, (3 * sizeof(Survivor) + 144) * (size_t)std::max<int64_t>(cap, 1), st);
 }
 
 // Runs a sub-batch's launch sequence (enqueue) for the given key of shapes and buffers: the
@@ -1051,7 +1055,8 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
   const int64_t words = answer_stride(ix->m);
   const int64_t nsw = answer_words(words) / 32;   // summary words per query
   // sub-batch size: bounded pair list and bitmap (about 1 GiB together)
-  const size_t per_q = sizeof(PairEntry) * (size_t)std::max(ix->nb, 1) + sizeof(uint32_t) * words +
+  const bool tc_pass_q = ix->nb > 0 && ix->dk > 0 && ix->prm.tc_user_pass && ix->m_nz > 0;
+  const size_t per_q = (tc_pass_q ? 0 : sizeof(PairEntry) * (size_t)std::max(ix->nb, 1)) + sizeof(uint32_t) * words +
                        sizeof(int32_t) * (nsw + 1) + sizeof(float) * ix->dp + 16;
   int qb = (int)std::max<size_t>(1, std::min<size_t>((size_t)nq, (size_t(1) << 30) / per_q));
   qb = std::min(qb, 4096);
@@ -1059,7 +1064,10 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
   *wrote_out = false;
   // survivor-list capacity used by this call: twice the last call's count (at least 64k),
   // grown and re-run if a sub-batch exceeds it
-  int64_t surv_cap = std::max<int64_t>(cx->surv_hint, 1 << 16);
+  // capacities are multiples of 16 entries: the candidate blocks after the three lists are
+  // written as 16-byte words
+  int64_t surv_cap = (std::max<int64_t>(cx->surv_hint, 1 << 16) + 15) & ~int64_t(15);
+  int64_t surv_call_max = 0;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
 
@@ -1161,7 +1169,8 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
             up_launches = 0;
             SAH_TRY(run_user_pass_tc(ix, Qd, (uint16_t*)(w + L.qb), w + L.coltab, qn, kk, nqb, kmask,
                                      mask_words, (uint8_t*)(w + L.tneed), bitmap, words, surv + 2 * surv_cap,
-                                     survcnt + 2, surv, survcnt, surv_cap, stats, ST_YES_EARLY, ST_FP64, st,
+                                     survcnt + 2, surv + 3 * surv_cap, survcnt + 3, surv, survcnt, surv_cap, stats,
+                                     ST_YES_EARLY, ST_FP64, st,
                                      &up_launches, tm.slot(6)));
           } else if (reg_variant) {
             const size_t smem = (size_t)16 * kQChunk * dp4 + sizeof(PairInfo) * kQChunk + sizeof(float) * 64 * threads;
@@ -1280,14 +1289,14 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
         set_error("k must be >= 1 and the mode SAH_EXACT or SAH_SAALSH");
         return SAH_ERR_ARG;
       }
-      const int64_t nsmax = (int64_t)std::max(ns2[0], std::max(ns2[1], ns2[2]));
+      const int64_t nsmax = (int64_t)std::max(std::max(ns2[0], ns2[1]), std::max(ns2[2], ns2[3]));
       if (nsmax > surv_cap) {
         // a survivor list overflowed: grow it and run this sub-batch again
         if (attempt > 4) {
           set_error("survivor list kept overflowing");
           return SAH_ERR_OOM;
         }
-        surv_cap = nsmax * 5 / 4 + 1024;
+        surv_cap = (nsmax * 5 / 4 + 1024 + 15) & ~int64_t(15);
         continue;
       }
       const int64_t new_total = ob[nqb];
@@ -1327,7 +1336,9 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
       cx->bm_clean_bytes = bm_bytes;
       agg.survivors += (int64_t)(ns2[0] + ns2[1]);
       agg.pairs_rescored += (int64_t)ns2[2];
-      cx->surv_hint = std::max<int64_t>(1 << 16, 2 * nsmax);
+      // the next call starts from the largest list of this call's sub-batches (twice it)
+      surv_call_max = std::max(surv_call_max, nsmax);
+      cx->surv_hint = std::max<int64_t>(1 << 16, 2 * surv_call_max);
       agg.block_pairs_total += (int64_t)ix->nb * nqb;
       agg.block_pairs_kept += (int64_t)st_h[ST_PAIRS_KEPT];
       agg.users_scored += (int64_t)st_h[ST_USERS_SCORED];

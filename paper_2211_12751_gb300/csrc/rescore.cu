@@ -23,7 +23,9 @@ __global__ void pair_rescore_kernel(const Survivor* __restrict__ pairs, const un
                                     const double* __restrict__ T64, uint32_t* __restrict__ bitmap, int64_t words,
                                     Survivor* __restrict__ surv, unsigned long long* __restrict__ surv_count,
                                     int64_t surv_cap, unsigned long long* __restrict__ stats, int st_yes,
-                                    int st_fp64, int nq, const int* __restrict__ timeout) {
+                                    int st_fp64, int nq, const int* __restrict__ timeout,
+                                    const uint32_t* __restrict__ kept_mask, int mask_words,
+                                    const int32_t* __restrict__ ublock) {
   // after a timed-out wait of the pass the list may hold unwritten entries: nothing is read
   __shared__ int stop;
   if (threadIdx.x == 0) stop = *(volatile const int*)timeout;
@@ -44,7 +46,12 @@ __global__ void pair_rescore_kernel(const Survivor* __restrict__ pairs, const un
       const Survivor P = pairs[i];
       r = P.upos;
       j = P.j & 0x3fffffff;
-      if (r >= 0 && r < mz && j < nq) {
+      // with kept_mask: a pair whose leaf the node-level bound (Lemma 2) pruned for its row
+      // cannot answer "yes"; it is dropped before any arithmetic
+      const bool kept = kept_mask == nullptr ||
+                        (r >= 0 && r < mz && j < nq &&
+                         ((__ldg(&kept_mask[(int64_t)__ldg(&ublock[r]) * mask_words + (j >> 5)]) >> (j & 31)) & 1u));
+      if (kept && r >= 0 && r < mz && j < nq) {
         sa_row = (P.j >> 30) & 1;
         const int k = kk[j];
         const float4* u4 = reinterpret_cast<const float4*>(Ut + (int64_t)r * dp);
@@ -128,7 +135,8 @@ __global__ void pair_rescore_kernel(const Survivor* __restrict__ pairs, const un
 sah_status launch_pair_rescore(Index* ix, const Survivor* pairs, const unsigned long long* count, int64_t cap,
                                const float* Qd, const float* qn, const int32_t* kk, uint32_t* bitmap, int64_t words,
                                Survivor* surv, unsigned long long* surv_count, unsigned long long* stats, int st_yes,
-                               int st_fp64, int nq, int sms, cudaStream_t st) {
+                               int st_fp64, int nq, int sms, cudaStream_t st, const uint32_t* kept_mask,
+                               int mask_words) {
   // rows in registers pay off where most pairs also take the double-precision dot (exact
   // thresholds); otherwise the narrower kernel keeps more warps in flight
   auto fn = (ix->T64 != nullptr && ix->dp <= 64) ? pair_rescore_kernel<16> : pair_rescore_kernel<0>;
@@ -139,7 +147,8 @@ sah_status launch_pair_rescore(Index* ix, const Survivor* pairs, const unsigned 
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
   fn<<<sms * per_sm, 256, 0, st>>>(pairs, count, cap, ix->Ut, ix->unorm, ix->uid, ix->Lt, ix->Eu, ix->pnorm, ix->n,
                               ix->m_nz, ix->kmax, ix->l_exact ? 1 : 0, ix->d, ix->dp, Qd, qn, kk, ix->gamma, ix->T64,
-                              bitmap, words, surv, surv_count, cap, stats, st_yes, st_fp64, nq, ix->dev_timeout);
+                              bitmap, words, surv, surv_count, cap, stats, st_yes, st_fp64, nq, ix->dev_timeout,
+                              kept_mask, mask_words, ix->ublock);
   SAH_CUDA(cudaGetLastError());
   return SAH_OK;
 }

@@ -303,6 +303,7 @@ sah_status block_filter_tc(Index* ix, void* scratch, int nq, uint32_t* kept_mask
 sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* scratch, const float* qn,
                             const int32_t* kk, int nq, const uint32_t* kept_mask, int mask_words, uint8_t* tile_need,
                             uint32_t* bitmap, int64_t words, Survivor* resc, unsigned long long* resc_count,
+                            Survivor* cand, unsigned long long* cand_count,
                             Survivor* surv, unsigned long long* surv_count, int64_t surv_cap,
                             unsigned long long* stats, int st_yes, int st_fp64, cudaStream_t st, int* launches,
                             const cudaEvent_t* ev = nullptr);   // ev: begin / end of the GEMM kernel
@@ -329,10 +330,13 @@ sah_status codes_f8(Index* ix, const float* X, int64_t first, int64_t n, const i
 // rescore.cu
 // FP32 (and, with exact thresholds, double-precision) re-score of the pairs listed in
 // pairs[0, *count) (at most cap): "yes" pairs set their answer bit, open ones go to surv.
+// With kept_mask ([leaf][mask_words] bits of the rows the node-level bound kept), pairs of
+// a pruned (leaf, row) are dropped first.
 sah_status launch_pair_rescore(Index* ix, const Survivor* pairs, const unsigned long long* count, int64_t cap,
                                const float* Qd, const float* qn, const int32_t* kk, uint32_t* bitmap, int64_t words,
                                Survivor* surv, unsigned long long* surv_count, unsigned long long* stats, int st_yes,
-                               int st_fp64, int nq, int sms, cudaStream_t st);
+                               int st_fp64, int nq, int sms, cudaStream_t st, const uint32_t* kept_mask = nullptr,
+                               int mask_words = 0);
 sah_status run_verify_tc(Index* ix, CallCtx* cx, const Survivor* surv, const unsigned long long* surv_count_dev,
                          int64_t surv_cap, const float* Qd, const float* qn, const int32_t* kk, uint32_t* bitmap,
                          int64_t words, unsigned long long* stats, int stat_fp64, int stat_items,

@@ -49,6 +49,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <cstdlib>
 #include <cmath>
 
 #include "sah_internal.cuh"
@@ -58,11 +59,11 @@ namespace sah {
 namespace {
 
 constexpr int kUM = 128;             // users per tile (UMMA M)
-constexpr int kUThreads = 320;       // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr int kUThreads = 352;       // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue, warp 10 bounds loader
+constexpr int kLoaderWarp = 10;
+constexpr int kRingMax = 8;          // tiles of user bounds staged ahead by the loader warp (at most)
 constexpr int kEpiWarps = 8;
 constexpr int kMaxTileList = 1024;   // needed tiles per CTA and launch (the host splits longer ranges)
-constexpr int kRowsSmem = 512;       // rows of a chunk kept in shared memory (more: read from global)
-constexpr int kOpenBuf = 64;         // open pairs an epilogue warp buffers per tile
 constexpr int kMaxRows = 4096;       // rows of a sub-batch the column table takes
 
 // The columns of a sub-batch and their rows.
@@ -101,6 +102,16 @@ ColTable col_table_at(void* base, int nq) {
   T.qt = (float4*)p;
   return T;
 }
+
+// A candidate block of the user pass: one user's 32 tensor scores of a 32-column group
+// whose fast test it passed (144 bytes).
+struct __align__(16) CandBlock {
+  int32_t upos;       // user position (leaf order)
+  int32_t col0;       // sub-batch column of s[0]
+  int32_t pad[2];
+  float s[32];        // tensor scores of columns col0 .. col0 + 31
+};
+static_assert(sizeof(CandBlock) == 144, "candidate blocks are 144 bytes");
 
 // Exclusive prefix of v over the block (blockDim.x a multiple of 32, at most 1024); the
 // block's total goes to *total.  Every thread must call it.
@@ -442,16 +453,19 @@ struct UpParams {
   const int32_t* ublock;
   const uint32_t* kept_mask;   // [nb][mask_words]
   const uint8_t* tile_need;    // [ntiles]
-  float ctc, gamma;
+  float cband, gamma;          // score error factor of the MMA (times ||u|| ||q||); FP32 dot factor
   uint32_t* bitmap;
   int64_t words;
   Survivor* resc;
   unsigned long long* resc_count;
-  int64_t resc_cap;
+  int64_t resc_cap;            // also the capacity of the candidate list
+  CandBlock* cand;             // candidate blocks (capacity resc_cap)
+  unsigned long long* cand_count;
   unsigned long long* stats;
   int st_yes;
   int* timeout;
   int inject_stall;            // test hook: the MMA thread stops after its first tile
+  int nring;                   // entries of the bound ring (3..kRingMax)
 };
 
 // 32 consecutive FP32 columns of this thread's TMEM lane, waited for; the wait names the
@@ -473,6 +487,30 @@ __device__ __forceinline__ void tmem_ld32_wait(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 64 consecutive FP32 columns of this thread's TMEM lane, waited for
+__device__ __forceinline__ void tmem_ld64_wait(uint32_t taddr, float (&v)[64]) {
+  uint32_t r[64];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+      "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+      "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+        "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+        "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+        "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+        "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // one FP32 column of this thread's TMEM lane, waited for
 __device__ __forceinline__ float tmem_ld1_wait(uint32_t taddr) {
   uint32_t r;
@@ -485,68 +523,120 @@ __device__ __forceinline__ float tmem_ld1_wait(uint32_t taddr) {
   return __uint_as_float(r);
 }
 
-template <int KB, int STAGES, int NMAX>
+// Shared memory of the user pass.  A stage holds one 128-user tile (its hi K-blocks and,
+// with PRODS = 3, its lo K-blocks); B holds the column set (up to SETN query vectors, hi
+// and, with PRODS = 3, lo), resident while the set's tiles stream past.
+template <int KB, int STAGES, int SETN, int PRODS>
 struct UpSmem {
-  static constexpr uint32_t kTile = kUM * 128;             // one K-block of 128 user rows
-  static constexpr uint32_t kStage = 2 * KB * kTile;       // hi and lo
-  static constexpr uint32_t kBPart = NMAX * 128;           // one K-block of the columns
-  static constexpr size_t kOperands = (size_t)STAGES * kStage + 2 * KB * (size_t)kBPart;
-  // + per epilogue warp: (slots + 2) x 32 lower bounds, kOpenBuf open pairs, a 32-entry table
-  static constexpr size_t bytes(int slots) {
-    return 1024 + kOperands + (size_t)kEpiWarps * (32 * 4 * ((size_t)slots + 2) + 8 * kOpenBuf + 4 * 32);
+  static constexpr int kParts = PRODS == 3 ? 2 : 1;            // hi, or hi and lo
+  static constexpr uint32_t kTile = kUM * 128;                  // one K-block of 128 user rows
+  static constexpr uint32_t kStage = kParts * KB * kTile;
+  static constexpr uint32_t kBPart = SETN * 128;                // one K-block of the set's columns
+  static constexpr size_t kOperands = (size_t)STAGES * kStage + (size_t)kParts * KB * kBPart;
+  static constexpr int kW = SETN < 256 ? SETN : 256;            // columns per slice: one MMA, one TMEM slot
+  static constexpr uint32_t kTmemCols = 2 * kW;                 // two slots, one per epilogue group
+  // + the bound ring: nring entries of (slots + 5) rows of 128 words (the slots' lower
+  // bounds, a -inf row, a +inf row, ||u||, E_u, the caller's user id)
+  static constexpr size_t bytes(int slots, int nring) {
+    return 1024 + kOperands + (size_t)nring * ((size_t)slots + 5) * 512;
   }
-  // TMEM: two slots of kSW columns per epilogue group.  A chunk of up to kSW columns puts
-  // consecutive tiles of a group into alternate slots (the next tile's MMA runs while the
-  // current one is read); a wider chunk uses both slots of a tile as its halves.
-  static constexpr int kSW = NMAX < 128 ? NMAX : 128;
-  static constexpr uint32_t kTmemCols = 4 * kSW;
 };
 
-template <int KB, int STAGES, int NMAX>
+// Asynchronous global -> shared copies (no register involved); bytes past src_bytes are
+// zero-filled, and src_bytes = 0 reads nothing.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(tc::smem_addr(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::smem_addr(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+// One arrival on the barrier once every earlier cp.async of this thread has completed
+// (the barrier's expected count includes it).
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(tc::smem_addr(bar)) : "memory");
+}
+
+// Maximum of v[OFF .. OFF + 31] with three-input max instructions.
+template <int OFF, int NV>
+__device__ __forceinline__ float max32_at(const float (&v)[NV]) {
+  float g[11];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(v[OFF + 3 * i]), "f"(v[OFF + 3 * i + 1]), "f"(v[OFF + 3 * i + 2]));
+    g[i] = r;
+  }
+  g[10] = fmaxf(v[OFF + 30], v[OFF + 31]);
+  float a, b, c, r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(a) : "f"(g[0]), "f"(g[1]), "f"(g[2]));
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(b) : "f"(g[3]), "f"(g[4]), "f"(g[5]));
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(c) : "f"(g[6]), "f"(g[7]), "f"(g[8]));
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return fmaxf(r, fmaxf(g[9], g[10]));
+}
+
+// INL: candidates are resolved inside the epilogue (where they are dense: the paper's |P'|,
+// whose lower bounds are loose) or written as candidate blocks for cand_resolve_kernel
+// (where they are sparse: exact thresholds).
+template <int KB, int STAGES, int SETN, int PRODS, bool INL>
 __global__ void __launch_bounds__(kUThreads, 1)
 user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_constant__ CUtensorMap tmapUlo,
                     UpParams p) {
-  using S = UpSmem<KB, STAGES, NMAX>;
-  // the two epilogue groups run independent pipelines: group g owns the stages s = g mod 2
-  static_assert(STAGES % 2 == 0, "stages are split between the two epilogue groups");
+  using S = UpSmem<KB, STAGES, SETN, PRODS>;
+  constexpr int NROWS = INL ? (KB == 1 ? 512 : 128) : 1;   // rows of a set kept in shared memory
+  constexpr int W = S::kW;
+  constexpr int NG = SETN / 32;                     // 32-column groups of a set
   extern __shared__ uint8_t smem_raw[];
-  // accumulator barriers per (group, half of the columns): the MMA of a group's next tile
-  // starts on a half as soon as the epilogue has read that half
-  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], tfull_bar[2][2], tempty_bar[2][2], done_bar;
+  // per slot: the MMA's commit (tfull) and the four epilogue warps of its group (tempty)
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], tfull_bar[2], tempty_bar[2], done_bar;
+  // bound ring: the loader fills an entry (ring_full), the eight epilogue warps release it
+  __shared__ __align__(8) uint64_t ring_full[kRingMax], ring_empty[kRingMax];
   __shared__ uint32_t tmem_base_sh;
-  __shared__ __align__(16) float2 cq[NMAX];         // per column: ||q||, bound-table row of its largest k
-  __shared__ int2 crows[NMAX];                      // per column: first row in T.rows, row count
-  // the chunk's rows: {j | sa << 30, bound-table row offset (-1: past the cap, -2: no
-  // bound), bits of ||p_k||, k}
-  __shared__ int4 srows[kRowsSmem];
-  __shared__ int32_t wrow[NMAX / 32];               // per 32 columns: their common bound row, or -1
+  __shared__ __align__(16) float2 cq[SETN];         // per column: ||q||, bound-table row of its largest k
+  __shared__ int2 crows[INL ? SETN : 1];            // per column: first row (set-relative), row count
+  // the set's rows: {j | sa << 30, bound-table row offset (-1: past the cap, -2: no bound),
+  // bits of ||p_k||, k}
+  __shared__ int4 srows[NROWS];
+  __shared__ float2 gq[NG];                         // per 32 columns: largest ||q||, row of the smallest bound
   __shared__ int32_t kseen[65], kslot[65], klist[64], nsl_sh;
   __shared__ int32_t tlist[kMaxTileList];           // this CTA's needed tiles, in order
-  __shared__ int32_t ntl_sh, nopen_sh[kEpiWarps];
+  __shared__ int32_t ntl_sh;
   __shared__ uint32_t tma_issued[STAGES];            // TMA loads issued per stage (teardown drain)
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = base;                               // [STAGES][hi kb.. | lo kb..]
-  uint8_t* sB = base + STAGES * S::kStage;          // [hi kb.. | lo kb..]
-  // per epilogue warp: [slot_cap + 2][32] lower bounds (row slot_cap -inf, row slot_cap + 1
-  // +inf) and kOpenBuf open pairs
-  float* Lsm = reinterpret_cast<float*>(base + S::kOperands);
-  int2* Osm = reinterpret_cast<int2*>(Lsm + kEpiWarps * 32 * (p.slot_cap + 2));
-  int32_t* Ism = reinterpret_cast<int32_t*>(Osm + kEpiWarps * kOpenBuf);   // per warp: 32 entries
+  uint8_t* sB = base + STAGES * S::kStage;          // [hi kb.. | lo kb..], SETN rows each
+  // ring entry e, for the tile's 128 users: row sl (< slot_cap) the lower bound L of slot
+  // sl, row slot_cap -inf, row slot_cap + 1 +inf, row slot_cap + 2 ||u||, row slot_cap + 3
+  // E_u, row slot_cap + 4 the caller's user id (users past m_nz read as 0); bound "offsets"
+  // below are row * 128
+  const int ring_rows = p.slot_cap + 5;
+  const int nring = p.nring;
+  float* ring = reinterpret_cast<float*>(base + S::kOperands);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) {
       tc::mbar_init(&full_bar[s], 1);
       tc::mbar_init(&empty_bar[s], 1);
+      tma_issued[s] = 0;
     }
-    for (int a = 0; a < 2; ++a)
-      for (int h = 0; h < 2; ++h) {
-        tc::mbar_init(&tfull_bar[a][h], 1);
-        tc::mbar_init(&tempty_bar[a][h], 4);
-      }
+    for (int a = 0; a < 2; ++a) {
+      tc::mbar_init(&tfull_bar[a], 1);
+      tc::mbar_init(&tempty_bar[a], 4);
+    }
     tc::mbar_init(&done_bar, 1);
-    for (int s = 0; s < STAGES; ++s) tma_issued[s] = 0;
+    for (int e = 0; e < nring; ++e) {
+      tc::mbar_init(&ring_full[e], 32);   // the loader's lanes, each once its copies land
+      tc::mbar_init(&ring_empty[e], kEpiWarps);
+    }
     tc::fence_mbar_init();
+  }
+  for (int i = tid; i < nring * 128; i += kUThreads) {
+    float* ent = ring + (i / 128) * ring_rows * 128;
+    ent[p.slot_cap * 128 + (i % 128)] = -INFINITY;
+    ent[(p.slot_cap + 1) * 128 + (i % 128)] = INFINITY;
   }
   if (warp == 0) {
     tc::tmem_alloc(&tmem_base_sh, S::kTmemCols);
@@ -565,19 +655,16 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
     if (lane == 0) ntl_sh = cnt < kMaxTileList ? cnt : kMaxTileList;
   }
   const int ncol = *p.T.ncol;
-  int it_base = 0;     // tiles processed by earlier chunks (all roles count the same)
-  int use0 = 0, use1 = 0;   // epilogue: uses so far of its group's two TMEM slots
-  int kt = 0;               // epilogue: tiles of its group so far
-  int mkt[2] = {0, 0}, mu[2][2] = {{0, 0}, {0, 0}};   // the MMA thread's copies, per group
-  int mma_tiles = 0;        // the MMA thread: accumulator slots committed so far
-  unsigned long long yes_cnt = 0;
+  int it_base = 0;     // tiles of earlier sets (the stages' running index)
+  int jbase = 0;       // jobs of earlier sets (the slots' running index)
+  int mma_jobs = 0;    // the MMA thread: jobs issued so far
+  unsigned long long yes_cnt = 0;   // "yes" taken in the epilogue (INL)
   bool failed = false;
-  for (int c0 = 0; c0 < ncol; c0 += NMAX) {
-    const int nn = min(NMAX, ncol - c0);
-    const int N = (nn + 15) & ~15;
-    const int H = N > S::kSW ? 2 : 1;   // TMEM slots per tile
-    // ---- the chunk's columns: distinct k of their rows, bound-table rows, B operand
-    __syncthreads();   // the previous chunk is done with every shared table
+  for (int c0 = 0; c0 < ncol; c0 += SETN) {
+    const int nn = min(SETN, ncol - c0);
+    const int ns = (nn + W - 1) / W;                 // slices of the set
+    // ---- the set's columns: distinct k of their rows, bound-table rows, B operand
+    __syncthreads();   // the previous set is done with every shared table
     for (int k = tid; k <= 64; k += kUThreads) kseen[k] = 0;
     __syncthreads();
     const int rb = p.T.start[c0], re = p.T.start[c0 + nn];
@@ -587,61 +674,64 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
     }
     __syncthreads();
     if (tid == 0) {
-      int ns = 0;
+      int ns_ = 0;
       for (int k = 1; k <= p.kmax; ++k) {
         kslot[k] = -1;
         if (kseen[k]) {
-          kslot[k] = ns < p.slot_cap ? ns : -1;   // past the cap: bounds read from global memory
-          klist[ns++] = k;
+          kslot[k] = ns_ < p.slot_cap ? ns_ : -1;   // past the cap: bounds read from global memory
+          klist[ns_++] = k;
         }
       }
-      nsl_sh = ns < p.slot_cap ? ns : p.slot_cap;
+      nsl_sh = ns_ < p.slot_cap ? ns_ : p.slot_cap;
     }
     __syncthreads();
-    for (int i = rb + tid; i < re && i - rb < kRowsSmem; i += kUThreads) {
-      const int4 rw = p.T.rows[i];
-      const int k = rw.y;
-      const int sl = (k >= 1 && k <= p.kmax) ? kslot[k] : -1;
-      srows[i - rb] = make_int4(rw.x, sl >= 0 ? 32 * sl : (k <= p.kmax ? -1 : -2), rw.z, k);
+    if (INL) {
+      for (int i = rb + tid; i < re && i - rb < NROWS; i += kUThreads) {
+        const int4 rw = p.T.rows[i];
+        const int k = rw.y;
+        const int sl = (k >= 1 && k <= p.kmax) ? kslot[k] : -1;
+        srows[i - rb] = make_int4(rw.x, sl >= 0 ? 128 * sl : (k <= p.kmax ? -1 : -2), rw.z, k);
+      }
+      for (int c = tid; c < SETN; c += kUThreads)
+        crows[INL ? c : 0] = c < nn ? make_int2(p.T.start[c0 + c] - rb, p.T.start[c0 + c + 1] - p.T.start[c0 + c])
+                                   : make_int2(0, 0);
     }
-    for (int c = tid; c < NMAX; c += kUThreads) {
+    for (int c = tid; c < SETN; c += kUThreads) {
       float qn = 0.f;
       int row = p.slot_cap + 1;   // past nn: the +inf row, never a candidate
-      int2 cr = make_int2(0, 0);
       if (c < nn) {
         const int kq = p.T.kq[c0 + c];
         const int sl = kq > 0 ? kslot[kq] : -1;
         qn = p.qn[p.T.rep[c0 + c]];
         // no bound row (only k > k_max rows, or past the cap): the -inf row, every user a candidate
         row = sl >= 0 ? sl : p.slot_cap;
-        cr = make_int2(p.T.start[c0 + c] - rb, p.T.start[c0 + c + 1] - p.T.start[c0 + c]);   // chunk-relative
       }
-      cq[c] = make_float2(qn, __int_as_float(32 * row));
-      crows[c] = cr;
+      cq[c] = make_float2(qn, __int_as_float(128 * row));
     }
     __syncthreads();
-    if (tid < NMAX / 32) {
-      // the columns < nn of the group share one bound row: the "no" test needs one table read
-      int common = -1;
-      bool same = true;
+    if (tid < NG) {
+      // the group's fast test: its largest ||q|| against its smallest bound, which belongs
+      // to its largest k (bounds fall as k grows; slots follow k; the -inf row is last)
+      float qmax = 0.f;
+      int row = -1;
       for (int c = 32 * tid; c < min(nn, 32 * tid + 32); ++c) {
-        const int off = __float_as_int(cq[c].y);
-        if (common == -1) common = off;
-        same = same && off == common;
+        qmax = fmaxf(qmax, cq[c].x);
+        row = max(row, __float_as_int(cq[c].y) / 128);
       }
-      wrow[tid] = same ? common : -1;
+      gq[tid] = make_float2(qmax, __int_as_float(128 * (row < 0 ? p.slot_cap + 1 : row)));
     }
-    for (int i = tid; i < N * KB * 8; i += kUThreads) {
+    const int Nfill = (nn + 15) & ~15;
+    for (int i = tid; i < Nfill * KB * 8; i += kUThreads) {
       const int rr = i / (KB * 8), rem = i % (KB * 8), kb = rem / 8, ch = rem % 8;
       uint4 hi = make_uint4(0u, 0u, 0u, 0u), lo = hi;
       if (rr < nn) {
         const int64_t off = (int64_t)p.T.rep[c0 + rr] * p.dk + kb * 64 + ch * 8;
         hi = *reinterpret_cast<const uint4*>(p.Qhi + off);
-        lo = *reinterpret_cast<const uint4*>(p.Qlo + off);
+        if (PRODS == 3) lo = *reinterpret_cast<const uint4*>(p.Qlo + off);
       }
       const uint32_t o = tc::sw128_offset(rr, ch);
       *reinterpret_cast<uint4*>(sB + kb * S::kBPart + o) = hi;
-      *reinterpret_cast<uint4*>(sB + (KB + kb) * S::kBPart + o) = lo;
+      if (PRODS == 3) *reinterpret_cast<uint4*>(sB + (KB + kb) * S::kBPart + o) = lo;
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc::tc_fence_before();
@@ -649,355 +739,325 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
     tc::tc_fence_after();
     const uint32_t tbase = tmem_base_sh;
     const int ntl = ntl_sh;
+    const int njobs = ntl * ns;
 
     if (warp == 0) {
       if (lane == 0) {
-        // TMA producer for both groups: one thread that never blocks on either, so a group
-        // whose stage is still busy does not hold up the other
+        // ---- TMA producer: the set's tiles in order, one stage each
         if (c0 == 0) {
           tc::prefetch_tensormap(&tmapUhi);
-          tc::prefetch_tensormap(&tmapUlo);
+          if (PRODS == 3) tc::prefetch_tensormap(&tmapUlo);
         }
-        const int end = it_base + ntl;
-        int nx[2] = {it_base + ((0 - it_base) & 1), it_base + ((1 - it_base) & 1)};
-        uint32_t idle = 0;
-        for (;;) {
-          bool any_left = false, progressed = false;
-#pragma unroll
-          for (int g = 0; g < 2; ++g) {
-            if (nx[g] >= end) continue;
-            any_left = true;
-            const int s = nx[g] % STAGES;
-            if (nx[g] >= STAGES && !tc::mbar_test_wait(&empty_bar[s], ((nx[g] / STAGES) & 1) ^ 1)) continue;
-            const int t = tlist[nx[g] - it_base];
-            tc::mbar_arrive_expect_tx(&full_bar[s], S::kStage);
-            uint8_t* dst = sA + s * S::kStage;
-            for (int kb = 0; kb < KB; ++kb) {
-              tc::tma_load_2d(dst + kb * S::kTile, &tmapUhi, &full_bar[s], kb * 64, t * kUM);
-              tc::tma_load_2d(dst + (KB + kb) * S::kTile, &tmapUlo, &full_bar[s], kb * 64, t * kUM);
-            }
-            ++tma_issued[s];
-            nx[g] += 2;
-            progressed = true;
+        for (int li = 0; li < ntl; ++li) {
+          const int it = it_base + li, s = it % STAGES;
+          if (it >= STAGES && !tc::mbar_wait(&empty_bar[s], ((it / STAGES) & 1) ^ 1, p.timeout, nullptr)) break;
+          const int t = tlist[li];
+          tc::mbar_arrive_expect_tx(&full_bar[s], S::kStage);
+          uint8_t* dst = sA + s * S::kStage;
+          for (int kb = 0; kb < KB; ++kb) {
+            tc::tma_load_2d(dst + kb * S::kTile, &tmapUhi, &full_bar[s], kb * 64, t * kUM);
+            if (PRODS == 3) tc::tma_load_2d(dst + (KB + kb) * S::kTile, &tmapUlo, &full_bar[s], kb * 64, t * kUM);
           }
-          if (!any_left) break;
-          if (progressed) {
-            idle = 0;
-            continue;
-          }
-          if (++idle % tc::kFlagEvery == 0 && *(volatile int*)p.timeout) break;
-          if (idle > tc::kSpinLimit) {
-            atomicExch(p.timeout, 1);
-            break;
-          }
-          if (idle > 32) __nanosleep(32);
+          ++tma_issued[s];
         }
       }
     } else if (warp == 1) {
       if (lane == 0) {
-        // MMA issuer for both groups (hi.hi + hi.lo + lo.hi into group g's TMEM slots), one
-        // thread that never blocks on either group
+        // ---- MMA issuer: job j = (tile j / ns, slice j mod ns) into slot (jbase + j) & 1
         const uint32_t a0 = tc::smem_addr(sA), b0 = tc::smem_addr(sB);
-        const int end = it_base + ntl;
-        int nx[2] = {it_base + ((0 - it_base) & 1), it_base + ((1 - it_base) & 1)};
-        int hh[2] = {0, 0};
-        uint32_t idle = 0;
-        for (;;) {
-          // test hook: a partner that stops working; the epilogue's bounded wait runs out
-          if (p.inject_stall && mma_tiles >= 1) break;
-          bool any_left = false, progressed = false;
+        for (int j = 0; j < njobs; ++j) {
+          if (p.inject_stall && mma_jobs >= 1) break;   // test hook: a partner that stops working
+          const int li = j / ns, sc = j - li * ns;
+          const int it = it_base + li, s = it % STAGES;
+          if (sc == 0 && !tc::mbar_wait(&full_bar[s], (it / STAGES) & 1, p.timeout, nullptr)) break;
+          const int jg = jbase + j, slot = jg & 1, u = jg >> 1;
+          if (u >= 1 && !tc::mbar_wait(&tempty_bar[slot], (u - 1) & 1, p.timeout, nullptr)) break;
+          tc::tc_fence_after();
+          const int nh = min(W, nn - sc * W);
+          const uint32_t idesc = tc::idesc_bf16_f32(kUM, (uint32_t)((nh + 15) & ~15));
+          const uint32_t d = tbase + slot * W;
+          const uint32_t aS = a0 + s * S::kStage;
+          const uint32_t bS = b0 + sc * W * 128;           // rows sc W.. of each B K-block
+          uint32_t acc = 0;
 #pragma unroll
-          for (int g = 0; g < 2; ++g) {
-            if (nx[g] >= end) continue;
-            any_left = true;
-            const int s = nx[g] % STAGES;
-            if (hh[g] == 0 && !tc::mbar_test_wait(&full_bar[s], (nx[g] / STAGES) & 1)) continue;
-            const int sl = H == 2 ? hh[g] : (mkt[g] & 1);
-            const int u = mu[g][sl];
-            if (u >= 1 && !tc::mbar_test_wait(&tempty_bar[g][sl], (u & 1) ^ 1)) continue;
-            tc::tc_fence_after();
-            const int nh = hh[g] == 0 ? (N < S::kSW ? N : S::kSW) : N - S::kSW;
-            const uint32_t idesc = tc::idesc_bf16_f32(kUM, (uint32_t)nh);
-            const uint32_t d = tbase + (2 * g + sl) * S::kSW;
-            const uint32_t bh = b0 + hh[g] * S::kSW * 128;   // rows kSW hh.. of each B part
-            const uint32_t aS = a0 + s * S::kStage;
-            uint32_t acc = 0;
+          for (int prod = 0; prod < PRODS; ++prod) {
+            // (A, B) parts: (hi, hi), then with PRODS = 3 (hi, lo) and (lo, hi)
+            const uint32_t ap = aS + (prod == 2 ? KB : 0) * S::kTile;
+            const uint32_t bp = bS + (prod == 1 ? KB : 0) * S::kBPart;
 #pragma unroll
-            for (int prod = 0; prod < 3; ++prod) {
-              // (A, B) parts: (hi, hi), (hi, lo), (lo, hi)
-              const uint32_t ap = aS + (prod == 2 ? KB : 0) * S::kTile;
-              const uint32_t bp = bh + (prod == 1 ? KB : 0) * S::kBPart;
+            for (int kb = 0; kb < KB; ++kb)
 #pragma unroll
-              for (int kb = 0; kb < KB; ++kb)
-#pragma unroll
-                for (int k16 = 0; k16 < 4; ++k16) {
-                  tc::umma_bf16(d, tc::sw128_kmajor_desc(ap + kb * S::kTile + k16 * 32),
-                                tc::sw128_kmajor_desc(bp + kb * S::kBPart + k16 * 32), idesc, acc);
-                  acc = 1;
-                }
-            }
-            tc::umma_commit(&tfull_bar[g][sl]);
-            ++mu[g][sl];
-            ++mma_tiles;
-            if (++hh[g] == H) {
-              tc::umma_commit(&empty_bar[s]);
-              hh[g] = 0;
-              ++mkt[g];
-              nx[g] += 2;
-            }
-            progressed = true;
+              for (int k16 = 0; k16 < 4; ++k16) {
+                tc::umma_bf16(d, tc::sw128_kmajor_desc(ap + kb * S::kTile + k16 * 32),
+                              tc::sw128_kmajor_desc(bp + kb * S::kBPart + k16 * 32), idesc, acc);
+                acc = 1;
+              }
           }
-          if (!any_left) break;
-          if (progressed) {
-            idle = 0;
-            continue;
-          }
-          if (++idle % tc::kFlagEvery == 0 && *(volatile int*)p.timeout) break;
-          if (idle > tc::kSpinLimit) {
-            atomicExch(p.timeout, 1);
-            break;
-          }
-          if (idle > 32) __nanosleep(32);
+          tc::umma_commit(&tfull_bar[slot]);
+          if (sc == ns - 1) tc::umma_commit(&empty_bar[s]);   // the tile's stage is free again
+          ++mma_jobs;
         }
       }
-    } else {
-      // ---- epilogue: group g takes the tiles it with it & 1 == g (accumulator g); a warp
-      // reads TMEM lane quadrant warp & 3, one user per lane
-      const int ew = warp - 2, g = ew >> 2, quad = warp & 3;
-      const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
-      const int inf_row = 32 * p.slot_cap;
-      float* Lw = Lsm + ew * 32 * (p.slot_cap + 2);
-      int2* Ob = Osm + ew * kOpenBuf;
-      int32_t* Inv = Ism + ew * 32;
-      Lw[inf_row + lane] = -INFINITY;
-      Lw[inf_row + 32 + lane] = INFINITY;
+    } else if (warp == kLoaderWarp) {
+      // ---- bound loader: for each tile of the set, in order, the lower bounds of the set's k,
+      // ||u||, E_u and the caller's id of its 128 users copied asynchronously into the ring, nring - 1 tiles
+      // ahead of the epilogue; each lane's arrival on the entry's barrier waits for its copies
       const int nsl = nsl_sh;
-      const int wc = (nn + 31) >> 5;
-      // values of the group's next tile, loaded while the current one is processed
-      constexpr int kPre = 8;
-      int Bu_n = 0, id_n = 0;
-      float nu_n = 0.f, E_n = 0.f;
-      float L_n[kPre];
-      uint32_t kw0_n = 0;   // word `lane` of the kept bits of the warp's first leaf
-      auto load_user = [&](int li) {
-        Bu_n = 0;
-        id_n = 0;
-        nu_n = 0.f;
-        E_n = 0.f;
+      for (int li = 0; li < ntl; ++li) {
+        const int rt = it_base + li, e = rt % nring;
+        bool ok = true;
+        if (rt >= nring) ok = tc::mbar_wait(&ring_empty[e], ((rt / nring) & 1) ^ 1, p.timeout, nullptr);
+        if (!__all_sync(0xffffffffu, ok)) break;
+        float* ent = ring + e * ring_rows * 128;
+        const int64_t r0 = (int64_t)tlist[li] * kUM;
+        {
+          const int64_t u4 = r0 + 4 * lane;            // 16-byte chunk of 4 users
+          const int nb = (int)std::min<int64_t>(16, std::max<int64_t>(0, (p.mz - u4) * 4));
+          cp_async16(ent + (p.slot_cap + 2) * 128 + 4 * lane, nb ? (const void*)(p.unorm + u4) : (const void*)p.unorm, nb);
+          cp_async16(ent + (p.slot_cap + 3) * 128 + 4 * lane, nb ? (const void*)(p.Eu + u4) : (const void*)p.Eu, nb);
+          cp_async16(ent + (p.slot_cap + 4) * 128 + 4 * lane, nb ? (const void*)(p.uid + u4) : (const void*)p.uid, nb);
+        }
+        for (int sl = 0; sl < nsl; ++sl) {
+          const float* Lrow = p.Lt + (int64_t)(klist[sl] - 1) * p.mz;
 #pragma unroll
-        for (int j = 0; j < kPre; ++j) L_n[j] = 0.f;
-        if (li < ntl) {
-          const int64_t rr = (int64_t)tlist[li] * kUM + quad * 32 + lane;
-          if (rr < p.mz) {
-            Bu_n = p.ublock[rr];
-            nu_n = p.unorm[rr];
-            E_n = p.Eu[rr];
-            id_n = p.uid[rr];
-#pragma unroll
-            for (int j = 0; j < kPre; ++j)
-              if (j < nsl) L_n[j] = __ldg(&p.Lt[(int64_t)(klist[j] - 1) * p.mz + rr]);
+          for (int qq = 0; qq < 4; ++qq) {
+            const int u = qq * 32 + lane;
+            const bool v = r0 + u < p.mz;
+            cp_async4(ent + sl * 128 + u, v ? (const void*)(Lrow + r0 + u) : (const void*)Lrow, v ? 4 : 0);
           }
         }
+        cp_async_arrive(&ring_full[e]);
+      }
+      asm volatile("cp.async.wait_all;" ::: "memory");   // nothing in flight when the role ends
+    } else {
+      // ---- epilogue: group g (warps 2-5, 6-9) takes the jobs of slot g, so that two jobs'
+      // epilogues overlap; a warp reads TMEM lane quadrant warp & 3, one user per lane.  The
+      // users' bounds come from the loader's ring; ids and norms are read only by the rare
+      // candidate path.
+      const int ew = warp - 2, g = ew >> 2, quad = warp & 3;
+      static_assert(W % 64 == 0, "the epilogue reads 64 columns at a time");
+      const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
+      const int ul = quad * 32 + lane;                 // this thread's user within the tile
+
+      // ring entries: every epilogue warp takes and releases each tile of the set once, in
+      // order (a tile without a job of this warp is taken and released at once)
+      int held = -1, next_rel = 0;
+      auto ring_take = [&](int li) -> bool {
+        const int rt = it_base + li;
+        return __all_sync(0xffffffffu, tc::mbar_wait(&ring_full[rt % nring], (rt / nring) & 1, p.timeout, nullptr));
       };
-      // open pairs of a tile wait in Ob; their list slots are claimed with one atomic at
-      // the end of the tile and written after the next wait
-      int prev_n = 0;
-      unsigned long long prev_base = 0;
-      auto emit_prev = [&]() {
-        if (prev_n == 0) return;
-        const unsigned long long b0 = __shfl_sync(0xffffffffu, prev_base, 0);
-        for (int i = lane; i < prev_n; i += 32) {
-          const int2 e = Ob[i];
-          if ((int64_t)(b0 + i) < p.resc_cap) p.resc[b0 + i] = Survivor{e.x, e.y, 0.f};
-        }
-        prev_n = 0;
+      auto ring_give = [&](int li) {
         __syncwarp();
-        if (lane == 0) nopen_sh[ew] = 0;
-        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&ring_empty[(it_base + li) % nring]);
       };
-      // an open pair into the buffer; a full buffer goes out at once
-      auto push_open = [&](int32_t upos, int32_t jv) {
-        const int slot = atomicAdd(&nopen_sh[ew], 1);
-        if (slot < kOpenBuf) {
-          Ob[slot] = make_int2(upos, jv);
-        } else {
-          const unsigned long long gs = atomicAdd(p.resc_count, 1ull);
-          if ((int64_t)gs < p.resc_cap) p.resc[gs] = Survivor{upos, jv, 0.f};
+      auto advance_to = [&](int li) -> bool {   // release every tile before li, take li
+        if (held >= 0) {
+          ring_give(held);
+          next_rel = held + 1;
+          held = -1;
         }
-      };
-      // the kept words of the first leaf of the warp's users in the next tile
-      auto load_words = [&](int li) {
-        const int b0 = __shfl_sync(0xffffffffu, Bu_n, 0);
-        kw0_n = 0u;
-        if (li < ntl && lane < p.mask_words) kw0_n = __ldg(&p.kept_mask[(int64_t)b0 * p.mask_words + lane]);
-      };
-      if (lane == 0) nopen_sh[ew] = 0;
-      __syncwarp();
-      const int first = ((g - it_base) & 1);   // local index of the group's first tile
-      load_user(first);
-      load_words(first);
-      for (int li = first; li < ntl; li += 2) {
-        const int a = g;
-        const int64_t r = (int64_t)tlist[li] * kUM + quad * 32 + lane;
-        const bool valid = r < p.mz;
-        const int Bu = Bu_n;
-        const int B0 = __shfl_sync(0xffffffffu, Bu, 0);
-        const uint32_t kw0 = kw0_n;
-        const int32_t id = id_n;
-        const float nu = nu_n, E = E_n;
-        const float cu = __fmul_ru(p.ctc, nu);
-        const float nun = __fmul_ru(nu, 1.f + 2.f * p.gamma);
-        // this tile's lower bounds L - E (less the band's absolute slack) per distinct k
-#pragma unroll
-        for (int j = 0; j < kPre; ++j)
-          if (j < nsl) Lw[32 * j + lane] = valid ? __fsub_rd(__fsub_rd(L_n[j], E), 1e-30f) : INFINITY;
-        for (int sl = kPre; sl < nsl; ++sl) {
-          float Llo = INFINITY;
-          if (valid) Llo = __fsub_rd(__fsub_rd(__ldg(&p.Lt[(int64_t)(klist[sl] - 1) * p.mz + r]), E), 1e-30f);
-          Lw[32 * sl + lane] = Llo;
+        for (; next_rel < li; ++next_rel) {
+          if (!ring_take(next_rel)) return false;
+          ring_give(next_rel);
         }
-        __syncwarp();
-        for (int h = 0; h < H; ++h) {
-          const int sl = H == 2 ? h : (kt & 1);
-          const int u = sl ? use1++ : use0++;
-          // TMEM address of column 0 of this chunk, as seen from this half's slot
-          const uint32_t acc_addr = tbase + lane_addr + (2 * a + sl) * S::kSW - h * S::kSW;
-          if (!tc::mbar_wait(&tfull_bar[a][sl], u & 1, p.timeout, nullptr)) {
+        if (li < ntl) {
+          if (!ring_take(li)) return false;
+          held = li;
+        }
+        return true;
+      };
+      int cur_li = -1;
+      const float* ent = ring;
+      float cu = 0.f, E = 0.f;
+      int64_t r = 0;
+      bool valid = false;
+      // the bound L - E - 1e-30 (rounded down) of the ring row at `off` for user ul
+      auto Lm = [&](int off, int u, float Eu_) { return __fsub_rd(__fsub_rd(ent[off + u], Eu_), 1e-30f); };
+      const int j0 = (g - jbase) & 1;
+      for (int j = j0; j < njobs; j += 2) {
+        const int li = j / ns, sc = j - li * ns;
+        if (li != cur_li) {
+          if (!advance_to(li)) {
             failed = true;
             break;
           }
-          tc::tc_fence_after();
-          if (h == 0) {
-            emit_prev();
-            load_user(li + 2);
+          cur_li = li;
+          ent = ring + ((it_base + li) % nring) * ring_rows * 128;
+          r = (int64_t)tlist[li] * kUM + ul;
+          valid = r < p.mz;
+          cu = __fmul_ru(p.cband, ent[(p.slot_cap + 2) * 128 + ul]);
+          E = ent[(p.slot_cap + 3) * 128 + ul];
+        }
+        const int jg = jbase + j, slot = jg & 1;      // slot == g
+        if (!tc::mbar_wait(&tfull_bar[slot], (jg >> 1) & 1, p.timeout, nullptr)) {
+          failed = true;
+          break;
+        }
+        tc::tc_fence_after();
+        const int cs0 = sc * W;                        // the slice's first column in the set
+        // fast test of every 32 columns of the slice: their largest score against the smallest
+        // bound of the 32 less their largest band, rounded down (so never above
+        // L - E - c ||u|| ||q|| for any of the columns); "no" for all 32 unless it reaches
+        constexpr int NG8 = W / 32;
+        float thr[NG8];
+#pragma unroll
+        for (int q = 0; q < NG8; ++q) {
+          const int cw = cs0 + 32 * q;
+          thr[q] = INFINITY;
+          if (cw < nn && valid) {
+            const float2 gg = gq[cw >> 5];
+            thr[q] = __fsub_rd(Lm(__float_as_int(gg.y), ul, E), __fmul_ru(cu, gg.x));
           }
-          const int wend = h + 1 < H ? (S::kSW / 32) * (h + 1) : wc;
-          for (int w = (S::kSW / 32) * h; w < wend; ++w) {
-            float v[32];
-            tmem_ld32_wait(acc_addr + 32 * w, v);
-            // "no" unless s + c_tc ||u|| ||q|| (rounded up) reaches the column's lowest L - E
-            bool any0 = false, any1 = false, any2 = false, any3 = false;
-            const int wr = wrow[w];
-            if (wr >= 0) {
-              const float Lg = Lw[wr + lane];
+        }
+        const int rem = nn - cs0;                      // columns of the slice inside the set
+        const uint32_t acc_addr = tbase + lane_addr + slot * W;   // the slice's first column
+        if constexpr (INL) {
+          // dense candidates: the 32-column groups some user passes are examined here
+          uint32_t need = 0;
 #pragma unroll
-              for (int i = 0; i < 32; i += 4) {
-                const float4 ca = *reinterpret_cast<const float4*>(&cq[32 * w + i]);
-                const float4 cb = *reinterpret_cast<const float4*>(&cq[32 * w + i + 2]);
-                any0 |= __fmaf_ru(cu, ca.x, v[i]) >= Lg;
-                any1 |= __fmaf_ru(cu, ca.z, v[i + 1]) >= Lg;
-                any2 |= __fmaf_ru(cu, cb.x, v[i + 2]) >= Lg;
-                any3 |= __fmaf_ru(cu, cb.z, v[i + 3]) >= Lg;
+          for (int x2 = 0; x2 < W / 64; ++x2) {
+            if (64 * x2 < rem) {
+              float vv[64];
+              tmem_ld64_wait(acc_addr + 64 * x2, vv);
+              if (64 * x2 + 64 > rem) {
+#pragma unroll
+                for (int i = 0; i < 64; ++i)
+                  if (64 * x2 + i >= rem) vv[i] = -INFINITY;
               }
-            } else {
-#pragma unroll
-            for (int i = 0; i < 32; i += 4) {
-              const float4 ca = *reinterpret_cast<const float4*>(&cq[32 * w + i]);
-              const float4 cb = *reinterpret_cast<const float4*>(&cq[32 * w + i + 2]);
-              any0 |= __fmaf_ru(cu, ca.x, v[i]) >= Lw[__float_as_int(ca.y) + lane];
-              any1 |= __fmaf_ru(cu, ca.z, v[i + 1]) >= Lw[__float_as_int(ca.w) + lane];
-              any2 |= __fmaf_ru(cu, cb.x, v[i + 2]) >= Lw[__float_as_int(cb.y) + lane];
-              any3 |= __fmaf_ru(cu, cb.z, v[i + 3]) >= Lw[__float_as_int(cb.w) + lane];
+              const bool a0 = max32_at<0>(vv) >= thr[2 * x2];
+              const bool a1 = max32_at<32>(vv) >= thr[2 * x2 + 1];
+              if (__any_sync(0xffffffffu, a0 || a1))
+                need |= ((__any_sync(0xffffffffu, a0) ? 1u : 0u) | (__any_sync(0xffffffffu, a1) ? 2u : 0u)) << (2 * x2);
             }
-            }
-            if (!__any_sync(0xffffffffu, (any0 || any1) || (any2 || any3))) continue;
+          }
+          while (need) {
+            const int x = __ffs(need) - 1;             // 32-column group of the slice
+            need &= need - 1;
+            const int cw = cs0 + 32 * x;               // set column of the group's first score
+            const int left = nn - cw;
+            float v[32];
+            tmem_ld32_wait(acc_addr + 32 * x, v);
             uint32_t cand = 0;
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
-              const float2 c2 = cq[32 * w + i];
-              cand |= (__fmaf_ru(cu, c2.x, v[i]) >= Lw[__float_as_int(c2.y) + lane] ? 1u : 0u) << i;
+              const float2 c2 = cq[cw + i < SETN ? cw + i : SETN - 1];
+              cand |= (i < left && __fmaf_ru(cu, c2.x, v[i]) >= Lm(__float_as_int(c2.y), ul, E) ? 1u : 0u) << i;
             }
-            // per candidate column (the whole warp reads its score again from TMEM), the
-            // column's rows whose leaf the block bound kept: the "no" test with the row's
-            // own k, then the "yes" tests.  L + E is bounded above from the table's
-            // L - E - 1e-30 (rounded down) with four units in the last place and 2e-30 to
-            // spare.
+            if (!valid) cand = 0u;
+            // per candidate column: its rows for every candidate user, a (user, row) pair per
+            // lane: the "no" test with the row's own k, then the "yes" tests (Alg. 5); what
+            // stays open goes to the FP32 re-score.  L + E is bounded above from L - E - 1e-30
+            // (rounded down) with four units in the last place and 2e-30 to spare.
             uint32_t uni = __reduce_or_sync(0xffffffffu, cand);
             while (uni) {
               const int i = __ffs(uni) - 1;
               uni &= uni - 1;
-              const float sv = tmem_ld1_wait(acc_addr + 32 * w + i);
-              const bool is_c = valid && ((cand >> i) & 1u);
-              const unsigned cm = __ballot_sync(0xffffffffu, is_c);
-              // candidate rank -> lane, through this warp's 32-entry table
-              __syncwarp();
-              if (is_c) Inv[__popc(cm & ((1u << lane) - 1u))] = lane;
-              __syncwarp();
-              const int2 cr = crows[32 * w + i];
-              const float qn = cq[32 * w + i].x;
-              // every (candidate user, row) pair of the column on its own lane
+              const float sv = tmem_ld1_wait(acc_addr + 32 * x + i);
+              const unsigned cm = __ballot_sync(0xffffffffu, (cand >> i) & 1u);
+              const int2 cr = crows[cw + i];
+              const float qn = cq[cw + i].x;
               const int P = __popc(cm) * cr.y;
               for (int pb = 0; pb < P; pb += 32) {
                 const int pp = pb + lane;
                 const bool act = pp < P;
                 const int ci = act ? pp / cr.y : 0, q = act ? pp % cr.y : 0;
-                const int src = act ? Inv[ci] : lane;
+                const int src = act ? (int)__fns(cm, 0, ci + 1) : lane;
                 const float s_ = __shfl_sync(0xffffffffu, sv, src);
                 const float cu_ = __shfl_sync(0xffffffffu, cu, src);
-                const float nun_ = __shfl_sync(0xffffffffu, nun, src);
                 const float E_ = __shfl_sync(0xffffffffu, E, src);
-                const int Bu_ = __shfl_sync(0xffffffffu, Bu, src);
-                const int id_ = __shfl_sync(0xffffffffu, id, src);
                 const int r_ = __shfl_sync(0xffffffffu, (int)r, src);
-                int4 rw = make_int4(0, -2, 0, 0);
+                bool open = false;
+                int jv = 0;
                 if (act) {
-                  if (cr.x + q < kRowsSmem) {
+                  int4 rw;
+                  if (cr.x + q < NROWS) {
                     rw = srows[cr.x + q];
                   } else {
                     rw = p.T.rows[rb + cr.x + q];
                     const int sl3 = (rw.y >= 1 && rw.y <= p.kmax) ? kslot[rw.y] : -1;
-                    rw = make_int4(rw.x, sl3 >= 0 ? 32 * sl3 : (rw.y <= p.kmax ? -1 : -2), rw.z, rw.y);
+                    rw = make_int4(rw.x, sl3 >= 0 ? 128 * sl3 : (rw.y <= p.kmax ? -1 : -2), rw.z, rw.y);
+                  }
+                  const int jr = rw.x & 0x3fffffff, k = rw.w;
+                  jv = rw.x;
+                  float Lq = -INFINITY;   // L - E - 1e-30 rounded down, or -inf without a bound
+                  if (rw.y >= 0) {
+                    Lq = Lm(rw.y, quad * 32 + src, E_);
+                  } else if (rw.y == -1) {   // past the ring's slots
+                    Lq = __fsub_rd(__fsub_rd(__ldg(&p.Lt[(int64_t)(k - 1) * p.mz + r_]), E_), 1e-30f);
+                  }
+                  if (!(__fmaf_ru(cu_, qn, s_) < Lq)) {   // not "no"
+                    const float lo = __fsub_rd(s_, __fmul_ru(cu_, qn) + 1e-30f);
+                    const float nun_ = __fmul_ru(ent[(p.slot_cap + 2) * 128 + quad * 32 + src], 1.f + 2.f * p.gamma);
+                    bool yes = lo >= __fmul_ru(nun_, __int_as_float(rw.z));
+                    if (!yes && p.l_exact && k <= p.kmax && Lq != -INFINITY)
+                      yes = lo >= __fadd_ru(__fadd_ru(Lq, 2.f * E_), __fmaf_ru(fabsf(Lq), 0x1p-21f, 2e-30f));
+                    if (yes) {
+                      ++yes_cnt;
+                      set_answer(p.bitmap, p.words, jr, __float_as_int(ent[(p.slot_cap + 4) * 128 + quad * 32 + src]));
+                    } else {
+                      open = true;
+                    }
                   }
                 }
-                const int j = rw.x & 0x3fffffff, k = rw.w;
-                // the kept bit: from the words of leaf B0 spread over the lanes, else memory
-                uint32_t kwv = __shfl_sync(0xffffffffu, kw0, (j >> 5) & 31);
-                if (!act) continue;
-                if (Bu_ != B0 || (j >> 5) >= 32) kwv = __ldg(&p.kept_mask[(int64_t)Bu_ * p.mask_words + (j >> 5)]);
-                if (!((kwv >> (j & 31)) & 1u)) continue;
-                float Lq = -INFINITY;   // L - E - 1e-30 rounded down, or -inf without a bound
-                if (rw.y >= 0) {
-                  Lq = Lw[rw.y + src];
-                } else if (rw.y == -1) {   // past the table's cap
-                  Lq = __fsub_rd(__fsub_rd(__ldg(&p.Lt[(int64_t)(k - 1) * p.mz + r_]), E_), 1e-30f);
-                }
-                if (__fmaf_ru(cu_, qn, s_) < Lq) continue;   // "no"
-                const float lo = __fsub_rd(s_, __fmul_ru(cu_, qn) + 1e-30f);
-                bool yes = lo >= __fmul_ru(nun_, __int_as_float(rw.z));
-                if (!yes && p.l_exact && k <= p.kmax && Lq != -INFINITY)
-                  yes = lo >= __fadd_ru(__fadd_ru(Lq, 2.f * E_), __fmaf_ru(fabsf(Lq), 0x1p-21f, 2e-30f));
-                if (yes) {
-                  ++yes_cnt;
-                  set_answer(p.bitmap, p.words, j, id_);
-                } else {
-                  push_open((int32_t)r_, rw.x);
+                const unsigned m = __ballot_sync(0xffffffffu, open);
+                if (m) {
+                  unsigned long long b0 = 0;
+                  if (lane == 0) b0 = atomicAdd(p.resc_count, (unsigned long long)__popc(m));
+                  const unsigned long long sl_i = __shfl_sync(0xffffffffu, b0, 0) + __popc(m & ((1u << lane) - 1u));
+                  if (open && (int64_t)sl_i < p.resc_cap) p.resc[sl_i] = Survivor{r_, jv, 0.f};
                 }
               }
             }
           }
-          tc::tc_fence_before();
-          __syncwarp();
-          if (lane == 0) tc::mbar_arrive(&tempty_bar[a][sl]);
+        } else {
+        // a user whose 32 scores pass writes them, as a candidate block, for the resolve kernel
+          auto push_block = [&](bool mine, const float (&vv)[64], int h, int col0) {
+            const unsigned m = __ballot_sync(0xffffffffu, mine);
+            if (m == 0u) return;
+            unsigned long long b0 = 0;
+            if (lane == __ffs(m) - 1) b0 = atomicAdd(p.cand_count, (unsigned long long)__popc(m));
+            const unsigned long long slot_i = __shfl_sync(0xffffffffu, b0, __ffs(m) - 1) + __popc(m & ((1u << lane) - 1u));
+            if (mine && (int64_t)slot_i < p.resc_cap) {
+              CandBlock* cb = p.cand + slot_i;
+              reinterpret_cast<int4*>(cb)[0] = make_int4((int32_t)r, col0, 0, 0);
+              float4* d4 = reinterpret_cast<float4*>(cb->s);
+#pragma unroll
+              for (int i = 0; i < 8; ++i)
+                d4[i] = make_float4(vv[32 * h + 4 * i], vv[32 * h + 4 * i + 1], vv[32 * h + 4 * i + 2], vv[32 * h + 4 * i + 3]);
+            }
+          };
+#pragma unroll
+          for (int x2 = 0; x2 < W / 64; ++x2) {
+            if (64 * x2 < rem) {
+              float vv[64];
+              tmem_ld64_wait(acc_addr + 64 * x2, vv);
+              if (64 * x2 + 64 > rem) {
+#pragma unroll
+                for (int i = 0; i < 64; ++i)
+                  if (64 * x2 + i >= rem) vv[i] = -INFINITY;
+              }
+              const bool a0 = max32_at<0>(vv) >= thr[2 * x2];
+              const bool a1 = max32_at<32>(vv) >= thr[2 * x2 + 1];
+              push_block(a0, vv, 0, c0 + cs0 + 64 * x2);
+              push_block(a1, vv, 1, c0 + cs0 + 64 * x2 + 32);
+            }
+          }
         }
-        ++kt;
-        if (failed) break;
-        // claim the re-score slots of this tile's open pairs (written after the next wait)
+        tc::tc_fence_before();
         __syncwarp();
-        const int no = min(nopen_sh[ew], kOpenBuf);
-        prev_n = no;
-        if (no && lane == 0) prev_base = atomicAdd(p.resc_count, (unsigned long long)no);
-        load_words(li + 2);
+        if (lane == 0) tc::mbar_arrive(&tempty_bar[slot]);
       }
-      if (!failed) emit_prev();
+      if (!failed && !advance_to(ntl)) failed = true;   // release the set's remaining tiles
     }
     it_base += ntl;
+    jbase += njobs;
     tc::tc_fence_before();
     // a timed-out wait anywhere ends the pass for the whole CTA
     failed = __syncthreads_or(failed || *(volatile int*)p.timeout);
     if (failed) break;
   }
   // ---- teardown
-  if (warp >= 2) {
+  if (INL && warp >= 2) {
     for (int o = 16; o > 0; o >>= 1) yes_cnt += __shfl_xor_sync(0xffffffffu, yes_cnt, o);
     if (lane == 0 && yes_cnt) atomicAdd(&p.stats[p.st_yes], yes_cnt);
   }
@@ -1019,23 +1079,27 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
 }
 
 
-template <int KB, int STAGES, int NMAX>
+template <int KB, int STAGES, int SETN, int PRODS, bool INL>
 sah_status launch_pass(Index* ix, UpParams p, int sms, cudaStream_t st, int* launches, const cudaEvent_t* ev) {
-  using S = UpSmem<KB, STAGES, NMAX>;
-  auto fn = user_pass_tc_kernel<KB, STAGES, NMAX>;
+  using S = UpSmem<KB, STAGES, SETN, PRODS>;
+  auto fn = user_pass_tc_kernel<KB, STAGES, SETN, PRODS, INL>;
   // lower-bound rows per warp: what shared memory holds beside the operands
   int optin = 0;
   SAH_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ix->device));
   cudaFuncAttributes fa{};
   SAH_CUDA(cudaFuncGetAttributes(&fa, fn));
-  const int64_t spare = (int64_t)optin - (int64_t)fa.sharedSizeBytes - (int64_t)S::bytes(0);
-  const int rows = (int)std::max<int64_t>(0, spare / (kEpiWarps * 32 * 4));
-  p.slot_cap = std::min({ix->kmax, 64, rows});
-  if (p.slot_cap < 1) {
-    set_error("tensor-core user pass: no shared memory left for the lower bounds");
+  // the ring: up to 8 slots of bounds and up to kRingMax entries, at least 3 entries
+  const int64_t spare = (int64_t)optin - (int64_t)fa.sharedSizeBytes - (int64_t)S::bytes(0, 0);
+  int slots = std::min({ix->kmax, 8, 64});
+  while (slots > 1 && spare / ((int64_t)(slots + 5) * 512) < 3) --slots;
+  const int nring = (int)std::min<int64_t>(kRingMax, spare / ((int64_t)(slots + 5) * 512));
+  if (nring < 3) {
+    set_error("tensor-core user pass: no shared memory left for the bound ring");
     return SAH_ERR_UNSUPPORTED;
   }
-  const size_t smem = S::bytes(p.slot_cap);
+  p.slot_cap = slots;
+  p.nring = nring;
+  const size_t smem = S::bytes(p.slot_cap, p.nring);
   SAH_TRY(raise_smem_limit((const void*)fn, (size_t)((int)smem)));
   const unsigned grid = (unsigned)std::max(1, std::min(p.ntiles, sms));
   const int64_t seg = (int64_t)kMaxTileList * grid;   // tiles per launch: at most kMaxTileList per CTA
@@ -1049,6 +1113,102 @@ sah_status launch_pass(Index* ix, UpParams p, int sms, cudaStream_t st, int* lau
     if (launches) *launches += 1;
   }
   return SAH_OK;
+}
+
+
+// The per-row tests of Alg. 5 on the user pass's candidate blocks (one user, the tensor
+// scores of 32 columns), a warp per block and a lane per column; the sub-batch's column table
+// is staged in shared memory, the user's values come with the block.  With L = L_u^k, E its
+// error and the band e = c ||u|| ||q|| (rounded up):
+//   s + e <  L - E                                            -> "no" (k items beat <u,q>)
+//   s - e >= ||u|| ||p_k|| (1 + 2 gamma)                       -> "yes" (Alg. 5)
+//   s - e >= L + E, when L is the exact k-th score (|P'| = n)  -> "yes"
+//   otherwise the pair is re-scored in FP32 (and FP64) by pair_rescore_kernel.
+// L + E is bounded above from L - E - 1e-30 (rounded down) with four units in the last place
+// and 2e-30 to spare.
+__global__ void __launch_bounds__(512)
+cand_resolve_kernel(const CandBlock* __restrict__ cand, const unsigned long long* __restrict__ cand_count,
+                    int64_t cap, ColTable T, const float* __restrict__ Lt, const float* __restrict__ Eu,
+                    const float* __restrict__ unorm, const int32_t* __restrict__ uid, int64_t mz, int kmax,
+                    int l_exact, float cband, float gamma, uint32_t* __restrict__ bitmap, int64_t words,
+                    Survivor* __restrict__ resc, unsigned long long* __restrict__ resc_count,
+                    unsigned long long* __restrict__ stats, int st_yes, const int* __restrict__ timeout) {
+  extern __shared__ int4 cres_sm[];
+  __shared__ int stop;
+  if (threadIdx.x == 0) stop = *(volatile const int*)timeout;
+  const int64_t total = block_count(cand_count, cap);   // synchronises the block
+  if (stop || total == 0) return;   // after a timed-out wait the list may hold unwritten entries
+  const int ncol = *T.ncol;
+  const int nrows = T.start[ncol];
+  int4* rows = cres_sm;                                      // [nrows]
+  int* start = reinterpret_cast<int*>(rows + nrows);         // [ncol + 1]
+  float* qnc = reinterpret_cast<float*>(start + ncol + 1);   // [ncol]
+  int* kqc = reinterpret_cast<int*>(qnc + ncol);             // [ncol] the column's largest k <= k_max
+  for (int i = threadIdx.x; i < nrows; i += blockDim.x) rows[i] = T.rows[i];
+  for (int i = threadIdx.x; i <= ncol; i += blockDim.x) start[i] = T.start[i];
+  for (int i = threadIdx.x; i < ncol; i += blockDim.x) {
+    qnc[i] = T.qnc[i];
+    kqc[i] = T.kq[i];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  unsigned long long yes_cnt = 0;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < total; b += nw) {
+    const int4 h0 = reinterpret_cast<const int4*>(cand + b)[0];
+    const int64_t r = h0.x;
+    const int c = h0.y + lane;
+    const float s = cand[b].s[lane];
+    const float nu = unorm[r], E = Eu[r];
+    const int32_t uidv = uid[r];
+    const float cu = __fmul_ru(cband, nu);
+    const float nun = __fmul_ru(nu, 1.f + 2.f * gamma);
+    const bool live = c < ncol;
+    const float qn = live ? qnc[c] : 0.f;
+    const float lo = __fsub_rd(s, __fmul_ru(cu, qn) + 1e-30f);
+    // the column's own "no" first: its smallest bound belongs to its largest k (bounds fall as
+    // k grows); below it, every row of the column is "no"
+    // (a column holds rows of k <= k_max only, or rows of k > k_max only, which have no bound)
+    bool cand_c = live;
+    if (live) {
+      const int kq = kqc[c];
+      if (kq > 0) cand_c = !(__fmaf_ru(cu, qn, s) < __fsub_rd(__fsub_rd(Lt[(int64_t)(kq - 1) * mz + r], E), 1e-30f));
+    }
+    const int q0 = cand_c ? start[c] : 0, nr = cand_c ? start[c + 1] - q0 : 0;
+    const int nmax = __reduce_max_sync(0xffffffffu, nr);
+    for (int t = 0; t < nmax; ++t) {
+      bool open = false;
+      int jv = 0;
+      if (t < nr) {
+        const int4 rw = rows[q0 + t];
+        const int j = rw.x & 0x3fffffff, k = rw.y;
+        jv = rw.x;
+        float Lq = -INFINITY;   // L - E - 1e-30 rounded down, or -inf without a bound
+        if (k <= kmax) Lq = __fsub_rd(__fsub_rd(Lt[(int64_t)(k - 1) * mz + r], E), 1e-30f);
+        if (!(__fmaf_ru(cu, qn, s) < Lq)) {   // not "no"
+          bool yes = lo >= __fmul_ru(nun, __int_as_float(rw.z));
+          if (!yes && l_exact && k <= kmax && Lq != -INFINITY)
+            yes = lo >= __fadd_ru(__fadd_ru(Lq, 2.f * E), __fmaf_ru(fabsf(Lq), 0x1p-21f, 2e-30f));
+          if (yes) {
+            ++yes_cnt;
+            set_answer(bitmap, words, j, uidv);
+          } else {
+            open = true;
+          }
+        }
+      }
+      // open pairs: one append per warp
+      const unsigned m = __ballot_sync(0xffffffffu, open);
+      if (m) {
+        unsigned long long b0 = 0;
+        if (lane == 0) b0 = atomicAdd(resc_count, (unsigned long long)__popc(m));
+        const unsigned long long slot = __shfl_sync(0xffffffffu, b0, 0) + __popc(m & ((1u << lane) - 1u));
+        if (open && (int64_t)slot < cap) resc[slot] = Survivor{(int32_t)r, jv, 0.f};
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) yes_cnt += __shfl_xor_sync(0xffffffffu, yes_cnt, o);
+  if (lane == 0 && yes_cnt) atomicAdd(&stats[st_yes], yes_cnt);
 }
 
 }  // namespace
@@ -1091,6 +1251,7 @@ sah_status block_filter_tc(Index* ix, void* scratch, int nq, uint32_t* kept_mask
 sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* scratch, const float* qn,
                             const int32_t* kk, int nq, const uint32_t* kept_mask, int mask_words, uint8_t* tile_need,
                             uint32_t* bitmap, int64_t words, Survivor* resc, unsigned long long* resc_count,
+                            Survivor* cand, unsigned long long* cand_count,
                             Survivor* surv, unsigned long long* surv_count, int64_t surv_cap,
                             unsigned long long* stats, int st_yes, int st_fp64, cudaStream_t st, int* launches,
                             const cudaEvent_t* ev) {
@@ -1120,26 +1281,46 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
   p.ublock = ix->ublock;
   p.kept_mask = kept_mask;
   p.tile_need = tile_need;
-  p.ctc = (float)(1.01 * (3.0 * std::ldexp(1.0, -16) + (6.0 * ix->dk + 16.0) * std::ldexp(1.0, -23)));
+  // BF16 operands (u_hi = bf16(u), q_hi = bf16(q), each within 2^-8 of its value) and
+  // FP32 accumulation of dk products, every addition allowed two units in the last place:
+  // |s_tc - <u,q>| <= c_bf ||u|| ||q||
+  p.cband = (float)(1.01 * (std::ldexp(1.0, -7) + std::ldexp(1.0, -16) + (2.0 * ix->dk + 16.0) * std::ldexp(1.0, -23)));
   p.gamma = ix->gamma;
   p.bitmap = bitmap;
   p.words = words;
   p.resc = resc;
   p.resc_count = resc_count;
   p.resc_cap = surv_cap;
+  p.cand = reinterpret_cast<CandBlock*>(cand);
+  p.cand_count = cand_count;
   p.stats = stats;
   p.st_yes = st_yes;
   p.timeout = ix->dev_timeout;
   p.inject_stall = ix->inject_site == SAH_INJECT_USER_PASS ? 1 : 0;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
+  // candidates are sparse against exact thresholds (|P'| = n): candidate blocks; dense
+  // against the paper's |P'|: resolved in the epilogue
   if (ix->dk == 64) {
-    SAH_TRY((launch_pass<1, 4, 128>(ix, p, sms, st, launches, ev)));
+    if (ix->l_exact) SAH_TRY((launch_pass<1, 4, 512, 1, false>(ix, p, sms, st, launches, ev)));
+    else SAH_TRY((launch_pass<1, 4, 512, 1, true>(ix, p, sms, st, launches, ev)));
   } else {
-    SAH_TRY((launch_pass<2, 2, 64>(ix, p, sms, st, launches, ev)));
+    if (ix->l_exact) SAH_TRY((launch_pass<2, 2, 512, 1, false>(ix, p, sms, st, launches, ev)));
+    else SAH_TRY((launch_pass<2, 2, 512, 1, true>(ix, p, sms, st, launches, ev)));
   }
+  {
+    // the column table in shared memory: rows, starts, norms and largest k of at most nq columns
+    const size_t csm = sizeof(int4) * (size_t)nq + sizeof(int) * (size_t)(nq + 1) + 2 * sizeof(float) * (size_t)nq;
+    SAH_TRY(raise_smem_limit((const void*)cand_resolve_kernel, csm));
+    cand_resolve_kernel<<<sms * 2, 512, csm, st>>>(reinterpret_cast<const CandBlock*>(cand), cand_count, surv_cap, T,
+                                                    ix->Lt, ix->Eu, ix->unorm, ix->uid, ix->m_nz, ix->kmax, p.l_exact,
+                                                    p.cband, ix->gamma, bitmap, words, resc, resc_count, stats, st_yes,
+                                                    ix->dev_timeout);
+  }
+  SAH_CUDA(cudaGetLastError());
+  if (launches) *launches += 1;
   SAH_TRY(launch_pair_rescore(ix, resc, resc_count, surv_cap, Qd, qn, kk, bitmap, words, surv, surv_count, stats,
-                               st_yes, st_fp64, nq, sms, st));
+                               st_yes, st_fp64, nq, sms, st, kept_mask, mask_words));
   SAH_CUDA(cudaGetLastError());
   if (launches) *launches += 1;
   return SAH_OK;
