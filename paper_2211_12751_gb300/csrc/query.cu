@@ -872,7 +872,8 @@ WsLayout layout_for(const Index* ix, int qb) {
   const bool tc_pass = ix->nb > 0 && ix->dk > 0 && ix->prm.tc_user_pass && ix->m_nz > 0;
   L.pairs = take(tc_pass ? 0 : sizeof(PairEntry) * (size_t)std::max(ix->nb, 1) * qb);
   L.pcount = take(sizeof(int32_t) * std::max(ix->nb, 1));
-  L.kmask = take(sizeof(uint32_t) * (size_t)std::max(ix->nb, 1) * ((qb + 31) / 32));
+  // kept bits per (leaf, row), then one flag per leaf (the tensor-core block filter's)
+  L.kmask = take(sizeof(uint32_t) * (size_t)std::max(ix->nb, 1) * ((qb + 31) / 32) + sizeof(int32_t) * std::max(ix->nb, 1));
   L.coltab = take(user_pass_tc_scratch_bytes(qb, ix->dp));
   L.chunk = take(sizeof(int32_t) * ((size_t)qb * (2 * (answer_words(answer_stride(ix->m)) / 32) + 1)));
   // the control block, contiguous so that one memset clears its counters (and, with the

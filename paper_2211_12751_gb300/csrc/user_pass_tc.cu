@@ -300,133 +300,174 @@ column_table_kernel(const float* __restrict__ Qd, const float* __restrict__ qn, 
 }
 
 // A3 over the columns: Lemma 2 for every (leaf, distinct query vector) pair, then the bound
-// compared with L^k(B) for each row of the column.  A CTA takes kFilterLeaves consecutive
-// leaves (centres, cone angles and lower bounds staged in shared memory) and a thread a
-// column, which it tests against each leaf in turn; the column vectors come from the
-// column table's transposed copy, so that a warp's loads of a 16-byte word of 32 columns
-// coalesce, and the (j, k) of the rows are staged in shared memory.  The leaf's decisions
-// go to kept_mask[B] (bit j of word j / 32), as the row-wise block filter writes them.  The
-// arithmetic of the bound is the row-wise kernel's.
-constexpr int kFilterLeaves = 4;
-constexpr int kFilterRows = 1024;   // rows staged in shared memory (the rest read from memory)
-
-__global__ void __launch_bounds__(128)
+// compared with L^k(B) for each row of the column.  The <c_B, q> of all pairs are a small
+// GEMM (leaf centres x query columns): a CTA takes kBfLeaves leaves and runs over every
+// chunk of kBfChunk columns in tiles of kBfCols, K in chunks of kBfK dimensions staged in
+// shared memory, each thread accumulating 2 leaves x 4 columns in registers.  With cos phi = <c_B, q> / ||q||
+// (c_B a unit vector) and the additive slack covering the FP32 dot and the stored cone:
+//   ub = ||q|| (1 + slack)                                  if cos phi >= cos omega - slack
+//   ub = ||q|| (cos phi cos omega + s_up sin omega + 2 slack)  otherwise,
+// with s_up = sqrt(1 - (|cos phi| - slack)_+^2) >= sin phi.  A row (j, k) of the column is
+// kept unless ub < L^k(B).  The leaf's decisions are OR-ed into kept_mask[B] (bit j of word
+// j / 32; zeroed before the launch), the 128-user tiles of every leaf with a kept row are
+// flagged for the user pass, and leaf_flag[B] (zeroed too) counts a leaf's users once.
+constexpr int kBfLeaves = 32;
+constexpr int kBfCols = 64;
+constexpr int kBfK = 32;
+constexpr int kBfChunk = 256;   // columns per CTA
+constexpr int kBfRows = 1024;   // rows of the CTA's columns staged in shared memory (more: from memory)
+__global__ void __launch_bounds__(256)
 block_filter_cols_kernel(const float* __restrict__ bcent, const float* __restrict__ bcos,
                          const float* __restrict__ bsin, const float* __restrict__ LB, int nb, int kmax, int dp,
                          int nq, ColTable T, float slack, uint32_t* __restrict__ kept_mask, int mask_words,
                          const int32_t* __restrict__ bstart, uint8_t* __restrict__ tile_need,
-                         unsigned long long* __restrict__ stats, int st_pairs, int st_users, int st_scored) {
-  extern __shared__ float4 cen[];   // [kFilterLeaves][dp / 4] the leaves' unit centres
-  __shared__ int2 rs[kFilterRows];   // (j, k) of the rows
-  __shared__ uint32_t kbits[kFilterLeaves][kMaxRows / 32];
-  __shared__ float lbs[kFilterLeaves][65];   // the leaves' lower bounds L^k(B), k = 1..64
-  __shared__ float cws[kFilterLeaves], sws[kFilterLeaves];
-  __shared__ int kept_sh[kFilterLeaves];
+                         int32_t* __restrict__ leaf_flag, unsigned long long* __restrict__ stats, int st_pairs,
+                         int st_users, int st_scored) {
+  __shared__ __align__(16) float As[kBfK][kBfLeaves];   // centres, dimension-major
+  __shared__ __align__(16) float Bs[kBfK][kBfCols];     // columns, dimension-major
+  __shared__ uint32_t kbits[kBfLeaves][kMaxRows / 32];
+  __shared__ float lbs[kBfLeaves][65];                  // L^k(B), k = 1..64
+  __shared__ float cws[kBfLeaves], sws[kBfLeaves];
+  __shared__ int kept_sh[kBfLeaves];
+  __shared__ float cqn[kBfChunk];           // the CTA's columns: ||q||
+  __shared__ int cst[kBfChunk + 1];         // their rows: cst[c] .. cst[c + 1] (relative to the first)
+  __shared__ int2 crw[kBfRows];             // (j, k) of those rows
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int B0 = blockIdx.x * kBfLeaves;
+  const int nl = min(kBfLeaves, nb - B0);
+  const int ncol_all = *T.ncol;
+  const int cbeg = blockIdx.y * kBfChunk;
+  if (cbeg >= ncol_all) return;
+  const int ncol = min(ncol_all, cbeg + kBfChunk);   // columns [cbeg, ncol)
   const int dp4 = dp / 4;
-  const int B0 = blockIdx.x * kFilterLeaves;
-  const int nl = min(kFilterLeaves, nb - B0);
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int ncol = *T.ncol;
-  const int nrows = T.start[ncol];
-  const float4* cg = reinterpret_cast<const float4*>(bcent + (int64_t)B0 * dp);
-  for (int i = tid; i < nl * dp4; i += nt) cen[i] = cg[i];
   const int k64 = min(kmax, 64);
-  for (int i = tid; i < nl * k64; i += nt) {
+  const int rbase = T.start[cbeg];
+  for (int c = tid; c <= ncol - cbeg; c += 256) {
+    cst[c] = T.start[cbeg + c] - rbase;
+    if (c < ncol - cbeg) cqn[c] = T.qnc[cbeg + c];
+  }
+  const int nrw = T.start[ncol] - rbase;
+  for (int q = tid; q < min(nrw, kBfRows); q += 256) {
+    const int4 rw = T.rows[rbase + q];
+    crw[q] = make_int2(rw.x & 0x3fffffff, rw.y);
+  }
+  for (int i = tid; i < nl * k64; i += 256) {
     const int k = i / nl + 1, l = i - (k - 1) * nl;   // consecutive threads, consecutive leaves
     lbs[l][k] = LB[(int64_t)(k - 1) * nb + B0 + l];
   }
-  for (int q = tid; q < min(nrows, kFilterRows); q += nt) {
-    const int4 rw = T.rows[q];
-    rs[q] = make_int2(rw.x & 0x3fffffff, rw.y);
-  }
-  for (int i = tid; i < nl * mask_words; i += nt) kbits[i / mask_words][i % mask_words] = 0u;
-  if (tid < nl) {
-    cws[tid] = bcos[B0 + tid];
-    sws[tid] = bsin[B0 + tid];
+  for (int i = tid; i < kBfLeaves * mask_words; i += 256) kbits[i / mask_words][i % mask_words] = 0u;
+  if (tid < kBfLeaves) {
+    cws[tid] = tid < nl ? bcos[B0 + tid] : -2.f;
+    sws[tid] = tid < nl ? bsin[B0 + tid] : 0.f;
     kept_sh[tid] = 0;
   }
-  __syncthreads();
-  int kept[kFilterLeaves] = {};
-  for (int c = tid; c < ncol; c += nt) {
-    const float nrm = T.qnc[c];
-    const int r0 = T.start[c], r1 = T.start[c + 1];
-    const float4* qc = T.qt + c;   // word i at qc[i * nq]
-#pragma unroll
-    for (int l = 0; l < kFilterLeaves; ++l) {
-      if (l >= nl) break;
-      const float cw = cws[l], sw = sws[l];
-      const float4* cl = cen + l * dp4;
-      float ub = INFINITY;   // no cone bound: every row kept
-      if (!(cw < -1.5f) && nrm > 0.f) {
-        float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
-#pragma unroll 4
-        for (int i = 0; i < dp4; ++i) {
-          const float4 a = cl[i], b = __ldg(qc + (int64_t)i * nq);
-          d0 = fmaf(a.x, b.x, d0);
-          d1 = fmaf(a.y, b.y, d1);
-          d2 = fmaf(a.z, b.z, d2);
-          d3 = fmaf(a.w, b.w, d3);
-        }
-        const float dq = (d0 + d1) + (d2 + d3);
-        const float cphi = fminf(1.f, fmaxf(-1.f, dq / nrm));
-        float sphi;
-        if (cphi * cphi <= 0.5f) {
-          sphi = sqrtf(fmaxf(0.f, fmaf(-cphi, cphi, 1.f)));
-        } else {
-          float o2 = 0.f;
-          for (int i = 0; i < dp4; ++i) {
-            const float4 a = cl[i], b = __ldg(qc + (int64_t)i * nq);
-            float o;
-            o = fmaf(-dq, a.x, b.x); o2 = fmaf(o, o, o2);
-            o = fmaf(-dq, a.y, b.y); o2 = fmaf(o, o, o2);
-            o = fmaf(-dq, a.z, b.z); o2 = fmaf(o, o, o2);
-            o = fmaf(-dq, a.w, b.w); o2 = fmaf(o, o, o2);
-          }
-          sphi = fminf(1.f, sqrtf(o2) / nrm);
-        }
-        if (cphi >= cw - slack) ub = nrm * (1.f + slack);
-        else ub = nrm * (fmaf(cphi, cw, sphi * sw) + 2.f * slack);
+  int kept[2] = {0, 0};
+  for (int col0 = cbeg; col0 < ncol; col0 += kBfCols) {
+    float acc[2][4] = {};
+    for (int k0 = 0; k0 < dp; k0 += kBfK) {
+      __syncthreads();
+      // centres: 16-byte words (4 dimensions) of kBfLeaves rows; consecutive threads take
+      // consecutive leaves, so that the transposed stores hit distinct banks
+      for (int i = tid; i < kBfLeaves * (kBfK / 4); i += 256) {
+        const int l = i % kBfLeaves, w = i / kBfLeaves;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (l < nl && k0 + 4 * w < dp) v = *reinterpret_cast<const float4*>(bcent + (int64_t)(B0 + l) * dp + k0 + 4 * w);
+        As[4 * w][l] = v.x;
+        As[4 * w + 1][l] = v.y;
+        As[4 * w + 2][l] = v.z;
+        As[4 * w + 3][l] = v.w;
       }
-      for (int q = r0; q < r1; ++q) {
-        int2 jk;
-        if (q < kFilterRows) {
-          jk = rs[q];
-        } else {
-          const int4 rw = T.rows[q];
-          jk = make_int2(rw.x & 0x3fffffff, rw.y);
+      // columns: word w (4 dimensions) of column c from the transposed copy (coalesced)
+      for (int i = tid; i < (kBfK / 4) * kBfCols; i += 256) {
+        const int w = i / kBfCols, c = i % kBfCols;
+        const int wg = k0 / 4 + w;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (col0 + c < ncol && wg < dp4) v = T.qt[(int64_t)wg * nq + col0 + c];
+        Bs[4 * w][c] = v.x;
+        Bs[4 * w + 1][c] = v.y;
+        Bs[4 * w + 2][c] = v.z;
+        Bs[4 * w + 3][c] = v.w;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int k = 0; k < kBfK; ++k) {
+        const float2 a = *reinterpret_cast<const float2*>(&As[k][2 * ty]);
+        const float4 b = *reinterpret_cast<const float4*>(&Bs[k][4 * tx]);
+        acc[0][0] = fmaf(a.x, b.x, acc[0][0]);
+        acc[0][1] = fmaf(a.x, b.y, acc[0][1]);
+        acc[0][2] = fmaf(a.x, b.z, acc[0][2]);
+        acc[0][3] = fmaf(a.x, b.w, acc[0][3]);
+        acc[1][0] = fmaf(a.y, b.x, acc[1][0]);
+        acc[1][1] = fmaf(a.y, b.y, acc[1][1]);
+        acc[1][2] = fmaf(a.y, b.z, acc[1][2]);
+        acc[1][3] = fmaf(a.y, b.w, acc[1][3]);
+      }
+    }
+    // Lemma 2 for the thread's 8 (leaf, column) pairs, then the column's rows
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      const int l = 2 * ty + a;
+      if (l >= nl) continue;
+      const float cw = cws[l], sw = sws[l];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int c = col0 + 4 * tx + b;
+        if (c >= ncol) continue;
+        const float nrm = cqn[c - cbeg];
+        float ub = INFINITY;   // no cone bound: every row kept
+        if (!(cw < -1.5f) && nrm > 0.f) {
+          const float cphi = fminf(1.f, fmaxf(-1.f, acc[a][b] / nrm));
+          const float cl = fmaxf(0.f, fabsf(cphi) - slack);
+          const float sphi = sqrtf(fmaxf(0.f, fmaf(-cl, cl, 1.f)));
+          if (cphi >= cw - slack) ub = nrm * (1.f + slack);
+          else ub = nrm * (fmaf(cphi, cw, sphi * sw) + 2.f * slack);
         }
-        const int j = jk.x, k = jk.y;
-        const float lb = (k <= kmax) ? (k <= 64 ? lbs[l][k] : LB[(int64_t)(k - 1) * nb + B0 + l]) : -INFINITY;
-        if (!(ub < lb)) {
-          atomicOr(&kbits[l][j >> 5], 1u << (j & 31));
-          ++kept[l];
+        const int r0 = cst[c - cbeg], r1 = cst[c - cbeg + 1];
+        for (int q = r0; q < r1; ++q) {
+          int2 jk;
+          if (q < kBfRows) {
+            jk = crw[q];
+          } else {
+            const int4 rw = T.rows[rbase + q];
+            jk = make_int2(rw.x & 0x3fffffff, rw.y);
+          }
+          const int j = jk.x, k = jk.y;
+          const float lb = (k <= kmax) ? (k <= 64 ? lbs[l][k] : LB[(int64_t)(k - 1) * nb + B0 + l]) : -INFINITY;
+          if (!(ub < lb)) {
+            atomicOr(&kbits[l][j >> 5], 1u << (j & 31));
+            ++kept[a];
+          }
         }
       }
     }
   }
 #pragma unroll
-  for (int l = 0; l < kFilterLeaves; ++l) {
-    const int v = __reduce_add_sync(0xffffffffu, kept[l]);
-    if ((tid & 31) == 0 && v) atomicAdd(&kept_sh[l], v);
-  }
+  for (int a = 0; a < 2; ++a)
+    if (kept[a]) atomicAdd(&kept_sh[2 * ty + a], kept[a]);
   __syncthreads();
-  for (int i = tid; i < nl * mask_words; i += nt)
-    kept_mask[(int64_t)B0 * mask_words + i] = kbits[i / mask_words][i % mask_words];
+  for (int i = tid; i < nl * mask_words; i += 256) {
+    const uint32_t w = kbits[i / mask_words][i % mask_words];
+    if (w) atomicOr(&kept_mask[(int64_t)B0 * mask_words + i], w);
+  }
   // the user pass streams the 128-user tiles that hold a user of a leaf with a kept row
   if (tid < nl && kept_sh[tid] > 0) {
     const int t0 = bstart[B0 + tid] / kUM, t1 = (bstart[B0 + tid + 1] - 1) / kUM;
     for (int t = t0; t <= t1; ++t) tile_need[t] = 1;
   }
-  if (tid == 0) {
+  if (tid < 32) {
     unsigned long long pairs = 0, users = 0, scored = 0;
-    for (int l = 0; l < nl; ++l) {
-      if (!kept_sh[l]) continue;
-      const unsigned long long u = (unsigned long long)(bstart[B0 + l + 1] - bstart[B0 + l]);
-      pairs += kept_sh[l];
-      users += u;
-      scored += (unsigned long long)kept_sh[l] * u;
+    if (tid < nl && kept_sh[tid]) {
+      const unsigned long long u = (unsigned long long)(bstart[B0 + tid + 1] - bstart[B0 + tid]);
+      pairs = kept_sh[tid];
+      scored = (unsigned long long)kept_sh[tid] * u;
+      if (atomicExch(&leaf_flag[B0 + tid], 1) == 0) users = u;   // the leaf's users, once
     }
-    if (pairs) {
+    for (int o = 16; o > 0; o >>= 1) {
+      pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+      users += __shfl_xor_sync(0xffffffffu, users, o);
+      scored += __shfl_xor_sync(0xffffffffu, scored, o);
+    }
+    if (tid == 0 && pairs) {
       atomicAdd(&stats[st_pairs], pairs);
       atomicAdd(&stats[st_users], users);
       atomicAdd(&stats[st_scored], scored);
@@ -1240,10 +1281,13 @@ sah_status block_filter_tc(Index* ix, void* scratch, int nq, uint32_t* kept_mask
                            cudaStream_t st) {
   if (ix->nb == 0 || nq == 0) return SAH_OK;
   const ColTable T = col_table_at(scratch, nq);
-  block_filter_cols_kernel<<<(ix->nb + kFilterLeaves - 1) / kFilterLeaves, 128,
-                             sizeof(float) * ix->dp * kFilterLeaves, st>>>(
-      ix->bcent, ix->bcos, ix->bsin, ix->LB, ix->nb, ix->kmax, ix->dp, nq, T, ix->cone_slack, kept_mask, mask_words,
-      ix->bstart, tile_need, stats, st_pairs, st_users, st_scored);
+  // the kept bits and the leaf flags after them are OR-ed / set by the CTAs of every column chunk
+  int32_t* leaf_flag = reinterpret_cast<int32_t*>(kept_mask + (size_t)ix->nb * mask_words);
+  SAH_CUDA(cudaMemsetAsync(kept_mask, 0, sizeof(uint32_t) * (size_t)ix->nb * mask_words + sizeof(int32_t) * ix->nb, st));
+  const dim3 grid((unsigned)((ix->nb + kBfLeaves - 1) / kBfLeaves), (unsigned)((nq + kBfChunk - 1) / kBfChunk));
+  block_filter_cols_kernel<<<grid, 256, 0, st>>>(ix->bcent, ix->bcos, ix->bsin, ix->LB, ix->nb, ix->kmax, ix->dp, nq, T,
+                                                 ix->cone_slack, kept_mask, mask_words, ix->bstart, tile_need,
+                                                 leaf_flag, stats, st_pairs, st_users, st_scored);
   SAH_CUDA(cudaGetLastError());
   return SAH_OK;
 }
