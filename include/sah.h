@@ -78,7 +78,16 @@ typedef struct {
                            epilogue applies the bound tests of Alg. 5 to the pairs of the leaves
                            Lemma 2 kept; 0 runs Lemma 3 and FP32 dot products on the CUDA cores.
                            Results are identical; only the speed differs. */
+  int32_t blocking;     /* sah_blocking: how users are grouped into blocks.  SAH_BLOCK_CONE (0,
+                           default): Cone-Tree leaves (Alg. 3) with the cone bounds of Lemma 2
+                           and Lemma 3.  SAH_BLOCK_NORM (1): Simpfer's norm-based blocking, the
+                           ablation the paper calls SA-Simpfer (Experiments, ablation study):
+                           users in descending norm order cut into runs of leaf_size, each
+                           block and user bounded by Cauchy-Schwarz alone (||q|| for a unit
+                           user).  Results are identical; only the pruning differs. */
 } sah_params;
+
+typedef enum { SAH_BLOCK_CONE = 0, SAH_BLOCK_NORM = 1 } sah_blocking;
 
 /* Fills *p with the paper's parameters (k_max 50, N_0 20, b 0.5, K 128) and the build's
  * defaults for the rest (code_bits 16, p_prime 4 * k_max, FP32, probe radius 0, seed 0,
@@ -182,6 +191,8 @@ typedef struct {
   double build_gemm_ms;         /* index build, |P'| = n with SAH_BF16: the tcgen05 GEMM's time */
   int64_t build_overflow_rows;  /* users of that GEMM whose candidate list overflowed */
   int64_t pairs_rescored;       /* pairs the tensor-core user pass left to the FP32 re-score */
+  int64_t tc_scores;            /* (user, distinct query vector) scores the tensor-core user pass computed */
+  int64_t block_col_pairs;      /* (leaf, distinct query vector) pairs of the tensor-core block filter */
 } sah_stats;
 
 sah_status sah_index_stats(const sah_index* index, sah_stats* out);

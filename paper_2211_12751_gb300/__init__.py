@@ -24,6 +24,7 @@ SAH_ERR_BUFFER_TOO_SMALL, SAH_ERR_DEVICE_TIMEOUT, SAH_ERR_BUSY, SAH_ERR_UNSUPPOR
 EXACT, SAALSH = 0, 1
 INJECT_USER_PASS, INJECT_VERIFY = 1, 2
 FP32, BF16, FP8 = 0, 1, 2
+BLOCK_CONE, BLOCK_NORM = 0, 1   # sah_blocking: Cone-Tree leaves, or Simpfer's norm-sorted blocks
 
 _lib = None
 
@@ -47,6 +48,7 @@ class Params(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("srp", ctypes.c_void_p),
         ("tc_user_pass", ctypes.c_int32),
+        ("blocking", ctypes.c_int32),
     ]
 
 
@@ -57,7 +59,7 @@ class Stats(ctypes.Structure):
         "survivors", "fp64_rescored", "results", "users_in_kept_blocks", "items_scanned")] + [
         ("stage_ms", ctypes.c_double * 8), ("stage_launches", ctypes.c_int64 * 8),
         ("build_gemm_ms", ctypes.c_double), ("build_overflow_rows", ctypes.c_int64),
-        ("pairs_rescored", ctypes.c_int64)]
+        ("pairs_rescored", ctypes.c_int64), ("tc_scores", ctypes.c_int64), ("block_col_pairs", ctypes.c_int64)]
 
     def as_dict(self):
         out = {}

@@ -124,6 +124,7 @@ void sah_default_params(sah_params* p) {
   p->seed = 0;
   p->srp = nullptr;
   p->tc_user_pass = 1;
+  p->blocking = SAH_BLOCK_CONE;
 }
 
 const char* sah_status_string(sah_status s) {
@@ -159,7 +160,8 @@ sah_status sah_build_index(const float* U, int64_t m, const float* P, int64_t n,
   }
   if (prm.k_max < 1 || prm.k_max > sah::kMaxKmax || prm.leaf_size < 1 || prm.leaf_size > sah::kMaxLeaf ||
       !(prm.b > 0.f && prm.b < 1.f) || prm.n_tables < 1 || prm.code_bits < 1 || prm.code_bits > 16 ||
-      prm.probe_radius < 0 || prm.probe_radius > prm.code_bits) {
+      prm.probe_radius < 0 || prm.probe_radius > prm.code_bits ||
+      (prm.blocking != SAH_BLOCK_CONE && prm.blocking != SAH_BLOCK_NORM)) {
     sah::set_error("sah_build_index: parameter out of range");
     return SAH_ERR_ARG;
   }

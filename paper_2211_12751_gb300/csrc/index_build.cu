@@ -192,14 +192,29 @@ __global__ void ct_scatter_kernel(const int32_t* __restrict__ perm, const CtTile
 // member's cos/sin theta_u to it (sin from the orthogonal component, which stays accurate
 // near theta = 0), and omega = max theta_u.  A zero centre marks the block with
 // bcos = -2 (no cone bound for it or its users).
+// norm_blocks (Simpfer's blocking): no cone at all; the block is given omega = pi around a
+// zero centre and every user theta_u = pi/2, so that Lemma 2 and Lemma 3 both reduce to
+// Cauchy-Schwarz, ||q|| for a unit user (cos phi = <0, q> = 0 and cos(phi - theta_u) = 1).
 __global__ void leaf_stats_kernel(const float* __restrict__ Uh, int dp, const int32_t* __restrict__ bstart,
                                   float* __restrict__ bcent, float* __restrict__ bcos, float* __restrict__ bsin,
-                                  float* __restrict__ ucos, float* __restrict__ usin) {
+                                  float* __restrict__ ucos, float* __restrict__ usin, int norm_blocks) {
   extern __shared__ float cs[];   // dp floats
   __shared__ float red[32];
   __shared__ unsigned long long best;
   int B = blockIdx.x;
   int s = bstart[B], e = bstart[B + 1], cnt = e - s;
+  if (norm_blocks) {
+    for (int i = threadIdx.x; i < dp; i += blockDim.x) bcent[(int64_t)B * dp + i] = 0.f;
+    for (int r = s + threadIdx.x; r < e; r += blockDim.x) {
+      ucos[r] = 0.f;
+      usin[r] = 1.f;
+    }
+    if (threadIdx.x == 0) {
+      bcos[B] = -1.f;
+      bsin[B] = 0.f;
+    }
+    return;
+  }
   for (int i = threadIdx.x; i < dp; i += blockDim.x) {
     float acc = 0.f;
     for (int r = s; r < e; ++r) acc += Uh[(int64_t)r * dp + i];
@@ -548,8 +563,21 @@ sah_status build_index_device(Index* ix, const float* U_dev, const float* P_dev,
   const int N0 = ix->prm.leaf_size;
   const uint64_t seed_mix = splitmix64(ix->prm.seed);
   std::vector<Seg> leaves, active;
-  Seg root{0, (int32_t)mz, 1ull};
-  (root.len > N0 ? active : leaves).push_back(root);
+  const bool norm_blocks = ix->prm.blocking == SAH_BLOCK_NORM;
+  if (norm_blocks) {
+    // Simpfer's blocks: the users in descending norm order (ties: lower id first), cut into
+    // consecutive runs of N0
+    std::vector<int32_t> id(mz);
+    std::iota(id.begin(), id.end(), 0);
+    std::stable_sort(id.begin(), id.end(), [&](int32_t a, int32_t b) { return un_h[nz[a]] > un_h[nz[b]]; });
+    SAH_CUDA(cudaMemcpyAsync(perm, id.data(), sizeof(int32_t) * mz, cudaMemcpyHostToDevice, st));
+    SAH_CUDA(cudaStreamSynchronize(st));
+    for (int64_t s0 = 0; s0 < mz; s0 += N0)
+      leaves.push_back(Seg{(int32_t)s0, (int32_t)std::min<int64_t>(N0, mz - s0), 0ull});
+  } else {
+    Seg root{0, (int32_t)mz, 1ull};
+    (root.len > N0 ? active : leaves).push_back(root);
+  }
   // scratch sized for the largest level: at most mz / kTile + #segments tiles
   const int64_t max_tiles = mz / kTile + mz / (N0 + 1) + 2;
   const int64_t max_segs = mz / (N0 + 1) + 2;
@@ -678,7 +706,7 @@ sah_status build_index_device(Index* ix, const float* U_dev, const float* P_dev,
   SAH_TRY(dev_alloc(ix, (void**)&ix->bcos, sizeof(float) * ix->nb));
   SAH_TRY(dev_alloc(ix, (void**)&ix->bsin, sizeof(float) * ix->nb));
   leaf_stats_kernel<<<ix->nb, 256, sizeof(float) * dp, st>>>(Uh_t, dp, ix->bstart, ix->bcent, ix->bcos,
-                                                             ix->bsin, ix->ucos, ix->usin);
+                                                             ix->bsin, ix->ucos, ix->usin, norm_blocks ? 1 : 0);
   SAH_CUDA(cudaGetLastError());
   SAH_TRY(dev_alloc(ix, (void**)&ix->ublock, sizeof(int32_t) * mz));
   user_block_kernel<<<ix->nb, 256, 0, st>>>(ix->bstart, ix->nb, ix->ublock);

@@ -18,6 +18,7 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "sah_internal.cuh"
 
@@ -41,6 +42,8 @@ enum StatSlot {
   ST_BAD_Q,
   ST_BAD_K,
   ST_EMIT_OVERFLOW,
+  ST_TC_SCORES,      // (user, column) scores of the tensor-core user pass
+  ST_BF_COLPAIRS,    // (leaf, distinct column) pairs of the tensor-core block filter
   ST_COUNT
 };
 
@@ -918,6 +921,11 @@ sah_status ensure_surv(CallCtx* cx, int64_t cap, cudaStream_t st) {
   return ensure_buf(&cx->surv, (3 * sizeof(Survivor) + 144) * (size_t)std::max<int64_t>(cap, 1), st);
 }
 
+// Captures (begin, enqueue, end, instantiate) never overlap in one process: the server's
+// workers each own a context and may replay their graphs concurrently, but one capture at a
+// time.  Replays and direct launch sequences of other threads are not held up.
+std::mutex g_capture_mu;
+
 // Runs a sub-batch's launch sequence (enqueue) for the given key of shapes and buffers: the
 // first time directly, the second time captured into a CUDA graph, which later calls with
 // the same key replay as one launch.  A capture that fails (an operation that cannot be
@@ -947,6 +955,7 @@ sah_status run_captured(CallCtx* cx, const std::vector<uint64_t>& key, F&& enque
   e->last_use = cx->graph_clock;
   if (e->bad) return enqueue();
   if (!e->exec) {
+    std::lock_guard<std::mutex> lk(g_capture_mu);
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
       cudaGetLastError();
@@ -1152,7 +1161,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
             SAH_TRY(prepare_user_pass_tc(ix, Qd, qn, (const uint64_t*)(w + L.qh), w + L.coltab, kk, modes_q, nqb,
                                          st, &bf_launches));
             SAH_TRY(block_filter_tc(ix, w + L.coltab, nqb, kmask, mask_words, (uint8_t*)(w + L.tneed), stats,
-                                    ST_PAIRS_KEPT, ST_KEPT_USERS, ST_USERS_SCORED, st));
+                                    ST_PAIRS_KEPT, ST_KEPT_USERS, ST_USERS_SCORED, ST_BF_COLPAIRS, st));
           } else {
             block_filter_kernel<<<ix->nb, 128, sizeof(float) * ix->dp, st>>>(
                 ix->bcent, ix->bcos, ix->bsin, ix->LB, ix->nb, ix->kmax, ix->n, ix->dp, Qd, qn, kk, nqb,
@@ -1171,7 +1180,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
             SAH_TRY(run_user_pass_tc(ix, Qd, (uint16_t*)(w + L.qb), w + L.coltab, qn, kk, nqb, kmask,
                                      mask_words, (uint8_t*)(w + L.tneed), bitmap, words, surv + 2 * surv_cap,
                                      survcnt + 2, surv + 3 * surv_cap, survcnt + 3, surv, survcnt, surv_cap, stats,
-                                     ST_YES_EARLY, ST_FP64, st,
+                                     ST_YES_EARLY, ST_FP64, ST_TC_SCORES, st,
                                      &up_launches, tm.slot(6)));
           } else if (reg_variant) {
             const size_t smem = (size_t)16 * kQChunk * dp4 + sizeof(PairInfo) * kQChunk + sizeof(float) * 64 * threads;
@@ -1337,6 +1346,8 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
       cx->bm_clean_bytes = bm_bytes;
       agg.survivors += (int64_t)(ns2[0] + ns2[1]);
       agg.pairs_rescored += (int64_t)ns2[2];
+      agg.tc_scores += (int64_t)st_h[ST_TC_SCORES];
+      agg.block_col_pairs += (int64_t)st_h[ST_BF_COLPAIRS];
       // the next call starts from the largest list of this call's sub-batches (twice it)
       surv_call_max = std::max(surv_call_max, nsmax);
       cx->surv_hint = std::max<int64_t>(1 << 16, 2 * surv_call_max);

@@ -70,7 +70,7 @@ struct CallCtx {
   size_t pin_bytes = 0;
   std::vector<GraphEntry> graphs;
   uint64_t graph_clock = 0;
-  bool graphs_allowed = false;   // the index's own context; the server's workers run directly
+  bool graphs_allowed = false;   // set for the index's own context and for each server worker's
   // the answer bitmaps sit at the start of ws; this many bytes of it are known to be zero
   // (the emit pass clears what it reads), valid while ws.base equals bm_clean_base
   void* bm_clean_base = nullptr;
@@ -298,15 +298,15 @@ size_t user_pass_tc_scratch_bytes(int nq, int dp);
 sah_status prepare_user_pass_tc(Index* ix, const float* Qd, const float* qn, const uint64_t* qh, void* scratch,
                                 const int32_t* kk, const int32_t* modes, int nq, cudaStream_t st, int* launches);
 sah_status block_filter_tc(Index* ix, void* scratch, int nq, uint32_t* kept_mask, int mask_words, uint8_t* tile_need,
-                           unsigned long long* stats, int st_pairs, int st_users, int st_scored,
+                           unsigned long long* stats, int st_pairs, int st_users, int st_scored, int st_colpairs,
                            cudaStream_t st);
 sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* scratch, const float* qn,
                             const int32_t* kk, int nq, const uint32_t* kept_mask, int mask_words, uint8_t* tile_need,
                             uint32_t* bitmap, int64_t words, Survivor* resc, unsigned long long* resc_count,
                             Survivor* cand, unsigned long long* cand_count,
                             Survivor* surv, unsigned long long* surv_count, int64_t surv_cap,
-                            unsigned long long* stats, int st_yes, int st_fp64, cudaStream_t st, int* launches,
-                            const cudaEvent_t* ev = nullptr);   // ev: begin / end of the GEMM kernel
+                            unsigned long long* stats, int st_yes, int st_fp64, int st_scores, cudaStream_t st,
+                            int* launches, const cudaEvent_t* ev = nullptr);   // ev: begin / end of the GEMM kernel
 // topk_tc.cu: the 64 largest FP32 scores of every user over all items, through tcgen05
 sah_status topk_full_tc(Index* ix, float* vlast, int32_t* ids64, cudaStream_t st, double* gemm_ms);
 // verify_tc.cu

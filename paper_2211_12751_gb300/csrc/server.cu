@@ -184,6 +184,7 @@ sah_status sah_server_start(sah_index* index, int32_t max_slots, int32_t max_bat
   cudaSetDevice(s->device);
   for (int i = 0; i < workers; ++i) {
     auto* w = new Worker();
+    w->ctx.graphs_allowed = true;   // a repeated batch shape replays its captured graph
     bool ok = cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) == cudaSuccess &&
               cudaMallocHost((void**)&w->q_h, sizeof(float) * (size_t)max_batch * ix->d) == cudaSuccess &&
               cudaMallocHost((void**)&w->km_h, sizeof(int32_t) * 2 * (size_t)max_batch) == cudaSuccess &&

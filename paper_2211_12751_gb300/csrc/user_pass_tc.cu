@@ -322,7 +322,7 @@ block_filter_cols_kernel(const float* __restrict__ bcent, const float* __restric
                          int nq, ColTable T, float slack, uint32_t* __restrict__ kept_mask, int mask_words,
                          const int32_t* __restrict__ bstart, uint8_t* __restrict__ tile_need,
                          int32_t* __restrict__ leaf_flag, unsigned long long* __restrict__ stats, int st_pairs,
-                         int st_users, int st_scored) {
+                         int st_users, int st_scored, int st_colpairs) {
   __shared__ __align__(16) float As[kBfK][kBfLeaves];   // centres, dimension-major
   __shared__ __align__(16) float Bs[kBfK][kBfCols];     // columns, dimension-major
   __shared__ uint32_t kbits[kBfLeaves][kMaxRows / 32];
@@ -454,6 +454,7 @@ block_filter_cols_kernel(const float* __restrict__ bcent, const float* __restric
     const int t0 = bstart[B0 + tid] / kUM, t1 = (bstart[B0 + tid + 1] - 1) / kUM;
     for (int t = t0; t <= t1; ++t) tile_need[t] = 1;
   }
+  if (tid == 0) atomicAdd(&stats[st_colpairs], (unsigned long long)nl * (unsigned long long)(ncol - cbeg));
   if (tid < 32) {
     unsigned long long pairs = 0, users = 0, scored = 0;
     if (tid < nl && kept_sh[tid]) {
@@ -504,6 +505,7 @@ struct UpParams {
   unsigned long long* cand_count;
   unsigned long long* stats;
   int st_yes;
+  int st_scores;               // stats slot: (user, column) scores computed
   int* timeout;
   int inject_stall;            // test hook: the MMA thread stops after its first tile
   int nring;                   // entries of the bound ring (3..kRingMax)
@@ -694,6 +696,15 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
       cnt += __popc(m);
     }
     if (lane == 0) ntl_sh = cnt < kMaxTileList ? cnt : kMaxTileList;
+    // the users of the needed tiles times the columns: the scores this CTA computes
+    __syncwarp();
+    unsigned long long users = 0;
+    for (int i = lane; i < min(cnt, kMaxTileList); i += 32) {
+      const int64_t left = p.mz - (int64_t)tlist[i] * kUM;
+      users += (unsigned long long)(left < kUM ? left : kUM);
+    }
+    for (int o = 16; o > 0; o >>= 1) users += __shfl_xor_sync(0xffffffffu, users, o);
+    if (lane == 0 && users) atomicAdd(&p.stats[p.st_scores], users * (unsigned long long)(*p.T.ncol));
   }
   const int ncol = *p.T.ncol;
   int it_base = 0;     // tiles of earlier sets (the stages' running index)
@@ -1277,7 +1288,7 @@ sah_status prepare_user_pass_tc(Index* ix, const float* Qd, const float* qn, con
 }
 
 sah_status block_filter_tc(Index* ix, void* scratch, int nq, uint32_t* kept_mask, int mask_words, uint8_t* tile_need,
-                           unsigned long long* stats, int st_pairs, int st_users, int st_scored,
+                           unsigned long long* stats, int st_pairs, int st_users, int st_scored, int st_colpairs,
                            cudaStream_t st) {
   if (ix->nb == 0 || nq == 0) return SAH_OK;
   const ColTable T = col_table_at(scratch, nq);
@@ -1287,7 +1298,7 @@ sah_status block_filter_tc(Index* ix, void* scratch, int nq, uint32_t* kept_mask
   const dim3 grid((unsigned)((ix->nb + kBfLeaves - 1) / kBfLeaves), (unsigned)((nq + kBfChunk - 1) / kBfChunk));
   block_filter_cols_kernel<<<grid, 256, 0, st>>>(ix->bcent, ix->bcos, ix->bsin, ix->LB, ix->nb, ix->kmax, ix->dp, nq, T,
                                                  ix->cone_slack, kept_mask, mask_words, ix->bstart, tile_need,
-                                                 leaf_flag, stats, st_pairs, st_users, st_scored);
+                                                 leaf_flag, stats, st_pairs, st_users, st_scored, st_colpairs);
   SAH_CUDA(cudaGetLastError());
   return SAH_OK;
 }
@@ -1297,8 +1308,8 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
                             uint32_t* bitmap, int64_t words, Survivor* resc, unsigned long long* resc_count,
                             Survivor* cand, unsigned long long* cand_count,
                             Survivor* surv, unsigned long long* surv_count, int64_t surv_cap,
-                            unsigned long long* stats, int st_yes, int st_fp64, cudaStream_t st, int* launches,
-                            const cudaEvent_t* ev) {
+                            unsigned long long* stats, int st_yes, int st_fp64, int st_scores, cudaStream_t st,
+                            int* launches, const cudaEvent_t* ev) {
   if (ix->m_nz == 0 || nq == 0 || ix->dk <= 0) return SAH_OK;
   const uint16_t* Qhi = Qsplit;
   const uint16_t* Qlo = Qsplit + (size_t)nq * ix->dk;
@@ -1339,6 +1350,7 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
   p.cand_count = cand_count;
   p.stats = stats;
   p.st_yes = st_yes;
+  p.st_scores = st_scores;
   p.timeout = ix->dev_timeout;
   p.inject_stall = ix->inject_site == SAH_INJECT_USER_PASS ? 1 : 0;
   int sms = 152;

@@ -60,7 +60,7 @@ def test_reference_arm_line_on_rank_0():
     assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
     assert d["higher_is_better"] is True and d["steps"] == 1 and d["n_gpus"] == 1
     assert d["value"] > 0
-    assert d["config"]["workload"].startswith("c2: n=17770 items, m=480000 users, d=50")
+    assert d["config"]["workload"].startswith("c5: n=1000000 items, m=2000000 users, d=128")
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
