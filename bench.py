@@ -320,7 +320,7 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- measurement on the GPU
 def make_index(sah, Ud, Pd, stream, threshold, precision="bf16", tc=1, n_tables=N_TABLES, code_bits=CODE_BITS,
-               leaf=LEAF, probe_radius=0):
+               leaf=LEAF, probe_radius=0, blocking=0):
     """Alg. 4 from device copies of U and P; returns (index, build seconds)."""
     import torch
     pp = (1 << 30) if threshold == "full" else 0
@@ -328,7 +328,7 @@ def make_index(sah, Ud, Pd, stream, threshold, precision="bf16", tc=1, n_tables=
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ix = sah.Index(Ud, Pd, k_max=50, leaf_size=leaf, p_prime=pp, seed=0, precision=prec, n_tables=n_tables,
-                   code_bits=code_bits, tc_user_pass=tc, probe_radius=probe_radius, stream=stream)
+                   code_bits=code_bits, tc_user_pass=tc, probe_radius=probe_radius, blocking=blocking, stream=stream)
     torch.cuda.synchronize()
     return ix, time.perf_counter() - t0
 
@@ -492,9 +492,9 @@ def dominant(stage_ms, roofs):
 
 
 def measure_config(sah, W, Ud, Pd, dev, stream, flush, threshold, precision, steps, warmup, peaks, peak_kind,
-                   tc=1, Q=None, K=None, modes=None):
+                   tc=1, Q=None, K=None, modes=None, blocking=0):
     """Build an index on W and time a batch (default: the workload's own requests)."""
-    ix, build_s = make_index(sah, Ud, Pd, stream, threshold, precision, tc=tc)
+    ix, build_s = make_index(sah, Ud, Pd, stream, threshold, precision, tc=tc, blocking=blocking)
     if Q is None:
         Q, K, _ = W.requests()
     b = Batch(ix, Q, K, dev, stream, modes=modes)
@@ -504,8 +504,9 @@ def measure_config(sah, W, Ud, Pd, dev, stream, flush, threshold, precision, ste
     ist = ix.stats()
     rec = {"index_build_s": build_s, "queries_per_step": len(K), "value": len(K) / (np.mean(times) / 1e3),
            "ms_per_step": float(np.mean(times)), "stages_ms": {nm: float(sms[i]) for i, nm in enumerate(STAGE_NAMES)},
-           "stage_counts": {k: st[k] for k in ("block_pairs_kept", "users_in_kept_blocks", "tc_scores", "pairs_rescored",
-                                               "survivors", "fp64_rescored", "items_scanned", "results")},
+           "stage_counts": {k: st[k] for k in ("block_pairs_total", "block_pairs_kept", "users_in_kept_blocks",
+                                               "users_scored", "tc_scores", "pairs_rescored", "survivors",
+                                               "fp64_rescored", "items_scanned", "results")},
            "rooflines": roofs}
     if ist.get("build_gemm_ms", 0) > 0:
         rec["index_gemm_ms"] = ist["build_gemm_ms"]
@@ -686,7 +687,38 @@ def run_variants(sah, dev, stream, flush, peaks, peak_kind, W5, Ud5, Pd5, steps)
                                            tc=tc)
             out[f"c2_{thr}_{prec}"] = rec2
             ix2.close()
+    out["ablation_blocking"] = blocking_ablation(sah, dev, stream, flush, peaks, peak_kind, W2, Ud2, Pd2, W5, Ud5,
+                                                 Pd5, vs)
     return out
+
+
+def blocking_ablation(sah, dev, stream, flush, peaks, peak_kind, W2, Ud2, Pd2, W5, Ud5, Pd5, vs):
+    """Cone-Tree blocks (SAH) against Simpfer's norm-sorted blocks with Cauchy-Schwarz bounds
+    (the paper's SA-Simpfer ablation, Experiments, ablation study), everything else equal:
+    exact mode with the tensor-core user pass (BF16) and with the FP32 path (where Lemma 3
+    runs per user), and SA-ALSH mode (Alg. 2 for the survivors, F1 against the exact
+    answers) on the paper's |P'|."""
+    res = {}
+    for blk, tag in ((0, "cone"), (1, "norm")):
+        for thr, prec, tc in (("full", "bf16", 1), ("paper", "bf16", 1), ("paper", "fp32", 0)):
+            ix, b, rec = measure_config(sah, W2, Ud2, Pd2, dev, stream, flush, thr, prec, vs, 2, peaks, peak_kind,
+                                        tc=tc, blocking=blk)
+            r = {k: rec[k] for k in ("value", "ms_per_step", "index_build_s", "stages_ms", "stage_counts")}
+            if thr == "paper" and prec == "bf16":
+                modes = np.full(len(b.K), sah.SAALSH, np.int32)
+                bs = Batch(ix, b.Q, b.K, dev, stream, modes=modes)
+                ts = bs.timed(vs, 2, flush)
+                f1s = [f1_sets(x, y) for x, y in zip(bs.host, b.host)]
+                r["saalsh"] = {"value": len(b.K) / (np.mean(ts) / 1e3), "ms_per_step": float(np.mean(ts)),
+                               "f1_vs_exact": float(np.mean(f1s)), "min_f1": float(np.min(f1s))}
+            res[f"c2_{thr}_{prec}_{tag}"] = r
+            ix.close()
+        ix, b, rec = measure_config(sah, W5, Ud5, Pd5, dev, stream, flush, "full", "bf16", vs, 2, peaks, peak_kind,
+                                    blocking=blk)
+        res[f"c5_full_bf16_{tag}"] = {k: rec[k] for k in ("value", "ms_per_step", "index_build_s", "stages_ms",
+                                                          "stage_counts")}
+        ix.close()
+    return res
 
 
 # ---------------------------------------------------------------- our arm

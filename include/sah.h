@@ -85,9 +85,17 @@ typedef struct {
                            users in descending norm order cut into runs of leaf_size, each
                            block and user bounded by Cauchy-Schwarz alone (||q|| for a unit
                            user).  Results are identical; only the pruning differs. */
+  int32_t transform;    /* sah_transform: the asymmetric transformation behind the SimHash codes.
+                           SAH_SAT (0, default): SA-ALSH's shifting-invariant transformation
+                           (Eq. 6, Eq. 7), items shifted by their partition's centroid c_j and
+                           padded to its radius R_j.  SAH_QNF (1): H2-ALSH's query-normalized-
+                           first transformation (Eq. 3, Eq. 4), items unshifted and padded to
+                           their partition's largest norm M_j (c_j = 0, R_j = M_j); the
+                           paper's H2-ALSH comparison.  Exact mode does not depend on it. */
 } sah_params;
 
 typedef enum { SAH_BLOCK_CONE = 0, SAH_BLOCK_NORM = 1 } sah_blocking;
+typedef enum { SAH_SAT = 0, SAH_QNF = 1 } sah_transform;
 
 /* Fills *p with the paper's parameters (k_max 50, N_0 20, b 0.5, K 128) and the build's
  * defaults for the rest (code_bits 16, p_prime 4 * k_max, FP32, probe radius 0, seed 0,
@@ -128,15 +136,34 @@ sah_status sah_rkmips_batch(sah_index* index, const float* Q, int32_t nq, const 
                             const int32_t* modes, int32_t buffers_on_device, int32_t* out_ids,
                             int64_t cap, int64_t* out_offsets, void* cuda_stream);
 
+/* kMIPS over the items by the index's SimHash tables (the paper's SA-ALSH vs H2-ALSH
+ * comparison, Experiments, kMIPS; with SAH_QNF the tables are H2-ALSH's): for each of the
+ * nq query vectors u (rows of Q, nq x d), Alg. 2's candidate loop without a query item.
+ * C starts as P' (the index's |P'| largest-norm items, scored exactly); then partition by
+ * partition (descending M_j) it stops once phi, the k-th largest FP32 score in C, exceeds
+ * mu_j = M_j ||u|| (rounded up), else adds the partition's items whose code lies within
+ * probe_radius of u's in some table (codes of [u; 0], Eq. 4 / Eq. 7, in FP32).  Writes u's k
+ * best items of C, best first (equal scores: the earlier-found first), to out_ids[j * k ..]
+ * (the caller's item ids; -1 past the items C holds) and, if out_scores is not NULL, their
+ * FP32 scores (-inf past the end).  1 <= k <= 64.  If buffers_on_device != 0, Q, out_ids and
+ * out_scores are device pointers, otherwise host pointers (copied inside the call).
+ * With |P'| = n there are no partitions and C holds every item: the exact kMIPS.
+ * Errors: SAH_ERR_ARG (k out of range, nq < 0, NULL buffers, a non-finite query value),
+ * SAH_ERR_OOM, SAH_ERR_CUDA. */
+sah_status sah_kmips(sah_index* index, const float* Q, int32_t nq, int32_t k, int32_t buffers_on_device,
+                     int32_t* out_ids, float* out_scores, void* cuda_stream);
+
 /* ---- Serving: continuous batching over one index -------------------------------------
  * A server owns `workers` host threads, each with its own CUDA stream, workspace and
  * pinned staging buffers.  Requests are queued by sah_server_submit (any thread); every
  * free worker takes all queued requests up to max_batch as one batch, answers them with
  * one pass of the query path and publishes each request's ids and latency (submit to
  * completion).  Requests arriving while batches run are taken by the next free worker,
- * so batches overlap on the device.  A batch is admitted only if its workspace fits the
- * worker's share of hbm_budget_bytes (0: 8 GiB) and the device's free memory; otherwise it
- * is halved until it fits.  Results are identical to sah_rkmips for the same request.
+ * so batches overlap on the device.  A batch is admitted only if its workspace (the part
+ * that grows with the batch size) fits the worker's share of hbm_budget_bytes (0: 8 GiB)
+ * and half the device's free memory; otherwise it is halved until it fits.  A worker
+ * replays a captured CUDA graph for a batch shape it has seen twice (captures are taken
+ * one at a time per process).  Results are identical to sah_rkmips for the same request.
  * The index must outlive the server and must not be used through the blocking calls
  * while the server runs. */
 
@@ -200,7 +227,8 @@ sah_status sah_index_stats(const sah_index* index, sah_stats* out);
 /* Copies the index's Cone-Tree blocks (the leaves of Alg. 3, Alg. 4) to host arrays:
  * ids[m_nz] the caller ids of the users with a nonzero norm in leaf order, starts[nb + 1]
  * the first position of every leaf, cos_theta[m_nz] each user's cos(theta_u) to its
- * leaf centre, cos_omega[nb] each leaf's cos(omega) (-2 for a zero centre).  *m_nz and
+ * leaf centre, cos_omega[nb] each leaf's cos(omega) (-2 for a zero centre; with
+ * SAH_BLOCK_NORM the blocks are norm runs: cos_theta 0 and cos_omega -1).  *m_nz and
  * *nb receive the sizes; any array pointer may be NULL (to query the sizes first). */
 sah_status sah_index_blocks(const sah_index* index, int64_t* m_nz, int32_t* nb, int32_t* ids,
                             int32_t* starts, float* cos_theta, float* cos_omega);

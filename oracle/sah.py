@@ -4,6 +4,7 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).  Each function follows one
 passage of the paper, in the paper's order and notation:
 
 * SRP hashing ................ Eq. 1 (h_srp(p) = sgn(<a, p>)), collision rate Eq. 2
+* QNF (H2-ALSH) .............. Eq. 3 (item transform), Eq. 4 (user transform), Eq. 5
 * SAT ........................ Eq. 6 (item transform), Eq. 7 (user transform), Eq. 8
 * SA-ALSH family ............. Eq. 9
 * SA-ALSH indexing ........... Alg. 1
@@ -32,6 +33,12 @@ Readings where the paper is silent (each is also listed with the design notes):
   2x + 1 (mod 2^64).  SplitMix64 is Steele, Lea and Flood's generator (OOPSLA 2014).
 * Alg. 1 with a partition maximum M_j = 0 would never end: all zero-norm items form one
   final partition.
+* QNF in place of SAT (the paper's H2-ALSH comparison): the same norm partitions and
+  SimHash tables, each partition transformed by Eq. 3 with M = M_j, its largest norm
+  (H2-ALSH's homocentric partitions), and users by Eq. 4.
+* Standalone kMIPS (the paper's SA-ALSH vs H2-ALSH comparison): Alg. 2's candidate loop
+  without a query item: C seeded with P', partitions in order, stop once the k-th largest
+  score phi of C exceeds mu_j = M_j ||u||; the answer is the k best of C.
 """
 from __future__ import annotations
 
@@ -97,6 +104,21 @@ def sat_item(p: np.ndarray, c: np.ndarray, R: float) -> np.ndarray:
     return np.concatenate([diff, [np.sqrt(max(rad, 0.0))]])
 
 
+def qnf_item(p: np.ndarray, M: float) -> np.ndarray:
+    """Eq. 3: I(p) = [p; sqrt(M^2 - ||p||^2)] (radicand clamped at 0)."""
+    p = np.asarray(p, np.float64)
+    rad = M * M - float(p @ p)
+    return np.concatenate([p, [np.sqrt(max(rad, 0.0))]])
+
+
+def qnf_user(u: np.ndarray, M: float) -> np.ndarray:
+    """Eq. 4: U(u) = [lambda u; 0] with lambda = M / ||u||."""
+    u = np.asarray(u, np.float64)
+    nu = np.sqrt(u @ u)
+    lam = M / nu if nu > 0 else 0.0
+    return np.concatenate([lam * u, [0.0]])
+
+
 def sat_user(u: np.ndarray, R: float) -> np.ndarray:
     """Eq. 7: U(u) = [lambda u; 0] with lambda = R / ||u||."""
     u = np.asarray(u, np.float64)
@@ -117,17 +139,20 @@ class SAALSHIndex:
     n_tables: int
     code_bits: int
     A: np.ndarray                          # (n_tables*code_bits) x (d+1) projections
+    transform: str = "sat"                 # "sat" (Eq. 6, 7) or "qnf" (Eq. 3, 4)
 
 
 def sa_alsh_index(P_sorted: np.ndarray, norms_sorted: np.ndarray, first: int, b: float,
-                  A: np.ndarray, n_tables: int, code_bits: int) -> SAALSHIndex:
+                  A: np.ndarray, n_tables: int, code_bits: int, transform: str = "sat") -> SAALSHIndex:
     """Alg. 1 on the items at positions first..n-1 of the descending-norm order.
 
     Partition S_j starts at the largest remaining norm M_j and takes every following
     item with ||p|| > b * M_j; zero-norm items form one final partition.  Per partition:
     centroid c_j, radius R_j = max ||p - c_j||, the SAT item transform of every member,
-    and ``n_tables`` SimHash tables keyed by the packed SRP code.
+    and ``n_tables`` SimHash tables keyed by the packed SRP code.  With transform "qnf"
+    every member gets Eq. 3's transform with M = M_j instead (no shift: c_j = 0, R_j = M_j).
     """
+    assert transform in ("sat", "qnf")
     n = P_sorted.shape[0]
     parts, Ms = [], []
     i = first
@@ -142,11 +167,16 @@ def sa_alsh_index(P_sorted: np.ndarray, norms_sorted: np.ndarray, first: int, b:
         parts.append(np.arange(j0, i))
         Ms.append(Mj)
     cents, radii, codes, tables = [], [], [], []
-    for S in parts:
+    for S, Mj in zip(parts, Ms):
         X = np.asarray(P_sorted[S], np.float64)
-        c = X.mean(axis=0)
-        R = float(np.max(np.sqrt(((X - c) ** 2).sum(axis=1))))
-        I = np.stack([sat_item(x, c, R) for x in X])
+        if transform == "qnf":
+            c = np.zeros(X.shape[1])
+            R = float(Mj)
+            I = np.stack([qnf_item(x, R) for x in X])
+        else:
+            c = X.mean(axis=0)
+            R = float(np.max(np.sqrt(((X - c) ** 2).sum(axis=1))))
+            I = np.stack([sat_item(x, c, R) for x in X])
         bits = sign_bits(srp_projections(A, I))
         cd = pack_codes(bits, n_tables, code_bits)
         tab = []
@@ -161,12 +191,13 @@ def sa_alsh_index(P_sorted: np.ndarray, norms_sorted: np.ndarray, first: int, b:
         tables.append(tab)
     return SAALSHIndex(items=parts, M=np.asarray(Ms), centroids=cents, radii=np.asarray(radii),
                        codes=codes, tables=tables, n_tables=n_tables, code_bits=code_bits,
-                       A=np.asarray(A, np.float64))
+                       A=np.asarray(A, np.float64), transform=transform)
 
 
 def user_codes(index: SAALSHIndex, u: np.ndarray, R: float) -> np.ndarray:
-    """Eq. 9 for a user: SRP codes of U(u) (Eq. 7) in every table."""
-    bits = srp_bits(index.A, sat_user(u, R))
+    """Eq. 9 for a user: SRP codes of U(u) (Eq. 7; Eq. 4 under QNF) in every table."""
+    x = qnf_user(u, R) if index.transform == "qnf" else sat_user(u, R)
+    bits = srp_bits(index.A, x)
     return pack_codes(bits, index.n_tables, index.code_bits)[0]
 
 
@@ -219,6 +250,32 @@ def sa_alsh_decide(index: SAALSHIndex, P_sorted: np.ndarray, u: np.ndarray, q: n
         if sq < phi:
             return False
     return True
+
+
+def sa_alsh_kmips(index: SAALSHIndex, P_sorted: np.ndarray, u: np.ndarray, k: int,
+                  seed_items: np.ndarray, probe_radius: int) -> np.ndarray:
+    """kMIPS of u by the candidate loop of Alg. 2 (no query item): C starts as
+    ``seed_items``; partition by partition, stop once phi, the k-th largest score in C,
+    exceeds mu_j = M_j ||u||, else add S_j's SimHash candidates.  Returns the positions
+    (in P_sorted) of C's k largest scores, best first (equal scores: lower position
+    first); fewer than k when C holds fewer."""
+    u = np.asarray(u, np.float64)
+    P64 = np.asarray(P_sorted, np.float64)
+    nu = float(np.sqrt(u @ u))
+    C = set(int(i) for i in seed_items)
+    phi = kth_largest(ips(P64[sorted(C)], u), k) if C else -np.inf
+    for j in range(len(index.items)):
+        if phi > index.M[j] * nu:
+            break
+        ucodes = user_codes(index, u, float(index.radii[j]))
+        C |= simhash_candidates(index, j, ucodes, probe_radius)
+        phi = kth_largest(ips(P64[sorted(C)], u), k) if C else -np.inf
+    pos = np.asarray(sorted(C), dtype=np.int64)
+    if len(pos) == 0:
+        return pos
+    sc = ips(P64[pos], u)
+    order = np.lexsort((pos, -sc))
+    return pos[order][:k]
 
 
 # ----------------------------------------------------------------------------- Cone-Tree
@@ -300,7 +357,7 @@ class SAHIndex:
 
 def sah_index(P, U, kmax: int = 50, N0: int = 20, p_prime: Optional[int] = None, b: float = 0.5,
               A: Optional[np.ndarray] = None, n_tables: int = 8, code_bits: int = 4,
-              seed: int = 0) -> SAHIndex:
+              seed: int = 0, transform: str = "sat") -> SAHIndex:
     """Alg. 4: item norms and descending sort, P' lower bounds, SA-ALSH on P \\ P',
     Cone-Tree over the users, and the per-block lower-bound arrays."""
     P = np.asarray(P, np.float64)
@@ -322,7 +379,7 @@ def sah_index(P, U, kmax: int = 50, N0: int = 20, p_prime: Optional[int] = None,
             L[i, :top.shape[0]] = top
     sa = None
     if A is not None:
-        sa = sa_alsh_index(Ps, ns, pp, b, A, n_tables, code_bits)
+        sa = sa_alsh_index(Ps, ns, pp, b, A, n_tables, code_bits, transform)
     blocks = cone_tree(Uhat, nz, N0, seed) if len(nz) else []
     LB = np.array([L[blk.members].min(axis=0) for blk in blocks]).reshape(len(blocks), kmax)
     return SAHIndex(P_sorted=Ps, order=order, norms=ns, p_prime=pp, kmax=kmax, L=L,

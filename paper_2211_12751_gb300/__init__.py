@@ -25,6 +25,7 @@ EXACT, SAALSH = 0, 1
 INJECT_USER_PASS, INJECT_VERIFY = 1, 2
 FP32, BF16, FP8 = 0, 1, 2
 BLOCK_CONE, BLOCK_NORM = 0, 1   # sah_blocking: Cone-Tree leaves, or Simpfer's norm-sorted blocks
+SAT, QNF = 0, 1                 # sah_transform: SA-ALSH's SAT (Eq. 6-7) or H2-ALSH's QNF (Eq. 3-4)
 
 _lib = None
 
@@ -49,6 +50,7 @@ class Params(ctypes.Structure):
         ("srp", ctypes.c_void_p),
         ("tc_user_pass", ctypes.c_int32),
         ("blocking", ctypes.c_int32),
+        ("transform", ctypes.c_int32),
     ]
 
 
@@ -109,6 +111,8 @@ def load(path: Optional[str] = None):
     lib.sah_index_inject_stall.restype = I32
     lib.sah_rkmips_bruteforce_noalloc.argtypes = [P, I64, P, I64, I32, P, I32, P, I64, P, P]
     lib.sah_rkmips_bruteforce_noalloc.restype = I32
+    lib.sah_kmips.argtypes = [P, P, I32, I32, I32, P, P, P]
+    lib.sah_kmips.restype = I32
     lib.sah_server_start.argtypes = [P, I32, I32, I32, I64, ctypes.POINTER(P)]
     lib.sah_server_start.restype = I32
     lib.sah_server_submit.argtypes = [P, P, I32, I32, ctypes.POINTER(ctypes.c_uint64)]
@@ -297,6 +301,25 @@ class Index:
                                   out_ids.numel(), out_offsets.data_ptr(), _stream_handle(stream))
         _check(st)
         return int(out_offsets[nq].item()) if nq else 0
+
+    def kmips(self, Q, k: int, stream=None):
+        """sah_kmips: the k best items of each row of Q found through the SimHash tables
+        (host arrays in, host arrays out): (ids nq x k, -1 past the end; FP32 scores)."""
+        Q = _host_f32(Q)
+        Q = Q.reshape(-1, self.d) if Q.size else np.zeros((0, self.d), np.float32)
+        nq = Q.shape[0]
+        ids = np.empty((nq, int(k)), np.int32)
+        sc = np.empty((nq, int(k)), np.float32)
+        _check(load().sah_kmips(self._h, Q.ctypes.data, nq, int(k), 0, ids.ctypes.data, sc.ctypes.data,
+                                _stream_handle(stream)))
+        return ids, sc
+
+    def kmips_device(self, Q, k: int, out_ids, out_scores=None, stream=None):
+        """sah_kmips with device buffers (torch tensors): Q float32 nq x d, out_ids int32
+        nq x k, out_scores float32 nq x k or None."""
+        nq = Q.shape[0]
+        _check(load().sah_kmips(self._h, Q.data_ptr(), nq, int(k), 1, out_ids.data_ptr(),
+                                out_scores.data_ptr() if out_scores is not None else None, _stream_handle(stream)))
 
     def raw_batch(self, Q, nq, ks, modes, on_device, out_ids, cap, offsets, stream=None) -> int:
         """Direct call of sah_rkmips_batch with raw pointers; returns the status."""

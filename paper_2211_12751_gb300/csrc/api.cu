@@ -125,6 +125,7 @@ void sah_default_params(sah_params* p) {
   p->srp = nullptr;
   p->tc_user_pass = 1;
   p->blocking = SAH_BLOCK_CONE;
+  p->transform = SAH_SAT;
 }
 
 const char* sah_status_string(sah_status s) {
@@ -161,7 +162,8 @@ sah_status sah_build_index(const float* U, int64_t m, const float* P, int64_t n,
   if (prm.k_max < 1 || prm.k_max > sah::kMaxKmax || prm.leaf_size < 1 || prm.leaf_size > sah::kMaxLeaf ||
       !(prm.b > 0.f && prm.b < 1.f) || prm.n_tables < 1 || prm.code_bits < 1 || prm.code_bits > 16 ||
       prm.probe_radius < 0 || prm.probe_radius > prm.code_bits ||
-      (prm.blocking != SAH_BLOCK_CONE && prm.blocking != SAH_BLOCK_NORM)) {
+      (prm.blocking != SAH_BLOCK_CONE && prm.blocking != SAH_BLOCK_NORM) ||
+      (prm.transform != SAH_SAT && prm.transform != SAH_QNF)) {
     sah::set_error("sah_build_index: parameter out of range");
     return SAH_ERR_ARG;
   }
@@ -370,6 +372,38 @@ sah_status sah_rkmips(sah_index* index, const float* q, int32_t k, int32_t mode,
   sah_status s = batch_impl(index, q, 1, &k, &mode, 0, out_ids, cap, offs, (cudaStream_t)cuda_stream);
   index->impl.inject_site = 0;   // the test hook applies to one call
   *out_count = offs[1];
+  return s;
+}
+
+sah_status sah_kmips(sah_index* index, const float* Q, int32_t nq, int32_t k, int32_t buffers_on_device,
+                     int32_t* out_ids, float* out_scores, void* cuda_stream) {
+  if (!index || nq < 0 || k < 1 || k > 64 || (nq > 0 && (!Q || !out_ids))) {
+    sah::set_error("sah_kmips: need an index, nq >= 0, 1 <= k <= 64, Q and out_ids");
+    return SAH_ERR_ARG;
+  }
+  Index* ix = &index->impl;
+  cudaSetDevice(ix->device);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (nq == 0) return SAH_OK;
+  if (buffers_on_device) return sah::run_kmips(ix, Q, nq, k, out_ids, out_scores, st);
+  // host buffers: staged through the device
+  const size_t bq = sizeof(float) * (size_t)nq * ix->d, bo = (size_t)nq * k;
+  char* buf = nullptr;
+  SAH_CUDA(cudaMallocAsync((void**)&buf, bq + bo * (sizeof(int32_t) + sizeof(float)) + 512, st));
+  float* Qd = (float*)buf;
+  int32_t* ids_d = (int32_t*)(buf + ((bq + 255) & ~(size_t)255));
+  float* sc_d = (float*)((char*)ids_d + ((bo * sizeof(int32_t) + 255) & ~(size_t)255));
+  sah_status s = SAH_OK;
+  if (cudaMemcpyAsync(Qd, Q, bq, cudaMemcpyHostToDevice, st) != cudaSuccess) s = SAH_ERR_CUDA;
+  if (s == SAH_OK) s = sah::run_kmips(ix, Qd, nq, k, ids_d, out_scores ? sc_d : nullptr, st);
+  if (s == SAH_OK &&
+      (cudaMemcpyAsync(out_ids, ids_d, sizeof(int32_t) * bo, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+       (out_scores && cudaMemcpyAsync(out_scores, sc_d, sizeof(float) * bo, cudaMemcpyDeviceToHost, st) != cudaSuccess) ||
+       cudaStreamSynchronize(st) != cudaSuccess)) {
+    s = SAH_ERR_CUDA;
+    sah::set_error(std::string("sah_kmips: ") + cudaGetErrorString(cudaGetLastError()));
+  }
+  cudaFreeAsync(buf, st);
   return s;
 }
 

@@ -360,6 +360,176 @@ __global__ void __launch_bounds__(kSaWarps * 32) saalsh_decide_kernel(SaParams p
   if (lane == 0 && scored) atomicAdd(prm.items_stat, scored);
 }
 
+// Standalone kMIPS (Alg. 2's candidate loop without a query item), one warp per query
+// vector: C is seeded with P' (positions 0 .. pp-1, scored exactly), then the partitions in
+// order until phi, the k-th largest score in C, exceeds mu_j = M_j ||u|| (rounded up); each
+// visited partition adds the items whose code is within the probe radius of the query's in
+// some table.  The k-slot list is spread over the lanes (slots 2l, 2l + 1), positions as ids.
+struct KmParams {
+  const float* Q;            // nq x dp, padded
+  const float* qn;           // ||u||
+  const uint16_t* qcode;     // nq x K
+  int nq, k, pp;
+  const float* Ps;
+  const int32_t* pid;
+  int dp;
+  float gamma;
+  int parts;
+  const int32_t* start;
+  const float* M;
+  const float* R;
+  const int32_t* boff;
+  const int32_t* rbin;
+  int nbin, rshift;
+  const uint16_t* bcode;
+  const int32_t* bitem;
+  const uint32_t* probes;
+  int nprobes;
+  int K;
+  int32_t* out_ids;          // nq x k
+  float* out_scores;         // nq x k, or null
+  unsigned long long* items_stat;
+};
+
+__device__ __forceinline__ float dot_rows(const float* __restrict__ p, const float* __restrict__ u, int dp) {
+  const float4* p4 = reinterpret_cast<const float4*>(p);
+  const float4* u4 = reinterpret_cast<const float4*>(u);
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll 4
+  for (int e = 0; e < dp / 4; ++e) {
+    const float4 pa = p4[e], ua = u4[e];
+    s0 = fmaf(ua.x, pa.x, s0);
+    s1 = fmaf(ua.y, pa.y, s1);
+    s2 = fmaf(ua.z, pa.z, s2);
+    s3 = fmaf(ua.w, pa.w, s3);
+  }
+  return (s0 + s1) + (s2 + s3);
+}
+
+__global__ void __launch_bounds__(kSaWarps * 32) kmips_kernel(KmParams prm) {
+  __shared__ int32_t queue[kSaWarps][kQueue];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * kSaWarps + warp;
+  const int64_t nw = (int64_t)gridDim.x * kSaWarps;
+  int32_t* q = queue[warp];
+  const int k = prm.k;
+  unsigned long long scored = 0;
+  for (int64_t r = gw; r < prm.nq; r += nw) {
+    const float* u = prm.Q + r * prm.dp;
+    const float nu = prm.qn[r];
+    float a = -INFINITY, b = -INFINITY;
+    int ia = -1, ib = -1;
+    float phi = -INFINITY;
+    // any candidate that beats phi enters the list (duplicates of listed items skipped)
+    auto offer = [&](float v, int id) {
+      unsigned cand = __ballot_sync(0xffffffffu, v > phi);
+      while (cand) {
+        const int src = __ffs(cand) - 1;
+        cand &= cand - 1;
+        const float vv = __shfl_sync(0xffffffffu, v, src);
+        const int iid = __shfl_sync(0xffffffffu, id, src);
+        if (!(vv > phi)) continue;
+        if (__any_sync(0xffffffffu, ia == iid || ib == iid)) continue;
+        insert_with_id(a, b, ia, ib, vv, iid, lane);
+        phi = slot_value(a, b, k - 1);
+      }
+    };
+    // C = P'
+    for (int c0 = 0; c0 < prm.pp; c0 += 32) {
+      const int c = c0 + lane;
+      float v = -INFINITY;
+      if (c < prm.pp) v = dot_rows(prm.Ps + (int64_t)c * prm.dp, u, prm.dp);
+      scored += (c < prm.pp) ? 1 : 0;
+      offer(v, c < prm.pp ? c : -1);
+    }
+    for (int j = 0; j < prm.parts; ++j) {
+      const float mu = __fmul_ru(__fmul_ru(prm.M[j], nu), 1.f + 2.f * prm.gamma);
+      if (phi > mu) break;                                       // nothing left beats phi
+      const int s0 = prm.start[j], s1 = prm.start[j + 1];
+      const bool all = !(prm.R[j] > 0.f);                        // R_j = 0: every item collides
+      const int ntasks = all ? 1 : prm.K * prm.nprobes;
+      for (int base = 0; base < ntasks; base += 32) {
+        const int task = base + lane;
+        int lo = 0, len = 0;
+        if (task < ntasks) {
+          if (all) {
+            lo = s0;
+            len = s1 - s0;
+          } else {
+            const int t = task / prm.nprobes, pr = task % prm.nprobes;
+            const uint32_t code = prm.qcode[r * prm.K + t] ^ prm.probes[pr];
+            const int seg = j * prm.K + t;
+            const int b0 = prm.boff[seg];
+            const int32_t* rb = prm.rbin + (int64_t)seg * (prm.nbin + 1);
+            const int c8 = (int)(code >> prm.rshift);
+            const int lo8 = b0 + rb[c8], hi8 = b0 + rb[c8 + 1];
+            const int l = lower_bound_u16(prm.bcode, lo8, hi8, code);
+            const int h = lower_bound_u16(prm.bcode, l, hi8, code + 1);
+            lo = l;
+            len = h - l;
+          }
+        }
+        int incl = len;
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        const int excl = incl - len;
+        for (int q0 = 0; q0 < total; q0 += kQueue) {
+          const int from = max(excl, q0), to = min(excl + len, q0 + kQueue);
+          for (int x = from; x < to; ++x) q[x - q0] = all ? (lo + (x - excl)) : prm.bitem[lo + (x - excl)];
+          __syncwarp();
+          const int qn_ = min(kQueue, total - q0);
+          for (int c0 = 0; c0 < qn_; c0 += 32) {
+            const int c = c0 + lane;
+            float v = -INFINITY;
+            int id = -1;
+            if (c < qn_) {
+              id = q[c];
+              v = dot_rows(prm.Ps + (int64_t)id * prm.dp, u, prm.dp);
+            }
+            scored += (c < qn_) ? 1 : 0;
+            offer(v, id);
+          }
+          __syncwarp();
+        }
+      }
+    }
+    // the k slots, best first: slot 2l in a, 2l + 1 in b
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int slot = 2 * lane + h;
+      if (slot < k) {
+        const int pos = h ? ib : ia;
+        prm.out_ids[r * k + slot] = pos >= 0 ? prm.pid[pos] : -1;
+        if (prm.out_scores) prm.out_scores[r * k + slot] = pos >= 0 ? (h ? b : a) : -INFINITY;
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) scored += __shfl_xor_sync(0xffffffffu, scored, o);
+  if (lane == 0 && scored && prm.items_stat) atomicAdd(prm.items_stat, scored);
+}
+
+// Query rows padded to dp with their norms; a non-finite value raises *bad.
+__global__ void kmips_prep_kernel(const float* __restrict__ Q, int nq, int d, int dp, float* __restrict__ Qp,
+                                  float* __restrict__ qn, int* __restrict__ bad) {
+  const int r = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= nq) return;
+  float s = 0.f;
+  bool fin = true;
+  for (int e = lane; e < dp; e += 32) {
+    const float x = e < d ? Q[(int64_t)r * d + e] : 0.f;
+    fin &= isfinite(x);
+    Qp[(int64_t)r * dp + e] = x;
+    s = fmaf(x, x, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (!__all_sync(0xffffffffu, fin) && lane == 0) atomicExch(bad, 1);
+  if (lane == 0) qn[r] = sqrtf(s);
+}
+
 // SRP projection vectors drawn from the seed when the caller gives none: SplitMix64
 // uniforms through the Box-Muller transform.
 std::vector<float> draw_srp(uint64_t seed, int rows, int cols) {
@@ -449,6 +619,11 @@ sah_status build_saalsh(Index* ix, const float* srp_host, cudaStream_t st) {
   radius_kernel<<<grid_for(n - first, 256), 256, 0, st>>>(ix->Ps, dp, first, n, part_of_d, ix->sa_cent,
                                                           reinterpret_cast<unsigned int*>(ix->sa_R));
   SAH_CUDA(cudaGetLastError());
+  if (ix->prm.transform == SAH_QNF) {
+    // Eq. 3: no shift, every partition padded to its largest norm (c_j = 0, R_j = M_j)
+    SAH_CUDA(cudaMemsetAsync(ix->sa_cent, 0, sizeof(float) * (size_t)t * dp, st));
+    SAH_CUDA(cudaMemcpyAsync(ix->sa_R, M.data(), sizeof(float) * t, cudaMemcpyHostToDevice, st));
+  }
 
   // SRP matrix, rows padded to d1p
   const int rows = K * bits;
@@ -620,6 +795,92 @@ sah_status run_saalsh(Index* ix, const Survivor* surv, const unsigned long long*
   saalsh_decide_kernel<<<grid, kSaWarps * 32, 0, st>>>(p);
   SAH_CUDA(cudaGetLastError());
   if (launches) *launches += 1;
+  return SAH_OK;
+}
+
+sah_status run_kmips(Index* ix, const float* Q_dev, int32_t nq, int32_t k, int32_t* out_ids, float* out_scores,
+                     cudaStream_t st) {
+  if (nq == 0) return SAH_OK;
+  const int d = ix->d, dp = ix->dp;
+  const int K = ix->sa_parts > 0 ? ix->sa_K : 0;
+  // workspace: padded rows, norms, codes, the non-finite flag, the scored-items counter
+  const size_t b_rows = sizeof(float) * (size_t)nq * dp, b_qn = sizeof(float) * (size_t)nq,
+               b_code = sizeof(uint16_t) * (size_t)nq * std::max(K, 1);
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t total = up(b_rows) + up(b_qn) + up(b_code) + 256;
+  char* ws = nullptr;
+  if (cudaMallocAsync((void**)&ws, total, st) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("sah_kmips: workspace allocation failed");
+    return SAH_ERR_OOM;
+  }
+  float* Qp = (float*)ws;
+  float* qn = (float*)(ws + up(b_rows));
+  uint16_t* qcode = (uint16_t*)(ws + up(b_rows) + up(b_qn));
+  int* bad = (int*)(ws + up(b_rows) + up(b_qn) + up(b_code));
+  unsigned long long* scored = (unsigned long long*)(bad + 2);
+  sah_status s = SAH_OK;
+  int bad_h = 0;
+  unsigned long long scored_h = 0;
+  do {
+    if (cudaMemsetAsync(bad, 0, 256, st) != cudaSuccess) { s = SAH_ERR_CUDA; break; }
+    kmips_prep_kernel<<<grid_for(nq, 8), 256, 0, st>>>(Q_dev, nq, d, dp, Qp, qn, bad);
+    if (K > 0)
+      user_codes_simple_kernel<<<grid_for((int64_t)nq * K, 256), 256, 0, st>>>(Qp, d, dp, nq, ix->sa_A, ix->sa_d1p,
+                                                                               K, ix->sa_bits, qcode);
+    KmParams p;
+    p.Q = Qp;
+    p.qn = qn;
+    p.qcode = qcode;
+    p.nq = nq;
+    p.k = k;
+    p.pp = ix->pp;
+    p.Ps = ix->Ps;
+    p.pid = ix->pid;
+    p.dp = dp;
+    p.gamma = ix->gamma;
+    p.parts = ix->sa_parts;
+    p.start = ix->sa_start;
+    p.M = ix->sa_M;
+    p.R = ix->sa_R;
+    p.boff = ix->sa_boff;
+    p.rbin = ix->sa_rbin;
+    p.nbin = ix->sa_nbin;
+    p.rshift = ix->sa_rshift;
+    p.bcode = ix->sa_bcode;
+    p.bitem = ix->sa_bitem;
+    p.probes = ix->sa_probes;
+    p.nprobes = ix->sa_nprobes;
+    p.K = K;
+    p.out_ids = out_ids;
+    p.out_scores = out_scores;
+    p.items_stat = scored;
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
+    const unsigned grid = (unsigned)std::min<int64_t>((nq + kSaWarps - 1) / kSaWarps, (int64_t)sms * 16);
+    kmips_kernel<<<grid, kSaWarps * 32, 0, st>>>(p);
+    if (cudaGetLastError() != cudaSuccess) { s = SAH_ERR_CUDA; break; }
+    if (cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(&scored_h, scored, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      s = SAH_ERR_CUDA;
+      break;
+    }
+  } while (false);
+  cudaFreeAsync(ws, st);
+  if (s == SAH_ERR_CUDA) {
+    set_error(std::string("sah_kmips: ") + cudaGetErrorString(cudaGetLastError()));
+    return s;
+  }
+  if (bad_h) {
+    set_error("sah_kmips: a query vector holds a non-finite value");
+    return SAH_ERR_ARG;
+  }
+  // the call's counters: queries and the items scored (P' and the candidates)
+  sah_stats stt{};
+  stt.queries = nq;
+  stt.items_scanned = (int64_t)scored_h;
+  ix->main_ctx.stats = stt;
   return SAH_OK;
 }
 

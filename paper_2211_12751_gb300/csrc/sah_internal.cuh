@@ -279,6 +279,10 @@ sah_status build_index_device(Index* ix, const float* U_dev, const float* P_dev,
 sah_status build_saalsh(Index* ix, const float* srp_host, cudaStream_t st);
 // Alg. 2 for every SA-ALSH survivor; sets the answer bits of the "yes" ones.
 // (the number of survivors is read on the device from *count_dev, at most cap)
+// Standalone kMIPS through the SimHash tables (sah_kmips): Q_dev nq x d on the device,
+// out_ids / out_scores (may be null) nq x k on the device.
+sah_status run_kmips(Index* ix, const float* Q_dev, int32_t nq, int32_t k, int32_t* out_ids, float* out_scores,
+                     cudaStream_t st);
 sah_status run_saalsh(Index* ix, const Survivor* surv, const unsigned long long* count_dev, int64_t cap,
                       const float* Qd, const float* qn, const int32_t* kk, uint32_t* bitmap, int64_t words,
                       unsigned long long* stats, int stat_items, cudaStream_t st, int* launches);

@@ -94,8 +94,9 @@ void worker_loop(sah_server* s, Worker* w) {
       while (B > 1) {
         const size_t need = sah::batch_workspace_bytes(ix, B);
         const size_t grow = need > w->ctx.ws.bytes ? need - w->ctx.ws.bytes : 0;
-        if ((int64_t)(need + w->ctx.surv.bytes + w->ctx.res.bytes + w->ctx.tcws.bytes) <= per_worker_budget &&
-            grow <= free_b / 2)
+        // the part of the workspace that grows with the batch; the survivor lists and the
+        // result buffer are sized by the counts of earlier batches and do not shrink with B
+        if ((int64_t)need <= per_worker_budget && grow <= free_b / 2)
           break;
         B /= 2;
         ++s->split_ticks;

@@ -643,7 +643,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
   // bits of ||p_k||, k}
   __shared__ int4 srows[NROWS];
   __shared__ float2 gq[NG];                         // per 32 columns: largest ||q||, row of the smallest bound
-  __shared__ int32_t kseen[65], kslot[65], klist[64], nsl_sh;
+  __shared__ int32_t kseen[65], kslot[65], kfast[65], klist[64], nsl_sh;
   __shared__ int32_t tlist[kMaxTileList];           // this CTA's needed tiles, in order
   __shared__ int32_t ntl_sh;
   __shared__ uint32_t tma_issued[STAGES];            // TMA loads issued per stage (teardown drain)
@@ -726,15 +726,28 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
     }
     __syncthreads();
     if (tid == 0) {
-      int ns_ = 0;
+      // the slotted k: every distinct k of the set, or, with more of them than slots, the
+      // ranks ceil((i + 1) D / slots) (the largest k among them).  kslot[k]: k's own slot
+      // (-1: its rows read their bound from global memory); kfast[k]: the slot of the
+      // smallest slotted k' >= k, whose bound L^k' <= L^k serves the column's first test.
+      int D = 0;
+      for (int k = 1; k <= p.kmax; ++k)
+        if (kseen[k]) kseen[k] = ++D;
+      const int ns_ = D < p.slot_cap ? D : p.slot_cap;
+      int i = 0;
       for (int k = 1; k <= p.kmax; ++k) {
         kslot[k] = -1;
-        if (kseen[k]) {
-          kslot[k] = ns_ < p.slot_cap ? ns_ : -1;   // past the cap: bounds read from global memory
-          klist[ns_++] = k;
+        kfast[k] = -1;
+        if (!kseen[k]) continue;
+        const int rank = kseen[k];
+        while (((i + 1) * D + ns_ - 1) / ns_ < rank) ++i;
+        kfast[k] = i;
+        if (((i + 1) * D + ns_ - 1) / ns_ == rank) {
+          kslot[k] = i;
+          klist[i] = k;
         }
       }
-      nsl_sh = ns_ < p.slot_cap ? ns_ : p.slot_cap;
+      nsl_sh = ns_;
     }
     __syncthreads();
     if (INL) {
@@ -753,7 +766,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
       int row = p.slot_cap + 1;   // past nn: the +inf row, never a candidate
       if (c < nn) {
         const int kq = p.T.kq[c0 + c];
-        const int sl = kq > 0 ? kslot[kq] : -1;
+        const int sl = kq > 0 ? kfast[kq] : -1;
         qn = p.qn[p.T.rep[c0 + c]];
         // no bound row (only k > k_max rows, or past the cap): the -inf row, every user a candidate
         row = sl >= 0 ? sl : p.slot_cap;

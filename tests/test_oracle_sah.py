@@ -321,3 +321,101 @@ def test_simhash_pins_catch_planted_mistakes(monkeypatch):
         caught["sgn0_minus"] = not _simhash_matches(g, _simhash_state(g))
     assert sah.pack_codes is orig_pack and sah.sign_bits is orig_bits and sah.simhash_candidates is orig_cand
     assert all(caught.values()), caught
+
+
+# ------------------------------------------------------------------ QNF (H2-ALSH) and kMIPS
+def _qnf_golden():
+    with open(os.path.join(GOLDEN, "qnf_sat_3items.json")) as f:
+        return json.load(f)
+
+
+def _qnf_index(g, transform):
+    P = np.array(g["P"], float)
+    order = np.array(g["order"])
+    Ps = P[order]
+    A = np.array(g["A"], float)
+    ix = sah.sa_alsh_index(Ps, np.linalg.norm(Ps, axis=1), 0, g["b"], A, g["n_tables"], g["code_bits"],
+                           transform)
+    return P, order, Ps, ix
+
+
+def test_golden_qnf_and_sat_codes():
+    """Eq. 3-4 against Eq. 6-7 on a case worked by hand: QNF keeps the items unshifted
+    and pads them to norm M, SAT shifts them by the centroid and pads to R; one item's
+    codes differ between the two, and the user's codes do not."""
+    g = _qnf_golden()
+    for tr in ("sat", "qnf"):
+        P, order, Ps, ix = _qnf_index(g, tr)
+        assert [len(s) for s in ix.items] == [3]
+        assert np.allclose(ix.centroids[0], g[tr]["centroid"]) and np.isclose(ix.radii[0] ** 2, g[tr]["R2"])
+        by_item = np.empty((3, 2), dtype=np.int64)
+        by_item[order] = ix.codes[0].astype(np.int64)
+        assert by_item.tolist() == g[tr]["codes_by_item"], tr
+        uc = sah.user_codes(ix, np.array(g["u"], float), float(ix.radii[0]))
+        assert uc.tolist() == g["user_codes"]
+    # Eq. 5: ||I(p) - U(u)||^2 = 2 M (M - <p, u> / ||u||) under QNF
+    M = np.sqrt(20.0)
+    u = np.array(g["u"], float)
+    for p in np.array(g["P"], float):
+        lhs = np.sum((sah.qnf_item(p, M) - sah.qnf_user(u, M)) ** 2)
+        assert np.isclose(lhs, 2 * M * (M - p @ u / np.linalg.norm(u)))
+
+
+def test_golden_kmips_by_transform_and_radius():
+    g = _qnf_golden()
+    u = np.array(g["u"], float)
+    for c in g["kmips"]:
+        P, order, Ps, ix = _qnf_index(g, c["transform"])
+        pos = sah.sa_alsh_kmips(ix, Ps, u, c["k"], np.array([], dtype=int), c["probe_radius"])
+        assert order[pos].tolist() == c["items"], c
+
+
+def test_qnf_pins_catch_a_shifted_qnf():
+    """A QNF that shifts by the centroid (SAT's step) gives SAT's codes, which the golden
+    QNF codes reject."""
+    g = _qnf_golden()
+    P, order, Ps, ix_sat = _qnf_index(g, "sat")
+    by_item = np.empty((3, 2), dtype=np.int64)
+    by_item[order] = ix_sat.codes[0].astype(np.int64)
+    assert by_item.tolist() != g["qnf"]["codes_by_item"]
+
+
+@pytest.mark.parametrize("transform", ["sat", "qnf"])
+def test_kmips_full_probe_is_exact_topk(transform):
+    """With the probe radius at code_bits every item of a visited partition is a candidate,
+    and the mu_j stop only skips partitions that cannot beat phi: the answer is the exact
+    top-k (brute force in FP64)."""
+    W = workload.make("c1", n=300, m=20, d=8)
+    norms = np.linalg.norm(W.P.astype(np.float64), axis=1)
+    order = np.argsort(-norms, kind="stable")
+    Ps = W.P.astype(np.float64)[order]
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((6 * 4, 9))
+    ix = sah.sa_alsh_index(Ps, norms[order], 10, 0.5, A, 6, 4, transform)
+    for i in range(8):
+        u = W.U[i].astype(np.float64)
+        for k in (1, 5, 20):
+            got = sah.sa_alsh_kmips(ix, Ps, u, k, np.arange(10), 4)
+            sc = Ps @ u
+            want = np.lexsort((np.arange(len(sc)), -sc))[:k]
+            assert np.array_equal(got, want), (transform, i, k)
+
+
+def test_kmips_answer_is_best_of_candidates():
+    """At radius 0 the answer is the k best of the seed and the collected candidates, in
+    descending score, and every answer item beats or ties every other candidate."""
+    W = workload.make("c1", n=400, m=10, d=8)
+    norms = np.linalg.norm(W.P.astype(np.float64), axis=1)
+    order = np.argsort(-norms, kind="stable")
+    Ps = W.P.astype(np.float64)[order]
+    A = np.random.default_rng(6).standard_normal((8 * 3, 9))
+    ix = sah.sa_alsh_index(Ps, norms[order], 5, 0.5, A, 8, 3)
+    for i in range(10):
+        u = W.U[i].astype(np.float64)
+        got = sah.sa_alsh_kmips(ix, Ps, u, 10, np.arange(5), 0)
+        sc = Ps[got] @ u
+        assert np.all(np.diff(sc) <= 0)
+        assert len(got) == 10                     # the seed alone holds 5; candidates add the rest
+        # the seed is always in C: a seed item left out cannot beat the answer's last
+        for i in set(range(5)) - set(got.tolist()):
+            assert Ps[i] @ u <= sc[-1]
