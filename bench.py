@@ -320,7 +320,7 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- measurement on the GPU
 def make_index(sah, Ud, Pd, stream, threshold, precision="bf16", tc=1, n_tables=N_TABLES, code_bits=CODE_BITS,
-               leaf=LEAF, probe_radius=0, blocking=0):
+               leaf=LEAF, probe_radius=0, blocking=0, transform=0):
     """Alg. 4 from device copies of U and P; returns (index, build seconds)."""
     import torch
     pp = (1 << 30) if threshold == "full" else 0
@@ -328,7 +328,8 @@ def make_index(sah, Ud, Pd, stream, threshold, precision="bf16", tc=1, n_tables=
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ix = sah.Index(Ud, Pd, k_max=50, leaf_size=leaf, p_prime=pp, seed=0, precision=prec, n_tables=n_tables,
-                   code_bits=code_bits, tc_user_pass=tc, probe_radius=probe_radius, blocking=blocking, stream=stream)
+                   code_bits=code_bits, tc_user_pass=tc, probe_radius=probe_radius, blocking=blocking, transform=transform,
+                   stream=stream)
     torch.cuda.synchronize()
     return ix, time.perf_counter() - t0
 
@@ -492,9 +493,10 @@ def dominant(stage_ms, roofs):
 
 
 def measure_config(sah, W, Ud, Pd, dev, stream, flush, threshold, precision, steps, warmup, peaks, peak_kind,
-                   tc=1, Q=None, K=None, modes=None, blocking=0):
+                   tc=1, Q=None, K=None, modes=None, blocking=0, transform=0):
     """Build an index on W and time a batch (default: the workload's own requests)."""
-    ix, build_s = make_index(sah, Ud, Pd, stream, threshold, precision, tc=tc, blocking=blocking)
+    ix, build_s = make_index(sah, Ud, Pd, stream, threshold, precision, tc=tc, blocking=blocking,
+                             transform=transform)
     if Q is None:
         Q, K, _ = W.requests()
     b = Batch(ix, Q, K, dev, stream, modes=modes)
@@ -689,29 +691,39 @@ def run_variants(sah, dev, stream, flush, peaks, peak_kind, W5, Ud5, Pd5, steps)
             ix2.close()
     out["ablation_blocking"] = blocking_ablation(sah, dev, stream, flush, peaks, peak_kind, W2, Ud2, Pd2, W5, Ud5,
                                                  Pd5, vs)
+    out["kmips_sat_vs_qnf"] = kmips_comparison(sah, dev, stream)
     return out
 
 
 def blocking_ablation(sah, dev, stream, flush, peaks, peak_kind, W2, Ud2, Pd2, W5, Ud5, Pd5, vs):
-    """Cone-Tree blocks (SAH) against Simpfer's norm-sorted blocks with Cauchy-Schwarz bounds
-    (the paper's SA-Simpfer ablation, Experiments, ablation study), everything else equal:
-    exact mode with the tensor-core user pass (BF16) and with the FP32 path (where Lemma 3
-    runs per user), and SA-ALSH mode (Alg. 2 for the survivors, F1 against the exact
-    answers) on the paper's |P'|."""
+    """The paper's ablation (Experiments, ablation study) on C2-shaped data, everything else
+    equal: Cone-Tree blocks (Alg. 3, Lemma 2-3) against Simpfer's norm-sorted blocks with
+    Cauchy-Schwarz bounds, and SAT (SA-ALSH) against QNF (H2-ALSH) codes, i.e. SAH,
+    SA-Simpfer, H2-Cone and H2-Simpfer in SA-ALSH mode (F1 against the exact answers), plus
+    the exact mode's cost under both blockings (tensor-core user pass, BF16; FP32 path,
+    where Lemma 3 runs per user), and the exact C5 step under both blockings."""
     res = {}
+    names = {(0, 0): "SAH", (1, 0): "SA-Simpfer", (0, 1): "H2-Cone", (1, 1): "H2-Simpfer"}
     for blk, tag in ((0, "cone"), (1, "norm")):
         for thr, prec, tc in (("full", "bf16", 1), ("paper", "bf16", 1), ("paper", "fp32", 0)):
             ix, b, rec = measure_config(sah, W2, Ud2, Pd2, dev, stream, flush, thr, prec, vs, 2, peaks, peak_kind,
                                         tc=tc, blocking=blk)
-            r = {k: rec[k] for k in ("value", "ms_per_step", "index_build_s", "stages_ms", "stage_counts")}
+            res[f"c2_{thr}_{prec}_{tag}"] = {k: rec[k] for k in ("value", "ms_per_step", "index_build_s",
+                                                                  "stages_ms", "stage_counts")}
             if thr == "paper" and prec == "bf16":
-                modes = np.full(len(b.K), sah.SAALSH, np.int32)
-                bs = Batch(ix, b.Q, b.K, dev, stream, modes=modes)
-                ts = bs.timed(vs, 2, flush)
-                f1s = [f1_sets(x, y) for x, y in zip(bs.host, b.host)]
-                r["saalsh"] = {"value": len(b.K) / (np.mean(ts) / 1e3), "ms_per_step": float(np.mean(ts)),
-                               "f1_vs_exact": float(np.mean(f1s)), "min_f1": float(np.min(f1s))}
-            res[f"c2_{thr}_{prec}_{tag}"] = r
+                for tr in (0, 1):
+                    ixs = ix if tr == 0 else make_index(sah, Ud2, Pd2, stream, "paper", "bf16", blocking=blk,
+                                                        transform=1)[0]
+                    modes = np.full(len(b.K), sah.SAALSH, np.int32)
+                    bs = Batch(ixs, b.Q, b.K, dev, stream, modes=modes)
+                    ts = bs.timed(vs, 2, flush)
+                    f1s = [f1_sets(x, y) for x, y in zip(bs.host, b.host)]
+                    res[f"c2_paper_bf16_saalsh_{names[(blk, tr)]}"] = {
+                        "blocking": tag, "transform": "qnf" if tr else "sat",
+                        "value": len(b.K) / (np.mean(ts) / 1e3), "ms_per_step": float(np.mean(ts)),
+                        "f1_vs_exact": float(np.mean(f1s)), "min_f1": float(np.min(f1s))}
+                    if tr:
+                        ixs.close()
             ix.close()
         ix, b, rec = measure_config(sah, W5, Ud5, Pd5, dev, stream, flush, "full", "bf16", vs, 2, peaks, peak_kind,
                                     blocking=blk)
@@ -719,6 +731,59 @@ def blocking_ablation(sah, dev, stream, flush, peaks, peak_kind, W2, Ud2, Pd2, W
                                                           "stage_counts")}
         ix.close()
     return res
+
+
+def kmips_comparison(sah, dev, stream, reps=5):
+    """SA-ALSH against H2-ALSH's QNF as standalone kMIPS (the paper's kMIPS comparison,
+    Experiments): 100 user vectors drawn uniformly at random as queries, k in
+    {1, 5, 10, 20, 30, 40, 50}; the same partitions (b = 0.5), tables and probes, only the
+    transform differs.  F1 = |A & E| / k against the exact top-k, which the same call gives
+    on an index with |P'| = n (C then holds every item; the GPU tests tie it to the FP64
+    top-k).  Times: CUDA events around one call for the 100 queries, median of reps."""
+    import torch
+    out = {}
+    ks = (1, 5, 10, 20, 30, 40, 50)
+    for wname in ("c2", "c3"):
+        W = workload.make(wname)
+        Ud, Pd = torch.from_numpy(W.U).to(dev), torch.from_numpy(W.P).to(dev)
+        rows = workload.sample_rows(W.m, 100, seed=31)
+        Qd = torch.from_numpy(np.ascontiguousarray(W.U[rows])).to(dev)
+        ixe, _ = make_index(sah, Ud, Pd, stream, "full")
+        exact = {}
+        for k in ks:
+            e_ids = torch.empty((100, k), dtype=torch.int32, device=dev)
+            ixe.kmips_device(Qd, k, e_ids, stream=stream)
+            torch.cuda.synchronize()
+            exact[k] = e_ids.cpu().numpy()
+        ixe.close()
+        res = []
+        for bits, radius in ((16, 0), (8, 1)):
+            for tr, tname in ((0, "SA-ALSH"), (1, "H2-ALSH (QNF)")):
+                ix, build_s = make_index(sah, Ud, Pd, stream, "paper", n_tables=64, code_bits=bits,
+                                         probe_radius=radius, transform=tr)
+                for k in ks:
+                    o_ids = torch.empty((100, k), dtype=torch.int32, device=dev)
+                    times = []
+                    for _ in range(reps + 1):
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        ix.kmips_device(Qd, k, o_ids, stream=stream)
+                        e1.record(stream)
+                        torch.cuda.synchronize()
+                        times.append(e0.elapsed_time(e1))
+                    got = o_ids.cpu().numpy()
+                    f1 = float(np.mean([len(set(got[r].tolist()) & set(exact[k][r].tolist())) / k
+                                        for r in range(100)]))
+                    res.append({"method": tname, "code_bits": bits, "probe_radius": radius, "k": k,
+                                "f1": f1, "ms_per_100_queries": float(np.median(times[1:])),
+                                "items_scored_per_query": ix.stats()["items_scanned"] / 100.0,
+                                "index_build_s": build_s})
+                ix.close()
+        out[wname] = {"workload": config_block(W)["workload"], "queries": "100 user vectors (seed 31)",
+                      "tables": 64, "b": 0.5, "p_prime": 200, "points": res}
+        del Ud, Pd
+    return out
 
 
 # ---------------------------------------------------------------- our arm

@@ -911,14 +911,21 @@ sah_status ensure_buf(Workspace* b, size_t bytes, cudaStream_t st) {
   return SAH_OK;
 }
 
-sah_status ensure_ws(CallCtx* cx, size_t bytes, cudaStream_t st) { return ensure_buf(&cx->ws, bytes, st); }
+sah_status ensure_ws(CallCtx* cx, size_t bytes, cudaStream_t st) {
+  if (cx->ws.bytes >= bytes) return SAH_OK;
+  ++cx->alloc_epoch;
+  return ensure_buf(&cx->ws, bytes, st);
+}
 
 // three lists of cap entries: exact-mode survivors, SA-ALSH survivors, and the pairs the
 // tensor-core user pass leaves to the FP32 re-score
 sah_status ensure_surv(CallCtx* cx, int64_t cap, cudaStream_t st) {
   // exact survivors, SA-ALSH survivors, open pairs of the tensor-core user pass (cap entries
   // each), then its candidate blocks (cap blocks of 144 bytes)
-  return ensure_buf(&cx->surv, (3 * sizeof(Survivor) + 144) * (size_t)std::max<int64_t>(cap, 1), st);
+  const size_t bytes = (3 * sizeof(Survivor) + 144) * (size_t)std::max<int64_t>(cap, 1);
+  if (cx->surv.bytes >= bytes) return SAH_OK;
+  ++cx->alloc_epoch;
+  return ensure_buf(&cx->surv, bytes, st);
 }
 
 // Captures (begin, enqueue, end, instantiate) never overlap in one process: the server's
@@ -1126,6 +1133,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
         if (cx->pin) cudaFreeHost(cx->pin);
         cx->pin = nullptr;
         cx->pin_bytes = 0;
+        ++cx->alloc_epoch;
         SAH_CUDA(cudaMallocHost(&cx->pin, pin_need));
         cx->pin_bytes = pin_need;
       }
@@ -1280,7 +1288,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
                                            (uint64_t)nqb, (uint64_t)q0, (uint64_t)surv_cap, (uint64_t)res_total,
                                            (uint64_t)direct, (uint64_t)cx->ws.base, (uint64_t)cx->surv.base,
                                            (uint64_t)cx->res.base, (uint64_t)cx->res.bytes, (uint64_t)cx->tcws.base,
-                                           (uint64_t)cx->tcws.bytes, (uint64_t)cx->pin};
+                                           (uint64_t)cx->tcws.bytes, (uint64_t)cx->pin, cx->alloc_epoch};
         SAH_TRY(run_captured(cx, key, enqueue, st));
       }
       SAH_CUDA(cudaStreamSynchronize(st));
@@ -1328,6 +1336,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
         SAH_CUDA(cudaStreamSynchronize(st));
         if (cx->res.base) cudaFree(cx->res.base);
         cx->res = nr;
+        ++cx->alloc_epoch;
         SAH_CUDA(cudaMemsetAsync(&stats[ST_EMIT_OVERFLOW], 0, sizeof(unsigned long long), st));
         {
           int32_t* qcnt = (int32_t*)(w + L.chunk) + (int64_t)nqb * nsw;

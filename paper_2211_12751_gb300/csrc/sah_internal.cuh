@@ -70,6 +70,9 @@ struct CallCtx {
   size_t pin_bytes = 0;
   std::vector<GraphEntry> graphs;
   uint64_t graph_clock = 0;
+  // bumped whenever a buffer of this context is (re)allocated: part of every graph's key, so
+  // that no graph captured against a freed buffer (device or pinned host) is replayed
+  uint64_t alloc_epoch = 0;
   bool graphs_allowed = false;   // set for the index's own context and for each server worker's
   // the answer bitmaps sit at the start of ws; this many bytes of it are known to be zero
   // (the emit pass clears what it reads), valid while ws.base equals bm_clean_base

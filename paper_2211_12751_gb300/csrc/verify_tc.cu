@@ -909,6 +909,7 @@ sah_status run_verify_tc(Index* ix, CallCtx* cx, const Survivor* surv, const uns
     if (cx->tcws.base) cudaFree(cx->tcws.base);
     cx->tcws.base = nullptr;
     cx->tcws.bytes = 0;
+    ++cx->alloc_epoch;
     cudaError_t e = cudaMalloc(&cx->tcws.base, need + need / 4);
     if (e != cudaSuccess) {
       cudaGetLastError();

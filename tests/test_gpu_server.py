@@ -65,3 +65,31 @@ def test_slots_budget_and_errors(sah):
     with pytest.raises(sah.SahError):
         srv.submit(W.P[0], 0)                                # k < 1
     srv.stop()
+
+
+def test_repeated_batch_shapes_across_buffer_growth(sah):
+    """Workers replay captured graphs for repeated batch shapes; batches that grow the
+    worker's buffers in between (a larger workspace, more results) must not replay a graph
+    captured against the freed ones.  Waves of 1, 7, 64, 7 and 1 requests, three times, each
+    wave drained before the next, so that the same shapes recur after every growth."""
+    W = workload.make("c2", m=20000, n=3000)
+    ix = sah.Index(W.U, W.P, k_max=50, leaf_size=128, p_prime=0, precision=1, n_tables=16, code_bits=8)
+    rng = np.random.default_rng(3)
+    srv = sah.Server(ix, max_slots=256, max_batch=64, workers=1)
+    checked = 0
+    reqs = []
+    for rep in range(3):
+        for size in (1, 7, 64, 7, 1):
+            qi = rng.integers(0, W.n, size)
+            ks = rng.integers(1, 51, size)
+            if rep == 2:
+                ks[:] = 50                      # more answers: the result buffer grows
+            tickets = [srv.submit(W.P[qi[r]], int(ks[r]), 0) for r in range(size)]
+            got = _drain(srv, tickets)
+            reqs += [(W.P[qi[r]], int(ks[r]), got[t][0]) for r, t in enumerate(tickets)]
+    srv.stop()
+    for q, k, ids in reqs:
+        assert np.array_equal(ids, ix.rkmips(q, k))
+        checked += 1
+    assert checked == 3 * (1 + 7 + 64 + 7 + 1)
+    ix.close()
