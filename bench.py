@@ -63,7 +63,7 @@ def parse():
                          "user the GPU returns)")
     ap.add_argument("--sustain-s", type=float, default=2.0,
                     help="seconds of back-to-back steps after the timed ones (clock samples under load)")
-    ap.add_argument("--serve-rates", default="1000,2000,5000,10000,20000,50000")
+    ap.add_argument("--serve-rates", default="1000,2000,5000,10000,20000,50000,100000,200000")
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--sweep", action="store_true",
                     help="instead of the bench line, one JSON line of parameter sweeps on C2-shaped data")
@@ -321,9 +321,10 @@ def run_reference(args):
 # ---------------------------------------------------------------- measurement on the GPU
 def make_index(sah, Ud, Pd, stream, threshold, precision="bf16", tc=1, n_tables=N_TABLES, code_bits=CODE_BITS,
                leaf=LEAF, probe_radius=0, blocking=0, transform=0):
-    """Alg. 4 from device copies of U and P; returns (index, build seconds)."""
+    """Alg. 4 from device copies of U and P; returns (index, build seconds).  threshold:
+    "full" (|P'| = n), "paper" (|P'| = 4 k_max) or an integer |P'|."""
     import torch
-    pp = (1 << 30) if threshold == "full" else 0
+    pp = (1 << 30) if threshold == "full" else (0 if threshold == "paper" else int(threshold))
     prec = {"bf16": sah.BF16, "fp8": sah.FP8, "fp32": sah.FP32}[precision]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -649,6 +650,47 @@ def c3_accuracy(W, host, qrows, K, rec, cband):
                       f"{sorted(set(int(k) for k in K.tolist()))}"}
 
 
+def _bf16_round(x):
+    """Round-to-nearest-even to BF16, from float32 bits."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32)
+    return ((b + np.uint32(0x7FFF) + ((b >> np.uint32(16)) & np.uint32(1))) & np.uint32(0xFFFF0000)).view(np.float32)
+
+
+def _e4m3_rows(X):
+    """The library's E4M3 rows: y = x * (448 / max|x_i|) in FP32, rounded to nearest even E4M3
+    (3 mantissa bits, subnormal spacing 2^-9, finite saturation at 448), and the scale back
+    max|x_i| / 448 in FP32."""
+    X = np.asarray(X, np.float32)
+    mx = np.abs(X).max(axis=1).astype(np.float32)
+    inv = np.where(mx > 0, np.float32(448.0) / np.where(mx > 0, mx, 1), 0).astype(np.float32)
+    y = (X * inv[:, None]).astype(np.float64)
+    a = np.abs(y)
+    q = 2.0 ** (np.floor(np.log2(np.maximum(a, 2.0 ** -6))) - 3)
+    r = np.minimum(np.round(a / q) * q, 448.0)
+    return np.sign(y) * r, (mx / np.float32(448.0)).astype(np.float64)
+
+
+def emulated_score_error(W, qrows, users, fmt):
+    """Largest |s - <u,q>| / (||u|| ||q||) over the sample of users and the batch's first two
+    query vectors, with s the score from the tensor cores' operands rounded as the library
+    rounds them (BF16, or E4M3 with per-vector scales), their products summed in FP64 (the
+    FP32 accumulation adds at most (K + 16) 2^-23 of the sum on top)."""
+    U = W.U[users].astype(np.float32)
+    worst = 0.0
+    for qi in np.unique(qrows)[:2]:
+        q = W.P[W.query_idx[qi]].astype(np.float32)
+        exact = U.astype(np.float64) @ q.astype(np.float64)
+        if fmt == "bf16":
+            s = _bf16_round(U).astype(np.float64) @ _bf16_round(q[None, :])[0].astype(np.float64)
+        else:
+            u8, su = _e4m3_rows(U)
+            q8, sq = _e4m3_rows(q[None, :])
+            s = (u8 @ q8[0]) * su * sq[0]
+        nrm = np.linalg.norm(U.astype(np.float64), axis=1) * np.linalg.norm(q.astype(np.float64))
+        worst = max(worst, float(np.max(np.abs(s - exact) / nrm)))
+    return worst
+
+
 def run_variants(sah, dev, stream, flush, peaks, peak_kind, W5, Ud5, Pd5, steps):
     import torch
     out = {}
@@ -677,9 +719,23 @@ def run_variants(sah, dev, stream, flush, peaks, peak_kind, W5, Ud5, Pd5, steps)
     dk = 64 if W3.d <= 64 else 128
     cband = 1.01 * (2.0 ** -7 + 2.0 ** -16 + (2.0 * dk + 16.0) * 2.0 ** -23)
     rec3["accuracy"] = c3_accuracy(W3, b3.host, q3, K3, rec3, cband)
+    sample3 = workload.sample_rows(W3.m, 2000, seed=22)
+    rec3["accuracy"]["max_score_error_rel_emulated"] = emulated_score_error(W3, q3, sample3, "bf16")
     out["c3_full_bf16"] = rec3
     ix3.close()
-    del b3, Ud3, Pd3
+    del b3
+    # the same with the E4M3 user pass (per-vector scales, kind::f8f6f4): the band is about
+    # 0.13 ||u|| ||q||, so most pairs near a threshold go to the re-score
+    ix8, b8, rec8 = measure_config(sah, W3, Ud3, Pd3, dev, stream, flush, "full", "bf16", vs, 2, peaks, peak_kind,
+                                   tc=2, Q=Q3, K=K3)
+    K8 = 128.0
+    c8 = 1.01 * (2.0 ** -4 * (2.0 + 2.0 ** -4) + 2.0 * (1.0 + 2.0 ** -4) * 2.0 ** -10 * np.sqrt(K8) / 448.0
+                 + 2.0 ** -20 * K8 / 448.0 ** 2 + 1.13 * ((K8 + 16.0) * 2.0 ** -23 + 8.0 * 2.0 ** -24))
+    rec8["accuracy"] = c3_accuracy(W3, b8.host, q3, K3, rec8, c8)
+    rec8["accuracy"]["max_score_error_rel_emulated"] = emulated_score_error(W3, q3, sample3, "fp8")
+    out["c3_full_fp8"] = rec8
+    ix8.close()
+    del b8, Ud3, Pd3
     # C2 (n 17,770, m 480k, d 50): the tensor-core path against the plain FP32 GPU path
     W2 = workload.make("c2")
     Ud2, Pd2 = torch.from_numpy(W2.U).to(dev), torch.from_numpy(W2.P).to(dev)
@@ -736,10 +792,11 @@ def blocking_ablation(sah, dev, stream, flush, peaks, peak_kind, W2, Ud2, Pd2, W
 def kmips_comparison(sah, dev, stream, reps=5):
     """SA-ALSH against H2-ALSH's QNF as standalone kMIPS (the paper's kMIPS comparison,
     Experiments): 100 user vectors drawn uniformly at random as queries, k in
-    {1, 5, 10, 20, 30, 40, 50}; the same partitions (b = 0.5), tables and probes, only the
-    transform differs.  F1 = |A & E| / k against the exact top-k, which the same call gives
-    on an index with |P'| = n (C then holds every item; the GPU tests tie it to the FP64
-    top-k).  Times: CUDA events around one call for the 100 queries, median of reps."""
+    {1, 5, 10, 20, 30, 40, 50}; the same partitions (b = 0.5), 64 tables and probes, only the
+    transform differs; |P'| = 1, so that the candidates, not the seed, make the answer.
+    F1 = |A & E| / k against the exact top-k, which the same call gives on an index with
+    |P'| = n (C then holds every item; the GPU tests tie it to the FP64 top-k).  Times: CUDA
+    events around one call for the 100 queries, median of reps."""
     import torch
     out = {}
     ks = (1, 5, 10, 20, 30, 40, 50)
@@ -757,10 +814,9 @@ def kmips_comparison(sah, dev, stream, reps=5):
             exact[k] = e_ids.cpu().numpy()
         ixe.close()
         res = []
-        for bits, radius in ((16, 0), (8, 1)):
+        for bits in (8, 12, 16):
             for tr, tname in ((0, "SA-ALSH"), (1, "H2-ALSH (QNF)")):
-                ix, build_s = make_index(sah, Ud, Pd, stream, "paper", n_tables=64, code_bits=bits,
-                                         probe_radius=radius, transform=tr)
+                ix, build_s = make_index(sah, Ud, Pd, stream, 1, n_tables=64, code_bits=bits, transform=tr)
                 for k in ks:
                     o_ids = torch.empty((100, k), dtype=torch.int32, device=dev)
                     times = []
@@ -775,13 +831,13 @@ def kmips_comparison(sah, dev, stream, reps=5):
                     got = o_ids.cpu().numpy()
                     f1 = float(np.mean([len(set(got[r].tolist()) & set(exact[k][r].tolist())) / k
                                         for r in range(100)]))
-                    res.append({"method": tname, "code_bits": bits, "probe_radius": radius, "k": k,
+                    res.append({"method": tname, "code_bits": bits, "probe_radius": 0, "k": k,
                                 "f1": f1, "ms_per_100_queries": float(np.median(times[1:])),
                                 "items_scored_per_query": ix.stats()["items_scanned"] / 100.0,
                                 "index_build_s": build_s})
                 ix.close()
         out[wname] = {"workload": config_block(W)["workload"], "queries": "100 user vectors (seed 31)",
-                      "tables": 64, "b": 0.5, "p_prime": 200, "points": res}
+                      "tables": 64, "b": 0.5, "p_prime": 1, "points": res}
         del Ud, Pd
     return out
 

@@ -73,11 +73,15 @@ typedef struct {
   uint64_t seed;        /* Cone-Tree random points (Alg. 3) and, when srp is NULL, the SRP matrix */
   const float* srp;     /* optional host matrix (n_tables * code_bits) x (d + 1) of SRP projection
                            vectors (Eq. 1); NULL draws it from seed.  Copied at build time. */
-  int32_t tc_user_pass; /* with SAH_BF16: 1 (default) runs the user pass as one tcgen05 GEMM
-                           U Q^T per 256 queries (split BF16 operands, FP32 accumulation) whose
-                           epilogue applies the bound tests of Alg. 5 to the pairs of the leaves
-                           Lemma 2 kept; 0 runs Lemma 3 and FP32 dot products on the CUDA cores.
-                           Results are identical; only the speed differs. */
+  int32_t tc_user_pass; /* with SAH_BF16 or SAH_FP8 and d <= 128: 1 (default) runs the user pass
+                           as one tcgen05 GEMM U Q^T per sub-batch over its distinct query
+                           vectors (BF16 operands, FP32 accumulation) whose epilogue applies the
+                           bound tests of Alg. 5 to the pairs of the leaves Lemma 2 kept, with a
+                           score band of about 2^-7 ||u|| ||q||; 2 runs the same GEMM on E4M3
+                           operands with a scale per user and per query vector (kind::f8f6f4,
+                           band about 0.13 ||u|| ||q||); 0 runs Lemma 3 and FP32 dot products on
+                           the CUDA cores.  Pairs inside the band are re-scored in FP32, then
+                           FP64: results are identical; only the speed differs. */
   int32_t blocking;     /* sah_blocking: how users are grouped into blocks.  SAH_BLOCK_CONE (0,
                            default): Cone-Tree leaves (Alg. 3) with the cone bounds of Lemma 2
                            and Lemma 3.  SAH_BLOCK_NORM (1): Simpfer's norm-based blocking, the

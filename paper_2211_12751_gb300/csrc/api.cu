@@ -163,7 +163,7 @@ sah_status sah_build_index(const float* U, int64_t m, const float* P, int64_t n,
       !(prm.b > 0.f && prm.b < 1.f) || prm.n_tables < 1 || prm.code_bits < 1 || prm.code_bits > 16 ||
       prm.probe_radius < 0 || prm.probe_radius > prm.code_bits ||
       (prm.blocking != SAH_BLOCK_CONE && prm.blocking != SAH_BLOCK_NORM) ||
-      (prm.transform != SAH_SAT && prm.transform != SAH_QNF)) {
+      (prm.transform != SAH_SAT && prm.transform != SAH_QNF) || prm.tc_user_pass < 0 || prm.tc_user_pass > 2) {
     sah::set_error("sah_build_index: parameter out of range");
     return SAH_ERR_ARG;
   }

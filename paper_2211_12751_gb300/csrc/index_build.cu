@@ -726,6 +726,7 @@ sah_status build_index_device(Index* ix, const float* U_dev, const float* P_dev,
     SAH_TRY(raise_smem_limit((const void*)topk_lower_bounds_kernel, (size_t)((int)smem)));
     unsigned grid = grid_for(mz, kTopkWarps * kUsersPerWarp);
     if (ix->prm.precision != SAH_FP32) SAH_TRY(build_bf16_copies(ix, st));
+    if (ix->prm.precision != SAH_FP32 && ix->prm.tc_user_pass == 2) SAH_TRY(build_fp8_users(ix, st));
     if (ix->pp > 0) {
       if (ix->l_exact) {
         SAH_CUDA(cudaMallocAsync((void**)&ids64, sizeof(int32_t) * 64 * (size_t)mz, st));

@@ -139,6 +139,11 @@ struct Index {
   CUtensorMap tmap_Plo{};
   CUtensorMap tmap_U{};       // TMA map of Ub: box 64 x 128, 128-byte swizzle
   CUtensorMap tmap_Ulo{};     // the same for Ulo
+  // FP8 user pass (tc_user_pass 2): the users in E4M3 (128 bytes a row, leaf order) with
+  // their per-row scales, and the TMA map of the rows (box 128 x 128 bytes, 128-byte swizzle)
+  uint8_t* U8 = nullptr;
+  float* usc = nullptr;
+  CUtensorMap tmap_U8{};
   int* dev_timeout = nullptr; // set by a kernel whose bounded wait ran out
   int inject_site = 0;        // test hook for the next query call (SAH_INJECT_*), 0: none
 
@@ -318,6 +323,12 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
 sah_status topk_full_tc(Index* ix, float* vlast, int32_t* ids64, cudaStream_t st, double* gemm_ms);
 // verify_tc.cu
 sah_status build_bf16_copies(Index* ix, cudaStream_t st);
+// E4M3 rows with a per-row scale (the FP8 user pass): row r of X (rows x dp, the first d
+// used, d <= 128) times 448 / max|x_i| rounded to E4M3 with finite saturation, padded to 128
+// bytes with zeros; scale[r] = max|x_i| / 448 (0 for a zero row).  One warp per row.
+void launch_e4m3_rows(const float* X, int64_t rows, int dp, int d, uint8_t* out, float* scale, cudaStream_t st);
+// The users' E4M3 rows, scales and TMA map (tc_user_pass 2).
+sah_status build_fp8_users(Index* ix, cudaStream_t st);
 // Decides every survivor with the tcgen05 kernel and sets the answer bits; the counters
 // of double-precision decisions and scanned items go to stats[stat_fp64], stats[stat_items].
 // codes_tc.cu

@@ -75,15 +75,18 @@ struct ColTable {
   int4* rows;         // [nq]: {j | sa << 30, k, bits of ||p_k|| (-inf past n), 0}
   float* qnc;         // [nq]: ||q|| of each column
   float4* qt;         // [dp / 4][nq]: the columns' vectors, transposed (16-byte words)
+  uint8_t* q8;        // [nq][128]: every row in E4M3 (FP8 user pass), scaled by 448 / max|q_i|
+  float* qsc;         // [nq]: max|q_i| / 448, the row's scale back
 };
 
 size_t col_table_bytes(int nq, int dp) {
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   return up(sizeof(int32_t)) + 3 * up(sizeof(int32_t) * (nq + 1)) + up(sizeof(int4) * (nq + 1)) +
-         up(sizeof(float) * nq) + up(sizeof(float4) * (size_t)(dp / 4) * nq);
+         up(sizeof(float) * nq) + up(sizeof(float4) * (size_t)(dp / 4) * nq) + up((size_t)128 * nq) +
+         up(sizeof(float) * nq);
 }
 
-ColTable col_table_at(void* base, int nq) {
+ColTable col_table_at(void* base, int nq, int dp) {
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   char* p = (char*)base;
   ColTable T;
@@ -100,6 +103,10 @@ ColTable col_table_at(void* base, int nq) {
   T.qnc = (float*)p;
   p += up(sizeof(float) * nq);
   T.qt = (float4*)p;
+  p += up(sizeof(float4) * (size_t)(dp / 4) * nq);
+  T.q8 = (uint8_t*)p;
+  p += up((size_t)128 * nq);
+  T.qsc = (float*)p;
   return T;
 }
 
@@ -509,6 +516,10 @@ struct UpParams {
   int* timeout;
   int inject_stall;            // test hook: the MMA thread stops after its first tile
   int nring;                   // entries of the bound ring (3..kRingMax)
+  // FP8 user pass: the columns' E4M3 rows and scales (column table), the users' scales
+  const uint8_t* Q8;
+  const float* qsc;
+  const float* usc;
 };
 
 // 32 consecutive FP32 columns of this thread's TMEM lane, waited for; the wait names the
@@ -623,7 +634,9 @@ __device__ __forceinline__ float max32_at(const float (&v)[NV]) {
 // INL: candidates are resolved inside the epilogue (where they are dense: the paper's |P'|,
 // whose lower bounds are loose) or written as candidate blocks for cand_resolve_kernel
 // (where they are sparse: exact thresholds).
-template <int KB, int STAGES, int SETN, int PRODS, bool INL>
+// F8: E4M3 operands with per-row scales (kind::f8f6f4, one 128-byte K-block, KB = 1): the
+// accumulator times the column's and the user's scale is the score.
+template <int KB, int STAGES, int SETN, int PRODS, bool INL, bool F8>
 __global__ void __launch_bounds__(kUThreads, 1)
 user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_constant__ CUtensorMap tmapUlo,
                     UpParams p) {
@@ -638,6 +651,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
   __shared__ __align__(8) uint64_t ring_full[kRingMax], ring_empty[kRingMax];
   __shared__ uint32_t tmem_base_sh;
   __shared__ __align__(16) float2 cq[SETN];         // per column: ||q||, bound-table row of its largest k
+  __shared__ float csq[F8 ? SETN : 1];              // per column: its E4M3 scale (F8)
   __shared__ int2 crows[INL ? SETN : 1];            // per column: first row (set-relative), row count
   // the set's rows: {j | sa << 30, bound-table row offset (-1: past the cap, -2: no bound),
   // bits of ||p_k||, k}
@@ -654,7 +668,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
   // sl, row slot_cap -inf, row slot_cap + 1 +inf, row slot_cap + 2 ||u||, row slot_cap + 3
   // E_u, row slot_cap + 4 the caller's user id (users past m_nz read as 0); bound "offsets"
   // below are row * 128
-  const int ring_rows = p.slot_cap + 5;
+  const int ring_rows = p.slot_cap + 5 + (F8 ? 1 : 0);   // F8: row slot_cap + 5 the user's scale
   const int nring = p.nring;
   float* ring = reinterpret_cast<float*>(base + S::kOperands);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -772,6 +786,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
         row = sl >= 0 ? sl : p.slot_cap;
       }
       cq[c] = make_float2(qn, __int_as_float(128 * row));
+      if constexpr (F8) csq[c] = c < nn ? p.qsc[p.T.rep[c0 + c]] : 0.f;
     }
     __syncthreads();
     if (tid < NG) {
@@ -790,9 +805,13 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
       const int rr = i / (KB * 8), rem = i % (KB * 8), kb = rem / 8, ch = rem % 8;
       uint4 hi = make_uint4(0u, 0u, 0u, 0u), lo = hi;
       if (rr < nn) {
-        const int64_t off = (int64_t)p.T.rep[c0 + rr] * p.dk + kb * 64 + ch * 8;
-        hi = *reinterpret_cast<const uint4*>(p.Qhi + off);
-        if (PRODS == 3) lo = *reinterpret_cast<const uint4*>(p.Qlo + off);
+        if constexpr (F8) {
+          hi = *reinterpret_cast<const uint4*>(p.Q8 + (int64_t)p.T.rep[c0 + rr] * 128 + ch * 16);
+        } else {
+          const int64_t off = (int64_t)p.T.rep[c0 + rr] * p.dk + kb * 64 + ch * 8;
+          hi = *reinterpret_cast<const uint4*>(p.Qhi + off);
+          if (PRODS == 3) lo = *reinterpret_cast<const uint4*>(p.Qlo + off);
+        }
       }
       const uint32_t o = tc::sw128_offset(rr, ch);
       *reinterpret_cast<uint4*>(sB + kb * S::kBPart + o) = hi;
@@ -839,7 +858,8 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
           if (u >= 1 && !tc::mbar_wait(&tempty_bar[slot], (u - 1) & 1, p.timeout, nullptr)) break;
           tc::tc_fence_after();
           const int nh = min(W, nn - sc * W);
-          const uint32_t idesc = tc::idesc_bf16_f32(kUM, (uint32_t)((nh + 15) & ~15));
+          const uint32_t idesc = F8 ? tc::idesc_e4m3_f32(kUM, (uint32_t)((nh + 15) & ~15))
+                                    : tc::idesc_bf16_f32(kUM, (uint32_t)((nh + 15) & ~15));
           const uint32_t d = tbase + slot * W;
           const uint32_t aS = a0 + s * S::kStage;
           const uint32_t bS = b0 + sc * W * 128;           // rows sc W.. of each B K-block
@@ -853,8 +873,13 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
             for (int kb = 0; kb < KB; ++kb)
 #pragma unroll
               for (int k16 = 0; k16 < 4; ++k16) {
-                tc::umma_bf16(d, tc::sw128_kmajor_desc(ap + kb * S::kTile + k16 * 32),
-                              tc::sw128_kmajor_desc(bp + kb * S::kBPart + k16 * 32), idesc, acc);
+                // 32 bytes of K per instruction: 16 BF16 or 32 E4M3 values
+                if constexpr (F8)
+                  tc::umma_e4m3(d, tc::sw128_kmajor_desc(ap + kb * S::kTile + k16 * 32),
+                                tc::sw128_kmajor_desc(bp + kb * S::kBPart + k16 * 32), idesc, acc);
+                else
+                  tc::umma_bf16(d, tc::sw128_kmajor_desc(ap + kb * S::kTile + k16 * 32),
+                                tc::sw128_kmajor_desc(bp + kb * S::kBPart + k16 * 32), idesc, acc);
                 acc = 1;
               }
           }
@@ -881,6 +906,8 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
           cp_async16(ent + (p.slot_cap + 2) * 128 + 4 * lane, nb ? (const void*)(p.unorm + u4) : (const void*)p.unorm, nb);
           cp_async16(ent + (p.slot_cap + 3) * 128 + 4 * lane, nb ? (const void*)(p.Eu + u4) : (const void*)p.Eu, nb);
           cp_async16(ent + (p.slot_cap + 4) * 128 + 4 * lane, nb ? (const void*)(p.uid + u4) : (const void*)p.uid, nb);
+          if constexpr (F8)
+            cp_async16(ent + (p.slot_cap + 5) * 128 + 4 * lane, nb ? (const void*)(p.usc + u4) : (const void*)p.usc, nb);
         }
         for (int sl = 0; sl < nsl; ++sl) {
           const float* Lrow = p.Lt + (int64_t)(klist[sl] - 1) * p.mz;
@@ -933,7 +960,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
       };
       int cur_li = -1;
       const float* ent = ring;
-      float cu = 0.f, E = 0.f;
+      float cu = 0.f, E = 0.f, su = 1.f;
       int64_t r = 0;
       bool valid = false;
       // the bound L - E - 1e-30 (rounded down) of the ring row at `off` for user ul
@@ -952,6 +979,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
           valid = r < p.mz;
           cu = __fmul_ru(p.cband, ent[(p.slot_cap + 2) * 128 + ul]);
           E = ent[(p.slot_cap + 3) * 128 + ul];
+          if constexpr (F8) su = ent[(p.slot_cap + 5) * 128 + ul];
         }
         const int jg = jbase + j, slot = jg & 1;      // slot == g
         if (!tc::mbar_wait(&tfull_bar[slot], (jg >> 1) & 1, p.timeout, nullptr)) {
@@ -984,6 +1012,10 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
             if (64 * x2 < rem) {
               float vv[64];
               tmem_ld64_wait(acc_addr + 64 * x2, vv);
+              if constexpr (F8) {
+#pragma unroll
+                for (int i = 0; i < 64; ++i) vv[i] = (vv[i] * csq[cs0 + 64 * x2 + i]) * su;
+              }
               if (64 * x2 + 64 > rem) {
 #pragma unroll
                 for (int i = 0; i < 64; ++i)
@@ -1002,6 +1034,10 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
             const int left = nn - cw;
             float v[32];
             tmem_ld32_wait(acc_addr + 32 * x, v);
+            if constexpr (F8) {
+#pragma unroll
+              for (int i = 0; i < 32; ++i) v[i] = (v[i] * csq[cw + i < SETN ? cw + i : SETN - 1]) * su;
+            }
             uint32_t cand = 0;
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
@@ -1017,7 +1053,8 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
             while (uni) {
               const int i = __ffs(uni) - 1;
               uni &= uni - 1;
-              const float sv = tmem_ld1_wait(acc_addr + 32 * x + i);
+              float sv = tmem_ld1_wait(acc_addr + 32 * x + i);
+              if constexpr (F8) sv = (sv * csq[cw + i]) * su;
               const unsigned cm = __ballot_sync(0xffffffffu, (cand >> i) & 1u);
               const int2 cr = crows[cw + i];
               const float qn = cq[cw + i].x;
@@ -1096,6 +1133,10 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
             if (64 * x2 < rem) {
               float vv[64];
               tmem_ld64_wait(acc_addr + 64 * x2, vv);
+              if constexpr (F8) {
+#pragma unroll
+                for (int i = 0; i < 64; ++i) vv[i] = (vv[i] * csq[cs0 + 64 * x2 + i]) * su;
+              }
               if (64 * x2 + 64 > rem) {
 #pragma unroll
                 for (int i = 0; i < 64; ++i)
@@ -1144,10 +1185,11 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
 }
 
 
-template <int KB, int STAGES, int SETN, int PRODS, bool INL>
+template <int KB, int STAGES, int SETN, int PRODS, bool INL, bool F8 = false>
 sah_status launch_pass(Index* ix, UpParams p, int sms, cudaStream_t st, int* launches, const cudaEvent_t* ev) {
   using S = UpSmem<KB, STAGES, SETN, PRODS>;
-  auto fn = user_pass_tc_kernel<KB, STAGES, SETN, PRODS, INL>;
+  auto fn = user_pass_tc_kernel<KB, STAGES, SETN, PRODS, INL, F8>;
+  constexpr int kFixedRows = 5 + (F8 ? 1 : 0);   // ring rows beside the bound slots
   // lower-bound rows per warp: what shared memory holds beside the operands
   int optin = 0;
   SAH_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ix->device));
@@ -1156,15 +1198,15 @@ sah_status launch_pass(Index* ix, UpParams p, int sms, cudaStream_t st, int* lau
   // the ring: up to 8 slots of bounds and up to kRingMax entries, at least 3 entries
   const int64_t spare = (int64_t)optin - (int64_t)fa.sharedSizeBytes - (int64_t)S::bytes(0, 0);
   int slots = std::min({ix->kmax, 8, 64});
-  while (slots > 1 && spare / ((int64_t)(slots + 5) * 512) < 3) --slots;
-  const int nring = (int)std::min<int64_t>(kRingMax, spare / ((int64_t)(slots + 5) * 512));
+  while (slots > 1 && spare / ((int64_t)(slots + kFixedRows) * 512) < 3) --slots;
+  const int nring = (int)std::min<int64_t>(kRingMax, spare / ((int64_t)(slots + kFixedRows) * 512));
   if (nring < 3) {
     set_error("tensor-core user pass: no shared memory left for the bound ring");
     return SAH_ERR_UNSUPPORTED;
   }
   p.slot_cap = slots;
   p.nring = nring;
-  const size_t smem = S::bytes(p.slot_cap, p.nring);
+  const size_t smem = S::bytes(p.slot_cap + kFixedRows - 5, p.nring);
   SAH_TRY(raise_smem_limit((const void*)fn, (size_t)((int)smem)));
   const unsigned grid = (unsigned)std::max(1, std::min(p.ntiles, sms));
   const int64_t seg = (int64_t)kMaxTileList * grid;   // tiles per launch: at most kMaxTileList per CTA
@@ -1172,7 +1214,8 @@ sah_status launch_pass(Index* ix, UpParams p, int sms, cudaStream_t st, int* lau
     p.tile0 = (int)t0;
     p.tile_end = (int)std::min<int64_t>(p.ntiles, t0 + seg);
     if (ev && t0 == 0) SAH_CUDA(cudaEventRecord(ev[0], st));
-    fn<<<grid, kUThreads, smem, st>>>(ix->tmap_U, ix->tmap_Ulo, p);
+    if constexpr (F8) fn<<<grid, kUThreads, smem, st>>>(ix->tmap_U8, ix->tmap_U8, p);
+    else fn<<<grid, kUThreads, smem, st>>>(ix->tmap_U, ix->tmap_Ulo, p);
     if (ev && t0 + seg >= p.ntiles) SAH_CUDA(cudaEventRecord(ev[1], st));
     SAH_CUDA(cudaGetLastError());
     if (launches) *launches += 1;
@@ -1288,7 +1331,7 @@ sah_status prepare_user_pass_tc(Index* ix, const float* Qd, const float* qn, con
     return SAH_ERR_ARG;
   }
   // the distinct query vectors of the sub-batch
-  const ColTable T = col_table_at(scratch, nq);
+  const ColTable T = col_table_at(scratch, nq, ix->dp);
   int ht = 64;
   while (ht < 2 * nq) ht <<= 1;
   const size_t tsmem = sizeof(int32_t) * (2 * (size_t)ht + 5 * (size_t)nq);
@@ -1297,6 +1340,12 @@ sah_status prepare_user_pass_tc(Index* ix, const float* Qd, const float* qn, con
                                                T);
   SAH_CUDA(cudaGetLastError());
   if (launches) *launches += 1;
+  if (ix->prm.tc_user_pass == 2) {
+    // the FP8 user pass: every row of the sub-batch in E4M3 with its scale
+    launch_e4m3_rows(Qd, nq, ix->dp, ix->d, T.q8, T.qsc, st);
+    SAH_CUDA(cudaGetLastError());
+    if (launches) *launches += 1;
+  }
   return SAH_OK;
 }
 
@@ -1304,7 +1353,7 @@ sah_status block_filter_tc(Index* ix, void* scratch, int nq, uint32_t* kept_mask
                            unsigned long long* stats, int st_pairs, int st_users, int st_scored, int st_colpairs,
                            cudaStream_t st) {
   if (ix->nb == 0 || nq == 0) return SAH_OK;
-  const ColTable T = col_table_at(scratch, nq);
+  const ColTable T = col_table_at(scratch, nq, ix->dp);
   // the kept bits and the leaf flags after them are OR-ed / set by the CTAs of every column chunk
   int32_t* leaf_flag = reinterpret_cast<int32_t*>(kept_mask + (size_t)ix->nb * mask_words);
   SAH_CUDA(cudaMemsetAsync(kept_mask, 0, sizeof(uint32_t) * (size_t)ix->nb * mask_words + sizeof(int32_t) * ix->nb, st));
@@ -1326,7 +1375,7 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
   if (ix->m_nz == 0 || nq == 0 || ix->dk <= 0) return SAH_OK;
   const uint16_t* Qhi = Qsplit;
   const uint16_t* Qlo = Qsplit + (size_t)nq * ix->dk;
-  const ColTable T = col_table_at(scratch, nq);
+  const ColTable T = col_table_at(scratch, nq, ix->dp);
   UpParams p{};
   p.mz = ix->m_nz;
   p.n = ix->n;
@@ -1353,6 +1402,25 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
   // FP32 accumulation of dk products, every addition allowed two units in the last place:
   // |s_tc - <u,q>| <= c_bf ||u|| ||q||
   p.cband = (float)(1.01 * (std::ldexp(1.0, -7) + std::ldexp(1.0, -16) + (2.0 * ix->dk + 16.0) * std::ldexp(1.0, -23)));
+  const bool f8 = ix->prm.tc_user_pass == 2;
+  if (f8) {
+    // E4M3 operands: every value y = x 448 / max|x_i| is rounded to within 2^-4 |y| + 2^-10
+    // (half the subnormal spacing); over K = 128 products, with the scales at most
+    // ||x|| / 448, the rounding is bounded by
+    //   (2^-4 (1 + 2^-4) + 2^-4) ||u|| ||q|| + 2 (1 + 2^-4) 2^-10 sqrt(K) / 448 ||u|| ||q||
+    //   + 2^-20 K / 448^2 ||u|| ||q||,
+    // the FP32 accumulation of K products (two units in the last place per addition) and
+    // the two scale multiplications and scale roundings by 1.13 ((K + 16) 2^-23 + 8 2^-24)
+    // of it (the rounded operands' products sum to at most (1 + 2^-4)^2 ||u|| ||q||)
+    const double K = 128.0;
+    p.cband = (float)(1.01 * (std::ldexp(1.0, -4) * (2.0 + std::ldexp(1.0, -4)) +
+                              2.0 * (1.0 + std::ldexp(1.0, -4)) * std::ldexp(1.0, -10) * std::sqrt(K) / 448.0 +
+                              std::ldexp(1.0, -20) * K / (448.0 * 448.0) +
+                              1.13 * ((K + 16.0) * std::ldexp(1.0, -23) + 8.0 * std::ldexp(1.0, -24))));
+    p.Q8 = T.q8;
+    p.qsc = T.qsc;
+    p.usc = ix->usc;
+  }
   p.gamma = ix->gamma;
   p.bitmap = bitmap;
   p.words = words;
@@ -1370,7 +1438,10 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
   // candidates are sparse against exact thresholds (|P'| = n): candidate blocks; dense
   // against the paper's |P'|: resolved in the epilogue
-  if (ix->dk == 64) {
+  if (f8) {
+    if (ix->l_exact) SAH_TRY((launch_pass<1, 4, 512, 1, false, true>(ix, p, sms, st, launches, ev)));
+    else SAH_TRY((launch_pass<1, 4, 512, 1, true, true>(ix, p, sms, st, launches, ev)));
+  } else if (ix->dk == 64) {
     if (ix->l_exact) SAH_TRY((launch_pass<1, 4, 512, 1, false>(ix, p, sms, st, launches, ev)));
     else SAH_TRY((launch_pass<1, 4, 512, 1, true>(ix, p, sms, st, launches, ev)));
   } else {

@@ -20,6 +20,7 @@
 // Survivors are first sorted by the tile where their norm cut falls, so that rows in
 // one CTA need similar numbers of tiles.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -813,7 +814,60 @@ constexpr size_t tc_smem_bytes() {
   return 2 * ((size_t)KB * kRows * 128 + (size_t)STAGES * KB * kTileN * 128) + 1024;
 }
 
+__global__ void e4m3_rows_kernel(const float* __restrict__ X, int64_t rows, int dp, int d, uint8_t* __restrict__ out,
+                                 float* __restrict__ scale) {
+  const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= rows) return;
+  float x[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int e = lane * 4 + q;
+    x[q] = e < d ? X[r * dp + e] : 0.f;
+  }
+  float mx = fmaxf(fmaxf(fabsf(x[0]), fabsf(x[1])), fmaxf(fabsf(x[2]), fabsf(x[3])));
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const float inv = mx > 0.f ? 448.f / mx : 0.f;
+  uint32_t packed = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const __nv_fp8_e4m3 v(x[q] * inv);
+    packed |= (uint32_t)v.__x << (8 * q);
+  }
+  reinterpret_cast<uint32_t*>(out + r * 128)[lane] = packed;
+  if (lane == 0) scale[r] = mx / 448.f;
+}
+
 }  // namespace
+
+void launch_e4m3_rows(const float* X, int64_t rows, int dp, int d, uint8_t* out, float* scale, cudaStream_t st) {
+  if (rows > 0) e4m3_rows_kernel<<<grid_for(rows, 8), 256, 0, st>>>(X, rows, dp, d, out, scale);
+}
+
+sah_status build_fp8_users(Index* ix, cudaStream_t st) {
+  if (ix->d > 128 || ix->m_nz == 0) return SAH_OK;
+  SAH_TRY(dev_alloc(ix, (void**)&ix->U8, (size_t)ix->m_nz * 128));
+  SAH_TRY(dev_alloc(ix, (void**)&ix->usc, sizeof(float) * (size_t)ix->m_nz));
+  launch_e4m3_rows(ix->Ut, ix->m_nz, ix->dp, ix->d, ix->U8, ix->usc, st);
+  SAH_CUDA(cudaGetLastError());
+  auto encode = get_encode_fn();
+  if (!encode) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return SAH_ERR_UNSUPPORTED;
+  }
+  cuuint64_t dims[2] = {128, (cuuint64_t)ix->m_nz};
+  cuuint64_t strides[1] = {128};
+  cuuint32_t box[2] = {128, 128};
+  cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(&ix->tmap_U8, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, ix->U8, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled (E4M3 users) failed with code " + std::to_string((int)r));
+    return SAH_ERR_CUDA;
+  }
+  return SAH_OK;
+}
 
 // BF16 copies of the users and items (K padded to 64 or 128) and the TMA map of the
 // items, for the tensor-core path.

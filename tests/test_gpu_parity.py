@@ -14,11 +14,13 @@ pytestmark = pytest.mark.gpu
 
 
 # precision variants: FP32 on the CUDA cores; BF16 copies with the FP32 user pass; BF16
-# copies with the tensor-core user pass (split BF16 operands)
+# copies with the tensor-core user pass (BF16 operands); the tensor-core user pass on E4M3
+# operands with per-vector scales (a band of about 0.13 ||u|| ||q||, most pairs re-scored)
 VARIANTS = {
     "fp32": dict(precision=0),
     "bf16-simt": dict(precision=1, tc_user_pass=0),
     "bf16-tc": dict(precision=1, tc_user_pass=1),
+    "fp8-tc": dict(precision=1, tc_user_pass=2),
 }
 
 
