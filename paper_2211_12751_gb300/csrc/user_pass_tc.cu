@@ -68,7 +68,7 @@ constexpr int kMaxRows = 4096;       // rows of a sub-batch the column table tak
 
 // The columns of a sub-batch and their rows.
 struct ColTable {
-  int32_t* ncol;      // [1]
+  int32_t* ncol;      // [2]: the number of columns; a flag raised when two rows share a hash but not their bits
   int32_t* rep;       // [nq]: a row holding the column's vector
   int32_t* kq;        // [nq]: largest k <= k_max among the column's rows (0: none)
   int32_t* start;     // [nq + 1]: the column's rows in rows[start[c], start[c + 1])
@@ -77,13 +77,14 @@ struct ColTable {
   float4* qt;         // [dp / 4][nq]: the columns' vectors, transposed (16-byte words)
   uint8_t* q8;        // [nq][128]: every row in E4M3 (FP8 user pass), scaled by 448 / max|q_i|
   float* qsc;         // [nq]: max|q_i| / 448, the row's scale back
+  int32_t* colof;     // [nq]: the column of each row (-1: none)
 };
 
 size_t col_table_bytes(int nq, int dp) {
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   return up(sizeof(int32_t)) + 3 * up(sizeof(int32_t) * (nq + 1)) + up(sizeof(int4) * (nq + 1)) +
          up(sizeof(float) * nq) + up(sizeof(float4) * (size_t)(dp / 4) * nq) + up((size_t)128 * nq) +
-         up(sizeof(float) * nq);
+         up(sizeof(float) * nq) + up(sizeof(int32_t) * nq);
 }
 
 ColTable col_table_at(void* base, int nq, int dp) {
@@ -107,6 +108,8 @@ ColTable col_table_at(void* base, int nq, int dp) {
   T.q8 = (uint8_t*)p;
   p += up((size_t)128 * nq);
   T.qsc = (float*)p;
+  p += up(sizeof(float) * nq);
+  T.colof = (int32_t*)p;
   return T;
 }
 
@@ -150,13 +153,18 @@ __device__ int block_exclusive_scan(int v, int* wsum, int* total) {
 }
 
 // One CTA of 1024 threads.  Rows with k > n ask for every user and get no column.
+// mode 0: the rows grouped by (hash of the padded row's bits, k <= k_max); the grid-wide
+// column_check_kernel then compares every row with its column's first row bitwise.  mode 1:
+// nothing unless that check raised the flag (two different vectors with one hash); then the
+// table is built again with every probe comparing the rows bitwise.
 __global__ void __launch_bounds__(1024, 1)
-column_table_kernel(const float* __restrict__ Qd, const float* __restrict__ qn, const uint64_t* __restrict__ qh,
-                    int nq, int dp, const int32_t* __restrict__ kk, const int32_t* __restrict__ modes, int kmax,
-                    int64_t n, const float* __restrict__ pnorm, int ht, ColTable T) {
+column_table_kernel(const float* __restrict__ Qd, const uint64_t* __restrict__ qh, int nq, int dp,
+                    const int32_t* __restrict__ kk, const int32_t* __restrict__ modes, int kmax, int64_t n,
+                    const float* __restrict__ pnorm, int ht, ColTable T, int mode) {
   extern __shared__ int32_t sm[];
   __shared__ int wsum[32];
-  __shared__ int total_sh, collide_sh;
+  __shared__ int total_sh;
+  if (mode == 1 && *(volatile int32_t*)(T.ncol + 1) == 0) return;
   int32_t* owner = sm;             // [ht] a row of the slot's vector, -1 empty
   int32_t* minrow = owner + ht;    // [ht] the first row of the slot's vector
   int32_t* colof = minrow + ht;    // [nq] slot, then column, of each row (-1: none)
@@ -175,19 +183,10 @@ column_table_kernel(const float* __restrict__ Qd, const float* __restrict__ qn, 
   }
   __syncthreads();
   // a thread per row: linear probing on (hash of the padded row's bits, k <= k_max); a
-  // slot's owner is a row of its vector.  Equal hashes are then checked bitwise (a 16-byte
-  // word per thread and step, so that the loads coalesce); should two different vectors
-  // share a hash, the table is built again with every probe comparing the rows bitwise.
+  // slot's owner is a row of its vector (mode 1: of its bits)
   const int dp4 = dp / 4;
-  if (tid == 0) collide_sh = 0;
-  for (int pass = 0; pass < 2; ++pass) {
-    if (pass == 1) {
-      for (int i = tid; i < ht; i += nt) {
-        owner[i] = -1;
-        minrow[i] = INT_MAX;
-      }
-      __syncthreads();
-    }
+  const int pass = mode;
+  {
     for (int j = tid; j < nq; j += nt) {
       const int k = kk[j];
       colof[j] = -1;
@@ -218,33 +217,6 @@ column_table_kernel(const float* __restrict__ Qd, const float* __restrict__ qn, 
       atomicMin(&minrow[slot], j);
     }
     __syncthreads();
-    if (pass == 1) break;
-    for (int x0 = tid; x0 < nq * dp4; x0 += 4 * nt) {
-      uint4 a[4], b[4];
-      bool chk[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int x = x0 + e * nt;
-        chk[e] = false;
-        a[e] = b[e] = make_uint4(0u, 0u, 0u, 0u);
-        if (x < nq * dp4) {
-          const int j = x / dp4, i = x - j * dp4;
-          const int sl = colof[j];
-          const int o = sl >= 0 ? owner[sl] : j;
-          if (o != j) {
-            chk[e] = true;
-            a[e] = __ldcg(reinterpret_cast<const uint4*>(Qd + (int64_t)j * dp) + i);
-            b[e] = __ldcg(reinterpret_cast<const uint4*>(Qd + (int64_t)o * dp) + i);
-          }
-        }
-      }
-#pragma unroll
-      for (int e = 0; e < 4; ++e)
-        if (chk[e] && (a[e].x != b[e].x || a[e].y != b[e].y || a[e].z != b[e].z || a[e].w != b[e].w))
-          collide_sh = 1;
-    }
-    __syncthreads();
-    if (!collide_sh) break;
   }
   // columns numbered by their first rows, in row order
   const int per = (nq + nt - 1) / nt;
@@ -285,60 +257,105 @@ column_table_kernel(const float* __restrict__ Qd, const float* __restrict__ qn, 
   }
   if (tid == 0) {
     T.start[ncol] = total_sh;
-    *T.ncol = ncol;
+    T.ncol[0] = ncol;
+    T.ncol[1] = 0;
   }
   __syncthreads();
   for (int j = tid; j < nq; j += nt) {
     const int cc = colof[j];
+    T.colof[j] = cc;
     if (cc < 0) continue;
     const int k = kk[j];
     const int sa = (modes != nullptr && modes[j] == SAH_SAALSH && k <= kmax) ? 1 : 0;
     const float pk = k <= n ? pnorm[k - 1] : -INFINITY;
     T.rows[atomicAdd(&cnt[cc], 1)] = make_int4(j | (sa << 30), k, __float_as_int(pk), 0);
   }
-  // the columns' vectors transposed (read row by row, so that the loads coalesce) and
-  // their norms, for the block filter's thread-per-column reads
-  const float4* Q4 = reinterpret_cast<const float4*>(Qd);
-  for (int x = tid; x < ncol * dp4; x += nt) {
-    const int c = x / dp4, i = x - c * dp4;
-    T.qt[(int64_t)i * nq + c] = Q4[(int64_t)crep[c] * dp4 + i];
+  (void)crep;
+}
+
+// Every row against its column's first row, a 16-byte word per thread: any difference (two
+// vectors that share a hash) raises the table's flag.
+__global__ void column_check_kernel(const float* __restrict__ Qd, int nq, int dp, ColTable T) {
+  const int dp4 = dp / 4;
+  const int64_t total = (int64_t)nq * dp4;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(x / dp4), i = (int)(x - (int64_t)j * dp4);
+    const int c = T.colof[j];
+    if (c < 0) continue;
+    const int r = T.rep[c];
+    if (r == j) continue;
+    const uint4 a = __ldcg(reinterpret_cast<const uint4*>(Qd + (int64_t)j * dp) + i);
+    const uint4 b = __ldcg(reinterpret_cast<const uint4*>(Qd + (int64_t)r * dp) + i);
+    if (a.x != b.x || a.y != b.y || a.z != b.z || a.w != b.w) T.ncol[1] = 1;
   }
-  for (int c = tid; c < ncol; c += nt) T.qnc[c] = qn[crep[c]];
+}
+
+// The columns' vectors transposed (16-byte words, dimension-major: the block filter reads a
+// word of consecutive columns at once) and their norms.
+__global__ void column_transpose_kernel(const float* __restrict__ Qd, const float* __restrict__ qn, int nq, int dp,
+                                        ColTable T) {
+  const int dp4 = dp / 4;
+  const int ncol = T.ncol[0];
+  const float4* Q4 = reinterpret_cast<const float4*>(Qd);
+  const int64_t total = (int64_t)ncol * dp4;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(x / ncol), c = (int)(x - (int64_t)i * ncol);   // consecutive threads, consecutive columns
+    T.qt[(int64_t)i * nq + c] = Q4[(int64_t)T.rep[c] * dp4 + i];
+    if (i == 0) T.qnc[c] = qn[T.rep[c]];
+  }
 }
 
 // A3 over the columns: Lemma 2 for every (leaf, distinct query vector) pair, then the bound
 // compared with L^k(B) for each row of the column.  The <c_B, q> of all pairs are a small
-// GEMM (leaf centres x query columns): a CTA takes kBfLeaves leaves and runs over every
-// chunk of kBfChunk columns in tiles of kBfCols, K in chunks of kBfK dimensions staged in
-// shared memory, each thread accumulating 2 leaves x 4 columns in registers.  With cos phi = <c_B, q> / ||q||
-// (c_B a unit vector) and the additive slack covering the FP32 dot and the stored cone:
+// GEMM (leaf centres x query columns): a CTA takes kBfLeaves leaves and a chunk of kBfChunk
+// columns, in tiles of kBfCols columns, K in chunks of kBfK dimensions staged in shared
+// memory; each thread accumulates 4 leaves x 8 columns in registers (three 16-byte shared
+// loads per 32 FMAs).  With cos phi = <c_B, q> / ||q|| (c_B a unit vector; 1 / ||q|| taken
+// once per column, its rounding far inside the slack) and the additive slack covering the
+// FP32 dot and the stored cone:
 //   ub = ||q|| (1 + slack)                                  if cos phi >= cos omega - slack
 //   ub = ||q|| (cos phi cos omega + s_up sin omega + 2 slack)  otherwise,
 // with s_up = sqrt(1 - (|cos phi| - slack)_+^2) >= sin phi.  A row (j, k) of the column is
 // kept unless ub < L^k(B).  The leaf's decisions are OR-ed into kept_mask[B] (bit j of word
 // j / 32; zeroed before the launch), the 128-user tiles of every leaf with a kept row are
 // flagged for the user pass, and leaf_flag[B] (zeroed too) counts a leaf's users once.
-constexpr int kBfLeaves = 32;
-constexpr int kBfCols = 64;
+constexpr int kBfLeaves = 64;
+constexpr int kBfCols = 128;
 constexpr int kBfK = 32;
 constexpr int kBfChunk = 256;   // columns per CTA
 constexpr int kBfRows = 1024;   // rows of the CTA's columns staged in shared memory (more: from memory)
-__global__ void __launch_bounds__(256)
+
+// dynamic shared memory of the block filter (mask_words <= kMaxRows / 32)
+struct BfSmem {
+  static constexpr size_t kAs = sizeof(float) * kBfK * kBfLeaves;
+  static constexpr size_t kBs = sizeof(float) * kBfK * kBfCols;
+  static constexpr size_t kLbs = sizeof(float) * kBfLeaves * 65;
+  static constexpr size_t kCrw = sizeof(int2) * kBfRows;
+  static constexpr size_t kCol = sizeof(float) * 2 * kBfChunk + sizeof(int) * (kBfChunk + 4);
+  static size_t bytes(int mask_words) {
+    return kAs + kBs + kLbs + kCrw + kCol + sizeof(uint32_t) * (size_t)kBfLeaves * mask_words;
+  }
+};
+
+__global__ void __launch_bounds__(256, 2)
 block_filter_cols_kernel(const float* __restrict__ bcent, const float* __restrict__ bcos,
                          const float* __restrict__ bsin, const float* __restrict__ LB, int nb, int kmax, int dp,
                          int nq, ColTable T, float slack, uint32_t* __restrict__ kept_mask, int mask_words,
                          const int32_t* __restrict__ bstart, uint8_t* __restrict__ tile_need,
                          int32_t* __restrict__ leaf_flag, unsigned long long* __restrict__ stats, int st_pairs,
                          int st_users, int st_scored, int st_colpairs) {
-  __shared__ __align__(16) float As[kBfK][kBfLeaves];   // centres, dimension-major
-  __shared__ __align__(16) float Bs[kBfK][kBfCols];     // columns, dimension-major
-  __shared__ uint32_t kbits[kBfLeaves][kMaxRows / 32];
-  __shared__ float lbs[kBfLeaves][65];                  // L^k(B), k = 1..64
+  extern __shared__ __align__(16) uint8_t bf_smem[];
+  float(*As)[kBfLeaves] = reinterpret_cast<float(*)[kBfLeaves]>(bf_smem);                 // centres, dim-major
+  float(*Bs)[kBfCols] = reinterpret_cast<float(*)[kBfCols]>(bf_smem + BfSmem::kAs);        // columns, dim-major
+  float(*lbs)[65] = reinterpret_cast<float(*)[65]>(bf_smem + BfSmem::kAs + BfSmem::kBs);   // L^k(B), k = 1..64
+  int2* crw = reinterpret_cast<int2*>(bf_smem + BfSmem::kAs + BfSmem::kBs + BfSmem::kLbs); // (j, k) of the rows
+  float* cqn = reinterpret_cast<float*>(bf_smem + BfSmem::kAs + BfSmem::kBs + BfSmem::kLbs + BfSmem::kCrw);
+  float* cinv = cqn + kBfChunk;              // 1 / ||q|| (0 when ||q|| = 0: no bound)
+  int* cst = reinterpret_cast<int*>(cinv + kBfChunk);   // the columns' rows: cst[c] .. cst[c + 1]
+  uint32_t* kbits = reinterpret_cast<uint32_t*>(bf_smem + BfSmem::kAs + BfSmem::kBs + BfSmem::kLbs +
+                                                BfSmem::kCrw + BfSmem::kCol);           // [kBfLeaves][mask_words]
   __shared__ float cws[kBfLeaves], sws[kBfLeaves];
   __shared__ int kept_sh[kBfLeaves];
-  __shared__ float cqn[kBfChunk];           // the CTA's columns: ||q||
-  __shared__ int cst[kBfChunk + 1];         // their rows: cst[c] .. cst[c + 1] (relative to the first)
-  __shared__ int2 crw[kBfRows];             // (j, k) of those rows
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int B0 = blockIdx.x * kBfLeaves;
   const int nl = min(kBfLeaves, nb - B0);
@@ -351,7 +368,11 @@ block_filter_cols_kernel(const float* __restrict__ bcent, const float* __restric
   const int rbase = T.start[cbeg];
   for (int c = tid; c <= ncol - cbeg; c += 256) {
     cst[c] = T.start[cbeg + c] - rbase;
-    if (c < ncol - cbeg) cqn[c] = T.qnc[cbeg + c];
+    if (c < ncol - cbeg) {
+      const float nrm = T.qnc[cbeg + c];
+      cqn[c] = nrm;
+      cinv[c] = nrm > 0.f ? 1.f / nrm : 0.f;
+    }
   }
   const int nrw = T.start[ncol] - rbase;
   for (int q = tid; q < min(nrw, kBfRows); q += 256) {
@@ -362,15 +383,19 @@ block_filter_cols_kernel(const float* __restrict__ bcent, const float* __restric
     const int k = i / nl + 1, l = i - (k - 1) * nl;   // consecutive threads, consecutive leaves
     lbs[l][k] = LB[(int64_t)(k - 1) * nb + B0 + l];
   }
-  for (int i = tid; i < kBfLeaves * mask_words; i += 256) kbits[i / mask_words][i % mask_words] = 0u;
+  for (int i = tid; i < kBfLeaves * mask_words; i += 256) kbits[i] = 0u;
   if (tid < kBfLeaves) {
     cws[tid] = tid < nl ? bcos[B0 + tid] : -2.f;
     sws[tid] = tid < nl ? bsin[B0 + tid] : 0.f;
     kept_sh[tid] = 0;
   }
-  int kept[2] = {0, 0};
+  int kept[4] = {0, 0, 0, 0};
   for (int col0 = cbeg; col0 < ncol; col0 += kBfCols) {
-    float acc[2][4] = {};
+    float acc[4][8];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
     for (int k0 = 0; k0 < dp; k0 += kBfK) {
       __syncthreads();
       // centres: 16-byte words (4 dimensions) of kBfLeaves rows; consecutive threads take
@@ -396,34 +421,33 @@ block_filter_cols_kernel(const float* __restrict__ bcent, const float* __restric
         Bs[4 * w + 3][c] = v.w;
       }
       __syncthreads();
-#pragma unroll 8
+#pragma unroll 4
       for (int k = 0; k < kBfK; ++k) {
-        const float2 a = *reinterpret_cast<const float2*>(&As[k][2 * ty]);
-        const float4 b = *reinterpret_cast<const float4*>(&Bs[k][4 * tx]);
-        acc[0][0] = fmaf(a.x, b.x, acc[0][0]);
-        acc[0][1] = fmaf(a.x, b.y, acc[0][1]);
-        acc[0][2] = fmaf(a.x, b.z, acc[0][2]);
-        acc[0][3] = fmaf(a.x, b.w, acc[0][3]);
-        acc[1][0] = fmaf(a.y, b.x, acc[1][0]);
-        acc[1][1] = fmaf(a.y, b.y, acc[1][1]);
-        acc[1][2] = fmaf(a.y, b.z, acc[1][2]);
-        acc[1][3] = fmaf(a.y, b.w, acc[1][3]);
+        const float4 a = *reinterpret_cast<const float4*>(&As[k][4 * ty]);
+        const float4 b0 = *reinterpret_cast<const float4*>(&Bs[k][4 * tx]);
+        const float4 b1 = *reinterpret_cast<const float4*>(&Bs[k][64 + 4 * tx]);
+        const float av[4] = {a.x, a.y, a.z, a.w};
+        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
       }
     }
-    // Lemma 2 for the thread's 8 (leaf, column) pairs, then the column's rows
+    // Lemma 2 for the thread's 32 (leaf, column) pairs, then the column's rows
 #pragma unroll
-    for (int a = 0; a < 2; ++a) {
-      const int l = 2 * ty + a;
+    for (int a = 0; a < 4; ++a) {
+      const int l = 4 * ty + a;
       if (l >= nl) continue;
       const float cw = cws[l], sw = sws[l];
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int c = col0 + 4 * tx + b;
+      for (int b = 0; b < 8; ++b) {
+        const int c = col0 + (b < 4 ? 4 * tx + b : 64 + 4 * tx + (b - 4));
         if (c >= ncol) continue;
-        const float nrm = cqn[c - cbeg];
+        const float nrm = cqn[c - cbeg], inv = cinv[c - cbeg];
         float ub = INFINITY;   // no cone bound: every row kept
         if (!(cw < -1.5f) && nrm > 0.f) {
-          const float cphi = fminf(1.f, fmaxf(-1.f, acc[a][b] / nrm));
+          const float cphi = fminf(1.f, fmaxf(-1.f, acc[a][b] * inv));
           const float cl = fmaxf(0.f, fabsf(cphi) - slack);
           const float sphi = sqrtf(fmaxf(0.f, fmaf(-cl, cl, 1.f)));
           if (cphi >= cw - slack) ub = nrm * (1.f + slack);
@@ -441,7 +465,7 @@ block_filter_cols_kernel(const float* __restrict__ bcent, const float* __restric
           const int j = jk.x, k = jk.y;
           const float lb = (k <= kmax) ? (k <= 64 ? lbs[l][k] : LB[(int64_t)(k - 1) * nb + B0 + l]) : -INFINITY;
           if (!(ub < lb)) {
-            atomicOr(&kbits[l][j >> 5], 1u << (j & 31));
+            atomicOr(&kbits[l * mask_words + (j >> 5)], 1u << (j & 31));
             ++kept[a];
           }
         }
@@ -449,11 +473,11 @@ block_filter_cols_kernel(const float* __restrict__ bcent, const float* __restric
     }
   }
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
-    if (kept[a]) atomicAdd(&kept_sh[2 * ty + a], kept[a]);
+  for (int a = 0; a < 4; ++a)
+    if (kept[a]) atomicAdd(&kept_sh[4 * ty + a], kept[a]);
   __syncthreads();
   for (int i = tid; i < nl * mask_words; i += 256) {
-    const uint32_t w = kbits[i / mask_words][i % mask_words];
+    const uint32_t w = kbits[i];
     if (w) atomicOr(&kept_mask[(int64_t)B0 * mask_words + i], w);
   }
   // the user pass streams the 128-user tiles that hold a user of a leaf with a kept row
@@ -462,7 +486,7 @@ block_filter_cols_kernel(const float* __restrict__ bcent, const float* __restric
     for (int t = t0; t <= t1; ++t) tile_need[t] = 1;
   }
   if (tid == 0) atomicAdd(&stats[st_colpairs], (unsigned long long)nl * (unsigned long long)(ncol - cbeg));
-  if (tid < 32) {
+  if (tid < kBfLeaves) {
     unsigned long long pairs = 0, users = 0, scored = 0;
     if (tid < nl && kept_sh[tid]) {
       const unsigned long long u = (unsigned long long)(bstart[B0 + tid + 1] - bstart[B0 + tid]);
@@ -475,7 +499,7 @@ block_filter_cols_kernel(const float* __restrict__ bcent, const float* __restric
       users += __shfl_xor_sync(0xffffffffu, users, o);
       scored += __shfl_xor_sync(0xffffffffu, scored, o);
     }
-    if (tid == 0 && pairs) {
+    if ((tid & 31) == 0 && pairs) {
       atomicAdd(&stats[st_pairs], pairs);
       atomicAdd(&stats[st_users], users);
       atomicAdd(&stats[st_scored], scored);
@@ -1336,10 +1360,14 @@ sah_status prepare_user_pass_tc(Index* ix, const float* Qd, const float* qn, con
   while (ht < 2 * nq) ht <<= 1;
   const size_t tsmem = sizeof(int32_t) * (2 * (size_t)ht + 5 * (size_t)nq);
   SAH_TRY(raise_smem_limit((const void*)column_table_kernel, tsmem));
-  column_table_kernel<<<1, 1024, tsmem, st>>>(Qd, qn, qh, nq, ix->dp, kk, modes, ix->kmax, ix->n, ix->pnorm, ht,
-                                               T);
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
+  column_table_kernel<<<1, 1024, tsmem, st>>>(Qd, qh, nq, ix->dp, kk, modes, ix->kmax, ix->n, ix->pnorm, ht, T, 0);
+  column_check_kernel<<<sms, 512, 0, st>>>(Qd, nq, ix->dp, T);
+  column_table_kernel<<<1, 1024, tsmem, st>>>(Qd, qh, nq, ix->dp, kk, modes, ix->kmax, ix->n, ix->pnorm, ht, T, 1);
+  column_transpose_kernel<<<sms, 512, 0, st>>>(Qd, qn, nq, ix->dp, T);
   SAH_CUDA(cudaGetLastError());
-  if (launches) *launches += 1;
+  if (launches) *launches += 4;
   if (ix->prm.tc_user_pass == 2) {
     // the FP8 user pass: every row of the sub-batch in E4M3 with its scale
     launch_e4m3_rows(Qd, nq, ix->dp, ix->d, T.q8, T.qsc, st);
@@ -1358,7 +1386,9 @@ sah_status block_filter_tc(Index* ix, void* scratch, int nq, uint32_t* kept_mask
   int32_t* leaf_flag = reinterpret_cast<int32_t*>(kept_mask + (size_t)ix->nb * mask_words);
   SAH_CUDA(cudaMemsetAsync(kept_mask, 0, sizeof(uint32_t) * (size_t)ix->nb * mask_words + sizeof(int32_t) * ix->nb, st));
   const dim3 grid((unsigned)((ix->nb + kBfLeaves - 1) / kBfLeaves), (unsigned)((nq + kBfChunk - 1) / kBfChunk));
-  block_filter_cols_kernel<<<grid, 256, 0, st>>>(ix->bcent, ix->bcos, ix->bsin, ix->LB, ix->nb, ix->kmax, ix->dp, nq, T,
+  const size_t smem = BfSmem::bytes(mask_words);
+  SAH_TRY(raise_smem_limit((const void*)block_filter_cols_kernel, smem));
+  block_filter_cols_kernel<<<grid, 256, smem, st>>>(ix->bcent, ix->bcos, ix->bsin, ix->LB, ix->nb, ix->kmax, ix->dp, nq, T,
                                                  ix->cone_slack, kept_mask, mask_words, ix->bstart, tile_need,
                                                  leaf_flag, stats, st_pairs, st_users, st_scored, st_colpairs);
   SAH_CUDA(cudaGetLastError());

@@ -77,8 +77,10 @@ def _gauss_rows(rng, rows, d, sigma):
     return _rescale_rows(X, np.exp(rng.normal(0.0, sigma, rows)))
 
 
-def _mf_rows(rng, rows, W, sigma):
+def _mf_rows(rng, rows, W, sigma, nonneg=False):
     G = rng.standard_normal((rows, W.shape[0]))
+    if nonneg:
+        G = np.abs(G)
     return _rescale_rows(G @ W, np.exp(rng.normal(0.0, sigma, rows)))
 
 
@@ -108,15 +110,20 @@ def make(name: str = "c1", seed: int = 0, **override) -> Workload:
     if r["kind"] == "gauss":
         P = _gauss_rows(rng, n, d, r["sigma"])
         U = _gauss_rows(rng, m, d, r["sigma"])
-    elif r["kind"] == "mf":
+    elif r["kind"] in ("mf", "nmf"):
+        # "nmf": non-negative factors (|N(0,1)| entries), like the NMF embeddings the paper's
+        # recommendation datasets are made of; "mf": zero-mean factors
+        nonneg = r["kind"] == "nmf"
         rank = int(r.get("rank", 50))
         W = rng.standard_normal((rank, d)) / np.sqrt(rank)
-        P = _mf_rows(rng, n, W, r["sigma"])
+        if nonneg:
+            W = np.abs(W)
+        P = _mf_rows(rng, n, W, r["sigma"], nonneg)
         nb = int(round(r["boost_frac"] * n))
         if nb:
             boosted = rng.choice(n, size=nb, replace=False)
             P[boosted] *= r["boost"]
-        U = _mf_rows(rng, m, W, r["sigma"])
+        U = _mf_rows(rng, m, W, r["sigma"], nonneg)
     else:
         raise ValueError(r["kind"])
     nq = min(int(r["nq"]), n)
