@@ -886,9 +886,11 @@ def main():
         torch.distributed.barrier()
     value, _ = whole_job_value(sum(times), nq, args.steps, world, torch_max_reducer(dev))
     # back-to-back steps after the timed ones: the sustained rate and clocks under load
-    with ClockSampler(local) as clk2:
-        sus_value, sus_steps = main_b.sustained(args.sustain_s)
-    clocks_sus = clk2.summary()
+    sus_value, sus_steps, clocks_sus = None, 0, None
+    if args.sustain_s > 0:
+        with ClockSampler(local) as clk2:
+            sus_value, sus_steps = main_b.sustained(args.sustain_s)
+        clocks_sus = clk2.summary()
     e2e_times, h2d, d2h = main_b.e2e(args.steps, args.warmup, flush)
     e2e_value, _ = whole_job_value(sum(e2e_times), nq, args.steps, world, torch_max_reducer(dev))
     sms, lau, st = main_b.stages()
