@@ -305,95 +305,76 @@ __global__ void column_transpose_kernel(const float* __restrict__ Qd, const floa
   }
 }
 
-// A3 over the columns: Lemma 2 for every (leaf, distinct query vector) pair, then the bound
-// compared with L^k(B) for each row of the column.  The <c_B, q> of all pairs are a small
-// GEMM (leaf centres x query columns): a CTA takes kBfLeaves leaves and a chunk of kBfChunk
-// columns, in tiles of kBfCols columns, K in chunks of kBfK dimensions staged in shared
-// memory; each thread accumulates 4 leaves x 8 columns in registers (three 16-byte shared
-// loads per 32 FMAs).  With cos phi = <c_B, q> / ||q|| (c_B a unit vector; 1 / ||q|| taken
-// once per column, its rounding far inside the slack) and the additive slack covering the
-// FP32 dot and the stored cone:
+// A3 for the tensor-core user pass: Lemma 2 decides which 128-user tiles the GEMM scores.  A
+// leaf is needed once one row (j, k) of one column passes its bound: ub >= L^k(B).  (A pair
+// the bound prunes is decided "no" by the user pass's own tests anyway, which are tighter,
+// so no per-row mask is kept.)  The <c_B, q> are a small GEMM (leaf centres x query
+// columns): a CTA takes kBfLeaves leaves and runs over the sub-batch's columns in tiles of
+// kBfCols, K in chunks of kBfK dimensions staged in shared memory, each thread accumulating
+// 2 leaves x 8 columns; after every column tile the CTA stops if all its leaves are needed.
+// With cos phi = <c_B, q> / ||q|| (c_B a unit vector; 1 / ||q|| taken once per column, its
+// rounding far inside the slack) and the additive slack covering the FP32 dot and the cone:
 //   ub = ||q|| (1 + slack)                                  if cos phi >= cos omega - slack
 //   ub = ||q|| (cos phi cos omega + s_up sin omega + 2 slack)  otherwise,
-// with s_up = sqrt(1 - (|cos phi| - slack)_+^2) >= sin phi.  A row (j, k) of the column is
-// kept unless ub < L^k(B).  The leaf's decisions are OR-ed into kept_mask[B] (bit j of word
-// j / 32; zeroed before the launch), the 128-user tiles of every leaf with a kept row are
-// flagged for the user pass, and leaf_flag[B] (zeroed too) counts a leaf's users once.
-constexpr int kBfLeaves = 64;
+// with s_up = sqrt(1 - (|cos phi| - slack)_+^2) >= sin phi.  The tiles of every needed leaf
+// are flagged for the user pass, and leaf_flag[B] (zeroed before the launch) counts a
+// leaf's users once.
+constexpr int kBfLeaves = 32;
 constexpr int kBfCols = 128;
 constexpr int kBfK = 32;
-constexpr int kBfChunk = 256;   // columns per CTA
-constexpr int kBfRows = 1024;   // rows of the CTA's columns staged in shared memory (more: from memory)
+constexpr int kBfRows = 512;    // rows of a column tile staged in shared memory (more: from memory)
 
-// dynamic shared memory of the block filter (mask_words <= kMaxRows / 32)
-struct BfSmem {
-  static constexpr size_t kAs = sizeof(float) * kBfK * kBfLeaves;
-  static constexpr size_t kBs = sizeof(float) * kBfK * kBfCols;
-  static constexpr size_t kLbs = sizeof(float) * kBfLeaves * 65;
-  static constexpr size_t kCrw = sizeof(int2) * kBfRows;
-  static constexpr size_t kCol = sizeof(float) * 2 * kBfChunk + sizeof(int) * (kBfChunk + 4);
-  static size_t bytes(int mask_words) {
-    return kAs + kBs + kLbs + kCrw + kCol + sizeof(uint32_t) * (size_t)kBfLeaves * mask_words;
-  }
-};
-
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256)
 block_filter_cols_kernel(const float* __restrict__ bcent, const float* __restrict__ bcos,
                          const float* __restrict__ bsin, const float* __restrict__ LB, int nb, int kmax, int dp,
-                         int nq, ColTable T, float slack, uint32_t* __restrict__ kept_mask, int mask_words,
-                         const int32_t* __restrict__ bstart, uint8_t* __restrict__ tile_need,
-                         int32_t* __restrict__ leaf_flag, unsigned long long* __restrict__ stats, int st_pairs,
-                         int st_users, int st_scored, int st_colpairs) {
-  extern __shared__ __align__(16) uint8_t bf_smem[];
-  float(*As)[kBfLeaves] = reinterpret_cast<float(*)[kBfLeaves]>(bf_smem);                 // centres, dim-major
-  float(*Bs)[kBfCols] = reinterpret_cast<float(*)[kBfCols]>(bf_smem + BfSmem::kAs);        // columns, dim-major
-  float(*lbs)[65] = reinterpret_cast<float(*)[65]>(bf_smem + BfSmem::kAs + BfSmem::kBs);   // L^k(B), k = 1..64
-  int2* crw = reinterpret_cast<int2*>(bf_smem + BfSmem::kAs + BfSmem::kBs + BfSmem::kLbs); // (j, k) of the rows
-  float* cqn = reinterpret_cast<float*>(bf_smem + BfSmem::kAs + BfSmem::kBs + BfSmem::kLbs + BfSmem::kCrw);
-  float* cinv = cqn + kBfChunk;              // 1 / ||q|| (0 when ||q|| = 0: no bound)
-  int* cst = reinterpret_cast<int*>(cinv + kBfChunk);   // the columns' rows: cst[c] .. cst[c + 1]
-  uint32_t* kbits = reinterpret_cast<uint32_t*>(bf_smem + BfSmem::kAs + BfSmem::kBs + BfSmem::kLbs +
-                                                BfSmem::kCrw + BfSmem::kCol);           // [kBfLeaves][mask_words]
+                         int nq, ColTable T, float slack, const int32_t* __restrict__ bstart,
+                         uint8_t* __restrict__ tile_need, int32_t* __restrict__ leaf_flag,
+                         unsigned long long* __restrict__ stats, int st_pairs, int st_users, int st_scored,
+                         int st_colpairs) {
+  __shared__ __align__(16) float As[kBfK][kBfLeaves];   // centres, dimension-major
+  __shared__ __align__(16) float Bs[kBfK][kBfCols];     // columns, dimension-major
+  __shared__ float lbs[kBfLeaves][65];                  // L^k(B), k = 1..64
   __shared__ float cws[kBfLeaves], sws[kBfLeaves];
-  __shared__ int kept_sh[kBfLeaves];
+  __shared__ int needed[kBfLeaves];
+  __shared__ float cqn[kBfCols], cinv[kBfCols];         // the tile's columns: ||q||, 1 / ||q||
+  __shared__ int cst[kBfCols + 1];                      // their rows: cst[c] .. cst[c + 1] (tile-relative)
+  __shared__ int2 crw[kBfRows];                         // (j, k) of those rows
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int B0 = blockIdx.x * kBfLeaves;
   const int nl = min(kBfLeaves, nb - B0);
-  const int ncol_all = *T.ncol;
-  const int cbeg = blockIdx.y * kBfChunk;
-  if (cbeg >= ncol_all) return;
-  const int ncol = min(ncol_all, cbeg + kBfChunk);   // columns [cbeg, ncol)
+  const int ncol = *T.ncol;
   const int dp4 = dp / 4;
   const int k64 = min(kmax, 64);
-  const int rbase = T.start[cbeg];
-  for (int c = tid; c <= ncol - cbeg; c += 256) {
-    cst[c] = T.start[cbeg + c] - rbase;
-    if (c < ncol - cbeg) {
-      const float nrm = T.qnc[cbeg + c];
-      cqn[c] = nrm;
-      cinv[c] = nrm > 0.f ? 1.f / nrm : 0.f;
-    }
-  }
-  const int nrw = T.start[ncol] - rbase;
-  for (int q = tid; q < min(nrw, kBfRows); q += 256) {
-    const int4 rw = T.rows[rbase + q];
-    crw[q] = make_int2(rw.x & 0x3fffffff, rw.y);
-  }
   for (int i = tid; i < nl * k64; i += 256) {
     const int k = i / nl + 1, l = i - (k - 1) * nl;   // consecutive threads, consecutive leaves
     lbs[l][k] = LB[(int64_t)(k - 1) * nb + B0 + l];
   }
-  for (int i = tid; i < kBfLeaves * mask_words; i += 256) kbits[i] = 0u;
   if (tid < kBfLeaves) {
     cws[tid] = tid < nl ? bcos[B0 + tid] : -2.f;
     sws[tid] = tid < nl ? bsin[B0 + tid] : 0.f;
-    kept_sh[tid] = 0;
+    needed[tid] = tid < nl ? 0 : 1;
   }
-  int kept[4] = {0, 0, 0, 0};
-  for (int col0 = cbeg; col0 < ncol; col0 += kBfCols) {
-    float acc[4][8];
+  int tiles_done = 0;
+  for (int col0 = 0; col0 < ncol; col0 += kBfCols) {
+    __syncthreads();
+    const int nc = min(kBfCols, ncol - col0);
+    const int rbase = T.start[col0];
+    for (int c = tid; c <= nc; c += 256) {
+      cst[c] = T.start[col0 + c] - rbase;
+      if (c < nc) {
+        const float nrm = T.qnc[col0 + c];
+        cqn[c] = nrm;
+        cinv[c] = nrm > 0.f ? 1.f / nrm : 0.f;
+      }
+    }
+    const int nrw = T.start[col0 + nc] - rbase;
+    for (int q = tid; q < min(nrw, kBfRows); q += 256) {
+      const int4 rw = T.rows[rbase + q];
+      crw[q] = make_int2(rw.x & 0x3fffffff, rw.y);
+    }
+    float acc[2][8];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 2; ++a)
 #pragma unroll
       for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
     for (int k0 = 0; k0 < dp; k0 += kBfK) {
@@ -414,7 +395,7 @@ block_filter_cols_kernel(const float* __restrict__ bcent, const float* __restric
         const int w = i / kBfCols, c = i % kBfCols;
         const int wg = k0 / 4 + w;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (col0 + c < ncol && wg < dp4) v = T.qt[(int64_t)wg * nq + col0 + c];
+        if (c < nc && wg < dp4) v = T.qt[(int64_t)wg * nq + col0 + c];
         Bs[4 * w][c] = v.x;
         Bs[4 * w + 1][c] = v.y;
         Bs[4 * w + 2][c] = v.z;
@@ -423,75 +404,64 @@ block_filter_cols_kernel(const float* __restrict__ bcent, const float* __restric
       __syncthreads();
 #pragma unroll 4
       for (int k = 0; k < kBfK; ++k) {
-        const float4 a = *reinterpret_cast<const float4*>(&As[k][4 * ty]);
+        const float2 a = *reinterpret_cast<const float2*>(&As[k][2 * ty]);
         const float4 b0 = *reinterpret_cast<const float4*>(&Bs[k][4 * tx]);
         const float4 b1 = *reinterpret_cast<const float4*>(&Bs[k][64 + 4 * tx]);
-        const float av[4] = {a.x, a.y, a.z, a.w};
+        const float av[2] = {a.x, a.y};
         const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 2; ++i)
 #pragma unroll
           for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
       }
     }
-    // Lemma 2 for the thread's 32 (leaf, column) pairs, then the column's rows
+    // Lemma 2 for the thread's (leaf, column) pairs of leaves not yet needed
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int l = 4 * ty + a;
+    for (int a = 0; a < 2; ++a) {
+      const int l = 2 * ty + a;
       if (l >= nl) continue;
       const float cw = cws[l], sw = sws[l];
 #pragma unroll
       for (int b = 0; b < 8; ++b) {
-        const int c = col0 + (b < 4 ? 4 * tx + b : 64 + 4 * tx + (b - 4));
-        if (c >= ncol) continue;
-        const float nrm = cqn[c - cbeg], inv = cinv[c - cbeg];
+        const int c = b < 4 ? 4 * tx + b : 64 + 4 * tx + (b - 4);
+        if (c >= nc || needed[l]) continue;
+        const float nrm = cqn[c];
         float ub = INFINITY;   // no cone bound: every row kept
         if (!(cw < -1.5f) && nrm > 0.f) {
-          const float cphi = fminf(1.f, fmaxf(-1.f, acc[a][b] * inv));
+          const float cphi = fminf(1.f, fmaxf(-1.f, acc[a][b] * cinv[c]));
           const float cl = fmaxf(0.f, fabsf(cphi) - slack);
           const float sphi = sqrtf(fmaxf(0.f, fmaf(-cl, cl, 1.f)));
           if (cphi >= cw - slack) ub = nrm * (1.f + slack);
           else ub = nrm * (fmaf(cphi, cw, sphi * sw) + 2.f * slack);
         }
-        const int r0 = cst[c - cbeg], r1 = cst[c - cbeg + 1];
-        for (int q = r0; q < r1; ++q) {
-          int2 jk;
-          if (q < kBfRows) {
-            jk = crw[q];
-          } else {
-            const int4 rw = T.rows[rbase + q];
-            jk = make_int2(rw.x & 0x3fffffff, rw.y);
-          }
-          const int j = jk.x, k = jk.y;
+        for (int q = cst[c]; q < cst[c + 1]; ++q) {
+          const int k = q < kBfRows ? crw[q].y : T.rows[rbase + q].y;
           const float lb = (k <= kmax) ? (k <= 64 ? lbs[l][k] : LB[(int64_t)(k - 1) * nb + B0 + l]) : -INFINITY;
           if (!(ub < lb)) {
-            atomicOr(&kbits[l * mask_words + (j >> 5)], 1u << (j & 31));
-            ++kept[a];
+            needed[l] = 1;
+            break;
           }
         }
       }
     }
+    ++tiles_done;
+    if (__syncthreads_and(tid >= kBfLeaves || needed[tid])) break;   // every leaf needed
   }
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-    if (kept[a]) atomicAdd(&kept_sh[4 * ty + a], kept[a]);
   __syncthreads();
-  for (int i = tid; i < nl * mask_words; i += 256) {
-    const uint32_t w = kbits[i];
-    if (w) atomicOr(&kept_mask[(int64_t)B0 * mask_words + i], w);
-  }
-  // the user pass streams the 128-user tiles that hold a user of a leaf with a kept row
-  if (tid < nl && kept_sh[tid] > 0) {
+  // the user pass streams the 128-user tiles of every needed leaf
+  if (tid < nl && needed[tid]) {
     const int t0 = bstart[B0 + tid] / kUM, t1 = (bstart[B0 + tid + 1] - 1) / kUM;
     for (int t = t0; t <= t1; ++t) tile_need[t] = 1;
   }
-  if (tid == 0) atomicAdd(&stats[st_colpairs], (unsigned long long)nl * (unsigned long long)(ncol - cbeg));
-  if (tid < kBfLeaves) {
+  if (tid == 0)
+    atomicAdd(&stats[st_colpairs], (unsigned long long)nl * (unsigned long long)min(ncol, tiles_done * kBfCols));
+  if (tid < 32) {
+    // a needed leaf's users are scored against every column (and every row of the sub-batch)
     unsigned long long pairs = 0, users = 0, scored = 0;
-    if (tid < nl && kept_sh[tid]) {
+    if (tid < nl && needed[tid]) {
       const unsigned long long u = (unsigned long long)(bstart[B0 + tid + 1] - bstart[B0 + tid]);
-      pairs = kept_sh[tid];
-      scored = (unsigned long long)kept_sh[tid] * u;
+      pairs = (unsigned long long)T.start[ncol];
+      scored = pairs * u;
       if (atomicExch(&leaf_flag[B0 + tid], 1) == 0) users = u;   // the leaf's users, once
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -499,7 +469,7 @@ block_filter_cols_kernel(const float* __restrict__ bcent, const float* __restric
       users += __shfl_xor_sync(0xffffffffu, users, o);
       scored += __shfl_xor_sync(0xffffffffu, scored, o);
     }
-    if ((tid & 31) == 0 && pairs) {
+    if (tid == 0 && pairs) {
       atomicAdd(&stats[st_pairs], pairs);
       atomicAdd(&stats[st_users], users);
       atomicAdd(&stats[st_scored], scored);
@@ -1382,15 +1352,13 @@ sah_status block_filter_tc(Index* ix, void* scratch, int nq, uint32_t* kept_mask
                            cudaStream_t st) {
   if (ix->nb == 0 || nq == 0) return SAH_OK;
   const ColTable T = col_table_at(scratch, nq, ix->dp);
-  // the kept bits and the leaf flags after them are OR-ed / set by the CTAs of every column chunk
+  // the leaf flags (after the kept-row words, which this path leaves unused) start zero
   int32_t* leaf_flag = reinterpret_cast<int32_t*>(kept_mask + (size_t)ix->nb * mask_words);
-  SAH_CUDA(cudaMemsetAsync(kept_mask, 0, sizeof(uint32_t) * (size_t)ix->nb * mask_words + sizeof(int32_t) * ix->nb, st));
-  const dim3 grid((unsigned)((ix->nb + kBfLeaves - 1) / kBfLeaves), (unsigned)((nq + kBfChunk - 1) / kBfChunk));
-  const size_t smem = BfSmem::bytes(mask_words);
-  SAH_TRY(raise_smem_limit((const void*)block_filter_cols_kernel, smem));
-  block_filter_cols_kernel<<<grid, 256, smem, st>>>(ix->bcent, ix->bcos, ix->bsin, ix->LB, ix->nb, ix->kmax, ix->dp, nq, T,
-                                                 ix->cone_slack, kept_mask, mask_words, ix->bstart, tile_need,
-                                                 leaf_flag, stats, st_pairs, st_users, st_scored, st_colpairs);
+  SAH_CUDA(cudaMemsetAsync(leaf_flag, 0, sizeof(int32_t) * ix->nb, st));
+  const unsigned grid = (unsigned)((ix->nb + kBfLeaves - 1) / kBfLeaves);
+  block_filter_cols_kernel<<<grid, 256, 0, st>>>(ix->bcent, ix->bcos, ix->bsin, ix->LB, ix->nb, ix->kmax, ix->dp, nq, T,
+                                                 ix->cone_slack, ix->bstart, tile_need, leaf_flag, stats, st_pairs,
+                                                 st_users, st_scored, st_colpairs);
   SAH_CUDA(cudaGetLastError());
   return SAH_OK;
 }
@@ -1490,7 +1458,7 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
   SAH_CUDA(cudaGetLastError());
   if (launches) *launches += 1;
   SAH_TRY(launch_pair_rescore(ix, resc, resc_count, surv_cap, Qd, qn, kk, bitmap, words, surv, surv_count, stats,
-                               st_yes, st_fp64, nq, sms, st, kept_mask, mask_words));
+                               st_yes, st_fp64, nq, sms, st, nullptr, mask_words));
   SAH_CUDA(cudaGetLastError());
   if (launches) *launches += 1;
   return SAH_OK;
