@@ -1106,22 +1106,12 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
             }
           }
         } else {
-        // a user whose 32 scores pass writes them, as a candidate block, for the resolve kernel
-          auto push_block = [&](bool mine, const float (&vv)[64], int h, int col0) {
-            const unsigned m = __ballot_sync(0xffffffffu, mine);
-            if (m == 0u) return;
-            unsigned long long b0 = 0;
-            if (lane == __ffs(m) - 1) b0 = atomicAdd(p.cand_count, (unsigned long long)__popc(m));
-            const unsigned long long slot_i = __shfl_sync(0xffffffffu, b0, __ffs(m) - 1) + __popc(m & ((1u << lane) - 1u));
-            if (mine && (int64_t)slot_i < p.resc_cap) {
-              CandBlock* cb = p.cand + slot_i;
-              reinterpret_cast<int4*>(cb)[0] = make_int4((int32_t)r, col0, 0, 0);
-              float4* d4 = reinterpret_cast<float4*>(cb->s);
-#pragma unroll
-              for (int i = 0; i < 8; ++i)
-                d4[i] = make_float4(vv[32 * h + 4 * i], vv[32 * h + 4 * i + 1], vv[32 * h + 4 * i + 2], vv[32 * h + 4 * i + 3]);
-            }
-          };
+          // sparse candidates: the hot loop only marks the 32-column groups some user of the
+          // warp passes; those groups are read again from TMEM and every passing user writes
+          // its 32 scores, as a candidate block, for the resolve kernel.  (Keeping the block
+          // writes out of the unrolled loop keeps it small: with them inside, the pass took a
+          // third longer although few groups pass.)
+          uint32_t need = 0;
 #pragma unroll
           for (int x2 = 0; x2 < W / 64; ++x2) {
             if (64 * x2 < rem) {
@@ -1138,8 +1128,36 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
               }
               const bool a0 = max32_at<0>(vv) >= thr[2 * x2];
               const bool a1 = max32_at<32>(vv) >= thr[2 * x2 + 1];
-              push_block(a0, vv, 0, c0 + cs0 + 64 * x2);
-              push_block(a1, vv, 1, c0 + cs0 + 64 * x2 + 32);
+              need |= ((__any_sync(0xffffffffu, a0) ? 1u : 0u) | (__any_sync(0xffffffffu, a1) ? 2u : 0u)) << (2 * x2);
+            }
+          }
+          while (need) {
+            const int x = __ffs(need) - 1;             // 32-column group of the slice
+            need &= need - 1;
+            const int cw = cs0 + 32 * x;               // set column of the group's first score
+            const int left = nn - cw;
+            float v[32];
+            tmem_ld32_wait(acc_addr + 32 * x, v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              if constexpr (F8) v[i] = (v[i] * csq[cw + i < SETN ? cw + i : SETN - 1]) * su;
+              if (i >= left) v[i] = -INFINITY;
+            }
+            // the group's threshold, as in the fast test
+            const float2 gg = gq[cw >> 5];
+            const float t = valid ? __fsub_rd(Lm(__float_as_int(gg.y), ul, E), __fmul_ru(cu, gg.x)) : INFINITY;
+            const bool mine = max32_at<0>(v) >= t;
+            const unsigned m = __ballot_sync(0xffffffffu, mine);
+            if (m == 0u) continue;
+            unsigned long long b0 = 0;
+            if (lane == __ffs(m) - 1) b0 = atomicAdd(p.cand_count, (unsigned long long)__popc(m));
+            const unsigned long long slot_i = __shfl_sync(0xffffffffu, b0, __ffs(m) - 1) + __popc(m & ((1u << lane) - 1u));
+            if (mine && (int64_t)slot_i < p.resc_cap) {
+              CandBlock* cb = p.cand + slot_i;
+              reinterpret_cast<int4*>(cb)[0] = make_int4((int32_t)r, c0 + cw, 0, 0);
+              float4* d4 = reinterpret_cast<float4*>(cb->s);
+#pragma unroll
+              for (int i = 0; i < 8; ++i) d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
             }
           }
         }
