@@ -455,6 +455,24 @@ __global__ void block_lower_bounds_kernel(const float* __restrict__ Lt, const fl
   LB[(int64_t)k * nb + B] = mn;
 }
 
+// The same minimum, min over u of (L_u^k - E_u) / ||u|| rounded down, over each tile of 128
+// consecutive user positions (the tensor-core user pass's tiles).
+__global__ void tile_lower_bounds_kernel(const float* __restrict__ Lt, const float* __restrict__ Eu,
+                                         const float* __restrict__ unorm, int64_t m, int kmax, int ntiles,
+                                         float* __restrict__ TLB) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)ntiles * kmax) return;
+  const int k = (int)(t / ntiles), tile = (int)(t % ntiles);
+  float mn = INFINITY;
+  const int64_t r1 = m < (int64_t)(tile + 1) * 128 ? m : (int64_t)(tile + 1) * 128;
+  for (int64_t r = (int64_t)tile * 128; r < r1; ++r) {
+    const float L = Lt[(int64_t)k * m + r];
+    const float v = (L == -INFINITY) ? -INFINITY : __fdiv_rd(__fsub_rd(L, Eu[r]), unorm[r]);
+    mn = fminf(mn, v);
+  }
+  TLB[(int64_t)k * ntiles + tile] = mn;
+}
+
 // leaf (block) of every user position
 __global__ void user_block_kernel(const int32_t* __restrict__ bstart, int nb, int32_t* __restrict__ ublock) {
   const int B = blockIdx.x;
@@ -762,6 +780,13 @@ sah_status build_index_device(Index* ix, const float* U_dev, const float* P_dev,
   block_lower_bounds_kernel<<<grid_for((int64_t)kmax * ix->nb, 256), 256, 0, st>>>(
       ix->Lt, ix->Eu, ix->unorm, ix->bstart, ix->nb, mz, kmax, ix->LB);
   SAH_CUDA(cudaGetLastError());
+  {
+    const int ntiles = (int)((mz + 127) / 128);
+    SAH_TRY(dev_alloc(ix, (void**)&ix->tile_lb, sizeof(float) * (size_t)kmax * ntiles));
+    tile_lower_bounds_kernel<<<grid_for((int64_t)kmax * ntiles, 256), 256, 0, st>>>(ix->Lt, ix->Eu, ix->unorm, mz,
+                                                                                   kmax, ntiles, ix->tile_lb);
+    SAH_CUDA(cudaGetLastError());
+  }
   SAH_CUDA(cudaStreamSynchronize(st));
 
   cudaFreeAsync(pn_raw, st);

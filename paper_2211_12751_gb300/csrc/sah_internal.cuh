@@ -121,6 +121,7 @@ struct Index {
   float* bcos = nullptr;      // cos omega (-2 marks a zero centre: no cone bound)
   float* bsin = nullptr;      // sin omega
   float* LB = nullptr;        // [kmax][nb]: L^k(B) for unit users, rounded down
+  float* tile_lb = nullptr;   // [kmax][ceil(m_nz / 128)]: the same minimum over each 128-user tile
 
   // lower-bound arrays (Alg. 4): Lt[k-1][u] = k-th largest FP32 score of u over P'
   float* Lt = nullptr;        // [kmax][m_nz]

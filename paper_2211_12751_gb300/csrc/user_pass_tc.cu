@@ -158,9 +158,9 @@ __device__ int block_exclusive_scan(int v, int* wsum, int* total) {
 // nothing unless that check raised the flag (two different vectors with one hash); then the
 // table is built again with every probe comparing the rows bitwise.
 __global__ void __launch_bounds__(1024, 1)
-column_table_kernel(const float* __restrict__ Qd, const uint64_t* __restrict__ qh, int nq, int dp,
-                    const int32_t* __restrict__ kk, const int32_t* __restrict__ modes, int kmax, int64_t n,
-                    const float* __restrict__ pnorm, int ht, ColTable T, int mode) {
+column_table_kernel(const float* __restrict__ Qd, const float* __restrict__ qn, const uint64_t* __restrict__ qh,
+                    int nq, int dp, const int32_t* __restrict__ kk, const int32_t* __restrict__ modes, int kmax,
+                    int64_t n, const float* __restrict__ pnorm, int ht, int npow, ColTable T, int mode) {
   extern __shared__ int32_t sm[];
   __shared__ int wsum[32];
   __shared__ int total_sh;
@@ -172,6 +172,8 @@ column_table_kernel(const float* __restrict__ Qd, const uint64_t* __restrict__ q
   int32_t* cnt = cid + nq;         // [nq] rows per column, then the scatter cursor
   int32_t* kq = cnt + nq;          // [nq] largest k <= k_max per column
   int32_t* crep = kq + nq;         // [nq] the first row of each column
+  float* skey = reinterpret_cast<float*>(crep + nq);   // [npow] sort keys (npow: a power of two >= nq)
+  int32_t* sidx = reinterpret_cast<int32_t*>(skey + npow);
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int i = tid; i < ht; i += nt) {
     owner[i] = -1;
@@ -242,16 +244,55 @@ column_table_kernel(const float* __restrict__ Qd, const uint64_t* __restrict__ q
     if (k <= kmax) atomicMax(&kq[cc], k);
   }
   __syncthreads();
+  // The columns in descending order of ||q|| (columns whose rows have no bound, k > k_max,
+  // first; equal norms by first row): the user pass scores, per tile of users, only the
+  // prefix of columns whose norm can reach the tile's bound.  A bitonic sort of
+  // (key, column) pairs, then every table renumbered.
+  for (int i = tid; i < npow; i += nt) {
+    skey[i] = i < ncol ? (kq[i] > 0 ? qn[crep[i]] : INFINITY) : -INFINITY;
+    sidx[i] = i < ncol ? i : INT_MAX;
+  }
+  __syncthreads();
+  for (int size = 2; size <= npow; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = tid; i < npow; i += nt) {
+        const int j = i ^ stride;
+        if (j > i) {
+          const float ki = skey[i], kj = skey[j];
+          const int ii = sidx[i], ij = sidx[j];
+          const bool i_first = ki > kj || (ki == kj && ii < ij);
+          if (((i & size) == 0) != i_first) {
+            skey[i] = kj;
+            skey[j] = ki;
+            sidx[i] = ij;
+            sidx[j] = ii;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // position pos holds old column sidx[pos]: its first row, largest k and row count move
+  // there (cid holds the counts from now on, minrow the old-to-new map)
+  for (int pos = tid; pos < ncol; pos += nt) {
+    const int old = sidx[pos];
+    T.rep[pos] = crep[old];
+    T.kq[pos] = kq[old];
+    cid[pos] = cnt[old];
+    minrow[old] = pos;
+  }
+  __syncthreads();
+  for (int j = tid; j < nq; j += nt)
+    if (colof[j] >= 0) colof[j] = minrow[colof[j]];
   // CSR starts of the columns' rows
   const int perc = (ncol + nt - 1) / nt;
   const int c0 = tid * perc, c1 = min(ncol, c0 + perc);
   int s = 0;
-  for (int cc = c0; cc < c1; ++cc) s += cnt[cc];
+  for (int cc = c0; cc < c1; ++cc) s += cid[cc];
   int o = block_exclusive_scan(s, wsum, &total_sh);
   for (int cc = c0; cc < c1; ++cc) {
     T.start[cc] = o;
-    T.kq[cc] = kq[cc];
-    const int x = cnt[cc];
+    const int x = cid[cc];
     cnt[cc] = o;
     o += x;
   }
@@ -514,6 +555,10 @@ struct UpParams {
   const uint8_t* Q8;
   const float* qsc;
   const float* usc;
+  // the tiles' bounds min over u of (L_u^k - E_u) / ||u|| ([k_max][ntiles]) and the factor
+  // that turns one into the smallest ||q|| a column needs to reach the fast test
+  const float* tile_lb;
+  float prune_scale;
 };
 
 // 32 consecutive FP32 columns of this thread's TMEM lane, waited for; the wait names the
@@ -652,6 +697,9 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
   __shared__ int4 srows[NROWS];
   __shared__ float2 gq[NG];                         // per 32 columns: largest ||q||, row of the smallest bound
   __shared__ int32_t kseen[65], kslot[65], kfast[65], klist[64], nsl_sh;
+  __shared__ float ckey[SETN];                      // per column: ||q||, +inf without a bound (descending)
+  __shared__ uint16_t tnc[kMaxTileList];            // per tile of the set: the columns it needs (a prefix)
+  __shared__ int kmaxset_sh, nload_sh, njobs_sh;
   __shared__ int32_t tlist[kMaxTileList];           // this CTA's needed tiles, in order
   __shared__ int32_t ntl_sh;
   __shared__ uint32_t tma_issued[STAGES];            // TMA loads issued per stage (teardown drain)
@@ -704,25 +752,16 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
       cnt += __popc(m);
     }
     if (lane == 0) ntl_sh = cnt < kMaxTileList ? cnt : kMaxTileList;
-    // the users of the needed tiles times the columns: the scores this CTA computes
-    __syncwarp();
-    unsigned long long users = 0;
-    for (int i = lane; i < min(cnt, kMaxTileList); i += 32) {
-      const int64_t left = p.mz - (int64_t)tlist[i] * kUM;
-      users += (unsigned long long)(left < kUM ? left : kUM);
-    }
-    for (int o = 16; o > 0; o >>= 1) users += __shfl_xor_sync(0xffffffffu, users, o);
-    if (lane == 0 && users) atomicAdd(&p.stats[p.st_scores], users * (unsigned long long)(*p.T.ncol));
   }
   const int ncol = *p.T.ncol;
-  int it_base = 0;     // tiles of earlier sets (the stages' running index)
+  int it_base = 0;     // tiles of earlier sets (the bound ring's running index)
+  int ld_base = 0;     // tiles loaded for earlier sets (the stages' running index)
   int jbase = 0;       // jobs of earlier sets (the slots' running index)
   int mma_jobs = 0;    // the MMA thread: jobs issued so far
   unsigned long long yes_cnt = 0;   // "yes" taken in the epilogue (INL)
   bool failed = false;
   for (int c0 = 0; c0 < ncol; c0 += SETN) {
     const int nn = min(SETN, ncol - c0);
-    const int ns = (nn + W - 1) / W;                 // slices of the set
     // ---- the set's columns: distinct k of their rows, bound-table rows, B operand
     __syncthreads();   // the previous set is done with every shared table
     for (int k = tid; k <= 64; k += kUThreads) kseen[k] = 0;
@@ -756,6 +795,12 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
         }
       }
       nsl_sh = ns_;
+      int km = 0;
+      for (int k = p.kmax; k >= 1 && km == 0; --k)
+        if (kseen[k]) km = k;
+      kmaxset_sh = km;   // the set's largest k <= k_max (0: no row has a bound)
+      nload_sh = 0;
+      njobs_sh = 0;
     }
     __syncthreads();
     if (INL) {
@@ -780,9 +825,45 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
         row = sl >= 0 ? sl : p.slot_cap;
       }
       cq[c] = make_float2(qn, __int_as_float(128 * row));
+      ckey[c] = c < nn ? (p.T.kq[c0 + c] > 0 ? qn : INFINITY) : -INFINITY;
       if constexpr (F8) csq[c] = c < nn ? p.qsc[p.T.rep[c0 + c]] : 0.f;
     }
     __syncthreads();
+    // Per tile, the columns it needs.  A column reaches the fast test of user u only if
+    // (1 + 2c) ||u|| ||q|| >= L_u^k - E_u (the score is at most (1 + c) ||u|| ||q||), so
+    // with the columns in descending order of ||q|| a tile needs the prefix with
+    // ||q|| >= min over its users of (L_u^K - E_u) / ||u|| / (1 + 2c), K the set's largest
+    // k (L falls as k grows); columns without a bound come first.  A tile that needs none is
+    // not loaded at all.
+    {
+      unsigned long long scores = 0;
+      for (int li = tid; li < ntl_sh; li += kUThreads) {
+        const int t = tlist[li];
+        int nc = nn;
+        if (kmaxset_sh > 0) {
+          const float tau = p.tile_lb[(int64_t)(kmaxset_sh - 1) * p.ntiles + t];
+          if (tau > 0.f) {
+            const float th = tau * p.prune_scale;
+            int lo = 0, hi = nn;
+            while (lo < hi) {
+              const int mid = (lo + hi) >> 1;
+              if (ckey[mid] >= th) lo = mid + 1;
+              else hi = mid;
+            }
+            nc = lo;
+          }
+        }
+        tnc[li] = (uint16_t)nc;
+        if (nc > 0) {
+          atomicAdd(&nload_sh, 1);
+          atomicAdd(&njobs_sh, (nc + W - 1) / W);
+          const int64_t left = p.mz - (int64_t)t * kUM;
+          scores += (unsigned long long)(left < kUM ? left : kUM) * (unsigned long long)nc;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) scores += __shfl_xor_sync(0xffffffffu, scores, o);
+      if (lane == 0 && scores) atomicAdd(&p.stats[p.st_scores], scores);   // (user, column) scores computed
+    }
     if (tid < NG) {
       // the group's fast test: its largest ||q|| against its smallest bound, which belongs
       // to its largest k (bounds fall as k grows; slots follow k; the -inf row is last)
@@ -817,7 +898,6 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
     tc::tc_fence_after();
     const uint32_t tbase = tmem_base_sh;
     const int ntl = ntl_sh;
-    const int njobs = ntl * ns;
 
     if (warp == 0) {
       if (lane == 0) {
@@ -826,8 +906,10 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
           tc::prefetch_tensormap(&tmapUhi);
           if (PRODS == 3) tc::prefetch_tensormap(&tmapUlo);
         }
+        int ld = 0;
         for (int li = 0; li < ntl; ++li) {
-          const int it = it_base + li, s = it % STAGES;
+          if (tnc[li] == 0) continue;                   // a tile that needs no column
+          const int it = ld_base + ld++, s = it % STAGES;
           if (it >= STAGES && !tc::mbar_wait(&empty_bar[s], ((it / STAGES) & 1) ^ 1, p.timeout, nullptr)) break;
           const int t = tlist[li];
           tc::mbar_arrive_expect_tx(&full_bar[s], S::kStage);
@@ -841,17 +923,30 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
       }
     } else if (warp == 1) {
       if (lane == 0) {
-        // ---- MMA issuer: job j = (tile j / ns, slice j mod ns) into slot (jbase + j) & 1
+        // ---- MMA issuer: the jobs (tile, slice of its column prefix) in order, job jr into
+        // slot (jbase + jr) & 1
         const uint32_t a0 = tc::smem_addr(sA), b0 = tc::smem_addr(sB);
-        for (int j = 0; j < njobs; ++j) {
-          if (p.inject_stall && mma_jobs >= 1) break;   // test hook: a partner that stops working
-          const int li = j / ns, sc = j - li * ns;
-          const int it = it_base + li, s = it % STAGES;
-          if (sc == 0 && !tc::mbar_wait(&full_bar[s], (it / STAGES) & 1, p.timeout, nullptr)) break;
-          const int jg = jbase + j, slot = jg & 1, u = jg >> 1;
+        int ld = 0, jr = -1, li = -1, sc = 0, nst = 0, s = 0;
+        for (;;) {
+          if (++sc >= nst) {                            // the next tile with columns
+            sc = 0;
+            do {
+              ++li;
+            } while (li < ntl && tnc[li] == 0);
+            if (li >= ntl) break;
+            nst = (tnc[li] + W - 1) / W;
+            const int it = ld_base + ld++;
+            s = it % STAGES;
+            if (p.inject_stall && mma_jobs >= 1) break;   // test hook: a partner that stops working
+            if (!tc::mbar_wait(&full_bar[s], (it / STAGES) & 1, p.timeout, nullptr)) break;
+          }
+          ++jr;
+          if (p.inject_stall && mma_jobs >= 1) break;
+          const int jg = jbase + jr, slot = jg & 1, u = jg >> 1;
           if (u >= 1 && !tc::mbar_wait(&tempty_bar[slot], (u - 1) & 1, p.timeout, nullptr)) break;
           tc::tc_fence_after();
-          const int nh = min(W, nn - sc * W);
+          const int nh = min(W, (int)tnc[li] - sc * W);
+          const int ns = nst;                             // slices of this tile's prefix
           const uint32_t idesc = F8 ? tc::idesc_e4m3_f32(kUM, (uint32_t)((nh + 15) & ~15))
                                     : tc::idesc_bf16_f32(kUM, (uint32_t)((nh + 15) & ~15));
           const uint32_t d = tbase + slot * W;
@@ -959,9 +1054,21 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
       bool valid = false;
       // the bound L - E - 1e-30 (rounded down) of the ring row at `off` for user ul
       auto Lm = [&](int off, int u, float Eu_) { return __fsub_rd(__fsub_rd(ent[off + u], Eu_), 1e-30f); };
-      const int j0 = (g - jbase) & 1;
-      for (int j = j0; j < njobs; j += 2) {
-        const int li = j / ns, sc = j - li * ns;
+      // the jobs (tile, slice of its column prefix) in the MMA issuer's order; this group
+      // takes those of its slot
+      int jr = -1, li = -1, sc = 0, nst = 0;
+      for (;;) {
+        if (++sc >= nst) {                              // the next tile with columns
+          sc = 0;
+          do {
+            ++li;
+          } while (li < ntl && tnc[li] == 0);
+          if (li >= ntl) break;
+          nst = (tnc[li] + W - 1) / W;
+        }
+        ++jr;
+        if (((jbase + jr) & 1) != g) continue;
+        const int nct = tnc[li];                        // columns of the set this tile needs
         if (li != cur_li) {
           if (!advance_to(li)) {
             failed = true;
@@ -975,7 +1082,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
           E = ent[(p.slot_cap + 3) * 128 + ul];
           if constexpr (F8) su = ent[(p.slot_cap + 5) * 128 + ul];
         }
-        const int jg = jbase + j, slot = jg & 1;      // slot == g
+        const int jg = jbase + jr, slot = jg & 1;     // slot == g
         if (!tc::mbar_wait(&tfull_bar[slot], (jg >> 1) & 1, p.timeout, nullptr)) {
           failed = true;
           break;
@@ -991,12 +1098,12 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
         for (int q = 0; q < NG8; ++q) {
           const int cw = cs0 + 32 * q;
           thr[q] = INFINITY;
-          if (cw < nn && valid) {
+          if (cw < nct && valid) {
             const float2 gg = gq[cw >> 5];
             thr[q] = __fsub_rd(Lm(__float_as_int(gg.y), ul, E), __fmul_ru(cu, gg.x));
           }
         }
-        const int rem = nn - cs0;                      // columns of the slice inside the set
+        const int rem = nct - cs0;                     // columns of the slice the MMA computed
         const uint32_t acc_addr = tbase + lane_addr + slot * W;   // the slice's first column
         if constexpr (INL) {
           // dense candidates: the 32-column groups some user passes are examined here
@@ -1025,7 +1132,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
             const int x = __ffs(need) - 1;             // 32-column group of the slice
             need &= need - 1;
             const int cw = cs0 + 32 * x;               // set column of the group's first score
-            const int left = nn - cw;
+            const int left = nct - cw;
             float v[32];
             tmem_ld32_wait(acc_addr + 32 * x, v);
             if constexpr (F8) {
@@ -1135,7 +1242,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
             const int x = __ffs(need) - 1;             // 32-column group of the slice
             need &= need - 1;
             const int cw = cs0 + 32 * x;               // set column of the group's first score
-            const int left = nn - cw;
+            const int left = nct - cw;
             float v[32];
             tmem_ld32_wait(acc_addr + 32 * x, v);
 #pragma unroll
@@ -1168,7 +1275,8 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
       if (!failed && !advance_to(ntl)) failed = true;   // release the set's remaining tiles
     }
     it_base += ntl;
-    jbase += njobs;
+    ld_base += nload_sh;
+    jbase += njobs_sh;
     tc::tc_fence_before();
     // a timed-out wait anywhere ends the pass for the whole CTA
     failed = __syncthreads_or(failed || *(volatile int*)p.timeout);
@@ -1346,13 +1454,17 @@ sah_status prepare_user_pass_tc(Index* ix, const float* Qd, const float* qn, con
   const ColTable T = col_table_at(scratch, nq, ix->dp);
   int ht = 64;
   while (ht < 2 * nq) ht <<= 1;
-  const size_t tsmem = sizeof(int32_t) * (2 * (size_t)ht + 5 * (size_t)nq);
+  int npow = 1;
+  while (npow < nq) npow <<= 1;
+  const size_t tsmem = sizeof(int32_t) * (2 * (size_t)ht + 5 * (size_t)nq + 2 * (size_t)npow);
   SAH_TRY(raise_smem_limit((const void*)column_table_kernel, tsmem));
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
-  column_table_kernel<<<1, 1024, tsmem, st>>>(Qd, qh, nq, ix->dp, kk, modes, ix->kmax, ix->n, ix->pnorm, ht, T, 0);
+  column_table_kernel<<<1, 1024, tsmem, st>>>(Qd, qn, qh, nq, ix->dp, kk, modes, ix->kmax, ix->n, ix->pnorm, ht, npow,
+                                               T, 0);
   column_check_kernel<<<sms, 512, 0, st>>>(Qd, nq, ix->dp, T);
-  column_table_kernel<<<1, 1024, tsmem, st>>>(Qd, qh, nq, ix->dp, kk, modes, ix->kmax, ix->n, ix->pnorm, ht, T, 1);
+  column_table_kernel<<<1, 1024, tsmem, st>>>(Qd, qn, qh, nq, ix->dp, kk, modes, ix->kmax, ix->n, ix->pnorm, ht, npow,
+                                               T, 1);
   column_transpose_kernel<<<sms, 512, 0, st>>>(Qd, qn, nq, ix->dp, T);
   SAH_CUDA(cudaGetLastError());
   if (launches) *launches += 4;
@@ -1419,6 +1531,7 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
   // |s_tc - <u,q>| <= c_bf ||u|| ||q||
   p.cband = (float)(1.01 * (std::ldexp(1.0, -7) + std::ldexp(1.0, -16) + (2.0 * ix->dk + 16.0) * std::ldexp(1.0, -23)));
   const bool f8 = ix->prm.tc_user_pass == 2;
+  p.tile_lb = ix->tile_lb;
   if (f8) {
     // E4M3 operands: every value y = x 448 / max|x_i| is rounded to within 2^-4 |y| + 2^-10
     // (half the subnormal spacing); over K = 128 products, with the scales at most
@@ -1450,6 +1563,9 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
   p.st_scores = st_scores;
   p.timeout = ix->dev_timeout;
   p.inject_stall = ix->inject_site == SAH_INJECT_USER_PASS ? 1 : 0;
+  // the smallest ||q|| a column needs against a tile bound tau is tau / ((1 + 2c)(1 + 2^-16)):
+  // the 2^-16 covers the FP32 rounding of ||q||; the factor is rounded down again
+  p.prune_scale = (float)(1.0 / ((1.0 + 2.0 * (double)p.cband) * (1.0 + std::ldexp(1.0, -16))) * (1.0 - std::ldexp(1.0, -20)));
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
   // candidates are sparse against exact thresholds (|P'| = n): candidate blocks; dense
