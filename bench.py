@@ -449,7 +449,9 @@ STAGE_NAMES = ["prep", "block_pass", "user_pass", "kmips_decision", "compaction"
 def stage_rooflines(stage_ms, launches, st, d, dp, peaks, peak_kind):
     """The kernels that carry the stages, each against its bound, from the library's
     algorithmic counters (work per call) and its CUDA-event stage times:
-      user pass (A4/A8)  tensor: 2 d flops per (user, distinct query vector) score;
+      user pass (A4/A8)  tensor: 2 d flops per (user, distinct query vector) score computed, or
+                         HBM: 2 d_pad + 12 bytes per user row streamed, whichever its
+                         arithmetic intensity makes the bound;
       block pass (A3)    FP32 ALU: 2 d flops per (leaf, distinct query vector) <c_B, q>;
       kMIPS (A5)         tensor: 2 d flops per (survivor, item) scored before its decision.
     A call makes one launch of each per sub-batch (prep launches = sub-batches)."""
@@ -457,16 +459,25 @@ def stage_rooflines(stage_ms, launches, st, d, dp, peaks, peak_kind):
     nsub = max(1.0, float(launches[0]))
     out = {}
     if st.get("tc_scores", 0) > 0 and stage_ms[6] > 0:
+        # the user pass is tensor-bound when it scores many columns per user row it streams,
+        # HBM-bound when (with the per-tile column prefix) it scores few: the bound is the one
+        # its arithmetic intensity (flops per algorithmic byte) puts it under
         fl = 2.0 * d * st["tc_scores"]
+        by = (2.0 * dp + 12.0) * st.get("tc_rows", 0)   # BF16 rows + 12 B of bounds per user and set
         t = stage_ms[6] / 1e3
-        out["user_pass"] = {"kernel": "user_pass_tc_kernel", "bound": "tensor", "unit": "TFLOP/s",
-                            "achieved": fl / t / 1e12, "peak": peaks["bf16_tflops"],
-                            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json bf16_tflops, burst)",
-                            "algorithmic_flops_per_launch": fl / nsub, "launch_ms": stage_ms[6] / nsub,
-                            "scores_per_call": st["tc_scores"],
-                            # the same kernel seen from HBM: every user row (BF16, d_pad) once per
-                            # set of up to 512 distinct query vectors
-                            "hbm_bytes_min_per_call": 2.0 * dp * st["users_in_kept_blocks"]}
+        ridge = peaks["bf16_tflops"] * 1e12 / (peaks["hbm_gbs"] * 1e9)
+        tensor = {"bound": "tensor", "unit": "TFLOP/s", "achieved": fl / t / 1e12, "peak": peaks["bf16_tflops"],
+                  "peak_source": f"{peak_kind} (MEASURED_PEAKS.json bf16_tflops, burst)",
+                  "algorithmic_flops_per_launch": fl / nsub}
+        hbm = {"bound": "hbm", "unit": "GB/s", "achieved": by / t / 1e9, "peak": peaks["hbm_gbs"],
+               "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+               "algorithmic_bytes_per_launch": by / nsub}
+        ai = fl / by if by > 0 else float("inf")
+        main, other = (tensor, hbm) if ai >= ridge else (hbm, tensor)
+        other["frac"] = other["achieved"] / other["peak"]
+        out["user_pass"] = dict(main, kernel="user_pass_tc_kernel", launch_ms=stage_ms[6] / nsub,
+                                scores_per_call=st["tc_scores"], rows_per_call=st.get("tc_rows", 0),
+                                arithmetic_intensity=ai, ridge=ridge, other_bound=other)
     if st.get("block_col_pairs", 0) > 0 and stage_ms[1] > 0:
         fl = 2.0 * d * st["block_col_pairs"]
         t = stage_ms[1] / 1e3
@@ -912,8 +923,9 @@ def main():
             "stage_rooflines": roofs,
             "stages_ms": {nm: float(sms[i]) for i, nm in enumerate(STAGE_NAMES)},
             "stage_counts": {k: st[k] for k in ("block_pairs_total", "block_pairs_kept", "users_in_kept_blocks",
-                                                "block_col_pairs", "tc_scores", "users_yes_early", "pairs_rescored",
-                                                "survivors", "fp64_rescored", "items_scanned", "results")},
+                                                "block_col_pairs", "tc_scores", "tc_rows", "users_yes_early",
+                                                "pairs_rescored", "survivors", "fp64_rescored", "items_scanned",
+                                                "results")},
             "index_build_s": build_s,
             "index_build": {"inputs": "U and P already on the device", "gemm_ms": ist.get("build_gemm_ms", 0.0),
                             "overflow_rows": ist.get("build_overflow_rows", 0), "device_bytes": ist["device_bytes"]},

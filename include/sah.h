@@ -224,6 +224,8 @@ typedef struct {
   int64_t pairs_rescored;       /* pairs the tensor-core user pass left to the FP32 re-score */
   int64_t tc_scores;            /* (user, distinct query vector) scores the tensor-core user pass computed */
   int64_t block_col_pairs;      /* (leaf, distinct query vector) pairs of the tensor-core block filter */
+  int64_t tc_rows;              /* user rows the tensor-core user pass streamed (each column set streams
+                                   the tiles that need one of its columns) */
 } sah_stats;
 
 sah_status sah_index_stats(const sah_index* index, sah_stats* out);

@@ -61,7 +61,8 @@ class Stats(ctypes.Structure):
         "survivors", "fp64_rescored", "results", "users_in_kept_blocks", "items_scanned")] + [
         ("stage_ms", ctypes.c_double * 8), ("stage_launches", ctypes.c_int64 * 8),
         ("build_gemm_ms", ctypes.c_double), ("build_overflow_rows", ctypes.c_int64),
-        ("pairs_rescored", ctypes.c_int64), ("tc_scores", ctypes.c_int64), ("block_col_pairs", ctypes.c_int64)]
+        ("pairs_rescored", ctypes.c_int64), ("tc_scores", ctypes.c_int64), ("block_col_pairs", ctypes.c_int64),
+        ("tc_rows", ctypes.c_int64)]
 
     def as_dict(self):
         out = {}

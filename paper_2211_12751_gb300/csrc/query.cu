@@ -44,6 +44,7 @@ enum StatSlot {
   ST_EMIT_OVERFLOW,
   ST_TC_SCORES,      // (user, column) scores of the tensor-core user pass
   ST_BF_COLPAIRS,    // (leaf, distinct column) pairs of the tensor-core block filter
+  ST_TC_ROWS,        // user rows the tensor-core user pass streamed (once per column set)
   ST_COUNT
 };
 
@@ -1188,7 +1189,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
             SAH_TRY(run_user_pass_tc(ix, Qd, (uint16_t*)(w + L.qb), w + L.coltab, qn, kk, nqb, kmask,
                                      mask_words, (uint8_t*)(w + L.tneed), bitmap, words, surv + 2 * surv_cap,
                                      survcnt + 2, surv + 3 * surv_cap, survcnt + 3, surv, survcnt, surv_cap, stats,
-                                     ST_YES_EARLY, ST_FP64, ST_TC_SCORES, st,
+                                     ST_YES_EARLY, ST_FP64, ST_TC_SCORES, ST_TC_ROWS, st,
                                      &up_launches, tm.slot(6)));
           } else if (reg_variant) {
             const size_t smem = (size_t)16 * kQChunk * dp4 + sizeof(PairInfo) * kQChunk + sizeof(float) * 64 * threads;
@@ -1357,6 +1358,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
       agg.pairs_rescored += (int64_t)ns2[2];
       agg.tc_scores += (int64_t)st_h[ST_TC_SCORES];
       agg.block_col_pairs += (int64_t)st_h[ST_BF_COLPAIRS];
+      agg.tc_rows += (int64_t)st_h[ST_TC_ROWS];
       // the next call starts from the largest list of this call's sub-batches (twice it)
       surv_call_max = std::max(surv_call_max, nsmax);
       cx->surv_hint = std::max<int64_t>(1 << 16, 2 * surv_call_max);

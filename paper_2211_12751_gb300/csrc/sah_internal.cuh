@@ -318,7 +318,7 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
                             uint32_t* bitmap, int64_t words, Survivor* resc, unsigned long long* resc_count,
                             Survivor* cand, unsigned long long* cand_count,
                             Survivor* surv, unsigned long long* surv_count, int64_t surv_cap,
-                            unsigned long long* stats, int st_yes, int st_fp64, int st_scores, cudaStream_t st,
+                            unsigned long long* stats, int st_yes, int st_fp64, int st_scores, int st_rows, cudaStream_t st,
                             int* launches, const cudaEvent_t* ev = nullptr);   // ev: begin / end of the GEMM kernel
 // topk_tc.cu: the 64 largest FP32 scores of every user over all items, through tcgen05
 sah_status topk_full_tc(Index* ix, float* vlast, int32_t* ids64, cudaStream_t st, double* gemm_ms);
