@@ -677,8 +677,8 @@ __device__ inline int block_exclusive_scan(int v, int* total) {
 // Answers per summary word, then their scan, one CTA per query j: a thread per summary
 // word sw reads the bitmap words the summary marks (independent loads, all in flight at
 // once) and counts their bits; a row with k > n counts the summary word's users.  The
-// block scans the counts in chunks of blockDim words and writes each word's exclusive
-// prefix to wpre[j * nsw + sw], appends the words with answers to list (one atomic per
+// block scans the counts in chunks of blockDim words and writes the exclusive prefix of
+// every word with answers to wpre[j * nsw + sw], appends those words to list (one atomic per
 // warp), and writes the query's total to cnt[j].  The last CTA to finish (a ticket taken
 // after a fence) then turns the totals into the offsets: offsets[j] = base + the answers
 // of the queries before j, offsets[nq] the end (also into offsets2 when given).
@@ -713,7 +713,7 @@ __global__ void answer_count_scan_kernel(const uint32_t* __restrict__ bitmap, in
     int chunk_total;
     const int pre = block_exclusive_scan(c, &chunk_total);
     const int g = j * nsw + sw;
-    if (sw < nsw) wpre[g] = carry + pre;
+    if (sw < nsw && c > 0) wpre[g] = carry + pre;   // read only for the listed words (c > 0)
     carry += chunk_total;
     const unsigned mk = __ballot_sync(0xffffffffu, c > 0);
     if (mk) {

@@ -248,14 +248,17 @@ column_table_kernel(const float* __restrict__ Qd, const float* __restrict__ qn, 
   // first; equal norms by first row): the user pass scores, per tile of users, only the
   // prefix of columns whose norm can reach the tile's bound.  A bitonic sort of
   // (key, column) pairs, then every table renumbered.
-  for (int i = tid; i < npow; i += nt) {
+  int np = 1;                                     // the sort's width: a power of two >= ncol
+  while (np < ncol) np <<= 1;
+  (void)npow;                                     // (the shared memory is sized for the largest)
+  for (int i = tid; i < np; i += nt) {
     skey[i] = i < ncol ? (kq[i] > 0 ? qn[crep[i]] : INFINITY) : -INFINITY;
     sidx[i] = i < ncol ? i : INT_MAX;
   }
   __syncthreads();
-  for (int size = 2; size <= npow; size <<= 1) {
+  for (int size = 2; size <= np; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int i = tid; i < npow; i += nt) {
+      for (int i = tid; i < np; i += nt) {
         const int j = i ^ stride;
         if (j > i) {
           const float ki = skey[i], kj = skey[j];
@@ -620,15 +623,17 @@ __device__ __forceinline__ float tmem_ld1_wait(uint32_t taddr) {
 // Shared memory of the user pass.  A stage holds one 128-user tile (its hi K-blocks and,
 // with PRODS = 3, its lo K-blocks); B holds the column set (up to SETN query vectors, hi
 // and, with PRODS = 3, lo), resident while the set's tiles stream past.
-template <int KB, int STAGES, int SETN, int PRODS>
+template <int KB, int STAGES, int SETN, int PRODS, int NSLOT = 2>
 struct UpSmem {
   static constexpr int kParts = PRODS == 3 ? 2 : 1;            // hi, or hi and lo
   static constexpr uint32_t kTile = kUM * 128;                  // one K-block of 128 user rows
   static constexpr uint32_t kStage = kParts * KB * kTile;
   static constexpr uint32_t kBPart = SETN * 128;                // one K-block of the set's columns
   static constexpr size_t kOperands = (size_t)STAGES * kStage + (size_t)kParts * KB * kBPart;
-  static constexpr int kW = SETN < 256 ? SETN : 256;            // columns per slice: one MMA, one TMEM slot
-  static constexpr uint32_t kTmemCols = 2 * kW;                 // two slots, one per epilogue group
+  // columns per slice: one MMA into one of NSLOT TMEM slots (512 columns in all; the two
+  // epilogue groups take the slots alternately)
+  static constexpr int kW = SETN < 512 / NSLOT ? SETN : 512 / NSLOT;
+  static constexpr uint32_t kTmemCols = NSLOT * kW;
   // + the bound ring: nring entries of (slots + 5) rows of 128 words (the slots' lower
   // bounds, a -inf row, a +inf row, ||u||, E_u, the caller's user id)
   static constexpr size_t bytes(int slots, int nring) {
@@ -676,17 +681,18 @@ __device__ __forceinline__ float max32_at(const float (&v)[NV]) {
 // (where they are sparse: exact thresholds).
 // F8: E4M3 operands with per-row scales (kind::f8f6f4, one 128-byte K-block, KB = 1): the
 // accumulator times the column's and the user's scale is the score.
-template <int KB, int STAGES, int SETN, int PRODS, bool INL, bool F8>
+template <int KB, int STAGES, int SETN, int PRODS, bool INL, bool F8, int NSLOT>
 __global__ void __launch_bounds__(kUThreads, 1)
 user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_constant__ CUtensorMap tmapUlo,
                     UpParams p) {
-  using S = UpSmem<KB, STAGES, SETN, PRODS>;
+  using S = UpSmem<KB, STAGES, SETN, PRODS, NSLOT>;
+  static_assert(NSLOT % 2 == 0, "the two epilogue groups take the slots alternately");
   constexpr int NROWS = INL ? (KB == 1 ? 512 : 128) : 1;   // rows of a set kept in shared memory
   constexpr int W = S::kW;
   constexpr int NG = SETN / 32;                     // 32-column groups of a set
   extern __shared__ uint8_t smem_raw[];
   // per slot: the MMA's commit (tfull) and the four epilogue warps of its group (tempty)
-  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], tfull_bar[2], tempty_bar[2], done_bar;
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], tfull_bar[NSLOT], tempty_bar[NSLOT], done_bar;
   // bound ring: the loader fills an entry (ring_full), the eight epilogue warps release it
   __shared__ __align__(8) uint64_t ring_full[kRingMax], ring_empty[kRingMax];
   __shared__ uint32_t tmem_base_sh;
@@ -722,7 +728,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
       tc::mbar_init(&empty_bar[s], 1);
       tma_issued[s] = 0;
     }
-    for (int a = 0; a < 2; ++a) {
+    for (int a = 0; a < NSLOT; ++a) {
       tc::mbar_init(&tfull_bar[a], 1);
       tc::mbar_init(&tempty_bar[a], 4);
     }
@@ -933,7 +939,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
     } else if (warp == 1) {
       if (lane == 0) {
         // ---- MMA issuer: the jobs (tile, slice of its column prefix) in order, job jr into
-        // slot (jbase + jr) & 1
+        // slot (jbase + jr) % NSLOT
         const uint32_t a0 = tc::smem_addr(sA), b0 = tc::smem_addr(sB);
         int ld = 0, jr = -1, li = -1, sc = 0, nst = 0, s = 0;
         for (;;) {
@@ -951,7 +957,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
           }
           ++jr;
           if (p.inject_stall && mma_jobs >= 1) break;
-          const int jg = jbase + jr, slot = jg & 1, u = jg >> 1;
+          const int jg = jbase + jr, slot = jg % NSLOT, u = jg / NSLOT;
           if (u >= 1 && !tc::mbar_wait(&tempty_bar[slot], (u - 1) & 1, p.timeout, nullptr)) break;
           tc::tc_fence_after();
           const int nh = min(W, (int)tnc[li] - sc * W);
@@ -1091,8 +1097,8 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
           E = ent[(p.slot_cap + 3) * 128 + ul];
           if constexpr (F8) su = ent[(p.slot_cap + 5) * 128 + ul];
         }
-        const int jg = jbase + jr, slot = jg & 1;     // slot == g
-        if (!tc::mbar_wait(&tfull_bar[slot], (jg >> 1) & 1, p.timeout, nullptr)) {
+        const int jg = jbase + jr, slot = jg % NSLOT;  // slot % 2 == g
+        if (!tc::mbar_wait(&tfull_bar[slot], (jg / NSLOT) & 1, p.timeout, nullptr)) {
           failed = true;
           break;
         }
@@ -1314,10 +1320,10 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
 }
 
 
-template <int KB, int STAGES, int SETN, int PRODS, bool INL, bool F8 = false>
+template <int KB, int STAGES, int SETN, int PRODS, bool INL, bool F8 = false, int NSLOT = 2>
 sah_status launch_pass(Index* ix, UpParams p, int sms, cudaStream_t st, int* launches, const cudaEvent_t* ev) {
-  using S = UpSmem<KB, STAGES, SETN, PRODS>;
-  auto fn = user_pass_tc_kernel<KB, STAGES, SETN, PRODS, INL, F8>;
+  using S = UpSmem<KB, STAGES, SETN, PRODS, NSLOT>;
+  auto fn = user_pass_tc_kernel<KB, STAGES, SETN, PRODS, INL, F8, NSLOT>;
   constexpr int kFixedRows = 5 + (F8 ? 1 : 0);   // ring rows beside the bound slots
   // lower-bound rows per warp: what shared memory holds beside the operands
   int optin = 0;
@@ -1589,10 +1595,11 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
     else SAH_TRY((launch_pass<1, 4, 512, 1, true>(ix, p, sms, st, launches, ev)));
   } else {
     // d > 64: with exact thresholds the column prefixes are short and one set of 512 keeps the
-    // users' rows streamed once (two stages fit beside it); with the paper's |P'| the
-    // prefixes are long, and sets of 256 leave room for four stages (measured on the
-    // 1M-item / 2M-user workload: 0.98 against 1.59 ms, and 4.0 against 5.1 ms)
-    if (ix->l_exact) SAH_TRY((launch_pass<2, 2, 512, 1, false>(ix, p, sms, st, launches, ev)));
+    // users' rows streamed once (two stages fit beside it), with four TMEM slots of 128
+    // columns; with the paper's |P'| the prefixes are long, and sets of 256 leave room for
+    // four stages (measured on the 1M-item / 2M-user workload: 0.95 against 1.59 ms, and 4.0
+    // against 5.1 ms)
+    if (ix->l_exact) SAH_TRY((launch_pass<2, 2, 512, 1, false, false, 4>(ix, p, sms, st, launches, ev)));
     else SAH_TRY((launch_pass<2, 4, 256, 1, true>(ix, p, sms, st, launches, ev)));
   }
   {
