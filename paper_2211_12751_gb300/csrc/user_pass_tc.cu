@@ -706,7 +706,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
   __shared__ int32_t kseen[65], kslot[65], kfast[65], klist[64], nsl_sh;
   __shared__ float ckey[SETN];                      // per column: ||q||, +inf without a bound (descending)
   __shared__ uint16_t tnc[kMaxTileList];            // per tile of the set: the columns it needs (a prefix)
-  __shared__ int kmaxset_sh, nload_sh, njobs_sh;
+  __shared__ int kmaxset_sh, nload_sh, njobs_sh, maxtnc_sh;
   __shared__ int32_t tlist[kMaxTileList];           // this CTA's needed tiles, in order
   __shared__ int32_t ntl_sh;
   __shared__ uint32_t tma_issued[STAGES];            // TMA loads issued per stage (teardown drain)
@@ -808,6 +808,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
       kmaxset_sh = km;   // the set's largest k <= k_max (0: no row has a bound)
       nload_sh = 0;
       njobs_sh = 0;
+      maxtnc_sh = 0;
     }
     __syncthreads();
     if (INL) {
@@ -862,6 +863,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
         }
         tnc[li] = (uint16_t)nc;
         if (nc > 0) {
+          atomicMax(&maxtnc_sh, nc);
           atomicAdd(&nload_sh, 1);
           atomicAdd(&njobs_sh, (nc + W - 1) / W);
           const int64_t left = p.mz - (int64_t)t * kUM;
@@ -879,6 +881,10 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
         atomicAdd(&p.stats[p.st_rows], rows);       // user rows streamed for them
       }
     }
+    __syncthreads();
+    // no tile of this CTA needs a column of the set (its norms are all too small): nothing
+    // of it is staged, loaded or computed
+    if (njobs_sh == 0) continue;
     if (tid < NG) {
       // the group's fast test: its largest ||q|| against its smallest bound, which belongs
       // to its largest k (bounds fall as k grows; slots follow k; the -inf row is last)
@@ -890,7 +896,7 @@ user_pass_tc_kernel(const __grid_constant__ CUtensorMap tmapUhi, const __grid_co
       }
       gq[tid] = make_float2(qmax, __int_as_float(128 * (row < 0 ? p.slot_cap + 1 : row)));
     }
-    const int Nfill = (nn + 15) & ~15;
+    const int Nfill = (maxtnc_sh + 15) & ~15;          // the widest prefix a tile of the CTA needs
     for (int i = tid; i < Nfill * KB * 8; i += kUThreads) {
       const int rr = i / (KB * 8), rem = i % (KB * 8), kb = rem / 8, ch = rem % 8;
       uint4 hi = make_uint4(0u, 0u, 0u, 0u), lo = hi;
