@@ -65,6 +65,9 @@ def parse():
                     help="seconds of back-to-back steps after the timed ones (clock samples under load)")
     ap.add_argument("--serve-rates", default="1000,2000,5000,10000,20000,50000,100000,200000")
     ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--m", type=int, default=0, help="users (0: the workload's); a smaller case of the same recipe")
+    ap.add_argument("--n", type=int, default=0, help="items (0: the workload's)")
+    ap.add_argument("--nq", type=int, default=0, help="item queries (0: the workload's)")
     ap.add_argument("--sweep", action="store_true",
                     help="instead of the bench line, one JSON line of parameter sweeps on C2-shaped data")
     return ap.parse_args()
@@ -881,7 +884,8 @@ def main():
             torch.distributed.destroy_process_group()
         return
 
-    W = workload.make(args.workload)
+    over = {k: v for k, v in (("m", args.m), ("n", args.n), ("nq", args.nq)) if v > 0}
+    W = workload.make(args.workload, **over)
     Q, K, qrows = W.requests()
     nq = len(K)
     Ud, Pd = torch.from_numpy(W.U).to(dev), torch.from_numpy(W.P).to(dev)
