@@ -1367,7 +1367,7 @@ sah_status launch_pass(Index* ix, UpParams p, int sms, cudaStream_t st, int* lau
 
 // The per-row tests of Alg. 5 on the user pass's candidate blocks (one user, the tensor
 // scores of 32 columns), a warp per block and a lane per column; the sub-batch's column table
-// is staged in shared memory, the user's values come with the block.  With L = L_u^k, E its
+// is read in place, the user's values come with the block.  With L = L_u^k, E its
 // error and the band e = c ||u|| ||q|| (rounded up):
 //   s + e <  L - E                                            -> "no" (k items beat <u,q>)
 //   s - e >= ||u|| ||p_k|| (1 + 2 gamma)                       -> "yes" (Alg. 5)
@@ -1382,24 +1382,17 @@ cand_resolve_kernel(const CandBlock* __restrict__ cand, const unsigned long long
                     int l_exact, float cband, float gamma, uint32_t* __restrict__ bitmap, int64_t words,
                     Survivor* __restrict__ resc, unsigned long long* __restrict__ resc_count,
                     unsigned long long* __restrict__ stats, int st_yes, const int* __restrict__ timeout) {
-  extern __shared__ int4 cres_sm[];
   __shared__ int stop;
   if (threadIdx.x == 0) stop = *(volatile const int*)timeout;
   const int64_t total = block_count(cand_count, cap);   // synchronises the block
   if (stop || total == 0) return;   // after a timed-out wait the list may hold unwritten entries
   const int ncol = *T.ncol;
-  const int nrows = T.start[ncol];
-  int4* rows = cres_sm;                                      // [nrows]
-  int* start = reinterpret_cast<int*>(rows + nrows);         // [ncol + 1]
-  float* qnc = reinterpret_cast<float*>(start + ncol + 1);   // [ncol]
-  int* kqc = reinterpret_cast<int*>(qnc + ncol);             // [ncol] the column's largest k <= k_max
-  for (int i = threadIdx.x; i < nrows; i += blockDim.x) rows[i] = T.rows[i];
-  for (int i = threadIdx.x; i <= ncol; i += blockDim.x) start[i] = T.start[i];
-  for (int i = threadIdx.x; i < ncol; i += blockDim.x) {
-    qnc[i] = T.qnc[i];
-    kqc[i] = T.kq[i];
-  }
-  __syncthreads();
+  // the column table is read in place (it is small and stays in L2 and L1): staging all of
+  // it in every CTA's shared memory cost more than the blocks' own work
+  const int4* __restrict__ rows = T.rows;
+  const int* __restrict__ start = T.start;
+  const float* __restrict__ qnc = T.qnc;
+  const int* __restrict__ kqc = T.kq;                        // the column's largest k <= k_max
   const int lane = threadIdx.x & 31;
   unsigned long long yes_cnt = 0;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1609,10 +1602,7 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
     else SAH_TRY((launch_pass<2, 4, 256, 1, true>(ix, p, sms, st, launches, ev)));
   }
   {
-    // the column table in shared memory: rows, starts, norms and largest k of at most nq columns
-    const size_t csm = sizeof(int4) * (size_t)nq + sizeof(int) * (size_t)(nq + 1) + 2 * sizeof(float) * (size_t)nq;
-    SAH_TRY(raise_smem_limit((const void*)cand_resolve_kernel, csm));
-    cand_resolve_kernel<<<sms * 2, 512, csm, st>>>(reinterpret_cast<const CandBlock*>(cand), cand_count, surv_cap, T,
+    cand_resolve_kernel<<<sms * 2, 512, 0, st>>>(reinterpret_cast<const CandBlock*>(cand), cand_count, surv_cap, T,
                                                     ix->Lt, ix->Eu, ix->unorm, ix->uid, ix->m_nz, ix->kmax, p.l_exact,
                                                     p.cband, ix->gamma, bitmap, words, resc, resc_count, stats, st_yes,
                                                     ix->dev_timeout);
