@@ -1072,12 +1072,15 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
   // row stride of the answer bitmaps (the kernels that set answers take it as "words")
   const int64_t words = answer_stride(ix->m);
   const int64_t nsw = answer_words(words) / 32;   // summary words per query
-  // sub-batch size: bounded pair list and bitmap (about 1 GiB together)
+  // sub-batch size: with the tensor-core user pass up to the column table's 16,384 rows and
+  // about 8 GiB of answer bitmaps (every sub-batch streams all users' rows once); otherwise a
+  // bounded pair list and bitmap (about 1 GiB together) and 4,096 rows
   const bool tc_pass_q = ix->nb > 0 && ix->dk > 0 && ix->prm.tc_user_pass && ix->m_nz > 0;
   const size_t per_q = (tc_pass_q ? 0 : sizeof(PairEntry) * (size_t)std::max(ix->nb, 1)) + sizeof(uint32_t) * words +
                        sizeof(int32_t) * (nsw + 1) + sizeof(float) * ix->dp + 16;
-  int qb = (int)std::max<size_t>(1, std::min<size_t>((size_t)nq, (size_t(1) << 30) / per_q));
-  qb = std::min(qb, 4096);
+  const size_t ws_cap = tc_pass_q ? (size_t(8) << 30) : (size_t(1) << 30);
+  int qb = (int)std::max<size_t>(1, std::min<size_t>((size_t)nq, ws_cap / per_q));
+  qb = std::min(qb, tc_pass_q ? kTcMaxRows : 4096);
   const bool direct = out_dev != nullptr && qb >= nq;   // one sub-batch: emit into the caller's buffer
   *wrote_out = false;
   // survivor-list capacity used by this call: twice the last call's count (at least 64k),

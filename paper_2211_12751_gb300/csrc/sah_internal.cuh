@@ -296,7 +296,7 @@ sah_status run_saalsh(Index* ix, const Survivor* surv, const unsigned long long*
                       const float* Qd, const float* qn, const int32_t* kk, uint32_t* bitmap, int64_t words,
                       unsigned long long* stats, int stat_items, cudaStream_t st, int* launches);
 // user_pass_tc.cu: the user pass on tcgen05 over every user tile and the distinct query
-// vectors of the sub-batch (nq <= 4096 rows).
+// vectors of the sub-batch (nq <= kTcMaxRows rows).
 //  prepare_user_pass_tc: the column table (distinct vectors, their rows) into scratch
 //    (user_pass_tc_scratch_bytes); the split hi / lo BF16 queries (2 nq dk entries) and
 //    qh, a 64-bit hash of each padded query row's bits, are written by the query
@@ -313,6 +313,9 @@ sah_status prepare_user_pass_tc(Index* ix, const float* Qd, const float* qn, con
 sah_status block_filter_tc(Index* ix, void* scratch, int nq, uint32_t* kept_mask, int mask_words, uint8_t* tile_need,
                            unsigned long long* stats, int st_pairs, int st_users, int st_scored, int st_colpairs,
                            cudaStream_t st);
+// Rows of one sub-batch the tensor-core user pass's column table takes.
+constexpr int kTcMaxRows = 16384;
+
 sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* scratch, const float* qn,
                             const int32_t* kk, int nq, const uint32_t* kept_mask, int mask_words, uint8_t* tile_need,
                             uint32_t* bitmap, int64_t words, Survivor* resc, unsigned long long* resc_count,

@@ -64,7 +64,7 @@ constexpr int kLoaderWarp = 10;
 constexpr int kRingMax = 8;          // tiles of user bounds staged ahead by the loader warp (at most)
 constexpr int kEpiWarps = 8;
 constexpr int kMaxTileList = 1024;   // needed tiles per CTA and launch (the host splits longer ranges)
-constexpr int kMaxRows = 4096;       // rows of a sub-batch the column table takes
+constexpr int kMaxRows = kTcMaxRows;   // rows of a sub-batch the column table takes
 
 // The columns of a sub-batch and their rows.
 struct ColTable {
@@ -78,13 +78,26 @@ struct ColTable {
   uint8_t* q8;        // [nq][128]: every row in E4M3 (FP8 user pass), scaled by 448 / max|q_i|
   float* qsc;         // [nq]: max|q_i| / 448, the row's scale back
   int32_t* colof;     // [nq]: the column of each row (-1: none)
+  int32_t* scratch;   // the column table kernel's work arrays when they exceed shared memory
 };
+
+// the column table kernel's work arrays: hash table (2 ht), per-row and per-column arrays
+// (5 nq), sort keys and indices (2 npow); ht a power of two >= 2 nq (at least 64), npow one >= nq
+inline size_t col_scratch_ints(int nq, int* ht_out = nullptr, int* npow_out = nullptr) {
+  int ht = 64;
+  while (ht < 2 * nq) ht <<= 1;
+  int npow = 1;
+  while (npow < nq) npow <<= 1;
+  if (ht_out) *ht_out = ht;
+  if (npow_out) *npow_out = npow;
+  return 2 * (size_t)ht + 5 * (size_t)nq + 2 * (size_t)npow;
+}
 
 size_t col_table_bytes(int nq, int dp) {
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   return up(sizeof(int32_t)) + 3 * up(sizeof(int32_t) * (nq + 1)) + up(sizeof(int4) * (nq + 1)) +
          up(sizeof(float) * nq) + up(sizeof(float4) * (size_t)(dp / 4) * nq) + up((size_t)128 * nq) +
-         up(sizeof(float) * nq) + up(sizeof(int32_t) * nq);
+         up(sizeof(float) * nq) + up(sizeof(int32_t) * nq) + up(sizeof(int32_t) * col_scratch_ints(nq));
 }
 
 ColTable col_table_at(void* base, int nq, int dp) {
@@ -110,6 +123,8 @@ ColTable col_table_at(void* base, int nq, int dp) {
   T.qsc = (float*)p;
   p += up(sizeof(float) * nq);
   T.colof = (int32_t*)p;
+  p += up(sizeof(int32_t) * nq);
+  T.scratch = (int32_t*)p;
   return T;
 }
 
@@ -160,8 +175,12 @@ __device__ int block_exclusive_scan(int v, int* wsum, int* total) {
 __global__ void __launch_bounds__(1024, 1)
 column_table_kernel(const float* __restrict__ Qd, const float* __restrict__ qn, const uint64_t* __restrict__ qh,
                     int nq, int dp, const int32_t* __restrict__ kk, const int32_t* __restrict__ modes, int kmax,
-                    int64_t n, const float* __restrict__ pnorm, int ht, int npow, ColTable T, int mode) {
-  extern __shared__ int32_t sm[];
+                    int64_t n, const float* __restrict__ pnorm, int ht, int npow, ColTable T, int mode,
+                    int in_global) {
+  extern __shared__ int32_t sm_dyn[];
+  // the work arrays: in shared memory, or (a sub-batch too large for it) in the table's
+  // global scratch, which the CTA's barriers order just as well
+  int32_t* sm = in_global ? T.scratch : sm_dyn;
   __shared__ int wsum[32];
   __shared__ int total_sh;
   if (mode == 1 && *(volatile int32_t*)(T.ncol + 1) == 0) return;
@@ -1466,19 +1485,19 @@ sah_status prepare_user_pass_tc(Index* ix, const float* Qd, const float* qn, con
   }
   // the distinct query vectors of the sub-batch
   const ColTable T = col_table_at(scratch, nq, ix->dp);
-  int ht = 64;
-  while (ht < 2 * nq) ht <<= 1;
-  int npow = 1;
-  while (npow < nq) npow <<= 1;
-  const size_t tsmem = sizeof(int32_t) * (2 * (size_t)ht + 5 * (size_t)nq + 2 * (size_t)npow);
-  SAH_TRY(raise_smem_limit((const void*)column_table_kernel, tsmem));
+  int ht = 0, npow = 0;
+  const size_t need = sizeof(int32_t) * col_scratch_ints(nq, &ht, &npow);
+  // up to 4,096 rows the work arrays fit in shared memory (180 KB)
+  const int in_global = need > 200 * 1024 ? 1 : 0;
+  const size_t tsmem = in_global ? 0 : need;
+  if (!in_global) SAH_TRY(raise_smem_limit((const void*)column_table_kernel, tsmem));
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
   column_table_kernel<<<1, 1024, tsmem, st>>>(Qd, qn, qh, nq, ix->dp, kk, modes, ix->kmax, ix->n, ix->pnorm, ht, npow,
-                                               T, 0);
+                                               T, 0, in_global);
   column_check_kernel<<<sms, 512, 0, st>>>(Qd, nq, ix->dp, T);
   column_table_kernel<<<1, 1024, tsmem, st>>>(Qd, qn, qh, nq, ix->dp, kk, modes, ix->kmax, ix->n, ix->pnorm, ht, npow,
-                                               T, 1);
+                                               T, 1, in_global);
   column_transpose_kernel<<<sms, 512, 0, st>>>(Qd, qn, nq, ix->dp, T);
   SAH_CUDA(cudaGetLastError());
   if (launches) *launches += 4;

@@ -265,3 +265,30 @@ def test_repeated_calls_same_answers(sah, variant):
         assert all(np.array_equal(res[o[j]:o[j + 1]], want[j]) for j in range(len(K))), it
         small = ix.rkmips_batch(Q[:7], K[:7])                 # another shape in between
         assert all(np.array_equal(g, w) for g, w in zip(small, want[:7])), it
+
+
+@pytest.mark.parametrize("variant", ["bf16-tc", "fp8-tc"])
+@pytest.mark.parametrize("p_prime", [0, 1 << 30])
+def test_sub_batch_past_shared_memory_column_table(sah, variant, p_prime):
+    """9,000 rows in one call (one tensor-core sub-batch, whose column table no longer fits in
+    shared memory: about 6,000 distinct vectors) give the answers of the same rows asked in
+    calls of 700 rows, and a sample of rows agrees with the oracle."""
+    W = workload.make("c2", m=6000, n=2500)
+    ix = sah.Index(W.U, W.P, k_max=50, leaf_size=128, p_prime=p_prime, seed=3, **VARIANTS[variant])
+    rng = np.random.default_rng(21)
+    nrow = 9000
+    # rows: items of P, foreign vectors and repeats of both, each with its own k
+    foreign = (rng.standard_normal((3500, W.d)) * W.P.std()).astype(np.float32)
+    pool = np.vstack([W.P, foreign])
+    pick = rng.integers(0, len(pool), nrow)
+    Q = pool[pick]
+    K = rng.choice(np.array([1, 2, 5, 10, 25, 50, 51, 300], np.int32), nrow)
+    whole = ix.rkmips_batch(Q, K)
+    parts = []
+    for a in range(0, nrow, 700):
+        parts += ix.rkmips_batch(Q[a:a + 700], K[a:a + 700])
+    for j in range(nrow):
+        assert np.array_equal(whole[j], parts[j]), j
+    for j in rng.choice(nrow, 24, replace=False):
+        c = oracle.count_above(W.U, W.P, Q[j])
+        assert np.array_equal(whole[j], np.flatnonzero(c < K[j]).astype(np.int32)), (j, int(K[j]))
