@@ -260,6 +260,16 @@ sah_status sah_index_set_timing(sah_index* index, int32_t enable);
  * Errors: SAH_ERR_ARG (NULL index, site outside 0..2). */
 sah_status sah_index_inject_stall(sah_index* index, int32_t site);
 
+/* Test hook (the paper has no counterpart): with enable != 0, the next query call on this
+ * index gives every row the same 64-bit hash of its vector, so that with the tensor-core
+ * user pass every two different vectors of a sub-batch collide in the column table: the
+ * bitwise check finds them and the table is built again comparing whole vectors.  The
+ * answers are those of a call without the hook.  The hook applies to one call, which runs
+ * its launch sequence directly (never a replayed CUDA graph), then clears itself; enable 0
+ * clears it.  Not for use with a running server.
+ * Errors: SAH_ERR_ARG (NULL index). */
+sah_status sah_index_inject_hash_collision(sah_index* index, int32_t enable);
+
 /* Exact RkMIPS for one query without allocating any memory (the paper has no
  * counterpart; it exists for callers that may not allocate).
  *

@@ -110,6 +110,8 @@ def load(path: Optional[str] = None):
     lib.sah_index_set_timing.restype = I32
     lib.sah_index_inject_stall.argtypes = [P, I32]
     lib.sah_index_inject_stall.restype = I32
+    lib.sah_index_inject_hash_collision.argtypes = [P, I32]
+    lib.sah_index_inject_hash_collision.restype = I32
     lib.sah_rkmips_bruteforce_noalloc.argtypes = [P, I64, P, I64, I32, P, I32, P, I64, P, P]
     lib.sah_rkmips_bruteforce_noalloc.restype = I32
     lib.sah_kmips.argtypes = [P, P, I32, I32, I32, P, P, P]
@@ -344,6 +346,11 @@ class Index:
         """sah_index_inject_stall: the next query call's MMA thread at `site` (1: user pass,
         2: kMIPS decision) stops after one tile, so the call returns SAH_ERR_DEVICE_TIMEOUT."""
         _check(load().sah_index_inject_stall(self._h, int(site)))
+
+    def inject_hash_collision(self, enable: bool = True):
+        """sah_index_inject_hash_collision: the next query call gives every row one hash, so
+        the column table is built again comparing whole vectors; the answers do not change."""
+        _check(load().sah_index_inject_hash_collision(self._h, 1 if enable else 0))
 
     def set_timing(self, enable: bool = True):
         _check(load().sah_index_set_timing(self._h, 1 if enable else 0))

@@ -358,7 +358,8 @@ sah_status sah_rkmips_batch(sah_index* index, const float* Q, int32_t nq, const 
   }
   const sah_status s = batch_impl(index, Q, nq, ks, modes, buffers_on_device, out_ids, cap, out_offsets,
                                   (cudaStream_t)cuda_stream);
-  index->impl.inject_site = 0;   // the test hook applies to one call
+  index->impl.inject_site = 0;   // the test hooks apply to one call
+  index->impl.inject_collide = 0;
   return s;
 }
 
@@ -370,7 +371,8 @@ sah_status sah_rkmips(sah_index* index, const float* q, int32_t k, int32_t mode,
   }
   int64_t offs[2] = {0, 0};
   sah_status s = batch_impl(index, q, 1, &k, &mode, 0, out_ids, cap, offs, (cudaStream_t)cuda_stream);
-  index->impl.inject_site = 0;   // the test hook applies to one call
+  index->impl.inject_site = 0;   // the test hooks apply to one call
+  index->impl.inject_collide = 0;
   *out_count = offs[1];
   return s;
 }
@@ -470,6 +472,15 @@ sah_status sah_index_inject_stall(sah_index* index, int32_t site) {
     return SAH_ERR_ARG;
   }
   index->impl.inject_site = site;
+  return SAH_OK;
+}
+
+sah_status sah_index_inject_hash_collision(sah_index* index, int32_t enable) {
+  if (!index) {
+    sah::set_error("sah_index_inject_hash_collision: index is NULL");
+    return SAH_ERR_ARG;
+  }
+  index->impl.inject_collide = enable != 0 ? 1 : 0;
   return SAH_OK;
 }
 

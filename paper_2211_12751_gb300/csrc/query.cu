@@ -60,7 +60,7 @@ __global__ void prep_queries_kernel(const float* __restrict__ Q, int nq, int d, 
                                     float* __restrict__ Qd, float* __restrict__ qn,
                                     const int32_t* __restrict__ ks, int32_t* __restrict__ kk,
                                     const int32_t* __restrict__ modes, unsigned long long* __restrict__ stats,
-                                    uint16_t* __restrict__ Qhi, int dk, uint64_t* __restrict__ qh) {
+                                    uint16_t* __restrict__ Qhi, int dk, uint64_t* __restrict__ qh, int collide) {
   int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   int lane = threadIdx.x & 31;
   if (j >= nq) return;
@@ -83,7 +83,7 @@ __global__ void prep_queries_kernel(const float* __restrict__ Q, int nq, int d, 
   if (qh) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
-    if (lane == 0) qh[j] = h;
+    if (lane == 0) qh[j] = collide ? 0ull : h;   // (a test hook makes every row collide)
   }
   if (Qhi) {
     uint16_t* Qlo = Qhi + (int64_t)nq * dk;
@@ -1160,7 +1160,8 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
         prep_queries_kernel<<<grid_for(nqb, 8), 256, 0, st>>>(Q_dev + (int64_t)q0 * ix->d, nqb, ix->d, ix->dp, Qd, qn,
                                                                ks_dev + q0, kk, modes_q, stats,
                                                                tc_pass ? (uint16_t*)(w + L.qb) : nullptr, ix->dk,
-                                                               tc_pass ? (uint64_t*)(w + L.qh) : nullptr);
+                                                               tc_pass ? (uint64_t*)(w + L.qh) : nullptr,
+                                                               ix->inject_collide);
         SAH_CUDA(cudaGetLastError());
         tm.end(0, 1);
         if (ix->nb > 0) {
@@ -1283,7 +1284,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
           SAH_CUDA(cudaMemcpyAsync(timeout_h, ix->dev_timeout, sizeof(int), cudaMemcpyDeviceToHost, st));
         return SAH_OK;
       };
-      if (tm.on || !ix->use_graphs || !cx->graphs_allowed || ix->inject_site) {
+      if (tm.on || !ix->use_graphs || !cx->graphs_allowed || ix->inject_site || ix->inject_collide) {
         SAH_TRY(enqueue());
       } else {
         // the same shapes and buffers as an earlier call: replay its captured graph

@@ -147,6 +147,7 @@ struct Index {
   CUtensorMap tmap_U8{};
   int* dev_timeout = nullptr; // set by a kernel whose bounded wait ran out
   int inject_site = 0;        // test hook for the next query call (SAH_INJECT_*), 0: none
+  int inject_collide = 0;     // test hook for the next query call: every row hashes alike
 
   // SA-ALSH over the items behind P' (Alg. 1): norm partitions S_j (descending M_j), their
   // centroids and radii, SRP codes of the SAT-transformed items (Eq. 6, Eq. 9) sorted

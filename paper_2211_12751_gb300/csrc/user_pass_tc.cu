@@ -4,9 +4,11 @@
 //
 // Columns.  The rows of a sub-batch are (q, k) requests; rows asking for the same vector q
 // (with k <= k_max) share one GEMM column, so a batch that asks each item at several k
-// costs one column per item.  column_table_kernel finds the distinct vectors (hash table in
-// shared memory on a hash of each row's bits, then a bitwise check of the rows) and lists
-// each column's rows.
+// costs one column per item.  Five grid-wide kernels find the distinct vectors (a hash
+// table on a 64-bit hash of each row's bits), put the columns in descending order of ||q||
+// and list each column's rows, checking every row bitwise against its column's first row;
+// should two different vectors share a hash, one CTA builds the table again comparing
+// whole vectors.
 //
 // Operands.  BF16 alone carries 8 significant bits, which makes the score's error band
 // (about 2^-7 ||u|| ||q||) so wide that many pairs would stay open.  Every FP32 vector x
@@ -81,16 +83,53 @@ struct ColTable {
   int32_t* scratch;   // the column table kernel's work arrays when they exceed shared memory
 };
 
-// the column table kernel's work arrays: hash table (2 ht), per-row and per-column arrays
-// (5 nq), sort keys and indices (2 npow); ht a power of two >= 2 nq (at least 64), npow one >= nq
-inline size_t col_scratch_ints(int nq, int* ht_out = nullptr, int* npow_out = nullptr) {
-  int ht = 64;
-  while (ht < 2 * nq) ht <<= 1;
-  int npow = 1;
-  while (npow < nq) npow <<= 1;
-  if (ht_out) *ht_out = ht;
-  if (npow_out) *npow_out = npow;
-  return 2 * (size_t)ht + 5 * (size_t)nq + 2 * (size_t)npow;
+// The hash table's slots (a power of two >= 2 nq, at least 64) and the sort's width (a
+// power of two >= nq).
+inline void col_table_dims(int nq, int* ht, int* npow) {
+  *ht = 64;
+  while (*ht < 2 * nq) *ht <<= 1;
+  *npow = 1;
+  while (*npow < nq) *npow <<= 1;
+}
+
+// The grid-wide table build's work arrays (int32), in the table's scratch: the hash table,
+// then the parts that start zero, then the rest.
+struct ColWork {
+  int32_t* owner;    // [ht] a row of the slot's vector, -1 empty
+  int32_t* minrow;   // [ht] the first row of the slot's vector
+  int32_t* kqr;      // [nq] per first row: the column's largest k <= k_max (0: none)
+  int32_t* cntr;     // [nq] per first row: the column's rows
+  int32_t* rank;     // [nq] per listed column: columns ahead of it in the order
+  int32_t* before;   // [nq] per listed column: rows of the columns ahead of it
+  int32_t* ctr;      // [8] columns listed, rows with a column
+  int32_t* slot;     // [nq] per row: its slot (-1: no column)
+  int32_t* reps;     // [nq] the columns' first rows, in no particular order
+  int32_t* posr;     // [nq] per first row: the column's place in the order
+  int32_t* cursor;   // [nq] per place: the next free entry of its rows
+};
+
+__host__ __device__ inline ColWork col_work_at(int32_t* s, int nq, int ht) {
+  ColWork W;
+  W.owner = s;
+  W.minrow = W.owner + ht;
+  W.kqr = W.minrow + ht;
+  W.cntr = W.kqr + nq;
+  W.rank = W.cntr + nq;
+  W.before = W.rank + nq;
+  W.ctr = W.before + nq;
+  W.slot = W.ctr + 8;
+  W.reps = W.slot + nq;
+  W.posr = W.reps + nq;
+  W.cursor = W.posr + nq;
+  return W;
+}
+
+// int32 entries of the table's scratch: the grid-wide build's arrays (2 ht + 9 nq + 8),
+// which also hold the single-CTA rebuild's (2 ht + 5 nq + 2 npow, npow < 2 nq)
+inline size_t col_scratch_ints(int nq) {
+  int ht = 0, npow = 0;
+  col_table_dims(nq, &ht, &npow);
+  return 2 * (size_t)ht + 9 * (size_t)nq + 8;
 }
 
 size_t col_table_bytes(int nq, int dp) {
@@ -167,23 +206,25 @@ __device__ int block_exclusive_scan(int v, int* wsum, int* total) {
   return r;
 }
 
-// One CTA of 1024 threads.  Rows with k > n ask for every user and get no column.
-// mode 0: the rows grouped by (hash of the padded row's bits, k <= k_max); the grid-wide
-// column_check_kernel then compares every row with its column's first row bitwise.  mode 1:
-// nothing unless that check raised the flag (two different vectors with one hash); then the
-// table is built again with every probe comparing the rows bitwise.
+// The table built again by one CTA of 1024 threads, every probe of the hash table comparing
+// the rows bitwise: nothing unless the grid-wide build's check raised the table's flag (two
+// different vectors with one hash).  The same table as the grid-wide build's: rows with
+// k > n get no column; a column per (vector, k <= k_max); columns in descending order of
+// the key (+inf for columns whose rows all have k > k_max, ||q|| otherwise), equal keys by
+// first row.
 __global__ void __launch_bounds__(1024, 1)
-column_table_kernel(const float* __restrict__ Qd, const float* __restrict__ qn, const uint64_t* __restrict__ qh,
-                    int nq, int dp, const int32_t* __restrict__ kk, const int32_t* __restrict__ modes, int kmax,
-                    int64_t n, const float* __restrict__ pnorm, int ht, int npow, ColTable T, int mode,
-                    int in_global) {
+column_table_rebuild_kernel(const float* __restrict__ Qd, const float* __restrict__ qn,
+                            const uint64_t* __restrict__ qh, int nq, int dp, const int32_t* __restrict__ kk,
+                            const int32_t* __restrict__ modes, int kmax, int64_t n, const float* __restrict__ pnorm,
+                            int ht, int npow, ColTable T, int in_global) {
   extern __shared__ int32_t sm_dyn[];
   // the work arrays: in shared memory, or (a sub-batch too large for it) in the table's
-  // global scratch, which the CTA's barriers order just as well
+  // global scratch, which the CTA's barriers order just as well; the sort's keys and
+  // indices stay in shared memory either way
   int32_t* sm = in_global ? T.scratch : sm_dyn;
   __shared__ int wsum[32];
   __shared__ int total_sh;
-  if (mode == 1 && *(volatile int32_t*)(T.ncol + 1) == 0) return;
+  if (*(volatile int32_t*)(T.ncol + 1) == 0) return;
   int32_t* owner = sm;             // [ht] a row of the slot's vector, -1 empty
   int32_t* minrow = owner + ht;    // [ht] the first row of the slot's vector
   int32_t* colof = minrow + ht;    // [nq] slot, then column, of each row (-1: none)
@@ -191,7 +232,8 @@ column_table_kernel(const float* __restrict__ Qd, const float* __restrict__ qn, 
   int32_t* cnt = cid + nq;         // [nq] rows per column, then the scatter cursor
   int32_t* kq = cnt + nq;          // [nq] largest k <= k_max per column
   int32_t* crep = kq + nq;         // [nq] the first row of each column
-  float* skey = reinterpret_cast<float*>(crep + nq);   // [npow] sort keys (npow: a power of two >= nq)
+  // [npow] sort keys and column indices (npow: a power of two >= nq)
+  float* skey = in_global ? reinterpret_cast<float*>(sm_dyn) : reinterpret_cast<float*>(crep + nq);
   int32_t* sidx = reinterpret_cast<int32_t*>(skey + npow);
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int i = tid; i < ht; i += nt) {
@@ -206,7 +248,6 @@ column_table_kernel(const float* __restrict__ Qd, const float* __restrict__ qn, 
   // a thread per row: linear probing on (hash of the padded row's bits, k <= k_max); a
   // slot's owner is a row of its vector (mode 1: of its bits)
   const int dp4 = dp / 4;
-  const int pass = mode;
   {
     for (int j = tid; j < nq; j += nt) {
       const int k = kk[j];
@@ -223,7 +264,7 @@ column_table_kernel(const float* __restrict__ Qd, const float* __restrict__ qn, 
           cur = prev;
         }
         bool same = qh[cur] == key && (kk[cur] <= kmax ? 0 : 1) == cls;
-        if (same && pass == 1) {
+        if (same) {
           const uint4* a4 = reinterpret_cast<const uint4*>(Qd + (int64_t)j * dp);
           const uint4* c4 = reinterpret_cast<const uint4*>(Qd + (int64_t)cur * dp);
           for (int i = 0; same && i < dp4; ++i) {
@@ -277,18 +318,18 @@ column_table_kernel(const float* __restrict__ Qd, const float* __restrict__ qn, 
   __syncthreads();
   for (int size = 2; size <= np; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int i = tid; i < np; i += nt) {
-        const int j = i ^ stride;
-        if (j > i) {
-          const float ki = skey[i], kj = skey[j];
-          const int ii = sidx[i], ij = sidx[j];
-          const bool i_first = ki > kj || (ki == kj && ii < ij);
-          if (((i & size) == 0) != i_first) {
-            skey[i] = kj;
-            skey[j] = ki;
-            sidx[i] = ij;
-            sidx[j] = ii;
-          }
+      // a thread per compared pair (i, i + stride): i has a zero bit at the stride's position
+      for (int pr = tid; pr < np / 2; pr += nt) {
+        const int i = ((pr & ~(stride - 1)) << 1) | (pr & (stride - 1));
+        const int j = i + stride;
+        const float ki = skey[i], kj = skey[j];
+        const int ii = sidx[i], ij = sidx[j];
+        const bool i_first = ki > kj || (ki == kj && ii < ij);
+        if (((i & size) == 0) != i_first) {
+          skey[i] = kj;
+          skey[j] = ki;
+          sidx[i] = ij;
+          sidx[j] = ii;
         }
       }
       __syncthreads();
@@ -336,16 +377,166 @@ column_table_kernel(const float* __restrict__ Qd, const float* __restrict__ qn, 
   (void)crep;
 }
 
-// Every row against its column's first row, a 16-byte word per thread: any difference (two
+// ---- The grid-wide table build.  col_init_kernel clears the work arrays.
+__global__ void col_init_kernel(ColWork W, int nq, int ht) {
+  const int64_t nz = 4 * (int64_t)nq + 8;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < ht + nz; x += (int64_t)gridDim.x * blockDim.x) {
+    if (x < ht) {
+      W.owner[x] = -1;
+      W.minrow[x] = INT_MAX;
+    } else {
+      W.kqr[x - ht] = 0;   // kqr, cntr, rank, before, ctr: contiguous
+    }
+  }
+}
+
+// A thread per row: linear probing on (hash of the padded row's bits, k <= k_max) claims or
+// finds the row's slot; the slot keeps its first row.  Rows with k outside 1..n get none.
+__global__ void col_hash_kernel(const uint64_t* __restrict__ qh, const int32_t* __restrict__ kk, int nq, int kmax,
+                                int64_t n, int ht, ColWork W) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nq) return;
+  const int k = kk[j];
+  int slot = -1;
+  if (k >= 1 && k <= n) {
+    const int cls = k <= kmax ? 0 : 1;
+    const uint64_t key = qh[j];
+    slot = (int)(splitmix64(key + (uint64_t)cls) & (uint64_t)(ht - 1));
+    for (int probe = 0; probe < ht; ++probe) {
+      const int cur = atomicCAS(&W.owner[slot], -1, j);
+      if (cur == -1 || (qh[cur] == key && (kk[cur] <= kmax ? 0 : 1) == cls)) break;
+      slot = (slot + 1) & (ht - 1);
+    }
+    atomicMin(&W.minrow[slot], j);
+  }
+  W.slot[j] = slot;
+}
+
+// A thread per row: its column's row count and largest k <= k_max accumulate at the
+// column's first row, which lists itself.  The appends and the row total are counted per
+// warp (every lane reaches the ballots).
+__global__ void col_reps_kernel(const int32_t* __restrict__ kk, int nq, int kmax, ColWork W) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int s = j < nq ? W.slot[j] : -1;
+  const int r = s >= 0 ? W.minrow[s] : -1;
+  if (s >= 0) {
+    atomicAdd(&W.cntr[r], 1);
+    const int k = kk[j];
+    if (k <= kmax) atomicMax(&W.kqr[r], k);
+  }
+  const unsigned has = __ballot_sync(0xffffffffu, s >= 0);
+  const unsigned first = __ballot_sync(0xffffffffu, s >= 0 && r == j);
+  int base = 0;
+  if (lane == 0) {
+    if (has) atomicAdd(&W.ctr[1], __popc(has));
+    if (first) base = atomicAdd(&W.ctr[0], __popc(first));
+  }
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if ((first >> lane) & 1u) W.reps[base + __popc(first & ((1u << lane) - 1u))] = j;
+}
+
+// A column's order key: ascending in it is descending in ||q|| (+inf for columns without a
+// k <= k_max), then ascending in first row.  The norms are non-negative floats, whose bits
+// order as their values.
+__device__ __forceinline__ uint64_t col_order_key(const float* __restrict__ qn, const int32_t* __restrict__ kk,
+                                                  int kmax, int r) {
+  const float key = kk[r] <= kmax ? qn[r] : INFINITY;
+  return ((uint64_t)(~__float_as_uint(key)) << 32) | (uint32_t)r;
+}
+
+// The order by counting: a column's place is the number of columns whose key is smaller,
+// and its first entry in the row list the rows of those columns.  A CTA takes 1,024 listed
+// columns (4 per thread) against a chunk of 512 staged in shared memory and adds its
+// partial counts; the grid covers every (slice, chunk) pair of the sub-batch's rows, and
+// the parts past the listed columns return at once.
+constexpr int kRankOwn = 4;
+constexpr int kRankThreads = 256;
+constexpr int kRankChunk = 512;
+__global__ void __launch_bounds__(kRankThreads)
+col_rank_kernel(const float* __restrict__ qn, const int32_t* __restrict__ kk, int kmax, ColWork W) {
+  __shared__ uint64_t ck[kRankChunk];
+  __shared__ int cc[kRankChunk];
+  const int ncol = *(volatile int32_t*)W.ctr;
+  const int own0 = blockIdx.x * (kRankOwn * kRankThreads), oth0 = blockIdx.y * kRankChunk;
+  if (own0 >= ncol || oth0 >= ncol) return;
+  const int nch = min(kRankChunk, ncol - oth0);
+  for (int i = threadIdx.x; i < nch; i += kRankThreads) {
+    const int r = W.reps[oth0 + i];
+    ck[i] = col_order_key(qn, kk, kmax, r);
+    cc[i] = W.cntr[r];
+  }
+  uint64_t mine[kRankOwn];
+#pragma unroll
+  for (int t = 0; t < kRankOwn; ++t) {
+    const int x = own0 + t * kRankThreads + threadIdx.x;
+    mine[t] = x < ncol ? col_order_key(qn, kk, kmax, W.reps[x]) : 0ull;
+  }
+  __syncthreads();
+  int rk[kRankOwn] = {}, bf[kRankOwn] = {};
+  for (int i = 0; i < nch; ++i) {
+    const uint64_t o = ck[i];
+    const int w = cc[i];
+#pragma unroll
+    for (int t = 0; t < kRankOwn; ++t) {
+      const bool ahead = o < mine[t];
+      rk[t] += ahead ? 1 : 0;
+      bf[t] += ahead ? w : 0;
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < kRankOwn; ++t) {
+    const int x = own0 + t * kRankThreads + threadIdx.x;
+    if (x < ncol) {
+      if (rk[t]) atomicAdd(&W.rank[x], rk[t]);
+      if (bf[t]) atomicAdd(&W.before[x], bf[t]);
+    }
+  }
+}
+
+// A thread per listed column: the column moves to its place (first row, largest k, start
+// of its rows); the table's counts and its flag are set.
+__global__ void col_place_kernel(ColWork W, ColTable T) {
+  const int ncol = *(volatile int32_t*)W.ctr;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x == 0) {
+    T.ncol[0] = ncol;
+    T.ncol[1] = 0;
+    T.start[ncol] = W.ctr[1];
+  }
+  if (x >= ncol) return;
+  const int pos = W.rank[x], r = W.reps[x];
+  T.rep[pos] = r;
+  T.kq[pos] = W.kqr[r];
+  T.start[pos] = W.before[x];
+  W.cursor[pos] = W.before[x];
+  W.posr[r] = pos;
+}
+
+// A thread per (row, 16-byte word): the row's column and its entry in the column's rows
+// (word 0), and the row against its column's first row bitwise: any difference (two
 // vectors that share a hash) raises the table's flag.
-__global__ void column_check_kernel(const float* __restrict__ Qd, int nq, int dp, ColTable T) {
+__global__ void col_scatter_kernel(const float* __restrict__ Qd, const int32_t* __restrict__ kk,
+                                   const int32_t* __restrict__ modes, int kmax, int64_t n,
+                                   const float* __restrict__ pnorm, int nq, int dp, ColWork W, ColTable T) {
   const int dp4 = dp / 4;
   const int64_t total = (int64_t)nq * dp4;
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
     const int j = (int)(x / dp4), i = (int)(x - (int64_t)j * dp4);
-    const int c = T.colof[j];
-    if (c < 0) continue;
-    const int r = T.rep[c];
+    const int s = W.slot[j];
+    if (s < 0) {
+      if (i == 0) T.colof[j] = -1;
+      continue;
+    }
+    const int r = W.minrow[s];
+    if (i == 0) {
+      const int c = W.posr[r];
+      T.colof[j] = c;
+      const int k = kk[j];
+      const int sa = (modes != nullptr && modes[j] == SAH_SAALSH && k <= kmax) ? 1 : 0;
+      const float pk = pnorm[k - 1];
+      T.rows[atomicAdd(&W.cursor[c], 1)] = make_int4(j | (sa << 30), k, __float_as_int(pk), 0);
+    }
     if (r == j) continue;
     const uint4 a = __ldcg(reinterpret_cast<const uint4*>(Qd + (int64_t)j * dp) + i);
     const uint4 b = __ldcg(reinterpret_cast<const uint4*>(Qd + (int64_t)r * dp) + i);
@@ -1486,21 +1677,31 @@ sah_status prepare_user_pass_tc(Index* ix, const float* Qd, const float* qn, con
   // the distinct query vectors of the sub-batch
   const ColTable T = col_table_at(scratch, nq, ix->dp);
   int ht = 0, npow = 0;
-  const size_t need = sizeof(int32_t) * col_scratch_ints(nq, &ht, &npow);
-  // up to 4,096 rows the work arrays fit in shared memory (180 KB)
-  const int in_global = need > 200 * 1024 ? 1 : 0;
-  const size_t tsmem = in_global ? 0 : need;
-  if (!in_global) SAH_TRY(raise_smem_limit((const void*)column_table_kernel, tsmem));
+  col_table_dims(nq, &ht, &npow);
+  const ColWork W = col_work_at(T.scratch, nq, ht);
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
-  column_table_kernel<<<1, 1024, tsmem, st>>>(Qd, qn, qh, nq, ix->dp, kk, modes, ix->kmax, ix->n, ix->pnorm, ht, npow,
-                                               T, 0, in_global);
-  column_check_kernel<<<sms, 512, 0, st>>>(Qd, nq, ix->dp, T);
-  column_table_kernel<<<1, 1024, tsmem, st>>>(Qd, qn, qh, nq, ix->dp, kk, modes, ix->kmax, ix->n, ix->pnorm, ht, npow,
-                                               T, 1, in_global);
+  const unsigned rows_grid = (unsigned)((nq + 255) / 256);
+  col_init_kernel<<<(unsigned)std::max(1, std::min(sms * 4, (ht + 4 * nq + 8 + 255) / 256)), 256, 0, st>>>(W, nq, ht);
+  col_hash_kernel<<<rows_grid, 256, 0, st>>>(qh, kk, nq, ix->kmax, ix->n, ht, W);
+  col_reps_kernel<<<rows_grid, 256, 0, st>>>(kk, nq, ix->kmax, W);
+  const dim3 rank_grid((unsigned)((nq + kRankOwn * kRankThreads - 1) / (kRankOwn * kRankThreads)),
+                       (unsigned)((nq + kRankChunk - 1) / kRankChunk));
+  col_rank_kernel<<<rank_grid, kRankThreads, 0, st>>>(qn, kk, ix->kmax, W);
+  col_place_kernel<<<rows_grid, 256, 0, st>>>(W, T);
+  col_scatter_kernel<<<(unsigned)(sms * 4), 256, 0, st>>>(Qd, kk, modes, ix->kmax, ix->n, ix->pnorm, nq, ix->dp, W, T);
+  // the rebuild (nothing unless the check raised the flag): its work arrays in shared memory
+  // up to 4,096 rows (180 KB), past that all but the sort's (128 KB at 16,384 rows) in the
+  // table's scratch
+  const size_t need = sizeof(int32_t) * (2 * (size_t)ht + 5 * (size_t)nq + 2 * (size_t)npow);
+  const int in_global = need > 200 * 1024 ? 1 : 0;
+  const size_t tsmem = in_global ? sizeof(int32_t) * 2 * (size_t)npow : need;
+  SAH_TRY(raise_smem_limit((const void*)column_table_rebuild_kernel, tsmem));
+  column_table_rebuild_kernel<<<1, 1024, tsmem, st>>>(Qd, qn, qh, nq, ix->dp, kk, modes, ix->kmax, ix->n, ix->pnorm,
+                                                       ht, npow, T, in_global);
   column_transpose_kernel<<<sms, 512, 0, st>>>(Qd, qn, nq, ix->dp, T);
   SAH_CUDA(cudaGetLastError());
-  if (launches) *launches += 4;
+  if (launches) *launches += 8;
   if (ix->prm.tc_user_pass == 2) {
     // the FP8 user pass: every row of the sub-batch in E4M3 with its scale
     launch_e4m3_rows(Qd, nq, ix->dp, ix->d, T.q8, T.qsc, st);
