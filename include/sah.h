@@ -226,6 +226,8 @@ typedef struct {
   int64_t block_col_pairs;      /* (leaf, distinct query vector) pairs of the tensor-core block filter */
   int64_t tc_rows;              /* user rows the tensor-core user pass streamed (each column set streams
                                    the tiles that need one of its columns) */
+  int64_t cand_blocks;          /* candidate blocks (one user's scores of 32 columns) the tensor-core
+                                   user pass left to its resolve kernel (exact thresholds) */
 } sah_stats;
 
 sah_status sah_index_stats(const sah_index* index, sah_stats* out);

@@ -62,7 +62,7 @@ class Stats(ctypes.Structure):
         ("stage_ms", ctypes.c_double * 8), ("stage_launches", ctypes.c_int64 * 8),
         ("build_gemm_ms", ctypes.c_double), ("build_overflow_rows", ctypes.c_int64),
         ("pairs_rescored", ctypes.c_int64), ("tc_scores", ctypes.c_int64), ("block_col_pairs", ctypes.c_int64),
-        ("tc_rows", ctypes.c_int64)]
+        ("tc_rows", ctypes.c_int64), ("cand_blocks", ctypes.c_int64)]
 
     def as_dict(self):
         out = {}

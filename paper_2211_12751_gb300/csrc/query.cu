@@ -45,6 +45,7 @@ enum StatSlot {
   ST_TC_SCORES,      // (user, column) scores of the tensor-core user pass
   ST_BF_COLPAIRS,    // (leaf, distinct column) pairs of the tensor-core block filter
   ST_TC_ROWS,        // user rows the tensor-core user pass streamed (once per column set)
+  ST_CAND_BLOCKS,    // candidate blocks (a user's 32 scores) the tensor-core user pass wrote
   ST_COUNT
 };
 
@@ -653,6 +654,136 @@ __global__ void zero_users_kernel(const int32_t* __restrict__ zid, int64_t nz, i
   set_answer(bitmap, words, j, id);
 }
 
+// Answers per summary word, then their scan.  Per query j: a summary word sw that marks any
+// bitmap word gets its count of answers; the exclusive prefix of the counts within the query
+// is written to wpre[j * nsw + sw] and the word is appended to list; cnt[j] gets the query's
+// total; a row with k > n counts every summary word's users.  The last CTA of the second
+// kernel (a ticket taken after a fence) turns the totals into the offsets: offsets[j] = base
+// + the answers of the queries before j, offsets[nq] the end (also into offsets2 when
+// given).
+//
+// answer_count_light_kernel, a warp per query (kAnswerWarps per CTA): the lanes read the top
+// words and count the summary words they mark; a query with at most kLightWords of them is
+// counted here, one summary word per lane and round (a lane finds its word from the scan of
+// the top words' bit counts), every other query (and every row with k > n) goes to the heavy
+// list.  answer_count_heavy_kernel, a CTA of kHeavyThreads per listed query (the CTAs loop
+// over the list): a thread per summary word, kHeavyThreads words per step, a block scan per
+// step.  Either way a summary word's bitmap words are read by predicated loads that all go
+// out before any is used.
+constexpr int kAnswerWarps = 8;
+constexpr int kLightWords = 64;
+constexpr int kHeavyThreads = 512;
+
+__device__ __forceinline__ int warp_inclusive_scan(int x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// Position of the n-th set bit of x (n counted from 0, n < popc(x)): halving the word.
+__device__ __forceinline__ int nth_set_bit(uint32_t x, int n) {
+  int pos = 0;
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    const int c = __popc(x & ((1u << h) - 1u));
+    if (n >= c) {
+      n -= c;
+      x >>= h;
+      pos += h;
+    }
+  }
+  return pos;
+}
+
+// The answers in the bitmap words p[b] whose bit b of sm is set: 32 predicated loads issued
+// back to back, then their bit counts.
+__device__ __forceinline__ int count_marked_words(const uint32_t* p, uint32_t sm) {
+  uint32_t v[32];
+#pragma unroll
+  for (int b = 0; b < 32; ++b) {
+    v[b] = 0u;
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.global.u32 %0, [%1];\n\t}"
+        : "+r"(v[b])
+        : "l"(p + b), "r"(sm & (1u << b)));
+  }
+  int c = 0;
+#pragma unroll
+  for (int b = 0; b < 32; ++b) c += __popc(v[b]);
+  return c;
+}
+
+// Users a summary word of a k > n row holds.
+__device__ __forceinline__ int all_users_in(int sw, int64_t m) {
+  return (int)std::max<int64_t>(0, std::min<int64_t>(1024, m - (int64_t)sw * 1024));
+}
+
+__global__ void __launch_bounds__(kAnswerWarps * 32)
+answer_count_light_kernel(const uint32_t* __restrict__ bitmap, int64_t stride, const int32_t* __restrict__ kk,
+                          int64_t n, int32_t* __restrict__ wpre, int32_t* __restrict__ list,
+                          unsigned int* __restrict__ list_count, int32_t* __restrict__ cnt,
+                          int32_t* __restrict__ heavy, unsigned int* __restrict__ heavy_count, int nq) {
+  const int64_t w = answer_words(stride);
+  const int nsw = (int)(w / 32), ntop = (int)(w / 1024);
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * kAnswerWarps + (threadIdx.x >> 5);
+  if (j >= nq) return;   // warp-uniform; no block barrier follows
+  const uint32_t* row = bitmap + (int64_t)j * stride;
+  int marked = 0;
+  if (kk[j] <= n) {
+    for (int t0 = 0; t0 < ntop; t0 += 32) marked += __popc(t0 + lane < ntop ? row[w + nsw + t0 + lane] : 0u);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) marked += __shfl_xor_sync(0xffffffffu, marked, o);
+  }
+  if (kk[j] > n || marked > kLightWords) {
+    if (lane == 0) heavy[atomicAdd(heavy_count, 1u)] = j;
+    return;
+  }
+  const int64_t g0 = (int64_t)j * nsw;
+  int carry = 0;
+  for (int t0 = 0; t0 < ntop && marked > 0; t0 += 32) {
+    const uint32_t top = t0 + lane < ntop ? row[w + nsw + t0 + lane] : 0u;
+    const int pc = __popc(top);
+    const int incl = warp_inclusive_scan(pc, lane);
+    const int excl = incl - pc;
+    const int here = __shfl_sync(0xffffffffu, incl, 31);
+    marked -= here;
+    for (int r0 = 0; r0 < here; r0 += 32) {
+      // this lane's summary word, the r-th marked one: its top word is the first lane's with
+      // incl > r (a binary search over the lanes' inclusive counts, every lane taking part)
+      const int r = r0 + lane;
+      int lo = 0, hi = 31;
+#pragma unroll
+      for (int step = 0; step < 5; ++step) {
+        const int mid = (lo + hi) >> 1;
+        const int im = __shfl_sync(0xffffffffu, incl, mid);
+        if (im > r) hi = mid; else lo = mid + 1;
+      }
+      const uint32_t tl = __shfl_sync(0xffffffffu, top, lo);
+      const int el = __shfl_sync(0xffffffffu, excl, lo);
+      int c = 0, sw = 0;
+      if (r < here) {
+        sw = (t0 + lo) * 32 + nth_set_bit(tl, r - el);
+        c = count_marked_words(row + (int64_t)sw * 32, row[w + sw]);
+      }
+      const int ci = warp_inclusive_scan(c, lane);
+      const unsigned mk = __ballot_sync(0xffffffffu, c > 0);
+      unsigned b0 = 0;
+      if (lane == 0 && mk) b0 = atomicAdd(list_count, (unsigned)__popc(mk));
+      b0 = __shfl_sync(0xffffffffu, b0, 0);
+      if (c > 0) {
+        const int g = (int)(g0 + sw);
+        wpre[g] = carry + ci - c;
+        list[b0 + __popc(mk & ((1u << lane) - 1u))] = g;
+      }
+      carry += __shfl_sync(0xffffffffu, ci, 31);
+    }
+  }
+  if (lane == 0) cnt[j] = carry;
+}
+
 __device__ inline int block_exclusive_scan(int v, int* total) {
   __shared__ int wsum[32];
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -674,72 +805,67 @@ __device__ inline int block_exclusive_scan(int v, int* total) {
   return before + x - v;
 }
 
-// Answers per summary word, then their scan, one CTA per query j: a thread per summary
-// word sw reads the bitmap words the summary marks (independent loads, all in flight at
-// once) and counts their bits; a row with k > n counts the summary word's users.  The
-// block scans the counts in chunks of blockDim words and writes the exclusive prefix of
-// every word with answers to wpre[j * nsw + sw], appends those words to list (one atomic per
-// warp), and writes the query's total to cnt[j].  The last CTA to finish (a ticket taken
-// after a fence) then turns the totals into the offsets: offsets[j] = base + the answers
-// of the queries before j, offsets[nq] the end (also into offsets2 when given).
-__global__ void answer_count_scan_kernel(const uint32_t* __restrict__ bitmap, int64_t stride,
-                                         const int32_t* __restrict__ kk, int64_t n, int64_t m,
-                                         int32_t* __restrict__ wpre, int32_t* __restrict__ list,
-                                         unsigned int* __restrict__ list_count, int32_t* __restrict__ cnt, int nq,
-                                         int64_t base, int64_t* __restrict__ offsets, int64_t* __restrict__ offsets2,
-                                         unsigned int* __restrict__ ticket) {
+__global__ void __launch_bounds__(kHeavyThreads)
+answer_count_heavy_kernel(const uint32_t* __restrict__ bitmap, int64_t stride, const int32_t* __restrict__ kk,
+                          int64_t n, int64_t m, int32_t* __restrict__ wpre, int32_t* __restrict__ list,
+                          unsigned int* __restrict__ list_count, int32_t* __restrict__ cnt,
+                          const int32_t* __restrict__ heavy, const unsigned int* __restrict__ heavy_count, int nq,
+                          int64_t base, int64_t* __restrict__ offsets, int64_t* __restrict__ offsets2,
+                          unsigned int* __restrict__ ticket) {
   const int64_t w = answer_words(stride);
   const int nsw = (int)(w / 32);
-  const int j = blockIdx.x;
   const int lane = threadIdx.x & 31;
-  const bool all_users = kk[j] > n;
-  const uint32_t* row = bitmap + (int64_t)j * stride;
-  int carry = 0;
-  for (int c0 = 0; c0 < nsw; c0 += blockDim.x) {
-    const int sw = c0 + threadIdx.x;
-    int c = 0;
-    if (sw < nsw) {
-      if (all_users) {
-        c = (int)std::max<int64_t>(0, std::min<int64_t>(1024, m - (int64_t)sw * 1024));
-      } else {
-        const uint32_t sm = row[w + sw];
-        if (sm) {
-#pragma unroll
-          for (int b = 0; b < 32; ++b)
-            if ((sm >> b) & 1u) c += __popc(row[sw * 32 + b]);
+  const int nh = (int)*heavy_count;
+  for (int h = blockIdx.x; h < nh; h += gridDim.x) {
+    const int j = heavy[h];
+    const bool all_users = kk[j] > n;
+    const uint32_t* row = bitmap + (int64_t)j * stride;
+    int carry = 0;
+    for (int c0 = 0; c0 < nsw; c0 += kHeavyThreads) {
+      const int sw = c0 + threadIdx.x;
+      int c = 0;
+      if (sw < nsw) {
+        if (all_users) {
+          c = all_users_in(sw, m);
+        } else {
+          const uint32_t sm = row[w + sw];
+          if (sm) c = count_marked_words(row + (int64_t)sw * 32, sm);
         }
       }
+      int chunk_total;
+      const int pre = block_exclusive_scan(c, &chunk_total);
+      const int g = j * nsw + sw;
+      if (sw < nsw && c > 0) wpre[g] = carry + pre;
+      carry += chunk_total;
+      const unsigned mk = __ballot_sync(0xffffffffu, c > 0);
+      if (mk) {
+        unsigned b0 = 0;
+        if (lane == 0) b0 = atomicAdd(list_count, (unsigned)__popc(mk));
+        b0 = __shfl_sync(0xffffffffu, b0, 0);
+        if (c > 0) list[b0 + __popc(mk & ((1u << lane) - 1u))] = g;
+      }
     }
-    int chunk_total;
-    const int pre = block_exclusive_scan(c, &chunk_total);
-    const int g = j * nsw + sw;
-    if (sw < nsw && c > 0) wpre[g] = carry + pre;   // read only for the listed words (c > 0)
-    carry += chunk_total;
-    const unsigned mk = __ballot_sync(0xffffffffu, c > 0);
-    if (mk) {
-      unsigned b0 = 0;
-      if (lane == 0) b0 = atomicAdd(list_count, (unsigned)__popc(mk));
-      b0 = __shfl_sync(0xffffffffu, b0, 0);
-      if (c > 0) list[b0 + __popc(mk & ((1u << lane) - 1u))] = g;
-    }
+    if (threadIdx.x == 0) cnt[j] = carry;
   }
+  __syncthreads();
   __shared__ bool last;
   if (threadIdx.x == 0) {
-    cnt[j] = carry;
     __threadfence();
     last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
-  // the query offsets, in 64 bits: a contiguous run of queries per thread, then a block scan
-  __shared__ long long wtot[32];
-  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // the query offsets, in 64 bits: a contiguous run of queries per thread (loads from L2,
+  // where the other CTAs' totals are), then a block scan
+  __shared__ long long wtot[kHeavyThreads / 32];
+  const int warp = threadIdx.x >> 5;
   const int qper = (nq + blockDim.x - 1) / blockDim.x;
   const int q0 = min((int)threadIdx.x * qper, nq), q1 = min(q0 + qper, nq);
   long long t = 0;
-  for (int q = q0; q < q1; ++q) t += *(volatile int32_t*)&cnt[q];
+  for (int q = q0; q < q1; ++q) t += __ldcg(&cnt[q]);
   long long x = t;
+#pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const long long y = __shfl_up_sync(0xffffffffu, x, o);
     if (lane >= o) x += y;
@@ -747,7 +873,7 @@ __global__ void answer_count_scan_kernel(const uint32_t* __restrict__ bitmap, in
   if (lane == 31) wtot[warp] = x;
   __syncthreads();
   long long before = base, all = base;
-  for (int v = 0; v < nw; ++v) {
+  for (int v = 0; v < kHeavyThreads / 32; ++v) {
     if (v < warp) before += wtot[v];
     all += wtot[v];
   }
@@ -755,7 +881,7 @@ __global__ void answer_count_scan_kernel(const uint32_t* __restrict__ bitmap, in
   for (int q = q0; q < q1; ++q) {
     offsets[q] = o;
     if (offsets2) offsets2[q] = o;
-    o += *(volatile int32_t*)&cnt[q];
+    o += __ldcg(&cnt[q]);
   }
   if (threadIdx.x == 0) {
     offsets[nq] = all;
@@ -821,7 +947,10 @@ __global__ void answer_emit_kernel(uint32_t* __restrict__ bitmap, int64_t stride
       const int je = ge / nsw, swe = ge - je * nsw;
       uint32_t* row = bitmap + (int64_t)je * stride;
       if ((se >> lane) & 1u) row[(int64_t)swe * 32 + lane] = 0u;
-      if (lane == 0 && se) row[w + swe] = 0u;
+      if (lane == 0 && se) {
+        row[w + swe] = 0u;
+        row[w + nsw + (swe >> 5)] = 0u;   // the top word (every listed word under it clears it)
+      }
       if (ae) {
         const int64_t lo = (int64_t)swe * 1024, hi = std::min<int64_t>(m, lo + 1024);
         for (int64_t i = lo + lane; i < hi; i += 32) out[de + (i - lo)] = (int32_t)i;
@@ -851,11 +980,10 @@ __global__ void answer_emit_kernel(uint32_t* __restrict__ bitmap, int64_t stride
 // ---------------------------------------------------------------- workspace
 namespace {
 
-constexpr int kAnswerThreads = 512;   // summary words counted and scanned per step of a query's CTA
-constexpr int kCtlCounters = 6;   // survivor counts (4), answer-list length, scan ticket
+constexpr int kCtlCounters = 7;   // survivor counts (4), answer-list length, scan ticket, heavy-list length
 
 struct WsLayout {
-  size_t qd, qb, qn, qh, kk, pairs, pcount, kmask, tneed, tneed_end, coltab, survcnt, alist_n, ticket, bitmap, chunk,
+  size_t qd, qb, qn, qh, kk, pairs, pcount, kmask, tneed, tneed_end, coltab, survcnt, alist_n, ticket, heavy_n, bitmap, chunk,
       offsets, stats, total;
 };
 
@@ -879,7 +1007,8 @@ WsLayout layout_for(const Index* ix, int qb) {
   // kept bits per (leaf, row), then one flag per leaf (the tensor-core block filter's)
   L.kmask = take(sizeof(uint32_t) * (size_t)std::max(ix->nb, 1) * ((qb + 31) / 32) + sizeof(int32_t) * std::max(ix->nb, 1));
   L.coltab = take(user_pass_tc_scratch_bytes(qb, ix->dp));
-  L.chunk = take(sizeof(int32_t) * ((size_t)qb * (2 * (answer_words(answer_stride(ix->m)) / 32) + 1)));
+  // per-word prefixes (qb nsw) | per-query counts (qb) | listed words (qb nsw) | heavy rows (qb)
+  L.chunk = take(sizeof(int32_t) * ((size_t)qb * (2 * (answer_words(answer_stride(ix->m)) / 32) + 2)));
   // the control block, contiguous so that one memset clears its counters (and, with the
   // tensor-core user pass, the tile flags) and one copy reads it back: stats[ST_COUNT] |
   // survivor counts[3] | answer-list length (u64) | scan ticket (u64) | offsets[qb + 1] |
@@ -889,7 +1018,8 @@ WsLayout layout_for(const Index* ix, int qb) {
   L.survcnt = L.stats + sizeof(unsigned long long) * ST_COUNT;
   L.alist_n = L.survcnt + 4 * sizeof(unsigned long long);
   L.ticket = L.alist_n + sizeof(unsigned long long);
-  L.offsets = L.ticket + sizeof(unsigned long long);
+  L.heavy_n = L.ticket + sizeof(unsigned long long);
+  L.offsets = L.heavy_n + sizeof(unsigned long long);
   L.tneed = L.offsets + sizeof(int64_t) * (size_t)(qb + 1);
   L.tneed_end = L.tneed + ntiles;
   L.total = o;
@@ -1193,7 +1323,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
             SAH_TRY(run_user_pass_tc(ix, Qd, (uint16_t*)(w + L.qb), w + L.coltab, qn, kk, nqb, kmask,
                                      mask_words, (uint8_t*)(w + L.tneed), bitmap, words, surv + 2 * surv_cap,
                                      survcnt + 2, surv + 3 * surv_cap, survcnt + 3, surv, survcnt, surv_cap, stats,
-                                     ST_YES_EARLY, ST_FP64, ST_TC_SCORES, ST_TC_ROWS, st,
+                                     ST_YES_EARLY, ST_FP64, ST_TC_SCORES, ST_TC_ROWS, ST_CAND_BLOCKS, st,
                                      &up_launches, tm.slot(6)));
           } else if (reg_variant) {
             const size_t smem = (size_t)16 * kQChunk * dp4 + sizeof(PairInfo) * kQChunk + sizeof(float) * 64 * threads;
@@ -1244,20 +1374,24 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
           }
         }
         tm.begin(4);
-        int n_compact = 2;
+        int n_compact = 3;
         if (ix->nzero > 0) {
           zero_users_kernel<<<grid_for(ix->nzero * nqb, 256), 256, 0, st>>>(ix->zero_uid, ix->nzero, nqb, bitmap,
                                                                              words);
           ++n_compact;
         }
         // after the per-word counts: the per-query counts, the list of words with answers
-        // and its length
+        // and its length, the heavy rows and theirs
         int32_t* qcnt = chunk + (int64_t)nqb * nsw;
         int32_t* alist = qcnt + nqb;
+        int32_t* heavy = alist + (int64_t)nqb * nsw;
         unsigned int* alist_n = (unsigned int*)(w + L.alist_n);
-        answer_count_scan_kernel<<<nqb, kAnswerThreads, 0, st>>>(
-            bitmap, words, kk, ix->n, ix->m, chunk, alist, alist_n, qcnt, nqb, direct ? 0 : res_total, offsets,
-            direct ? offsets_dev : nullptr, (unsigned int*)(w + L.ticket));
+        unsigned int* heavy_n = (unsigned int*)(w + L.heavy_n);
+        answer_count_light_kernel<<<(nqb + kAnswerWarps - 1) / kAnswerWarps, kAnswerWarps * 32, 0, st>>>(
+            bitmap, words, kk, ix->n, chunk, alist, alist_n, qcnt, heavy, heavy_n, nqb);
+        answer_count_heavy_kernel<<<(unsigned)std::max(1, std::min(nqb, sms * 2)), kHeavyThreads, 0, st>>>(
+            bitmap, words, kk, ix->n, ix->m, chunk, alist, alist_n, qcnt, heavy, heavy_n, nqb,
+            direct ? 0 : res_total, offsets, direct ? offsets_dev : nullptr, (unsigned int*)(w + L.ticket));
         int32_t* dst;
         int64_t dst_cap;
         if (direct) {
@@ -1363,6 +1497,7 @@ sah_status run_batch(Index* ix, CallCtx* cx, const float* Q_dev, int32_t nq, con
       agg.tc_scores += (int64_t)st_h[ST_TC_SCORES];
       agg.block_col_pairs += (int64_t)st_h[ST_BF_COLPAIRS];
       agg.tc_rows += (int64_t)st_h[ST_TC_ROWS];
+      agg.cand_blocks += (int64_t)st_h[ST_CAND_BLOCKS];
       // the next call starts from the largest list of this call's sub-batches (twice it)
       surv_call_max = std::max(surv_call_max, nsmax);
       cx->surv_hint = std::max<int64_t>(1 << 16, 2 * surv_call_max);

@@ -226,21 +226,26 @@ __device__ inline int64_t block_count(const unsigned long long* c, int64_t cap) 
 }
 
 // Answer bitmaps.  Per query one row of answer_stride(m) 32-bit words: w = ceil(m / 32)
-// rounded up to a multiple of 32 words whose bit (id & 31) of word (id >> 5) marks user id,
-// then w / 32 summary words whose bit i marks a nonzero word i, so that counting and
-// emitting visit only the words that hold answers.
+// rounded up to a multiple of 1024 words whose bit (id & 31) of word (id >> 5) marks user
+// id, then w / 32 summary words whose bit i marks a nonzero word i, then w / 1024 top words
+// whose bit i marks a nonzero summary word i, so that counting and emitting visit only the
+// words that hold answers.
 __host__ __device__ inline int64_t answer_stride(int64_t m) {
-  const int64_t w = ((m + 31) / 32 + 31) / 32 * 32;
-  return w + w / 32;
+  const int64_t w = ((m + 31) / 32 + 1023) / 1024 * 1024;
+  return w + w / 32 + w / 1024;
 }
-__host__ __device__ inline int64_t answer_words(int64_t stride) { return (int64_t)((uint64_t)stride / 33 * 32); }
+__host__ __device__ inline int64_t answer_words(int64_t stride) {
+  return (int64_t)((uint64_t)stride / 1057 * 1024);
+}
 
-// Both ORs are reductions the thread does not wait for.
+// The three ORs are reductions the thread does not wait for.
 __device__ __forceinline__ void set_answer(uint32_t* bitmap, int64_t stride, int j, int32_t id) {
   uint32_t* row = bitmap + (int64_t)j * stride;
+  const int64_t w = answer_words(stride);
   const int wi = id >> 5;
   atomicOr(&row[wi], 1u << (id & 31));
-  atomicOr(&row[answer_words(stride) + (wi >> 5)], 1u << (wi & 31));
+  atomicOr(&row[w + (wi >> 5)], 1u << (wi & 31));
+  atomicOr(&row[w + (w >> 5) + (wi >> 10)], 1u << ((wi >> 5) & 31));
 }
 
 // A float widened to double by rewriting its fields (IEEE 754 binary32 -> binary64, exact
@@ -322,7 +327,8 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
                             uint32_t* bitmap, int64_t words, Survivor* resc, unsigned long long* resc_count,
                             Survivor* cand, unsigned long long* cand_count,
                             Survivor* surv, unsigned long long* surv_count, int64_t surv_cap,
-                            unsigned long long* stats, int st_yes, int st_fp64, int st_scores, int st_rows, cudaStream_t st,
+                            unsigned long long* stats, int st_yes, int st_fp64, int st_scores, int st_rows, int st_cand,
+                            cudaStream_t st,
                             int* launches, const cudaEvent_t* ev = nullptr);   // ev: begin / end of the GEMM kernel
 // topk_tc.cu: the 64 largest FP32 scores of every user over all items, through tcgen05
 sah_status topk_full_tc(Index* ix, float* vlast, int32_t* ids64, cudaStream_t st, double* gemm_ms);

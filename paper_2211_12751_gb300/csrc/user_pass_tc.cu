@@ -1584,18 +1584,24 @@ sah_status launch_pass(Index* ix, UpParams p, int sms, cudaStream_t st, int* lau
 //   s - e >= L + E, when L is the exact k-th score (|P'| = n)  -> "yes"
 //   otherwise the pair is re-scored in FP32 (and FP64) by pair_rescore_kernel.
 // L + E is bounded above from L - E - 1e-30 (rounded down) with four units in the last place
-// and 2e-30 to spare.
-__global__ void __launch_bounds__(512)
+// and 2e-30 to spare.  The kernel is bound by the latency of its dependent gathers (block,
+// then column, then bound and rows), so the loads that do not depend on each other go out
+// together, the column's first row is fetched before its "no" test is known, and the next
+// block's header and score are fetched while the current one is decided.
+constexpr int kResolveThreads = 512;
+constexpr int kResolveCtasPerSm = 3;
+__global__ void __launch_bounds__(kResolveThreads, kResolveCtasPerSm)
 cand_resolve_kernel(const CandBlock* __restrict__ cand, const unsigned long long* __restrict__ cand_count,
                     int64_t cap, ColTable T, const float* __restrict__ Lt, const float* __restrict__ Eu,
                     const float* __restrict__ unorm, const int32_t* __restrict__ uid, int64_t mz, int kmax,
                     int l_exact, float cband, float gamma, uint32_t* __restrict__ bitmap, int64_t words,
                     Survivor* __restrict__ resc, unsigned long long* __restrict__ resc_count,
-                    unsigned long long* __restrict__ stats, int st_yes, const int* __restrict__ timeout) {
+                    unsigned long long* __restrict__ stats, int st_yes, int st_cand, const int* __restrict__ timeout) {
   __shared__ int stop;
   if (threadIdx.x == 0) stop = *(volatile const int*)timeout;
   const int64_t total = block_count(cand_count, cap);   // synchronises the block
   if (stop || total == 0) return;   // after a timed-out wait the list may hold unwritten entries
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&stats[st_cand], (unsigned long long)total);
   const int ncol = *T.ncol;
   // the column table is read in place (it is small and stays in L2 and L1): staging all of
   // it in every CTA's shared memory cost more than the blocks' own work
@@ -1606,33 +1612,51 @@ cand_resolve_kernel(const CandBlock* __restrict__ cand, const unsigned long long
   const int lane = threadIdx.x & 31;
   unsigned long long yes_cnt = 0;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < total; b += nw) {
-    const int4 h0 = reinterpret_cast<const int4*>(cand + b)[0];
-    const int64_t r = h0.x;
-    const int c = h0.y + lane;
-    const float s = cand[b].s[lane];
+  int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int2 hn = make_int2(0, 0);
+  float sn = 0.f;
+  if (b < total) {
+    hn = reinterpret_cast<const int2*>(cand + b)[0];
+    sn = cand[b].s[lane];
+  }
+  for (; b < total; b += nw) {
+    const int64_t r = hn.x;
+    const int c = hn.y + lane;
+    const float s = sn;
+    if (b + nw < total) {   // the next block, while this one is decided
+      hn = reinterpret_cast<const int2*>(cand + b + nw)[0];
+      sn = cand[b + nw].s[lane];
+    }
+    const bool live = c < ncol;
     const float nu = unorm[r], E = Eu[r];
     const int32_t uidv = uid[r];
+    float qn = 0.f;
+    int kq = 0, q0 = 0, q1 = 0;
+    if (live) {
+      qn = qnc[c];
+      kq = kqc[c];
+      q0 = start[c];
+      q1 = start[c + 1];
+    }
+    // the column's first row, before its "no" test is known
+    int4 rw0 = make_int4(0, 0, 0, 0);
+    if (q1 > q0) rw0 = rows[q0];
     const float cu = __fmul_ru(cband, nu);
     const float nun = __fmul_ru(nu, 1.f + 2.f * gamma);
-    const bool live = c < ncol;
-    const float qn = live ? qnc[c] : 0.f;
     const float lo = __fsub_rd(s, __fmul_ru(cu, qn) + 1e-30f);
     // the column's own "no" first: its smallest bound belongs to its largest k (bounds fall as
     // k grows); below it, every row of the column is "no"
     // (a column holds rows of k <= k_max only, or rows of k > k_max only, which have no bound)
     bool cand_c = live;
-    if (live) {
-      const int kq = kqc[c];
-      if (kq > 0) cand_c = !(__fmaf_ru(cu, qn, s) < __fsub_rd(__fsub_rd(Lt[(int64_t)(kq - 1) * mz + r], E), 1e-30f));
-    }
-    const int q0 = cand_c ? start[c] : 0, nr = cand_c ? start[c + 1] - q0 : 0;
+    if (live && kq > 0)
+      cand_c = !(__fmaf_ru(cu, qn, s) < __fsub_rd(__fsub_rd(Lt[(int64_t)(kq - 1) * mz + r], E), 1e-30f));
+    const int nr = cand_c ? q1 - q0 : 0;
     const int nmax = __reduce_max_sync(0xffffffffu, nr);
     for (int t = 0; t < nmax; ++t) {
       bool open = false;
       int jv = 0;
       if (t < nr) {
-        const int4 rw = rows[q0 + t];
+        const int4 rw = t == 0 ? rw0 : rows[q0 + t];
         const int j = rw.x & 0x3fffffff, k = rw.y;
         jv = rw.x;
         float Lq = -INFINITY;   // L - E - 1e-30 rounded down, or -inf without a bound
@@ -1732,7 +1756,7 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
                             uint32_t* bitmap, int64_t words, Survivor* resc, unsigned long long* resc_count,
                             Survivor* cand, unsigned long long* cand_count,
                             Survivor* surv, unsigned long long* surv_count, int64_t surv_cap,
-                            unsigned long long* stats, int st_yes, int st_fp64, int st_scores, int st_rows,
+                            unsigned long long* stats, int st_yes, int st_fp64, int st_scores, int st_rows, int st_cand,
                             cudaStream_t st,
                             int* launches, const cudaEvent_t* ev) {
   if (ix->m_nz == 0 || nq == 0 || ix->dk <= 0) return SAH_OK;
@@ -1822,10 +1846,10 @@ sah_status run_user_pass_tc(Index* ix, const float* Qd, uint16_t* Qsplit, void* 
     else SAH_TRY((launch_pass<2, 4, 256, 1, true>(ix, p, sms, st, launches, ev)));
   }
   {
-    cand_resolve_kernel<<<sms * 2, 512, 0, st>>>(reinterpret_cast<const CandBlock*>(cand), cand_count, surv_cap, T,
-                                                    ix->Lt, ix->Eu, ix->unorm, ix->uid, ix->m_nz, ix->kmax, p.l_exact,
-                                                    p.cband, ix->gamma, bitmap, words, resc, resc_count, stats, st_yes,
-                                                    ix->dev_timeout);
+    cand_resolve_kernel<<<sms * kResolveCtasPerSm, kResolveThreads, 0, st>>>(
+        reinterpret_cast<const CandBlock*>(cand), cand_count, surv_cap, T, ix->Lt, ix->Eu, ix->unorm, ix->uid,
+        ix->m_nz, ix->kmax, p.l_exact, p.cband, ix->gamma, bitmap, words, resc, resc_count, stats, st_yes, st_cand,
+        ix->dev_timeout);
   }
   SAH_CUDA(cudaGetLastError());
   if (launches) *launches += 1;
