@@ -667,8 +667,9 @@ __global__ void zero_users_kernel(const int32_t* __restrict__ zid, int64_t nz, i
 // counted here, one summary word per lane and round (a lane finds its word from the scan of
 // the top words' bit counts), every other query (and every row with k > n) goes to the heavy
 // list.  answer_count_heavy_kernel, a CTA of kHeavyThreads per listed query (the CTAs loop
-// over the list): a thread per summary word, kHeavyThreads words per step, a block scan per
-// step.  Either way a summary word's bitmap words are read by predicated loads that all go
+// over the list): the marked summary words dealt out the same way, a thread per word and
+// kHeavyThreads words per step, a block scan per step (a row with k > n: every summary
+// word).  Either way a summary word's bitmap words are read by predicated loads that all go
 // out before any is used.
 constexpr int kAnswerWarps = 8;
 constexpr int kLightWords = 64;
@@ -805,6 +806,23 @@ __device__ inline int block_exclusive_scan(int v, int* total) {
   return before + x - v;
 }
 
+// One step of a heavy query: each thread's count c of word g; its prefix (carry + the block's
+// exclusive scan) for the listed words and the list entries; returns the step's total.
+__device__ __forceinline__ int heavy_step(int c, int g, int carry, int lane, int32_t* __restrict__ wpre,
+                                          int32_t* __restrict__ list, unsigned int* __restrict__ list_count) {
+  int tot;
+  const int pre = block_exclusive_scan(c, &tot);
+  if (c > 0) wpre[g] = carry + pre;
+  const unsigned mk = __ballot_sync(0xffffffffu, c > 0);
+  if (mk) {
+    unsigned b0 = 0;
+    if (lane == 0) b0 = atomicAdd(list_count, (unsigned)__popc(mk));
+    b0 = __shfl_sync(0xffffffffu, b0, 0);
+    if (c > 0) list[b0 + __popc(mk & ((1u << lane) - 1u))] = g;
+  }
+  return tot;
+}
+
 __global__ void __launch_bounds__(kHeavyThreads)
 answer_count_heavy_kernel(const uint32_t* __restrict__ bitmap, int64_t stride, const int32_t* __restrict__ kk,
                           int64_t n, int64_t m, int32_t* __restrict__ wpre, int32_t* __restrict__ list,
@@ -813,36 +831,49 @@ answer_count_heavy_kernel(const uint32_t* __restrict__ bitmap, int64_t stride, c
                           int64_t base, int64_t* __restrict__ offsets, int64_t* __restrict__ offsets2,
                           unsigned int* __restrict__ ticket) {
   const int64_t w = answer_words(stride);
-  const int nsw = (int)(w / 32);
+  const int nsw = (int)(w / 32), ntop = (int)(w / 1024);
   const int lane = threadIdx.x & 31;
   const int nh = (int)*heavy_count;
+  __shared__ uint32_t tw[kHeavyThreads];   // a chunk of top words
+  __shared__ int tpre[kHeavyThreads];      // the exclusive prefix of their bit counts
   for (int h = blockIdx.x; h < nh; h += gridDim.x) {
     const int j = heavy[h];
-    const bool all_users = kk[j] > n;
     const uint32_t* row = bitmap + (int64_t)j * stride;
+    const int64_t g0 = (int64_t)j * nsw;
     int carry = 0;
-    for (int c0 = 0; c0 < nsw; c0 += kHeavyThreads) {
-      const int sw = c0 + threadIdx.x;
-      int c = 0;
-      if (sw < nsw) {
-        if (all_users) {
-          c = all_users_in(sw, m);
-        } else {
-          const uint32_t sm = row[w + sw];
-          if (sm) c = count_marked_words(row + (int64_t)sw * 32, sm);
-        }
+    if (kk[j] > n) {
+      // every user: each summary word's users, kHeavyThreads words per step
+      for (int c0 = 0; c0 < nsw; c0 += kHeavyThreads) {
+        const int sw = c0 + threadIdx.x;
+        const int c = sw < nsw ? all_users_in(sw, m) : 0;
+        carry += heavy_step(c, (int)(g0 + sw), carry, lane, wpre, list, list_count);
       }
-      int chunk_total;
-      const int pre = block_exclusive_scan(c, &chunk_total);
-      const int g = j * nsw + sw;
-      if (sw < nsw && c > 0) wpre[g] = carry + pre;
-      carry += chunk_total;
-      const unsigned mk = __ballot_sync(0xffffffffu, c > 0);
-      if (mk) {
-        unsigned b0 = 0;
-        if (lane == 0) b0 = atomicAdd(list_count, (unsigned)__popc(mk));
-        b0 = __shfl_sync(0xffffffffu, b0, 0);
-        if (c > 0) list[b0 + __popc(mk & ((1u << lane) - 1u))] = g;
+    } else {
+      // the summary words the top words mark, dealt out in ascending order: a thread per
+      // marked word and step, which finds its top word by a binary search over the prefix
+      for (int t0 = 0; t0 < ntop; t0 += kHeavyThreads) {
+        const int nt = min(kHeavyThreads, ntop - t0);
+        const uint32_t top = (int)threadIdx.x < nt ? row[w + nsw + t0 + threadIdx.x] : 0u;
+        int marked;
+        const int ex = block_exclusive_scan(__popc(top), &marked);
+        tw[threadIdx.x] = top;
+        tpre[threadIdx.x] = ex;
+        __syncthreads();
+        for (int r0 = 0; r0 < marked; r0 += kHeavyThreads) {
+          const int r = r0 + threadIdx.x;
+          int c = 0, sw = 0;
+          if (r < marked) {
+            int lo = 0, hi = nt - 1;   // the last top word whose prefix is <= r holds it
+            while (lo < hi) {
+              const int mid = (lo + hi + 1) >> 1;
+              if (tpre[mid] <= r) lo = mid; else hi = mid - 1;
+            }
+            sw = (t0 + lo) * 32 + nth_set_bit(tw[lo], r - tpre[lo]);
+            c = count_marked_words(row + (int64_t)sw * 32, row[w + sw]);
+          }
+          carry += heavy_step(c, (int)(g0 + sw), carry, lane, wpre, list, list_count);
+        }
+        __syncthreads();   // the chunk's top words are read until here
       }
     }
     if (threadIdx.x == 0) cnt[j] = carry;
