@@ -4,11 +4,13 @@
 //
 // Columns.  The rows of a sub-batch are (q, k) requests; rows asking for the same vector q
 // (with k <= k_max) share one GEMM column, so a batch that asks each item at several k
-// costs one column per item.  Five grid-wide kernels find the distinct vectors (a hash
-// table on a 64-bit hash of each row's bits), put the columns in descending order of ||q||
-// and list each column's rows, checking every row bitwise against its column's first row;
-// should two different vectors share a hash, one CTA builds the table again comparing
-// whole vectors.
+// costs one column per item.  The distinct vectors are found by a hash table on a 64-bit
+// hash of each row's bits, the columns put in descending order of ||q|| and each column's
+// rows listed; every row is then checked bitwise against its column's first row, and should
+// two different vectors share a hash, one CTA builds the table again comparing whole
+// vectors.  Up to kSmallTable rows one CTA builds the table in shared memory; past that five
+// grid-wide kernels do (a single CTA's sort and probes would take longer than the rest of
+// the table).
 //
 // Operands.  BF16 alone carries 8 significant bits, which makes the score's error band
 // (about 2^-7 ||u|| ||q||) so wide that many pairs would stay open.  Every FP32 vector x
@@ -206,17 +208,19 @@ __device__ int block_exclusive_scan(int v, int* wsum, int* total) {
   return r;
 }
 
-// The table built again by one CTA of 1024 threads, every probe of the hash table comparing
-// the rows bitwise: nothing unless the grid-wide build's check raised the table's flag (two
-// different vectors with one hash).  The same table as the grid-wide build's: rows with
-// k > n get no column; a column per (vector, k <= k_max); columns in descending order of
-// the key (+inf for columns whose rows all have k > k_max, ||q|| otherwise), equal keys by
-// first row.
+// The table built by one CTA of 1024 threads.  mode 0: the hash table probed on (hash of the
+// padded row's bits, k <= k_max), for sub-batches of up to kSmallTable rows, whose rows
+// column_check_kernel then checks bitwise.  mode 1: nothing unless a check raised the
+// table's flag (two different vectors with one hash); then every probe compares the rows
+// bitwise.  The same table as the grid-wide build's: rows with k > n get no column; a column
+// per (vector, k <= k_max); columns in descending order of the key (+inf for columns whose
+// rows all have k > k_max, ||q|| otherwise), equal keys by first row.
+constexpr int kSmallTable = 2048;
 __global__ void __launch_bounds__(1024, 1)
-column_table_rebuild_kernel(const float* __restrict__ Qd, const float* __restrict__ qn,
-                            const uint64_t* __restrict__ qh, int nq, int dp, const int32_t* __restrict__ kk,
-                            const int32_t* __restrict__ modes, int kmax, int64_t n, const float* __restrict__ pnorm,
-                            int ht, int npow, ColTable T, int in_global) {
+column_table_cta_kernel(const float* __restrict__ Qd, const float* __restrict__ qn, const uint64_t* __restrict__ qh,
+                        int nq, int dp, const int32_t* __restrict__ kk, const int32_t* __restrict__ modes, int kmax,
+                        int64_t n, const float* __restrict__ pnorm, int ht, int npow, ColTable T, int mode,
+                        int in_global) {
   extern __shared__ int32_t sm_dyn[];
   // the work arrays: in shared memory, or (a sub-batch too large for it) in the table's
   // global scratch, which the CTA's barriers order just as well; the sort's keys and
@@ -224,7 +228,7 @@ column_table_rebuild_kernel(const float* __restrict__ Qd, const float* __restric
   int32_t* sm = in_global ? T.scratch : sm_dyn;
   __shared__ int wsum[32];
   __shared__ int total_sh;
-  if (*(volatile int32_t*)(T.ncol + 1) == 0) return;
+  if (mode == 1 && *(volatile int32_t*)(T.ncol + 1) == 0) return;
   int32_t* owner = sm;             // [ht] a row of the slot's vector, -1 empty
   int32_t* minrow = owner + ht;    // [ht] the first row of the slot's vector
   int32_t* colof = minrow + ht;    // [nq] slot, then column, of each row (-1: none)
@@ -248,6 +252,7 @@ column_table_rebuild_kernel(const float* __restrict__ Qd, const float* __restric
   // a thread per row: linear probing on (hash of the padded row's bits, k <= k_max); a
   // slot's owner is a row of its vector (mode 1: of its bits)
   const int dp4 = dp / 4;
+  const int pass = mode;
   {
     for (int j = tid; j < nq; j += nt) {
       const int k = kk[j];
@@ -264,7 +269,7 @@ column_table_rebuild_kernel(const float* __restrict__ Qd, const float* __restric
           cur = prev;
         }
         bool same = qh[cur] == key && (kk[cur] <= kmax ? 0 : 1) == cls;
-        if (same) {
+        if (same && pass == 1) {
           const uint4* a4 = reinterpret_cast<const uint4*>(Qd + (int64_t)j * dp);
           const uint4* c4 = reinterpret_cast<const uint4*>(Qd + (int64_t)cur * dp);
           for (int i = 0; same && i < dp4; ++i) {
@@ -375,6 +380,23 @@ column_table_rebuild_kernel(const float* __restrict__ Qd, const float* __restric
     T.rows[atomicAdd(&cnt[cc], 1)] = make_int4(j | (sa << 30), k, __float_as_int(pk), 0);
   }
   (void)crep;
+}
+
+// Every row against its column's first row, a 16-byte word per thread: any difference (two
+// vectors that share a hash) raises the table's flag.
+__global__ void column_check_kernel(const float* __restrict__ Qd, int nq, int dp, ColTable T) {
+  const int dp4 = dp / 4;
+  const int64_t total = (int64_t)nq * dp4;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(x / dp4), i = (int)(x - (int64_t)j * dp4);
+    const int c = T.colof[j];
+    if (c < 0) continue;
+    const int r = T.rep[c];
+    if (r == j) continue;
+    const uint4 a = __ldcg(reinterpret_cast<const uint4*>(Qd + (int64_t)j * dp) + i);
+    const uint4 b = __ldcg(reinterpret_cast<const uint4*>(Qd + (int64_t)r * dp) + i);
+    if (a.x != b.x || a.y != b.y || a.z != b.z || a.w != b.w) T.ncol[1] = 1;
+  }
 }
 
 // ---- The grid-wide table build.  col_init_kernel clears the work arrays.
@@ -1584,13 +1606,10 @@ sah_status launch_pass(Index* ix, UpParams p, int sms, cudaStream_t st, int* lau
 //   s - e >= L + E, when L is the exact k-th score (|P'| = n)  -> "yes"
 //   otherwise the pair is re-scored in FP32 (and FP64) by pair_rescore_kernel.
 // L + E is bounded above from L - E - 1e-30 (rounded down) with four units in the last place
-// and 2e-30 to spare.  The kernel is bound by the latency of its dependent gathers (block,
-// then column, then bound and rows), so the loads that do not depend on each other go out
-// together, the column's first row is fetched before its "no" test is known, and the next
-// block's header and score are fetched while the current one is decided.
+// and 2e-30 to spare.
 constexpr int kResolveThreads = 512;
-constexpr int kResolveCtasPerSm = 3;
-__global__ void __launch_bounds__(kResolveThreads, kResolveCtasPerSm)
+constexpr int kResolveCtasPerSm = 2;
+__global__ void __launch_bounds__(kResolveThreads)
 cand_resolve_kernel(const CandBlock* __restrict__ cand, const unsigned long long* __restrict__ cand_count,
                     int64_t cap, ColTable T, const float* __restrict__ Lt, const float* __restrict__ Eu,
                     const float* __restrict__ unorm, const int32_t* __restrict__ uid, int64_t mz, int kmax,
@@ -1612,51 +1631,34 @@ cand_resolve_kernel(const CandBlock* __restrict__ cand, const unsigned long long
   const int lane = threadIdx.x & 31;
   unsigned long long yes_cnt = 0;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int2 hn = make_int2(0, 0);
-  float sn = 0.f;
-  if (b < total) {
-    hn = reinterpret_cast<const int2*>(cand + b)[0];
-    sn = cand[b].s[lane];
-  }
-  for (; b < total; b += nw) {
-    const int64_t r = hn.x;
-    const int c = hn.y + lane;
-    const float s = sn;
-    if (b + nw < total) {   // the next block, while this one is decided
-      hn = reinterpret_cast<const int2*>(cand + b + nw)[0];
-      sn = cand[b + nw].s[lane];
-    }
-    const bool live = c < ncol;
+  for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < total; b += nw) {
+    const int4 h0 = reinterpret_cast<const int4*>(cand + b)[0];
+    const int64_t r = h0.x;
+    const int c = h0.y + lane;
+    const float s = cand[b].s[lane];
     const float nu = unorm[r], E = Eu[r];
     const int32_t uidv = uid[r];
-    float qn = 0.f;
-    int kq = 0, q0 = 0, q1 = 0;
-    if (live) {
-      qn = qnc[c];
-      kq = kqc[c];
-      q0 = start[c];
-      q1 = start[c + 1];
-    }
-    // the column's first row, before its "no" test is known
-    int4 rw0 = make_int4(0, 0, 0, 0);
-    if (q1 > q0) rw0 = rows[q0];
     const float cu = __fmul_ru(cband, nu);
     const float nun = __fmul_ru(nu, 1.f + 2.f * gamma);
+    const bool live = c < ncol;
+    const float qn = live ? qnc[c] : 0.f;
     const float lo = __fsub_rd(s, __fmul_ru(cu, qn) + 1e-30f);
     // the column's own "no" first: its smallest bound belongs to its largest k (bounds fall as
     // k grows); below it, every row of the column is "no"
     // (a column holds rows of k <= k_max only, or rows of k > k_max only, which have no bound)
     bool cand_c = live;
-    if (live && kq > 0)
-      cand_c = !(__fmaf_ru(cu, qn, s) < __fsub_rd(__fsub_rd(Lt[(int64_t)(kq - 1) * mz + r], E), 1e-30f));
+    if (live) {
+      const int kq = kqc[c];
+      if (kq > 0) cand_c = !(__fmaf_ru(cu, qn, s) < __fsub_rd(__fsub_rd(Lt[(int64_t)(kq - 1) * mz + r], E), 1e-30f));
+    }
+    const int q0 = cand_c ? start[c] : 0, q1 = cand_c ? start[c + 1] : 0;
     const int nr = cand_c ? q1 - q0 : 0;
     const int nmax = __reduce_max_sync(0xffffffffu, nr);
     for (int t = 0; t < nmax; ++t) {
       bool open = false;
       int jv = 0;
       if (t < nr) {
-        const int4 rw = t == 0 ? rw0 : rows[q0 + t];
+        const int4 rw = rows[q0 + t];
         const int j = rw.x & 0x3fffffff, k = rw.y;
         jv = rw.x;
         float Lq = -INFINITY;   // L - E - 1e-30 rounded down, or -inf without a bound
@@ -1705,27 +1707,37 @@ sah_status prepare_user_pass_tc(Index* ix, const float* Qd, const float* qn, con
   const ColWork W = col_work_at(T.scratch, nq, ht);
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
-  const unsigned rows_grid = (unsigned)((nq + 255) / 256);
-  col_init_kernel<<<(unsigned)std::max(1, std::min(sms * 4, (ht + 4 * nq + 8 + 255) / 256)), 256, 0, st>>>(W, nq, ht);
-  col_hash_kernel<<<rows_grid, 256, 0, st>>>(qh, kk, nq, ix->kmax, ix->n, ht, W);
-  col_reps_kernel<<<rows_grid, 256, 0, st>>>(kk, nq, ix->kmax, W);
-  const dim3 rank_grid((unsigned)((nq + kRankOwn * kRankThreads - 1) / (kRankOwn * kRankThreads)),
-                       (unsigned)((nq + kRankChunk - 1) / kRankChunk));
-  col_rank_kernel<<<rank_grid, kRankThreads, 0, st>>>(qn, kk, ix->kmax, W);
-  col_place_kernel<<<rows_grid, 256, 0, st>>>(W, T);
-  col_scatter_kernel<<<(unsigned)(sms * 4), 256, 0, st>>>(Qd, kk, modes, ix->kmax, ix->n, ix->pnorm, nq, ix->dp, W, T);
-  // the rebuild (nothing unless the check raised the flag): its work arrays in shared memory
-  // up to 4,096 rows (180 KB), past that all but the sort's (128 KB at 16,384 rows) in the
-  // table's scratch
+  // the single CTA's work arrays: in shared memory up to 4,096 rows (180 KB), past that all
+  // but the sort's (128 KB at 16,384 rows) in the table's scratch (a rebuild only)
   const size_t need = sizeof(int32_t) * (2 * (size_t)ht + 5 * (size_t)nq + 2 * (size_t)npow);
   const int in_global = need > 200 * 1024 ? 1 : 0;
   const size_t tsmem = in_global ? sizeof(int32_t) * 2 * (size_t)npow : need;
-  SAH_TRY(raise_smem_limit((const void*)column_table_rebuild_kernel, tsmem));
-  column_table_rebuild_kernel<<<1, 1024, tsmem, st>>>(Qd, qn, qh, nq, ix->dp, kk, modes, ix->kmax, ix->n, ix->pnorm,
-                                                       ht, npow, T, in_global);
+  SAH_TRY(raise_smem_limit((const void*)column_table_cta_kernel, tsmem));
+  if (nq <= kSmallTable) {
+    column_table_cta_kernel<<<1, 1024, tsmem, st>>>(Qd, qn, qh, nq, ix->dp, kk, modes, ix->kmax, ix->n, ix->pnorm,
+                                                     ht, npow, T, 0, in_global);
+    column_check_kernel<<<sms, 512, 0, st>>>(Qd, nq, ix->dp, T);
+    if (launches) *launches += 2;
+  } else {
+    const unsigned rows_grid = (unsigned)((nq + 255) / 256);
+    col_init_kernel<<<(unsigned)std::max(1, std::min(sms * 4, (ht + 4 * nq + 8 + 255) / 256)), 256, 0, st>>>(W, nq,
+                                                                                                            ht);
+    col_hash_kernel<<<rows_grid, 256, 0, st>>>(qh, kk, nq, ix->kmax, ix->n, ht, W);
+    col_reps_kernel<<<rows_grid, 256, 0, st>>>(kk, nq, ix->kmax, W);
+    const dim3 rank_grid((unsigned)((nq + kRankOwn * kRankThreads - 1) / (kRankOwn * kRankThreads)),
+                         (unsigned)((nq + kRankChunk - 1) / kRankChunk));
+    col_rank_kernel<<<rank_grid, kRankThreads, 0, st>>>(qn, kk, ix->kmax, W);
+    col_place_kernel<<<rows_grid, 256, 0, st>>>(W, T);
+    col_scatter_kernel<<<(unsigned)(sms * 4), 256, 0, st>>>(Qd, kk, modes, ix->kmax, ix->n, ix->pnorm, nq, ix->dp, W,
+                                                            T);
+    if (launches) *launches += 6;
+  }
+  // the rebuild (nothing unless a check raised the flag)
+  column_table_cta_kernel<<<1, 1024, tsmem, st>>>(Qd, qn, qh, nq, ix->dp, kk, modes, ix->kmax, ix->n, ix->pnorm, ht,
+                                                   npow, T, 1, in_global);
   column_transpose_kernel<<<sms, 512, 0, st>>>(Qd, qn, nq, ix->dp, T);
   SAH_CUDA(cudaGetLastError());
-  if (launches) *launches += 8;
+  if (launches) *launches += 2;
   if (ix->prm.tc_user_pass == 2) {
     // the FP8 user pass: every row of the sub-batch in E4M3 with its scale
     launch_e4m3_rows(Qd, nq, ix->dp, ix->d, T.q8, T.qsc, st);

@@ -295,14 +295,15 @@ def test_sub_batch_past_shared_memory_column_table(sah, variant, p_prime):
 
 
 @pytest.mark.parametrize("variant", ["bf16-tc", "fp8-tc"])
-def test_hash_collisions_rebuild_the_column_table(sah, variant):
+@pytest.mark.parametrize("nrows", [400, 2100])             # the one-CTA and the grid-wide build
+def test_hash_collisions_rebuild_the_column_table(sah, variant, nrows):
     """Every row given one hash: the bitwise check finds the different vectors sharing a
     column and the table is built again comparing whole vectors, with unchanged answers."""
     W = workload.make("c2", m=5000, n=2000)
     ix = sah.Index(W.U, W.P, k_max=50, leaf_size=128, p_prime=1 << 30, seed=5, **VARIANTS[variant])
     rng = np.random.default_rng(8)
     vecs = W.P[rng.choice(W.n, 150, replace=False)]
-    pick = rng.integers(0, 150, 400)                       # 150 vectors, most asked several times
+    pick = rng.integers(0, 150, nrows)                     # 150 vectors, most asked several times
     Q = vecs[pick]
     K = rng.choice(np.array([1, 3, 10, 50, 60], np.int32), len(pick))
     plain = ix.rkmips_batch(Q, K)
