@@ -12,20 +12,19 @@
 // grid-wide kernels do (a single CTA's sort and probes would take longer than the rest of
 // the table).
 //
-// Operands.  BF16 alone carries 8 significant bits, which makes the score's error band
-// (about 2^-7 ||u|| ||q||) so wide that many pairs would stay open.  Every FP32 vector x
-// is therefore split into x_hi = bf16(x) and x_lo = bf16(x - x_hi) (x - x_hi is exact in
-// FP32), and the MMA accumulates the three products that matter over a K three times as
-// long:  u_hi q_hi + u_hi q_lo + u_lo q_hi.  Per coordinate the dropped parts are bounded
-// by 3 * 2^-16 |u_i q_i| (u_lo q_lo and the two second-level rounding residues), so with
-// the FP32 accumulation of 3K products
-//   |s_tc - <u,q>| <= c_tc ||u|| ||q||,   c_tc = 1.01 (3 * 2^-16 + (6K + 16) 2^-23),
-// where the accumulation term lets every addition inside the tensor core lose up to two
-// units in the last place (no rounding mode is assumed).  That is about 1e-4 relative:
-// the band holds few pairs.
+// Operands.  The users' rows and the column vectors are BF16 (8 significant bits), one
+// product per score, accumulated in FP32 over K = dk:
+//   |s_tc - <u,q>| <= c_bf ||u|| ||q||,   c_bf = 1.01 (2^-7 + 2^-16 + (2 dk + 16) 2^-23),
+// the two roundings to BF16, the FP32 rounding of the inputs and an accumulation in which
+// every addition may lose up to two units in the last place (no rounding mode is assumed).
+// The kernel also takes split operands (x_hi = bf16(x), x_lo = bf16(x - x_hi), three
+// products u_hi q_hi + u_hi q_lo + u_lo q_hi, a band near 1e-4): measured, the lo stream
+// doubled the traffic and cost more MMA time than the narrower band saved in re-scores.
+// With tc_user_pass = 2 the operands are E4M3 with a scale per row (kind::f8f6f4) and the
+// band c_8 = 0.130.
 //
 // Tests per (user, row) whose leaf the node-level bound (Lemma 2) kept, with L = L_u^k,
-// E the error of L, and the band e = c_tc ||u|| ||q||:
+// E the error of L, and the band e = c ||u|| ||q||:
 //   s + e <  L - E                                            -> "no" (k items beat <u,q>)
 //   s - e >= L + E, when L is the exact k-th score (|P'| = n)  -> "yes"
 //   s - e >= ||u|| ||p_k|| (1 + 2 gamma)                       -> "yes" (Alg. 5)
@@ -36,18 +35,24 @@
 // vector-level bound) is not applied: with the score from the tensor cores it would cost
 // more than it saves.
 //
-// Kernel shape: one persistent launch per sub-batch, one CTA per SM, 320 threads, looping
-// over chunks of up to 256 columns.  Two groups of four epilogue warps (2-5, 6-9) take
-// alternate 128-user tiles; each group owns a TMA stage and two TMEM slots, so the two
-// pipelines never wait on each other.  One thread of warp 0 streams the tiles (hi and lo
-// K-blocks) for both groups and one thread of warp 1 issues both groups' MMAs, each in a
-// loop that polls the barriers without blocking on either group.  A chunk of up to 128
-// columns puts a group's consecutive tiles into its two slots in turn, so the next tile's
-// MMA runs while the current one is read; a wider chunk uses the two slots as halves of a
-// tile.  An epilogue warp (one user per lane) keeps its users' lower bounds for the
-// chunk's distinct k in shared memory and reads its TMEM lanes 32 columns at a time: one
-// fused multiply-add and one compare per column find the users a column can concern;
-// only those take the per-row tests.
+// Column prefixes.  The columns are sorted by descending ||q||, and every 128-user tile has
+// a bound tile_lb^k = min over its users of (L_u^k - E_u) / ||u||.  A column can pass a
+// user's fast test only if (1 + 2c) ||u|| ||q|| >= L_u^k - E_u, so a tile needs only the
+// prefix of a column set whose norms reach tile_lb^K times a rounding margin (K the set's
+// largest k); every other pair is "no" by Cauchy-Schwarz.  A tile with an empty prefix is
+// not loaded, and a set that no tile of the CTA needs is skipped.
+//
+// Kernel shape: one persistent launch per sub-batch, one CTA per SM, 352 threads.  Warp 0
+// streams the CTA's needed user tiles by TMA through a ring of stages; warp 1 issues the
+// MMAs (M = 128 users, N = the tile's prefix within a TMEM slot of up to 256 columns); warps
+// 2-9 are the epilogue, two groups of four that take the slots alternately, one user per
+// lane; warp 10 copies the next tiles' bounds into a shared-memory ring with cp.async.  A
+// column set of up to 512 columns stays in shared memory as the B operand.  The epilogue
+// reads its TMEM lanes 64 columns at a time and runs the fast test per group of 32 columns
+// (the group's largest score against the bound of the group's largest k, less the group's
+// band); with exact thresholds it only marks the groups some user passes, and a rare loop
+// reads those again and writes candidate blocks for cand_resolve_kernel; with the paper's
+// |P'| the candidates are resolved in the epilogue itself.
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
