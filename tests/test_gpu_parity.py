@@ -315,3 +315,24 @@ def test_hash_collisions_rebuild_the_column_table(sah, variant, nrows):
     for j in rng.choice(len(K), 8, replace=False):
         c = oracle.count_above(W.U, W.P, Q[j])
         assert np.array_equal(plain[j], np.flatnonzero(c < K[j]).astype(np.int32)), j
+
+
+def test_tensor_core_call_over_several_sub_batches(sah):
+    """20,000 rows in one call take two sub-batches of the tensor-core path (16,384 + 3,616
+    rows, the second built by the grid-wide column table): the answers equal those of the
+    same rows asked in calls of 5,000, and a sample agrees with the oracle."""
+    W = workload.make("c2", m=6000, n=2500)
+    ix = sah.Index(W.U, W.P, k_max=50, leaf_size=128, p_prime=1 << 30, seed=4, **VARIANTS["bf16-tc"])
+    rng = np.random.default_rng(33)
+    nrow = 20000
+    Q = W.P[rng.integers(0, W.n, nrow)]
+    K = rng.choice(np.array([1, 5, 10, 50, 51, W.n + 1], np.int32), nrow)
+    whole = ix.rkmips_batch(Q, K)
+    parts = []
+    for a in range(0, nrow, 5000):
+        parts += ix.rkmips_batch(Q[a:a + 5000], K[a:a + 5000])
+    for j in range(nrow):
+        assert np.array_equal(whole[j], parts[j]), j
+    for j in rng.choice(nrow, 16, replace=False):
+        c = oracle.count_above(W.U, W.P, Q[j])
+        assert np.array_equal(whole[j], np.flatnonzero(c < K[j]).astype(np.int32)), (j, int(K[j]))
